@@ -1,0 +1,198 @@
+/*
+ * fdcore -- GB300 (sm_103a) library for batched Monte Carlo evaluation of
+ * compiled self-energy Feynman graphs (arXiv 2403.18840).
+ *
+ * The paper states the problem as I_f = int dx f(x) over the unit hypercube
+ * (Sec. IV) with f the order-n self-energy integrand (Sec. II.A, Eq.
+ * sigma_integration) and its counterterm derivatives Sigma^(n,m,l)
+ * (Sec. VI.A, Eq. sigma_xi_dmu_dlambda).  This header is the whole boundary:
+ * plain pointers and sizes, no framework types.
+ *
+ * Conventions shared by every call
+ *  - Device buffers are owned by the caller and passed as raw device pointers;
+ *    `stream` is a cudaStream_t cast to void* (NULL = legacy default stream).
+ *  - Opaque handles are owned by the library (create/free pairs).
+ *  - Calls are asynchronous on `stream` unless stated otherwise.
+ *  - No exception crosses the boundary: every failure returns a status other
+ *    than FD_OK and sets a thread-local message readable by fd_last_error().
+ *    Arguments are validated before any launch; on error nothing is launched.
+ *  - Hypercube points are structure-of-arrays: x[d * n + i] for dimension d
+ *    and sample i (FP32).
+ *  - Units: Rydberg, hbar^2/2m = 1, e^2 = 2: eps_k = k^2 - mu and
+ *    V(q) = 8 pi / (q^2 + Lambda) (Eq. ueg_action with Yukawa screening,
+ *    Eq. interaction_ct).
+ */
+#ifndef FDCORE_H
+#define FDCORE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FD_OK = 0,
+    FD_EINVAL = 1,    /* bad argument (null pointer, size, range, NaN parameter) */
+    FD_EFORMAT = 2,   /* malformed graph tape */
+    FD_ENOMEM = 3,    /* device or host allocation failed */
+    FD_ECUDA = 4,     /* CUDA runtime error */
+    FD_ETIMEOUT = 5,  /* a bounded device wait gave up (kernel returned early) */
+    FD_ENOTSUP = 6    /* valid request this build does not support */
+} fd_status;
+
+typedef struct fd_graph fd_graph;
+typedef struct fd_vegas fd_vegas;
+typedef struct fd_flow fd_flow;
+
+/* Physical parameters of one instance (Sec. VI.A).  k_ext: external momentum
+ * |k| (along z); mu: renormalised chemical potential mu_R = E_F; beta = 1/T;
+ * Lambda: Yukawa screening lambda^2; k_cut: radius cutoff of every loop
+ * momentum.  k_F is informational (post-processing uses it). */
+typedef struct {
+    double k_ext, k_F, mu, beta, Lambda, k_cut;
+    int32_t order;   /* must equal the order of the instance's graph */
+    int32_t reserved;
+} fd_params;
+
+/* Sample-tile size of the reduction: partial sums are kept per instance and
+ * per tile of this many consecutive samples. */
+#define FD_TILE_SAMPLES 16384
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *fd_last_error(void);
+
+/* ---- graphs (Sec. V.A: the compiled computational graph) -----------------
+ * fd_graph_load parses and validates a tape produced by the graph compiler
+ * (format in paper_2403_18840_gb300/fdgraph.py: header, root table
+ * (n, m, l, dk) per root, 64-bit instructions), checks every slot index and
+ * opcode against the declared sizes, and uploads it to the current device.
+ * Synchronous.  FD_EFORMAT on any inconsistency; the buffer is not retained. */
+fd_status fd_graph_load(const void *buf, size_t len, fd_graph **out);
+/* n_roots: number of roots; dim: hypercube dimension 4N-1; n_instr: tape
+ * length; n_slots: per-sample state size in 4-byte slots. Any pointer may be NULL. */
+fd_status fd_graph_info(const fd_graph *g, int32_t *n_roots, int32_t *dim,
+                        int64_t *n_instr, int32_t *n_slots);
+/* roots[4*r + {0,1,2,3}] = (n, m, l, dk) of root r (host array of 4*n_roots). */
+fd_status fd_graph_roots(const fd_graph *g, int32_t *roots);
+void fd_graph_free(fd_graph *g);
+
+/* ---- VEGAS map (Sec. IV, separable map q(x) = prod q_k(x_k)) ---------------
+ * A map owns FP64 bin edges [dim][n_bins+1] (uniform at creation), their FP32
+ * copy used by the sampling kernels, and an FP64 training histogram
+ * [dim][n_bins] that fd_integrand_eval accumulates (sum of (f J)^2 per bin)
+ * and fd_vegas_update consumes.  create/free/set/get are synchronous. */
+fd_status fd_vegas_create(int32_t dim, int32_t n_bins, fd_vegas **out);
+void fd_vegas_free(fd_vegas *m);
+/* host FP64 edges [dim][n_bins+1]; must be strictly increasing from 0 to 1 */
+fd_status fd_vegas_set_edges(fd_vegas *m, const double *edges);
+fd_status fd_vegas_get_edges(const fd_vegas *m, double *edges);
+/* host FP64 copy of the histogram [dim][n_bins] */
+fd_status fd_vegas_get_hist(const fd_vegas *m, double *hist);
+/* overwrite the histogram from host FP64 [dim][n_bins] (entries >= 0) */
+fd_status fd_vegas_set_hist(fd_vegas *m, const double *hist);
+/* zero the histogram (async) */
+fd_status fd_vegas_clear_hist(fd_vegas *m, void *stream);
+/* Lepage's update (3-point smoothing, damping exponent alpha, equal-share
+ * redistribution of the edges) in FP64 on the device, then zero the
+ * histogram. */
+fd_status fd_vegas_update(fd_vegas *m, double alpha, void *stream);
+
+/* ---- sample generation ---------------------------------------------------
+ * Philox4x32-10 stream of sample i of instance `inst` at iteration `iter`:
+ * counter (i_lo, i_hi, iter, (inst << 8) | block), key (seed_lo, seed_hi);
+ * u = ((w >> 9) + 0.5) 2^-23.  map == NULL: x = u, w = 1; otherwise the VEGAS
+ * map, w = its Jacobian.  x: device [dim][n], w: device [n] (may be NULL).
+ * dim must equal the map's dimension when map != NULL. */
+fd_status fd_map_samples(const fd_vegas *map, uint64_t seed, uint64_t iter, int32_t inst,
+                         int64_t n, int32_t dim, float *x, float *w, void *stream);
+
+/* ---- integrand evaluation (Eqs. sigma_integration, sigma_xi_dmu_dlambda) --
+ * One launch over n_inst instances; instance j evaluates graph
+ * graphs[graph_of_inst[j]] with params[j] on n_per_inst samples drawn as in
+ * fd_map_samples with maps[j] (NULL entry = identity) -- or, when `points`
+ * is not NULL, on the given points instead (points: device
+ * [n_inst][dim_max][n_per_inst] with dim_max the largest graph dimension,
+ * point_w: device [n_inst][n_per_inst] sample weights).
+ * For each sample and root r it computes
+ *   f_r = w * J(x) * sum_t s_t d^m_mu d^l_Lambda (d_k)^dk [prod G0 prod V] e^{i pi x_out}
+ * in FP32 (J: loop-momentum and time Jacobians of the roots' own variables).
+ * Outputs
+ *  partials (device, required): FP64 [n_inst][n_tiles][R_max][2][2] with
+ *    n_tiles = ceil(n_per_inst / FD_TILE_SAMPLES), R_max the largest root
+ *    count; entry (.., r, c, 0) = sum of f (c = 0 real, 1 imaginary) over the
+ *    tile, (.., r, c, 1) = sum of f^2.  Tiles are summed in a fixed order
+ *    inside the tile, so results are bitwise reproducible.
+ *  per_sample_f (device, optional): FP32 [n_inst][R_max][2][n_per_inst].
+ *  VEGAS maps (when given and `points` is NULL) accumulate their histograms.
+ * params and graph_of_inst are host arrays; graphs/maps host arrays of handles.
+ * FD_ETIMEOUT if a bounded wait for a tape copy gave up. */
+fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_graphs,
+                            const fd_params *params, const int32_t *graph_of_inst,
+                            int32_t n_inst, fd_vegas *const *maps, const float *points,
+                            const float *point_w, uint64_t seed, uint64_t iter,
+                            int64_t n_per_inst, double *partials, float *per_sample_f,
+                            void *stream);
+
+/* Synchronise `stream`; FD_ETIMEOUT if a kernel recorded a bounded wait
+ * that gave up since the last call (the record is cleared). */
+fd_status fd_device_status(void *stream);
+
+/* Number of doubles of the `partials` buffer for this launch shape. */
+int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_per_inst);
+
+/* ---- reduction (FP64, fixed order) ---------------------------------------
+ * From partials [n_inst][n_tiles][r_max][2][2] compute, per instance, root
+ * and real/imaginary part, the mean and the variance of the mean over
+ * n_per_inst samples: out (device) [n_inst][r_max][2][2] = (mean, var).
+ * Tiles are combined in index order with Neumaier compensation. */
+fd_status fd_accumulate(const double *partials, int32_t n_inst, int32_t r_max,
+                        int64_t n_per_inst, double *out, void *stream);
+
+/* ---- affine coupling flow (Appendix A, Eqs. NFtransform, coupling_layer) --
+ * A flow of n_layers affine coupling layers over [0,1]^dim in logit space,
+ * each conditioned by an MLP (in -> hidden -> hidden -> out, ReLU), BF16
+ * weights/activations on tensor cores with FP32 accumulation, FP32 master
+ * weights and Adam state.  Parameter blob layout (FP32, host): per layer
+ * W1 [H][a], b1 [H], W2 [H][H], b2 [H], W3 [2b][H], b3 [2b] with a/b the
+ * sizes of the conditioning/transformed halves (first ceil(dim/2)
+ * coordinates condition on even layers). */
+fd_status fd_flow_create(int32_t dim, int32_t n_layers, int32_t hidden, uint64_t seed,
+                         fd_flow **out);
+void fd_flow_free(fd_flow *f);
+int64_t fd_flow_param_count(const fd_flow *f);
+fd_status fd_flow_set_params(fd_flow *f, const float *blob, int64_t n);
+fd_status fd_flow_get_params(const fd_flow *f, float *blob, int64_t n);
+/* z ~ U(0,1)^dim from the Philox stream (as fd_map_samples), x = T(z) and
+ * w = 1/q(x).  x: device [dim][n], w: device [n]. */
+fd_status fd_flow_sample(const fd_flow *f, uint64_t seed, uint64_t iter, int32_t inst,
+                         int64_t n, float *x, float *w, void *stream);
+/* log q(x) for given points (inverse pass).  x: device [dim][n], logq: device [n]. */
+fd_status fd_flow_log_density(const fd_flow *f, const float *x, int64_t n, float *logq,
+                              void *stream);
+/* Weighted forward-KL loss L = -sum w log q(x) / sum w and its gradient in
+ * blob layout.  x: device [dim][n]; w: device [n] (>= 0); loss: device [1];
+ * grad: device [param_count]. */
+fd_status fd_flow_grad(fd_flow *f, const float *x, const float *w, int64_t n, float *loss,
+                       float *grad, void *stream);
+/* `steps` Adam steps (lr, beta = (0.9, 0.999), eps = 1e-8) on the batch
+ * (x, w).  loss_out: host array [steps] of losses (synchronous readback at
+ * the end), may be NULL. */
+fd_status fd_flow_train(fd_flow *f, const float *x, const float *w, int64_t n, int32_t steps,
+                        float lr, float *loss_out, void *stream);
+
+/* ---- renormalisation post-processing (host, FP64; Sec. VI.A) -------------
+ * sigma_re/sigma_im/dsigma_re: FP64 [N+1][N+1][N+1] indexed (n, m, l) holding
+ * Sigma^(n,m,l)(k_F, i w0) and d_k Re Sigma^(n,m,l) for n + m + l <= N.
+ * Solves dmu(xi) = Re Sigma(xi)|_FS order by order and returns the xi-series
+ * coefficients dmu, a, b [N+1] and partial sums meff [N+1] of the series of
+ * (1 - b) / (1 + a) (Eq. eff_mass_ratio).  Synchronous, host memory only. */
+fd_status fd_postprocess(int32_t N, const double *sigma_re, const double *sigma_im,
+                         const double *dsigma_re, double k_F, double beta, double Lambda,
+                         double *dmu, double *a, double *b, double *meff);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDCORE_H */

@@ -1,0 +1,182 @@
+"""Thin Python layer over the fdcore C-ABI: handles, device buffers and streams.
+
+Every computation runs in the library's kernels; this module only prepares
+arguments (torch supplies device memory and streams) and owns handles.
+"""
+import ctypes
+import hashlib
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import fdgraph
+
+_TAPE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tapes")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def ueg_params(order, rs, T_over_TF, lam_over_kF, kext_over_kF, kc_over_kF=6.0):
+    """fd_params of one instance (Rydberg units, eps = k^2 - mu, V = 8 pi/(q^2 + Lambda))."""
+    kF = (9.0 * math.pi / 4.0) ** (1.0 / 3.0) / rs
+    EF = kF * kF
+    p = L.fd_params()
+    p.k_ext = kext_over_kF * kF
+    p.k_F = kF
+    p.mu = EF
+    p.beta = 1.0 / (T_over_TF * EF)
+    p.Lambda = (lam_over_kF * kF) ** 2
+    p.k_cut = kc_over_kF * kF
+    p.order = order
+    return p
+
+
+def tape_bytes(order, roots):
+    """Compiled tape for (order, roots), cached on disk by compiler source hash."""
+    src = open(fdgraph.__file__, "rb").read()
+    key = hashlib.sha1(src + repr((order, list(roots))).encode()).hexdigest()[:16]
+    path = os.path.join(_TAPE_DIR, "tape_o%d_%s.bin" % (order, key))
+    if os.path.exists(path):
+        return open(path, "rb").read()
+    data = fdgraph.compile_graph(order, roots).to_bytes()
+    os.makedirs(_TAPE_DIR, exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "wb") as f:
+        f.write(data)
+    os.replace(tmp, path)
+    return data
+
+
+class Graph:
+    """A compiled self-energy graph loaded on the current device."""
+
+    def __init__(self, order, roots=None, with_dk=False, tape=None):
+        self.order = order
+        self.roots = list(roots) if roots is not None else fdgraph.graph_roots(order, with_dk)
+        data = tape if tape is not None else tape_bytes(order, self.roots)
+        self._buf = ctypes.create_string_buffer(data, len(data))
+        h = ctypes.c_void_p()
+        L.check(L.lib().fd_graph_load(self._buf, len(data), ctypes.byref(h)))
+        self.handle = h
+        nr, dim, ns = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ni = ctypes.c_int64()
+        L.check(L.lib().fd_graph_info(h, ctypes.byref(nr), ctypes.byref(dim), ctypes.byref(ni), ctypes.byref(ns)))
+        self.n_roots, self.dim, self.n_instr, self.n_slots = nr.value, dim.value, ni.value, ns.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.fd_graph_free(h)
+            self.handle = None
+
+
+class Vegas:
+    """VEGAS map of one instance (FP64 edges on the device)."""
+
+    def __init__(self, dim, n_bins=1024):
+        h = ctypes.c_void_p()
+        L.check(L.lib().fd_vegas_create(dim, n_bins, ctypes.byref(h)))
+        self.handle, self.dim, self.n_bins = h, dim, n_bins
+
+    def set_edges(self, edges):
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        assert e.shape == (self.dim, self.n_bins + 1)
+        L.check(L.lib().fd_vegas_set_edges(self.handle, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def edges(self):
+        e = np.empty((self.dim, self.n_bins + 1))
+        L.check(L.lib().fd_vegas_get_edges(self.handle, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return e
+
+    def hist(self):
+        h = np.empty((self.dim, self.n_bins))
+        L.check(L.lib().fd_vegas_get_hist(self.handle, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return h
+
+    def set_hist(self, hist):
+        h = np.ascontiguousarray(hist, dtype=np.float64)
+        assert h.shape == (self.dim, self.n_bins)
+        L.check(L.lib().fd_vegas_set_hist(self.handle, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def clear(self, stream=None):
+        L.check(L.lib().fd_vegas_clear_hist(self.handle, _stream_ptr(stream)))
+
+    def update(self, alpha=0.5, stream=None):
+        L.check(L.lib().fd_vegas_update(self.handle, alpha, _stream_ptr(stream)))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.fd_vegas_free(h)
+            self.handle = None
+
+
+def map_samples(vegas, seed, it, inst, n, dim, stream=None):
+    x = torch.empty((dim, n), dtype=torch.float32, device="cuda")
+    w = torch.empty((n,), dtype=torch.float32, device="cuda")
+    L.check(L.lib().fd_map_samples(vegas.handle if vegas else None, seed, it, inst, n, dim, _ptr(x), _ptr(w),
+                                   _stream_ptr(stream)))
+    return x, w
+
+
+class EvalPlan:
+    """Launch description of one batched fd_integrand_eval call (reusable buffers)."""
+
+    def __init__(self, graphs, params, graph_of_inst, n_per_inst, maps=None, per_sample=False):
+        self.graphs = list(graphs)
+        self.n_inst = len(params)
+        self.n_per_inst = int(n_per_inst)
+        self.r_max = max(g.n_roots for g in self.graphs)
+        self.dim_max = max(g.dim for g in self.graphs)
+        self._g = (ctypes.c_void_p * len(self.graphs))(*[g.handle for g in self.graphs])
+        self._p = (L.fd_params * self.n_inst)(*params)
+        self._gi = (ctypes.c_int32 * self.n_inst)(*graph_of_inst)
+        self.maps = maps
+        self._m = None
+        if maps is not None:
+            self._m = (ctypes.c_void_p * self.n_inst)(*[m.handle if m is not None else None for m in maps])
+        cnt = L.lib().fd_partials_count(self.n_inst, self.r_max, self.n_per_inst)
+        self.partials = torch.zeros(cnt, dtype=torch.float64, device="cuda")
+        self.stats = torch.zeros((self.n_inst, self.r_max, 2, 2), dtype=torch.float64, device="cuda")
+        self.per_sample = None
+        if per_sample:
+            self.per_sample = torch.zeros((self.n_inst, self.r_max, 2, self.n_per_inst), dtype=torch.float32,
+                                          device="cuda")
+
+    def run(self, seed, it, points=None, point_w=None, stream=None):
+        L.check(L.lib().fd_integrand_eval(self._g, len(self.graphs), self._p, self._gi, self.n_inst, self._m,
+                                          _ptr(points), _ptr(point_w), seed, it, self.n_per_inst,
+                                          _ptr(self.partials), _ptr(self.per_sample), _stream_ptr(stream)))
+        L.check(L.lib().fd_accumulate(_ptr(self.partials), self.n_inst, self.r_max, self.n_per_inst,
+                                      _ptr(self.stats), _stream_ptr(stream)))
+        return self.stats
+
+
+def device_status(stream=None):
+    L.check(L.lib().fd_device_status(_stream_ptr(stream)))
+
+
+def postprocess(N, sigma, dsigma, kF, beta, Lam):
+    """Host FP64 post-process: dict (n,m,l)->complex estimates -> dmu, a, b, meff series."""
+    shape = (N + 1, N + 1, N + 1)
+    sre, sim, dre = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+    for (n, m, l), v in sigma.items():
+        sre[n, m, l], sim[n, m, l] = complex(v).real, complex(v).imag
+    for (n, m, l), v in dsigma.items():
+        dre[n, m, l] = complex(v).real
+    outs = [np.zeros(N + 1) for _ in range(4)]
+    P = ctypes.POINTER(ctypes.c_double)
+    L.check(L.lib().fd_postprocess(N, sre.ctypes.data_as(P), sim.ctypes.data_as(P), dre.ctypes.data_as(P), kF,
+                                   beta, Lam, *[o.ctypes.data_as(P) for o in outs]))
+    return dict(zip(("dmu", "a", "b", "meff"), outs))

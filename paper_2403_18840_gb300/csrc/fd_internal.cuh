@@ -1,0 +1,161 @@
+// Internal definitions shared by the fdcore translation units (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/fdcore.h"
+
+// ---- error plumbing ---------------------------------------------------------
+namespace fd {
+
+fd_status set_error(fd_status st, const std::string &msg);
+fd_status cuda_error(cudaError_t e, const char *what);
+
+#define FD_CHECK_CUDA(call)                                     \
+    do {                                                        \
+        cudaError_t e__ = (call);                               \
+        if (e__ != cudaSuccess) return ::fd::cuda_error(e__, #call); \
+    } while (0)
+
+#define FD_REQUIRE(cond, msg)                                   \
+    do {                                                        \
+        if (!(cond)) return ::fd::set_error(FD_EINVAL, (msg));  \
+    } while (0)
+
+// device-side status word (one per device, zero when healthy)
+int *device_status_word();
+
+}  // namespace fd
+
+// ---- tape format (mirrors paper_2403_18840_gb300/fdgraph.py) -------------------
+enum : uint32_t {
+    OP_MOM = 1,
+    OP_FERMI = 2,
+    OP_GLEAF = 3,
+    OP_VLEAF = 4,
+    OP_MUL = 5,
+    OP_FMA = 6,
+    OP_ADD = 7,
+    OP_MULC = 8,
+    OP_ROOT = 9,
+    OP_ROOT0 = 10,
+    OP_CONST = 11,
+    OP_END = 63,
+};
+
+constexpr uint32_t TAPE_MAGIC = 0x50544446u;  // 'FDTP'
+constexpr uint32_t TAPE_VERSION = 1;
+constexpr int FD_MAX_ORDER = 6;
+constexpr int FD_MAX_DIM = 4 * FD_MAX_ORDER - 1;
+constexpr int FD_MAX_M = 7;         // largest Taylor order of a leaf family (incl. d/dk)
+constexpr int FD_MAX_INST = 256;    // instances per launch (kernel-parameter descriptors)
+
+struct TapeHeader {
+    uint32_t magic, version, order, dim, n_roots, n_slots, n_instr, root_off, instr_off,
+        total_bytes, n_mom, n_g, n_v, n_arith, r0, r1;
+};
+
+__host__ __device__ inline uint32_t ins_op(uint64_t w) { return (uint32_t)(w & 63u); }
+__host__ __device__ inline uint32_t ins_d(uint64_t w) { return (uint32_t)((w >> 6) & 8191u); }
+__host__ __device__ inline uint32_t ins_a(uint64_t w) { return (uint32_t)((w >> 19) & 8191u); }
+__host__ __device__ inline uint32_t ins_b(uint64_t w) { return (uint32_t)((w >> 32) & 8191u); }
+__host__ __device__ inline uint32_t ins_c(uint64_t w) { return (uint32_t)((w >> 45) & 8191u); }
+__host__ __device__ inline uint32_t ins_imm(uint64_t w) { return (uint32_t)((w >> 58) & 63u); }
+__host__ __device__ inline uint32_t ins_hi(uint64_t w) { return (uint32_t)(w >> 32); }
+
+struct fd_graph {
+    int device;
+    TapeHeader hdr;
+    uint64_t *d_tape;            // device copy of the instruction words (16-byte aligned)
+    uint32_t *d_roots;           // device root table: (n | m<<8 | l<<16 | dk<<24, re | im<<16)
+    uint32_t h_roots[2 * 256];
+};
+
+struct fd_vegas {
+    int device;
+    int dim, n_bins;
+    double *d_edges;   // [dim][n_bins+1]
+    float *d_edges32;  // [dim][n_bins+1]
+    double *d_hist;    // [dim][n_bins]
+};
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) ----------------------------------------
+struct u32x4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// u = ((w >> 9) + 0.5) * 2^-23, exact in FP32, strictly inside (0, 1)
+__device__ __forceinline__ float word_to_uniform(uint32_t w) {
+    return __uint2float_rn(w >> 9) * 1.1920928955078125e-07f + 5.9604644775390625e-08f;
+}
+
+// ---- bounded mbarrier / bulk-copy helpers (inline PTX) ----------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared through the TMA engine, completing on `bar`.
+// dst/src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`; gives up after `limit` polls (returns false).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbarrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// status codes written to the device status word
+constexpr int DEV_ST_TIMEOUT = 1;
