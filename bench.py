@@ -1,0 +1,291 @@
+"""Benchmark: integrand evaluations per second at order 5 (VEGAS sampler) on GB300.
+
+One step = one VEGAS iteration of the order-5 self-energy graph (r_s = 1,
+k = k_F, 15 roots Sigma^(n,m,l) with n + m + l = 5, 2^24 samples): Philox ->
+VEGAS map -> loop momenta / times -> leaf families -> tape contraction ->
+FP64 tile partials and VEGAS histogram (one kernel), then the fixed-order
+reduction and the FP64 grid update (two kernels).  Inputs are generated on the
+device; L2 is flushed (a 256 MiB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.  Under torchrun (N > 1) every
+rank runs an independent replica with its own Philox instance index (weak
+scaling, no data-path collective); rank 0 prints.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+WL = workloads.BENCH_ORDER5
+METRIC = "integrand evals/s at order 5 (VEGAS)"
+UNIT = "samples/s"
+
+
+def _parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--samples", type=int, default=WL["n_samples"])
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path))
+    return {}
+
+
+def fp32_peak_tflops(n_sm, mhz):
+    """Non-tensor FP32 peak: 128 FP32 lanes per SM, FMA = 2 flops."""
+    return n_sm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def sfu_peak_tops(n_sm, mhz, per_clk=16):
+    """Special-function unit (MUFU) peak: per_clk results per SM per clock."""
+    return n_sm * per_clk * mhz * 1e6 / 1e12
+
+
+def cpu_baseline(n_sample=48, budget_s=20.0):
+    """The FP64 oracle (as it stands) on a bounded sample of the same workload."""
+    from oracle import conventions, integrand, philox
+    order = WL["order"]
+    P = conventions.ueg_params(WL["rs"], WL["T_over_TF"], WL["lam_over_kF"], WL["kext_over_kF"])
+    roots = integrand.graph_roots(order)
+    integrand.eval_roots(philox.uniforms(WL["seed"], 0, 0, np.arange(2), 4 * order - 1), roots, P)  # warm caches
+    done, t0 = 0, time.perf_counter()
+    while done == 0 or (time.perf_counter() - t0 < budget_s and done < 4 * n_sample):
+        x = philox.uniforms(WL["seed"], 0, 0, np.arange(done, done + n_sample), 4 * order - 1)
+        integrand.eval_roots(x, roots, P)
+        done += n_sample
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d order-5 samples (15 roots, 2232 diagrams each), single-threaded numpy FP64" % done,
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline()
+    steps_done = []
+    for _ in range(args.warmup):
+        cpu_baseline(n_sample=16, budget_s=1.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        steps_done.append(cpu_baseline(n_sample=16, budget_s=2.0)["value"])
+    dt = time.perf_counter() - t0
+    value = float(np.mean(steps_done))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WL["name"], "order": WL["order"], "rs": WL["rs"],
+                                            "kext_over_kF": WL["kext_over_kF"], "roots": 15,
+                                            "step": "bounded CPU sample of the order-5 workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "16 samples per step, oracle FP64 single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "reference_full_sample": cb}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2403_18840_gb300 import api, fdgraph
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    order = WL["order"]
+    roots = fdgraph.graph_roots(order)
+    G = api.Graph(order, roots=roots)
+    tape = api.tape_bytes(order, roots)
+    flops_ps, sfu_ps = fdgraph.tape_work(tape)
+    V = api.Vegas(G.dim, WL["n_bins"])
+    params = [api.ueg_params(order, WL["rs"], WL["T_over_TF"], WL["lam_over_kF"], WL["kext_over_kF"])]
+    n = args.samples
+    plan = api.EvalPlan([G], params, [0], n, maps=[V])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    seed = WL["seed"] + 1000 * rank
+
+    def step(it, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        api.L.check(api.L.lib().fd_integrand_eval(plan._g, 1, plan._p, plan._gi, 1, plan._m, None, None, seed,
+                                                  it, n, api._ptr(plan.partials), None, api._stream_ptr(stream)))
+        if ev is not None:
+            ev[1].record(stream)
+        api.L.check(api.L.lib().fd_accumulate(api._ptr(plan.partials), 1, plan.r_max, n, api._ptr(plan.stats),
+                                              api._stream_ptr(stream)))
+        V.update(0.5, stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for it in range(args.warmup):
+        step(it)
+    torch.cuda.synchronize()
+    api.device_status()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 255)                      # L2 flush between timed steps (not timed)
+        step(args.warmup + k, evs[k])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    api.device_status()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    kern_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    t_step = float(np.sum(step_ms)) / 1e3
+    t_kern = float(np.mean(kern_ms)) / 1e3
+    if dist:
+        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = world * n * args.steps / t_step
+
+    # end to end through the C-ABI with host buffers: grid in, estimates and grid out
+    e_host = V.edges()
+    stats_host = torch.empty_like(plan.stats, device="cpu").pin_memory()
+    e2e_steps = max(2, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        V.set_edges(e_host)                        # H2D of the step's input grid
+        step(100 + k)
+        stats_host.copy_(plan.stats, non_blocking=True)
+        torch.cuda.synchronize()
+        e_host = V.edges()                         # D2H of the updated grid
+    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    h2d = int(e_host.nbytes)
+    d2h = int(e_host.nbytes + stats_host.numel() * 8)
+
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    mhz_max = _peaks().get("sm_max_mhz", 2070.0)
+    peak = fp32_peak_tflops(n_sm, mhz_max)
+    achieved = flops_ps * n / t_kern / 1e12
+    sfu_achieved = sfu_ps * n / t_kern / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WL["name"], "order": order, "rs": WL["rs"], "kext_over_kF": WL["kext_over_kF"],
+                   "lam_over_kF": WL["lam_over_kF"], "T_over_TF": WL["T_over_TF"], "roots": len(roots),
+                   "dim": G.dim, "samples_per_step": n, "sampler": "vegas", "n_bins": WL["n_bins"],
+                   "tape_instr": G.n_instr, "slots_per_sample": G.n_slots,
+                   "l2": "256 MiB flush write between timed steps; inputs generated on device",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "integrand_kernel",
+                     "flops_per_sample": flops_ps, "sfu_per_sample": sfu_ps,
+                     "sfu_achieved_tops": sfu_achieved,
+                     "peak_basis": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (n_sm, mhz_max),
+                     "kernel_ms": 1e3 * t_kern},
+        "e2e": {"value": n / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "wall_s": t_wall,
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        dist = tdist
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, dist)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -772,3 +772,61 @@ def graph_roots(order, with_dk=False):
             for m in range(order - n + 1):
                 roots.append((n, m, order - n - m, dk))
     return roots
+
+
+# --------------------------------------------------------------------------
+# algorithmic work per sample (roofline accounting)
+# --------------------------------------------------------------------------
+
+def _g_family_flops(M, dk):
+    """FP32 flops of one G family (FMA = 2) as written in the kernel's recurrence."""
+    f = 5                                   # dx, tau, tau*, -eps tau*, times phi
+    Mx = M + dk
+    for k in range(Mx):
+        f += 2 * (k + 1) + 4                # Phi_hat convolution, scale, Psi, A
+    if Mx:
+        for j in range(Mx + 1):
+            f += 2 * (j + 1)                # c_j convolution
+    if dk:
+        f += 2 * (M + 1) + 1
+    return f
+
+
+def tape_work(data):
+    """(fp32_flops, sfu_ops) per sample of a serialised tape, prologue and epilogue included.
+
+    Counting rule (FMA = 2 flops, everything else 1): tape arithmetic as
+    written; MOM 8; FERMI 4 + 2 SFU (exp, rcp); G family per _g_family_flops
+    + 1 SFU (exp); V family 2 + (L + dk) + (dk: 2 + 2(L+1)) + 1 SFU (rcp);
+    per sample the map: 6 per VEGAS dimension, 14 + 2 SFU (sincospi, sqrt)
+    per loop momentum, 3 + 1 SFU per time, and 2 per root for the Jacobian.
+    """
+    hdr = struct.unpack("<16I", data[:64])
+    order, dim, n_roots, n_instr, ins_off = hdr[2], hdr[3], hdr[4], hdr[6], hdr[8]
+    words = struct.unpack("<%dQ" % n_instr, data[ins_off:ins_off + 8 * n_instr])
+    flops = 0
+    sfu = 0
+    for w in words:
+        op = w & 63
+        imm = (w >> 58) & 63
+        if op in (OP_MUL, OP_ADD, OP_MULC, OP_ROOT0):
+            flops += 1
+        elif op == OP_FMA:
+            flops += 2
+        elif op == OP_ROOT:
+            flops += 4
+        elif op == OP_MOM:
+            flops += 8
+        elif op == OP_FERMI:
+            flops += 4
+            sfu += 2
+        elif op == OP_GLEAF:
+            flops += _g_family_flops(imm & 7, (imm >> 3) & 1)
+            sfu += 1
+        elif op == OP_VLEAF:
+            L, dk = imm & 7, (imm >> 3) & 1
+            flops += 2 + (L + dk) + ((2 + 2 * (L + 1)) if dk else 0)
+            sfu += 1
+    flops += 6 * dim + 14 * order + 3 * (order - 1) + 2 * n_roots
+    sfu += 2 * order + (order - 1)
+    return flops, sfu

@@ -101,6 +101,9 @@ def _compare(f, ref, mag, label):
     the fraction within 1e-5 M is reported and must stay above 95%.
     """
     err = np.abs(f[:, 0, :] - ref.real) + np.abs(f[:, 1, :] - ref.imag)
+    # FP32 flushes values below ~1e-38 to zero: absolute floor 1e-30 (the
+    # integrand itself is O(1e-3..1e3) where it matters)
+    err = np.maximum(err - 1e-30, 0.0)
     scale = np.maximum(mag, 1e-30)
     rel = err / scale
     frac = float(np.mean(rel <= 1e-5))
@@ -154,7 +157,7 @@ def test_tiny_sample_counts(api):
         ref, mag = _oracle(2, G.roots, n, 3)
         f = plan.per_sample[0].cpu().numpy().astype(np.float64)
         err = np.abs(f[:, 0, :] - ref.real) + np.abs(f[:, 1, :] - ref.imag)
-        assert np.all(err <= 2e-4 * mag)
+        assert np.all(err <= 2e-4 * mag + 1e-30)
 
 
 def test_batched_instances_multiple_graphs(api):
@@ -245,7 +248,7 @@ def test_integrated_order2_against_oracle(api):
     order = 2
     G = api.Graph(order, with_dk=True)
     plan = api.EvalPlan([G], [_gparams(api, order)], [0], 1 << 20)
-    st = plan.run(77, 0).cpu().numpy()
+    st = plan.run(77, 0).cpu().numpy()[0]
     n = 1 << 15
     P = _oparams(order)
     x = ophilox.uniforms(78, 0, 0, np.arange(n), 7)
