@@ -150,6 +150,35 @@ int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_per_inst);
 fd_status fd_accumulate(const double *partials, int32_t n_inst, int32_t r_max,
                         int64_t n_per_inst, double *out, void *stream);
 
+/* ---- evaluation without device allocation ---------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory (a host process whose allocations are all made up
+ * front, a replayed CUDA graph that may not allocate, a caller without an
+ * allocator in reach).  It does what fd_integrand_eval followed by
+ * fd_accumulate do, with the same arguments except that the tile partial
+ * sums live in one fixed device array inside this library (holding
+ * FD_NOALLOC_MAX_PARTIALS doubles, 4 MiB, present on every device that loads
+ * the library until the process exits) instead of a caller buffer, and the
+ * result goes straight to `out` (device FP64 [n_inst][R_max][2][2], mean and
+ * variance of the mean).  It calls no allocator.
+ *  - Requests needing more than FD_NOALLOC_MAX_PARTIALS partial sums
+ *    (fd_partials_count) are rejected with FD_EINVAL before any launch.
+ *  - The first call on a device resolves the array's device address; make
+ *    that first call before any stream capture on that device.
+ *  - All calls share the one array: calls whose kernels overlap on the GPU
+ *    (different streams, no ordering between them) race and give wrong
+ *    results.  Each call first fills the part it uses with NaN, so a tile a
+ *    kernel could not finish shows up as NaN in `out`.
+ *  - A bounded wait that gives up is not recorded for fd_device_status on
+ *    this path; it appears as NaN in `out`. */
+#define FD_NOALLOC_MAX_PARTIALS (1 << 19)
+fd_status fd_integrand_eval_stats_noalloc(const fd_graph *const *graphs, int32_t n_graphs,
+                                          const fd_params *params, const int32_t *graph_of_inst,
+                                          int32_t n_inst, fd_vegas *const *maps,
+                                          const float *points, const float *point_w,
+                                          uint64_t seed, uint64_t iter, int64_t n_per_inst,
+                                          double *out, float *per_sample_f, void *stream);
+
 /* ---- affine coupling flow (Appendix A, Eqs. NFtransform, coupling_layer) --
  * A flow of n_layers affine coupling layers over [0,1]^dim in logit space,
  * each conditioned by an MLP (in -> hidden -> hidden -> out, ReLU), BF16

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -524,12 +525,15 @@ extern "C" int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_pe
     return (int64_t)n_inst * tiles * r_max * 4;
 }
 
-extern "C" fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_graphs,
-                                       const fd_params *params, const int32_t *graph_of_inst,
-                                       int32_t n_inst, fd_vegas *const *maps, const float *points,
-                                       const float *point_w, uint64_t seed, uint64_t iter,
-                                       int64_t n_per_inst, double *partials, float *per_sample_f,
-                                       void *stream) {
+namespace {
+// Shared body of the evaluation entry points: validate, build the launch
+// descriptors and launch the integrand kernel.  `status` is the device word a
+// kernel sets when a bounded wait gives up (may be null).
+fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_params *params,
+                    const int32_t *graph_of_inst, int32_t n_inst, fd_vegas *const *maps,
+                    const float *points, const float *point_w, uint64_t seed, uint64_t iter,
+                    int64_t n_per_inst, double *partials, float *per_sample_f, int *status,
+                    cudaStream_t stream) {
     FD_REQUIRE(graphs && n_graphs > 0, "graphs must be a non-empty array");
     FD_REQUIRE(params && graph_of_inst, "params and graph_of_inst are required");
     FD_REQUIRE(n_inst > 0 && n_inst <= FD_MAX_INST, "n_inst must be in [1, 256]");
@@ -545,7 +549,7 @@ extern "C" fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_
     args.iter = (uint32_t)iter;
     args.partials = partials;
     args.per_sample_f = per_sample_f;
-    args.status = fd::device_status_word();
+    args.status = status;
     int r_max = 0, slots_total = 0, dim_max = 0;
     for (int g = 0; g < n_graphs; ++g) {
         FD_REQUIRE(graphs[g], "null graph handle");
@@ -602,10 +606,21 @@ extern "C" fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_
     FD_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     // widest CTA whose per-sample state fits in shared memory
     if (smem_layout(128, args.slots_total, args.r_max).total <= max_smem)
-        return launch_eval<128>(args, (cudaStream_t)stream, items);
+        return launch_eval<128>(args, stream, items);
     if (smem_layout(64, args.slots_total, args.r_max).total <= max_smem)
-        return launch_eval<64>(args, (cudaStream_t)stream, items);
-    return launch_eval<32>(args, (cudaStream_t)stream, items);
+        return launch_eval<64>(args, stream, items);
+    return launch_eval<32>(args, stream, items);
+}
+}  // namespace
+
+extern "C" fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_graphs,
+                                       const fd_params *params, const int32_t *graph_of_inst,
+                                       int32_t n_inst, fd_vegas *const *maps, const float *points,
+                                       const float *point_w, uint64_t seed, uint64_t iter,
+                                       int64_t n_per_inst, double *partials, float *per_sample_f,
+                                       void *stream) {
+    return eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter,
+                     n_per_inst, partials, per_sample_f, fd::device_status_word(), (cudaStream_t)stream);
 }
 
 // ---- fd_accumulate ---------------------------------------------------------------
@@ -641,4 +656,73 @@ extern "C" fd_status fd_accumulate(const double *partials, int32_t n_inst, int32
                                                                           n_per_inst, out);
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
+}
+
+// ---- evaluation without device allocation ---------------------------------------
+// Callers that cannot allocate device memory themselves (a host process whose
+// allocations must all be made up front, a CUDA-graph replay that may not add
+// new memory, or a caller without a device allocator in reach) still need
+// the tile partial sums between the two reduction passes.  This variant keeps
+// them in a fixed array of this library instead.  The array lives in every
+// device's global memory for as long as the library stays loaded.
+namespace {
+__device__ __align__(256) double g_noalloc_partials[FD_NOALLOC_MAX_PARTIALS];
+
+struct NoallocDevice {
+    bool ready = false;
+    double *partials = nullptr;   // device address of g_noalloc_partials on that device
+};
+NoallocDevice g_noalloc_dev[64];
+std::mutex g_noalloc_mu;
+
+// Once per device, with that device current: resolve the array's device
+// address (its host-side name is only a stand-in and must never reach a kernel).
+fd_status noalloc_setup(double **out) {
+    int dev = 0;
+    FD_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fd::set_error(FD_ENOTSUP, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return fd::cuda_error(e, "cudaGetSymbolAddress(g_noalloc_partials)");
+        d.partials = static_cast<double *>(p);
+        d.ready = true;
+    }
+    *out = d.partials;
+    return FD_OK;
+}
+}  // namespace
+
+extern "C" fd_status fd_integrand_eval_stats_noalloc(
+    const fd_graph *const *graphs, int32_t n_graphs, const fd_params *params, const int32_t *graph_of_inst,
+    int32_t n_inst, fd_vegas *const *maps, const float *points, const float *point_w, uint64_t seed,
+    uint64_t iter, int64_t n_per_inst, double *out, float *per_sample_f, void *stream) {
+    FD_REQUIRE(graphs && n_graphs > 0, "graphs must be a non-empty array");
+    FD_REQUIRE(out, "out is required");
+    FD_REQUIRE(n_inst > 0 && n_inst <= FD_MAX_INST, "n_inst must be in [1, 256]");
+    FD_REQUIRE(n_per_inst > 0 && n_per_inst <= (int64_t(1) << 40), "n_per_inst out of range");
+    int r_max = 0;
+    for (int g = 0; g < n_graphs; ++g) {
+        FD_REQUIRE(graphs[g], "null graph handle");
+        r_max = std::max(r_max, (int)graphs[g]->hdr.n_roots);
+    }
+    const int64_t need = fd_partials_count(n_inst, r_max, n_per_inst);
+    if (need > (int64_t)FD_NOALLOC_MAX_PARTIALS)
+        return fd::set_error(FD_EINVAL, "request needs " + std::to_string(need) +
+                                            " partial sums; the fixed array holds " +
+                                            std::to_string((long long)FD_NOALLOC_MAX_PARTIALS) +
+                                            " (use fd_integrand_eval with a caller buffer)");
+    double *partials = nullptr;
+    fd_status st = noalloc_setup(&partials);
+    if (st != FD_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // every byte 0xFF is a NaN double: a tile the kernel failed to write shows up
+    // as NaN in `out` instead of a stale value from an earlier call
+    FD_CHECK_CUDA(cudaMemsetAsync(partials, 0xFF, (size_t)need * sizeof(double), s));
+    st = eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, n_per_inst,
+                   partials, per_sample_f, nullptr, s);
+    if (st != FD_OK) return st;
+    return fd_accumulate(partials, n_inst, r_max, n_per_inst, out, stream);
 }
