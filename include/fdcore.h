@@ -77,6 +77,11 @@ fd_status fd_graph_info(const fd_graph *g, int32_t *n_roots, int32_t *dim,
 /* roots[4*r + {0,1,2,3}] = (n, m, l, dk) of root r (host array of 4*n_roots). */
 fd_status fd_graph_roots(const fd_graph *g, int32_t *roots);
 void fd_graph_free(fd_graph *g);
+/* Preferred CTA shape of evaluation launches whose first graph is g:
+ * (threads, samples per thread) in {(128,2), (256,1), (128,1), (64,2), (64,1)},
+ * or (0,0) for the automatic choice (most samples in flight per SM).
+ * A preference that does not fit in shared memory falls back to automatic. */
+fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_thread);
 
 /* ---- VEGAS map (Sec. IV, separable map q(x) = prod q_k(x_k)) ---------------
  * A map owns FP64 bin edges [dim][n_bins+1] (uniform at creation), their FP32

@@ -43,6 +43,7 @@ SIGNATURES = {
     "fd_graph_info": (_i32, [_vp, _pi, _pi, _c.POINTER(_i64), _pi]),
     "fd_graph_roots": (_i32, [_vp, _pi]),
     "fd_graph_free": (None, [_vp]),
+    "fd_graph_set_launch": (_i32, [_vp, _i32, _i32]),
     "fd_vegas_create": (_i32, [_i32, _i32, _c.POINTER(_vp)]),
     "fd_vegas_free": (None, [_vp]),
     "fd_vegas_set_edges": (_i32, [_vp, _pd]),

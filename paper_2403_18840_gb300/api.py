@@ -42,14 +42,21 @@ def ueg_params(order, rs, T_over_TF, lam_over_kF, kext_over_kF, kc_over_kF=6.0):
     return p
 
 
-def tape_bytes(order, roots):
-    """Compiled tape for (order, roots), cached on disk by compiler source hash."""
+DEFAULT_SCHEDULE = dict(budget=128, bundle=8, window=64)
+
+
+def tape_bytes(order, roots, budget=None, bundle=None, window=None):
+    """Compiled tape for (order, roots, schedule), cached on disk by compiler source hash."""
+    sch = dict(DEFAULT_SCHEDULE)
+    for k, v in (("budget", budget), ("bundle", bundle), ("window", window)):
+        if v is not None:
+            sch[k] = v
     src = open(fdgraph.__file__, "rb").read()
-    key = hashlib.sha1(src + repr((order, list(roots))).encode()).hexdigest()[:16]
+    key = hashlib.sha1(src + repr((order, list(roots), sorted(sch.items()))).encode()).hexdigest()[:16]
     path = os.path.join(_TAPE_DIR, "tape_o%d_%s.bin" % (order, key))
     if os.path.exists(path):
         return open(path, "rb").read()
-    data = fdgraph.compile_graph(order, roots).to_bytes()
+    data = fdgraph.compile_graph(order, roots, **sch).to_bytes()
     os.makedirs(_TAPE_DIR, exist_ok=True)
     tmp = path + ".tmp%d" % os.getpid()
     with open(tmp, "wb") as f:
@@ -61,10 +68,11 @@ def tape_bytes(order, roots):
 class Graph:
     """A compiled self-energy graph loaded on the current device."""
 
-    def __init__(self, order, roots=None, with_dk=False, tape=None):
+    def __init__(self, order, roots=None, with_dk=False, tape=None, budget=None, bundle=None, window=None):
         self.order = order
         self.roots = list(roots) if roots is not None else fdgraph.graph_roots(order, with_dk)
-        data = tape if tape is not None else tape_bytes(order, self.roots)
+        data = tape if tape is not None else tape_bytes(order, self.roots, budget, bundle, window)
+        self.tape = data
         self._buf = ctypes.create_string_buffer(data, len(data))
         h = ctypes.c_void_p()
         L.check(L.lib().fd_graph_load(self._buf, len(data), ctypes.byref(h)))
@@ -73,6 +81,9 @@ class Graph:
         ni = ctypes.c_int64()
         L.check(L.lib().fd_graph_info(h, ctypes.byref(nr), ctypes.byref(dim), ctypes.byref(ni), ctypes.byref(ns)))
         self.n_roots, self.dim, self.n_instr, self.n_slots = nr.value, dim.value, ni.value, ns.value
+
+    def set_launch(self, threads=0, samples_per_thread=0):
+        L.check(L.lib().fd_graph_set_launch(self.handle, threads, samples_per_thread))
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -66,59 +66,89 @@ static fd_status validate_tape(const uint8_t *buf, size_t len, TapeHeader &h) {
     if (h.order < 1 || h.order > (uint32_t)FD_MAX_ORDER) return fd::set_error(FD_EFORMAT, "order out of range");
     if (h.dim != 4 * h.order - 1) return fd::set_error(FD_EFORMAT, "dim != 4*order-1");
     if (h.n_roots < 1 || h.n_roots > 256) return fd::set_error(FD_EFORMAT, "root count out of range");
-    if (h.n_slots < 1 || h.n_slots > 8191) return fd::set_error(FD_EFORMAT, "slot count out of range");
+    if (h.n_slots < 2 || h.n_slots > 16383) return fd::set_error(FD_EFORMAT, "slot count out of range");
     if (h.n_instr < 1) return fd::set_error(FD_EFORMAT, "empty tape");
     if (h.total_bytes != len) return fd::set_error(FD_EFORMAT, "tape length differs from its header");
     if (h.root_off % 16 || h.instr_off % 16) return fd::set_error(FD_EFORMAT, "sections not 16-byte aligned");
     if ((uint64_t)h.root_off + 8ull * h.n_roots > len) return fd::set_error(FD_EFORMAT, "root table out of bounds");
     if ((uint64_t)h.instr_off + 8ull * h.n_instr > len) return fd::set_error(FD_EFORMAT, "instructions out of bounds");
     const uint32_t N = h.order;
-    const uint32_t fixed = 5 + 4 * N + 3 * (N - 1);   // prologue slots
+    const uint32_t fixed = 2;   // slot 0 = 0.0, slot 1 = 1.0
     const uint32_t S = h.n_slots;
-    if (fixed + 2 * h.n_roots > S) return fd::set_error(FD_EFORMAT, "slot count below the fixed layout");
-    // roots
+    if (S < fixed) return fd::set_error(FD_EFORMAT, "slot count below the fixed slots");
     for (uint32_t r = 0; r < h.n_roots; ++r) {
         const uint8_t *p = buf + h.root_off + 8 * r;
         const uint32_t n = p[0], m = p[1], l = p[2], dk = p[3];
-        uint16_t re, im;
-        memcpy(&re, p + 4, 2);
-        memcpy(&im, p + 6, 2);
         if (n < 1 || n > N || n + m + l > N || dk > 1) return fd::set_error(FD_EFORMAT, "bad root (n, m, l, dk)");
-        if (re != fixed + 2 * r || im != re + 1) return fd::set_error(FD_EFORMAT, "root accumulator slots out of layout");
     }
-    // instructions: opcode and operand ranges
+    std::vector<int> flushed(h.n_roots, 0);
     bool has_end = false;
+    uint32_t in_bundle = 0;                 // FMA words still expected in the current bundle
+    std::vector<uint32_t> bdst, bsrc;       // destinations and sources of the current bundle
     for (uint32_t k = 0; k < h.n_instr; ++k) {
         uint64_t w;
         memcpy(&w, buf + h.instr_off + 8ull * k, 8);
-        const uint32_t op = ins_op(w), d = ins_d(w), a = ins_a(w), b = ins_b(w), c = ins_c(w),
-                       imm = ins_imm(w);
-        auto in = [&](uint32_t s, uint32_t width) { return s + width <= S; };
+        const uint32_t op = (uint32_t)(w & 63u);
+        if (in_bundle && op != OP_FMA)
+            return fd::set_error(FD_EFORMAT, "bundle " + std::to_string(k) + " holds a non-FMA word");
+        const uint32_t d = (uint32_t)(w >> 6) & 16383u, a = (uint32_t)(w >> 20) & 16383u,
+                       b = (uint32_t)(w >> 34) & 16383u, c = (uint32_t)(w >> 48) & 16383u;
         bool ok = true;
         switch (op) {
-            case OP_MOM: ok = in(d, 4) && in(a, 4) && in(b, 4) && d >= fixed; break;
-            case OP_FERMI: ok = in(d, 4) && in(a, 4) && d >= fixed; break;
-            case OP_GLEAF:
-            case OP_VLEAF: {
-                const uint32_t M = imm & 7u, dk = (imm >> 3) & 1u, ks = (imm >> 4) & 3u;
-                ok = (M + dk <= (uint32_t)FD_MAX_M) && ks <= 2 && in(d, (M + 1) * (dk ? 2 : 1)) && d >= fixed &&
-                     in(a, 4);
-                if (op == OP_GLEAF) ok = ok && in(b, 1) && in(c, 1);
+            case OP_FMA:
+                ok = d >= fixed && d < S && a < S && b < S && c < S;
+                if (in_bundle) {
+                    bdst.push_back(d);
+                    bsrc.push_back(a);
+                    bsrc.push_back(b);
+                    bsrc.push_back(c);
+                    if (--in_bundle == 0) {
+                        // a bundle loads every operand before storing any result, so a
+                        // destination may reuse a slot the bundle reads; two results
+                        // may not share a slot
+                        for (size_t i = 0; i < bdst.size() && ok; ++i)
+                            for (size_t j = 0; j < bdst.size() && ok; ++j)
+                                ok = (i == j || bdst[i] != bdst[j]);
+                    }
+                }
+                break;
+            case OP_BUNDLE: {
+                const uint32_t n = (uint32_t)(w >> 6) & 15u;
+                ok = n >= 2 && n <= (uint32_t)FD_MAX_BUNDLE && k + n < h.n_instr &&
+                     k / FD_CHUNK_WORDS == (k + n) / FD_CHUNK_WORDS;
+                in_bundle = n;
+                bdst.clear();
+                bsrc.clear();
                 break;
             }
-            case OP_MUL:
-            case OP_ADD: ok = in(d, 1) && in(a, 1) && in(b, 1) && d >= fixed; break;
-            case OP_FMA: ok = in(d, 1) && in(a, 1) && in(b, 1) && in(c, 1) && d >= fixed; break;
-            case OP_MULC: ok = in(d, 1) && in(a, 1) && d >= fixed; break;
-            case OP_CONST: ok = in(d, 1) && d >= fixed; break;
-            case OP_ROOT: ok = in(d, 2) && in(a, 1) && in(b, 1) && in(c, 1) && d >= fixed - 0; break;
-            case OP_ROOT0: ok = in(d, 1) && in(a, 1); break;
+            case OP_NOP: break;
+            case OP_GLEAF:
+            case OP_VLEAF: {
+                const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
+                const uint32_t M = (uint32_t)(w >> 40) & 7u, dk = (uint32_t)(w >> 43) & 1u;
+                const uint32_t width = (M + 1) * (dk ? 2 : 1);
+                ok = d >= fixed && d + width <= S && M + dk <= (uint32_t)FD_MAX_M;
+                for (uint32_t j = 0; j <= (uint32_t)FD_MAX_ORDER && ok; ++j) {
+                    const uint32_t f = (a >> (2 * j)) & 3u;
+                    ok = f != 3u && (j <= N || f == 0u);
+                }
+                if (op == OP_GLEAF) ok = ok && la < N && lb < N;
+                break;
+            }
+            case OP_RACC: ok = a < S && b < N; break;
+            case OP_RFLUSH:
+                ok = d < h.n_roots;
+                if (ok) ++flushed[d];
+                break;
+            case OP_CONST: ok = d >= fixed && d < S; break;
             case OP_END: has_end = (k == h.n_instr - 1); ok = has_end; break;
             default: ok = false;
         }
         if (!ok) return fd::set_error(FD_EFORMAT, "instruction " + std::to_string(k) + " (op " +
                                                       std::to_string(op) + ") out of range");
     }
+    for (uint32_t r = 0; r < h.n_roots; ++r)
+        if (flushed[r] != 1) return fd::set_error(FD_EFORMAT, "root " + std::to_string(r) + " not flushed exactly once");
     if (!has_end) return fd::set_error(FD_EFORMAT, "tape does not end with END");
     return FD_OK;
 }

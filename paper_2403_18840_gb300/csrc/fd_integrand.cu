@@ -35,15 +35,16 @@
 
 namespace {
 
-constexpr int CHUNK_INSTR = 2048;                     // 16 KB per tape buffer
+constexpr int CHUNK_INSTR = FD_CHUNK_WORDS;           // 8 KB per tape buffer
 constexpr int CHUNK_BYTES = CHUNK_INSTR * 8;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;             // polls before a tape wait gives up
 constexpr float K_INV_2PI2 = 0.050660591821168885f;    // 1 / (2 pi^2)
 constexpr float K_8PI = 25.132741228718345f;
+constexpr int NK = FD_MAX_ORDER;                      // loop momenta / interaction lines held in registers
 
 struct InstDesc {
     const uint64_t *tape;      // instruction words (device)
-    const uint32_t *roots;     // root table (device)
+    const uint32_t *roots;     // root table (device): n | m<<8 | l<<16 | dk<<24, 0
     const float *edges;        // VEGAS FP32 edges [dim][nb+1] or null
     double *hist;              // VEGAS histogram [dim][nb] or null
     const float *points;       // explicit points [dim_max][n] or null
@@ -64,20 +65,19 @@ struct EvalArgs {
 };
 
 struct SmemLayout {
-    // byte offsets inside dynamic shared memory
-    int tape0, tape1, bars, acc, slots, total;
+    int tape0, tape1, bars, acc, slots, total;   // byte offsets in dynamic shared memory
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int threads, int slots_total, int r_max) {
+__host__ __device__ inline SmemLayout smem_layout(int threads, int P, int slots_total, int r_max) {
     SmemLayout L;
     L.tape0 = 0;
     L.tape1 = CHUNK_BYTES;
     L.bars = 2 * CHUNK_BYTES;
-    L.acc = L.bars + 16;                                     // 8-byte aligned
+    L.acc = L.bars + 16;
     const int nwarps = threads / 32;
     L.slots = L.acc + nwarps * r_max * 4 * 2 * 8;            // (sum, sumsq) x (re, im) x (value, comp)
     L.slots = (L.slots + 15) & ~15;
-    L.total = L.slots + slots_total * threads * 4;
+    L.total = L.slots + slots_total * threads * P * 4;
     return L;
 }
 
@@ -91,275 +91,403 @@ __device__ __forceinline__ void neumaier(double &s, double &c, double v) {
     s = t;
 }
 
-template <int T>
+// per-sample slots in shared memory: [slot][thread][P] FP32
+template <int T, int P>
 struct Slots {
-    float *base;   // &slots[tid]
-    __device__ __forceinline__ float &operator[](uint32_t s) const { return base[s * T]; }
+    float *base;
+    __device__ __forceinline__ float *at(uint32_t s) const { return base + (size_t)s * (T * P); }
+    __device__ __forceinline__ void load(uint32_t s, float (&v)[P]) const {
+        if constexpr (P == 2) {
+            const float2 f = *reinterpret_cast<const float2 *>(at(s));
+            v[0] = f.x;
+            v[1] = f.y;
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) v[p] = at(s)[p];
+        }
+    }
+    __device__ __forceinline__ void store(uint32_t s, const float (&v)[P]) const {
+        if constexpr (P == 2) {
+            *reinterpret_cast<float2 *>(at(s)) = make_float2(v[0], v[1]);
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) at(s)[p] = v[p];
+        }
+    }
+    __device__ __forceinline__ void store1(uint32_t s, int p, float v) const { at(s)[p] = v; }
 };
 
-// G0 Taylor family: c_j = (d/dmu)^j G0 / j!, j <= M (+ d/dk copies).
-// Written as sign * exp(-eps tau*) * phi(eps - dmu) with the Fermi factor
-// phi >= 1/2 (phi = 1 - f for eps >= 0, f for eps < 0) and tau* the matching
+// register-resident per-sample variables
+template <int P>
+struct Vars {
+    float kx[NK][P], ky[NK][P], kz[NK][P];     // loop momenta k_1..k_N
+    float tx[NK][P];                           // hypercube time of interaction line i (tx[0] = 0)
+    float re[P], im[P], hsum[P];               // root accumulator and |f| sum for VEGAS
+};
+
+template <int P>
+__device__ __forceinline__ float pick(const float (&a)[NK][P], uint32_t idx, int p) {
+    float r = a[0][p];
+#pragma unroll
+    for (int j = 1; j < NK; ++j) r = (idx == (uint32_t)j) ? a[j][p] : r;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t f_d(uint64_t w) { return (uint32_t)(w >> 6) & 16383u; }
+__device__ __forceinline__ uint32_t f_a(uint64_t w) { return (uint32_t)(w >> 20) & 16383u; }
+__device__ __forceinline__ uint32_t f_b(uint64_t w) { return (uint32_t)(w >> 34) & 16383u; }
+__device__ __forceinline__ uint32_t f_c(uint64_t w) { return (uint32_t)(w >> 48) & 16383u; }
+
+// signed momentum sum from a 2-bit-per-variable mask; k_ext is (0, 0, kext)
+template <int P>
+__device__ __forceinline__ void momentum(const Vars<P> &V, uint32_t mask, float kext, float (&px)[P],
+                                         float (&py)[P], float (&pz)[P], float &ks) {
+    float cf[NK + 1];
+#pragma unroll
+    for (int j = 0; j <= NK; ++j)
+        cf[j] = (float)((mask >> (2 * j)) & 1u) - (float)((mask >> (2 * j + 1)) & 1u);
+    ks = cf[0];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        float x = 0.0f, y = 0.0f, z = cf[0] * kext;
+#pragma unroll
+        for (int j = 0; j < NK; ++j) {
+            x = fmaf(cf[j + 1], V.kx[j][p], x);
+            y = fmaf(cf[j + 1], V.ky[j][p], y);
+            z = fmaf(cf[j + 1], V.kz[j][p], z);
+        }
+        px[p] = x;
+        py[p] = y;
+        pz[p] = z;
+    }
+}
+
+// G0 Taylor family: c_j = (d/dmu)^j G0 / j!, j <= M (+ d/dk copies).  Written as
+// sign * exp(-eps tau*) * phi(eps - dmu) with the Fermi factor phi >= 1/2
+// (phi = 1 - f for eps >= 0, f for eps < 0) and tau* the matching
 // antiperiodic time, so the exponent is never positive.  The series of
 // phi(eps - d) follows from the logistic ODE d phi / d eps = +-beta phi (1 - phi)
-// (Taylor-mode recurrence); the series of exp(d tau*) is tau*^k / k!.
-template <int T>
-__device__ __forceinline__ void g_leaf(const Slots<T> &S, uint64_t w, float beta) {
-    const uint32_t d = ins_d(w), a = ins_a(w), b = ins_b(w), c = ins_c(w), imm = ins_imm(w);
-    const int M = (int)(imm & 7u);
-    const int dk = (int)((imm >> 3) & 1u);
-    const float ks = (float)((int)((imm >> 4) & 3u) - 1);
-    const float eps = S[a], phi = S[a + 1], psi = S[a + 2], pz = S[a + 3];
-    const float dx = S[b] - S[c];
-    const bool pos = dx > 0.0f;
-    const float tau = beta * dx;
-    const bool occ = eps < 0.0f;
-    const float tstar = occ ? (pos ? tau - beta : tau) : (pos ? tau : tau + beta);
-    const float sgn = pos ? -1.0f : 1.0f;
-    const float X = sgn * __expf(-eps * tstar) * phi;
-    if (M == 0 && !dk) {
-        S[d] = X;
-        return;
-    }
-    const int Mx = M + dk;
-    // Phi_hat (series of phi(eps - d) / phi) and A (series of exp(d tau*))
-    float ph[FD_MAX_M + 1], ps[FD_MAX_M + 1], A[FD_MAX_M + 1], cf[FD_MAX_M + 1];
-    const float g = occ ? beta : -beta;
-    ph[0] = 1.0f;
-    ps[0] = psi;
-    A[0] = 1.0f;
+// (a Taylor-mode recurrence); the series of exp(d tau*) is tau*^k / k!.
+template <int T, int P>
+__device__ __forceinline__ void g_leaf(const Slots<T, P> &S, const Vars<P> &V, uint64_t w, const InstDesc &D) {
+    const uint32_t d = f_d(w), mask = f_a(w);
+    const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
+    const int M = (int)((w >> 40) & 7u);
+    const int dk = (int)((w >> 43) & 1u);
+    float px[P], py[P], pz[P], ks;
+    momentum(V, mask, D.kext, px, py, pz, ks);
+    const float beta = D.beta;
 #pragma unroll
-    for (int k = 0; k < FD_MAX_M; ++k) {
-        if (k < Mx) {
-            float s = 0.0f;
-#pragma unroll
-            for (int i = 0; i <= k; ++i) s = fmaf(ph[i], ps[k - i], s);
-            ph[k + 1] = g * s / (float)(k + 1);
-            ps[k + 1] = -phi * ph[k + 1];
-            A[k + 1] = A[k] * tstar / (float)(k + 1);
+    for (int p = 0; p < P; ++p) {
+        const float eps = fmaf(px[p], px[p], fmaf(py[p], py[p], pz[p] * pz[p])) - D.mu;
+        const float E = __expf(-beta * fabsf(eps));
+        const float phi = __frcp_rn(1.0f + E);
+        const float psi = E * phi;
+        const float dx = pick(V.tx, la, p) - pick(V.tx, lb, p);
+        const bool pos = dx > 0.0f;
+        const float tau = beta * dx;
+        const bool occ = eps < 0.0f;
+        const float tstar = occ ? (pos ? tau - beta : tau) : (pos ? tau : tau + beta);
+        const float X = (pos ? -1.0f : 1.0f) * __expf(-eps * tstar) * phi;
+        if (M == 0 && !dk) {
+            S.store1(d, p, X);
+            continue;
         }
-    }
+        const int Mx = M + dk;
+        float ph[FD_MAX_M + 1], ps[FD_MAX_M + 1], A[FD_MAX_M + 1], cf[FD_MAX_M + 1];
+        const float g = occ ? beta : -beta;
+        ph[0] = 1.0f;
+        ps[0] = psi;
+        A[0] = 1.0f;
 #pragma unroll
-    for (int j = 0; j <= FD_MAX_M; ++j) {
-        if (j <= Mx) {
-            float s = 0.0f;
+        for (int k = 0; k < FD_MAX_M; ++k) {
+            if (k < Mx) {
+                float s = 0.0f;
 #pragma unroll
-            for (int i = 0; i <= j; ++i) s = fmaf(A[j - i], ph[i], s);
-            cf[j] = X * s;
+                for (int i = 0; i <= k; ++i) s = fmaf(ph[i], ps[k - i], s);
+                ph[k + 1] = g * s / (float)(k + 1);
+                ps[k + 1] = -phi * ph[k + 1];
+                A[k + 1] = A[k] * tstar / (float)(k + 1);
+            }
         }
-    }
 #pragma unroll
-    for (int j = 0; j <= FD_MAX_M; ++j)
-        if (j <= M) S[d + j] = cf[j];
-    if (dk) {
-        const float kz = -2.0f * ks * pz;
+        for (int j = 0; j <= FD_MAX_M; ++j) {
+            if (j <= Mx) {
+                float s = 0.0f;
 #pragma unroll
-        for (int j = 0; j < FD_MAX_M; ++j)
-            if (j <= M) S[d + M + 1 + j] = kz * (float)(j + 1) * cf[j + 1];
+                for (int i = 0; i <= j; ++i) s = fmaf(A[j - i], ph[i], s);
+                cf[j] = X * s;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j <= FD_MAX_M; ++j)
+            if (j <= M) S.store1(d + j, p, cf[j]);
+        if (dk) {
+            const float kz = -2.0f * ks * pz[p];
+#pragma unroll
+            for (int j = 0; j < FD_MAX_M; ++j)
+                if (j <= M) S.store1(d + M + 1 + j, p, kz * (float)(j + 1) * cf[j + 1]);
+        }
     }
 }
 
 // V Taylor family: c_l = (d/dLambda)^l V / l! = 8 pi (-1)^l w^(l+1), w = 1/(q^2+Lambda)
-template <int T>
-__device__ __forceinline__ void v_leaf(const Slots<T> &S, uint64_t w, float Lambda) {
-    const uint32_t d = ins_d(w), a = ins_a(w), imm = ins_imm(w);
-    const int L = (int)(imm & 7u);
-    const int dk = (int)((imm >> 3) & 1u);
-    const float ks = (float)((int)((imm >> 4) & 3u) - 1);
-    const float q2 = S[a + 3], pz = S[a + 2];
-    const float inv = __frcp_rn(q2 + Lambda);
-    float cl = K_8PI * inv;
-    float cf[FD_MAX_M + 1];
+template <int T, int P>
+__device__ __forceinline__ void v_leaf(const Slots<T, P> &S, const Vars<P> &V, uint64_t w, const InstDesc &D) {
+    const uint32_t d = f_d(w), mask = f_a(w);
+    const int L = (int)((w >> 40) & 7u);
+    const int dk = (int)((w >> 43) & 1u);
+    float px[P], py[P], pz[P], ks;
+    momentum(V, mask, D.kext, px, py, pz, ks);
 #pragma unroll
-    for (int l = 0; l <= FD_MAX_M; ++l) {
-        if (l <= L + dk) {
-            cf[l] = cl;
-            cl = -inv * cl;
+    for (int p = 0; p < P; ++p) {
+        const float q2 = fmaf(px[p], px[p], fmaf(py[p], py[p], pz[p] * pz[p]));
+        const float inv = __frcp_rn(q2 + D.Lambda);
+        float cl = K_8PI * inv;
+        float cf[FD_MAX_M + 1];
+#pragma unroll
+        for (int l = 0; l <= FD_MAX_M; ++l) {
+            if (l <= L + dk) {
+                cf[l] = cl;
+                cl = -inv * cl;
+            }
         }
-    }
 #pragma unroll
-    for (int l = 0; l <= FD_MAX_M; ++l)
-        if (l <= L) S[d + l] = cf[l];
-    if (dk) {
-        const float kz = 2.0f * ks * pz;
+        for (int l = 0; l <= FD_MAX_M; ++l)
+            if (l <= L) S.store1(d + l, p, cf[l]);
+        if (dk) {
+            const float kz = 2.0f * ks * pz[p];
 #pragma unroll
-        for (int l = 0; l < FD_MAX_M; ++l)
-            if (l <= L) S[d + L + 1 + l] = kz * (float)(l + 1) * cf[l + 1];
+            for (int l = 0; l < FD_MAX_M; ++l)
+                if (l <= L) S.store1(d + L + 1 + l, p, kz * (float)(l + 1) * cf[l + 1]);
+        }
     }
 }
 
-template <int T>
-__device__ __forceinline__ bool run_chunk(const Slots<T> &S, const uint64_t *code, int cnt,
-                                          const InstDesc &D) {
+// Root r is complete for the current samples: weight, write, reduce, reset.
+template <int T, int P>
+__device__ __forceinline__ void flush_root(const Slots<T, P> &S, Vars<P> &V, uint32_t r, const InstDesc &D,
+                                           const EvalArgs &A, double *acc, int inst, const int64_t (&idx)[P],
+                                           const bool (&valid)[P]) {
+    const uint32_t rt = __ldg(D.roots + 2 * r);
+    const uint32_t n = rt & 255u;
+    const bool dkr = ((rt >> 24) & 255u) != 0;
+    float jw[P];
+    S.load(D.n_slots + D.dim + n - 1, jw);     // weight of the roots of order n
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const float J = jw[p];
+        const float fre = valid[p] ? V.re[p] * J : 0.0f;
+        const float fim = valid[p] ? V.im[p] * J : 0.0f;
+        V.re[p] = 0.0f;
+        V.im[p] = 0.0f;
+        if (!dkr) V.hsum[p] += fabsf(fre) + fabsf(fim);
+        if (A.per_sample_f && valid[p]) {
+            const int64_t o = (((int64_t)inst * A.r_max + r) * 2) * A.n_per_inst + idx[p];
+            A.per_sample_f[o] = fre;
+            A.per_sample_f[o + A.n_per_inst] = fim;
+        }
+        v[0] += fre;
+        v[1] = fmaf(fre, fre, v[1]);
+        v[2] += fim;
+        v[3] = fmaf(fim, fim, v[3]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        double *wa = acc + (size_t)(threadIdx.x >> 5) * A.r_max * 8;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) neumaier(wa[(r * 4 + q) * 2], wa[(r * 4 + q) * 2 + 1], (double)v[q]);
+    }
+}
+
+template <int T, int P>
+__device__ __forceinline__ void run_chunk(const Slots<T, P> &S, Vars<P> &V, const uint64_t *code, int cnt,
+                                          const InstDesc &D, const EvalArgs &A, double *acc, int inst,
+                                          const int64_t (&idx)[P], const bool (&valid)[P]) {
     for (int k = 0; k < cnt; ++k) {
         const uint64_t w = code[k];
-        switch (ins_op(w)) {
-            case OP_MUL:
-                S[ins_d(w)] = S[ins_a(w)] * S[ins_b(w)];
-                break;
-            case OP_FMA:
-                S[ins_d(w)] = fmaf(S[ins_a(w)], S[ins_b(w)], S[ins_c(w)]);
-                break;
-            case OP_ADD:
-                S[ins_d(w)] = S[ins_a(w)] + S[ins_b(w)];
-                break;
-            case OP_MULC:
-                S[ins_d(w)] = S[ins_a(w)] * __uint_as_float(ins_hi(w));
-                break;
-            case OP_CONST:
-                S[ins_d(w)] = __uint_as_float(ins_hi(w));
-                break;
+        const uint32_t op = (uint32_t)w & 63u;
+        if (op == OP_BUNDLE) {
+            // independent FMAs: every operand is loaded before any result is stored
+            const int n = (int)((w >> 6) & 15u);
+            const uint64_t *q = code + k + 1;
+            float a[FD_MAX_BUNDLE][P], b[FD_MAX_BUNDLE][P], c[FD_MAX_BUNDLE][P];
+            uint64_t ws[FD_MAX_BUNDLE];
+#pragma unroll
+            for (int j = 0; j < FD_MAX_BUNDLE; ++j) {
+                if (j < n) {
+                    ws[j] = q[j];
+                    S.load(f_a(ws[j]), a[j]);
+                    S.load(f_b(ws[j]), b[j]);
+                    S.load(f_c(ws[j]), c[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < FD_MAX_BUNDLE; ++j) {
+                if (j < n) {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) a[j][p] = fmaf(a[j][p], b[j][p], c[j][p]);
+                    S.store(f_d(ws[j]), a[j]);
+                }
+            }
+            k += n;
+            continue;
+        }
+        if (op == OP_FMA) {
+            float a[P], b[P], c[P];
+            S.load(f_a(w), a);
+            S.load(f_b(w), b);
+            S.load(f_c(w), c);
+#pragma unroll
+            for (int p = 0; p < P; ++p) a[p] = fmaf(a[p], b[p], c[p]);
+            S.store(f_d(w), a);
+            continue;
+        }
+        switch (op) {
             case OP_GLEAF:
-                g_leaf(S, w, D.beta);
+                g_leaf(S, V, w, D);
                 break;
             case OP_VLEAF:
-                v_leaf(S, w, D.Lambda);
+                v_leaf(S, V, w, D);
                 break;
-            case OP_FERMI: {
-                const uint32_t d = ins_d(w), a = ins_a(w);
-                const float eps = S[a + 3] - D.mu;
-                const float E = __expf(-D.beta * fabsf(eps));
-                const float phi = __frcp_rn(1.0f + E);
-                S[d] = eps;
-                S[d + 1] = phi;
-                S[d + 2] = E * phi;
-                S[d + 3] = S[a + 2];
-                break;
-            }
-            case OP_MOM: {
-                const uint32_t d = ins_d(w), a = ins_a(w), b = ins_b(w);
-                const float sg = (ins_imm(w) & 1u) ? -1.0f : 1.0f;
-                const float px = fmaf(sg, S[b], S[a]);
-                const float py = fmaf(sg, S[b + 1], S[a + 1]);
-                const float pz = fmaf(sg, S[b + 2], S[a + 2]);
-                S[d] = px;
-                S[d + 1] = py;
-                S[d + 2] = pz;
-                S[d + 3] = fmaf(px, px, fmaf(py, py, pz * pz));
+            case OP_RACC: {
+                float a[P];
+                S.load(f_a(w), a);
+                const uint32_t line = f_b(w);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    float sn = 0.0f, cs = 1.0f;
+                    if (line) sincospif(pick(V.tx, line, p), &sn, &cs);
+                    V.re[p] = fmaf(a[p], cs, V.re[p]);
+                    V.im[p] = fmaf(a[p], sn, V.im[p]);
+                }
                 break;
             }
-            case OP_ROOT: {
-                const uint32_t d = ins_d(w);
-                const float v = S[ins_a(w)];
-                S[d] = fmaf(v, S[ins_b(w)], S[d]);
-                S[d + 1] = fmaf(v, S[ins_c(w)], S[d + 1]);
+            case OP_RFLUSH:
+                flush_root<T, P>(S, V, f_d(w), D, A, acc, inst, idx, valid);
+                break;
+            case OP_CONST: {
+                float c[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) c[p] = __uint_as_float((uint32_t)(w >> 32));
+                S.store(f_d(w), c);
                 break;
             }
-            case OP_ROOT0:
-                S[ins_d(w)] += S[ins_a(w)];
+            case OP_NOP:
                 break;
-            case OP_END:
-                return true;
             default:
-                break;
+                return;   // OP_END
         }
     }
-    return false;
 }
 
-// Fixed part of the per-sample state (the tape's prologue slots) plus the
-// extra slots [n_slots, n_slots + order) holding the Jacobian of each root
-// order and [n_slots + order, + dim) holding the VEGAS bins.
-template <int T>
-__device__ __forceinline__ void prologue(const Slots<T> &S, const InstDesc &D, const EvalArgs &A,
-                                         int64_t i, int inst) {
+// Sample generation: Philox -> uniforms -> VEGAS (or given points) -> loop
+// momenta, times, phases and per-order weights in registers; VEGAS bins in
+// the slots [n_slots, n_slots + dim).
+template <int T, int P>
+__device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const InstDesc &D, const EvalArgs &A,
+                                         const int64_t (&idx)[P], int inst) {
     const int N = D.order, dim = D.dim;
-    float x[FD_MAX_DIM];
-    float jv_prefix = 1.0f;    // VEGAS / point weight over the dims consumed so far
-    float jn[FD_MAX_ORDER + 1];
-    if (D.points) {
+    float one[P], zero[P];
 #pragma unroll
-        for (int d = 0; d < FD_MAX_DIM; ++d)
-            if (d < dim) x[d] = D.points[(int64_t)d * A.n_per_inst + i];
-        jv_prefix = D.point_w ? D.point_w[i] : 1.0f;
-    } else {
-        const uint32_t c0 = (uint32_t)(uint64_t)i, c1 = (uint32_t)((uint64_t)i >> 32);
+    for (int p = 0; p < P; ++p) {
+        one[p] = 1.0f;
+        zero[p] = 0.0f;
+    }
+    S.store(0, zero);
+    S.store(1, one);
 #pragma unroll
-        for (int blk = 0; blk < (FD_MAX_DIM + 3) / 4; ++blk) {
-            if (4 * blk < dim) {
-                const u32x4 r = philox4x32_10(u32x4{c0, c1, A.iter, ((uint32_t)inst << 8) | (uint32_t)blk},
-                                              A.seed_lo, A.seed_hi);
-                const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+    for (int p = 0; p < P; ++p) {
+        const int64_t i = idx[p];
+        float x[FD_MAX_DIM];
+        float wgt = 1.0f;
+        if (D.points) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (4 * blk + q < FD_MAX_DIM) x[4 * blk + q] = word_to_uniform(wv[q]);
+            for (int d = 0; d < FD_MAX_DIM; ++d)
+                if (d < dim) x[d] = D.points[(int64_t)d * A.n_per_inst + i];
+            wgt = D.point_w ? D.point_w[i] : 1.0f;
+        } else {
+            const uint32_t c0 = (uint32_t)(uint64_t)i, c1 = (uint32_t)((uint64_t)i >> 32);
+#pragma unroll
+            for (int blk = 0; blk < (FD_MAX_DIM + 3) / 4; ++blk) {
+                if (4 * blk < dim) {
+                    const u32x4 r = philox4x32_10(
+                        u32x4{c0, c1, A.iter, ((uint32_t)inst << 8) | (uint32_t)blk}, A.seed_lo, A.seed_hi);
+                    const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (4 * blk + q < FD_MAX_DIM) x[4 * blk + q] = word_to_uniform(wv[q]);
+                }
             }
         }
-    }
-    // VEGAS map per dimension (bins kept for the histogram)
-    float jd[FD_MAX_DIM];
+        float jd[FD_MAX_DIM];
 #pragma unroll
-    for (int d = 0; d < FD_MAX_DIM; ++d) {
-        jd[d] = 1.0f;
-        if (d < dim && D.edges) {
-            const int nb = D.n_bins;
-            const float y = x[d] * (float)nb;
-            int bin = min((int)y, nb - 1);
-            const float *e = D.edges + (int64_t)d * (nb + 1);
-            const float lo = __ldg(e + bin), hi = __ldg(e + bin + 1);
-            x[d] = fmaf(y - (float)bin, hi - lo, lo);
-            jd[d] = (float)nb * (hi - lo);
-            S[D.n_slots + N + d] = __int_as_float(bin);
-        }
-    }
-    // k_ext record and constant zero
-    S[0] = 0.0f;
-    S[1] = 0.0f;
-    S[2] = 0.0f;
-    S[3] = D.kext;
-    S[4] = D.kext * D.kext;
-    const int t0 = 5 + 4 * N;
-    const int p0 = t0 + N - 1;
-    float jac = 1.0f;
-    int used = 0;    // hypercube coordinates consumed
-#pragma unroll
-    for (int j = 1; j <= FD_MAX_ORDER; ++j) {
-        if (j <= N) {
-            const int c0 = (j == 1) ? 0 : 4 * j - 5;
-            const float xa = x[c0], xb = x[c0 + 1], xc = x[c0 + 2];
-            const float r = D.kc * xa;
-            const float cth = fmaf(2.0f, xb, -1.0f);
-            const float sth = 2.0f * sqrtf(xb * (1.0f - xb));
-            float sp, cp;
-            sincospif(2.0f * xc, &sp, &cp);
-            const int rec = 5 + 4 * (j - 1);
-            S[rec] = r * sth * cp;
-            S[rec + 1] = r * sth * sp;
-            S[rec + 2] = r * cth;
-            S[rec + 3] = r * r;
-            jac *= D.kc * r * r * K_INV_2PI2;
-            jv_prefix *= D.points ? 1.0f : jd[c0] * jd[c0 + 1] * jd[c0 + 2];
-            used = c0 + 3;
-            if (j >= 2) {
-                const float xt = x[4 * j - 2];
-                S[t0 + j - 2] = xt;
-                float st, ct;
-                sincospif(xt, &st, &ct);
-                S[p0 + 2 * (j - 2)] = ct;
-                S[p0 + 2 * (j - 2) + 1] = st;
-                jac *= D.beta;
-                jv_prefix *= D.points ? 1.0f : jd[4 * j - 2];
-                used = 4 * j - 1;
+        for (int d = 0; d < FD_MAX_DIM; ++d) {
+            jd[d] = 1.0f;
+            if (d < dim && D.edges) {
+                const int nb = D.n_bins;
+                const float y = x[d] * (float)nb;
+                const int bin = min((int)y, nb - 1);
+                const float *e = D.edges + (int64_t)d * (nb + 1);
+                const float lo = __ldg(e + bin), hi = __ldg(e + bin + 1);
+                x[d] = fmaf(y - (float)bin, hi - lo, lo);
+                jd[d] = (float)nb * (hi - lo);
+                S.store1(D.n_slots + d, p, __int_as_float(bin));
             }
-            S[D.n_slots + j - 1] = jac * jv_prefix;
         }
+        float jac = wgt;
+#pragma unroll
+        for (int j = 0; j < NK; ++j) {
+            V.kx[j][p] = 0.0f;
+            V.ky[j][p] = 0.0f;
+            V.kz[j][p] = 0.0f;
+            V.tx[j][p] = 0.0f;
+            const int jj = j + 1;                       // loop momentum k_jj
+            if (jj <= N) {
+                const int c0 = (jj == 1) ? 0 : 4 * jj - 5;
+                const float xa = x[c0], xb = x[c0 + 1], xc = x[c0 + 2];
+                const float r = D.kc * xa;
+                const float cth = fmaf(2.0f, xb, -1.0f);
+                const float sth = 2.0f * sqrtf(xb * (1.0f - xb));
+                float sp, cp;
+                sincospif(2.0f * xc, &sp, &cp);
+                V.kx[j][p] = r * sth * cp;
+                V.ky[j][p] = r * sth * sp;
+                V.kz[j][p] = r * cth;
+                jac *= D.kc * r * r * K_INV_2PI2;
+                if (!D.points) jac *= jd[c0] * jd[c0 + 1] * jd[c0 + 2];
+                if (jj >= 2) {
+                    // time of interaction line jj - 1
+                    V.tx[jj - 1][p] = x[4 * jj - 2];
+                    jac *= D.beta;
+                    if (!D.points) jac *= jd[4 * jj - 2];
+                }
+                S.store1(D.n_slots + D.dim + j, p, jac);
+            }
+        }
+        V.re[p] = 0.0f;
+        V.im[p] = 0.0f;
+        V.hsum[p] = 0.0f;
     }
-    (void)used;
-    (void)jn;
 }
 
-template <int T>
+template <int T, int P>
 __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ EvalArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout(T, A.slots_total, A.r_max);
+    const SmemLayout L = smem_layout(T, P, A.slots_total, A.r_max);
     uint64_t *buf[2] = {reinterpret_cast<uint64_t *>(smem + L.tape0),
                         reinterpret_cast<uint64_t *>(smem + L.tape1)};
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     double *acc = reinterpret_cast<double *>(smem + L.acc);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const Slots<T> S{reinterpret_cast<float *>(smem + L.slots) + tid};
+    const int tid = threadIdx.x;
+    const Slots<T, P> S{reinterpret_cast<float *>(smem + L.slots) + tid * P};
     const int n_items = A.n_inst * A.tiles_per_inst;
-    const int racc = A.r_max * 4;   // doubles per warp for values (sum, sumsq) x (re, im)
+    const int racc = A.r_max * 8;   // doubles per warp
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -367,20 +495,19 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
         fence_mbarrier_init();
     }
     __syncthreads();
-    uint32_t phase[2] = {0u, 0u};   // completed loads per buffer (parity source)
+    uint32_t phase[2] = {0u, 0u};
     bool failed = false;
+    Vars<P> V;
 
     for (int item = blockIdx.x; item < n_items && !failed; item += gridDim.x) {
         const int inst = item / A.tiles_per_inst;
         const int tile = item % A.tiles_per_inst;
         const InstDesc &D = A.inst[inst];
         const int n_chunks = (D.n_instr + CHUNK_INSTR - 1) / CHUNK_INSTR;
-        // zero the per-warp accumulators
-        for (int k = tid; k < (T / 32) * racc * 2; k += T) acc[k] = 0.0;
+        for (int k = tid; k < (T / 32) * racc; k += T) acc[k] = 0.0;
         const int64_t first = (int64_t)tile * FD_TILE_SAMPLES;
         const int64_t last = min(first + (int64_t)FD_TILE_SAMPLES, A.n_per_inst);
-        const int passes = (int)((last - first + T - 1) / T);
-        // start streaming: chunk g of the cyclic sequence (pass-major) goes to buffer g % 2
+        const int passes = (int)((last - first + T * P - 1) / (T * P));
         const int64_t total_chunks = (int64_t)passes * n_chunks;
         const bool resident = n_chunks <= 2;
         __syncthreads();
@@ -394,15 +521,17 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
                 bulk_g2s(buf[g], D.tape + (int64_t)ch * CHUNK_INSTR, bytes, &bars[g]);
             }
         }
-        int64_t g = 0;   // global chunk counter
+        int64_t g = 0;
         for (int pass = 0; pass < passes && !failed; ++pass) {
-            const int64_t i = first + (int64_t)pass * T + tid;
-            const bool valid = i < last;
-            // zero roots, then the prologue
-            const int base_roots = 5 + 4 * D.order + 3 * (D.order - 1);
-            for (int r = 0; r < 2 * D.n_roots; ++r) S[base_roots + r] = 0.0f;
-            prologue(S, D, A, valid ? i : first, inst);
-            // tape
+            int64_t idx[P];
+            bool valid[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int64_t i = first + (int64_t)pass * T * P + (int64_t)p * T + tid;
+                valid[p] = i < last;
+                idx[p] = valid[p] ? i : first;
+            }
+            prologue<T, P>(S, V, D, A, idx, inst);
             for (int ch = 0; ch < n_chunks; ++ch, ++g) {
                 const int b = resident ? ch : (int)(g & 1);
                 if (!resident || pass == 0) {
@@ -417,9 +546,9 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
                     ++phase[b];
                 }
                 const int cnt = min(CHUNK_INSTR, D.n_instr - ch * CHUNK_INSTR);
-                run_chunk(S, buf[b], cnt, D);
+                run_chunk<T, P>(S, V, buf[b], cnt, D, A, acc, inst, idx, valid);
                 if (!resident) {
-                    __syncthreads();    // everybody is done with buffer b
+                    __syncthreads();
                     const int64_t nxt = g + 2;
                     if (tid == 0 && nxt < total_chunks) {
                         fence_proxy_async_smem();
@@ -432,56 +561,31 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
                 }
             }
             if (failed) break;
-            // epilogue: weighted roots
-            float hsum = 0.0f;
-            for (int r = 0; r < D.n_roots; ++r) {
-                const uint32_t rt = __ldg(D.roots + 2 * r), rs = __ldg(D.roots + 2 * r + 1);
-                const int n = (int)(rt & 255u);
-                const int dkr = (int)((rt >> 24) & 255u);
-                const float J = S[D.n_slots + n - 1];
-                float fre = valid ? S[rs & 0xFFFFu] * J : 0.0f;
-                float fim = valid ? S[rs >> 16] * J : 0.0f;
-                if (!dkr) hsum += fabsf(fre) + fabsf(fim);
-                if (A.per_sample_f && valid) {
-                    const int64_t o = (((int64_t)inst * A.r_max + r) * 2) * A.n_per_inst + i;
-                    A.per_sample_f[o] = fre;
-                    A.per_sample_f[o + A.n_per_inst] = fim;
-                }
-                float v[4] = {fre, fre * fre, fim, fim * fim};
+            if (D.hist && !D.points) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
-                }
-                if (lane == 0) {
-                    double *wa = acc + (size_t)warp * racc * 2;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) neumaier(wa[(r * 4 + q) * 2], wa[(r * 4 + q) * 2 + 1], (double)v[q]);
-                }
-            }
-            if (D.hist && valid && !D.points) {
-                const double h = (double)hsum * (double)hsum;
-                for (int d = 0; d < D.dim; ++d) {
-                    const int bin = __float_as_int(S[D.n_slots + D.order + d]);
-                    atomicAdd(D.hist + (int64_t)d * D.n_bins + bin, h);
+                for (int p = 0; p < P; ++p) {
+                    if (!valid[p]) continue;
+                    const double h = (double)V.hsum[p] * (double)V.hsum[p];
+                    for (int d = 0; d < D.dim; ++d) {
+                        const int bin = __float_as_int(S.at(D.n_slots + d)[p]);
+                        atomicAdd(D.hist + (int64_t)d * D.n_bins + bin, h);
+                    }
                 }
             }
         }
         __syncthreads();
         if (!failed) {
-            // combine warps in a fixed order into the tile partials
             for (int k = tid; k < D.n_roots * 4; k += T) {
                 double s = 0.0, c = 0.0;
                 for (int wp = 0; wp < T / 32; ++wp) {
-                    const double *wa = acc + (size_t)wp * racc * 2;
+                    const double *wa = acc + (size_t)wp * racc;
                     neumaier(s, c, wa[k * 2]);
                     neumaier(s, c, wa[k * 2 + 1]);
                 }
                 const int r = k / 4, q = k % 4;   // q: 0 re sum, 1 re sumsq, 2 im sum, 3 im sumsq
                 const int64_t o = (((int64_t)inst * A.tiles_per_inst + tile) * A.r_max + r) * 4;
-                A.partials[o + (q / 2) * 2 + (q % 2)] = s + c;
+                A.partials[o + q] = s + c;
             }
-            // roots beyond this graph's count are zero
             for (int k = D.n_roots * 4 + tid; k < A.r_max * 4; k += T) {
                 const int64_t o = ((int64_t)inst * A.tiles_per_inst + tile) * A.r_max * 4;
                 A.partials[o + k] = 0.0;
@@ -490,14 +594,13 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
         __syncthreads();
     }
     if (failed && tid == 0) {
-        // bounded wait for copies still in flight into this CTA's buffers
         for (int b = 0; b < 2; ++b) (void)mbar_wait_bounded(&bars[b], phase[b] & 1u, WAIT_LIMIT);
     }
 }
 
-template <int T>
+template <int T, int P>
 fd_status launch_eval(const EvalArgs &args, cudaStream_t stream, int items) {
-    const SmemLayout L = smem_layout(T, args.slots_total, args.r_max);
+    const SmemLayout L = smem_layout(T, P, args.slots_total, args.r_max);
     int dev = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
     int max_smem = 0, n_sm = 0;
@@ -507,17 +610,29 @@ fd_status launch_eval(const EvalArgs &args, cudaStream_t stream, int items) {
         return fd::set_error(FD_ENOTSUP, "graph needs " + std::to_string(L.total) +
                                              " bytes of shared memory per CTA (limit " +
                                              std::to_string(max_smem) + ")");
-    FD_CHECK_CUDA(cudaFuncSetAttribute(integrand_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total));
+    FD_CHECK_CUDA(cudaFuncSetAttribute(integrand_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total));
     int per_sm = 0;
-    FD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrand_kernel<T>, T, L.total));
+    FD_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrand_kernel<T, P>, T, L.total));
     per_sm = std::max(per_sm, 1);
     const int grid = std::min(items, n_sm * per_sm);
-    integrand_kernel<T><<<grid, T, L.total, stream>>>(args);
+    integrand_kernel<T, P><<<grid, T, L.total, stream>>>(args);
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
 }
 
 }  // namespace
+
+extern "C" fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_thread) {
+    FD_REQUIRE(g, "null graph");
+    const bool ok = (threads == 0 && samples_per_thread == 0) ||
+                    (threads == 128 && samples_per_thread == 2) || (threads == 256 && samples_per_thread == 1) ||
+                    (threads == 128 && samples_per_thread == 1) || (threads == 64 && samples_per_thread == 2) ||
+                    (threads == 64 && samples_per_thread == 1);
+    FD_REQUIRE(ok, "unsupported CTA shape (threads, samples per thread)");
+    g->launch_threads = threads;
+    g->launch_spt = samples_per_thread;
+    return FD_OK;
+}
 
 extern "C" int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_per_inst) {
     if (n_inst <= 0 || r_max <= 0 || n_per_inst <= 0) return 0;
@@ -555,7 +670,7 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
         FD_REQUIRE(graphs[g], "null graph handle");
         const TapeHeader &h = graphs[g]->hdr;
         r_max = std::max(r_max, (int)h.n_roots);
-        slots_total = std::max(slots_total, (int)(h.n_slots + h.order + h.dim));
+        slots_total = std::max(slots_total, (int)(h.n_slots + h.dim + h.order));
         dim_max = std::max(dim_max, (int)h.dim);
     }
     args.r_max = r_max;
@@ -604,12 +719,37 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
     int dev = 0, max_smem = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
     FD_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    // widest CTA whose per-sample state fits in shared memory
-    if (smem_layout(128, args.slots_total, args.r_max).total <= max_smem)
-        return launch_eval<128>(args, stream, items);
-    if (smem_layout(64, args.slots_total, args.r_max).total <= max_smem)
-        return launch_eval<64>(args, stream, items);
-    return launch_eval<32>(args, stream, items);
+    // CTA shape: the first graph's preference when it fits, otherwise the shape
+    // with the most samples in flight per SM (then the most warps)
+    const int pref_t = graphs[0]->launch_threads, pref_p = graphs[0]->launch_spt;
+    struct Shape { int t, p; };
+    const Shape shapes[] = {{128, 2}, {256, 1}, {128, 1}, {64, 2}, {64, 1}};
+    auto fits = [&](int t, int p) { return smem_layout(t, p, args.slots_total, args.r_max).total <= max_smem; };
+    int bt = 0, bp = 0;
+    if (pref_t && fits(pref_t, pref_p)) {
+        bt = pref_t;
+        bp = pref_p;
+    } else {
+        long best = -1;
+        for (const Shape &sh : shapes) {
+            if (!fits(sh.t, sh.p)) continue;
+            const int per_cta = smem_layout(sh.t, sh.p, args.slots_total, args.r_max).total;
+            const long ctas = std::max(1, (228 * 1024) / per_cta);
+            const long score = ctas * sh.t * sh.p * 1000 + ctas * sh.t;
+            if (score > best) {
+                best = score;
+                bt = sh.t;
+                bp = sh.p;
+            }
+        }
+    }
+    if (bt == 128 && bp == 2) return launch_eval<128, 2>(args, stream, items);
+    if (bt == 256 && bp == 1) return launch_eval<256, 1>(args, stream, items);
+    if (bt == 128 && bp == 1) return launch_eval<128, 1>(args, stream, items);
+    if (bt == 64 && bp == 2) return launch_eval<64, 2>(args, stream, items);
+    if (bt == 64 && bp == 1) return launch_eval<64, 1>(args, stream, items);
+    return fd::set_error(FD_ENOTSUP, "per-sample state of " + std::to_string(args.slots_total) +
+                                         " slots does not fit in shared memory with any CTA shape");
 }
 }  // namespace
 

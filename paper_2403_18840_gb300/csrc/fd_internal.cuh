@@ -29,44 +29,37 @@ int *device_status_word();
 
 }  // namespace fd
 
-// ---- tape format (mirrors paper_2403_18840_gb300/fdgraph.py) -------------------
+// ---- tape format, version 2 (mirrors paper_2403_18840_gb300/fdgraph.py) ----------
 enum : uint32_t {
-    OP_MOM = 1,
-    OP_FERMI = 2,
-    OP_GLEAF = 3,
-    OP_VLEAF = 4,
-    OP_MUL = 5,
-    OP_FMA = 6,
-    OP_ADD = 7,
-    OP_MULC = 8,
-    OP_ROOT = 9,
-    OP_ROOT0 = 10,
-    OP_CONST = 11,
+    OP_FMA = 1,      // S[d] = S[a] * S[b] + S[c]
+    OP_GLEAF = 2,    // G0 Taylor family from a momentum mask and two interaction lines
+    OP_VLEAF = 3,    // V Taylor family from a momentum mask
+    OP_RACC = 4,     // root accumulator += S[a] * exp(i pi x_line)
+    OP_RFLUSH = 5,   // root d complete
+    OP_CONST = 6,    // S[d] = f32 immediate
+    OP_NOP = 7,      // padding
+    OP_BUNDLE = 8,   // next n (<= 8) words are independent FMAs
     OP_END = 63,
 };
 
 constexpr uint32_t TAPE_MAGIC = 0x50544446u;  // 'FDTP'
-constexpr uint32_t TAPE_VERSION = 1;
+constexpr uint32_t TAPE_VERSION = 2;
 constexpr int FD_MAX_ORDER = 6;
 constexpr int FD_MAX_DIM = 4 * FD_MAX_ORDER - 1;
 constexpr int FD_MAX_M = 7;         // largest Taylor order of a leaf family (incl. d/dk)
 constexpr int FD_MAX_INST = 256;    // instances per launch (kernel-parameter descriptors)
+constexpr int FD_CHUNK_WORDS = 1024;  // tape chunk staged in shared memory; bundles never straddle one
+constexpr int FD_MAX_BUNDLE = 8;
 
 struct TapeHeader {
     uint32_t magic, version, order, dim, n_roots, n_slots, n_instr, root_off, instr_off,
         total_bytes, n_mom, n_g, n_v, n_arith, r0, r1;
 };
 
-__host__ __device__ inline uint32_t ins_op(uint64_t w) { return (uint32_t)(w & 63u); }
-__host__ __device__ inline uint32_t ins_d(uint64_t w) { return (uint32_t)((w >> 6) & 8191u); }
-__host__ __device__ inline uint32_t ins_a(uint64_t w) { return (uint32_t)((w >> 19) & 8191u); }
-__host__ __device__ inline uint32_t ins_b(uint64_t w) { return (uint32_t)((w >> 32) & 8191u); }
-__host__ __device__ inline uint32_t ins_c(uint64_t w) { return (uint32_t)((w >> 45) & 8191u); }
-__host__ __device__ inline uint32_t ins_imm(uint64_t w) { return (uint32_t)((w >> 58) & 63u); }
-__host__ __device__ inline uint32_t ins_hi(uint64_t w) { return (uint32_t)(w >> 32); }
 
 struct fd_graph {
     int device;
+    int launch_threads = 0, launch_spt = 0;   // preferred CTA shape (0 = automatic)
     TapeHeader hdr;
     uint64_t *d_tape;            // device copy of the instruction words (16-byte aligned)
     uint32_t *d_roots;           // device root table: (n | m<<8 | l<<16 | dk<<24, re | im<<16)

@@ -28,19 +28,20 @@ Pipeline
 5. Schedule the DAG depth-first, compute each leaf family just before its
    first use, allocate per-sample slots by liveness, and serialise.
 
-Tape format (little endian; all sections 16-byte aligned):
+Tape format, version 2 (little endian; sections 16-byte aligned):
   header  16 x u32: magic 'FDTP', version, order, dim, n_roots, n_slots,
-          n_instr, root_table_off, instr_off, total_bytes, n_mom_ops,
-          n_g_leaves, n_v_leaves, n_arith, reserved x2
-  roots   n_roots x (u8 n, u8 m, u8 l, u8 dk, u16 slot_re, u16 slot_im)
-  instr   n_instr x u64: op:6 | d:13 | a:13 | b:13 | c:13 | imm:6 (low to high);
-          ops with a float immediate keep it in the high 32 bits instead of
-          b/c/imm.
-Fixed slot layout (written by the kernel prologue before the tape runs):
-  0: constant 0; 1..4: k_ext record (0, 0, k, k^2); 5+4(j-1)..: record of k_j
-  (px, py, pz, p^2) for j = 1..N; then the hypercube time coordinate of
-  interaction lines 1..N-1; then cos(pi x), sin(pi x) of those lines; then the
-  root accumulators (re, im), which the prologue zeroes.
+          n_instr, root_table_off, instr_off, total_bytes, n_g_leaves,
+          n_v_leaves, n_arith, n_consts, reserved x2
+  roots   n_roots x (u8 n, u8 m, u8 l, u8 dk, u16 0, u16 0)
+  instr   n_instr x u64, low to high: op:6 | d:14 | a:14 | b:14 | c:14.
+          FMA uses all four slot fields.  Leaf ops keep in `a` a 2-bit sign
+          per momentum variable (k_ext, k_1..k_N; 1 = +, 2 = -) and in the
+          upper bits the two interaction lines (3 bits each), the Taylor
+          order (3 bits) and the d/dk flag.  RACC: `a` = value slot, `b` =
+          out-line; RFLUSH: `d` = root index; CONST: float in the high 32 bits.
+Per-sample state: slot 0 = 0.0 and slot 1 = 1.0 (written by the kernel),
+constants, leaf families and temporaries; loop momenta, times, phases,
+Jacobians and root accumulators live in registers of the interpreter.
 """
 import collections
 import itertools
@@ -49,20 +50,19 @@ import struct
 import sys
 
 MAGIC = 0x50544446  # 'FDTP'
-VERSION = 1
+VERSION = 2
 
-# opcodes (keep in sync with csrc/fd_tape.cuh)
-OP_MOM = 1      # S[d..d+3] = record(S[a..a+2] + sgn * S[b..b+2]); imm bit0: sgn<0
-OP_FERMI = 2    # S[d..d+3] = (eps, phi, 1-phi, pz) from momentum record a
-OP_GLEAF = 3    # S[d..] = Taylor coeffs of G0 from Fermi record a, times S[b]-S[c]; imm = M | dk<<3 | ks<<4
-OP_VLEAF = 4    # S[d..] = Taylor coeffs of V from momentum record a; imm = L | dk<<3 | ks<<4
-OP_MUL = 5      # S[d] = S[a] * S[b]
-OP_FMA = 6      # S[d] = S[a] * S[b] + S[c]
-OP_ADD = 7      # S[d] = S[a] + S[b]
-OP_MULC = 8     # S[d] = S[a] * f32(hi)
-OP_ROOT = 9     # S[d] += S[a] * S[b]; S[d+1] += S[a] * S[c]   (phase cos/sin of the out line)
-OP_ROOT0 = 10   # S[d] += S[a]                                   (out line 0: phase 1)
-OP_CONST = 11   # S[d] = f32(hi)
+# opcodes (keep in sync with csrc/fd_internal.cuh)
+OP_FMA = 1      # S[d] = S[a] * S[b] + S[c]   (MUL: c = slot 0 = 0.0; ADD: b = slot 1 = 1.0)
+OP_GLEAF = 2    # S[d..] = Taylor coefficients of G0; momentum mask, lines la/lb, M, dk
+OP_VLEAF = 3    # S[d..] = Taylor coefficients of V; momentum mask, L, dk
+OP_RACC = 4     # root accumulator += S[a] * exp(i pi x_line)   (line 0: phase 1)
+OP_RFLUSH = 5   # root r complete: weight by its Jacobian, reduce, reset the accumulator
+OP_CONST = 6    # S[d] = f32 immediate (high 32 bits)
+OP_NOP = 7      # padding (keeps bundles inside one tape chunk)
+OP_BUNDLE = 8   # the next n (<= 8) words are independent FMAs: load all, compute, store all
+CHUNK_WORDS = 1024   # tape chunk the GPU stages at a time; bundles never straddle one
+MAX_BUNDLE = 8
 OP_END = 63
 
 
@@ -291,18 +291,24 @@ def root_polynomials(order, roots):
 # --------------------------------------------------------------------------
 
 class DAG:
+    """Hash-consed expression DAG.  Leaves and constants are shared globally;
+    products and sums are shared within the current `scope` (one root
+    polynomial), which bounds how long a shared temporary stays alive."""
+
     def __init__(self):
         self.nodes = []          # (kind, args)
         self.index = {}
+        self.scope = None
 
     def make(self, kind, *args):
         if kind in ("mul", "add"):
             args = tuple(sorted(args))
         key = (kind,) + tuple(args)
-        if key in self.index:
-            return self.index[key]
+        ikey = key if kind in ("var", "const") else key + (self.scope,)
+        if ikey in self.index:
+            return self.index[ikey]
         self.nodes.append(key)
-        self.index[key] = len(self.nodes) - 1
+        self.index[ikey] = len(self.nodes) - 1
         return len(self.nodes) - 1
 
     def var(self, v):
@@ -372,70 +378,81 @@ def _horner(dag, monos):
 # 5. scheduling, leaf families, slot allocation, serialisation
 # --------------------------------------------------------------------------
 
-def _enc(op, d=0, a=0, b=0, c=0, imm=0):
-    assert 0 <= d < 8192 and 0 <= a < 8192 and 0 <= b < 8192 and 0 <= c < 8192 and 0 <= imm < 64
-    return op | (d << 6) | (a << 19) | (b << 32) | (c << 45) | (imm << 58)
+def _enc_fma(d, a, b, c):
+    for v in (d, a, b, c):
+        assert 0 <= v < 16384
+    return OP_FMA | (d << 6) | (a << 20) | (b << 34) | (c << 48)
 
 
-def _enc_f(op, d, a, f):
+def _enc_leaf(op, d, mask, la, lb, M, dk):
+    assert 0 <= d < 16384 and 0 <= mask < 16384 and 0 <= la < 8 and 0 <= lb < 8 and 0 <= M < 8
+    return op | (d << 6) | (mask << 20) | (la << 34) | (lb << 37) | (M << 40) | (int(dk) << 43)
+
+
+def _enc_racc(a, line):
+    return OP_RACC | (a << 20) | (line << 34)
+
+
+def _enc_flush(r):
+    return OP_RFLUSH | (r << 6)
+
+
+def _enc_const(d, f):
     bits = struct.unpack("<I", struct.pack("<f", f))[0]
-    assert 0 <= d < 8192 and 0 <= a < 8192
-    return op | (d << 6) | (a << 19) | (bits << 32)
+    return OP_CONST | (d << 6) | (bits << 32)
+
+
+def mom_mask(mom):
+    """2 bits per momentum variable (k_ext, k_1..k_N): 1 = +1, 2 = -1."""
+    m = 0
+    for j, c in enumerate(mom):
+        if c == 1:
+            m |= 1 << (2 * j)
+        elif c == -1:
+            m |= 2 << (2 * j)
+        else:
+            assert c == 0
+    return m
 
 
 class Tape:
-    def __init__(self, order, roots, words, n_slots, root_slots, stats):
+    def __init__(self, order, roots, words, n_slots, stats):
         self.order = order
         self.roots = roots
         self.words = words
         self.n_slots = n_slots
-        self.root_slots = root_slots
         self.stats = stats
 
     def to_bytes(self):
         n_roots = len(self.roots)
-        hdr_size = 64
-        rt_off = hdr_size
+        rt_off = 64
         rt_size = (8 * n_roots + 15) // 16 * 16
         ins_off = rt_off + rt_size
-        total = ins_off + 8 * len(self.words)
-        total = (total + 15) // 16 * 16
+        total = (ins_off + 8 * len(self.words) + 15) // 16 * 16
         st = self.stats
-        hdr = struct.pack("<16I", MAGIC, VERSION, self.order, 4 * self.order - 1, n_roots,
-                          self.n_slots, len(self.words), rt_off, ins_off, total,
-                          st["mom_ops"], st["g_leaves"], st["v_leaves"], st["arith"], 0, 0)
-        rt = b"".join(struct.pack("<4B2H", n, m, l, dk, self.root_slots[i][0], self.root_slots[i][1])
-                      for i, (n, m, l, dk) in enumerate(self.roots))
+        hdr = struct.pack("<16I", MAGIC, VERSION, self.order, 4 * self.order - 1, n_roots, self.n_slots,
+                          len(self.words), rt_off, ins_off, total, st.get("g_leaves", 0), st.get("v_leaves", 0),
+                          st.get("arith", 0), st.get("consts", 0), 0, 0)
+        rt = b"".join(struct.pack("<4B2H", n, m, l, dk, 0, 0) for (n, m, l, dk) in self.roots)
         rt += b"\0" * (rt_size - len(rt))
-        ins = struct.pack("<%dQ" % len(self.words), *self.words)
-        out = hdr + rt + ins
+        out = hdr + rt + struct.pack("<%dQ" % len(self.words), *self.words)
         return out + b"\0" * (total - len(out))
 
 
-def prologue_layout(order):
-    N = order
-    lay = {"zero": 0, "kext": 1}
-    lay["k"] = {j: 5 + 4 * (j - 1) for j in range(1, N + 1)}
-    t0 = 5 + 4 * N
-    lay["tx"] = {0: 0}
-    for i in range(1, N):
-        lay["tx"][i] = t0 + i - 1
-    p0 = t0 + N - 1
-    lay["cos"] = {i: p0 + 2 * (i - 1) for i in range(1, N)}
-    lay["sin"] = {i: p0 + 2 * (i - 1) + 1 for i in range(1, N)}
-    lay["end"] = p0 + 2 * (N - 1)
-    return lay
+FIXED_SLOTS = 2      # slot 0 = 0.0, slot 1 = 1.0 (written by the kernel prologue)
 
 
 class SlotAllocator:
     """First-fit allocator of contiguous per-sample slots above a fixed base."""
 
     def __init__(self, base):
-        self.base = base
         self.top = base
-        self.free = []          # sorted list of (start, length)
+        self.free = []          # sorted (start, length)
+        self.live = 0
+        self.peak = base
 
     def alloc(self, k):
+        self.live += k
         for i, (st, ln) in enumerate(self.free):
             if ln >= k:
                 if ln == k:
@@ -445,9 +462,11 @@ class SlotAllocator:
                 return st
         st = self.top
         self.top += k
+        self.peak = max(self.peak, self.top)
         return st
 
     def release(self, st, k):
+        self.live -= k
         self.free.append((st, k))
         self.free.sort()
         merged = []
@@ -456,67 +475,128 @@ class SlotAllocator:
                 merged[-1] = (merged[-1][0], merged[-1][1] + l)
             else:
                 merged.append((a, l))
-        # give back a trailing block
         if merged and merged[-1][0] + merged[-1][1] == self.top:
             self.top = merged[-1][0]
             merged.pop()
         self.free = merged
 
 
-def _mom_parent(mom):
-    nz = [i for i, c in enumerate(mom) if c != 0]
-    if len(nz) == 1:
-        assert mom[nz[0]] == 1, "canonical momenta start with a positive coefficient"
-        return None, nz[0], 1
-    last = nz[-1]
-    par = list(mom)
-    c = par[last]
-    par[last] = 0
-    return tuple(par), last, c
+def _kids(key):
+    kind = key[0]
+    if kind in ("mul", "add"):
+        return [key[1], key[2]]
+    if kind == "fma":
+        return [key[1], key[2], key[3]]
+    if kind == "mulc":
+        return [key[1]]
+    return []
 
 
-def compile_graph(order, roots):
-    """Compile the roots [(n, m, l, dk)] of an order-`order` graph into a Tape."""
+def compile_graph(order, roots, budget=96, bundle=4, window=32):
+    """Compile roots [(n, m, l, dk)] of an order-`order` graph into a Tape.
+
+    budget: per-sample slots the scheduler tries to keep leaf families and
+    temporaries within; leaf families beyond it are evicted (farthest next use
+    first) and recomputed when needed again.
+    bundle, window: up to `bundle` mutually independent products/sums found
+    within the next `window` scheduled operations are issued as one bundle,
+    which the interpreter executes with all operand loads first (ILP).
+    """
+    assert 1 <= bundle <= MAX_BUNDLE
     sys.setrecursionlimit(max(sys.getrecursionlimit(), 100000))
     N = order
     for (n, m, l, dk) in roots:
         assert 1 <= n <= N and m >= 0 and l >= 0 and dk in (0, 1)
     polys = root_polynomials(order, roots)
     dag = DAG()
-    outputs = []      # (root index, out line, node)
+    outputs = []
     for (r, o) in sorted(polys):
+        dag.scope = (r, o)
         outputs.append((r, o, horner(dag, polys[(r, o)])))
 
-    # ---- use counts --------------------------------------------------------
-    def kids_of(key):
-        kind = key[0]
-        if kind in ("mul", "add"):
-            return [key[1], key[2]]
-        if kind == "fma":
-            return [key[1], key[2], key[3]]
-        if kind == "mulc":
-            return [key[1]]
-        return []
+    # ---- pass 1: linear schedule (post-order, largest-need child first) ------
+    need = {}
 
-    uses = collections.Counter()
-    reachable = set()
-    stack = [node for _, _, node in outputs]
-    for _, _, node in outputs:
-        uses[node] += 1
-    while stack:
-        u = stack.pop()
-        if u in reachable:
+    def need_of(u):
+        stk = [(u, False)]
+        while stk:
+            x, done = stk.pop()
+            if x in need:
+                continue
+            ks = _kids(dag.nodes[x])
+            if not done:
+                stk.append((x, True))
+                stk.extend((k, False) for k in ks if k not in need)
+                continue
+            if not ks:
+                need[x] = 0
+                continue
+            nk = sorted((need[k] for k in ks), reverse=True)
+            need[x] = max(max(v + i for i, v in enumerate(nk)), 1)
+        return need[u]
+
+    items = []            # ('node', u) | ('racc', u, line) | ('flush', r)
+    emitted = set()
+    by_root = collections.defaultdict(list)
+    for (r, o, node) in outputs:
+        by_root[r].append((o, node))
+    for r in range(len(roots)):
+        for (o, node) in by_root.get(r, []):
+            stk = [(node, False)]
+            while stk:
+                u, done = stk.pop()
+                if u in emitted:
+                    continue
+                key = dag.nodes[u]
+                if key[0] in ("var", "const"):
+                    emitted.add(u)
+                    continue
+                ks = _kids(key)
+                if not done:
+                    stk.append((u, True))
+                    for k in sorted(ks, key=need_of):
+                        if k not in emitted:
+                            stk.append((k, False))
+                    continue
+                emitted.add(u)
+                items.append(("node", u))
+            items.append(("racc", node, o))
+        items.append(("flush", r))
+
+    # ---- pass 1b: bundles of independent FMAs (list scheduling, lookahead window)
+    groups = []
+    done = set()
+    taken = [False] * len(items)
+    front = 0
+    while front < len(items):
+        while front < len(items) and taken[front]:
+            front += 1
+        if front >= len(items):
+            break
+        it = items[front]
+        if it[0] != "node":
+            groups.append([it])
+            taken[front] = True
             continue
-        reachable.add(u)
-        for k in kids_of(dag.nodes[u]):
-            uses[k] += 1
-            stack.append(k)
+        bund = []
+        for j in range(front, min(len(items), front + window)):
+            if taken[j] or items[j][0] != "node":
+                continue
+            u = items[j][1]
+            ks = [k for k in _kids(dag.nodes[u]) if dag.nodes[k][0] not in ("var", "const")]
+            if all(k in done for k in ks):
+                bund.append(j)
+                if len(bund) == bundle:
+                    break
+        for j in bund:
+            taken[j] = True
+        for j in bund:
+            done.add(items[j][1])
+        groups.append([items[j] for j in bund])
 
-    # leaf families and their total use counts
+    # leaf families
     gfam, vfam = {}, {}
-    fam_uses = collections.Counter()
-    for u in reachable:
-        key = dag.nodes[u]
+    for key in dag.nodes:
         if key[0] != "var":
             continue
         v = key[1]
@@ -528,240 +608,185 @@ def compile_graph(order, roots):
             fk = ("V", v[1])
             L, dk = vfam.get(fk, (0, False))
             vfam[fk] = (max(L, v[2]), dk or v[0] == "Vd")
-        fam_uses[fk] += uses[u]
 
-    # momentum records needed (with parents) and their use counts
-    lay = prologue_layout(N)
-    fixed_mom = {}
-    for j in range(N + 1):
-        m = [0] * (N + 1)
-        m[j] = 1
-        fixed_mom[tuple(m)] = lay["kext"] if j == 0 else lay["k"][j]
-    mom_uses = collections.Counter()
-    needed = set()
+    def fam_of(v):
+        return ("G", v[1], v[2], v[3]) if v[0] in ("G", "Gd") else ("V", v[1])
 
-    def need(mom):
-        if mom in fixed_mom or mom in needed:
-            return
-        needed.add(mom)
-        par, _, _ = _mom_parent(mom)
-        if par is not None:
-            mom_uses[par] += 1
-            need(par)
+    def width(fk):
+        M, dk = gfam[fk] if fk[0] == "G" else vfam[fk]
+        return (M + 1) * (2 if dk else 1)
 
-    fermi_uses = collections.Counter()
-    for fk in gfam:
-        need(fk[1])
-        fermi_uses[fk[1]] += 1
-    for mom in set(fk[1] for fk in gfam):
-        mom_uses[mom] += 1            # its Fermi record
-    for fk in vfam:
-        need(fk[1])
-        mom_uses[fk[1]] += 1          # its V family
+    def operands(item):
+        if item[0] == "node":
+            return _kids(dag.nodes[item[1]])
+        if item[0] == "racc":
+            return [item[1]]
+        return []
 
-    # ---- emission ------------------------------------------------------------
-    n_roots = len(roots)
-    root_slots = [(lay["end"] + 2 * r, lay["end"] + 2 * r + 1) for r in range(n_roots)]
-    alloc = SlotAllocator(lay["end"] + 2 * n_roots)
+    # uses: families by group position, node use counts
+    fam_pos = collections.defaultdict(list)
+    node_uses = collections.Counter()
+    for pos, grp in enumerate(groups):
+        for it in grp:
+            for k in operands(it):
+                key = dag.nodes[k]
+                if key[0] == "var":
+                    if not fam_pos[fam_of(key[1])] or fam_pos[fam_of(key[1])][-1] != pos:
+                        fam_pos[fam_of(key[1])].append(pos)
+                else:
+                    node_uses[k] += 1
+    fam_ptr = collections.Counter()
+
+    # ---- pass 2: slots under the budget ---------------------------------------
+    consts = sorted({key[1] for key in dag.nodes if key[0] == "const"} |
+                    {key[2] for key in dag.nodes if key[0] == "mulc"})
+    alloc = SlotAllocator(FIXED_SLOTS)
     words = []
     stats = collections.Counter()
-    mom_slot = dict(fixed_mom)
-    fermi_slot = {}
-    fam_slot = {}          # family key -> (slot, width)
-    leaf_slot = {}
+    const_slot = {0.0: 0, 1.0: 1}
+    for c in consts:
+        if c not in const_slot:
+            const_slot[c] = alloc.alloc(1)
+            words.append(_enc_const(const_slot[c], c))
+            stats["consts"] += 1
+    resident = {}           # family -> slot
     node_slot = {}
-    const_slot = {}
 
-    def drop_mom(mom):
-        if mom in fixed_mom:
-            return
-        mom_uses[mom] -= 1
-        if mom_uses[mom] == 0:
-            alloc.release(mom_slot.pop(mom), 4)
+    def next_use(fk, pos):
+        lst = fam_pos[fk]
+        i = fam_ptr[fk]
+        while i < len(lst) and lst[i] < pos:
+            i += 1
+        fam_ptr[fk] = i
+        return lst[i] if i < len(lst) else None
 
-    def mom_record(mom):
-        if mom in mom_slot:
-            return mom_slot[mom]
-        par, k, c = _mom_parent(mom)
-        pa = mom_record(par)
-        d = alloc.alloc(4)
-        kslot = fixed_mom[tuple(1 if i == k else 0 for i in range(N + 1))]
-        words.append(_enc(OP_MOM, d=d, a=pa, b=kslot, imm=1 if c < 0 else 0))
-        stats["mom_ops"] += 1
-        mom_slot[mom] = d
-        drop_mom(par)
-        return d
+    def evict_for(k, pos, protect):
+        while alloc.live + k > budget:
+            cand = None
+            far = -1
+            for fk in resident:
+                if fk in protect:
+                    continue
+                nu = next_use(fk, pos)
+                d = 1 << 60 if nu is None else nu
+                if d > far:
+                    far, cand = d, fk
+            if cand is None:
+                return
+            alloc.release(resident.pop(cand), width(cand))
+            stats["evictions"] += 1
 
-    def fermi_record(mom):
-        if mom in fermi_slot:
-            return fermi_slot[mom]
-        m = mom_record(mom)
-        d = alloc.alloc(4)
-        words.append(_enc(OP_FERMI, d=d, a=m))
-        stats["fermi_ops"] += 1
-        fermi_slot[mom] = d
-        drop_mom(mom)
-        return d
-
-    def family(fk):
-        if fk in fam_slot:
-            return
+    def ensure(fk, pos, protect):
+        if fk in resident:
+            return resident[fk]
+        w = width(fk)
+        evict_for(w, pos, protect)
+        d = alloc.alloc(w)
         if fk[0] == "G":
             _, mom, la, lb = fk
             M, dk = gfam[fk]
-            f = fermi_record(mom)
-            width = (M + 1) * (2 if dk else 1)
-            d = alloc.alloc(width)
-            imm = M | (int(dk) << 3) | ((mom[0] + 1) << 4)
-            words.append(_enc(OP_GLEAF, d=d, a=f, b=lay["tx"][la], c=lay["tx"][lb], imm=imm))
+            words.append(_enc_leaf(OP_GLEAF, d, mom_mask(mom), la, lb, M, dk))
             stats["g_leaves"] += 1
-            fermi_uses[mom] -= 1
-            if fermi_uses[mom] == 0:
-                alloc.release(fermi_slot.pop(mom), 4)
-            for j in range(M + 1):
-                leaf_slot[("G", mom, la, lb, j)] = d + j
-                if dk:
-                    leaf_slot[("Gd", mom, la, lb, j)] = d + M + 1 + j
         else:
             _, mom = fk
             L, dk = vfam[fk]
-            m = mom_record(mom)
-            width = (L + 1) * (2 if dk else 1)
-            d = alloc.alloc(width)
-            imm = L | (int(dk) << 3) | ((mom[0] + 1) << 4)
-            words.append(_enc(OP_VLEAF, d=d, a=m, imm=imm))
+            words.append(_enc_leaf(OP_VLEAF, d, mom_mask(mom), 0, 0, L, dk))
             stats["v_leaves"] += 1
-            drop_mom(mom)
-            for j in range(L + 1):
-                leaf_slot[("V", mom, j)] = d + j
-                if dk:
-                    leaf_slot[("Vd", mom, j)] = d + L + 1 + j
-        fam_slot[fk] = (d, width)
+        resident[fk] = d
+        return d
 
-    def fam_key(v):
-        return ("G", v[1], v[2], v[3]) if v[0] in ("G", "Gd") else ("V", v[1])
-
-    def consume(k):
-        """One use of node k has been emitted; free its storage at the last use."""
-        uses[k] -= 1
-        if uses[k]:
-            return
+    def slot_of(k, pos, protect):
         key = dag.nodes[k]
         if key[0] == "var":
-            fk = fam_key(key[1])
-            fam_uses[fk] -= 1
-            if fam_uses[fk] == 0:
-                st, w = fam_slot.pop(fk)
-                alloc.release(st, w)
-        elif key[0] == "const":
-            pass
-        else:
-            alloc.release(node_slot[k], 1)
+            v = key[1]
+            fk = fam_of(v)
+            base = ensure(fk, pos, protect)
+            M = gfam[fk][0] if fk[0] == "G" else vfam[fk][0]
+            j = v[4] if fk[0] == "G" else v[2]
+            if v[0] in ("Gd", "Vd"):
+                j += M + 1
+            return base + j
+        if key[0] == "const":
+            return const_slot[key[1]]
+        return node_slot[k]
 
-    # register-need estimate (Sethi-Ullman on the tree view of the DAG); leaves
-    # count 0 because their families are allocated on demand
-    need_cache = {}
+    def drop_dead(pos):
+        for fk in list(resident):
+            if next_use(fk, pos + 1) is None:
+                alloc.release(resident.pop(fk), width(fk))
 
-    def need_of(u):
-        if u in need_cache:
-            return need_cache[u]
-        stk = [(u, False)]
-        while stk:
-            x, done = stk.pop()
-            if x in need_cache:
-                continue
-            ks = kids_of(dag.nodes[x])
-            if not done:
-                stk.append((x, True))
-                stk.extend((k, False) for k in ks if k not in need_cache)
-                continue
-            if not ks:
-                need_cache[x] = 0 if dag.nodes[x][0] in ("var", "const") else 1
-                continue
-            nk = sorted((need_cache[k] for k in ks), reverse=True)
-            need_cache[x] = max(max(v + i for i, v in enumerate(nk)), 1)
-        return need_cache[u]
+    def emit(word):
+        words.append(word)
 
-    def materialise(nid):
-        stack = [(nid, False)]
-        while stack:
-            u, expanded = stack.pop()
-            if u in node_slot:
-                continue
-            key = dag.nodes[u]
-            kind = key[0]
-            if kind == "var":
-                family(fam_key(key[1]))
-                node_slot[u] = leaf_slot[key[1]]
-                continue
-            if kind == "const":
-                c = key[1]
-                if c not in const_slot:
-                    d = alloc.alloc(1)
-                    words.append(_enc_f(OP_CONST, d, 0, c))
-                    const_slot[c] = d
-                node_slot[u] = const_slot[c]
-                continue
-            kids = kids_of(key)
-            if not expanded:
-                stack.append((u, True))
-                # evaluate the child with the largest need first
-                for k in sorted(kids, key=need_of):
-                    if k not in node_slot:
-                        stack.append((k, False))
-                continue
-            ks = [node_slot[k] for k in kids]
-            d = alloc.alloc(1)
-            if kind == "mul":
-                words.append(_enc(OP_MUL, d=d, a=ks[0], b=ks[1]))
-            elif kind == "add":
-                words.append(_enc(OP_ADD, d=d, a=ks[0], b=ks[1]))
-            elif kind == "fma":
-                words.append(_enc(OP_FMA, d=d, a=ks[0], b=ks[1], c=ks[2]))
+    def pad_to_fit(n):
+        # keep the next n words inside one tape chunk
+        if len(words) // CHUNK_WORDS != (len(words) + n - 1) // CHUNK_WORDS:
+            while len(words) % CHUNK_WORDS:
+                words.append(OP_NOP)
+                stats["nops"] += 1
+
+    def fma_word(u, ks, d):
+        kind = dag.nodes[u][0]
+        if kind == "mul":
+            return _enc_fma(d, ks[0], ks[1], 0)
+        if kind == "add":
+            return _enc_fma(d, ks[0], 1, ks[1])
+        if kind == "fma":
+            return _enc_fma(d, ks[0], ks[1], ks[2])
+        return _enc_fma(d, ks[0], const_slot[dag.nodes[u][2]], 0)     # mulc
+
+    for pos, grp in enumerate(groups):
+        protect = {fam_of(dag.nodes[k][1]) for it in grp for k in operands(it) if dag.nodes[k][0] == "var"}
+        if grp[0][0] == "node":
+            # operands first (leaf families are computed here when not resident)
+            opslots = [[slot_of(k, pos, protect) for k in operands(it)] for it in grp]
+            for it in grp:
+                for k in operands(it):
+                    if dag.nodes[k][0] not in ("var", "const"):
+                        node_uses[k] -= 1
+            for it in grp:
+                for k in set(operands(it)):
+                    if dag.nodes[k][0] not in ("var", "const") and node_uses[k] == 0 and k in node_slot:
+                        alloc.release(node_slot.pop(k), 1)
+                        node_uses[k] = -1
+            dests = []
+            for it in grp:
+                evict_for(1, pos, protect)
+                dests.append(alloc.alloc(1))
+            if len(grp) == 1:
+                pad_to_fit(1)
+                emit(fma_word(grp[0][1], opslots[0], dests[0]))
             else:
-                words.append(_enc_f(OP_MULC, d, ks[0], key[2]))
-            stats["arith"] += 1
-            node_slot[u] = d
-            for k in kids:
-                consume(k)
-        return node_slot[nid]
-
-    for (r, o, node) in outputs:
-        sl = materialise(node)
-        re, im = root_slots[r]
-        if o == 0:
-            words.append(_enc(OP_ROOT0, d=re, a=sl))
+                pad_to_fit(len(grp) + 1)
+                emit(OP_BUNDLE | (len(grp) << 6))
+                for it, ks, d in zip(grp, opslots, dests):
+                    emit(fma_word(it[1], ks, d))
+                stats["bundles"] += 1
+            for it, d in zip(grp, dests):
+                node_slot[it[1]] = d
+            stats["arith"] += len(grp)
         else:
-            words.append(_enc(OP_ROOT, d=re, a=sl, b=lay["cos"][o], c=lay["sin"][o]))
-        stats["root_ops"] += 1
-        consume(node)
-    words.append(_enc(OP_END))
-    stats["slots"] = alloc.top if not alloc.free else max(alloc.top, max(a + l for a, l in alloc.free))
-    stats["peak_slots"] = _peak(words)
-    stats["dag_nodes"] = len(reachable)
-    return Tape(N, list(roots), words, stats["peak_slots"], root_slots, dict(stats))
-
-
-def _peak(words):
-    """Highest slot index touched by the tape + 1 (the per-sample state size)."""
-    hi = 0
-    for w in words:
-        op = w & 63
-        d = (w >> 6) & 8191
-        if op == OP_END:
-            continue
-        if op in (OP_MOM, OP_FERMI):
-            hi = max(hi, d + 4)
-        elif op in (OP_GLEAF, OP_VLEAF):
-            imm = (w >> 58) & 63
-            M = imm & 7
-            dk = (imm >> 3) & 1
-            hi = max(hi, d + (M + 1) * (2 if dk else 1))
-        elif op == OP_ROOT:
-            hi = max(hi, d + 2)
-        else:
-            hi = max(hi, d + 1)
-    return hi
+            it = grp[0]
+            if it[0] == "racc":
+                k = it[1]
+                s_ = slot_of(k, pos, protect)
+                pad_to_fit(1)
+                emit(_enc_racc(s_, it[2]))
+                if dag.nodes[k][0] not in ("var", "const"):
+                    node_uses[k] -= 1
+                    if node_uses[k] == 0:
+                        alloc.release(node_slot.pop(k), 1)
+                stats["racc"] += 1
+            else:
+                pad_to_fit(1)
+                emit(_enc_flush(it[1]))
+        drop_dead(pos)
+    pad_to_fit(1)
+    words.append(OP_END)
+    stats["slots"] = alloc.peak
+    stats["budget"] = budget
+    stats["dag_nodes"] = len(emitted)
+    return Tape(N, list(roots), words, alloc.peak, dict(stats))
 
 
 def graph_roots(order, with_dk=False):
@@ -793,13 +818,15 @@ def _g_family_flops(M, dk):
 
 
 def tape_work(data):
-    """(fp32_flops, sfu_ops) per sample of a serialised tape, prologue and epilogue included.
+    """(fp32_flops, sfu_ops) per sample of a serialised tape, map and weighting included.
 
-    Counting rule (FMA = 2 flops, everything else 1): tape arithmetic as
-    written; MOM 8; FERMI 4 + 2 SFU (exp, rcp); G family per _g_family_flops
-    + 1 SFU (exp); V family 2 + (L + dk) + (dk: 2 + 2(L+1)) + 1 SFU (rcp);
-    per sample the map: 6 per VEGAS dimension, 14 + 2 SFU (sincospi, sqrt)
-    per loop momentum, 3 + 1 SFU per time, and 2 per root for the Jacobian.
+    Counting rule (FMA = 2 flops, other arithmetic 1): tape FMA as written
+    (a multiply by slot 1 = 1.0 or an add of slot 0 = 0.0 counts 1); a leaf's
+    momentum 3 (t - 1) for t terms plus |p|^2 5; G family: eps 1, Fermi factor
+    4 + 2 SFU (exp, rcp), the time part and series per _g_family_flops + 1 SFU
+    (exp); V family: 1 + 1 SFU (rcp) + 1 + (L + dk) + (dk: 2 + 2 (L + 1));
+    RACC 4; per sample the map: 6 per VEGAS dimension, 14 + 2 SFU (sincospi,
+    sqrt) per loop momentum, 3 + 1 SFU per time, 2 per root for the Jacobian.
     """
     hdr = struct.unpack("<16I", data[:64])
     order, dim, n_roots, n_instr, ins_off = hdr[2], hdr[3], hdr[4], hdr[6], hdr[8]
@@ -808,25 +835,24 @@ def tape_work(data):
     sfu = 0
     for w in words:
         op = w & 63
-        imm = (w >> 58) & 63
-        if op in (OP_MUL, OP_ADD, OP_MULC, OP_ROOT0):
-            flops += 1
-        elif op == OP_FMA:
-            flops += 2
-        elif op == OP_ROOT:
+        if op == OP_FMA:
+            b = (w >> 34) & 16383
+            c = (w >> 48) & 16383
+            flops += 1 if (c == 0 or b == 1) else 2
+        elif op in (OP_GLEAF, OP_VLEAF):
+            mask = (w >> 20) & 16383
+            terms = sum(1 for j in range(7) if (mask >> (2 * j)) & 3)
+            M = (w >> 40) & 7
+            dk = (w >> 43) & 1
+            flops += 3 * max(terms - 1, 0) + 5
+            if op == OP_GLEAF:
+                flops += 1 + 4 + _g_family_flops(M, dk)
+                sfu += 3
+            else:
+                flops += 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0)
+                sfu += 1
+        elif op == OP_RACC:
             flops += 4
-        elif op == OP_MOM:
-            flops += 8
-        elif op == OP_FERMI:
-            flops += 4
-            sfu += 2
-        elif op == OP_GLEAF:
-            flops += _g_family_flops(imm & 7, (imm >> 3) & 1)
-            sfu += 1
-        elif op == OP_VLEAF:
-            L, dk = imm & 7, (imm >> 3) & 1
-            flops += 2 + (L + dk) + ((2 + 2 * (L + 1)) if dk else 0)
-            sfu += 1
     flops += 6 * dim + 14 * order + 3 * (order - 1) + 2 * n_roots
     sfu += 2 * order + (order - 1)
     return flops, sfu

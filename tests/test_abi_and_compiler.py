@@ -40,27 +40,37 @@ def _load(data):
 
 def test_tape_validation_rejects_malformed_tapes():
     good = fdgraph.compile_graph(2, fdgraph.graph_roots(2)).to_bytes()
+    assert _load(good) in (L.FD_OK, L.FD_ECUDA)
     bad_magic = b"XXXX" + good[4:]
     assert _load(bad_magic) == L.FD_EFORMAT
     assert _load(good[:40]) == L.FD_EFORMAT                      # truncated
     hdr = list(struct.unpack("<16I", good[:64]))
-    # an instruction pointing past the slot count
-    words = list(struct.unpack("<%dQ" % hdr[6], good[hdr[8]:hdr[8] + 8 * hdr[6]]))
-    w = words[0]
-    w = (w & ~(8191 << 6)) | (8000 << 6)
-    bad = bytearray(good)
-    bad[hdr[8]:hdr[8] + 8] = struct.pack("<Q", w)
-    assert _load(bytes(bad)) == L.FD_EFORMAT
+    n_instr, off = hdr[6], hdr[8]
+    words = list(struct.unpack("<%dQ" % n_instr, good[off:off + 8 * n_instr]))
+
+    def patched(k, w):
+        bad = bytearray(good)
+        bad[off + 8 * k:off + 8 * k + 8] = struct.pack("<Q", w)
+        return bytes(bad)
+
+    k_fma = next(i for i, w in enumerate(words) if w & 63 == fdgraph.OP_FMA)
+    w = words[k_fma]
+    # destination slot beyond the declared slot count
+    assert _load(patched(k_fma, (w & ~(16383 << 6)) | (16000 << 6))) == L.FD_EFORMAT
+    # writing the fixed 0.0 slot
+    assert _load(patched(k_fma, w & ~(16383 << 6))) == L.FD_EFORMAT
     # unknown opcode
-    bad = bytearray(good)
-    bad[hdr[8]:hdr[8] + 8] = struct.pack("<Q", (words[0] & ~63) | 42)
-    assert _load(bytes(bad)) == L.FD_EFORMAT
+    assert _load(patched(k_fma, (w & ~63) | 42)) == L.FD_EFORMAT
+    # a leaf whose momentum mask names a variable beyond the order
+    k_leaf = next(i for i, w in enumerate(words) if w & 63 == fdgraph.OP_GLEAF)
+    wl = words[k_leaf] | (1 << (20 + 2 * 5))
+    assert _load(patched(k_leaf, wl)) == L.FD_EFORMAT
+    # a root flushed twice (and therefore another one never)
+    k_fl = [i for i, w in enumerate(words) if w & 63 == fdgraph.OP_RFLUSH]
+    assert _load(patched(k_fl[1], words[k_fl[0]])) == L.FD_EFORMAT
     # missing END
-    bad = bytearray(good)
-    last = hdr[8] + 8 * (hdr[6] - 1)
-    bad[last:last + 8] = struct.pack("<Q", words[0])
-    assert _load(bytes(bad)) == L.FD_EFORMAT
-    assert b"END" in L.lib().fd_last_error() or len(L.lib().fd_last_error()) > 0
+    assert _load(patched(n_instr - 1, words[k_fma])) == L.FD_EFORMAT
+    assert len(L.lib().fd_last_error()) > 0
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4])
