@@ -28,6 +28,23 @@ import numpy as np
 
 S_CLAMP = 5.0
 
+_PREC = {"mode": "f64"}
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as FP64."""
+    a32 = np.asarray(a, dtype=np.float32)
+    u = a32.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def set_precision(mode):
+    """'f64' (default) or 'bf16': the configured BF16 weight/activation contract
+    (weights and every GEMM input rounded to BF16, FP64 accumulation)."""
+    assert mode in ("f64", "bf16")
+    _PREC["mode"] = mode
+
 
 def layer_split(dim, layer):
     h = (dim + 1) // 2
@@ -69,8 +86,13 @@ def pack(layers):
 
 def _mlp(p, a):
     W1, b1, W2, b2, W3, b3 = p
-    h1 = np.maximum(W1 @ a + b1[:, None], 0.0)
-    h2 = np.maximum(W2 @ h1 + b2[:, None], 0.0)
+    if _PREC["mode"] == "bf16":
+        W1, W2, W3, a = bf16(W1), bf16(W2), bf16(W3), bf16(a)
+        h1 = bf16(np.maximum(W1 @ a + b1[:, None], 0.0))
+        h2 = bf16(np.maximum(W2 @ h1 + b2[:, None], 0.0))
+    else:
+        h1 = np.maximum(W1 @ a + b1[:, None], 0.0)
+        h2 = np.maximum(W2 @ h1 + b2[:, None], 0.0)
     o = W3 @ h2 + b3[:, None]
     return h1, h2, o
 
@@ -139,6 +161,9 @@ def loss_and_grad(blob, x, w, dim, n_layers, hidden):
         W1, b1, W2, b2, W3, b3 = layers[l]
         A, B = layer_split(dim, l)
         a, h1, h2, s, vB = saved[l]
+        if _PREC["mode"] == "bf16":
+            a = bf16(a)
+            W1, W2, W3 = bf16(W1), bf16(W2), bf16(W3)
         es = np.exp(-s)
         gB = g[B]
         g_t = -gB * es

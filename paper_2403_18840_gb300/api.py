@@ -174,6 +174,57 @@ class EvalPlan:
         return self.stats
 
 
+class Flow:
+    """Affine coupling flow with BF16 tensor-core kernels (FP32 master weights)."""
+
+    def __init__(self, dim, n_layers=8, hidden=128, seed=0):
+        h = ctypes.c_void_p()
+        L.check(L.lib().fd_flow_create(dim, n_layers, hidden, seed, ctypes.byref(h)))
+        self.handle, self.dim, self.n_layers, self.hidden = h, dim, n_layers, hidden
+        self.n_params = L.lib().fd_flow_param_count(h)
+
+    def set_params(self, blob):
+        b = np.ascontiguousarray(blob, dtype=np.float32)
+        assert b.size == self.n_params
+        L.check(L.lib().fd_flow_set_params(self.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), b.size))
+
+    def params(self):
+        b = np.empty(self.n_params, dtype=np.float32)
+        L.check(L.lib().fd_flow_get_params(self.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), b.size))
+        return b
+
+    def sample(self, seed, it, inst, n, stream=None):
+        x = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")
+        w = torch.empty((n,), dtype=torch.float32, device="cuda")
+        L.check(L.lib().fd_flow_sample(self.handle, seed, it, inst, n, _ptr(x), _ptr(w), _stream_ptr(stream)))
+        return x, w
+
+    def log_density(self, x, stream=None):
+        n = x.shape[1]
+        lq = torch.empty((n,), dtype=torch.float32, device="cuda")
+        L.check(L.lib().fd_flow_log_density(self.handle, _ptr(x), n, _ptr(lq), _stream_ptr(stream)))
+        return lq
+
+    def grad(self, x, w, stream=None):
+        n = x.shape[1]
+        loss = torch.empty((1,), dtype=torch.float32, device="cuda")
+        g = torch.empty((self.n_params,), dtype=torch.float32, device="cuda")
+        L.check(L.lib().fd_flow_grad(self.handle, _ptr(x), _ptr(w), n, _ptr(loss), _ptr(g), _stream_ptr(stream)))
+        return loss, g
+
+    def train(self, x, w, steps, lr, stream=None):
+        out = np.empty(steps, dtype=np.float32)
+        L.check(L.lib().fd_flow_train(self.handle, _ptr(x), _ptr(w), x.shape[1], steps, lr,
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream_ptr(stream)))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.fd_flow_free(h)
+            self.handle = None
+
+
 def device_status(stream=None):
     L.check(L.lib().fd_device_status(_stream_ptr(stream)))
 

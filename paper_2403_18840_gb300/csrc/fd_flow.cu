@@ -1,27 +1,1148 @@
-// Affine coupling flow: entry points (kernels follow in this file).
+// Affine coupling normalizing flow on the unit hypercube (Appendix A:
+// composition of coupling layers, Eq. coupling_layer; density by change of
+// variables, Eq. NFtransform; forward-KL training).  Hand-written BF16
+// tensor-core kernels (mma.sync m16n8k16, FP32 accumulation) for sm_103a.
+//
+// Layer l: the conditioning half A (first ceil(D/2) coordinates on even
+// layers, the rest on odd ones) feeds an MLP a -> 128 -> 128 -> 2b (ReLU);
+// its outputs are s_raw (rows 0..b-1 of W3) and t (rows b..2b-1);
+// s = 5 tanh(s_raw / 5); y_B <- y_B exp(s) + t.  The flow acts in logit space:
+// y = logit(z) for the uniform base z, x = sigmoid(y).
+//
+// Device layout of one layer's BF16 weights (contiguous, 16-byte aligned,
+// staged into shared memory by one 1-D TMA bulk copy):
+//   W1p [128][24]  (in padded 16, row stride 24)      6144 B
+//   W2  [128][136] (row stride 136)                  34816 B
+//   W3p [32][136]  (rows 0..15 s_raw, 16..31 t)       8704 B
+//   b1 [128], b2 [128], b3p [32] FP32                  1152 B
+// Warp tiles are 16 samples; the three GEMMs chain in registers (accumulator
+// fragments become the next GEMM's A fragments).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
 #include "fd_internal.cuh"
 
-extern "C" fd_status fd_flow_create(int32_t, int32_t, int32_t, uint64_t, fd_flow **out) {
-    if (out) *out = nullptr;
-    return fd::set_error(FD_ENOTSUP, "flow kernels not built yet");
+namespace {
+
+constexpr int H = 128;
+constexpr int W1_LD = 24, W2_LD = 136, W3_LD = 136;
+constexpr int OFF_W1 = 0;
+constexpr int OFF_W2 = OFF_W1 + H * W1_LD * 2;        // 6144
+constexpr int OFF_W3 = OFF_W2 + H * W2_LD * 2;        // 40960
+constexpr int OFF_B1 = OFF_W3 + 32 * W3_LD * 2;       // 49664
+constexpr int OFF_B2 = OFF_B1 + H * 4;
+constexpr int OFF_B3 = OFF_B2 + H * 4;
+constexpr int LAYER_BYTES = OFF_B3 + 32 * 4;          // 50816
+constexpr int YS = 24;                                // padded coordinates per sample row
+constexpr float S_CLAMP = 5.0f;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+
+static_assert(LAYER_BYTES % 16 == 0, "layer block must be 16-byte sized");
+
+struct FlowDims {
+    int D, K, h;          // dimension, layers, first-half size ceil(D/2)
+};
+
+__device__ __forceinline__ int a_size(const FlowDims &f, int l) { return (l % 2 == 0) ? f.h : f.D - f.h; }
+__device__ __forceinline__ int b_size(const FlowDims &f, int l) { return (l % 2 == 0) ? f.D - f.h : f.h; }
+__device__ __forceinline__ int a_idx(const FlowDims &f, int l, int i) { return (l % 2 == 0) ? i : f.h + i; }
+__device__ __forceinline__ int b_idx(const FlowDims &f, int l, int j) { return (l % 2 == 0) ? f.h + j : j; }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
 }
-extern "C" void fd_flow_free(fd_flow *) {}
-extern "C" int64_t fd_flow_param_count(const fd_flow *) { return 0; }
-extern "C" fd_status fd_flow_set_params(fd_flow *, const float *, int64_t) {
-    return fd::set_error(FD_ENOTSUP, "flow kernels not built yet");
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-extern "C" fd_status fd_flow_get_params(const fd_flow *, float *, int64_t) {
-    return fd::set_error(FD_ENOTSUP, "flow kernels not built yet");
+
+// B fragment of B[k][n] = W[n][k] (W row-major [n][k], i.e. B column-major)
+__device__ __forceinline__ void bfrag(const __nv_bfloat16 *W, int ld, int kt, int nt, int g, int t, uint32_t &b0,
+                                      uint32_t &b1) {
+    const __nv_bfloat16 *p = W + (nt * 8 + g) * ld + kt * 16 + 2 * t;
+    b0 = *reinterpret_cast<const uint32_t *>(p);
+    b1 = *reinterpret_cast<const uint32_t *>(p + 8);
 }
-extern "C" fd_status fd_flow_sample(const fd_flow *, uint64_t, uint64_t, int32_t, int64_t, float *, float *, void *) {
-    return fd::set_error(FD_ENOTSUP, "flow kernels not built yet");
+// B fragment of B[k][n] = W[k][n] (W row-major [k][n]: transposed access)
+__device__ __forceinline__ void bfrag_t(const __nv_bfloat16 *W, int ld, int kt, int nt, int g, int t, uint32_t &b0,
+                                        uint32_t &b1) {
+    const uint16_t *p = reinterpret_cast<const uint16_t *>(W) + (kt * 16 + 2 * t) * ld + nt * 8 + g;
+    b0 = (uint32_t)p[0] | ((uint32_t)p[ld] << 16);
+    b1 = (uint32_t)p[8 * ld] | ((uint32_t)p[9 * ld] << 16);
 }
-extern "C" fd_status fd_flow_log_density(const fd_flow *, const float *, int64_t, float *, void *) {
-    return fd::set_error(FD_ENOTSUP, "flow kernels not built yet");
+
+// accumulator tiles (2j, 2j+1) -> A fragment of k-tile j
+__device__ __forceinline__ void c_to_a(const float (&c0)[4], const float (&c1)[4], uint32_t (&a)[4]) {
+    a[0] = pack_bf16(c0[0], c0[1]);
+    a[1] = pack_bf16(c0[2], c0[3]);
+    a[2] = pack_bf16(c1[0], c1[1]);
+    a[3] = pack_bf16(c1[2], c1[3]);
 }
-extern "C" fd_status fd_flow_grad(fd_flow *, const float *, const float *, int64_t, float *, float *, void *) {
-    return fd::set_error(FD_ENOTSUP, "flow kernels not built yet");
+
+struct LayerSmem {
+    const __nv_bfloat16 *W1, *W2, *W3;
+    const float *b1, *b2, *b3;
+};
+
+__device__ __forceinline__ LayerSmem layer_view(const unsigned char *base) {
+    LayerSmem L;
+    L.W1 = reinterpret_cast<const __nv_bfloat16 *>(base + OFF_W1);
+    L.W2 = reinterpret_cast<const __nv_bfloat16 *>(base + OFF_W2);
+    L.W3 = reinterpret_cast<const __nv_bfloat16 *>(base + OFF_W3);
+    L.b1 = reinterpret_cast<const float *>(base + OFF_B1);
+    L.b2 = reinterpret_cast<const float *>(base + OFF_B2);
+    L.b3 = reinterpret_cast<const float *>(base + OFF_B3);
+    return L;
 }
-extern "C" fd_status fd_flow_train(fd_flow *, const float *, const float *, int64_t, int32_t, float, float *, void *) {
-    return fd::set_error(FD_ENOTSUP, "flow kernels not built yet");
+
+// MLP on one 16-sample tile: input A fragment (16 x 16, zero-padded) ->
+// h1, h2 as A fragments (post-ReLU, BF16) and o = [s_raw | t] accumulators.
+__device__ __forceinline__ void mlp_forward(const LayerSmem &L, const uint32_t (&ain)[4], uint32_t (&h1a)[8][4],
+                                            uint32_t (&h2a)[8][4], float (&o)[4][4], int g, int t) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+        uint32_t b0, b1;
+        bfrag(L.W1, W1_LD, 0, 2 * j, g, t, b0, b1);
+        mma16816(c0, ain, b0, b1);
+        bfrag(L.W1, W1_LD, 0, 2 * j + 1, g, t, b0, b1);
+        mma16816(c1, ain, b0, b1);
+        const float u0 = L.b1[16 * j + 2 * t], u1 = L.b1[16 * j + 2 * t + 1];
+        const float u2 = L.b1[16 * j + 8 + 2 * t], u3 = L.b1[16 * j + 9 + 2 * t];
+        c0[0] = fmaxf(c0[0] + u0, 0.f);
+        c0[1] = fmaxf(c0[1] + u1, 0.f);
+        c0[2] = fmaxf(c0[2] + u0, 0.f);
+        c0[3] = fmaxf(c0[3] + u1, 0.f);
+        c1[0] = fmaxf(c1[0] + u2, 0.f);
+        c1[1] = fmaxf(c1[1] + u3, 0.f);
+        c1[2] = fmaxf(c1[2] + u2, 0.f);
+        c1[3] = fmaxf(c1[3] + u3, 0.f);
+        c_to_a(c0, c1, h1a[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < 8; ++kt) {
+            uint32_t b0, b1;
+            bfrag(L.W2, W2_LD, kt, 2 * j, g, t, b0, b1);
+            mma16816(c0, h1a[kt], b0, b1);
+            bfrag(L.W2, W2_LD, kt, 2 * j + 1, g, t, b0, b1);
+            mma16816(c1, h1a[kt], b0, b1);
+        }
+        const float u0 = L.b2[16 * j + 2 * t], u1 = L.b2[16 * j + 2 * t + 1];
+        const float u2 = L.b2[16 * j + 8 + 2 * t], u3 = L.b2[16 * j + 9 + 2 * t];
+        c0[0] = fmaxf(c0[0] + u0, 0.f);
+        c0[1] = fmaxf(c0[1] + u1, 0.f);
+        c0[2] = fmaxf(c0[2] + u0, 0.f);
+        c0[3] = fmaxf(c0[3] + u1, 0.f);
+        c1[0] = fmaxf(c1[0] + u2, 0.f);
+        c1[1] = fmaxf(c1[1] + u3, 0.f);
+        c1[2] = fmaxf(c1[2] + u2, 0.f);
+        c1[3] = fmaxf(c1[3] + u3, 0.f);
+        c_to_a(c0, c1, h2a[j]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[nt][q] = 0.f;
+#pragma unroll
+        for (int kt = 0; kt < 8; ++kt) {
+            uint32_t b0, b1;
+            bfrag(L.W3, W3_LD, kt, nt, g, t, b0, b1);
+            mma16816(o[nt], h2a[kt], b0, b1);
+        }
+        const float u0 = L.b3[nt * 8 + 2 * t], u1 = L.b3[nt * 8 + 2 * t + 1];
+        o[nt][0] += u0;
+        o[nt][1] += u1;
+        o[nt][2] += u0;
+        o[nt][3] += u1;
+    }
+}
+
+// A fragment of the conditioning half of a 16-row tile of coordinates (smem rows of YS floats)
+__device__ __forceinline__ void input_frag(const float *ys, const FlowDims &f, int l, int g, int t, uint32_t (&a)[4]) {
+    const int na = a_size(f, l);
+    auto v = [&](int row, int i) { return i < na ? ys[row * YS + a_idx(f, l, i)] : 0.f; };
+    a[0] = pack_bf16(v(g, 2 * t), v(g, 2 * t + 1));
+    a[1] = pack_bf16(v(g + 8, 2 * t), v(g + 8, 2 * t + 1));
+    a[2] = pack_bf16(v(g, 8 + 2 * t), v(g, 9 + 2 * t));
+    a[3] = pack_bf16(v(g + 8, 8 + 2 * t), v(g + 8, 9 + 2 * t));
+}
+
+// (row, j) of accumulator element q of n-tile nt (0..1 -> s, 2..3 -> t)
+__device__ __forceinline__ int c_row(int q, int g) { return (q < 2) ? g : g + 8; }
+__device__ __forceinline__ int c_col(int nt, int q, int t) { return (nt & 1) * 8 + 2 * t + (q & 1); }
+
+// Apply the affine coupling to a 16-row tile; dir = +1 forward, -1 inverse.
+// ld[row] += sum_j s (forward) / -= (inverse), reduced over the quad.
+__device__ __forceinline__ void coupling(float *ys, float *ld, const FlowDims &f, int l, const float (&o)[4][4],
+                                         int g, int t, float dir) {
+    const int nb = b_size(f, l);
+    float part[2] = {0.f, 0.f};
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = c_col(half, q, t);
+            if (j < nb) {
+                const int row = c_row(q, g);
+                const float s = S_CLAMP * tanhf(o[half][q] * (1.0f / S_CLAMP));
+                const float tt = o[half + 2][q];
+                float &y = ys[row * YS + b_idx(f, l, j)];
+                y = dir > 0.f ? fmaf(y, __expf(s), tt) : (y - tt) * __expf(-s);
+                part[q >> 1] += s;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        part[r] += __shfl_xor_sync(0xffffffffu, part[r], 1);
+        part[r] += __shfl_xor_sync(0xffffffffu, part[r], 2);
+    }
+    if (t == 0) {
+        ld[g] += dir * part[0];
+        ld[g + 8] += dir * part[1];
+    }
+}
+
+__device__ __forceinline__ float log_sig_deriv(float y) {
+    // log(sigmoid(y) (1 - sigmoid(y))) = -|y| - 2 log(1 + exp(-|y|))
+    const float a = fabsf(y);
+    return -a - 2.0f * log1pf(__expf(-a));
+}
+
+// Stage layer l's weights into smem with a TMA bulk copy; bounded wait.
+__device__ __forceinline__ bool stage_layer(unsigned char *wsm, const unsigned char *wglob, int l, uint64_t *bar,
+                                            uint32_t &phase) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_expect_tx(bar, LAYER_BYTES);
+        bulk_g2s(wsm, wglob + (size_t)l * LAYER_BYTES, LAYER_BYTES, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, phase & 1u, WAIT_LIMIT);
+    const bool anyfail = __syncthreads_or(!ok);
+    if (!anyfail) ++phase;
+    return !anyfail;
+}
+
+// ---- sampling / density kernel -------------------------------------------------------
+// mode 0: z from Philox -> x, w = 1/q.   mode 1: x given -> log q(x).
+// CTA = 4 warps; block of 64 * ROUNDS samples processed layer-major so each
+// layer's weights are staged once per block.
+constexpr int ROUNDS = 4;
+constexpr int BLOCK = 64 * ROUNDS;
+
+__global__ void __launch_bounds__(128) flow_pass_kernel(const unsigned char *__restrict__ wglob, FlowDims f, int mode,
+                                                         int64_t n, uint32_t seed_lo, uint32_t seed_hi,
+                                                         uint32_t iter, uint32_t inst, const float *__restrict__ xin,
+                                                         float *__restrict__ xout, float *__restrict__ wout,
+                                                         int *status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *wsm = smem;
+    float *ys = reinterpret_cast<float *>(smem + LAYER_BYTES);     // [BLOCK][YS]
+    float *ld = ys + BLOCK * YS;                                    // [BLOCK]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ld + BLOCK);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const int64_t nblocks = (n + BLOCK - 1) / BLOCK;
+    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const int64_t base = blk * BLOCK;
+        // load / generate the block's coordinates (y = logit) and the log-Jacobian start
+        for (int r = tid; r < BLOCK; r += blockDim.x) {
+            const int64_t i = base + r;
+            const bool valid = i < n;
+            float acc = 0.f;
+            if (mode == 0) {
+                const int64_t ii = valid ? i : base;
+                const uint32_t c0 = (uint32_t)(uint64_t)ii, c1 = (uint32_t)((uint64_t)ii >> 32);
+                for (int blk4 = 0; 4 * blk4 < f.D; ++blk4) {
+                    const u32x4 rr = philox4x32_10(u32x4{c0, c1, iter, (inst << 8) | (uint32_t)blk4}, seed_lo, seed_hi);
+                    const uint32_t wv[4] = {rr.x, rr.y, rr.z, rr.w};
+                    for (int q = 0; q < 4 && 4 * blk4 + q < f.D; ++q) {
+                        const float z = word_to_uniform(wv[q]);
+                        const float y = __logf(z) - log1pf(-z);
+                        ys[r * YS + 4 * blk4 + q] = y;
+                        acc -= log_sig_deriv(y);            // log dy/dz
+                    }
+                }
+            } else {
+                for (int d = 0; d < f.D; ++d) {
+                    const float x = valid ? xin[(int64_t)d * n + i] : 0.5f;
+                    const float y = __logf(x) - log1pf(-x);
+                    ys[r * YS + d] = y;
+                    acc -= log_sig_deriv(y);                // log q gains -log dx/dy
+                }
+            }
+            for (int d = f.D; d < YS; ++d) ys[r * YS + d] = 0.f;
+            ld[r] = acc;
+        }
+        for (int step = 0; step < f.K; ++step) {
+            const int l = mode == 0 ? step : f.K - 1 - step;
+            if (!stage_layer(wsm, wglob, l, bar, phase)) {
+                if (tid == 0 && status) atomicExch(status, DEV_ST_TIMEOUT);
+                return;
+            }
+            const LayerSmem L = layer_view(wsm);
+            for (int r = 0; r < ROUNDS; ++r) {
+                float *tile = ys + (size_t)(r * 64 + warp * 16) * YS;
+                float *tld = ld + r * 64 + warp * 16;
+                uint32_t ain[4], h1a[8][4], h2a[8][4];
+                float o[4][4];
+                input_frag(tile, f, l, g, t, ain);
+                mlp_forward(L, ain, h1a, h2a, o, g, t);
+                coupling(tile, tld, f, l, o, g, t, mode == 0 ? 1.f : -1.f);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int r = tid; r < BLOCK; r += blockDim.x) {
+            const int64_t i = base + r;
+            if (i >= n) continue;
+            float acc = ld[r];
+            for (int d = 0; d < f.D; ++d) {
+                const float y = ys[r * YS + d];
+                acc += log_sig_deriv(y);
+                if (mode == 0) xout[(int64_t)d * n + i] = 1.0f / (1.0f + __expf(-y));
+            }
+            // mode 0: acc = log |det dx/dz|, w = 1/q = exp(acc); mode 1: acc = log q(x)
+            if (mode == 0) wout[i] = __expf(acc);
+            else wout[i] = acc;
+        }
+        __syncthreads();   // the next block reuses the coordinate tiles
+    }
+}
+
+// ---- training: inverse pass with loss and initial gradient -----------------------------
+// v = logit(x) through layers K-1..0; L = -sum w_hat log q; dL/dv0 = -(1 - 2 z) w_hat.
+// Writes v0 [D][n], g [D][n]; adds its part of the loss to *loss.
+__global__ void __launch_bounds__(128) flow_inverse_train_kernel(const unsigned char *__restrict__ wglob, FlowDims f,
+                                                                  int64_t n, const float *__restrict__ xin,
+                                                                  const float *__restrict__ w,
+                                                                  const double *__restrict__ wsum,
+                                                                  float *__restrict__ vout, float *__restrict__ gout,
+                                                                  float *__restrict__ loss, int *status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *wsm = smem;
+    float *ys = reinterpret_cast<float *>(smem + LAYER_BYTES);
+    float *ld = ys + BLOCK * YS;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ld + BLOCK);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const float inv_wsum = (float)(1.0 / *wsum);
+    const int64_t nblocks = (n + BLOCK - 1) / BLOCK;
+    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const int64_t base = blk * BLOCK;
+        for (int r = tid; r < BLOCK; r += blockDim.x) {
+            const int64_t i = base + r;
+            float acc = 0.f;
+            for (int d = 0; d < f.D; ++d) {
+                const float x = i < n ? xin[(int64_t)d * n + i] : 0.5f;
+                const float y = __logf(x) - log1pf(-x);
+                ys[r * YS + d] = y;
+                acc -= log_sig_deriv(y);
+            }
+            for (int d = f.D; d < YS; ++d) ys[r * YS + d] = 0.f;
+            ld[r] = acc;
+        }
+        for (int step = 0; step < f.K; ++step) {
+            const int l = f.K - 1 - step;
+            if (!stage_layer(wsm, wglob, l, bar, phase)) {
+                if (tid == 0 && status) atomicExch(status, DEV_ST_TIMEOUT);
+                return;
+            }
+            const LayerSmem L = layer_view(wsm);
+            for (int r = 0; r < ROUNDS; ++r) {
+                float *tile = ys + (size_t)(r * 64 + warp * 16) * YS;
+                float *tld = ld + r * 64 + warp * 16;
+                uint32_t ain[4], h1a[8][4], h2a[8][4];
+                float o[4][4];
+                input_frag(tile, f, l, g, t, ain);
+                mlp_forward(L, ain, h1a, h2a, o, g, t);
+                coupling(tile, tld, f, l, o, g, t, -1.f);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        float part = 0.f;
+        for (int r = tid; r < BLOCK; r += blockDim.x) {
+            const int64_t i = base + r;
+            if (i >= n) continue;
+            const float wh = w[i] * inv_wsum;
+            float logq = ld[r];
+            for (int d = 0; d < f.D; ++d) {
+                const float v = ys[r * YS + d];
+                logq += log_sig_deriv(v);
+                const float z = 1.0f / (1.0f + __expf(-v));
+                vout[(int64_t)d * n + i] = v;
+                gout[(int64_t)d * n + i] = -(1.0f - 2.0f * z) * wh;
+            }
+            part -= wh * logq;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        if (lane == 0) atomicAdd(loss, part);
+        __syncthreads();   // the next block reuses the coordinate tiles
+    }
+}
+
+// ---- training: backward through one layer ----------------------------------------------
+// For layer l (processed in the order 0..K-1 after the inverse pass): recompute
+// the MLP on v_A, propagate g through the coupling and the MLP, move v to the
+// previous boundary (v_B <- v_B e^s + t) and accumulate the layer's weight
+// gradients: dW2 in shared memory (FP32), dW1/dW3/biases in registers and
+// shared memory, added to the global FP32 gradient at the end.
+constexpr int TPAD = 72;   // padded sample stride of the transposed tiles (64 samples)
+
+struct BwdSmem {
+    // byte offsets
+    static constexpr int W = 0;
+    static constexpr int DW2 = W + LAYER_BYTES;                       // [128][128] f32
+    static constexpr int DB = DW2 + H * H * 4;                        // db1[128], db2[128], db3[32] f32
+    static constexpr int H1T = DB + (H + H + 32) * 4;                 // [128][TPAD] bf16
+    static constexpr int H2T = H1T + H * TPAD * 2;
+    static constexpr int GH1T = H2T + H * TPAD * 2;
+    static constexpr int GH2T = GH1T + H * TPAD * 2;
+    static constexpr int GOT = GH2T + H * TPAD * 2;                   // [32][TPAD]
+    static constexpr int AT = GOT + 32 * TPAD * 2;                    // [16][TPAD]
+    static constexpr int VT = AT + 16 * TPAD * 2;                     // v, g tiles [64][YS] f32 each
+    static constexpr int GT = VT + 64 * YS * 4;
+    static constexpr int BAR = GT + 64 * YS * 4;
+    static constexpr int TOTAL = BAR + 16;
+};
+
+__device__ __forceinline__ void st_bf16(__nv_bfloat16 *base, int row, int col, float v) {
+    base[row * TPAD + col] = __float2bfloat16_rn(v);
+}
+
+__global__ void __launch_bounds__(128) flow_backward_layer_kernel(const unsigned char *__restrict__ wglob, FlowDims f,
+                                                                   int l, int64_t n, const float *__restrict__ w,
+                                                                   const double *__restrict__ wsum,
+                                                                   float *__restrict__ vbuf, float *__restrict__ gbuf,
+                                                                   float *__restrict__ grad_layer, int *status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    float *dW2 = reinterpret_cast<float *>(smem + BwdSmem::DW2);
+    float *db = reinterpret_cast<float *>(smem + BwdSmem::DB);
+    __nv_bfloat16 *h1T = reinterpret_cast<__nv_bfloat16 *>(smem + BwdSmem::H1T);
+    __nv_bfloat16 *h2T = reinterpret_cast<__nv_bfloat16 *>(smem + BwdSmem::H2T);
+    __nv_bfloat16 *gh1T = reinterpret_cast<__nv_bfloat16 *>(smem + BwdSmem::GH1T);
+    __nv_bfloat16 *gh2T = reinterpret_cast<__nv_bfloat16 *>(smem + BwdSmem::GH2T);
+    __nv_bfloat16 *goT = reinterpret_cast<__nv_bfloat16 *>(smem + BwdSmem::GOT);
+    __nv_bfloat16 *aT = reinterpret_cast<__nv_bfloat16 *>(smem + BwdSmem::AT);
+    float *vt = reinterpret_cast<float *>(smem + BwdSmem::VT);
+    float *gt = reinterpret_cast<float *>(smem + BwdSmem::GT);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + BwdSmem::BAR);
+    for (int k = tid; k < H * H + H + H + 32; k += blockDim.x) {
+        if (k < H * H) dW2[k] = 0.f;
+        else db[k - H * H] = 0.f;
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbarrier_init();
+    }
+    uint32_t phase = 0;
+    if (!stage_layer(smem + BwdSmem::W, wglob, l, bar, phase)) {
+        if (tid == 0 && status) atomicExch(status, DEV_ST_TIMEOUT);
+        return;
+    }
+    const LayerSmem L = layer_view(smem + BwdSmem::W);
+    const int na = a_size(f, l), nb = b_size(f, l);
+    const float inv_wsum = (float)(1.0 / *wsum);
+    // register accumulators of dW3 (warp: n-tiles 4w..4w+3, both m-tiles) and dW1 (rows 32w..32w+31)
+    float dw3[2][4][4], dw1[2][2][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dw3[a][b][q] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dw1[a][b][q] = 0.f;
+
+    const int64_t nrounds = (n + 63) / 64;
+    for (int64_t rnd = blockIdx.x; rnd < nrounds; rnd += gridDim.x) {
+        const int64_t base = rnd * 64;
+        // load v and g tiles (64 samples)
+        for (int k = tid; k < 64 * YS; k += blockDim.x) {
+            const int r = k / YS, d = k % YS;
+            const int64_t i = base + r;
+            const bool ok = i < n && d < f.D;
+            vt[k] = ok ? vbuf[(int64_t)d * n + i] : 0.f;
+            gt[k] = ok ? gbuf[(int64_t)d * n + i] : 0.f;
+        }
+        __syncthreads();
+        float *tv = vt + warp * 16 * YS;
+        float *tg = gt + warp * 16 * YS;
+        const int col0 = warp * 16;       // sample column of this warp in the transposed tiles
+        {
+            uint32_t ain[4], h1a[8][4], h2a[8][4];
+            float o[4][4];
+            input_frag(tv, f, l, g, t, ain);
+            mlp_forward(L, ain, h1a, h2a, o, g, t);
+            // coupling backward (loss weight w_hat per sample row)
+            float go[4][4];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = c_col(half, q, t);
+                    const int row = c_row(q, g);
+                    const int64_t i = base + col0 + row;
+                    float gs = 0.f, gtt = 0.f;
+                    if (j < nb && i < n) {
+                        const float s = S_CLAMP * tanhf(o[half][q] * (1.0f / S_CLAMP));
+                        const float tt = o[half + 2][q];
+                        const int c = b_idx(f, l, j);
+                        const float vB = tv[row * YS + c];
+                        const float gB = tg[row * YS + c];
+                        const float es = __expf(-s);
+                        gtt = -gB * es;
+                        const float g_s = -gB * vB + w[i] * inv_wsum;
+                        gs = g_s * (1.0f - (s / S_CLAMP) * (s / S_CLAMP));
+                        tg[row * YS + c] = gB * es;
+                        tv[row * YS + c] = fmaf(vB, __expf(s), tt);
+                    }
+                    go[half][q] = gs;
+                    go[half + 2][q] = gtt;
+                }
+            }
+            // transposed tiles for the weight gradients: a, h1, h2, g_o
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // a fragment layout: ain regs hold (row, col) pairs of the 16 x 16 input tile
+                const int row = (q & 1) ? g + 8 : g;
+                const int cc = (q >> 1) * 8 + 2 * t;
+                st_bf16(aT, cc, col0 + row, bf_lo(ain[q]));
+                st_bf16(aT, cc + 1, col0 + row, bf_hi(ain[q]));
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = (q & 1) ? g + 8 : g;
+                    const int cc = 16 * j + (q >> 1) * 8 + 2 * t;
+                    st_bf16(h1T, cc, col0 + row, bf_lo(h1a[j][q]));
+                    st_bf16(h1T, cc + 1, col0 + row, bf_hi(h1a[j][q]));
+                    st_bf16(h2T, cc, col0 + row, bf_lo(h2a[j][q]));
+                    st_bf16(h2T, cc + 1, col0 + row, bf_hi(h2a[j][q]));
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = c_row(q, g);
+                    const int cc = nt * 8 + 2 * t + (q & 1);
+                    st_bf16(goT, cc, col0 + row, go[nt][q]);
+                }
+            }
+            // g_h2 = g_o W3 (B[k][n] = W3[k][n]), masked by h2 > 0
+            uint32_t ga[2][4];
+            c_to_a(go[0], go[1], ga[0]);
+            c_to_a(go[2], go[3], ga[1]);
+            uint32_t gh2a[8][4];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int kt = 0; kt < 2; ++kt) {
+                    uint32_t b0, b1;
+                    bfrag_t(L.W3, W3_LD, kt, 2 * j, g, t, b0, b1);
+                    mma16816(c0, ga[kt], b0, b1);
+                    bfrag_t(L.W3, W3_LD, kt, 2 * j + 1, g, t, b0, b1);
+                    mma16816(c1, ga[kt], b0, b1);
+                }
+                // mask: h2a[j] holds h2 at the same positions (reg0 = c0[0..1], reg1 = c0[2..3], ...)
+                c0[0] = bf_lo(h2a[j][0]) > 0.f ? c0[0] : 0.f;
+                c0[1] = bf_hi(h2a[j][0]) > 0.f ? c0[1] : 0.f;
+                c0[2] = bf_lo(h2a[j][1]) > 0.f ? c0[2] : 0.f;
+                c0[3] = bf_hi(h2a[j][1]) > 0.f ? c0[3] : 0.f;
+                c1[0] = bf_lo(h2a[j][2]) > 0.f ? c1[0] : 0.f;
+                c1[1] = bf_hi(h2a[j][2]) > 0.f ? c1[1] : 0.f;
+                c1[2] = bf_lo(h2a[j][3]) > 0.f ? c1[2] : 0.f;
+                c1[3] = bf_hi(h2a[j][3]) > 0.f ? c1[3] : 0.f;
+                c_to_a(c0, c1, gh2a[j]);
+            }
+            // g_h1 = g_h2 W2 (B[k][n] = W2[k][n]), masked by h1 > 0
+            uint32_t gh1a[8][4];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int kt = 0; kt < 8; ++kt) {
+                    uint32_t b0, b1;
+                    bfrag_t(L.W2, W2_LD, kt, 2 * j, g, t, b0, b1);
+                    mma16816(c0, gh2a[kt], b0, b1);
+                    bfrag_t(L.W2, W2_LD, kt, 2 * j + 1, g, t, b0, b1);
+                    mma16816(c1, gh2a[kt], b0, b1);
+                }
+                c0[0] = bf_lo(h1a[j][0]) > 0.f ? c0[0] : 0.f;
+                c0[1] = bf_hi(h1a[j][0]) > 0.f ? c0[1] : 0.f;
+                c0[2] = bf_lo(h1a[j][1]) > 0.f ? c0[2] : 0.f;
+                c0[3] = bf_hi(h1a[j][1]) > 0.f ? c0[3] : 0.f;
+                c1[0] = bf_lo(h1a[j][2]) > 0.f ? c1[0] : 0.f;
+                c1[1] = bf_hi(h1a[j][2]) > 0.f ? c1[1] : 0.f;
+                c1[2] = bf_lo(h1a[j][3]) > 0.f ? c1[2] : 0.f;
+                c1[3] = bf_hi(h1a[j][3]) > 0.f ? c1[3] : 0.f;
+                c_to_a(c0, c1, gh1a[j]);
+            }
+            // g_a = g_h1 W1 (B[k][n] = W1[k][n]), added to g_A
+            float gc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+            for (int kt = 0; kt < 8; ++kt) {
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    uint32_t b0, b1;
+                    bfrag_t(L.W1, W1_LD, kt, nt, g, t, b0, b1);
+                    mma16816(gc[nt], gh1a[kt], b0, b1);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = nt * 8 + 2 * t + (q & 1);
+                    if (i < na) tg[c_row(q, g) * YS + a_idx(f, l, i)] += gc[nt][q];
+                }
+            }
+            // transposed gradient tiles
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = (q & 1) ? g + 8 : g;
+                    const int cc = 16 * j + (q >> 1) * 8 + 2 * t;
+                    st_bf16(gh1T, cc, col0 + row, bf_lo(gh1a[j][q]));
+                    st_bf16(gh1T, cc + 1, col0 + row, bf_hi(gh1a[j][q]));
+                    st_bf16(gh2T, cc, col0 + row, bf_lo(gh2a[j][q]));
+                    st_bf16(gh2T, cc + 1, col0 + row, bf_hi(gh2a[j][q]));
+                }
+            }
+        }
+        __syncthreads();
+        // write v, g back
+        for (int k = tid; k < 64 * YS; k += blockDim.x) {
+            const int r = k / YS, d = k % YS;
+            const int64_t i = base + r;
+            if (i < n && d < f.D) {
+                vbuf[(int64_t)d * n + i] = vt[k];
+                gbuf[(int64_t)d * n + i] = gt[k];
+            }
+        }
+        // weight gradients over the 64 samples (K dimension = samples)
+        auto afrag_T = [&](const __nv_bfloat16 *T, int m0, int kt, uint32_t (&a)[4]) {
+            const __nv_bfloat16 *p = T + (m0 + g) * TPAD + kt * 16 + 2 * t;
+            a[0] = *reinterpret_cast<const uint32_t *>(p);
+            a[1] = *reinterpret_cast<const uint32_t *>(p + 8 * TPAD);
+            a[2] = *reinterpret_cast<const uint32_t *>(p + 8);
+            a[3] = *reinterpret_cast<const uint32_t *>(p + 8 * TPAD + 8);
+        };
+        // dW2[o][i] += sum_s gh2[s][o] h1[s][i]: warp owns rows 32w..32w+31
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int m0 = warp * 32 + mt * 16;
+#pragma unroll
+            for (int nh = 0; nh < 2; ++nh) {
+                float acc[8][4];
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+#pragma unroll
+                for (int kt = 0; kt < 4; ++kt) {
+                    uint32_t a[4];
+                    afrag_T(gh2T, m0, kt, a);
+#pragma unroll
+                    for (int nn = 0; nn < 8; ++nn) {
+                        uint32_t b0, b1;
+                        bfrag(h1T, TPAD, kt, nh * 8 + nn, g, t, b0, b1);
+                        mma16816(acc[nn], a, b0, b1);
+                    }
+                }
+#pragma unroll
+                for (int nn = 0; nn < 8; ++nn) {
+                    const int c = (nh * 8 + nn) * 8 + 2 * t;
+                    dW2[(m0 + g) * H + c] += acc[nn][0];
+                    dW2[(m0 + g) * H + c + 1] += acc[nn][1];
+                    dW2[(m0 + g + 8) * H + c] += acc[nn][2];
+                    dW2[(m0 + g + 8) * H + c + 1] += acc[nn][3];
+                }
+            }
+        }
+        // dW3[o][i] += sum_s go[s][o] h2[s][i]: warp owns n-tiles 4w..4w+3
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                uint32_t a[4];
+                afrag_T(goT, mt * 16, kt, a);
+#pragma unroll
+                for (int nn = 0; nn < 4; ++nn) {
+                    uint32_t b0, b1;
+                    bfrag(h2T, TPAD, kt, warp * 4 + nn, g, t, b0, b1);
+                    mma16816(dw3[mt][nn], a, b0, b1);
+                }
+            }
+        }
+        // dW1[o][i] += sum_s gh1[s][o] a[s][i]: warp owns rows 32w..32w+31
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                uint32_t a[4];
+                afrag_T(gh1T, warp * 32 + mt * 16, kt, a);
+#pragma unroll
+                for (int nn = 0; nn < 2; ++nn) {
+                    uint32_t b0, b1;
+                    bfrag(aT, TPAD, kt, nn, g, t, b0, b1);
+                    mma16816(dw1[mt][nn], a, b0, b1);
+                }
+            }
+        }
+        // bias gradients: sums over the 64 sample columns of the transposed tiles
+        for (int k = tid; k < H + H + 32; k += blockDim.x) {
+            const __nv_bfloat16 *row = k < H ? gh1T + k * TPAD : (k < 2 * H ? gh2T + (k - H) * TPAD : goT + (k - 2 * H) * TPAD);
+            float s = 0.f;
+            for (int c = 0; c < 64; ++c) s += __bfloat162float(row[c]);
+            db[k] += s;
+        }
+        __syncthreads();
+    }
+    // flush: global gradient layout of the layer = padded [W1p 128x16 | b1 | W2 128x128 | b2 | W3p 32x128 | b3p]
+    float *gW1 = grad_layer;
+    float *gb1 = gW1 + H * 16;
+    float *gW2 = gb1 + H;
+    float *gb2 = gW2 + H * H;
+    float *gW3 = gb2 + H;
+    float *gb3 = gW3 + 32 * H;
+    for (int k = tid; k < H * H; k += blockDim.x) atomicAdd(gW2 + k, dW2[k]);
+    for (int k = tid; k < H; k += blockDim.x) {
+        atomicAdd(gb1 + k, db[k]);
+        atomicAdd(gb2 + k, db[H + k]);
+    }
+    for (int k = tid; k < 32; k += blockDim.x) atomicAdd(gb3 + k, db[2 * H + k]);
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nn = 0; nn < 4; ++nn) {
+            const int r0 = mt * 16 + g, c = (warp * 4 + nn) * 8 + 2 * t;
+            atomicAdd(gW3 + r0 * H + c, dw3[mt][nn][0]);
+            atomicAdd(gW3 + r0 * H + c + 1, dw3[mt][nn][1]);
+            atomicAdd(gW3 + (r0 + 8) * H + c, dw3[mt][nn][2]);
+            atomicAdd(gW3 + (r0 + 8) * H + c + 1, dw3[mt][nn][3]);
+        }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nn = 0; nn < 2; ++nn) {
+            const int r0 = warp * 32 + mt * 16 + g, c = nn * 8 + 2 * t;
+            atomicAdd(gW1 + r0 * 16 + c, dw1[mt][nn][0]);
+            atomicAdd(gW1 + r0 * 16 + c + 1, dw1[mt][nn][1]);
+            atomicAdd(gW1 + (r0 + 8) * 16 + c, dw1[mt][nn][2]);
+            atomicAdd(gW1 + (r0 + 8) * 16 + c + 1, dw1[mt][nn][3]);
+        }
+}
+
+// ---- parameter plumbing -----------------------------------------------------------------
+constexpr int GRAD_LAYER = H * 16 + H + H * H + H + 32 * H + 32;   // padded per-layer gradient floats
+
+struct LayerIdx {
+    int a, b;              // half sizes
+    int64_t off;           // blob offset of the layer
+};
+
+__global__ void pack_weights_kernel(const float *__restrict__ blob, const LayerIdx *__restrict__ li, int K,
+                                    unsigned char *__restrict__ wpack) {
+    const int l = blockIdx.y;
+    if (l >= K) return;
+    const LayerIdx L = li[l];
+    const float *W1 = blob + L.off;
+    const float *b1 = W1 + H * L.a;
+    const float *W2 = b1 + H;
+    const float *b2 = W2 + H * H;
+    const float *W3 = b2 + H;
+    const float *b3 = W3 + 2 * L.b * H;
+    unsigned char *out = wpack + (size_t)l * LAYER_BYTES;
+    __nv_bfloat16 *pW1 = reinterpret_cast<__nv_bfloat16 *>(out + OFF_W1);
+    __nv_bfloat16 *pW2 = reinterpret_cast<__nv_bfloat16 *>(out + OFF_W2);
+    __nv_bfloat16 *pW3 = reinterpret_cast<__nv_bfloat16 *>(out + OFF_W3);
+    float *pb1 = reinterpret_cast<float *>(out + OFF_B1);
+    float *pb2 = reinterpret_cast<float *>(out + OFF_B2);
+    float *pb3 = reinterpret_cast<float *>(out + OFF_B3);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H * W2_LD; k += gridDim.x * blockDim.x) {
+        const int r = k / W2_LD, c = k % W2_LD;
+        pW2[k] = __float2bfloat16_rn(c < H ? W2[r * H + c] : 0.f);
+        if (k < H * W1_LD) {
+            const int r1 = k / W1_LD, c1 = k % W1_LD;
+            pW1[k] = __float2bfloat16_rn(c1 < L.a ? W1[r1 * L.a + c1] : 0.f);
+        }
+        if (k < 32 * W3_LD) {
+            const int r3 = k / W3_LD, c3 = k % W3_LD;
+            float v = 0.f;
+            if (c3 < H) {
+                if (r3 < 16 && r3 < L.b) v = W3[r3 * H + c3];                       // s rows
+                else if (r3 >= 16 && r3 - 16 < L.b) v = W3[(L.b + r3 - 16) * H + c3];  // t rows
+            }
+            pW3[k] = __float2bfloat16_rn(v);
+        }
+        if (k < H) {
+            pb1[k] = b1[k];
+            pb2[k] = b2[k];
+        }
+        if (k < 32) pb3[k] = (k < 16) ? (k < L.b ? b3[k] : 0.f) : (k - 16 < L.b ? b3[L.b + k - 16] : 0.f);
+    }
+}
+
+// padded per-layer gradients -> blob layout (overwrites grad_blob)
+__global__ void unpack_grad_kernel(const float *__restrict__ gpad, const LayerIdx *__restrict__ li, int K,
+                                   float *__restrict__ grad_blob) {
+    const int l = blockIdx.y;
+    if (l >= K) return;
+    const LayerIdx L = li[l];
+    const float *gW1 = gpad + (size_t)l * GRAD_LAYER;
+    const float *gb1 = gW1 + H * 16;
+    const float *gW2 = gb1 + H;
+    const float *gb2 = gW2 + H * H;
+    const float *gW3 = gb2 + H;
+    const float *gb3 = gW3 + 32 * H;
+    float *W1 = grad_blob + L.off;
+    float *b1 = W1 + H * L.a;
+    float *W2 = b1 + H;
+    float *b2 = W2 + H * H;
+    float *W3 = b2 + H;
+    float *b3 = W3 + 2 * L.b * H;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H * H; k += gridDim.x * blockDim.x) {
+        W2[k] = gW2[k];
+        if (k < H * L.a) W1[k] = gW1[(k / L.a) * 16 + k % L.a];
+        if (k < 2 * L.b * H) {
+            const int r = k / H, c = k % H;
+            W3[k] = r < L.b ? gW3[r * H + c] : gW3[(16 + r - L.b) * H + c];
+        }
+        if (k < H) {
+            b1[k] = gb1[k];
+            b2[k] = gb2[k];
+        }
+        if (k < 2 * L.b) b3[k] = k < L.b ? gb3[k] : gb3[16 + k - L.b];
+    }
+}
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1t, float b2t) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float gk = gr[k];
+    const float mk = 0.9f * m[k] + 0.1f * gk;
+    const float vk = 0.999f * v[k] + 0.001f * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    const float mh = mk / (1.0f - b1t);
+    const float vh = vk / (1.0f - b2t);
+    p[k] -= lr * mh / (sqrtf(vh) + 1e-8f);
+}
+
+__global__ void sum_weights_kernel(const float *__restrict__ w, int64_t n, double *__restrict__ out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        s += (double)w[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, sh[0]);
+}
+
+}  // namespace
+
+struct fd_flow {
+    int device;
+    int D, K, Hd;
+    int64_t n_params;
+    std::vector<LayerIdx> idx;
+    LayerIdx *d_idx = nullptr;
+    float *d_blob = nullptr, *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr, *d_gpad = nullptr;
+    unsigned char *d_wpack = nullptr;
+    double *d_wsum = nullptr;
+    float *d_loss = nullptr;
+    float *d_vbuf = nullptr, *d_gbuf = nullptr;
+    int64_t scratch_n = 0;
+    int64_t step = 0;
+};
+
+namespace {
+FlowDims dims_of(const fd_flow *f) { return FlowDims{f->D, f->K, (f->D + 1) / 2}; }
+
+fd_status repack(fd_flow *f, cudaStream_t s) {
+    pack_weights_kernel<<<dim3(32, f->K), 256, 0, s>>>(f->d_blob, f->d_idx, f->K, f->d_wpack);
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
+}
+
+int pass_smem() { return LAYER_BYTES + BLOCK * YS * 4 + BLOCK * 4 + 16; }
+
+fd_status ensure_scratch(fd_flow *f, int64_t n) {
+    if (f->scratch_n >= n) return FD_OK;
+    cudaFree(f->d_vbuf);
+    cudaFree(f->d_gbuf);
+    f->d_vbuf = f->d_gbuf = nullptr;
+    f->scratch_n = 0;
+    FD_CHECK_CUDA(cudaMalloc(&f->d_vbuf, (size_t)f->D * n * 4));
+    FD_CHECK_CUDA(cudaMalloc(&f->d_gbuf, (size_t)f->D * n * 4));
+    f->scratch_n = n;
+    return FD_OK;
+}
+
+int grid_for(int64_t units, int per_sm_ctas) {
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t g = std::min<int64_t>(units, (int64_t)n_sm * per_sm_ctas);
+    return (int)std::max<int64_t>(g, 1);
+}
+
+// loss and gradient (padded per-layer, then blob layout in d_grad) of the batch
+fd_status grad_impl(fd_flow *f, const float *x, const float *w, int64_t n, cudaStream_t s) {
+    fd_status st = ensure_scratch(f, n);
+    if (st != FD_OK) return st;
+    const FlowDims fd_ = dims_of(f);
+    int *status = fd::device_status_word();
+    FD_CHECK_CUDA(cudaMemsetAsync(f->d_wsum, 0, sizeof(double), s));
+    FD_CHECK_CUDA(cudaMemsetAsync(f->d_loss, 0, sizeof(float), s));
+    FD_CHECK_CUDA(cudaMemsetAsync(f->d_gpad, 0, (size_t)f->K * GRAD_LAYER * 4, s));
+    sum_weights_kernel<<<256, 256, 0, s>>>(w, n, f->d_wsum);
+    FD_CHECK_CUDA(cudaGetLastError());
+    const int sm1 = pass_smem();
+    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_inverse_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
+    flow_inverse_train_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm1, s>>>(
+        f->d_wpack, fd_, n, x, w, f->d_wsum, f->d_vbuf, f->d_gbuf, f->d_loss, status);
+    FD_CHECK_CUDA(cudaGetLastError());
+    const int sm2 = BwdSmem::TOTAL;
+    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_backward_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    for (int l = 0; l < f->K; ++l) {
+        flow_backward_layer_kernel<<<grid_for((n + 63) / 64, 1), 128, sm2, s>>>(
+            f->d_wpack, fd_, l, n, w, f->d_wsum, f->d_vbuf, f->d_gbuf, f->d_gpad + (size_t)l * GRAD_LAYER, status);
+        FD_CHECK_CUDA(cudaGetLastError());
+    }
+    unpack_grad_kernel<<<dim3(16, f->K), 256, 0, s>>>(f->d_gpad, f->d_idx, f->K, f->d_grad);
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
+}
+}  // namespace
+
+extern "C" fd_status fd_flow_create(int32_t dim, int32_t n_layers, int32_t hidden, uint64_t seed, fd_flow **out) {
+    FD_REQUIRE(out, "out is required");
+    *out = nullptr;
+    FD_REQUIRE(dim >= 2 && dim <= 32, "dim must be in [2, 32]");
+    FD_REQUIRE(n_layers >= 1 && n_layers <= 64, "n_layers must be in [1, 64]");
+    FD_REQUIRE(hidden == H, "hidden must be 128 (tensor-core tiling of this build)");
+    fd_flow *f = new fd_flow();
+    f->D = dim;
+    f->K = n_layers;
+    f->Hd = hidden;
+    FD_CHECK_CUDA(cudaGetDevice(&f->device));
+    const int h = (dim + 1) / 2;
+    int64_t off = 0;
+    for (int l = 0; l < n_layers; ++l) {
+        LayerIdx L;
+        L.a = (l % 2 == 0) ? h : dim - h;
+        L.b = dim - L.a;
+        L.off = off;
+        off += (int64_t)H * L.a + H + (int64_t)H * H + H + 2LL * L.b * H + 2 * L.b;
+        f->idx.push_back(L);
+        if (L.a > 16 || L.b > 16) {
+            delete f;
+            return fd::set_error(FD_ENOTSUP, "coupling halves larger than 16 coordinates");
+        }
+    }
+    f->n_params = off;
+    // initial weights: uniform(+-1/sqrt(fan_in)) for W1, W2 and zero output layer (identity flow)
+    std::vector<float> blob(off, 0.f);
+    uint64_t st = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto rnd = [&]() {
+        st ^= st << 13;
+        st ^= st >> 7;
+        st ^= st << 17;
+        return (double)(st >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < n_layers; ++l) {
+        const LayerIdx &L = f->idx[l];
+        float *W1 = blob.data() + L.off;
+        float *W2 = W1 + H * L.a + H;
+        for (int k = 0; k < H * L.a; ++k) W1[k] = (float)((2 * rnd() - 1) / std::sqrt((double)L.a));
+        for (int k = 0; k < H * H; ++k) W2[k] = (float)((2 * rnd() - 1) / std::sqrt((double)H));
+    }
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+    };
+    al((void **)&f->d_blob, off * 4);
+    al((void **)&f->d_m, off * 4);
+    al((void **)&f->d_v, off * 4);
+    al((void **)&f->d_grad, off * 4);
+    al((void **)&f->d_gpad, (size_t)n_layers * GRAD_LAYER * 4);
+    al((void **)&f->d_wpack, (size_t)n_layers * LAYER_BYTES);
+    al((void **)&f->d_idx, n_layers * sizeof(LayerIdx));
+    al((void **)&f->d_wsum, sizeof(double));
+    al((void **)&f->d_loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_idx, f->idx.data(), n_layers * sizeof(LayerIdx), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_blob, blob.data(), off * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        fd_flow_free(f);
+        return fd::cuda_error(e, "fd_flow_create");
+    }
+    fd_status s2 = repack(f, 0);
+    if (s2 == FD_OK) {
+        cudaError_t e2 = cudaDeviceSynchronize();
+        if (e2 != cudaSuccess) s2 = fd::cuda_error(e2, "fd_flow_create");
+    }
+    if (s2 != FD_OK) {
+        fd_flow_free(f);
+        return s2;
+    }
+    *out = f;
+    return FD_OK;
+}
+
+extern "C" void fd_flow_free(fd_flow *f) {
+    if (!f) return;
+    cudaFree(f->d_blob);
+    cudaFree(f->d_m);
+    cudaFree(f->d_v);
+    cudaFree(f->d_grad);
+    cudaFree(f->d_gpad);
+    cudaFree(f->d_wpack);
+    cudaFree(f->d_idx);
+    cudaFree(f->d_wsum);
+    cudaFree(f->d_loss);
+    cudaFree(f->d_vbuf);
+    cudaFree(f->d_gbuf);
+    delete f;
+}
+
+extern "C" int64_t fd_flow_param_count(const fd_flow *f) { return f ? f->n_params : 0; }
+
+extern "C" fd_status fd_flow_set_params(fd_flow *f, const float *blob, int64_t n) {
+    FD_REQUIRE(f && blob, "flow and blob are required");
+    FD_REQUIRE(n == f->n_params, "blob size differs from fd_flow_param_count");
+    for (int64_t k = 0; k < n; ++k) FD_REQUIRE(std::isfinite(blob[k]), "non-finite parameter");
+    FD_CHECK_CUDA(cudaDeviceSynchronize());
+    FD_CHECK_CUDA(cudaMemcpy(f->d_blob, blob, n * 4, cudaMemcpyHostToDevice));
+    FD_CHECK_CUDA(cudaMemset(f->d_m, 0, n * 4));
+    FD_CHECK_CUDA(cudaMemset(f->d_v, 0, n * 4));
+    f->step = 0;
+    fd_status st = repack(f, 0);
+    if (st != FD_OK) return st;
+    FD_CHECK_CUDA(cudaDeviceSynchronize());
+    return FD_OK;
+}
+
+extern "C" fd_status fd_flow_get_params(const fd_flow *f, float *blob, int64_t n) {
+    FD_REQUIRE(f && blob, "flow and blob are required");
+    FD_REQUIRE(n == f->n_params, "blob size differs from fd_flow_param_count");
+    FD_CHECK_CUDA(cudaDeviceSynchronize());
+    FD_CHECK_CUDA(cudaMemcpy(blob, f->d_blob, n * 4, cudaMemcpyDeviceToHost));
+    return FD_OK;
+}
+
+extern "C" fd_status fd_flow_sample(const fd_flow *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n,
+                                    float *x, float *w, void *stream) {
+    FD_REQUIRE(f && x && w, "flow, x and w are required");
+    FD_REQUIRE(n > 0 && n <= (int64_t(1) << 34), "n out of range");
+    FD_REQUIRE(inst >= 0 && inst < (1 << 24), "instance index out of range");
+    const int sm = pass_smem();
+    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, (cudaStream_t)stream>>>(
+        f->d_wpack, dims_of(f), 0, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)inst, nullptr, x,
+        w, fd::device_status_word());
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
+}
+
+extern "C" fd_status fd_flow_log_density(const fd_flow *f, const float *x, int64_t n, float *logq, void *stream) {
+    FD_REQUIRE(f && x && logq, "flow, x and logq are required");
+    FD_REQUIRE(n > 0 && n <= (int64_t(1) << 34), "n out of range");
+    const int sm = pass_smem();
+    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, (cudaStream_t)stream>>>(
+        f->d_wpack, dims_of(f), 1, n, 0, 0, 0, 0, x, nullptr, logq, fd::device_status_word());
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
+}
+
+extern "C" fd_status fd_flow_grad(fd_flow *f, const float *x, const float *w, int64_t n, float *loss, float *grad,
+                                  void *stream) {
+    FD_REQUIRE(f && x && w && loss && grad, "flow, x, w, loss and grad are required");
+    FD_REQUIRE(n > 0 && n <= (int64_t(1) << 30), "n out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    fd_status st = grad_impl(f, x, w, n, s);
+    if (st != FD_OK) return st;
+    FD_CHECK_CUDA(cudaMemcpyAsync(loss, f->d_loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    FD_CHECK_CUDA(cudaMemcpyAsync(grad, f->d_grad, f->n_params * 4, cudaMemcpyDeviceToDevice, s));
+    return FD_OK;
+}
+
+extern "C" fd_status fd_flow_train(fd_flow *f, const float *x, const float *w, int64_t n, int32_t steps, float lr,
+                                   float *loss_out, void *stream) {
+    FD_REQUIRE(f && x && w, "flow, x and w are required");
+    FD_REQUIRE(n > 0 && n <= (int64_t(1) << 30), "n out of range");
+    FD_REQUIRE(steps >= 1 && lr > 0.f && std::isfinite(lr), "steps >= 1 and a positive learning rate are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    float *d_losses = nullptr;
+    if (loss_out) FD_CHECK_CUDA(cudaMalloc(&d_losses, steps * sizeof(float)));
+    for (int k = 0; k < steps; ++k) {
+        fd_status st = grad_impl(f, x, w, n, s);
+        if (st != FD_OK) {
+            cudaFree(d_losses);
+            return st;
+        }
+        if (d_losses) FD_CHECK_CUDA(cudaMemcpyAsync(d_losses + k, f->d_loss, 4, cudaMemcpyDeviceToDevice, s));
+        f->step += 1;
+        const float b1t = (float)std::pow(0.9, (double)f->step), b2t = (float)std::pow(0.999, (double)f->step);
+        adam_kernel<<<(unsigned)((f->n_params + 255) / 256), 256, 0, s>>>(f->d_blob, f->d_grad, f->d_m, f->d_v,
+                                                                          f->n_params, lr, b1t, b2t);
+        FD_CHECK_CUDA(cudaGetLastError());
+        st = repack(f, s);
+        if (st != FD_OK) {
+            cudaFree(d_losses);
+            return st;
+        }
+    }
+    if (loss_out) {
+        FD_CHECK_CUDA(cudaMemcpyAsync(loss_out, d_losses, steps * sizeof(float), cudaMemcpyDeviceToHost, s));
+        FD_CHECK_CUDA(cudaStreamSynchronize(s));
+        cudaFree(d_losses);
+    }
+    return FD_OK;
 }

@@ -1,0 +1,114 @@
+"""GPU parity of the affine coupling flow kernels (BF16 tensor cores, FP32
+accumulation) against the FP64 oracle under the same BF16 contract."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import flow as oflow
+from oracle import philox as ophilox
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+D, K, H = 19, 8, 128
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2403_18840_gb300 import api as A
+    return A
+
+
+@pytest.fixture(autouse=True)
+def bf16_oracle():
+    oflow.set_precision("bf16")
+    yield
+    oflow.set_precision("f64")
+
+
+def _flow(api, seed=1, scale=0.06):
+    F = api.Flow(D, K, H, seed=0)
+    blob = workloads.normal_blob(seed, F.n_params, scale)
+    assert blob.size == oflow.n_params(D, K, H)
+    F.set_params(blob)
+    return F, blob
+
+
+def test_param_roundtrip_and_count(api):
+    F, blob = _flow(api)
+    assert np.array_equal(F.params().astype(np.float64), blob)
+
+
+def test_sample_parity(api):
+    F, blob = _flow(api)
+    n = 3000
+    x, w = F.sample(21, 2, 3, n)
+    torch.cuda.synchronize()
+    z = ophilox.uniforms(21, 2, 3, np.arange(n), D)
+    xr, lq = oflow.forward(blob, z, D, K, H)
+    xg = x.cpu().numpy().astype(np.float64)
+    lw = np.log(w.cpu().numpy().astype(np.float64))
+    dx = np.abs(xg - xr)
+    dl = np.abs(lw + lq)
+    print("sample: max |dx| %.3e  max |dlogq| %.3e  p99 %.3e" % (dx.max(), dl.max(), np.quantile(dl, 0.99)))
+    assert dx.max() < 2e-3 and np.quantile(dx, 0.99) < 2e-4
+    assert dl.max() < 2e-2 and np.quantile(dl, 0.99) < 2e-3
+
+
+def test_log_density_parity_and_consistency(api):
+    F, blob = _flow(api)
+    n = 2500
+    x, w = F.sample(5, 0, 0, n)
+    lq = F.log_density(x)
+    torch.cuda.synchronize()
+    # self-consistency: density of the flow's own samples is 1/w
+    a = lq.cpu().numpy().astype(np.float64)
+    b = -np.log(w.cpu().numpy().astype(np.float64))
+    assert np.quantile(np.abs(a - b), 0.99) < 1e-3
+    # parity on given points
+    pts = workloads.uniform_points(6, D, n, 0.01, 0.99)
+    lq2 = F.log_density(torch.tensor(pts, dtype=torch.float32, device="cuda").contiguous())
+    torch.cuda.synchronize()
+    _, ref = oflow.inverse(blob, pts, D, K, H)
+    d = np.abs(lq2.cpu().numpy().astype(np.float64) - ref)
+    print("log density: max %.3e p99 %.3e" % (d.max(), np.quantile(d, 0.99)))
+    assert d.max() < 2e-2 and np.quantile(d, 0.99) < 2e-3
+
+
+def test_gradient_parity(api):
+    F, blob = _flow(api)
+    n = 4096
+    pts = workloads.uniform_points(7, D, n, 0.02, 0.98)
+    wts = workloads.positive_weights(8, n)
+    loss, g = F.grad(torch.tensor(pts, dtype=torch.float32, device="cuda").contiguous(),
+                     torch.tensor(wts, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    Lr, gr = oflow.loss_and_grad(blob, pts, wts, D, K, H)
+    gg = g.cpu().numpy().astype(np.float64)
+    cos = float(gg @ gr / (np.linalg.norm(gg) * np.linalg.norm(gr)))
+    rel = float(np.linalg.norm(gg - gr) / np.linalg.norm(gr))
+    print("grad: loss %.6f vs %.6f  cos %.6f  rel %.3e" % (float(loss.item()), Lr, cos, rel))
+    assert abs(float(loss.item()) - Lr) < 1e-3 * max(1.0, abs(Lr))
+    assert cos >= 0.999 and rel <= 1e-2
+
+
+def test_training_reduces_loss_and_first_adam_step(api):
+    F, blob = _flow(api, seed=3, scale=0.04)
+    n = 8192
+    pts = workloads.uniform_points(9, D, n, 0.02, 0.98)
+    # a peaked target: weights concentrated near a corner
+    wts = np.exp(-20 * np.sum((pts[:4] - 0.3) ** 2, axis=0))
+    x = torch.tensor(pts, dtype=torch.float32, device="cuda").contiguous()
+    w = torch.tensor(wts, dtype=torch.float32, device="cuda")
+    _, g0 = F.grad(x, w)
+    p0 = F.params().astype(np.float64)
+    losses = F.train(x, w, 1, 1e-3)
+    p1 = F.params().astype(np.float64)
+    g0 = g0.cpu().numpy().astype(np.float64)
+    big = np.abs(g0) > 1e-5
+    # first Adam step from zero moments: every parameter moves by lr * sign(grad)
+    assert np.allclose((p0 - p1)[big], 1e-3 * np.sign(g0[big]), rtol=2e-3, atol=1e-7)
+    more = F.train(x, w, 60, 3e-3)
+    print("train losses", losses[0], more[0], more[-1])
+    assert more[-1] < more[0] - 0.05
