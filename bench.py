@@ -42,6 +42,8 @@ def _parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--samples", type=int, default=WL["n_samples"])
+    ap.add_argument("--flow-steps", type=int, default=workloads.FLOW_ORDER5["train_steps"])
+    ap.add_argument("--flow-batch", type=int, default=workloads.FLOW_ORDER5["batch"])
     return ap.parse_args()
 
 
@@ -238,6 +240,23 @@ def run_ours(args, rank, world, dist):
     h2d = int(e_host.nbytes)
     d2h = int(e_host.nbytes + stats_host.numel() * 8)
 
+    # learned proposal vs VEGAS at equal sample counts (training outside the timed region)
+    from paper_2403_18840_gb300 import driver
+    F = api.Flow(G.dim, workloads.FLOW_ORDER5["n_layers"], workloads.FLOW_ORDER5["hidden"],
+                 seed=workloads.FLOW_ORDER5["seed"])
+    t0 = time.perf_counter()
+    losses = driver.train_flow(G, params[0], F, V, steps=max(1, args.flow_steps), batch=args.flow_batch,
+                               lr=1e-3, seed=workloads.FLOW_ORDER5["seed"], vegas_steps=100, evals_per_batch=4)
+    torch.cuda.synchronize()
+    flow_train_s = time.perf_counter() - t0
+    cmp = driver.compare(G, params[0], V, F, workloads.FLOW_ORDER5["n_compare"], seed=seed + 7)
+    eff = {"root": list(roots[0]), "vegas": cmp["vegas"], "flow": cmp["flow"],
+           "flow_over_vegas": cmp["flow_over_vegas"], "means_agree_sigma": cmp["means_agree_sigma"],
+           "compare_samples": workloads.FLOW_ORDER5["n_compare"], "flow_train_steps": max(1, args.flow_steps),
+           "flow_batch": args.flow_batch, "flow_train_s": flow_train_s,
+           "flow_loss_first_last": [losses[0], losses[-1]],
+           "flow_train_note": "each integrand batch reused for 4 Adam steps; first 100 steps on VEGAS samples"}
+
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     mhz_max = _peaks().get("sm_max_mhz", 2070.0)
@@ -263,6 +282,7 @@ def run_ours(args, rank, world, dist):
                      "peak_basis": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (n_sm, mhz_max),
                      "kernel_ms": 1e3 * t_kern},
         "e2e": {"value": n / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "eff_samples_per_s": eff,
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "wall_s": t_wall,

@@ -57,8 +57,12 @@ typedef struct {
 } fd_params;
 
 /* Sample-tile size of the reduction: partial sums are kept per instance and
- * per tile of this many consecutive samples. */
+ * per tile of consecutive samples.  The tile holds FD_TILE_SAMPLES samples
+ * when n_per_inst >= 512 * FD_TILE_SAMPLES, otherwise the smallest power of
+ * two >= n_per_inst / 512 (at least 1024), so small launches still spread
+ * over the GPU; fd_tile_samples(n) returns it. */
 #define FD_TILE_SAMPLES 16384
+int64_t fd_tile_samples(int64_t n_per_inst);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *fd_last_error(void);
@@ -125,7 +129,7 @@ fd_status fd_map_samples(const fd_vegas *map, uint64_t seed, uint64_t iter, int3
  * in FP32 (J: loop-momentum and time Jacobians of the roots' own variables).
  * Outputs
  *  partials (device, required): FP64 [n_inst][n_tiles][R_max][2][2] with
- *    n_tiles = ceil(n_per_inst / FD_TILE_SAMPLES), R_max the largest root
+ *    n_tiles = ceil(n_per_inst / fd_tile_samples(n_per_inst)), R_max the largest root
  *    count; entry (.., r, c, 0) = sum of f (c = 0 real, 1 imaginary) over the
  *    tile, (.., r, c, 1) = sum of f^2.  Tiles are summed in a fixed order
  *    inside the tile, so results are bitwise reproducible.

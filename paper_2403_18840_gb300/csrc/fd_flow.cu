@@ -219,6 +219,11 @@ __device__ __forceinline__ void coupling(float *ys, float *ld, const FlowDims &f
     }
 }
 
+// Points on the faces of the cube (FP32 rounds narrow edge bins and
+// saturated sigmoids to exactly 0 or 1) are moved inside by one ulp before
+// the logit of the inverse direction.
+__device__ __forceinline__ float clamp_unit(float x) { return fminf(fmaxf(x, 1.1920929e-07f), 0.99999988f); }
+
 __device__ __forceinline__ float log_sig_deriv(float y) {
     // log(sigmoid(y) (1 - sigmoid(y))) = -|y| - 2 log(1 + exp(-|y|))
     const float a = fabsf(y);
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(128) flow_pass_kernel(const unsigned char *__r
                 }
             } else {
                 for (int d = 0; d < f.D; ++d) {
-                    const float x = valid ? xin[(int64_t)d * n + i] : 0.5f;
+                    const float x = clamp_unit(valid ? xin[(int64_t)d * n + i] : 0.5f);
                     const float y = __logf(x) - log1pf(-x);
                     ys[r * YS + d] = y;
                     acc -= log_sig_deriv(y);                // log q gains -log dx/dy
@@ -361,7 +366,7 @@ __global__ void __launch_bounds__(128) flow_inverse_train_kernel(const unsigned 
             const int64_t i = base + r;
             float acc = 0.f;
             for (int d = 0; d < f.D; ++d) {
-                const float x = i < n ? xin[(int64_t)d * n + i] : 0.5f;
+                const float x = clamp_unit(i < n ? xin[(int64_t)d * n + i] : 0.5f);
                 const float y = __logf(x) - log1pf(-x);
                 ys[r * YS + d] = y;
                 acc -= log_sig_deriv(y);

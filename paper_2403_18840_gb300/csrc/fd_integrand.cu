@@ -10,7 +10,7 @@
 // exp(i w0 tau_out) with w0 = pi / beta.
 //
 // Execution model (sm_103a):
-//  * persistent CTAs walk work items = (instance, tile of FD_TILE_SAMPLES
+//  * persistent CTAs walk work items = (instance, tile of fd_tile_samples(n)
 //    consecutive samples); each thread owns one sample per pass;
 //  * per-sample state lives in shared memory as [slot][thread] FP32 words
 //    (a warp touches 32 consecutive words per slot: conflict-free);
@@ -56,7 +56,7 @@ struct InstDesc {
 
 struct EvalArgs {
     int32_t n_inst, tiles_per_inst, r_max, slots_total, dim_max;
-    int64_t n_per_inst;
+    int64_t n_per_inst, tile;
     uint32_t seed_lo, seed_hi, iter;
     double *partials;
     float *per_sample_f;
@@ -505,8 +505,8 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
         const InstDesc &D = A.inst[inst];
         const int n_chunks = (D.n_instr + CHUNK_INSTR - 1) / CHUNK_INSTR;
         for (int k = tid; k < (T / 32) * racc; k += T) acc[k] = 0.0;
-        const int64_t first = (int64_t)tile * FD_TILE_SAMPLES;
-        const int64_t last = min(first + (int64_t)FD_TILE_SAMPLES, A.n_per_inst);
+        const int64_t first = (int64_t)tile * A.tile;
+        const int64_t last = min(first + A.tile, A.n_per_inst);
         const int passes = (int)((last - first + T * P - 1) / (T * P));
         const int64_t total_chunks = (int64_t)passes * n_chunks;
         const bool resident = n_chunks <= 2;
@@ -634,9 +634,17 @@ extern "C" fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t s
     return FD_OK;
 }
 
+extern "C" int64_t fd_tile_samples(int64_t n_per_inst) {
+    if (n_per_inst >= 512ll * FD_TILE_SAMPLES) return FD_TILE_SAMPLES;
+    int64_t t = 1024;
+    while (t * 512 < n_per_inst) t *= 2;
+    return t;
+}
+
 extern "C" int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_per_inst) {
     if (n_inst <= 0 || r_max <= 0 || n_per_inst <= 0) return 0;
-    const int64_t tiles = (n_per_inst + FD_TILE_SAMPLES - 1) / FD_TILE_SAMPLES;
+    const int64_t tl = fd_tile_samples(n_per_inst);
+    const int64_t tiles = (n_per_inst + tl - 1) / tl;
     return (int64_t)n_inst * tiles * r_max * 4;
 }
 
@@ -658,7 +666,8 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
     static EvalArgs args;   // large (kernel parameter space); built on the host per call
     args.n_inst = n_inst;
     args.n_per_inst = n_per_inst;
-    args.tiles_per_inst = (int32_t)((n_per_inst + FD_TILE_SAMPLES - 1) / FD_TILE_SAMPLES);
+    args.tile = fd_tile_samples(n_per_inst);
+    args.tiles_per_inst = (int32_t)((n_per_inst + args.tile - 1) / args.tile);
     args.seed_lo = (uint32_t)seed;
     args.seed_hi = (uint32_t)(seed >> 32);
     args.iter = (uint32_t)iter;
@@ -790,7 +799,8 @@ extern "C" fd_status fd_accumulate(const double *partials, int32_t n_inst, int32
                                    int64_t n_per_inst, double *out, void *stream) {
     FD_REQUIRE(partials && out, "partials and out are required");
     FD_REQUIRE(n_inst > 0 && r_max > 0 && n_per_inst > 0, "sizes must be positive");
-    const int tiles = (int)((n_per_inst + FD_TILE_SAMPLES - 1) / FD_TILE_SAMPLES);
+    const int64_t tl = fd_tile_samples(n_per_inst);
+    const int tiles = (int)((n_per_inst + tl - 1) / tl);
     const int total = n_inst * r_max * 2;
     accumulate_kernel<<<(total + 127) / 128, 128, 0, (cudaStream_t)stream>>>(partials, n_inst, r_max, tiles,
                                                                           n_per_inst, out);

@@ -1,0 +1,120 @@
+"""Monte Carlo drivers: VEGAS adaptation, flow training and sampler comparison.
+
+The integral is I_f = int dx f(x) over the unit hypercube (Sec. IV).  VEGAS
+adapts its separable map from the histogram the integrand kernel accumulates;
+the learned proposal (Appendix A) is trained by forward KL on samples that the
+method itself generates: points drawn from the current sampler q_s carry the
+weight |f(x)| / q_s(x), which the integrand kernel returns directly when it is
+given the sampler's 1/q as point weights.  The comparison is at equal error
+bars: efficiency 1 / (per-sample variance x time per sample).
+"""
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import api
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def adapt_vegas(G, params, vegas, n, iters, seed, alpha=0.5, first_iter=0):
+    """`iters` VEGAS iterations of n samples; returns the per-iteration stats [iters][R][2][2]."""
+    plan = api.EvalPlan([G], [params], [0], n, maps=[vegas])
+    out = []
+    for it in range(iters):
+        vegas.clear()
+        st = plan.run(seed, first_iter + it)
+        vegas.update(alpha)
+        out.append(st[0].clone())
+    torch.cuda.synchronize()
+    return torch.stack(out).cpu().numpy()
+
+
+def training_weights(per_sample, value_roots):
+    """Target |f| / q_s per sample: sum over value roots of |Re| + |Im| of the weighted integrand."""
+    ps = per_sample[0, value_roots]            # [Rv][2][n]
+    return ps.abs().sum(dim=(0, 1)).contiguous()
+
+
+def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, evals_per_batch=1, log=None):
+    """Forward-KL training of `flow` on |f|; the first `vegas_steps` batches come from VEGAS.
+
+    Every batch is drawn from the current sampler, evaluated by the integrand
+    kernel (points mode, weights 1/q), and used for `evals_per_batch` Adam steps.
+    Returns the list of losses.
+    """
+    value_roots = [r for r, (n, m, l, dk) in enumerate(G.roots) if dk == 0]
+    plan = api.EvalPlan([G], [params], [0], batch, per_sample=True)
+    losses = []
+    k = 0
+    while k < steps:
+        if k < vegas_steps:
+            x, w = api.map_samples(vegas, seed, 1000 + k, 1, batch, G.dim)
+        else:
+            x, w = flow.sample(seed, 1000 + k, 2, batch)
+        plan.run(seed, 1000 + k, points=x, point_w=w)
+        tw = training_weights(plan.per_sample, value_roots)
+        tw = torch.nan_to_num(tw, nan=0.0, posinf=0.0)
+        m = min(evals_per_batch, steps - k)
+        step_losses = flow.train(x, tw, m, lr).tolist()
+        losses.extend(step_losses)
+        k += m
+        if not all(math.isfinite(v) for v in step_losses):
+            raise FloatingPointError("flow training diverged at step %d" % k)
+        if log and k % 100 < m:
+            log(k, losses[-1])
+    return losses
+
+
+def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3):
+    """Per-sample variance of every root and seconds per sample for one sampler.
+
+    VEGAS: the map is applied inside the integrand kernel.  Flow: the sampling
+    kernel writes points and 1/q, the integrand kernel reads them.
+    Returns (stats [R][2][2] of the last rep, seconds per sample).
+    """
+    if flow is None:
+        plan = api.EvalPlan([G], [params], [0], n, maps=[vegas] if vegas is not None else None)
+        plan.run(seed, it)
+        torch.cuda.synchronize()
+        s, e = _events()
+        s.record()
+        for r in range(reps):
+            st = plan.run(seed, it + 1 + r)
+        e.record()
+        torch.cuda.synchronize()
+        return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
+    plan = api.EvalPlan([G], [params], [0], n)
+    x, w = flow.sample(seed, it, 3, n)
+    plan.run(seed, it, points=x, point_w=w)
+    torch.cuda.synchronize()
+    s, e = _events()
+    s.record()
+    for r in range(reps):
+        x, w = flow.sample(seed, it + 1 + r, 3, n)
+        st = plan.run(seed, it + 1 + r, points=x, point_w=w)
+    e.record()
+    torch.cuda.synchronize()
+    return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
+
+
+def compare(G, params, vegas, flow, n, seed, root=0):
+    """Variance-adjusted efficiency of flow vs VEGAS for the real part of `root`."""
+    sv, tv = measure_sampler(G, params, n, seed, 50000, vegas=vegas)
+    sf, tf = measure_sampler(G, params, n, seed, 60000, flow=flow)
+    var_v = sv[root, 0, 1] * n        # per-sample variance
+    var_f = sf[root, 0, 1] * n
+    out = {
+        "vegas": {"mean": float(sv[root, 0, 0]), "err": float(math.sqrt(sv[root, 0, 1])), "var_per_sample": float(var_v),
+                  "samples_per_s": 1.0 / tv, "eff_samples_per_s": 1.0 / tv},
+        "flow": {"mean": float(sf[root, 0, 0]), "err": float(math.sqrt(sf[root, 0, 1])), "var_per_sample": float(var_f),
+                 "samples_per_s": 1.0 / tf, "eff_samples_per_s": (1.0 / tf) * var_v / var_f},
+    }
+    out["flow_over_vegas"] = out["flow"]["eff_samples_per_s"] / out["vegas"]["eff_samples_per_s"]
+    out["means_agree_sigma"] = abs(out["flow"]["mean"] - out["vegas"]["mean"]) / math.sqrt(
+        sv[root, 0, 1] + sf[root, 0, 1])
+    return out

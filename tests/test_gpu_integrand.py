@@ -129,7 +129,7 @@ def test_per_sample_parity_order5(api):
 
 
 def test_partials_equal_sum_of_per_sample(api):
-    order, n = 3, 3 * 16384 + 77            # several tiles and a ragged tail
+    order, n = 3, 3 * 16384 + 77            # several tiles (fd_tile_samples) and a ragged tail
     G, f, stats = _per_sample(api, order, True, n, 41)
     for r in range(len(G.roots)):
         for c in range(2):
