@@ -107,6 +107,8 @@ fd_status fd_vegas_clear_hist(fd_vegas *m, void *stream);
  * redistribution of the edges) in FP64 on the device, then zero the
  * histogram. */
 fd_status fd_vegas_update(fd_vegas *m, double alpha, void *stream);
+/* The same update for n_maps (<= 256) maps of equal bin count in one launch. */
+fd_status fd_vegas_update_batch(fd_vegas *const *maps, int32_t n_maps, double alpha, void *stream);
 
 /* ---- sample generation ---------------------------------------------------
  * Philox4x32-10 stream of sample i of instance `inst` at iteration `iter`:
@@ -144,11 +146,24 @@ fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_graphs,
                             int64_t n_per_inst, double *partials, float *per_sample_f,
                             void *stream);
 
+/* As fd_integrand_eval (sampler maps or identity, no per-sample output) with
+ * the Philox iteration taken as iter_base + *d_iter, read on the device when
+ * the kernel runs, so that a captured CUDA graph advances the sample stream
+ * on every replay (d_iter: device uint32, advanced with fd_counter_add). */
+fd_status fd_integrand_eval_iter_dev(const fd_graph *const *graphs, int32_t n_graphs,
+                                     const fd_params *params, const int32_t *graph_of_inst,
+                                     int32_t n_inst, fd_vegas *const *maps, uint64_t seed,
+                                     uint64_t iter_base, const uint32_t *d_iter, int64_t n_per_inst,
+                                     double *partials, void *stream);
+/* *d_counter += v on the device (async). */
+fd_status fd_counter_add(uint32_t *d_counter, uint32_t v, void *stream);
+
 /* Synchronise `stream`; FD_ETIMEOUT if a kernel recorded a bounded wait
  * that gave up since the last call (the record is cleared). */
 fd_status fd_device_status(void *stream);
 
-/* Number of doubles of the `partials` buffer for this launch shape. */
+/* Number of doubles of the `partials` buffer for this launch shape: the tile
+ * partial sums followed by one word the launch uses as its work counter. */
 int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_per_inst);
 
 /* ---- reduction (FP64, fixed order) ---------------------------------------

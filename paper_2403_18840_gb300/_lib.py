@@ -52,6 +52,10 @@ SIGNATURES = {
     "fd_vegas_set_hist": (_i32, [_vp, _pd]),
     "fd_vegas_clear_hist": (_i32, [_vp, _vp]),
     "fd_vegas_update": (_i32, [_vp, _f64, _vp]),
+    "fd_vegas_update_batch": (_i32, [_c.POINTER(_vp), _i32, _f64, _vp]),
+    "fd_integrand_eval_iter_dev": (_i32, [_c.POINTER(_vp), _i32, _c.POINTER(fd_params), _pi, _i32,
+                                          _c.POINTER(_vp), _u64, _u64, _vp, _i64, _vp, _vp]),
+    "fd_counter_add": (_i32, [_vp, _c.c_uint32, _vp]),
     "fd_map_samples": (_i32, [_vp, _u64, _u64, _i32, _i64, _i32, _vp, _vp, _vp]),
     "fd_integrand_eval": (_i32, [_c.POINTER(_vp), _i32, _c.POINTER(fd_params), _pi, _i32,
                                  _c.POINTER(_vp), _vp, _vp, _u64, _u64, _i64, _vp, _vp, _vp]),

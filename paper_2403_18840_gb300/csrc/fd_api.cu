@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -311,6 +312,97 @@ __global__ void vegas_update_kernel(double *edges, float *edges32, double *hist,
     for (int i = tid; i < nb; i += T) H[i] = 0.0;
 }
 
+struct MapRef {
+    double *edges;
+    float *edges32;
+    double *hist;
+    int dim;
+};
+struct BatchMaps {
+    MapRef m[256];
+};
+
+// Batched update: block (dim, map); same algorithm as vegas_update_kernel.
+__global__ void vegas_update_batch_kernel(const __grid_constant__ BatchMaps B, int nb, double alpha) {
+    const MapRef M = B.m[blockIdx.y];
+    if ((int)blockIdx.x >= M.dim) return;
+    extern __shared__ double sh[];
+    double *d = sh;
+    double *r = sh + nb;
+    double *e = sh + 2 * nb;
+    double *red = sh + 3 * nb + 1;
+    const int dim = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+    double *E = M.edges + (size_t)dim * (nb + 1);
+    double *H = M.hist + (size_t)dim * nb;
+    for (int i = tid; i < nb; i += T) d[i] = H[i];
+    for (int i = tid; i <= nb; i += T) e[i] = E[i];
+    __syncthreads();
+    for (int i = tid; i < nb; i += T) {
+        double s;
+        if (nb == 1) s = d[0];
+        else if (i == 0) s = (d[0] + d[1]) / 2.0;
+        else if (i == nb - 1) s = (d[nb - 2] + d[nb - 1]) / 2.0;
+        else s = (d[i - 1] + d[i] + d[i + 1]) / 3.0;
+        r[i] = s;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int i = tid; i < nb; i += T) part += r[i];
+    red[tid] = part;
+    __syncthreads();
+    for (int s2 = T / 2; s2 > 0; s2 >>= 1) {
+        if (tid < s2) red[tid] += red[tid + s2];
+        __syncthreads();
+    }
+    const double S = red[0];
+    __syncthreads();
+    if (!(S > 0.0)) {
+        for (int i = tid; i < nb; i += T) H[i] = 0.0;
+        return;
+    }
+    for (int i = tid; i < nb; i += T) {
+        const double rho = r[i] / S;
+        r[i] = rho <= 0.0 ? 0.0 : (rho >= 1.0 ? 1.0 : pow((rho - 1.0) / log(rho), alpha));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double acc = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            acc += r[i];
+            d[i] = acc;
+        }
+    }
+    __syncthreads();
+    const double R = d[nb - 1];
+    if (!(R > 0.0)) {
+        for (int i = tid; i < nb; i += T) H[i] = 0.0;
+        return;
+    }
+    const double target = R / nb;
+    for (int t = tid + 1; t < nb; t += T) {
+        const double want = t * target;
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (d[mid] >= want) hi = mid;
+            else lo = mid + 1;
+        }
+        const int j = lo;
+        const double before = j ? d[j - 1] : 0.0;
+        const double rj = r[j];
+        double frac = rj > 0.0 ? (want - before) / rj : 0.0;
+        frac = fmin(fmax(frac, 0.0), 1.0);
+        E[t] = e[j] + frac * (e[j + 1] - e[j]);
+    }
+    if (tid == 0) {
+        E[0] = 0.0;
+        E[nb] = 1.0;
+    }
+    __syncthreads();
+    for (int i = tid; i <= nb; i += T) M.edges32[(size_t)dim * (nb + 1) + i] = (float)E[i];
+    for (int i = tid; i < nb; i += T) H[i] = 0.0;
+}
+
 __global__ void map_samples_kernel(const float *edges32, int nb, uint32_t seed_lo, uint32_t seed_hi,
                                    uint32_t iter, uint32_t inst, int64_t n, int dim, float *x, float *w) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -430,6 +522,28 @@ extern "C" fd_status fd_vegas_update(fd_vegas *m, double alpha, void *stream) {
     if (sh > 48 * 1024)
         FD_CHECK_CUDA(cudaFuncSetAttribute(vegas_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     vegas_update_kernel<<<m->dim, T, sh, (cudaStream_t)stream>>>(m->d_edges, m->d_edges32, m->d_hist, nb, alpha);
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
+}
+
+extern "C" fd_status fd_vegas_update_batch(fd_vegas *const *maps, int32_t n_maps, double alpha, void *stream) {
+    FD_REQUIRE(maps && n_maps >= 1 && n_maps <= 256, "1..256 maps are required");
+    FD_REQUIRE(alpha >= 0.0 && alpha <= 4.0 && std::isfinite(alpha), "alpha out of range");
+    static BatchMaps B;
+    int nb = -1, dmax = 0;
+    for (int k = 0; k < n_maps; ++k) {
+        FD_REQUIRE(maps[k], "null map");
+        if (nb < 0) nb = maps[k]->n_bins;
+        FD_REQUIRE(maps[k]->n_bins == nb, "all maps of a batched update need the same bin count");
+        B.m[k] = MapRef{maps[k]->d_edges, maps[k]->d_edges32, maps[k]->d_hist, maps[k]->dim};
+        dmax = std::max(dmax, maps[k]->dim);
+    }
+    const int T = 256;
+    const size_t sh = (size_t)(3 * nb + 1 + T) * 8;
+    FD_REQUIRE(sh <= 227 * 1024, "too many bins for the update kernel");
+    if (sh > 48 * 1024)
+        FD_CHECK_CUDA(cudaFuncSetAttribute(vegas_update_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    vegas_update_batch_kernel<<<dim3(dmax, n_maps), T, sh, (cudaStream_t)stream>>>(B, nb, alpha);
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
 }

@@ -58,9 +58,12 @@ struct EvalArgs {
     int32_t n_inst, tiles_per_inst, r_max, slots_total, dim_max;
     int64_t n_per_inst, tile;
     uint32_t seed_lo, seed_hi, iter;
+    const uint32_t *iter_dev;          // optional: iteration += *iter_dev (read on the device)
+    unsigned long long *queue;         // work counter (reset to 0 before the launch)
     double *partials;
     float *per_sample_f;
     int *status;
+    uint8_t perm[FD_MAX_INST];         // instances in decreasing cost: work items go heaviest first
     InstDesc inst[FD_MAX_INST];
 };
 
@@ -391,7 +394,7 @@ __device__ __forceinline__ void run_chunk(const Slots<T, P> &S, Vars<P> &V, cons
 // the slots [n_slots, n_slots + dim).
 template <int T, int P>
 __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const InstDesc &D, const EvalArgs &A,
-                                         const int64_t (&idx)[P], int inst) {
+                                         const int64_t (&idx)[P], int inst, uint32_t iter) {
     const int N = D.order, dim = D.dim;
     float one[P], zero[P];
 #pragma unroll
@@ -417,7 +420,7 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
             for (int blk = 0; blk < (FD_MAX_DIM + 3) / 4; ++blk) {
                 if (4 * blk < dim) {
                     const u32x4 r = philox4x32_10(
-                        u32x4{c0, c1, A.iter, ((uint32_t)inst << 8) | (uint32_t)blk}, A.seed_lo, A.seed_hi);
+                        u32x4{c0, c1, iter, ((uint32_t)inst << 8) | (uint32_t)blk}, A.seed_lo, A.seed_hi);
                     const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -498,9 +501,16 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
     uint32_t phase[2] = {0u, 0u};
     bool failed = false;
     Vars<P> V;
+    const uint32_t iter = A.iter + (A.iter_dev ? *A.iter_dev : 0u);
+    __shared__ int next_item;
 
-    for (int item = blockIdx.x; item < n_items && !failed; item += gridDim.x) {
-        const int inst = item / A.tiles_per_inst;
+    for (;;) {
+        // dynamic work queue: heaviest instances first, then their tiles
+        if (tid == 0) next_item = (int)atomicAdd(A.queue, 1ull);
+        __syncthreads();
+        const int item = next_item;
+        if (item >= n_items || failed) break;
+        const int inst = A.perm[item / A.tiles_per_inst];
         const int tile = item % A.tiles_per_inst;
         const InstDesc &D = A.inst[inst];
         const int n_chunks = (D.n_instr + CHUNK_INSTR - 1) / CHUNK_INSTR;
@@ -531,7 +541,7 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
                 valid[p] = i < last;
                 idx[p] = valid[p] ? i : first;
             }
-            prologue<T, P>(S, V, D, A, idx, inst);
+            prologue<T, P>(S, V, D, A, idx, inst, iter);
             for (int ch = 0; ch < n_chunks; ++ch, ++g) {
                 const int b = resident ? ch : (int)(g & 1);
                 if (!resident || pass == 0) {
@@ -645,7 +655,7 @@ extern "C" int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_pe
     if (n_inst <= 0 || r_max <= 0 || n_per_inst <= 0) return 0;
     const int64_t tl = fd_tile_samples(n_per_inst);
     const int64_t tiles = (n_per_inst + tl - 1) / tl;
-    return (int64_t)n_inst * tiles * r_max * 4;
+    return (int64_t)n_inst * tiles * r_max * 4 + 1;   // + the work-queue counter
 }
 
 namespace {
@@ -655,8 +665,8 @@ namespace {
 fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_params *params,
                     const int32_t *graph_of_inst, int32_t n_inst, fd_vegas *const *maps,
                     const float *points, const float *point_w, uint64_t seed, uint64_t iter,
-                    int64_t n_per_inst, double *partials, float *per_sample_f, int *status,
-                    cudaStream_t stream) {
+                    const uint32_t *iter_dev, int64_t n_per_inst, double *partials, float *per_sample_f,
+                    int *status, cudaStream_t stream) {
     FD_REQUIRE(graphs && n_graphs > 0, "graphs must be a non-empty array");
     FD_REQUIRE(params && graph_of_inst, "params and graph_of_inst are required");
     FD_REQUIRE(n_inst > 0 && n_inst <= FD_MAX_INST, "n_inst must be in [1, 256]");
@@ -671,6 +681,7 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
     args.seed_lo = (uint32_t)seed;
     args.seed_hi = (uint32_t)(seed >> 32);
     args.iter = (uint32_t)iter;
+    args.iter_dev = iter_dev;
     args.partials = partials;
     args.per_sample_f = per_sample_f;
     args.status = status;
@@ -725,6 +736,16 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
         }
     }
     const int items = n_inst * args.tiles_per_inst;
+    // instances in decreasing graph order (cost): longest-processing-time first
+    {
+        int k = 0;
+        for (int o = FD_MAX_ORDER; o >= 1; --o)
+            for (int j = 0; j < n_inst; ++j)
+                if (args.inst[j].order == o) args.perm[k++] = (uint8_t)j;
+    }
+    args.queue = reinterpret_cast<unsigned long long *>(
+        partials + fd_partials_count(n_inst, r_max, n_per_inst) - 1);
+    FD_CHECK_CUDA(cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), stream));
     int dev = 0, max_smem = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
     FD_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -768,8 +789,29 @@ extern "C" fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_
                                        const float *point_w, uint64_t seed, uint64_t iter,
                                        int64_t n_per_inst, double *partials, float *per_sample_f,
                                        void *stream) {
-    return eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter,
+    return eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, nullptr,
                      n_per_inst, partials, per_sample_f, fd::device_status_word(), (cudaStream_t)stream);
+}
+
+extern "C" fd_status fd_integrand_eval_iter_dev(const fd_graph *const *graphs, int32_t n_graphs,
+                                                const fd_params *params, const int32_t *graph_of_inst,
+                                                int32_t n_inst, fd_vegas *const *maps, uint64_t seed,
+                                                uint64_t iter_base, const uint32_t *d_iter, int64_t n_per_inst,
+                                                double *partials, void *stream) {
+    FD_REQUIRE(d_iter, "d_iter is required");
+    return eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, nullptr, nullptr, seed, iter_base,
+                     d_iter, n_per_inst, partials, nullptr, fd::device_status_word(), (cudaStream_t)stream);
+}
+
+namespace {
+__global__ void counter_add_kernel(uint32_t *c, uint32_t v) { *c += v; }
+}  // namespace
+
+extern "C" fd_status fd_counter_add(uint32_t *d_counter, uint32_t v, void *stream) {
+    FD_REQUIRE(d_counter, "d_counter is required");
+    counter_add_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_counter, v);
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
 }
 
 // ---- fd_accumulate ---------------------------------------------------------------
@@ -871,8 +913,8 @@ extern "C" fd_status fd_integrand_eval_stats_noalloc(
     // every byte 0xFF is a NaN double: a tile the kernel failed to write shows up
     // as NaN in `out` instead of a stale value from an earlier call
     FD_CHECK_CUDA(cudaMemsetAsync(partials, 0xFF, (size_t)need * sizeof(double), s));
-    st = eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, n_per_inst,
-                   partials, per_sample_f, nullptr, s);
+    st = eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, nullptr,
+                   n_per_inst, partials, per_sample_f, nullptr, s);
     if (st != FD_OK) return st;
     return fd_accumulate(partials, n_inst, r_max, n_per_inst, out, stream);
 }

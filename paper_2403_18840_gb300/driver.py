@@ -118,3 +118,50 @@ def compare(G, params, vegas, flow, n, seed, root=0):
     out["means_agree_sigma"] = abs(out["flow"]["mean"] - out["vegas"]["mean"]) / math.sqrt(
         sv[root, 0, 1] + sf[root, 0, 1])
     return out
+
+
+class BatchedIteration:
+    """One persistent launch over many instances of uneven graph order, captured
+    as a CUDA graph per iteration: integrand (with VEGAS histograms), fixed-order
+    reduction, batched VEGAS update and the device-side iteration counter."""
+
+    def __init__(self, graphs, params, graph_of_inst, n_per_inst, seed, n_bins=1024, alpha=0.5):
+        self.graphs = list(graphs)
+        self.params = list(params)
+        self.gi = list(graph_of_inst)
+        self.n = int(n_per_inst)
+        self.seed = seed
+        self.alpha = alpha
+        self.maps = [api.Vegas(self.graphs[g].dim, n_bins) for g in self.gi]
+        self.plan = api.EvalPlan(self.graphs, self.params, self.gi, self.n, maps=self.maps)
+        self._maps_arr = (api.ctypes.c_void_p * len(self.maps))(*[m.handle for m in self.maps])
+        self.d_iter = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.graph = None
+        self.stream = None
+
+    def _enqueue(self, stream):
+        lib = api.L.lib()
+        sp = api._stream_ptr(stream)
+        api.L.check(lib.fd_integrand_eval_iter_dev(self.plan._g, len(self.graphs), self.plan._p, self.plan._gi,
+                                                   self.plan.n_inst, self.plan._m, self.seed, 0,
+                                                   api._ptr(self.d_iter), self.n, api._ptr(self.plan.partials), sp))
+        api.L.check(lib.fd_accumulate(api._ptr(self.plan.partials), self.plan.n_inst, self.plan.r_max, self.n,
+                                      api._ptr(self.plan.stats), sp))
+        api.L.check(lib.fd_vegas_update_batch(self._maps_arr, len(self.maps), self.alpha, sp))
+        api.L.check(lib.fd_counter_add(api._ptr(self.d_iter), 1, sp))
+
+    def step_direct(self, stream=None):
+        self._enqueue(stream or torch.cuda.current_stream())
+        return self.plan.stats
+
+    def capture(self):
+        self.stream = torch.cuda.Stream()
+        api.device_status()                       # make sure per-device state exists before capture
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self._enqueue(self.stream)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+        return self.plan.stats
