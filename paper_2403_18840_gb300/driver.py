@@ -102,22 +102,35 @@ def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3):
     return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
 
 
-def compare(G, params, vegas, flow, n, seed, root=0):
-    """Variance-adjusted efficiency of flow vs VEGAS for the real part of `root`."""
-    sv, tv = measure_sampler(G, params, n, seed, 50000, vegas=vegas)
-    sf, tf = measure_sampler(G, params, n, seed, 60000, flow=flow)
-    var_v = sv[root, 0, 1] * n        # per-sample variance
-    var_f = sf[root, 0, 1] * n
-    out = {
-        "vegas": {"mean": float(sv[root, 0, 0]), "err": float(math.sqrt(sv[root, 0, 1])), "var_per_sample": float(var_v),
-                  "samples_per_s": 1.0 / tv, "eff_samples_per_s": 1.0 / tv},
-        "flow": {"mean": float(sf[root, 0, 0]), "err": float(math.sqrt(sf[root, 0, 1])), "var_per_sample": float(var_f),
-                 "samples_per_s": 1.0 / tf, "eff_samples_per_s": (1.0 / tf) * var_v / var_f},
-    }
-    out["flow_over_vegas"] = out["flow"]["eff_samples_per_s"] / out["vegas"]["eff_samples_per_s"]
-    out["means_agree_sigma"] = abs(out["flow"]["mean"] - out["vegas"]["mean"]) / math.sqrt(
-        sv[root, 0, 1] + sf[root, 0, 1])
-    return out
+def compare(G, params, vegas, flow, n, seed, root=0, batches=4):
+    """Variance-adjusted efficiency of flow vs VEGAS for the real part of `root`.
+
+    Each sampler draws `batches` independent batches of n samples; the
+    per-sample variance is the mean of the batch estimates (the integrand is
+    heavy-tailed, so single estimates scatter) and the batch means give the
+    combined estimate and its error.
+    """
+    res = {}
+    for name, kw, it0 in (("vegas", dict(vegas=vegas), 50000), ("flow", dict(flow=flow), 60000)):
+        means, vars_, secs = [], [], []
+        for b in range(batches):
+            st, sec = measure_sampler(G, params, n, seed, it0 + 10 * b, reps=1, **kw)
+            means.append(st[root, 0, 0])
+            vars_.append(st[root, 0, 1] * n)
+            secs.append(sec)
+        v = float(np.mean(vars_))
+        t = float(np.mean(secs))
+        m = float(np.mean(means))
+        err = float(math.sqrt(v / (n * batches)))
+        res[name] = {"mean": m, "err": err, "var_per_sample": v, "var_batches": [float(x) for x in vars_],
+                     "batch_means": [float(x) for x in means], "samples_per_s": 1.0 / t}
+    res["vegas"]["eff_samples_per_s"] = res["vegas"]["samples_per_s"]
+    res["flow"]["eff_samples_per_s"] = res["flow"]["samples_per_s"] * res["vegas"]["var_per_sample"] / \
+        res["flow"]["var_per_sample"]
+    res["flow_over_vegas"] = res["flow"]["eff_samples_per_s"] / res["vegas"]["eff_samples_per_s"]
+    res["means_agree_sigma"] = abs(res["flow"]["mean"] - res["vegas"]["mean"]) / math.sqrt(
+        res["flow"]["err"] ** 2 + res["vegas"]["err"] ** 2)
+    return res
 
 
 class BatchedIteration:
