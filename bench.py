@@ -267,6 +267,8 @@ def run_ours(args, rank, world, dist):
     n_sm = props.multi_processor_count
     mhz_max = _peaks().get("sm_max_mhz", 2070.0)
     peak = fp32_peak_tflops(n_sm, mhz_max)
+    measured = {"fp32_fma_tflops": api.measure_peak(0) / 1e12, "sfu_ex2_tops": api.measure_peak(1) / 1e12,
+                "sfu_rcp_tops": api.measure_peak(2) / 1e12}
     achieved = flops_ps * n / t_kern / 1e12
     sfu_achieved = sfu_ps * n / t_kern / 1e12
     line = {
@@ -286,6 +288,8 @@ def run_ours(args, rank, world, dist):
                      "executed_flops_per_sample": exec_flops_ps, "executed_sfu_per_sample": exec_sfu_ps,
                      "sfu_achieved_tops": sfu_achieved,
                      "peak_basis": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (n_sm, mhz_max),
+                     "measured_pipe_peaks": measured,
+                     "frac_of_measured_fp32": achieved / measured["fp32_fma_tflops"],
                      "kernel_ms": 1e3 * t_kern},
         "e2e": {"value": n / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "eff_samples_per_s": eff,

@@ -125,7 +125,9 @@ fd_status fd_map_samples(const fd_vegas *map, uint64_t seed, uint64_t iter, int3
  * fd_map_samples with maps[j] (NULL entry = identity) -- or, when `points`
  * is not NULL, on the given points instead (points: device
  * [n_inst][dim_max][n_per_inst] with dim_max the largest graph dimension,
- * point_w: device [n_inst][n_per_inst] sample weights).
+ * point_w: device [n_inst][n_per_inst] sample weights).  Given points with a
+ * map are coordinates of the map's input space: the map and its Jacobian are
+ * applied (a proposal that lives on top of an adapted VEGAS grid).
  * For each sample and root r it computes
  *   f_r = w * J(x) * sum_t s_t d^m_mu d^l_Lambda (d_k)^dk [prod G0 prod V] e^{i pi x_out}
  * in FP32 (J: loop-momentum and time Jacobians of the roots' own variables).
@@ -136,7 +138,7 @@ fd_status fd_map_samples(const fd_vegas *map, uint64_t seed, uint64_t iter, int3
  *    tile, (.., r, c, 1) = sum of f^2.  Tiles are summed in a fixed order
  *    inside the tile, so results are bitwise reproducible.
  *  per_sample_f (device, optional): FP32 [n_inst][R_max][2][n_per_inst].
- *  VEGAS maps (when given and `points` is NULL) accumulate their histograms.
+ *  VEGAS maps accumulate their histograms only when `points` is NULL.
  * params and graph_of_inst are host arrays; graphs/maps host arrays of handles.
  * FD_ETIMEOUT if a bounded wait for a tape copy gave up. */
 fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_graphs,
@@ -234,6 +236,13 @@ fd_status fd_flow_grad(fd_flow *f, const float *x, const float *w, int64_t n, fl
  * the end), may be NULL. */
 fd_status fd_flow_train(fd_flow *f, const float *x, const float *w, int64_t n, int32_t steps,
                         float lr, float *loss_out, void *stream);
+
+/* ---- pipe throughput probes -------------------------------------------------
+ * Measured throughput of one pipe of the current device, used as roofline
+ * denominators next to the unit-count peaks: kind 0 = FP32 FMA (flops per
+ * second, FMA = 2), 1 = SFU exp2 (results per second), 2 = SFU reciprocal.
+ * Synchronous; allocates a small scratch buffer. */
+fd_status fd_measure_peak(int32_t kind, double *ops_per_s);
 
 /* ---- renormalisation post-processing (host, FP64; Sec. VI.A) -------------
  * sigma_re/sigma_im/dsigma_re: FP64 [N+1][N+1][N+1] indexed (n, m, l) holding

@@ -73,6 +73,7 @@ SIGNATURES = {
     "fd_flow_log_density": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "fd_flow_grad": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fd_flow_train": (_i32, [_vp, _vp, _vp, _i64, _i32, _f32, _pf, _vp]),
+    "fd_measure_peak": (_i32, [_i32, _pd]),
     "fd_postprocess": (_i32, [_i32, _pd, _pd, _pd, _f64, _f64, _f64, _pd, _pd, _pd, _pd]),
 }
 

@@ -225,6 +225,13 @@ class Flow:
             self.handle = None
 
 
+def measure_peak(kind):
+    """Measured pipe throughput: 0 FP32 FMA (flop/s), 1 SFU ex2, 2 SFU rcp (results/s)."""
+    v = ctypes.c_double()
+    L.check(L.lib().fd_measure_peak(kind, ctypes.byref(v)))
+    return v.value
+
+
 def device_status(stream=None):
     L.check(L.lib().fd_device_status(_stream_ptr(stream)))
 

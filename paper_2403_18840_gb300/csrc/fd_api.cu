@@ -74,7 +74,7 @@ static fd_status validate_tape(const uint8_t *buf, size_t len, TapeHeader &h) {
     if ((uint64_t)h.root_off + 8ull * h.n_roots > len) return fd::set_error(FD_EFORMAT, "root table out of bounds");
     if ((uint64_t)h.instr_off + 8ull * h.n_instr > len) return fd::set_error(FD_EFORMAT, "instructions out of bounds");
     const uint32_t N = h.order;
-    const uint32_t fixed = 2;   // slot 0 = 0.0, slot 1 = 1.0
+    const uint32_t fixed = 2 + N;   // 0.0, 1.0, times of the N interaction lines
     const uint32_t S = h.n_slots;
     if (S < fixed) return fd::set_error(FD_EFORMAT, "slot count below the fixed slots");
     for (uint32_t r = 0; r < h.n_roots; ++r) {
@@ -85,41 +85,33 @@ static fd_status validate_tape(const uint8_t *buf, size_t len, TapeHeader &h) {
     std::vector<int> flushed(h.n_roots, 0);
     bool has_end = false;
     uint32_t in_bundle = 0;                 // FMA words still expected in the current bundle
-    std::vector<uint32_t> bdst, bsrc;       // destinations and sources of the current bundle
+    std::vector<uint32_t> bdst;             // destinations of the current bundle
     for (uint32_t k = 0; k < h.n_instr; ++k) {
         uint64_t w;
         memcpy(&w, buf + h.instr_off + 8ull * k, 8);
+        if (in_bundle) {
+            // bundle word: four u16 slot indices (d, a, b, c)
+            const uint32_t d = (uint32_t)(w & 0xFFFFu), a = (uint32_t)((w >> 16) & 0xFFFFu),
+                           b = (uint32_t)((w >> 32) & 0xFFFFu), c = (uint32_t)(w >> 48);
+            bool ok = d >= fixed && d < S && a < S && b < S && c < S;
+            for (uint32_t q : bdst) ok = ok && q != d;   // results may not share a slot
+            bdst.push_back(d);
+            if (!ok) return fd::set_error(FD_EFORMAT, "bundle word " + std::to_string(k) + " out of range");
+            --in_bundle;
+            continue;
+        }
         const uint32_t op = (uint32_t)(w & 63u);
-        if (in_bundle && op != OP_FMA)
-            return fd::set_error(FD_EFORMAT, "bundle " + std::to_string(k) + " holds a non-FMA word");
         const uint32_t d = (uint32_t)(w >> 6) & 16383u, a = (uint32_t)(w >> 20) & 16383u,
                        b = (uint32_t)(w >> 34) & 16383u, c = (uint32_t)(w >> 48) & 16383u;
+        (void)c;
         bool ok = true;
         switch (op) {
-            case OP_FMA:
-                ok = d >= fixed && d < S && a < S && b < S && c < S;
-                if (in_bundle) {
-                    bdst.push_back(d);
-                    bsrc.push_back(a);
-                    bsrc.push_back(b);
-                    bsrc.push_back(c);
-                    if (--in_bundle == 0) {
-                        // a bundle loads every operand before storing any result, so a
-                        // destination may reuse a slot the bundle reads; two results
-                        // may not share a slot
-                        for (size_t i = 0; i < bdst.size() && ok; ++i)
-                            for (size_t j = 0; j < bdst.size() && ok; ++j)
-                                ok = (i == j || bdst[i] != bdst[j]);
-                    }
-                }
-                break;
             case OP_BUNDLE: {
                 const uint32_t n = (uint32_t)(w >> 6) & 15u;
-                ok = n >= 2 && n <= (uint32_t)FD_MAX_BUNDLE && k + n < h.n_instr &&
+                ok = n >= 1 && n <= (uint32_t)FD_MAX_BUNDLE && k + n < h.n_instr &&
                      k / FD_CHUNK_WORDS == (k + n) / FD_CHUNK_WORDS;
                 in_bundle = n;
                 bdst.clear();
-                bsrc.clear();
                 break;
             }
             case OP_NOP: break;
@@ -130,8 +122,8 @@ static fd_status validate_tape(const uint8_t *buf, size_t len, TapeHeader &h) {
                 const uint32_t width = (M + 1) * (dk ? 2 : 1);
                 ok = d >= fixed && d + width <= S && M + dk <= (uint32_t)FD_MAX_M;
                 for (uint32_t j = 0; j <= (uint32_t)FD_MAX_ORDER && ok; ++j) {
-                    const uint32_t f = (a >> (2 * j)) & 3u;
-                    ok = f != 3u && (j <= N || f == 0u);
+                    const uint32_t f = (a >> (2 * j)) & 3u;   // 0 absent, 1 plus, 3 minus
+                    ok = f != 2u && (j <= N || f == 0u);
                 }
                 if (op == OP_GLEAF) ok = ok && la < N && lb < N;
                 break;
@@ -632,5 +624,70 @@ extern "C" fd_status fd_postprocess(int32_t N, const double *sigma_re, const dou
         if (b_out) b_out[i] = b[i];
         if (meff_out) meff_out[i] = acc;
     }
+    return FD_OK;
+}
+
+// ---- throughput probes (FP32 FMA, SFU ex2 / rcp) ------------------------------------
+namespace {
+// 8 independent dependency chains per thread so the pipe, not latency, bounds the rate
+template <int KIND>
+__global__ void peak_kernel(float *out, int iters, float seed) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = seed + 0.001f * (threadIdx.x + j);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (KIND == 0) {
+                v[j] = fmaf(v[j], 0.9999999f, 1e-7f);
+            } else if (KIND == 1) {
+                float r;
+                asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v[j]));
+                v[j] = r * -0.5f;
+            } else {
+                float r;
+                asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v[j]));
+                v[j] = r + 1.0f;   // continued fraction: nothing to fold
+            }
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += v[j];
+    if (s == 12345.678f) out[threadIdx.x] = s;   // keeps the work alive
+}
+}  // namespace
+
+// Measured throughput of one pipe on the current device (synchronous):
+// kind 0 = FP32 FMA (flops, FMA = 2), 1 = SFU ex2, 2 = SFU rcp (results).
+extern "C" fd_status fd_measure_peak(int32_t kind, double *ops_per_s) {
+    FD_REQUIRE(ops_per_s && kind >= 0 && kind <= 2, "kind in 0..2 and an output are required");
+    int dev = 0, n_sm = 0;
+    FD_CHECK_CUDA(cudaGetDevice(&dev));
+    FD_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    float *out = nullptr;
+    FD_CHECK_CUDA(cudaMalloc(&out, 1024 * sizeof(float)));
+    const int threads = 512, blocks = n_sm * 4, iters = kind == 0 ? 8192 : 2048;
+    cudaEvent_t a, b;
+    FD_CHECK_CUDA(cudaEventCreate(&a));
+    FD_CHECK_CUDA(cudaEventCreate(&b));
+    auto launch = [&]() {
+        if (kind == 0) peak_kernel<0><<<blocks, threads>>>(out, iters, 1.0f);
+        else if (kind == 1) peak_kernel<1><<<blocks, threads>>>(out, iters, 0.5f);
+        else peak_kernel<2><<<blocks, threads>>>(out, iters, 1.5f);
+    };
+    launch();
+    FD_CHECK_CUDA(cudaGetLastError());
+    FD_CHECK_CUDA(cudaEventRecord(a));
+    for (int r = 0; r < 5; ++r) launch();
+    FD_CHECK_CUDA(cudaEventRecord(b));
+    FD_CHECK_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    FD_CHECK_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    const double ops = 5.0 * blocks * threads * (double)iters * 8.0 * (kind == 0 ? 2.0 : 1.0);
+    *ops_per_s = ops / (ms * 1e-3);
     return FD_OK;
 }

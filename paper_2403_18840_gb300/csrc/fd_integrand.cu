@@ -124,7 +124,6 @@ struct Slots {
 template <int P>
 struct Vars {
     float kx[NK][P], ky[NK][P], kz[NK][P];     // loop momenta k_1..k_N
-    float tx[NK][P];                           // hypercube time of interaction line i (tx[0] = 0)
     float re[P], im[P], hsum[P];               // root accumulator and |f| sum for VEGAS
 };
 
@@ -147,8 +146,7 @@ __device__ __forceinline__ void momentum(const Vars<P> &V, uint32_t mask, float 
                                          float (&py)[P], float (&pz)[P], float &ks) {
     float cf[NK + 1];
 #pragma unroll
-    for (int j = 0; j <= NK; ++j)
-        cf[j] = (float)((mask >> (2 * j)) & 1u) - (float)((mask >> (2 * j + 1)) & 1u);
+    for (int j = 0; j <= NK; ++j) cf[j] = (float)(((int)(mask << (30 - 2 * j))) >> 30);   // signed 2-bit field
     ks = cf[0];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -180,13 +178,16 @@ __device__ __forceinline__ void g_leaf(const Slots<T, P> &S, const Vars<P> &V, u
     float px[P], py[P], pz[P], ks;
     momentum(V, mask, D.kext, px, py, pz, ks);
     const float beta = D.beta;
+    float ta[P], tb[P];
+    S.load(2 + la, ta);                        // hypercube time of the two lines
+    S.load(2 + lb, tb);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const float eps = fmaf(px[p], px[p], fmaf(py[p], py[p], pz[p] * pz[p])) - D.mu;
         const float E = __expf(-beta * fabsf(eps));
         const float phi = __frcp_rn(1.0f + E);
         const float psi = E * phi;
-        const float dx = pick(V.tx, la, p) - pick(V.tx, lb, p);
+        const float dx = ta[p] - tb[p];
         const bool pos = dx > 0.0f;
         const float tau = beta * dx;
         const bool occ = eps < 0.0f;
@@ -320,14 +321,15 @@ __device__ __forceinline__ void run_chunk(const Slots<T, P> &S, Vars<P> &V, cons
             const int n = (int)((w >> 6) & 15u);
             const uint64_t *q = code + k + 1;
             float a[FD_MAX_BUNDLE][P], b[FD_MAX_BUNDLE][P], c[FD_MAX_BUNDLE][P];
-            uint64_t ws[FD_MAX_BUNDLE];
+            uint32_t dst[FD_MAX_BUNDLE];
 #pragma unroll
             for (int j = 0; j < FD_MAX_BUNDLE; ++j) {
                 if (j < n) {
-                    ws[j] = q[j];
-                    S.load(f_a(ws[j]), a[j]);
-                    S.load(f_b(ws[j]), b[j]);
-                    S.load(f_c(ws[j]), c[j]);
+                    const uint2 ww = *reinterpret_cast<const uint2 *>(q + j);
+                    dst[j] = ww.x & 0xFFFFu;
+                    S.load(ww.x >> 16, a[j]);
+                    S.load(ww.y & 0xFFFFu, b[j]);
+                    S.load(ww.y >> 16, c[j]);
                 }
             }
 #pragma unroll
@@ -335,20 +337,10 @@ __device__ __forceinline__ void run_chunk(const Slots<T, P> &S, Vars<P> &V, cons
                 if (j < n) {
 #pragma unroll
                     for (int p = 0; p < P; ++p) a[j][p] = fmaf(a[j][p], b[j][p], c[j][p]);
-                    S.store(f_d(ws[j]), a[j]);
+                    S.store(dst[j], a[j]);
                 }
             }
             k += n;
-            continue;
-        }
-        if (op == OP_FMA) {
-            float a[P], b[P], c[P];
-            S.load(f_a(w), a);
-            S.load(f_b(w), b);
-            S.load(f_c(w), c);
-#pragma unroll
-            for (int p = 0; p < P; ++p) a[p] = fmaf(a[p], b[p], c[p]);
-            S.store(f_d(w), a);
             continue;
         }
         switch (op) {
@@ -359,13 +351,14 @@ __device__ __forceinline__ void run_chunk(const Slots<T, P> &S, Vars<P> &V, cons
                 v_leaf(S, V, w, D);
                 break;
             case OP_RACC: {
-                float a[P];
+                float a[P], tl[P];
                 S.load(f_a(w), a);
                 const uint32_t line = f_b(w);
+                S.load(2 + line, tl);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     float sn = 0.0f, cs = 1.0f;
-                    if (line) sincospif(pick(V.tx, line, p), &sn, &cs);
+                    if (line) sincospif(tl[p], &sn, &cs);
                     V.re[p] = fmaf(a[p], cs, V.re[p]);
                     V.im[p] = fmaf(a[p], sn, V.im[p]);
                 }
@@ -404,6 +397,7 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
     }
     S.store(0, zero);
     S.store(1, one);
+    S.store(2, zero);                           // time of interaction line 0
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int64_t i = idx[p];
@@ -449,7 +443,6 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
             V.kx[j][p] = 0.0f;
             V.ky[j][p] = 0.0f;
             V.kz[j][p] = 0.0f;
-            V.tx[j][p] = 0.0f;
             const int jj = j + 1;                       // loop momentum k_jj
             if (jj <= N) {
                 const int c0 = (jj == 1) ? 0 : 4 * jj - 5;
@@ -463,12 +456,12 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
                 V.ky[j][p] = r * sth * sp;
                 V.kz[j][p] = r * cth;
                 jac *= D.kc * r * r * K_INV_2PI2;
-                if (!D.points) jac *= jd[c0] * jd[c0 + 1] * jd[c0 + 2];
+                jac *= jd[c0] * jd[c0 + 1] * jd[c0 + 2];   // 1 without a map
                 if (jj >= 2) {
                     // time of interaction line jj - 1
-                    V.tx[jj - 1][p] = x[4 * jj - 2];
+                    S.store1(2 + jj - 1, p, x[4 * jj - 2]);   // time of interaction line jj - 1
                     jac *= D.beta;
-                    if (!D.points) jac *= jd[4 * jj - 2];
+                    jac *= jd[4 * jj - 2];
                 }
                 S.store1(D.n_slots + D.dim + j, p, jac);
             }
@@ -728,10 +721,12 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
         if (points) {
             D.points = points + (int64_t)j * dim_max * n_per_inst;
             D.point_w = point_w ? point_w + (int64_t)j * n_per_inst : nullptr;
-        } else if (maps && maps[j]) {
+        }
+        if (maps && maps[j]) {
+            // given points are the map's input coordinates; only drawn samples adapt the grid
             FD_REQUIRE(maps[j]->dim == D.dim, "VEGAS map dimension differs from the graph dimension");
             D.edges = maps[j]->d_edges32;
-            D.hist = maps[j]->d_hist;
+            D.hist = points ? nullptr : maps[j]->d_hist;
             D.n_bins = maps[j]->n_bins;
         }
     }

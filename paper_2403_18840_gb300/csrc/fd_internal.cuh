@@ -29,21 +29,21 @@ int *device_status_word();
 
 }  // namespace fd
 
-// ---- tape format, version 2 (mirrors paper_2403_18840_gb300/fdgraph.py) ----------
+// ---- tape format, version 3 (mirrors paper_2403_18840_gb300/fdgraph.py) ----------
 enum : uint32_t {
-    OP_FMA = 1,      // S[d] = S[a] * S[b] + S[c]
+    OP_FMA = 1,      // reserved (products and sums travel in bundles)
     OP_GLEAF = 2,    // G0 Taylor family from a momentum mask and two interaction lines
     OP_VLEAF = 3,    // V Taylor family from a momentum mask
     OP_RACC = 4,     // root accumulator += S[a] * exp(i pi x_line)
     OP_RFLUSH = 5,   // root d complete
     OP_CONST = 6,    // S[d] = f32 immediate
     OP_NOP = 7,      // padding
-    OP_BUNDLE = 8,   // next n (<= 8) words are independent FMAs
+    OP_BUNDLE = 8,   // next n (1..8) words are independent FMAs, u16 (d, a, b, c) each
     OP_END = 63,
 };
 
 constexpr uint32_t TAPE_MAGIC = 0x50544446u;  // 'FDTP'
-constexpr uint32_t TAPE_VERSION = 2;
+constexpr uint32_t TAPE_VERSION = 3;
 constexpr int FD_MAX_ORDER = 6;
 constexpr int FD_MAX_DIM = 4 * FD_MAX_ORDER - 1;
 constexpr int FD_MAX_M = 7;         // largest Taylor order of a leaf family (incl. d/dk)

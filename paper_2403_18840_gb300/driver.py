@@ -7,6 +7,13 @@ method itself generates: points drawn from the current sampler q_s carry the
 weight |f(x)| / q_s(x), which the integrand kernel returns directly when it is
 given the sampler's 1/q as point weights.  The comparison is at equal error
 bars: efficiency 1 / (per-sample variance x time per sample).
+
+With `on_vegas` the flow lives in the input coordinates y of the adapted VEGAS
+map: x = map(y), and the proposal density is q_flow(y) / J_map(y).  The flow
+starts as the identity, so the proposal starts as VEGAS itself and training
+adds the correlations between coordinates that a separable grid cannot hold;
+its target is |f(map(y))| J_map(y), which the kernel returns when it is given
+the map together with the points.
 """
 import math
 import time
@@ -40,7 +47,8 @@ def training_weights(per_sample, value_roots):
     return ps.abs().sum(dim=(0, 1)).contiguous()
 
 
-def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, evals_per_batch=1, log=None):
+def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, evals_per_batch=1, log=None,
+               on_vegas=True):
     """Forward-KL training of `flow` on |f|; the first `vegas_steps` batches come from VEGAS.
 
     Every batch is drawn from the current sampler, evaluated by the integrand
@@ -48,12 +56,13 @@ def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, e
     Returns the list of losses.
     """
     value_roots = [r for r, (n, m, l, dk) in enumerate(G.roots) if dk == 0]
-    plan = api.EvalPlan([G], [params], [0], batch, per_sample=True)
+    plan = api.EvalPlan([G], [params], [0], batch, maps=[vegas] if on_vegas else None, per_sample=True)
     losses = []
     k = 0
     while k < steps:
         if k < vegas_steps:
-            x, w = api.map_samples(vegas, seed, 1000 + k, 1, batch, G.dim)
+            # VEGAS draws: uniform in the map's input space, or mapped points
+            x, w = api.map_samples(None if on_vegas else vegas, seed, 1000 + k, 1, batch, G.dim)
         else:
             x, w = flow.sample(seed, 1000 + k, 2, batch)
         plan.run(seed, 1000 + k, points=x, point_w=w)
@@ -74,7 +83,8 @@ def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3):
     """Per-sample variance of every root and seconds per sample for one sampler.
 
     VEGAS: the map is applied inside the integrand kernel.  Flow: the sampling
-    kernel writes points and 1/q, the integrand kernel reads them.
+    kernel writes points and 1/q, the integrand kernel reads them (and applies
+    `vegas` on top when it is given).
     Returns (stats [R][2][2] of the last rep, seconds per sample).
     """
     if flow is None:
@@ -88,7 +98,7 @@ def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3):
         e.record()
         torch.cuda.synchronize()
         return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
-    plan = api.EvalPlan([G], [params], [0], n)
+    plan = api.EvalPlan([G], [params], [0], n, maps=[vegas] if vegas is not None else None)
     x, w = flow.sample(seed, it, 3, n)
     plan.run(seed, it, points=x, point_w=w)
     torch.cuda.synchronize()
@@ -102,7 +112,7 @@ def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3):
     return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
 
 
-def compare(G, params, vegas, flow, n, seed, root=0, batches=4):
+def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True):
     """Variance-adjusted efficiency of flow vs VEGAS for the real part of `root`.
 
     Each sampler draws `batches` independent batches of n samples; the
@@ -111,7 +121,8 @@ def compare(G, params, vegas, flow, n, seed, root=0, batches=4):
     combined estimate and its error.
     """
     res = {}
-    for name, kw, it0 in (("vegas", dict(vegas=vegas), 50000), ("flow", dict(flow=flow), 60000)):
+    flow_kw = dict(flow=flow, vegas=vegas if on_vegas else None)
+    for name, kw, it0 in (("vegas", dict(vegas=vegas), 50000), ("flow", flow_kw, 60000)):
         means, vars_, secs = [], [], []
         for b in range(batches):
             st, sec = measure_sampler(G, params, n, seed, it0 + 10 * b, reps=1, **kw)

@@ -33,15 +33,17 @@ Tape format, version 2 (little endian; sections 16-byte aligned):
           n_instr, root_table_off, instr_off, total_bytes, n_g_leaves,
           n_v_leaves, n_arith, n_consts, reserved x2
   roots   n_roots x (u8 n, u8 m, u8 l, u8 dk, u16 0, u16 0)
-  instr   n_instr x u64, low to high: op:6 | d:14 | a:14 | b:14 | c:14.
-          FMA uses all four slot fields.  Leaf ops keep in `a` a 2-bit sign
-          per momentum variable (k_ext, k_1..k_N; 1 = +, 2 = -) and in the
-          upper bits the two interaction lines (3 bits each), the Taylor
-          order (3 bits) and the d/dk flag.  RACC: `a` = value slot, `b` =
-          out-line; RFLUSH: `d` = root index; CONST: float in the high 32 bits.
-Per-sample state: slot 0 = 0.0 and slot 1 = 1.0 (written by the kernel),
-constants, leaf families and temporaries; loop momenta, times, phases,
-Jacobians and root accumulators live in registers of the interpreter.
+  instr   n_instr x u64, low to high: op:6 | d:14 | a:14 | b:14 | c:14, except
+          the words that follow a BUNDLE header (four u16 slot indices each).
+          Leaf ops keep in `a` a signed 2-bit coefficient per momentum
+          variable (k_ext, k_1..k_N; 1 = +1, 3 = -1) and in the upper bits the
+          two interaction lines (3 bits each), the Taylor order (3 bits) and
+          the d/dk flag.  RACC: `a` = value slot, `b` = out-line; RFLUSH:
+          `d` = root index; CONST: float in the high 32 bits.
+Per-sample state: slot 0 = 0.0, slot 1 = 1.0 and slots 2..N+1 = hypercube time
+of interaction lines 0..N-1 (written by the kernel), then constants, leaf
+families and temporaries; loop momenta, Jacobians and root accumulators live
+in registers or fixed extra slots of the interpreter.
 """
 import collections
 import itertools
@@ -50,17 +52,19 @@ import struct
 import sys
 
 MAGIC = 0x50544446  # 'FDTP'
-VERSION = 2
+VERSION = 3
 
 # opcodes (keep in sync with csrc/fd_internal.cuh)
-OP_FMA = 1      # S[d] = S[a] * S[b] + S[c]   (MUL: c = slot 0 = 0.0; ADD: b = slot 1 = 1.0)
+OP_FMA = 1      # (reserved; products and sums travel in bundles)
 OP_GLEAF = 2    # S[d..] = Taylor coefficients of G0; momentum mask, lines la/lb, M, dk
 OP_VLEAF = 3    # S[d..] = Taylor coefficients of V; momentum mask, L, dk
 OP_RACC = 4     # root accumulator += S[a] * exp(i pi x_line)   (line 0: phase 1)
 OP_RFLUSH = 5   # root r complete: weight by its Jacobian, reduce, reset the accumulator
 OP_CONST = 6    # S[d] = f32 immediate (high 32 bits)
 OP_NOP = 7      # padding (keeps bundles inside one tape chunk)
-OP_BUNDLE = 8   # the next n (<= 8) words are independent FMAs: load all, compute, store all
+OP_BUNDLE = 8   # the next n (1..8) words are independent FMAs S[d] = S[a] S[b] + S[c]
+                #   (u16 d, a, b, c; MUL: c = slot 0 = 0.0; ADD: b = slot 1 = 1.0):
+                #   the kernel loads all operands, computes, then stores all results
 CHUNK_WORDS = 1024   # tape chunk the GPU stages at a time; bundles never straddle one
 MAX_BUNDLE = 8
 OP_END = 63
@@ -379,9 +383,10 @@ def _horner(dag, monos):
 # --------------------------------------------------------------------------
 
 def _enc_fma(d, a, b, c):
+    """FMA word inside a bundle: four u16 slot indices (d, a, b, c), low to high."""
     for v in (d, a, b, c):
         assert 0 <= v < 16384
-    return OP_FMA | (d << 6) | (a << 20) | (b << 34) | (c << 48)
+    return d | (a << 16) | (b << 32) | (c << 48)
 
 
 def _enc_leaf(op, d, mask, la, lb, M, dk):
@@ -403,13 +408,14 @@ def _enc_const(d, f):
 
 
 def mom_mask(mom):
-    """2 bits per momentum variable (k_ext, k_1..k_N): 1 = +1, 2 = -1."""
+    """2 bits per momentum variable (k_ext, k_1..k_N) read as a signed 2-bit
+    integer: 0 = absent, 1 = +1, 3 = -1."""
     m = 0
     for j, c in enumerate(mom):
         if c == 1:
             m |= 1 << (2 * j)
         elif c == -1:
-            m |= 2 << (2 * j)
+            m |= 3 << (2 * j)
         else:
             assert c == 0
     return m
@@ -439,7 +445,10 @@ class Tape:
         return out + b"\0" * (total - len(out))
 
 
-FIXED_SLOTS = 2      # slot 0 = 0.0, slot 1 = 1.0 (written by the kernel prologue)
+def fixed_slots(order):
+    """Slots the kernel prologue writes: 0 = 0.0, 1 = 1.0, then the hypercube time
+    coordinate of interaction lines 0..N-1 (line 0: 0)."""
+    return 2 + order
 
 
 class SlotAllocator:
@@ -640,7 +649,7 @@ def compile_graph(order, roots, budget=96, bundle=4, window=32):
     # ---- pass 2: slots under the budget ---------------------------------------
     consts = sorted({key[1] for key in dag.nodes if key[0] == "const"} |
                     {key[2] for key in dag.nodes if key[0] == "mulc"})
-    alloc = SlotAllocator(FIXED_SLOTS)
+    alloc = SlotAllocator(fixed_slots(N))
     words = []
     stats = collections.Counter()
     const_slot = {0.0: 0, 1.0: 1}
@@ -753,15 +762,11 @@ def compile_graph(order, roots, budget=96, bundle=4, window=32):
             for it in grp:
                 evict_for(1, pos, protect)
                 dests.append(alloc.alloc(1))
-            if len(grp) == 1:
-                pad_to_fit(1)
-                emit(fma_word(grp[0][1], opslots[0], dests[0]))
-            else:
-                pad_to_fit(len(grp) + 1)
-                emit(OP_BUNDLE | (len(grp) << 6))
-                for it, ks, d in zip(grp, opslots, dests):
-                    emit(fma_word(it[1], ks, d))
-                stats["bundles"] += 1
+            pad_to_fit(len(grp) + 1)
+            emit(OP_BUNDLE | (len(grp) << 6))
+            for it, ks, d in zip(grp, opslots, dests):
+                emit(fma_word(it[1], ks, d))
+            stats["bundles"] += 1
             for it, d in zip(grp, dests):
                 node_slot[it[1]] = d
             stats["arith"] += len(grp)
@@ -833,13 +838,19 @@ def tape_work(data):
     words = struct.unpack("<%dQ" % n_instr, data[ins_off:ins_off + 8 * n_instr])
     flops = 0
     sfu = 0
-    for w in words:
+    k = 0
+    while k < len(words):
+        w = words[k]
         op = w & 63
-        if op == OP_FMA:
-            b = (w >> 34) & 16383
-            c = (w >> 48) & 16383
-            flops += 1 if (c == 0 or b == 1) else 2
-        elif op in (OP_GLEAF, OP_VLEAF):
+        if op == OP_BUNDLE:
+            n = (w >> 6) & 15
+            for q in words[k + 1:k + 1 + n]:
+                b = (q >> 32) & 0xFFFF
+                c = (q >> 48) & 0xFFFF
+                flops += 1 if (c == 0 or b == 1) else 2
+            k += 1 + n
+            continue
+        if op in (OP_GLEAF, OP_VLEAF):
             mask = (w >> 20) & 16383
             terms = sum(1 for j in range(7) if (mask >> (2 * j)) & 3)
             M = (w >> 40) & 7
@@ -853,6 +864,7 @@ def tape_work(data):
                 sfu += 1
         elif op == OP_RACC:
             flops += 4
+        k += 1
     flops += 6 * dim + 14 * order + 3 * (order - 1) + 2 * n_roots
     sfu += 2 * order + (order - 1)
     return flops, sfu

@@ -53,23 +53,45 @@ def test_tape_validation_rejects_malformed_tapes():
         bad[off + 8 * k:off + 8 * k + 8] = struct.pack("<Q", w)
         return bytes(bad)
 
-    k_fma = next(i for i, w in enumerate(words) if w & 63 == fdgraph.OP_FMA)
-    w = words[k_fma]
+    # walk the tape: instruction words vs the u16 FMA words that follow a bundle header
+    heads, fmas = [], []
+    k = 0
+    while k < n_instr:
+        heads.append(k)
+        if words[k] & 63 == fdgraph.OP_BUNDLE:
+            n = (words[k] >> 6) & 15
+            fmas.extend(range(k + 1, k + 1 + n))
+            k += n
+        k += 1
+    k_b = next(i for i in heads if words[i] & 63 == fdgraph.OP_BUNDLE)
+    k_f = k_b + 1
+    w = words[k_f]
     # destination slot beyond the declared slot count
-    assert _load(patched(k_fma, (w & ~(16383 << 6)) | (16000 << 6))) == L.FD_EFORMAT
-    # writing the fixed 0.0 slot
-    assert _load(patched(k_fma, w & ~(16383 << 6))) == L.FD_EFORMAT
+    assert _load(patched(k_f, (w & ~0xFFFF) | 16000)) == L.FD_EFORMAT
+    # writing a fixed slot (0.0 and the line times are read-only)
+    assert _load(patched(k_f, w & ~0xFFFF)) == L.FD_EFORMAT
+    assert _load(patched(k_f, (w & ~0xFFFF) | 2)) == L.FD_EFORMAT
+    # an operand slot beyond the declared slot count
+    assert _load(patched(k_f, (w & ~(0xFFFF << 48)) | (16000 << 48))) == L.FD_EFORMAT
     # unknown opcode
-    assert _load(patched(k_fma, (w & ~63) | 42)) == L.FD_EFORMAT
-    # a leaf whose momentum mask names a variable beyond the order
-    k_leaf = next(i for i, w in enumerate(words) if w & 63 == fdgraph.OP_GLEAF)
-    wl = words[k_leaf] | (1 << (20 + 2 * 5))
-    assert _load(patched(k_leaf, wl)) == L.FD_EFORMAT
+    assert _load(patched(k_b, (words[k_b] & ~63) | 42)) == L.FD_EFORMAT
+    # empty bundle, and a bundle longer than the hardware bundle
+    assert _load(patched(k_b, words[k_b] & ~(15 << 6))) == L.FD_EFORMAT
+    assert _load(patched(k_b, (words[k_b] & ~(15 << 6)) | (9 << 6))) == L.FD_EFORMAT
+    # two results of one bundle in the same slot
+    nb = (words[k_b] >> 6) & 15
+    if nb >= 2:
+        w2 = words[k_f + 1]
+        assert _load(patched(k_f + 1, (w2 & ~0xFFFF) | (w & 0xFFFF))) == L.FD_EFORMAT
+    # a leaf whose momentum mask names a variable beyond the order, or holds the unused code 2
+    k_leaf = next(i for i in heads if words[i] & 63 == fdgraph.OP_GLEAF)
+    assert _load(patched(k_leaf, words[k_leaf] | (1 << (20 + 2 * 5)))) == L.FD_EFORMAT
+    assert _load(patched(k_leaf, (words[k_leaf] & ~(3 << 20)) | (2 << 20))) == L.FD_EFORMAT
     # a root flushed twice (and therefore another one never)
-    k_fl = [i for i, w in enumerate(words) if w & 63 == fdgraph.OP_RFLUSH]
+    k_fl = [i for i in heads if words[i] & 63 == fdgraph.OP_RFLUSH]
     assert _load(patched(k_fl[1], words[k_fl[0]])) == L.FD_EFORMAT
     # missing END
-    assert _load(patched(n_instr - 1, words[k_fma])) == L.FD_EFORMAT
+    assert _load(patched(n_instr - 1, words[k_leaf])) == L.FD_EFORMAT
     assert len(L.lib().fd_last_error()) > 0
 
 

@@ -2,10 +2,12 @@
 
 Order-5 self-energy Sigma^(5) at r_s = 1, k = k_F (single-root graph, the
 quantity both samplers adapt to): VEGAS is adapted for 12 iterations, then the
-affine coupling flow is trained by forward KL on |f| from batches the method
-generates (VEGAS first, then the flow itself).  Over 4 independent batches of
-2^23 samples the flow must reach a higher variance-adjusted rate of effective
-samples than VEGAS, and both estimates must agree.
+affine coupling flow, living on the input coordinates of the adapted grid and
+starting as the identity (that is, as VEGAS), is trained by forward KL on
+|f| J_map from batches the method generates (VEGAS first, then the flow
+itself).  Over 4 independent batches of 2^23 samples the flow must reach a
+higher variance-adjusted rate of effective samples than VEGAS, and both
+estimates must agree.
 """
 import pytest
 
@@ -26,7 +28,8 @@ def test_flow_beats_vegas_at_order5():
                                evals_per_batch=2)
     cmp = driver.compare(G, p, V, F, 1 << 23, seed=13, batches=4)
     print({k: cmp[k] for k in ("flow_over_vegas", "means_agree_sigma")}, cmp["vegas"]["var_batches"],
-          cmp["flow"]["var_batches"])
-    assert losses[-1] < losses[0] - 1.0
+          cmp["flow"]["var_batches"], losses[0], losses[-1])
+    assert abs(losses[0]) < 1e-3              # identity flow: log q = 0 on the grid's coordinates
+    assert losses[-1] < losses[0] - 0.1
     assert cmp["flow_over_vegas"] > 1.1
     assert cmp["means_agree_sigma"] < 4.0

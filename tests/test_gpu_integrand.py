@@ -196,6 +196,29 @@ def test_points_mode(api):
     _compare(f[:len(G.roots)], ref, mag, "points")
 
 
+def test_points_on_vegas_map(api):
+    # points are coordinates of the map's input space: map and Jacobian apply
+    order, n, nb = 2, 2000, 1024
+    G = api.Graph(order, with_dk=True)
+    e = _fp32_edges(21, G.dim, nb)
+    m = api.Vegas(G.dim, nb)
+    m.set_edges(e)
+    y = workloads.uniform_points(22, G.dim, n)
+    w = workloads.positive_weights(23, n)
+    pts = torch.tensor(y, dtype=torch.float32, device="cuda").contiguous()
+    pw = torch.tensor(w, dtype=torch.float32, device="cuda")
+    plan = api.EvalPlan([G], [_gparams(api, order)], [0], n, maps=[m], per_sample=True)
+    plan.run(0, 0, points=pts, point_w=pw)
+    torch.cuda.synchronize()
+    x, jv, _ = ovegas.vegas_map(e, y.astype(np.float32).astype(np.float64))
+    ref, mag = oig.eval_roots(x, G.roots, _oparams(order), with_l1=True)
+    ref = ref * (w * jv)[None, :]
+    mag = mag * (w * jv)[None, :]
+    f = plan.per_sample[0].cpu().numpy().astype(np.float64)
+    _compare(f[:len(G.roots)], ref, mag, "points on a map")
+    assert np.all(m.hist() == 0.0)          # given points do not adapt the grid
+
+
 def test_vegas_histogram_parity(api):
     order, n, nb = 2, 20000, 64
     G = api.Graph(order)
