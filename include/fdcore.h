@@ -87,6 +87,35 @@ void fd_graph_free(fd_graph *g);
  * A preference that does not fit in shared memory falls back to automatic. */
 fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_thread);
 
+/* ---- specialised kernels (Sec. VI.A: graphs compiled once, evaluated in batches)
+ * fd_graph_jit translates the graph's validated tape into straight-line CUDA
+ * (one function per root-accumulate slice, intermediates in registers),
+ * compiles it for the current device with NVRTC (modules compiled in
+ * parallel and linked with nvJitLink when max_modules > 1 and the graph is
+ * large) and from then on evaluates the graph's instances with it (one launch
+ * per graph; graphs without one keep the interpreter).  threads in
+ * {64, 128, 256}, min_blocks in 1..8 (launch bounds; registers are capped at
+ * 65536 / (threads * min_blocks)).  root_units != 0: a split graph compiles
+ * one function per root (the root's slices share their leaves) instead of
+ * one function per slice.  cache_dir (may be NULL): directory for
+ * compiled images, keyed by a hash of the generated source and options.
+ * Synchronous; FD_ENOTSUP when the run-time compiler is unavailable or fails
+ * (fd_last_error holds its log).  Results agree with the interpreter up to
+ * FP32 rounding order. */
+fd_status fd_graph_jit(fd_graph *g, int32_t threads, int32_t min_blocks, int32_t max_modules,
+                       int32_t root_units, const char *cache_dir);
+/* Switch evaluation of g between its specialised kernel (on != 0) and the interpreter. */
+fd_status fd_graph_jit_enable(fd_graph *g, int32_t on);
+/* info[6] = threads, min_blocks, registers per thread, local bytes per thread,
+ * modules, enabled; compile_s (may be NULL) = seconds of the last fd_graph_jit. */
+fd_status fd_graph_jit_info(const fd_graph *g, int32_t *info, double *compile_s);
+/* The generated source of module `module` for a serialised tape (no device
+ * needed): copies at most cap - 1 bytes plus a terminating 0 into buf (may be
+ * NULL), *len = full length, *n_modules = module count. */
+fd_status fd_jit_emit(const void *tape, size_t tape_len, int32_t threads, int32_t min_blocks,
+                      int32_t max_modules, int32_t root_units, int32_t module, char *buf, int64_t cap,
+                      int64_t *len, int32_t *n_modules);
+
 /* ---- VEGAS map (Sec. IV, separable map q(x) = prod q_k(x_k)) ---------------
  * A map owns FP64 bin edges [dim][n_bins+1] (uniform at creation), their FP32
  * copy used by the sampling kernels, and an FP64 training histogram

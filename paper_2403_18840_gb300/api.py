@@ -15,6 +15,7 @@ from . import _lib as L
 from . import fdgraph
 
 _TAPE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tapes")
+_JIT_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "jit")
 
 
 def _stream_ptr(stream):
@@ -65,6 +66,19 @@ def tape_bytes(order, roots, budget=None, bundle=None, window=None):
     return data
 
 
+def jit_source(tape, threads=128, min_blocks=2, max_modules=1, module=0, root_units=True):
+    """Generated source of one module of the specialised kernel (no device needed)."""
+    n = ctypes.c_int64()
+    nm = ctypes.c_int32()
+    ru = 1 if root_units else 0
+    L.check(L.lib().fd_jit_emit(tape, len(tape), threads, min_blocks, max_modules, ru, module, None, 0,
+                                ctypes.byref(n), ctypes.byref(nm)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    L.check(L.lib().fd_jit_emit(tape, len(tape), threads, min_blocks, max_modules, ru, module, buf, n.value + 1,
+                                ctypes.byref(n), ctypes.byref(nm)))
+    return buf.value.decode(), nm.value
+
+
 class Graph:
     """A compiled self-energy graph loaded on the current device."""
 
@@ -84,6 +98,28 @@ class Graph:
 
     def set_launch(self, threads=0, samples_per_thread=0):
         L.check(L.lib().fd_graph_set_launch(self.handle, threads, samples_per_thread))
+
+    def jit(self, threads=128, min_blocks=2, max_modules=None, root_units=True, cache=True):
+        """Compile the specialised straight-line kernel (cached under _build/jit)
+        and evaluate this graph with it from now on."""
+        if max_modules is None:
+            max_modules = max(1, min(32, os.cpu_count() or 1))
+        cdir = _JIT_DIR if cache else None
+        if cdir:
+            os.makedirs(cdir, exist_ok=True)
+        L.check(L.lib().fd_graph_jit(self.handle, threads, min_blocks, max_modules, 1 if root_units else 0,
+                                     cdir.encode() if cdir else None))
+        return self.jit_info()
+
+    def jit_enable(self, on=True):
+        L.check(L.lib().fd_graph_jit_enable(self.handle, 1 if on else 0))
+
+    def jit_info(self):
+        info = (ctypes.c_int32 * 6)()
+        secs = ctypes.c_double()
+        L.check(L.lib().fd_graph_jit_info(self.handle, info, ctypes.byref(secs)))
+        return dict(threads=info[0], min_blocks=info[1], regs=info[2], local_bytes=info[3], modules=info[4],
+                    enabled=bool(info[5]), compile_s=secs.value)
 
     def __del__(self):
         h = getattr(self, "handle", None)

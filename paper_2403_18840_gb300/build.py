@@ -4,6 +4,7 @@ Translation units are compiled in parallel and linked into
 ``paper_2403_18840_gb300/_build/libfdcore.so`` (in-tree, git-ignored).
 """
 import os
+import shutil
 import subprocess
 import sys
 
@@ -11,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfdcore.so")
-SOURCES = ["fd_api.cu", "fd_integrand.cu", "fd_flow.cu"]
+SOURCES = ["fd_api.cu", "fd_integrand.cu", "fd_flow.cu", "fd_jit.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -27,11 +28,32 @@ def _needs_rebuild():
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 
+def _cuda_libdir():
+    nvcc = shutil.which(NVCC)
+    if not nvcc:
+        return ""
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+
+
+def _embed_runtime_header():
+    """The specialised kernels include fd_jit_rt.cuh; the library hands its text
+    to the run-time compiler, so it is embedded as a raw string literal."""
+    text = open(os.path.join(CSRC, "fd_jit_rt.cuh")).read()
+    assert ")FDRT" not in text
+    out = os.path.join(BUILD, "fd_jit_rt.inc")
+    body = 'R"FDRT(' + text + ')FDRT"\n'
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
+
+
 def build(force=False, verbose=False, extra_flags=()):
     """Compile (when sources changed) and return the library path."""
     if not force and not _needs_rebuild():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    _embed_runtime_header()
+    extra_flags = list(extra_flags) + ["-I", BUILD, '-DFD_CUDA_LIBDIR="%s"' % _cuda_libdir()]
     objs, procs = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)

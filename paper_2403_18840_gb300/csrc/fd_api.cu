@@ -59,7 +59,7 @@ extern "C" fd_status fd_device_status(void *stream) {
 }
 
 // ---- graphs ------------------------------------------------------------------------
-static fd_status validate_tape(const uint8_t *buf, size_t len, TapeHeader &h) {
+fd_status validate_tape(const uint8_t *buf, size_t len, TapeHeader &h) {
     if (len < sizeof(TapeHeader)) return fd::set_error(FD_EFORMAT, "tape shorter than its header");
     memcpy(&h, buf, sizeof(TapeHeader));
     if (h.magic != TAPE_MAGIC) return fd::set_error(FD_EFORMAT, "bad tape magic");
@@ -146,29 +146,41 @@ static fd_status validate_tape(const uint8_t *buf, size_t len, TapeHeader &h) {
     return FD_OK;
 }
 
-extern "C" fd_status fd_graph_load(const void *buf, size_t len, fd_graph **out) {
-    FD_REQUIRE(buf && out, "buf and out are required");
-    *out = nullptr;
+// Host part of a graph: validated header, instruction words and root table.
+fd_status graph_from_tape(const void *buf, size_t len, fd_graph &g) {
     TapeHeader h;
-    fd_status st = validate_tape((const uint8_t *)buf, len, h);
+    const fd_status st = validate_tape((const uint8_t *)buf, len, h);
     if (st != FD_OK) return st;
-    fd_graph *g = new fd_graph();
-    g->hdr = h;
-    FD_CHECK_CUDA(cudaGetDevice(&g->device));
-    const size_t ibytes = ((size_t)h.n_instr * 8 + 15) & ~(size_t)15;
-    cudaError_t e = cudaMalloc(&g->d_tape, ibytes + 16);
-    if (e != cudaSuccess) { delete g; return fd::cuda_error(e, "cudaMalloc(tape)"); }
-    e = cudaMemset(g->d_tape, 0, ibytes + 16);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(g->d_tape, (const uint8_t *)buf + h.instr_off, (size_t)h.n_instr * 8, cudaMemcpyHostToDevice);
+    g.hdr = h;
+    g.h_tape.resize(h.n_instr);
+    memcpy(g.h_tape.data(), (const uint8_t *)buf + h.instr_off, (size_t)h.n_instr * 8);
     for (uint32_t r = 0; r < h.n_roots; ++r) {
         const uint8_t *p = (const uint8_t *)buf + h.root_off + 8 * r;
         uint16_t re, im;
         memcpy(&re, p + 4, 2);
         memcpy(&im, p + 6, 2);
-        g->h_roots[2 * r] = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-        g->h_roots[2 * r + 1] = (uint32_t)re | ((uint32_t)im << 16);
+        g.h_roots[2 * r] = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+        g.h_roots[2 * r + 1] = (uint32_t)re | ((uint32_t)im << 16);
     }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_graph_load(const void *buf, size_t len, fd_graph **out) {
+    FD_REQUIRE(buf && out, "buf and out are required");
+    *out = nullptr;
+    fd_graph *g = new fd_graph();
+    const fd_status st = graph_from_tape(buf, len, *g);
+    if (st != FD_OK) {
+        delete g;
+        return st;
+    }
+    const TapeHeader &h = g->hdr;
+    cudaError_t e = cudaGetDevice(&g->device);
+    const size_t ibytes = ((size_t)h.n_instr * 8 + 15) & ~(size_t)15;
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_tape, ibytes + 16);
+    if (e == cudaSuccess) e = cudaMemset(g->d_tape, 0, ibytes + 16);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d_tape, g->h_tape.data(), (size_t)h.n_instr * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_roots, 8 * h.n_roots);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_roots, g->h_roots, 8 * h.n_roots, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -205,6 +217,7 @@ extern "C" fd_status fd_graph_roots(const fd_graph *g, int32_t *roots) {
 
 extern "C" void fd_graph_free(fd_graph *g) {
     if (!g) return;
+    if (g->jit_lib) cudaLibraryUnload(g->jit_lib);
     cudaFree(g->d_tape);
     cudaFree(g->d_roots);
     delete g;

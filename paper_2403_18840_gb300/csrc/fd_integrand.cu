@@ -38,34 +38,7 @@ namespace {
 constexpr int CHUNK_INSTR = FD_CHUNK_WORDS;           // 8 KB per tape buffer
 constexpr int CHUNK_BYTES = CHUNK_INSTR * 8;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;             // polls before a tape wait gives up
-constexpr float K_INV_2PI2 = 0.050660591821168885f;    // 1 / (2 pi^2)
-constexpr float K_8PI = 25.132741228718345f;
 constexpr int NK = FD_MAX_ORDER;                      // loop momenta / interaction lines held in registers
-
-struct InstDesc {
-    const uint64_t *tape;      // instruction words (device)
-    const uint32_t *roots;     // root table (device): n | m<<8 | l<<16 | dk<<24, 0
-    const float *edges;        // VEGAS FP32 edges [dim][nb+1] or null
-    double *hist;              // VEGAS histogram [dim][nb] or null
-    const float *points;       // explicit points [dim_max][n] or null
-    const float *point_w;      // explicit weights [n] or null
-    int32_t n_instr, n_slots, order, dim, n_roots, n_bins;
-    float kext, mu, beta, Lambda, kc;
-    float pad;
-};
-
-struct EvalArgs {
-    int32_t n_inst, tiles_per_inst, r_max, slots_total, dim_max;
-    int64_t n_per_inst, tile;
-    uint32_t seed_lo, seed_hi, iter;
-    const uint32_t *iter_dev;          // optional: iteration += *iter_dev (read on the device)
-    unsigned long long *queue;         // work counter (reset to 0 before the launch)
-    double *partials;
-    float *per_sample_f;
-    int *status;
-    uint8_t perm[FD_MAX_INST];         // instances in decreasing cost: work items go heaviest first
-    InstDesc inst[FD_MAX_INST];
-};
 
 struct SmemLayout {
     int tape0, tape1, bars, acc, slots, total;   // byte offsets in dynamic shared memory
@@ -82,16 +55,6 @@ __host__ __device__ inline SmemLayout smem_layout(int threads, int P, int slots_
     L.slots = (L.slots + 15) & ~15;
     L.total = L.slots + slots_total * threads * P * 4;
     return L;
-}
-
-// Neumaier compensated addition: (s, c) += v
-__device__ __forceinline__ void neumaier(double &s, double &c, double v) {
-    const double t = s + v;
-    if (fabs(s) >= fabs(v))
-        c += (s - t) + v;
-    else
-        c += (v - t) + s;
-    s = t;
 }
 
 // per-sample slots in shared memory: [slot][thread][P] FP32
@@ -163,12 +126,8 @@ __device__ __forceinline__ void momentum(const Vars<P> &V, uint32_t mask, float 
     }
 }
 
-// G0 Taylor family: c_j = (d/dmu)^j G0 / j!, j <= M (+ d/dk copies).  Written as
-// sign * exp(-eps tau*) * phi(eps - dmu) with the Fermi factor phi >= 1/2
-// (phi = 1 - f for eps >= 0, f for eps < 0) and tau* the matching
-// antiperiodic time, so the exponent is never positive.  The series of
-// phi(eps - d) follows from the logistic ODE d phi / d eps = +-beta phi (1 - phi)
-// (a Taylor-mode recurrence); the series of exp(d tau*) is tau*^k / k!.
+// G0 and V Taylor families of one leaf instruction (g_family / v_family),
+// written to the slots d, d + 1, ...
 template <int T, int P>
 __device__ __forceinline__ void g_leaf(const Slots<T, P> &S, const Vars<P> &V, uint64_t w, const InstDesc &D) {
     const uint32_t d = f_d(w), mask = f_a(w);
@@ -177,65 +136,17 @@ __device__ __forceinline__ void g_leaf(const Slots<T, P> &S, const Vars<P> &V, u
     const int dk = (int)((w >> 43) & 1u);
     float px[P], py[P], pz[P], ks;
     momentum(V, mask, D.kext, px, py, pz, ks);
-    const float beta = D.beta;
     float ta[P], tb[P];
     S.load(2 + la, ta);                        // hypercube time of the two lines
     S.load(2 + lb, tb);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const float eps = fmaf(px[p], px[p], fmaf(py[p], py[p], pz[p] * pz[p])) - D.mu;
-        const float E = __expf(-beta * fabsf(eps));
-        const float phi = __frcp_rn(1.0f + E);
-        const float psi = E * phi;
-        const float dx = ta[p] - tb[p];
-        const bool pos = dx > 0.0f;
-        const float tau = beta * dx;
-        const bool occ = eps < 0.0f;
-        const float tstar = occ ? (pos ? tau - beta : tau) : (pos ? tau : tau + beta);
-        const float X = (pos ? -1.0f : 1.0f) * __expf(-eps * tstar) * phi;
-        if (M == 0 && !dk) {
-            S.store1(d, p, X);
-            continue;
-        }
-        const int Mx = M + dk;
-        float ph[FD_MAX_M + 1], ps[FD_MAX_M + 1], A[FD_MAX_M + 1], cf[FD_MAX_M + 1];
-        const float g = occ ? beta : -beta;
-        ph[0] = 1.0f;
-        ps[0] = psi;
-        A[0] = 1.0f;
-#pragma unroll
-        for (int k = 0; k < FD_MAX_M; ++k) {
-            if (k < Mx) {
-                float s = 0.0f;
-#pragma unroll
-                for (int i = 0; i <= k; ++i) s = fmaf(ph[i], ps[k - i], s);
-                ph[k + 1] = g * s / (float)(k + 1);
-                ps[k + 1] = -phi * ph[k + 1];
-                A[k + 1] = A[k] * tstar / (float)(k + 1);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j <= FD_MAX_M; ++j) {
-            if (j <= Mx) {
-                float s = 0.0f;
-#pragma unroll
-                for (int i = 0; i <= j; ++i) s = fmaf(A[j - i], ph[i], s);
-                cf[j] = X * s;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j <= FD_MAX_M; ++j)
-            if (j <= M) S.store1(d + j, p, cf[j]);
-        if (dk) {
-            const float kz = -2.0f * ks * pz[p];
-#pragma unroll
-            for (int j = 0; j < FD_MAX_M; ++j)
-                if (j <= M) S.store1(d + M + 1 + j, p, kz * (float)(j + 1) * cf[j + 1]);
-        }
+        const float p2 = fmaf(px[p], px[p], fmaf(py[p], py[p], pz[p] * pz[p]));
+        g_family(p2, pz[p], ks, ta[p] - tb[p], D.beta, D.mu, M, dk,
+                 [&](int j, float v) { S.store1(d + j, p, v); });
     }
 }
 
-// V Taylor family: c_l = (d/dLambda)^l V / l! = 8 pi (-1)^l w^(l+1), w = 1/(q^2+Lambda)
 template <int T, int P>
 __device__ __forceinline__ void v_leaf(const Slots<T, P> &S, const Vars<P> &V, uint64_t w, const InstDesc &D) {
     const uint32_t d = f_d(w), mask = f_a(w);
@@ -246,25 +157,7 @@ __device__ __forceinline__ void v_leaf(const Slots<T, P> &S, const Vars<P> &V, u
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const float q2 = fmaf(px[p], px[p], fmaf(py[p], py[p], pz[p] * pz[p]));
-        const float inv = __frcp_rn(q2 + D.Lambda);
-        float cl = K_8PI * inv;
-        float cf[FD_MAX_M + 1];
-#pragma unroll
-        for (int l = 0; l <= FD_MAX_M; ++l) {
-            if (l <= L + dk) {
-                cf[l] = cl;
-                cl = -inv * cl;
-            }
-        }
-#pragma unroll
-        for (int l = 0; l <= FD_MAX_M; ++l)
-            if (l <= L) S.store1(d + l, p, cf[l]);
-        if (dk) {
-            const float kz = 2.0f * ks * pz[p];
-#pragma unroll
-            for (int l = 0; l < FD_MAX_M; ++l)
-                if (l <= L) S.store1(d + L + 1 + l, p, kz * (float)(l + 1) * cf[l + 1]);
-        }
+        v_family(q2, pz[p], ks, D.Lambda, L, dk, [&](int j, float v) { S.store1(d + j, p, v); });
     }
 }
 
@@ -288,7 +181,7 @@ __device__ __forceinline__ void flush_root(const Slots<T, P> &S, Vars<P> &V, uin
         V.im[p] = 0.0f;
         if (!dkr) V.hsum[p] += fabsf(fre) + fabsf(fim);
         if (A.per_sample_f && valid[p]) {
-            const int64_t o = (((int64_t)inst * A.r_max + r) * 2) * A.n_per_inst + idx[p];
+            const int64_t o = (((int64_t)D.id * A.r_max + r) * 2) * A.n_per_inst + idx[p];
             A.per_sample_f[o] = fre;
             A.per_sample_f[o + A.n_per_inst] = fim;
         }
@@ -414,7 +307,7 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
             for (int blk = 0; blk < (FD_MAX_DIM + 3) / 4; ++blk) {
                 if (4 * blk < dim) {
                     const u32x4 r = philox4x32_10(
-                        u32x4{c0, c1, iter, ((uint32_t)inst << 8) | (uint32_t)blk}, A.seed_lo, A.seed_hi);
+                        u32x4{c0, c1, iter, ((uint32_t)D.id << 8) | (uint32_t)blk}, A.seed_lo, A.seed_hi);
                     const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -455,7 +348,7 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
                 V.kx[j][p] = r * sth * cp;
                 V.ky[j][p] = r * sth * sp;
                 V.kz[j][p] = r * cth;
-                jac *= D.kc * r * r * K_INV_2PI2;
+                jac *= D.kc * r * r * FD_INV_2PI2;
                 jac *= jd[c0] * jd[c0 + 1] * jd[c0 + 2];   // 1 without a map
                 if (jj >= 2) {
                     // time of interaction line jj - 1
@@ -586,11 +479,11 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
                     neumaier(s, c, wa[k * 2 + 1]);
                 }
                 const int r = k / 4, q = k % 4;   // q: 0 re sum, 1 re sumsq, 2 im sum, 3 im sumsq
-                const int64_t o = (((int64_t)inst * A.tiles_per_inst + tile) * A.r_max + r) * 4;
+                const int64_t o = (((int64_t)D.id * A.tiles_per_inst + tile) * A.r_max + r) * 4;
                 A.partials[o + q] = s + c;
             }
             for (int k = D.n_roots * 4 + tid; k < A.r_max * 4; k += T) {
-                const int64_t o = ((int64_t)inst * A.tiles_per_inst + tile) * A.r_max * 4;
+                const int64_t o = ((int64_t)D.id * A.tiles_per_inst + tile) * A.r_max * 4;
                 A.partials[o + k] = 0.0;
             }
         }
@@ -652,6 +545,11 @@ extern "C" int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_pe
 }
 
 namespace {
+int dev_of_call() {
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+}
+
 // Shared body of the evaluation entry points: validate, build the launch
 // descriptors and launch the integrand kernel.  `status` is the device word a
 // kernel sets when a bounded wait gives up (may be null).
@@ -713,6 +611,7 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
         D.beta = (float)p.beta;
         D.Lambda = (float)p.Lambda;
         D.kc = (float)p.k_cut;
+        D.id = j;
         D.edges = nullptr;
         D.hist = nullptr;
         D.n_bins = 1;
@@ -730,16 +629,51 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
             D.n_bins = maps[j]->n_bins;
         }
     }
-    const int items = n_inst * args.tiles_per_inst;
+    args.queue = reinterpret_cast<unsigned long long *>(
+        partials + fd_partials_count(n_inst, r_max, n_per_inst) - 1);
+    // instances whose graph has a specialised kernel run as one launch per
+    // graph (stream-ordered, so they can share the work counter); the rest go
+    // through the interpreter in one launch
+    bool any_jit = false;
+    for (int g = 0; g < n_graphs; ++g) any_jit = any_jit || (graphs[g]->jit_enabled && graphs[g]->jit_kernel);
+    if (any_jit) {
+        static EvalArgs sub;
+        std::vector<int> rest;
+        for (int g = 0; g < n_graphs; ++g) {
+            std::vector<int> members;
+            for (int j = 0; j < n_inst; ++j)
+                if (graph_of_inst[j] == g) members.push_back(j);
+            if (members.empty()) continue;
+            const fd_graph *G = graphs[g];
+            if (!(G->jit_enabled && G->jit_kernel)) {
+                rest.insert(rest.end(), members.begin(), members.end());
+                continue;
+            }
+            FD_REQUIRE(G->device == dev_of_call(), "graph belongs to another device");
+            sub = args;
+            sub.n_inst = (int32_t)members.size();
+            for (size_t k = 0; k < members.size(); ++k) {
+                sub.inst[k] = args.inst[members[k]];
+                sub.perm[k] = (uint8_t)k;
+            }
+            FD_CHECK_CUDA(cudaMemsetAsync(sub.queue, 0, sizeof(unsigned long long), stream));
+            const fd_status st = jit_launch(G, sub, stream);
+            if (st != FD_OK) return st;
+        }
+        if (rest.empty()) return FD_OK;
+        sub = args;
+        sub.n_inst = (int32_t)rest.size();
+        for (size_t k = 0; k < rest.size(); ++k) sub.inst[k] = args.inst[rest[k]];
+        args = sub;
+    }
+    const int items = args.n_inst * args.tiles_per_inst;
     // instances in decreasing graph order (cost): longest-processing-time first
     {
         int k = 0;
         for (int o = FD_MAX_ORDER; o >= 1; --o)
-            for (int j = 0; j < n_inst; ++j)
+            for (int j = 0; j < args.n_inst; ++j)
                 if (args.inst[j].order == o) args.perm[k++] = (uint8_t)j;
     }
-    args.queue = reinterpret_cast<unsigned long long *>(
-        partials + fd_partials_count(n_inst, r_max, n_per_inst) - 1);
     FD_CHECK_CUDA(cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), stream));
     int dev = 0, max_smem = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));

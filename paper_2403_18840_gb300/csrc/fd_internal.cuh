@@ -6,6 +6,8 @@
 #include <string>
 
 #include "../../include/fdcore.h"
+#include "fd_jit_rt.cuh"
+#include <vector>
 
 // ---- error plumbing ---------------------------------------------------------
 namespace fd {
@@ -44,10 +46,6 @@ enum : uint32_t {
 
 constexpr uint32_t TAPE_MAGIC = 0x50544446u;  // 'FDTP'
 constexpr uint32_t TAPE_VERSION = 3;
-constexpr int FD_MAX_ORDER = 6;
-constexpr int FD_MAX_DIM = 4 * FD_MAX_ORDER - 1;
-constexpr int FD_MAX_M = 7;         // largest Taylor order of a leaf family (incl. d/dk)
-constexpr int FD_MAX_INST = 256;    // instances per launch (kernel-parameter descriptors)
 constexpr int FD_CHUNK_WORDS = 1024;  // tape chunk staged in shared memory; bundles never straddle one
 constexpr int FD_MAX_BUNDLE = 8;
 
@@ -64,7 +62,21 @@ struct fd_graph {
     uint64_t *d_tape;            // device copy of the instruction words (16-byte aligned)
     uint32_t *d_roots;           // device root table: (n | m<<8 | l<<16 | dk<<24, re | im<<16)
     uint32_t h_roots[2 * 256];
+    std::vector<uint64_t> h_tape;   // host copy of the validated instruction words
+    // specialised straight-line kernel (fd_graph_jit), null until compiled
+    cudaLibrary_t jit_lib = nullptr;
+    cudaKernel_t jit_kernel = nullptr;
+    int jit_threads = 0, jit_min_blocks = 0, jit_regs = 0, jit_local_bytes = 0, jit_modules = 0, jit_per_sm = 1;
+    double jit_compile_s = 0.0;
+    bool jit_enabled = false;       // evaluation uses the specialised kernel
 };
+
+// validated host part of a graph (fd_api.cu)
+fd_status graph_from_tape(const void *buf, size_t len, fd_graph &g);
+
+// launches the specialised kernel of graph g for the instances in `args`
+// (fd_jit.cu); the caller has reset the work counter
+fd_status jit_launch(const fd_graph *g, const EvalArgs &args, cudaStream_t stream);
 
 struct fd_vegas {
     int device;
@@ -73,30 +85,6 @@ struct fd_vegas {
     float *d_edges32;  // [dim][n_bins+1]
     double *d_hist;    // [dim][n_bins]
 };
-
-// ---- Philox4x32-10 (Salmon et al., SC'11) ----------------------------------------
-struct u32x4 {
-    uint32_t x, y, z, w;
-};
-
-__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// u = ((w >> 9) + 0.5) * 2^-23, exact in FP32, strictly inside (0, 1)
-__device__ __forceinline__ float word_to_uniform(uint32_t w) {
-    return __uint2float_rn(w >> 9) * 1.1920928955078125e-07f + 5.9604644775390625e-08f;
-}
 
 // ---- bounded mbarrier / bulk-copy helpers (inline PTX) ----------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {

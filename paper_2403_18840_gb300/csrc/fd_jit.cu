@@ -1,0 +1,665 @@
+// Specialised integrand kernels: the validated instruction tape of a graph is
+// translated into straight-line CUDA and compiled at run time for the device
+// (NVRTC, then nvJitLink when the code is split into several modules).
+//
+// Why: the tape interpreter keeps every intermediate value of a sample in
+// shared memory, so each FMA costs three shared loads and one store and the
+// interpreter is bound by shared-memory bandwidth far below the FP32 pipe.
+// In straight-line code the intermediates live in registers and the FP32 and
+// SFU pipes become the bound.  The paper compiles its graphs to code for the
+// same reason (Sec. VI.A: the graphs are compiled once and evaluated in
+// batches); here the compilation starts from the same tape the interpreter
+// runs, so both paths evaluate the same contraction.
+//
+// Translation.  The contraction of a root is a sum over root-accumulate
+// instructions (RACC: value x exp(i pi x_line)); the backward slice of each
+// RACC through the tape's slot definitions is one straight-line device
+// function (its leaves included).  Slices are written in SSA form (every
+// definition a new name, bundles read their operands before writing).  Small
+// graphs go into one module with the slices inlined (the compiler then shares
+// leaves between slices); large graphs are split into modules of similar size
+// that compile in parallel, with the slices as separate functions linked into
+// the kernel module.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <unistd.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fd_internal.cuh"
+
+namespace {
+
+const char kRuntimeHeader[] =
+#include "fd_jit_rt.inc"
+    ;
+
+constexpr int kJitVersion = 1;              // bump when the generated code changes meaning
+constexpr double kSingleModuleCost = 3500;  // below this the graph compiles as one module
+
+// ---- run-time compiler entry points (resolved with dlopen on first use) ---------
+typedef int (*nvrtcCreateProgram_t)(void **, const char *, const char *, int, const char *const *,
+                                    const char *const *);
+typedef int (*nvrtcCompileProgram_t)(void *, int, const char *const *);
+typedef int (*nvrtcGetSize_t)(void *, size_t *);
+typedef int (*nvrtcGetData_t)(void *, char *);
+typedef int (*nvrtcDestroyProgram_t)(void **);
+typedef int (*njlCreate_t)(void **, uint32_t, const char **);
+typedef int (*njlDestroy_t)(void **);
+typedef int (*njlAddData_t)(void *, int, const void *, size_t, const char *);
+typedef int (*njlComplete_t)(void *);
+typedef int (*njlGetSize_t)(void *, size_t *);
+typedef int (*njlGetData_t)(void *, void *);
+typedef int (*njlGetLog_t)(void *, char *);
+
+struct Rtc {
+    bool ok = false;
+    std::string why;
+    nvrtcCreateProgram_t create;
+    nvrtcCompileProgram_t compile;
+    nvrtcGetSize_t log_size, cubin_size;
+    nvrtcGetData_t log, cubin;
+    nvrtcDestroyProgram_t destroy;
+    njlCreate_t l_create;
+    njlDestroy_t l_destroy;
+    njlAddData_t l_add;
+    njlComplete_t l_complete;
+    njlGetSize_t l_cubin_size, l_log_size;
+    njlGetData_t l_cubin;
+    njlGetLog_t l_log;
+};
+
+#ifndef FD_CUDA_LIBDIR
+#define FD_CUDA_LIBDIR ""
+#endif
+
+void *open_lib(const char *name) {
+    void *h = dlopen(name, RTLD_NOW | RTLD_LOCAL);
+    if (!h && FD_CUDA_LIBDIR[0]) {
+        const std::string p = std::string(FD_CUDA_LIBDIR) + "/" + name;
+        h = dlopen(p.c_str(), RTLD_NOW | RTLD_LOCAL);
+    }
+    return h;
+}
+
+const Rtc &rtc() {
+    static Rtc R;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *a = open_lib("libnvrtc.so.13");
+        void *b = open_lib("libnvJitLink.so.13");
+        if (!a || !b) {
+            R.why = "libnvrtc.so.13 / libnvJitLink.so.13 not found";
+            return;
+        }
+        bool ok = true;
+        auto sym = [&](void *h, const char *n) {
+            void *p = dlsym(h, n);
+            if (!p) ok = false;
+            return p;
+        };
+        R.create = (nvrtcCreateProgram_t)sym(a, "nvrtcCreateProgram");
+        R.compile = (nvrtcCompileProgram_t)sym(a, "nvrtcCompileProgram");
+        R.log_size = (nvrtcGetSize_t)sym(a, "nvrtcGetProgramLogSize");
+        R.log = (nvrtcGetData_t)sym(a, "nvrtcGetProgramLog");
+        R.cubin_size = (nvrtcGetSize_t)sym(a, "nvrtcGetCUBINSize");
+        R.cubin = (nvrtcGetData_t)sym(a, "nvrtcGetCUBIN");
+        R.destroy = (nvrtcDestroyProgram_t)sym(a, "nvrtcDestroyProgram");
+        R.l_create = (njlCreate_t)sym(b, "__nvJitLinkCreate_13_0");
+        R.l_destroy = (njlDestroy_t)sym(b, "__nvJitLinkDestroy_13_0");
+        R.l_add = (njlAddData_t)sym(b, "__nvJitLinkAddData_13_0");
+        R.l_complete = (njlComplete_t)sym(b, "__nvJitLinkComplete_13_0");
+        R.l_cubin_size = (njlGetSize_t)sym(b, "__nvJitLinkGetLinkedCubinSize_13_0");
+        R.l_cubin = (njlGetData_t)sym(b, "__nvJitLinkGetLinkedCubin_13_0");
+        R.l_log_size = (njlGetSize_t)sym(b, "__nvJitLinkGetErrorLogSize_13_0");
+        R.l_log = (njlGetLog_t)sym(b, "__nvJitLinkGetErrorLog_13_0");
+        R.ok = ok;
+        if (!ok) R.why = "run-time compiler symbols missing";
+    });
+    return R;
+}
+
+// ---- tape decoding and slicing ---------------------------------------------------
+struct TIns {
+    uint32_t op;
+    uint32_t w;      // index of the instruction word
+    uint32_t n;      // bundle: member count (members at w + 1 .. w + n)
+};
+
+struct Slice {
+    uint32_t racc;                                // index into the instruction list
+    int root, line;
+    std::vector<std::pair<uint32_t, uint32_t>> keep;   // (instruction, kept bundle members bitmask)
+    int n_fma = 0, n_leaf = 0;
+    double cost() const { return n_fma + 30.0 * n_leaf; }
+};
+
+inline uint32_t fa(uint64_t w) { return (uint32_t)(w >> 20) & 16383u; }
+inline uint32_t fd_(uint64_t w) { return (uint32_t)(w >> 6) & 16383u; }
+
+int leaf_outputs(uint64_t w) {
+    const int M = (int)((w >> 40) & 7u), dk = (int)((w >> 43) & 1u);
+    return (M + 1) * (1 + dk);
+}
+
+std::vector<TIns> decode(const std::vector<uint64_t> &words) {
+    std::vector<TIns> out;
+    for (uint32_t k = 0; k < words.size(); ++k) {
+        const uint64_t w = words[k];
+        const uint32_t op = (uint32_t)(w & 63u);
+        if (op == OP_BUNDLE) {
+            const uint32_t n = (uint32_t)(w >> 6) & 15u;
+            out.push_back({op, k, n});
+            k += n;
+            continue;
+        }
+        if (op == OP_NOP) continue;
+        out.push_back({op, k, 0});
+        if (op == OP_END) break;
+    }
+    return out;
+}
+
+std::vector<Slice> make_slices(const std::vector<TIns> &ins, const std::vector<uint64_t> &words, int n_slots) {
+    std::vector<Slice> out;
+    std::vector<char> need(n_slots + 1, 0);
+    // root of each RACC: the next RFLUSH names it
+    std::vector<int> root_of(ins.size(), -1);
+    int cur = -1;
+    for (int i = (int)ins.size() - 1; i >= 0; --i) {
+        if (ins[i].op == OP_RFLUSH) cur = (int)fd_(words[ins[i].w]);
+        root_of[i] = cur;
+    }
+    for (uint32_t i = 0; i < ins.size(); ++i) {
+        if (ins[i].op != OP_RACC) continue;
+        Slice s;
+        s.racc = i;
+        s.root = root_of[i];
+        s.line = (int)((words[ins[i].w] >> 34) & 7u);
+        std::fill(need.begin(), need.end(), 0);
+        need[fa(words[ins[i].w])] = 1;
+        for (int j = (int)i - 1; j >= 0; --j) {
+            const TIns &t = ins[j];
+            if (t.op == OP_BUNDLE) {
+                uint32_t mask = 0;
+                for (uint32_t q = 0; q < t.n; ++q)
+                    if (need[words[t.w + 1 + q] & 0xFFFFu]) mask |= 1u << q;
+                if (!mask) continue;
+                for (uint32_t q = 0; q < t.n; ++q)
+                    if (mask >> q & 1u) need[words[t.w + 1 + q] & 0xFFFFu] = 0;
+                for (uint32_t q = 0; q < t.n; ++q) {
+                    if (!(mask >> q & 1u)) continue;
+                    const uint64_t m = words[t.w + 1 + q];
+                    need[(m >> 16) & 0xFFFFu] = 1;
+                    need[(m >> 32) & 0xFFFFu] = 1;
+                    need[(m >> 48) & 0xFFFFu] = 1;
+                    ++s.n_fma;
+                }
+                s.keep.push_back({(uint32_t)j, mask});
+            } else if (t.op == OP_GLEAF || t.op == OP_VLEAF) {
+                const uint64_t w = words[t.w];
+                const uint32_t d = fd_(w);
+                const int no = leaf_outputs(w);
+                bool any = false;
+                for (int q = 0; q < no; ++q) any = any || need[d + q];
+                if (!any) continue;
+                for (int q = 0; q < no; ++q) need[d + q] = 0;
+                s.keep.push_back({(uint32_t)j, 0});
+                ++s.n_leaf;
+            } else if (t.op == OP_CONST) {
+                const uint32_t d = fd_(words[t.w]);
+                if (!need[d]) continue;
+                need[d] = 0;
+                s.keep.push_back({(uint32_t)j, 0});
+            }
+        }
+        std::reverse(s.keep.begin(), s.keep.end());
+        out.push_back(std::move(s));
+    }
+    return out;
+}
+
+// ---- source emission ---------------------------------------------------------------
+std::string fnum(float f) {
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    char buf[48];
+    snprintf(buf, sizeof buf, "__int_as_float(0x%08xu)", b);
+    return buf;
+}
+
+// signed momentum sums of a 2-bit-per-variable mask: (x, y, z, k_ext coefficient)
+void momentum_expr(uint32_t mask, int N, std::string &x, std::string &y, std::string &z, std::string &ks) {
+    auto coef = [&](int j) { return (int)(((int32_t)(mask << (30 - 2 * j))) >> 30); };
+    auto sum = [&](const char *comp, bool with_ext) {
+        std::string e;
+        if (with_ext && coef(0)) e = coef(0) > 0 ? "V.kext" : "-V.kext";
+        for (int j = 1; j <= N; ++j) {
+            const int c = coef(j);
+            if (!c) continue;
+            const std::string term = std::string("V.") + comp + "[" + std::to_string(j - 1) + "]";
+            if (e.empty())
+                e = (c > 0 ? "" : "-") + term;
+            else
+                e += (c > 0 ? " + " : " - ") + term;
+        }
+        return e.empty() ? std::string("0.0f") : e;
+    };
+    x = sum("kx", false);
+    y = sum("ky", false);
+    z = sum("kz", true);
+    ks = coef(0) > 0 ? "1.0f" : coef(0) < 0 ? "-1.0f" : "0.0f";
+}
+
+std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, const std::vector<uint64_t> &words,
+                       int N, int n_slots, const char *qual) {
+    std::ostringstream o;
+    std::vector<std::string> cur(n_slots + 1);
+    cur[0] = "0.0f";
+    cur[1] = "1.0f";
+    for (int j = 0; j < N; ++j) cur[2 + j] = "V.t[" + std::to_string(j) + "]";
+    o << qual << " float fd_s" << q << "(const FdSV &V) {\n";
+    int k = 0;
+    for (const auto &kv : s.keep) {
+        const TIns &t = ins[kv.first];
+        const uint64_t w = words[t.w];
+        if (t.op == OP_BUNDLE) {
+            std::vector<std::pair<uint32_t, std::string>> upd;
+            for (uint32_t m = 0; m < t.n; ++m) {
+                if (!(kv.second >> m & 1u)) continue;
+                const uint64_t mw = words[t.w + 1 + m];
+                const uint32_t d = mw & 0xFFFFu, a = (mw >> 16) & 0xFFFFu, b = (mw >> 32) & 0xFFFFu,
+                               c = (uint32_t)(mw >> 48);
+                const std::string nm = "v" + std::to_string(k++);
+                if (b == 1)
+                    o << "  const float " << nm << " = " << cur[a] << " + " << cur[c] << ";\n";
+                else if (c == 0)
+                    o << "  const float " << nm << " = " << cur[a] << " * " << cur[b] << ";\n";
+                else
+                    o << "  const float " << nm << " = fmaf(" << cur[a] << ", " << cur[b] << ", " << cur[c] << ");\n";
+                upd.push_back({d, nm});
+            }
+            for (auto &u : upd) cur[u.first] = u.second;
+        } else if (t.op == OP_GLEAF || t.op == OP_VLEAF) {
+            const uint32_t d = fd_(w), mask = fa(w);
+            const int no = leaf_outputs(w);
+            const int M = (int)((w >> 40) & 7u), dk = (int)((w >> 43) & 1u);
+            std::string x, y, z, ks;
+            momentum_expr(mask, N, x, y, z, ks);
+            const std::string nm = "l" + std::to_string(k++);
+            o << "  float " << nm << "[" << no << "];\n  {\n    const float px = " << x << ", py = " << y
+              << ", pz = " << z << ";\n    const float p2 = fmaf(px, px, fmaf(py, py, pz * pz));\n";
+            if (t.op == OP_GLEAF) {
+                const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
+                o << "    g_family(p2, pz, " << ks << ", V.t[" << la << "] - V.t[" << lb << "], V.beta, V.mu, " << M
+                  << ", " << dk << ", [&](int j, float v) { " << nm << "[j] = v; });\n  }\n";
+            } else {
+                o << "    v_family(p2, pz, " << ks << ", V.Lam, " << M << ", " << dk << ", [&](int j, float v) { "
+                  << nm << "[j] = v; });\n  }\n";
+            }
+            for (int j = 0; j < no; ++j) cur[d + j] = nm + "[" + std::to_string(j) + "]";
+        } else if (t.op == OP_CONST) {
+            uint32_t bits = (uint32_t)(w >> 32);
+            float f;
+            memcpy(&f, &bits, 4);
+            cur[fd_(w)] = fnum(f);
+        }
+    }
+    o << "  return " << cur[fa(words[ins[s.racc].w])] << ";\n}\n";
+    return o.str();
+}
+
+struct Program {
+    std::vector<std::string> modules;   // module 0 holds the kernel
+    int n_modules = 1;
+};
+
+// A compilation unit: one slice, or every slice of one root (the slices are
+// then inlined into one function, so the compiler shares their leaves).
+struct Unit {
+    std::vector<int> slices;
+    int root = -1;
+    double cost = 0;
+};
+
+Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units) {
+    const TapeHeader &h = g.hdr;
+    const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
+    const std::vector<TIns> ins = decode(g.h_tape);
+    std::vector<Slice> sl = make_slices(ins, g.h_tape, (int)h.n_slots);
+    double total = 0;
+    for (auto &s : sl) total += s.cost();
+    std::vector<Unit> units;
+    if (root_units) {
+        for (size_t i = 0; i < sl.size(); ++i) {
+            if (units.empty() || units.back().root != sl[i].root) {
+                units.emplace_back();
+                units.back().root = sl[i].root;
+            }
+            units.back().slices.push_back((int)i);
+        }
+        for (Unit &u : units) {
+            std::vector<uint32_t> leaves;
+            for (int i : u.slices) {
+                u.cost += sl[i].n_fma;
+                for (auto &kv : sl[i].keep)
+                    if (ins[kv.first].op == OP_GLEAF || ins[kv.first].op == OP_VLEAF) leaves.push_back(kv.first);
+            }
+            std::sort(leaves.begin(), leaves.end());
+            u.cost += 30.0 * (double)(std::unique(leaves.begin(), leaves.end()) - leaves.begin());
+        }
+    } else {
+        for (size_t i = 0; i < sl.size(); ++i) {
+            units.emplace_back();
+            units.back().slices.push_back((int)i);
+            units.back().cost = sl[i].cost();
+        }
+    }
+    int n_mod = 1;
+    if (total > kSingleModuleCost && max_modules > 1)
+        n_mod = std::max(2, std::min(max_modules, (int)(total / 2500.0) + 1));
+    // largest units first onto the least loaded module (module 0 also holds the kernel)
+    std::vector<int> mod_of(units.size(), 0);
+    if (n_mod > 1) {
+        std::vector<int> order(units.size());
+        for (size_t i = 0; i < units.size(); ++i) order[i] = (int)i;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return units[a].cost > units[b].cost; });
+        std::vector<double> load(n_mod, 0.0);
+        load[0] = 300.0;
+        for (int i : order) {
+            const int m = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            mod_of[i] = m;
+            load[m] += units[i].cost;
+        }
+        // drop empty modules (fewer units than modules), keeping the kernel module 0
+        std::vector<int> remap(n_mod, -1), used(n_mod, 0);
+        used[0] = 1;
+        for (int m : mod_of) used[m] = 1;
+        int k = 0;
+        for (int m = 0; m < n_mod; ++m)
+            if (used[m]) remap[m] = k++;
+        for (int &m : mod_of) m = remap[m];
+        n_mod = k;
+    }
+    const bool multi = n_mod > 1;
+    const bool by_root = multi && root_units;
+    Program P;
+    P.n_modules = n_mod;
+    P.modules.assign(n_mod, std::string());
+    std::vector<std::ostringstream> src(n_mod);
+    for (int m = 0; m < n_mod; ++m)
+        src[m] << "// generated from a validated fdcore tape: order " << N << ", " << R << " roots, " << sl.size()
+               << " root-accumulate slices\n#include \"fd_jit_rt.cuh\"\n";
+    const char *slice_qual = (multi && !by_root) ? "extern \"C\" __device__ __noinline__" : "static __device__ __forceinline__";
+    for (size_t u = 0; u < units.size(); ++u) {
+        const int m = mod_of[u];
+        for (int i : units[u].slices) {
+            if (multi && !by_root && m != 0)
+                src[0] << "extern \"C\" __device__ float fd_s" << i << "(const FdSV &V);\n";
+            src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, slice_qual);
+        }
+        if (by_root) {
+            const int r = units[u].root;
+            if (m != 0)
+                src[0] << "extern \"C\" __device__ float2 fd_r" << r << "(const FdSV &V, const float *cs, const float *sn);\n";
+            src[m] << "extern \"C\" __device__ __noinline__ float2 fd_r" << r
+                   << "(const FdSV &V, const float *cs, const float *sn) {\n  float re = 0.0f, im = 0.0f, v;\n";
+            for (int i : units[u].slices)
+                src[m] << "  v = fd_s" << i << "(V); re = fmaf(v, cs[" << sl[i].line << "], re); im = fmaf(v, sn["
+                       << sl[i].line << "], im);\n";
+            src[m] << "  return make_float2(re, im);\n}\n";
+        }
+    }
+    // body: roots in flush order, each the sum of its slices times exp(i pi x_line)
+    std::ostringstream b;
+    b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV &V, const float (&cs)["
+      << N << "], const float (&sn)[" << N << "], K &k) {\n";
+    size_t si = 0;
+    for (const TIns &t : ins) {
+        if (t.op != OP_RFLUSH) continue;
+        const int r = (int)fd_(g.h_tape[t.w]);
+        const uint32_t rt = g.h_roots[2 * r];
+        const std::string fl = "k.template flush<" + std::to_string(r) + ", " + std::to_string(rt & 255u) + ", " +
+                               (((rt >> 24) & 255u) ? "1" : "0") + ">";
+        const bool has = si < sl.size() && sl[si].root == r;
+        if (by_root && has) {
+            b << "    {\n      const float2 z = fd_r" << r << "(V, cs, sn);\n      " << fl << "(z.x, z.y);\n    }\n";
+            while (si < sl.size() && sl[si].root == r) ++si;
+            continue;
+        }
+        b << "    {\n      float re = 0.0f, im = 0.0f, v;\n";
+        for (; si < sl.size() && sl[si].root == r; ++si)
+            b << "      v = fd_s" << si << "(V); re = fmaf(v, cs[" << sl[si].line << "], re); im = fmaf(v, sn["
+              << sl[si].line << "], im);\n";
+        b << "      " << fl << "(re, im);\n    }\n";
+    }
+    b << "  }\n};\n";
+    src[0] << b.str();
+    src[0] << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks
+           << ") fd_jit_kernel(const __grid_constant__ EvalArgs A) {\n  jit_main<FdBody, " << N << ", " << DIM << ", "
+           << R << ", " << T << ">(A);\n}\n";
+    for (int m = 0; m < n_mod; ++m) P.modules[m] = src[m].str();
+    return P;
+}
+
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const uint8_t *b = (const uint8_t *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct CompileOut {
+    std::vector<char> cubin;
+    std::string log;
+    bool ok = false;
+};
+
+void compile_module(const std::string &src, int m, bool rdc, int maxrreg, CompileOut &out) {
+    const Rtc &R = rtc();
+    void *prog = nullptr;
+    const char *hdrs[1] = {kRuntimeHeader};
+    const char *names[1] = {"fd_jit_rt.cuh"};
+    const std::string nm = "fd_jit_mod" + std::to_string(m) + ".cu";
+    if (R.create(&prog, src.c_str(), nm.c_str(), 1, hdrs, names) != 0) {
+        out.log = "nvrtcCreateProgram failed";
+        return;
+    }
+    const std::string rr = "--maxrregcount=" + std::to_string(maxrreg);
+    std::vector<const char *> opts = {"-arch=sm_103a", "-std=c++17", rr.c_str()};
+    if (rdc) opts.push_back("-rdc=true");
+    const int st = R.compile(prog, (int)opts.size(), opts.data());
+    size_t ls = 0;
+    R.log_size(prog, &ls);
+    if (ls > 1) {
+        out.log.resize(ls);
+        R.log(prog, &out.log[0]);
+    }
+    if (st == 0) {
+        size_t cs = 0;
+        R.cubin_size(prog, &cs);
+        out.cubin.resize(cs);
+        R.cubin(prog, out.cubin.data());
+        out.ok = cs > 0;
+    }
+    R.destroy(&prog);
+}
+
+fd_status build_cubin(const Program &P, int maxrreg, std::vector<char> &cubin) {
+    const Rtc &R = rtc();
+    if (!R.ok) return fd::set_error(FD_ENOTSUP, "run-time compilation unavailable: " + R.why);
+    const bool rdc = P.n_modules > 1;
+    std::vector<CompileOut> outs(P.n_modules);
+    std::vector<std::thread> th;
+    for (int m = 0; m < P.n_modules; ++m)
+        th.emplace_back(compile_module, std::cref(P.modules[m]), m, rdc, maxrreg, std::ref(outs[m]));
+    for (auto &t : th) t.join();
+    for (int m = 0; m < P.n_modules; ++m)
+        if (!outs[m].ok)
+            return fd::set_error(FD_ENOTSUP, "NVRTC failed on module " + std::to_string(m) + ": " +
+                                                 outs[m].log.substr(0, 4000));
+    if (!rdc) {
+        cubin = std::move(outs[0].cubin);
+        return FD_OK;
+    }
+    void *lk = nullptr;
+    const char *lopts[1] = {"-arch=sm_103a"};
+    if (R.l_create(&lk, 1, lopts) != 0) return fd::set_error(FD_ENOTSUP, "nvJitLinkCreate failed");
+    int st = 0;
+    for (int m = 0; m < P.n_modules && st == 0; ++m) {
+        const std::string nm = "fd_jit_mod" + std::to_string(m);
+        st = R.l_add(lk, 1 /* NVJITLINK_INPUT_CUBIN */, outs[m].cubin.data(), outs[m].cubin.size(), nm.c_str());
+    }
+    if (st == 0) st = R.l_complete(lk);
+    if (st != 0) {
+        size_t ls = 0;
+        R.l_log_size(lk, &ls);
+        std::string log(ls, '\0');
+        if (ls) R.l_log(lk, &log[0]);
+        R.l_destroy(&lk);
+        return fd::set_error(FD_ENOTSUP, "nvJitLink failed: " + log.substr(0, 4000));
+    }
+    size_t cs = 0;
+    R.l_cubin_size(lk, &cs);
+    cubin.resize(cs);
+    R.l_cubin(lk, cubin.data());
+    R.l_destroy(&lk);
+    return FD_OK;
+}
+
+}  // namespace
+
+fd_status jit_launch(const fd_graph *g, const EvalArgs &args, cudaStream_t stream) {
+    int dev = 0, n_sm = 0, per_sm = 0;
+    FD_CHECK_CUDA(cudaGetDevice(&dev));
+    (void)per_sm;
+    FD_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    per_sm = g->jit_per_sm;
+    const int items = args.n_inst * args.tiles_per_inst;
+    const int grid = std::min(items, n_sm * per_sm);
+    void *params[1] = {(void *)&args};
+    FD_CHECK_CUDA(cudaLaunchKernel((const void *)g->jit_kernel, dim3(grid), dim3(g->jit_threads), params, 0, stream));
+    return FD_OK;
+}
+
+extern "C" fd_status fd_jit_emit(const void *tape, size_t tape_len, int32_t threads, int32_t min_blocks,
+                                 int32_t max_modules, int32_t root_units, int32_t module, char *buf, int64_t cap,
+                                 int64_t *len, int32_t *n_modules) {
+    FD_REQUIRE(tape, "tape is required");
+    FD_REQUIRE(threads == 64 || threads == 128 || threads == 256, "threads must be 64, 128 or 256");
+    FD_REQUIRE(min_blocks >= 1 && min_blocks <= 8, "min_blocks must be in 1..8");
+    FD_REQUIRE(max_modules >= 1 && max_modules <= 64, "max_modules must be in 1..64");
+    fd_graph g;
+    const fd_status st = graph_from_tape(tape, tape_len, g);
+    if (st != FD_OK) return st;
+    const Program P = emit_program(g, threads, min_blocks, max_modules, root_units);
+    if (n_modules) *n_modules = P.n_modules;
+    FD_REQUIRE(module >= 0 && module < P.n_modules, "module out of range");
+    const std::string &s = P.modules[module];
+    if (len) *len = (int64_t)s.size();
+    if (buf && cap > 0) {
+        const int64_t n = std::min<int64_t>(cap - 1, (int64_t)s.size());
+        memcpy(buf, s.data(), (size_t)n);
+        buf[n] = '\0';
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_graph_jit(fd_graph *g, int32_t threads, int32_t min_blocks, int32_t max_modules,
+                                  int32_t root_units, const char *cache_dir) {
+    FD_REQUIRE(g, "null graph");
+    FD_REQUIRE(threads == 64 || threads == 128 || threads == 256, "threads must be 64, 128 or 256");
+    FD_REQUIRE(min_blocks >= 1 && min_blocks <= 8, "min_blocks must be in 1..8");
+    FD_REQUIRE(max_modules >= 1 && max_modules <= 64, "max_modules must be in 1..64");
+    int dev = 0;
+    FD_CHECK_CUDA(cudaGetDevice(&dev));
+    FD_REQUIRE(dev == g->device, "graph belongs to another device");
+    const auto t0 = std::chrono::steady_clock::now();
+    const int maxrreg = std::min(255, (65536 / (threads * min_blocks)) & ~7);
+    const Program P = emit_program(*g, threads, min_blocks, max_modules, root_units);
+    // cache key: generator version, launch shape, register cap and every module's source
+    uint64_t key = fnv1a(&kJitVersion, sizeof kJitVersion);
+    key = fnv1a(kRuntimeHeader, sizeof kRuntimeHeader, key);
+    const int32_t shape[4] = {threads, min_blocks, maxrreg, root_units};
+    key = fnv1a(shape, sizeof shape, key);
+    for (const auto &m : P.modules) key = fnv1a(m.data(), m.size(), key);
+    std::string path;
+    std::vector<char> cubin;
+    if (cache_dir && cache_dir[0]) {
+        char hex[32];
+        snprintf(hex, sizeof hex, "%016llx", (unsigned long long)key);
+        path = std::string(cache_dir) + "/fdjit_" + hex + ".cubin";
+        std::ifstream f(path, std::ios::binary);
+        if (f) cubin.assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+    }
+    if (cubin.empty()) {
+        const fd_status st = build_cubin(P, maxrreg, cubin);
+        if (st != FD_OK) return st;
+        if (!path.empty()) {
+            const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+            std::ofstream f(tmp, std::ios::binary);
+            f.write(cubin.data(), (std::streamsize)cubin.size());
+            f.close();
+            if (f) std::rename(tmp.c_str(), path.c_str());
+        }
+    }
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+    FD_CHECK_CUDA(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+    cudaError_t e = cudaLibraryGetKernel(&kern, lib, "fd_jit_kernel");
+    cudaFuncAttributes attr;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, (const void *)kern);
+    if (e != cudaSuccess) {
+        cudaLibraryUnload(lib);
+        return fd::cuda_error(e, "loading the specialised kernel");
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kern, threads, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        per_sm = std::max(1, 65536 / (std::max(attr.numRegs, 1) * threads));
+    }
+    if (g->jit_lib) cudaLibraryUnload(g->jit_lib);
+    g->jit_per_sm = std::max(per_sm, 1);
+    g->jit_lib = lib;
+    g->jit_kernel = kern;
+    g->jit_threads = threads;
+    g->jit_min_blocks = min_blocks;
+    g->jit_regs = attr.numRegs;
+    g->jit_local_bytes = (int)attr.localSizeBytes;
+    g->jit_modules = P.n_modules;
+    g->jit_compile_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    g->jit_enabled = true;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_graph_jit_enable(fd_graph *g, int32_t on) {
+    FD_REQUIRE(g, "null graph");
+    FD_REQUIRE(!on || g->jit_kernel, "graph has no specialised kernel (call fd_graph_jit first)");
+    g->jit_enabled = on != 0;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_graph_jit_info(const fd_graph *g, int32_t *info, double *compile_s) {
+    FD_REQUIRE(g && info, "graph and info are required");
+    info[0] = g->jit_threads;
+    info[1] = g->jit_min_blocks;
+    info[2] = g->jit_regs;
+    info[3] = g->jit_local_bytes;
+    info[4] = g->jit_modules;
+    info[5] = g->jit_enabled ? 1 : 0;
+    if (compile_s) *compile_s = g->jit_compile_s;
+    return FD_OK;
+}

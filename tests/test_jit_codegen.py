@@ -1,0 +1,63 @@
+"""CPU checks of the specialised-kernel generator (no device): the generated
+source of a small graph compiles for sm_103a, and a large graph splits into
+modules whose slice functions are each defined exactly once."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+from paper_2403_18840_gb300 import api, fdgraph
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2403_18840_gb300", "csrc")
+
+
+def _tape(order, with_dk):
+    return fdgraph.compile_graph(order, fdgraph.graph_roots(order, with_dk=with_dk), budget=8192).to_bytes()
+
+
+def test_small_graph_is_one_module_with_every_root_flushed():
+    tape = _tape(2, True)
+    src, n_mod = api.jit_source(tape, 128, 2, 8, 0)
+    assert n_mod == 1
+    roots = fdgraph.graph_roots(2, with_dk=True)
+    flushes = re.findall(r"flush<(\d+), (\d+), (\d+)>", src)
+    assert sorted(int(r) for r, _, _ in flushes) == list(range(len(roots)))
+    for r, n, dk in flushes:
+        assert (int(n), int(dk)) == (roots[int(r)][0], 1 if roots[int(r)][3] else 0)
+    assert "__launch_bounds__(128, 2)" in src
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None, reason="nvcc not available")
+def test_generated_source_compiles(tmp_path):
+    src, _ = api.jit_source(_tape(2, True), 128, 2, 1, 0)
+    f = tmp_path / "m0.cu"
+    f.write_text(src)
+    r = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-cubin",
+                        "-I", CSRC, "-o", str(tmp_path / "m0.cubin"), str(f)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("root_units", [False, True])
+def test_large_graph_splits_into_linked_modules(root_units):
+    tape = _tape(5, False)
+    _, n_mod = api.jit_source(tape, 128, 2, 8, 0, root_units)
+    assert 2 <= n_mod <= 8
+    unit = "fd_r" if root_units else "fd_s"
+    ret = "float2" if root_units else "float"
+    defined, declared, slices = [], set(), []
+    for m in range(n_mod):
+        src, _ = api.jit_source(tape, 128, 2, 8, m, root_units)
+        defined += re.findall(r'extern "C" __device__ __noinline__ %s (%s\d+)\(' % (ret, unit), src)
+        declared |= set(re.findall(r'extern "C" __device__ %s (%s\d+)\(const FdSV &V' % (ret, unit), src))
+        slices += re.findall(r"__device__ __\w+__ float (fd_s\d+)\(const FdSV &V\) \{", src)
+        assert ("fd_jit_kernel" in src) == (m == 0)
+    assert len(defined) == len(set(defined))
+    assert declared <= set(defined)
+    assert len(slices) == len(set(slices))            # every slice emitted exactly once
+    body, _ = api.jit_source(tape, 128, 2, 8, 0, root_units)
+    called = set(re.findall(r"= (%s\d+)\(V" % unit, body))
+    assert called == set(defined)
+    if root_units:
+        assert len(defined) == len(fdgraph.graph_roots(5))
