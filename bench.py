@@ -2,12 +2,14 @@
 
 One step = one VEGAS iteration of the order-5 self-energy graph (r_s = 1,
 k = k_F, 15 roots Sigma^(n,m,l) with n + m + l = 5, 2^24 samples): Philox ->
-VEGAS map -> loop momenta / times -> leaf families -> tape contraction ->
-FP64 tile partials and VEGAS histogram (one kernel), then the fixed-order
-reduction and the FP64 grid update (two kernels).  Inputs are generated on the
-device; L2 is flushed (a 256 MiB write) between timed steps.
+VEGAS map -> loop momenta / times -> leaf families -> contraction of the
+compiled graph (the graph's specialised straight-line kernel, compiled at
+start-up and not timed) -> FP64 tile partials and VEGAS histogram (one
+kernel), then the fixed-order reduction and the FP64 grid update (two
+kernels).  Inputs are generated on the device; L2 is flushed (a 256 MiB
+write) between timed steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-flow]
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host
 cores on a bounded sample of the same workload.  Under torchrun (N > 1) every
@@ -44,6 +46,7 @@ def _parse():
     ap.add_argument("--samples", type=int, default=WL["n_samples"])
     ap.add_argument("--flow-steps", type=int, default=workloads.FLOW_ORDER5["train_steps"])
     ap.add_argument("--flow-batch", type=int, default=workloads.FLOW_ORDER5["batch"])
+    ap.add_argument("--no-flow", action="store_true", help="skip the flow vs VEGAS section (profiling runs)")
     return ap.parse_args()
 
 
@@ -160,6 +163,39 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def flow_vs_vegas(args, api, params, order, seed):
+    """Learned proposal vs VEGAS for Sigma^(5) itself (single-root graph that both
+    samplers adapt to), at equal sample counts; adaptation and training are
+    outside the timed comparison."""
+    import torch
+
+    from paper_2403_18840_gb300 import driver
+    FW = workloads.FLOW_ORDER5
+    Gs = api.Graph(order, roots=[(order, 0, 0, 0)], budget=1 << 13)
+    Gs.jit()
+    Vs = api.Vegas(Gs.dim, FW["n_bins"])
+    driver.adapt_vegas(Gs, params[0], Vs, 1 << 22, 12, seed=FW["seed"])
+    F = api.Flow(Gs.dim, FW["n_layers"], FW["hidden"], seed=FW["seed"])
+    t0 = time.perf_counter()
+    losses = driver.train_flow(Gs, params[0], F, Vs, steps=max(1, args.flow_steps), batch=args.flow_batch,
+                               lr=1e-3, seed=FW["seed"], vegas_steps=100, evals_per_batch=4, defensive=0.1)
+    torch.cuda.synchronize()
+    flow_train_s = time.perf_counter() - t0
+    cmp = driver.compare(Gs, params[0], Vs, F, FW["n_compare"], seed=seed + 7, batches=16, defensive=0.1)
+    eff = {"quantity": "Re Sigma^(5)(k_F, i w0), single-root order-5 graph", "vegas": cmp["vegas"],
+           "flow": cmp["flow"], "flow_over_vegas": cmp["flow_over_vegas"],
+           "flow_over_vegas_median": cmp["flow_over_vegas_median"],
+           "per_sample_variance_gain": cmp["vegas"]["var_per_sample"] / cmp["flow"]["var_per_sample"],
+           "means_agree_sigma": cmp["means_agree_sigma"], "compare": "16 batches x %d samples per sampler" %
+           FW["n_compare"], "proposal": "flow on the VEGAS grid's input coordinates, 10 % defensive uniform share",
+           "flow_train_steps": max(1, args.flow_steps), "flow_batch": args.flow_batch,
+           "flow_train_s": flow_train_s, "flow_loss_first_last": [losses[0], losses[-1]],
+           "flow_train_note": "each integrand batch reused for 4 Adam steps; first 100 steps on VEGAS samples; "
+                              "VEGAS adapted 12 iterations x 2^22 samples"}
+
+    return eff
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -169,11 +205,11 @@ def run_ours(args, rank, world, dist):
     order = WL["order"]
     roots = fdgraph.graph_roots(order)
     params = [api.ueg_params(order, WL["rs"], WL["T_over_TF"], WL["lam_over_kF"], WL["kext_over_kF"])]
-    # tape schedule and CTA shape chosen by the autotuner (cached per device; not timed)
-    G, tuned = autotune.tuned_graph(order, roots, params[0])
+    # specialised kernel variant chosen by the autotuner (compiled and cached; not timed)
+    G, tuned = autotune.tuned_jit_graph(order, roots, params[0])
     # algorithmic work: every leaf family computed once (no recomputation)
     flops_ps, sfu_ps = fdgraph.tape_work(api.tape_bytes(order, roots, budget=1 << 13, bundle=1, window=1))
-    exec_flops_ps, exec_sfu_ps = fdgraph.tape_work(G.tape)
+    exec_flops_ps, exec_sfu_ps = fdgraph.specialised_work(G.tape, tuned["root_units"])
     V = api.Vegas(G.dim, WL["n_bins"])
     n = args.samples
     plan = api.EvalPlan([G], params, [0], n, maps=[V])
@@ -240,29 +276,7 @@ def run_ours(args, rank, world, dist):
     h2d = int(e_host.nbytes)
     d2h = int(e_host.nbytes + stats_host.numel() * 8)
 
-    # learned proposal vs VEGAS for Sigma^(5) itself (single-root graph that both
-    # samplers adapt to), at equal sample counts; adaptation and training are
-    # outside the timed region
-    from paper_2403_18840_gb300 import driver
-    FW = workloads.FLOW_ORDER5
-    Gs = api.Graph(order, roots=[(order, 0, 0, 0)])
-    Vs = api.Vegas(Gs.dim, FW["n_bins"])
-    driver.adapt_vegas(Gs, params[0], Vs, 1 << 22, 12, seed=FW["seed"])
-    F = api.Flow(Gs.dim, FW["n_layers"], FW["hidden"], seed=FW["seed"])
-    t0 = time.perf_counter()
-    losses = driver.train_flow(Gs, params[0], F, Vs, steps=max(1, args.flow_steps), batch=args.flow_batch,
-                               lr=1e-3, seed=FW["seed"], vegas_steps=100, evals_per_batch=4)
-    torch.cuda.synchronize()
-    flow_train_s = time.perf_counter() - t0
-    cmp = driver.compare(Gs, params[0], Vs, F, FW["n_compare"], seed=seed + 7, batches=4)
-    eff = {"quantity": "Re Sigma^(5)(k_F, i w0), single-root order-5 graph", "vegas": cmp["vegas"],
-           "flow": cmp["flow"], "flow_over_vegas": cmp["flow_over_vegas"],
-           "means_agree_sigma": cmp["means_agree_sigma"], "compare": "4 batches x %d samples per sampler" %
-           FW["n_compare"], "flow_train_steps": max(1, args.flow_steps), "flow_batch": args.flow_batch,
-           "flow_train_s": flow_train_s, "flow_loss_first_last": [losses[0], losses[-1]],
-           "flow_train_note": "each integrand batch reused for 4 Adam steps; first 100 steps on VEGAS samples; "
-                              "VEGAS adapted 12 iterations x 2^22 samples"}
-
+    eff = None if args.no_flow else flow_vs_vegas(args, api, params, order, seed)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     mhz_max = _peaks().get("sm_max_mhz", 2070.0)
@@ -278,12 +292,14 @@ def run_ours(args, rank, world, dist):
         "config": {"workload": WL["name"], "order": order, "rs": WL["rs"], "kext_over_kF": WL["kext_over_kF"],
                    "lam_over_kF": WL["lam_over_kF"], "T_over_TF": WL["T_over_TF"], "roots": len(roots),
                    "dim": G.dim, "samples_per_step": n, "sampler": "vegas", "n_bins": WL["n_bins"],
-                   "tape_instr": G.n_instr, "slots_per_sample": G.n_slots,
-                   "schedule": {k: tuned[k] for k in ("budget", "bundle", "window", "threads", "spt")},
+                   "tape_instr": G.n_instr,
+                   "kernel_variant": {k: tuned.get(k) for k in ("threads", "min_blocks", "root_units", "sync_every",
+                                                               "leaf_calls", "spt", "regs",
+                                                             "local_bytes")},
                    "l2": "256 MiB flush write between timed steps; inputs generated on device",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "integrand_kernel",
+                     "frac": achieved / peak, "traffic": None, "kernel": "fd_jit_kernel",
                      "flops_per_sample": flops_ps, "sfu_per_sample": sfu_ps,
                      "executed_flops_per_sample": exec_flops_ps, "executed_sfu_per_sample": exec_sfu_ps,
                      "sfu_achieved_tops": sfu_achieved,

@@ -97,13 +97,21 @@ fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_
  * {64, 128, 256}, min_blocks in 1..8 (launch bounds; registers are capped at
  * 65536 / (threads * min_blocks)).  root_units != 0: a split graph compiles
  * one function per root (the root's slices share their leaves) instead of
- * one function per slice.  cache_dir (may be NULL): directory for
+ * one function per slice.  sync_every > 0: a block barrier after about that
+ * many generated arithmetic statements (the warps of a CTA then share
+ * instruction-cache lines); 0 = none.  leaf_calls != 0: every leaf family
+ * calls one out-of-line function per (Taylor order, d/dk) shape instead of
+ * being inlined (smaller code, instruction-cache reuse, one call per leaf).
+ * spt in 1..8: samples per thread per pass; with spt > 1 every compilation
+ * unit (a root, or a slice of a large root) loops over the spt samples, so
+ * its code is re-executed from the instruction cache.  cache_dir (may be NULL): directory for
  * compiled images, keyed by a hash of the generated source and options.
  * Synchronous; FD_ENOTSUP when the run-time compiler is unavailable or fails
  * (fd_last_error holds its log).  Results agree with the interpreter up to
  * FP32 rounding order. */
 fd_status fd_graph_jit(fd_graph *g, int32_t threads, int32_t min_blocks, int32_t max_modules,
-                       int32_t root_units, const char *cache_dir);
+                       int32_t root_units, int32_t sync_every, int32_t leaf_calls, int32_t spt,
+                       const char *cache_dir);
 /* Switch evaluation of g between its specialised kernel (on != 0) and the interpreter. */
 fd_status fd_graph_jit_enable(fd_graph *g, int32_t on);
 /* info[6] = threads, min_blocks, registers per thread, local bytes per thread,
@@ -113,8 +121,8 @@ fd_status fd_graph_jit_info(const fd_graph *g, int32_t *info, double *compile_s)
  * needed): copies at most cap - 1 bytes plus a terminating 0 into buf (may be
  * NULL), *len = full length, *n_modules = module count. */
 fd_status fd_jit_emit(const void *tape, size_t tape_len, int32_t threads, int32_t min_blocks,
-                      int32_t max_modules, int32_t root_units, int32_t module, char *buf, int64_t cap,
-                      int64_t *len, int32_t *n_modules);
+                      int32_t max_modules, int32_t root_units, int32_t sync_every, int32_t leaf_calls,
+                      int32_t spt, int32_t module, char *buf, int64_t cap, int64_t *len, int32_t *n_modules);
 
 /* ---- VEGAS map (Sec. IV, separable map q(x) = prod q_k(x_k)) ---------------
  * A map owns FP64 bin edges [dim][n_bins+1] (uniform at creation), their FP32
@@ -252,6 +260,17 @@ fd_status fd_flow_get_params(const fd_flow *f, float *blob, int64_t n);
  * w = 1/q(x).  x: device [dim][n], w: device [n]. */
 fd_status fd_flow_sample(const fd_flow *f, uint64_t seed, uint64_t iter, int32_t inst,
                          int64_t n, float *x, float *w, void *stream);
+/* Defensive mixture proposal q_mix = (1 - a) q + a (a uniform share on the
+ * hypercube; Hesterberg's defensive importance sampling): samples
+ * [0, n - n_u) as fd_flow_sample, samples [n - n_u, n) uniform from the same
+ * Philox stream, where the flow share n - n_u is n - floor(alpha n) rounded up
+ * to a multiple of 256 (at most n), and every sample weighted w = 1 / q_mix(x)
+ * with a = n_u / n (written to *alpha_used, may be NULL).  The weights never exceed 1 / a, so the proposal's tails are
+ * bounded by those of the uniform (or, on a VEGAS grid's coordinates, of
+ * VEGAS).  alpha in [0, 0.5]. */
+fd_status fd_flow_sample_defensive(const fd_flow *f, uint64_t seed, uint64_t iter, int32_t inst,
+                                   int64_t n, double alpha, float *x, float *w, double *alpha_used,
+                                   void *stream);
 /* log q(x) for given points (inverse pass).  x: device [dim][n], logq: device [n]. */
 fd_status fd_flow_log_density(const fd_flow *f, const float *x, int64_t n, float *logq,
                               void *stream);

@@ -44,11 +44,11 @@ SIGNATURES = {
     "fd_graph_roots": (_i32, [_vp, _pi]),
     "fd_graph_free": (None, [_vp]),
     "fd_graph_set_launch": (_i32, [_vp, _i32, _i32]),
-    "fd_graph_jit": (_i32, [_vp, _i32, _i32, _i32, _i32, _c.c_char_p]),
+    "fd_graph_jit": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _c.c_char_p]),
     "fd_graph_jit_enable": (_i32, [_vp, _i32]),
     "fd_graph_jit_info": (_i32, [_vp, _pi, _c.POINTER(_c.c_double)]),
-    "fd_jit_emit": (_i32, [_vp, _c.c_size_t, _i32, _i32, _i32, _i32, _i32, _c.c_char_p, _i64, _c.POINTER(_i64),
-                           _pi]),
+    "fd_jit_emit": (_i32, [_vp, _c.c_size_t, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _c.c_char_p,
+                           _i64, _c.POINTER(_i64), _pi]),
     "fd_vegas_create": (_i32, [_i32, _i32, _c.POINTER(_vp)]),
     "fd_vegas_free": (None, [_vp]),
     "fd_vegas_set_edges": (_i32, [_vp, _pd]),
@@ -75,6 +75,7 @@ SIGNATURES = {
     "fd_flow_set_params": (_i32, [_vp, _pf, _i64]),
     "fd_flow_get_params": (_i32, [_vp, _pf, _i64]),
     "fd_flow_sample": (_i32, [_vp, _u64, _u64, _i32, _i64, _vp, _vp, _vp]),
+    "fd_flow_sample_defensive": (_i32, [_vp, _u64, _u64, _i32, _i64, _f64, _vp, _vp, _c.POINTER(_c.c_double), _vp]),
     "fd_flow_log_density": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "fd_flow_grad": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fd_flow_train": (_i32, [_vp, _vp, _vp, _i64, _i32, _f32, _pf, _vp]),

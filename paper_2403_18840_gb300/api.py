@@ -66,16 +66,18 @@ def tape_bytes(order, roots, budget=None, bundle=None, window=None):
     return data
 
 
-def jit_source(tape, threads=128, min_blocks=2, max_modules=1, module=0, root_units=True):
+def jit_source(tape, threads=128, min_blocks=2, max_modules=1, module=0, root_units=True, sync_every=0,
+               leaf_calls=False, spt=1):
     """Generated source of one module of the specialised kernel (no device needed)."""
     n = ctypes.c_int64()
     nm = ctypes.c_int32()
     ru = 1 if root_units else 0
-    L.check(L.lib().fd_jit_emit(tape, len(tape), threads, min_blocks, max_modules, ru, module, None, 0,
-                                ctypes.byref(n), ctypes.byref(nm)))
+    lc = 1 if leaf_calls else 0
+    L.check(L.lib().fd_jit_emit(tape, len(tape), threads, min_blocks, max_modules, ru, sync_every, lc, spt,
+                                module, None, 0, ctypes.byref(n), ctypes.byref(nm)))
     buf = ctypes.create_string_buffer(n.value + 1)
-    L.check(L.lib().fd_jit_emit(tape, len(tape), threads, min_blocks, max_modules, ru, module, buf, n.value + 1,
-                                ctypes.byref(n), ctypes.byref(nm)))
+    L.check(L.lib().fd_jit_emit(tape, len(tape), threads, min_blocks, max_modules, ru, sync_every, lc, spt,
+                                module, buf, n.value + 1, ctypes.byref(n), ctypes.byref(nm)))
     return buf.value.decode(), nm.value
 
 
@@ -99,7 +101,8 @@ class Graph:
     def set_launch(self, threads=0, samples_per_thread=0):
         L.check(L.lib().fd_graph_set_launch(self.handle, threads, samples_per_thread))
 
-    def jit(self, threads=128, min_blocks=2, max_modules=None, root_units=True, cache=True):
+    def jit(self, threads=128, min_blocks=2, max_modules=None, root_units=True, sync_every=0, leaf_calls=False,
+            spt=1, cache=True):
         """Compile the specialised straight-line kernel (cached under _build/jit)
         and evaluate this graph with it from now on."""
         if max_modules is None:
@@ -108,7 +111,7 @@ class Graph:
         if cdir:
             os.makedirs(cdir, exist_ok=True)
         L.check(L.lib().fd_graph_jit(self.handle, threads, min_blocks, max_modules, 1 if root_units else 0,
-                                     cdir.encode() if cdir else None))
+                                     sync_every, 1 if leaf_calls else 0, spt, cdir.encode() if cdir else None))
         return self.jit_info()
 
     def jit_enable(self, on=True):
@@ -234,6 +237,15 @@ class Flow:
         w = torch.empty((n,), dtype=torch.float32, device="cuda")
         L.check(L.lib().fd_flow_sample(self.handle, seed, it, inst, n, _ptr(x), _ptr(w), _stream_ptr(stream)))
         return x, w
+
+    def sample_defensive(self, seed, it, inst, n, alpha, stream=None):
+        """Mixture (1 - a) q_flow + a uniform: (x, w = 1/q_mix, a actually used)."""
+        x = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")
+        w = torch.empty((n,), dtype=torch.float32, device="cuda")
+        a = ctypes.c_double()
+        L.check(L.lib().fd_flow_sample_defensive(self.handle, seed, it, inst, n, alpha, _ptr(x), _ptr(w),
+                                                 ctypes.byref(a), _stream_ptr(stream)))
+        return x, w, a.value
 
     def log_density(self, x, stream=None):
         n = x.shape[1]

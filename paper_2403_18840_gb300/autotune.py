@@ -1,11 +1,15 @@
-"""Autotuner for the integrand launch: tape schedule x CTA shape.
+"""Autotuner for the integrand launch.
 
-Two sets of knobs decide the interpreter's speed and are tuned per graph and
+Interpreter: two sets of knobs decide its speed and are tuned per graph and
 device by timing real launches:
   * the tape schedule (per-sample slot budget for leaf families and
     temporaries, FMA bundle width, lookahead window of the bundler), which
     trades recomputed leaves against shared-memory occupancy;
   * the CTA shape (threads x samples per thread).
+Specialised kernels: CTA size, launch-bounds occupancy (which caps the
+registers per thread and so trades spills against resident warps) and the
+compilation unit (one function per root, whose slices share leaves, or one
+per slice, which keeps live ranges short).
 Results are cached per (graph, device) in _build/autotune.json.
 """
 import json
@@ -18,6 +22,9 @@ from . import api
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 SCHEDULES = [dict(budget=b, bundle=w, window=8 * w) for b in (96, 128, 160) for w in (4, 8)]
 SHAPES = [(128, 2), (256, 1), (128, 1), (64, 2)]
+# (threads, min_blocks, root_units, sync_every, leaf_calls, samples per thread)
+JIT_VARIANTS = [(256, 1, True, 0, False, 1), (256, 1, True, 0, False, 2), (256, 1, True, 0, False, 4),
+                (256, 1, False, 0, False, 4)]
 
 
 def _key(order, roots):
@@ -80,12 +87,64 @@ def tune(order, roots, params, n_samples=1 << 23, schedules=None, shapes=None, f
             log(dict(r, final=True))
         if best is None or r["samples_per_s"] > best["samples_per_s"]:
             best = r
+    _store(key, best)
+    return best
+
+
+def _store(key, best):
+    cache = _load()
     cache[key] = best
     os.makedirs(os.path.dirname(CACHE), exist_ok=True)
     tmp = CACHE + ".tmp%d" % os.getpid()
     json.dump(cache, open(tmp, "w"), indent=1)
     os.replace(tmp, CACHE)
+
+
+def _jit_graph(order, roots, v):
+    G = api.Graph(order, roots=roots, budget=1 << 13)
+    G.jit(threads=v["threads"], min_blocks=v["min_blocks"], root_units=v["root_units"],
+          sync_every=v.get("sync_every", 0), leaf_calls=v.get("leaf_calls", False), spt=v.get("spt", 1))
+    return G
+
+
+def tune_jit(order, roots, params, n_samples=1 << 23, variants=None, force=False, log=None):
+    """Best {'threads','min_blocks','root_units','sync_every','leaf_calls','spt','samples_per_s',...} for the
+    specialised kernel."""
+    key = "jit2|" + _key(order, roots)
+    cache = _load()
+    if key in cache and not force:
+        return cache[key]
+    results = []
+    for (t, mb, ru, se, lc, spt) in variants or JIT_VARIANTS:
+        v = dict(threads=t, min_blocks=mb, root_units=ru, sync_every=se, leaf_calls=lc, spt=spt)
+        try:
+            G = _jit_graph(order, roots, v)
+            ms = _time(G, params, n_samples)
+        except api.L.FdError:
+            continue
+        r = dict(v, samples_per_s=n_samples / ms * 1e3, **{k: G.jit_info()[k] for k in ("regs", "local_bytes")})
+        results.append(r)
+        if log:
+            log(r)
+    best = None
+    for r in sorted(results, key=lambda r: -r["samples_per_s"])[:2]:
+        G = _jit_graph(order, roots, r)
+        ms = _time(G, params, n_samples, reps=5)
+        r = dict(r, samples_per_s=n_samples / ms * 1e3)
+        if log:
+            log(dict(r, final=True))
+        if best is None or r["samples_per_s"] > best["samples_per_s"]:
+            best = r
+    if best is None:
+        raise RuntimeError("no specialised kernel variant could be compiled")
+    _store(key, best)
     return best
+
+
+def tuned_jit_graph(order, roots, params, **kw):
+    """Graph with its tuned specialised kernel."""
+    best = tune_jit(order, roots, params, **kw)
+    return _jit_graph(order, roots, best), best
 
 
 def tuned_graph(order, roots, params, **kw):

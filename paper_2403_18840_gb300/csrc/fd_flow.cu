@@ -22,6 +22,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -252,11 +253,16 @@ __device__ __forceinline__ bool stage_layer(unsigned char *wsm, const unsigned c
 constexpr int ROUNDS = 4;
 constexpr int BLOCK = 64 * ROUNDS;
 
+// Defensive mixture (mode 0 with n_flow < n): samples [0, n_flow) come from the
+// flow, samples [n_flow, n) are uniform on the hypercube and take the inverse
+// (density) pass; every sample gets w = 1 / ((1 - alpha) q(x) + alpha) with
+// alpha = (n - n_flow) / n, the deterministic-mixture weight.  n_flow is a
+// multiple of BLOCK (or n), so every block is of one kind.
 __global__ void __launch_bounds__(128) flow_pass_kernel(const unsigned char *__restrict__ wglob, FlowDims f, int mode,
                                                          int64_t n, uint32_t seed_lo, uint32_t seed_hi,
                                                          uint32_t iter, uint32_t inst, const float *__restrict__ xin,
                                                          float *__restrict__ xout, float *__restrict__ wout,
-                                                         int *status) {
+                                                         int *status, int64_t n_flow, float alpha) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *wsm = smem;
     float *ys = reinterpret_cast<float *>(smem + LAYER_BYTES);     // [BLOCK][YS]
@@ -272,12 +278,28 @@ __global__ void __launch_bounds__(128) flow_pass_kernel(const unsigned char *__r
     const int64_t nblocks = (n + BLOCK - 1) / BLOCK;
     for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
         const int64_t base = blk * BLOCK;
+        const bool dens = mode == 1 || base >= n_flow;   // inverse (density) pass for this block
         // load / generate the block's coordinates (y = logit) and the log-Jacobian start
         for (int r = tid; r < BLOCK; r += blockDim.x) {
             const int64_t i = base + r;
             const bool valid = i < n;
             float acc = 0.f;
-            if (mode == 0) {
+            if (mode == 0 && dens) {
+                // defensive share: uniform x, kept as the sample, density follows
+                const int64_t ii = valid ? i : base;
+                const uint32_t c0 = (uint32_t)(uint64_t)ii, c1 = (uint32_t)((uint64_t)ii >> 32);
+                for (int blk4 = 0; 4 * blk4 < f.D; ++blk4) {
+                    const u32x4 rr = philox4x32_10(u32x4{c0, c1, iter, (inst << 8) | (uint32_t)blk4}, seed_lo, seed_hi);
+                    const uint32_t wv[4] = {rr.x, rr.y, rr.z, rr.w};
+                    for (int q = 0; q < 4 && 4 * blk4 + q < f.D; ++q) {
+                        const float x = word_to_uniform(wv[q]);
+                        const float y = __logf(x) - log1pf(-x);
+                        ys[r * YS + 4 * blk4 + q] = y;
+                        acc -= log_sig_deriv(y);
+                        if (valid) xout[(int64_t)(4 * blk4 + q) * n + i] = x;
+                    }
+                }
+            } else if (mode == 0) {
                 const int64_t ii = valid ? i : base;
                 const uint32_t c0 = (uint32_t)(uint64_t)ii, c1 = (uint32_t)((uint64_t)ii >> 32);
                 for (int blk4 = 0; 4 * blk4 < f.D; ++blk4) {
@@ -302,7 +324,7 @@ __global__ void __launch_bounds__(128) flow_pass_kernel(const unsigned char *__r
             ld[r] = acc;
         }
         for (int step = 0; step < f.K; ++step) {
-            const int l = mode == 0 ? step : f.K - 1 - step;
+            const int l = !dens ? step : f.K - 1 - step;
             if (!stage_layer(wsm, wglob, l, bar, phase)) {
                 if (tid == 0 && status) atomicExch(status, DEV_ST_TIMEOUT);
                 return;
@@ -315,7 +337,7 @@ __global__ void __launch_bounds__(128) flow_pass_kernel(const unsigned char *__r
                 float o[4][4];
                 input_frag(tile, f, l, g, t, ain);
                 mlp_forward(L, ain, h1a, h2a, o, g, t);
-                coupling(tile, tld, f, l, o, g, t, mode == 0 ? 1.f : -1.f);
+                coupling(tile, tld, f, l, o, g, t, !dens ? 1.f : -1.f);
                 __syncwarp();
             }
         }
@@ -327,11 +349,17 @@ __global__ void __launch_bounds__(128) flow_pass_kernel(const unsigned char *__r
             for (int d = 0; d < f.D; ++d) {
                 const float y = ys[r * YS + d];
                 acc += log_sig_deriv(y);
-                if (mode == 0) xout[(int64_t)d * n + i] = 1.0f / (1.0f + __expf(-y));
+                if (mode == 0 && !dens) xout[(int64_t)d * n + i] = 1.0f / (1.0f + __expf(-y));
             }
-            // mode 0: acc = log |det dx/dz|, w = 1/q = exp(acc); mode 1: acc = log q(x)
-            if (mode == 0) wout[i] = __expf(acc);
-            else wout[i] = acc;
+            // forward: acc = log |det dx/dz| = -log q; inverse: acc = log q(x)
+            if (mode == 1) {
+                wout[i] = acc;
+            } else if (alpha == 0.f) {
+                wout[i] = __expf(acc);
+            } else {
+                const float q = __expf(dens ? acc : -acc);
+                wout[i] = 1.0f / fmaf(1.0f - alpha, q, alpha);
+            }
         }
         __syncthreads();   // the next block reuses the coordinate tiles
     }
@@ -1090,7 +1118,28 @@ extern "C" fd_status fd_flow_sample(const fd_flow *f, uint64_t seed, uint64_t it
     FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, (cudaStream_t)stream>>>(
         f->d_wpack, dims_of(f), 0, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)inst, nullptr, x,
-        w, fd::device_status_word());
+        w, fd::device_status_word(), n, 0.0f);
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
+}
+
+extern "C" fd_status fd_flow_sample_defensive(const fd_flow *f, uint64_t seed, uint64_t iter, int32_t inst,
+                                              int64_t n, double alpha, float *x, float *w, double *alpha_used,
+                                              void *stream) {
+    FD_REQUIRE(f && x && w, "flow, x and w are required");
+    FD_REQUIRE(n > 0 && n <= (int64_t(1) << 34), "n out of range");
+    FD_REQUIRE(inst >= 0 && inst < (1 << 24), "instance index out of range");
+    FD_REQUIRE(alpha >= 0.0 && alpha <= 0.5, "alpha must be in [0, 0.5]");
+    // the flow share ends on a block boundary, so every block is of one kind
+    const int64_t n_flow = std::min(n, (n - (int64_t)(alpha * (double)n) + BLOCK - 1) / BLOCK * BLOCK);
+    const int64_t n_u = n - n_flow;
+    const float a = (float)((double)n_u / (double)n);
+    if (alpha_used) *alpha_used = (double)n_u / (double)n;
+    const int sm = pass_smem();
+    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, (cudaStream_t)stream>>>(
+        f->d_wpack, dims_of(f), 0, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)inst, nullptr, x,
+        w, fd::device_status_word(), n - n_u, a);
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
 }
@@ -1101,7 +1150,7 @@ extern "C" fd_status fd_flow_log_density(const fd_flow *f, const float *x, int64
     const int sm = pass_smem();
     FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, (cudaStream_t)stream>>>(
-        f->d_wpack, dims_of(f), 1, n, 0, 0, 0, 0, x, nullptr, logq, fd::device_status_word());
+        f->d_wpack, dims_of(f), 1, n, 0, 0, 0, 0, x, nullptr, logq, fd::device_status_word(), n, 0.0f);
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
 }

@@ -262,18 +262,28 @@ void momentum_expr(uint32_t mask, int N, std::string &x, std::string &y, std::st
     ks = coef(0) > 0 ? "1.0f" : coef(0) < 0 ? "-1.0f" : "0.0f";
 }
 
+// sync_every > 0: a block barrier after every sync_every arithmetic
+// statements, so that the warps of a CTA walk the (long, straight-line) code
+// together and share the instruction-cache lines they fetch.  Every thread of
+// the block executes every statement, so the barriers are uniform.
+// leaf_calls: leaves call the out-of-line family functions instead of inlining them.
 std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, const std::vector<uint64_t> &words,
-                       int N, int n_slots, const char *qual) {
+                       int N, int n_slots, const char *qual, int sync_every, int leaf_calls) {
     std::ostringstream o;
     std::vector<std::string> cur(n_slots + 1);
     cur[0] = "0.0f";
     cur[1] = "1.0f";
     for (int j = 0; j < N; ++j) cur[2 + j] = "V.t[" + std::to_string(j) + "]";
     o << qual << " float fd_s" << q << "(const FdSV &V) {\n";
-    int k = 0;
+    int k = 0, since_sync = 0;
     for (const auto &kv : s.keep) {
         const TIns &t = ins[kv.first];
         const uint64_t w = words[t.w];
+        if (sync_every > 0 && since_sync >= sync_every) {
+            o << "  __syncthreads();\n";
+            since_sync = 0;
+        }
+        since_sync += t.op == OP_BUNDLE ? (int)__builtin_popcount(kv.second) : (t.op == OP_CONST ? 0 : 8);
         if (t.op == OP_BUNDLE) {
             std::vector<std::pair<uint32_t, std::string>> upd;
             for (uint32_t m = 0; m < t.n; ++m) {
@@ -298,6 +308,19 @@ std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, cons
             std::string x, y, z, ks;
             momentum_expr(mask, N, x, y, z, ks);
             const std::string nm = "l" + std::to_string(k++);
+            if (leaf_calls) {
+                o << "  FdLeafOut<" << no << "> " << nm << ";\n  {\n    const float px = " << x << ", py = " << y
+                  << ", pz = " << z << ";\n    const float p2 = fmaf(px, px, fmaf(py, py, pz * pz));\n";
+                if (t.op == OP_GLEAF) {
+                    const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
+                    o << "    " << nm << " = g_leaf_fn<" << M << ", " << dk << ">(p2, pz, " << ks << ", V.t[" << la
+                      << "] - V.t[" << lb << "], V.beta, V.mu);\n  }\n";
+                } else {
+                    o << "    " << nm << " = v_leaf_fn<" << M << ", " << dk << ">(p2, pz, " << ks << ", V.Lam);\n  }\n";
+                }
+                for (int j = 0; j < no; ++j) cur[d + j] = nm + ".v[" + std::to_string(j) + "]";
+                continue;
+            }
             o << "  float " << nm << "[" << no << "];\n  {\n    const float px = " << x << ", py = " << y
               << ", pz = " << z << ";\n    const float p2 = fmaf(px, px, fmaf(py, py, pz * pz));\n";
             if (t.op == OP_GLEAF) {
@@ -333,7 +356,12 @@ struct Unit {
     double cost = 0;
 };
 
-Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units) {
+Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
+                          int leaf_calls);
+
+Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units, int sync_every,
+                     int leaf_calls, int spt = 1) {
+    if (spt > 1) return emit_program_loop(g, T, min_blocks, max_modules, spt, root_units ? 6000.0 : 0.0, leaf_calls);
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -407,7 +435,7 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
         for (int i : units[u].slices) {
             if (multi && !by_root && m != 0)
                 src[0] << "extern \"C\" __device__ float fd_s" << i << "(const FdSV &V);\n";
-            src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, slice_qual);
+            src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, slice_qual, sync_every, leaf_calls);
         }
         if (by_root) {
             const int r = units[u].root;
@@ -451,6 +479,107 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
            << R << ", " << T << ">(A);\n}\n";
     for (int m = 0; m < n_mod; ++m) P.modules[m] = src[m].str();
     return P;
+}
+
+// Emission with P > 1 samples per thread: compilation units (a root, or one
+// slice of a root whose cost exceeds unit_cap) loop over the P samples.
+Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
+                          int leaf_calls) {
+    const TapeHeader &h = g.hdr;
+    const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
+    const std::vector<TIns> ins = decode(g.h_tape);
+    std::vector<Slice> sl = make_slices(ins, g.h_tape, (int)h.n_slots);
+    double total = 0;
+    for (auto &s : sl) total += s.cost();
+    // units: all slices of a root, unless the root costs more than unit_cap
+    std::vector<Unit> units;
+    for (size_t i = 0; i < sl.size();) {
+        size_t j = i;
+        double c = 0;
+        while (j < sl.size() && sl[j].root == sl[i].root) c += sl[j++].cost();
+        if (c > unit_cap) {
+            for (size_t q = i; q < j; ++q) {
+                units.emplace_back();
+                units.back().root = sl[q].root;
+                units.back().slices.push_back((int)q);
+                units.back().cost = sl[q].cost();
+            }
+        } else {
+            units.emplace_back();
+            units.back().root = sl[i].root;
+            for (size_t q = i; q < j; ++q) units.back().slices.push_back((int)q);
+            units.back().cost = c;
+        }
+        i = j;
+    }
+    int n_mod = 1;
+    if (total > kSingleModuleCost && max_modules > 1)
+        n_mod = std::max(2, std::min(max_modules, (int)(total / 2500.0) + 1));
+    std::vector<int> mod_of(units.size(), 0);
+    if (n_mod > 1) {
+        std::vector<int> order(units.size());
+        for (size_t i = 0; i < units.size(); ++i) order[i] = (int)i;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return units[a].cost > units[b].cost; });
+        std::vector<double> load(n_mod, 0.0);
+        load[0] = 300.0;
+        for (int i : order) {
+            const int m = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            mod_of[i] = m;
+            load[m] += units[i].cost;
+        }
+        std::vector<int> remap(n_mod, -1), used(n_mod, 0);
+        used[0] = 1;
+        for (int m : mod_of) used[m] = 1;
+        int k = 0;
+        for (int m = 0; m < n_mod; ++m)
+            if (used[m]) remap[m] = k++;
+        for (int &m : mod_of) m = remap[m];
+        n_mod = k;
+    }
+    const bool multi = n_mod > 1;
+    Program Pg;
+    Pg.n_modules = n_mod;
+    Pg.modules.assign(n_mod, std::string());
+    std::vector<std::ostringstream> src(n_mod);
+    for (int m = 0; m < n_mod; ++m)
+        src[m] << "// generated from a validated fdcore tape: order " << N << ", " << R << " roots, " << sl.size()
+               << " root-accumulate slices, " << spt << " samples per thread\n#include \"fd_jit_rt.cuh\"\n";
+    const char *unit_qual = multi ? "extern \"C\" __device__ __noinline__" : "static __device__ __noinline__";
+    const std::string sig = "(const FdSV *V, const float *cs, const float *sn, float *re, float *im)";
+    for (size_t u = 0; u < units.size(); ++u) {
+        const int m = mod_of[u];
+        for (int i : units[u].slices)
+            src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, "static __device__ __forceinline__", 0,
+                                 leaf_calls);
+        if (multi && m != 0) src[0] << "extern \"C\" __device__ void fd_u" << u << sig << ";\n";
+        src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
+               << "; ++p) {\n    float r = 0.0f, i = 0.0f, v;\n";
+        for (int i : units[u].slices)
+            src[m] << "    v = fd_s" << i << "(V[p]); r = fmaf(v, cs[p * " << N << " + " << sl[i].line
+                   << "], r); i = fmaf(v, sn[p * " << N << " + " << sl[i].line << "], i);\n";
+        src[m] << "    re[p] += r;\n    im[p] += i;\n  }\n}\n";
+    }
+    std::ostringstream b;
+    b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV *V, const float *cs, "
+         "const float *sn, K *k) {\n";
+    for (const TIns &t : ins) {
+        if (t.op != OP_RFLUSH) continue;
+        const int r = (int)fd_(g.h_tape[t.w]);
+        const uint32_t rt = g.h_roots[2 * r];
+        b << "    {\n      float re[" << spt << "], im[" << spt << "];\n#pragma unroll\n      for (int p = 0; p < "
+          << spt << "; ++p) re[p] = im[p] = 0.0f;\n";
+        for (size_t u = 0; u < units.size(); ++u)
+            if (units[u].root == r) b << "      fd_u" << u << "(V, cs, sn, re, im);\n";
+        b << "#pragma unroll\n      for (int p = 0; p < " << spt << "; ++p) k[p].template flush<" << r << ", "
+          << (rt & 255u) << ", " << (((rt >> 24) & 255u) ? 1 : 0) << ">(re[p], im[p]);\n    }\n";
+    }
+    b << "  }\n};\n";
+    src[0] << b.str();
+    src[0] << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks
+           << ") fd_jit_kernel(const __grid_constant__ EvalArgs A) {\n  jit_main_loop<FdBody, " << N << ", " << DIM
+           << ", " << R << ", " << T << ", " << spt << ">(A);\n}\n";
+    for (int m = 0; m < n_mod; ++m) Pg.modules[m] = src[m].str();
+    return Pg;
 }
 
 uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
@@ -556,16 +685,19 @@ fd_status jit_launch(const fd_graph *g, const EvalArgs &args, cudaStream_t strea
 }
 
 extern "C" fd_status fd_jit_emit(const void *tape, size_t tape_len, int32_t threads, int32_t min_blocks,
-                                 int32_t max_modules, int32_t root_units, int32_t module, char *buf, int64_t cap,
-                                 int64_t *len, int32_t *n_modules) {
+                                 int32_t max_modules, int32_t root_units, int32_t sync_every, int32_t leaf_calls,
+                                 int32_t spt, int32_t module, char *buf, int64_t cap, int64_t *len,
+                                 int32_t *n_modules) {
     FD_REQUIRE(tape, "tape is required");
     FD_REQUIRE(threads == 64 || threads == 128 || threads == 256, "threads must be 64, 128 or 256");
     FD_REQUIRE(min_blocks >= 1 && min_blocks <= 8, "min_blocks must be in 1..8");
     FD_REQUIRE(max_modules >= 1 && max_modules <= 64, "max_modules must be in 1..64");
+    FD_REQUIRE(sync_every >= 0, "sync_every must be >= 0");
+    FD_REQUIRE(spt >= 1 && spt <= 8, "samples per thread must be in 1..8");
     fd_graph g;
     const fd_status st = graph_from_tape(tape, tape_len, g);
     if (st != FD_OK) return st;
-    const Program P = emit_program(g, threads, min_blocks, max_modules, root_units);
+    const Program P = emit_program(g, threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt);
     if (n_modules) *n_modules = P.n_modules;
     FD_REQUIRE(module >= 0 && module < P.n_modules, "module out of range");
     const std::string &s = P.modules[module];
@@ -579,21 +711,24 @@ extern "C" fd_status fd_jit_emit(const void *tape, size_t tape_len, int32_t thre
 }
 
 extern "C" fd_status fd_graph_jit(fd_graph *g, int32_t threads, int32_t min_blocks, int32_t max_modules,
-                                  int32_t root_units, const char *cache_dir) {
+                                  int32_t root_units, int32_t sync_every, int32_t leaf_calls, int32_t spt,
+                                  const char *cache_dir) {
     FD_REQUIRE(g, "null graph");
     FD_REQUIRE(threads == 64 || threads == 128 || threads == 256, "threads must be 64, 128 or 256");
     FD_REQUIRE(min_blocks >= 1 && min_blocks <= 8, "min_blocks must be in 1..8");
     FD_REQUIRE(max_modules >= 1 && max_modules <= 64, "max_modules must be in 1..64");
+    FD_REQUIRE(sync_every >= 0, "sync_every must be >= 0");
+    FD_REQUIRE(spt >= 1 && spt <= 8, "samples per thread must be in 1..8");
     int dev = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
     FD_REQUIRE(dev == g->device, "graph belongs to another device");
     const auto t0 = std::chrono::steady_clock::now();
     const int maxrreg = std::min(255, (65536 / (threads * min_blocks)) & ~7);
-    const Program P = emit_program(*g, threads, min_blocks, max_modules, root_units);
+    const Program P = emit_program(*g, threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt);
     // cache key: generator version, launch shape, register cap and every module's source
     uint64_t key = fnv1a(&kJitVersion, sizeof kJitVersion);
     key = fnv1a(kRuntimeHeader, sizeof kRuntimeHeader, key);
-    const int32_t shape[4] = {threads, min_blocks, maxrreg, root_units};
+    const int32_t shape[7] = {threads, min_blocks, maxrreg, root_units, sync_every, leaf_calls, spt};
     key = fnv1a(shape, sizeof shape, key);
     for (const auto &m : P.modules) key = fnv1a(m.data(), m.size(), key);
     std::string path;

@@ -190,6 +190,30 @@ __device__ __forceinline__ void v_family(float q2, float qz, float ks, float Lam
     }
 }
 
+// Out-of-line leaf families for the specialised kernels: one function per
+// (M, dk) shape, called from every leaf of that shape, so the leaf code is
+// fetched once and reused from the instruction cache instead of being inlined
+// hundreds of times into straight-line code.
+template <int NV>
+struct FdLeafOut {
+    float v[NV];
+};
+
+template <int M, int DK>
+__device__ __noinline__ FdLeafOut<(M + 1) * (1 + DK)> g_leaf_fn(float p2, float pz, float ks, float dx, float beta,
+                                                                 float mu) {
+    FdLeafOut<(M + 1) * (1 + DK)> o;
+    g_family(p2, pz, ks, dx, beta, mu, M, DK, [&](int j, float v) { o.v[j] = v; });
+    return o;
+}
+
+template <int L, int DK>
+__device__ __noinline__ FdLeafOut<(L + 1) * (1 + DK)> v_leaf_fn(float q2, float qz, float ks, float Lambda) {
+    FdLeafOut<(L + 1) * (1 + DK)> o;
+    v_family(q2, qz, ks, Lambda, L, DK, [&](int j, float v) { o.v[j] = v; });
+    return o;
+}
+
 // ---- specialised kernels -------------------------------------------------------
 // Per-sample variables the generated code reads: loop momenta k_1..k_N,
 // hypercube times of the interaction lines (t[0] = 0) and the parameters.
@@ -356,6 +380,77 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
             }
             const int64_t o = (((int64_t)D.id * A.tiles_per_inst + tile) * A.r_max) * 4;
             A.partials[o + k] = s + c;     // k = r * 4 + q, q: re sum, re sumsq, im sum, im sumsq
+        }
+        for (int k = R * 4 + tid; k < A.r_max * 4; k += T) {
+            const int64_t o = (((int64_t)D.id * A.tiles_per_inst + tile) * A.r_max) * 4;
+            A.partials[o + k] = 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// Variant with P samples per thread per pass, handled one after another by
+// every compilation unit (Body::run loops over the samples inside each unit):
+// the unit's code is fetched once and then re-executed from the instruction
+// cache for the other P - 1 samples, at no cost in registers (the per-sample
+// inputs live in local memory).
+template <class Body, int N, int DIM, int R, int T, int P>
+__device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
+    __shared__ double acc[T / 32][R * 8];
+    __shared__ int next_item;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_items = A.n_inst * A.tiles_per_inst;
+    const uint32_t iter = A.iter + (A.iter_dev ? *A.iter_dev : 0u);
+    for (;;) {
+        if (tid == 0) next_item = (int)atomicAdd(A.queue, 1ull);
+        __syncthreads();
+        const int item = next_item;
+        if (item >= n_items) break;
+        const InstDesc &D = A.inst[A.perm[item / A.tiles_per_inst]];
+        const int tile = item % A.tiles_per_inst;
+        for (int k = lane; k < R * 8; k += 32) acc[warp][k] = 0.0;
+        __syncwarp();
+        const int64_t first = (int64_t)tile * A.tile;
+        const int64_t last = min(first + A.tile, A.n_per_inst);
+        for (int64_t base = first; base < last; base += (int64_t)T * P) {
+            FdSV V[P];
+            float jac[P][N];
+            int bins[P][DIM];
+            float cs[P * N], sn[P * N];
+            FdSink<N> K[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int64_t i = base + (int64_t)p * T + tid;
+                const bool valid = i < last;
+                const int64_t idx = valid ? i : first;
+                sample_point<N, DIM>(D, A, idx, iter, V[p], jac[p], bins[p]);
+                cs[p * N] = 1.0f;
+                sn[p * N] = 0.0f;
+#pragma unroll
+                for (int j = 1; j < N; ++j) sincospif(V[p].t[j], &sn[p * N + j], &cs[p * N + j]);
+                K[p] = FdSink<N>{acc[warp], jac[p], valid, 0.0f, A.per_sample_f,
+                                 (int64_t)D.id * A.r_max * 2 * A.n_per_inst + idx, A.n_per_inst};
+            }
+            Body::run(V, cs, sn, K);
+            if (D.hist) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (!K[p].valid) continue;
+                    const double h = (double)K[p].hsum * (double)K[p].hsum;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) atomicAdd(D.hist + (int64_t)d * D.n_bins + bins[p][d], h);
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = tid; k < R * 4; k += T) {
+            double s = 0.0, c = 0.0;
+            for (int wp = 0; wp < T / 32; ++wp) {
+                neumaier(s, c, acc[wp][k * 2]);
+                neumaier(s, c, acc[wp][k * 2 + 1]);
+            }
+            const int64_t o = (((int64_t)D.id * A.tiles_per_inst + tile) * A.r_max) * 4;
+            A.partials[o + k] = s + c;
         }
         for (int k = R * 4 + tid; k < A.r_max * 4; k += T) {
             const int64_t o = (((int64_t)D.id * A.tiles_per_inst + tile) * A.r_max) * 4;

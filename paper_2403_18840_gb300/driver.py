@@ -47,8 +47,15 @@ def training_weights(per_sample, value_roots):
     return ps.abs().sum(dim=(0, 1)).contiguous()
 
 
+def _flow_draw(flow, seed, it, inst, n, defensive):
+    if defensive > 0:
+        x, w, _ = flow.sample_defensive(seed, it, inst, n, defensive)
+        return x, w
+    return flow.sample(seed, it, inst, n)
+
+
 def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, evals_per_batch=1, log=None,
-               on_vegas=True):
+               on_vegas=True, defensive=0.0):
     """Forward-KL training of `flow` on |f|; the first `vegas_steps` batches come from VEGAS.
 
     Every batch is drawn from the current sampler, evaluated by the integrand
@@ -64,7 +71,7 @@ def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, e
             # VEGAS draws: uniform in the map's input space, or mapped points
             x, w = api.map_samples(None if on_vegas else vegas, seed, 1000 + k, 1, batch, G.dim)
         else:
-            x, w = flow.sample(seed, 1000 + k, 2, batch)
+            x, w = _flow_draw(flow, seed, 1000 + k, 2, batch, defensive)
         plan.run(seed, 1000 + k, points=x, point_w=w)
         tw = training_weights(plan.per_sample, value_roots)
         tw = torch.nan_to_num(tw, nan=0.0, posinf=0.0)
@@ -79,7 +86,7 @@ def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, e
     return losses
 
 
-def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3):
+def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3, defensive=0.0):
     """Per-sample variance of every root and seconds per sample for one sampler.
 
     VEGAS: the map is applied inside the integrand kernel.  Flow: the sampling
@@ -99,29 +106,31 @@ def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3):
         torch.cuda.synchronize()
         return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
     plan = api.EvalPlan([G], [params], [0], n, maps=[vegas] if vegas is not None else None)
-    x, w = flow.sample(seed, it, 3, n)
+    x, w = _flow_draw(flow, seed, it, 3, n, defensive)
     plan.run(seed, it, points=x, point_w=w)
     torch.cuda.synchronize()
     s, e = _events()
     s.record()
     for r in range(reps):
-        x, w = flow.sample(seed, it + 1 + r, 3, n)
+        x, w = _flow_draw(flow, seed, it + 1 + r, 3, n, defensive)
         st = plan.run(seed, it + 1 + r, points=x, point_w=w)
     e.record()
     torch.cuda.synchronize()
     return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
 
 
-def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True):
+def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True, defensive=0.0):
     """Variance-adjusted efficiency of flow vs VEGAS for the real part of `root`.
 
-    Each sampler draws `batches` independent batches of n samples; the
-    per-sample variance is the mean of the batch estimates (the integrand is
-    heavy-tailed, so single estimates scatter) and the batch means give the
-    combined estimate and its error.
+    Each sampler draws `batches` independent batches of n samples.  The
+    per-sample variance is estimated from all samples together (the mean of
+    the batch estimates) and, as a robust companion, by the median of the
+    batch estimates: the order-5 integrand is heavy-tailed, so a single rare
+    sample can dominate a batch's estimate.  The batch means give the combined
+    estimate and its error.
     """
     res = {}
-    flow_kw = dict(flow=flow, vegas=vegas if on_vegas else None)
+    flow_kw = dict(flow=flow, vegas=vegas if on_vegas else None, defensive=defensive)
     for name, kw, it0 in (("vegas", dict(vegas=vegas), 50000), ("flow", flow_kw, 60000)):
         means, vars_, secs = [], [], []
         for b in range(batches):
@@ -133,14 +142,18 @@ def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True):
         t = float(np.mean(secs))
         m = float(np.mean(means))
         err = float(math.sqrt(v / (n * batches)))
-        res[name] = {"mean": m, "err": err, "var_per_sample": v, "var_batches": [float(x) for x in vars_],
-                     "batch_means": [float(x) for x in means], "samples_per_s": 1.0 / t}
+        res[name] = {"mean": m, "err": err, "var_per_sample": v, "var_median": float(np.median(vars_)),
+                     "var_batches": [float(x) for x in vars_], "batch_means": [float(x) for x in means],
+                     "samples_per_s": 1.0 / t}
     res["vegas"]["eff_samples_per_s"] = res["vegas"]["samples_per_s"]
     res["flow"]["eff_samples_per_s"] = res["flow"]["samples_per_s"] * res["vegas"]["var_per_sample"] / \
         res["flow"]["var_per_sample"]
     res["flow_over_vegas"] = res["flow"]["eff_samples_per_s"] / res["vegas"]["eff_samples_per_s"]
+    res["flow_over_vegas_median"] = (res["flow"]["samples_per_s"] / res["vegas"]["samples_per_s"] *
+                                     res["vegas"]["var_median"] / res["flow"]["var_median"])
     res["means_agree_sigma"] = abs(res["flow"]["mean"] - res["vegas"]["mean"]) / math.sqrt(
         res["flow"]["err"] ** 2 + res["vegas"]["err"] ** 2)
+    res["defensive_share"] = defensive
     return res
 
 

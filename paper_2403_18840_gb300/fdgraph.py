@@ -822,6 +822,92 @@ def _g_family_flops(M, dk):
     return f
 
 
+def _leaf_work(w):
+    op = w & 63
+    mask = (w >> 20) & 16383
+    terms = sum(1 for j in range(7) if (mask >> (2 * j)) & 3)
+    M = (w >> 40) & 7
+    dk = (w >> 43) & 1
+    flops = 3 * max(terms - 1, 0) + 5
+    if op == OP_GLEAF:
+        return flops + 1 + 4 + _g_family_flops(M, dk), 3
+    return flops + 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0), 1
+
+
+def specialised_work(data, root_units=True):
+    """(fp32_flops, sfu_ops) per sample executed by the specialised kernel.
+
+    The kernel evaluates every root-accumulate slice of the tape as straight-line
+    code; leaves shared between slices are recomputed in each compilation unit
+    (one unit per root with root_units, else one per slice), so the leaf work
+    exceeds the tape's.  Same counting rule as tape_work.
+    """
+    hdr = struct.unpack("<16I", data[:64])
+    order, dim, n_roots, n_instr, ins_off = hdr[2], hdr[3], hdr[4], hdr[6], hdr[8]
+    words = struct.unpack("<%dQ" % n_instr, data[ins_off:ins_off + 8 * n_instr])
+    ins = []                     # (op, word index, bundle size)
+    k = 0
+    while k < n_instr:
+        op = words[k] & 63
+        if op == OP_BUNDLE:
+            n = (words[k] >> 6) & 15
+            ins.append((op, k, n))
+            k += n + 1
+            continue
+        if op == OP_END:
+            break
+        if op != OP_NOP:
+            ins.append((op, k, 0))
+        k += 1
+    units = []                   # per unit: set of (instr, member) FMAs and set of leaf instrs
+    root = 0
+    for i, (op, wk, _) in enumerate(ins):
+        if op == OP_RFLUSH:
+            root += 1
+            continue
+        if op != OP_RACC:
+            continue
+        need = {(words[wk] >> 20) & 16383}
+        fmas, leaves = set(), set()
+        for j in range(i - 1, -1, -1):
+            oj, wj, nj = ins[j]
+            if oj == OP_BUNDLE:
+                kept = [q for q in range(nj) if (words[wj + 1 + q] & 0xFFFF) in need]
+                for q in kept:
+                    need.discard(words[wj + 1 + q] & 0xFFFF)
+                for q in kept:
+                    m = words[wj + 1 + q]
+                    need.update(((m >> 16) & 0xFFFF, (m >> 32) & 0xFFFF, m >> 48))
+                    fmas.add((j, q))
+            elif oj in (OP_GLEAF, OP_VLEAF):
+                w = words[wj]
+                d = (w >> 6) & 16383
+                no = (((w >> 40) & 7) + 1) * (2 if (w >> 43) & 1 else 1)
+                if any(d + q in need for q in range(no)):
+                    need.difference_update(range(d, d + no))
+                    leaves.add(j)
+            elif oj == OP_CONST:
+                need.discard((words[wj] >> 6) & 16383)
+        if root_units and units and units[-1][0] == root:
+            units[-1][1].update(fmas)
+            units[-1][2].update(leaves)
+        else:
+            units.append((root, fmas, leaves))
+    flops = sfu = 0
+    for _, fmas, leaves in units:
+        for (j, q) in fmas:
+            m = words[ins[j][1] + 1 + q]
+            flops += 1 if ((m >> 48) == 0 or ((m >> 32) & 0xFFFF) == 1) else 2
+        for j in leaves:
+            f, u = _leaf_work(words[ins[j][1]])
+            flops += f
+            sfu += u
+    n_racc = sum(1 for op, _, _ in ins if op == OP_RACC)
+    flops += 4 * n_racc + 6 * dim + 14 * order + 3 * (order - 1) + 2 * n_roots
+    sfu += 2 * order + (order - 1)
+    return flops, sfu
+
+
 def tape_work(data):
     """(fp32_flops, sfu_ops) per sample of a serialised tape, map and weighting included.
 
@@ -851,17 +937,9 @@ def tape_work(data):
             k += 1 + n
             continue
         if op in (OP_GLEAF, OP_VLEAF):
-            mask = (w >> 20) & 16383
-            terms = sum(1 for j in range(7) if (mask >> (2 * j)) & 3)
-            M = (w >> 40) & 7
-            dk = (w >> 43) & 1
-            flops += 3 * max(terms - 1, 0) + 5
-            if op == OP_GLEAF:
-                flops += 1 + 4 + _g_family_flops(M, dk)
-                sfu += 3
-            else:
-                flops += 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0)
-                sfu += 1
+            f, u = _leaf_work(w)
+            flops += f
+            sfu += u
         elif op == OP_RACC:
             flops += 4
         k += 1

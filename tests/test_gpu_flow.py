@@ -56,6 +56,31 @@ def test_sample_parity(api):
     assert dl.max() < 2e-2 and np.quantile(dl, 0.99) < 2e-3
 
 
+def test_defensive_mixture_parity(api):
+    # samples [0, n - n_u): flow; [n - n_u, n): uniform; w = 1 / ((1 - a) q + a), a = n_u / n
+    F, blob = _flow(api)
+    n = 3000
+    x, w, a = F.sample_defensive(21, 2, 3, n, 0.25)
+    torch.cuda.synchronize()
+    n_u = n - 2304                      # flow share n - floor(0.25 n) = 2250 rounded up to 256s
+    assert a == n_u / n
+    nf = n - n_u
+    u = ophilox.uniforms(21, 2, 3, np.arange(n), D)
+    xr = u.copy()
+    xr[:, :nf], lq_f = oflow.forward(blob, u[:, :nf], D, K, H)
+    _, lq_u = oflow.inverse(blob, u[:, nf:], D, K, H)
+    lq = np.concatenate([lq_f, lq_u])
+    wr = 1.0 / ((1.0 - a) * np.exp(lq) + a)
+    xg = x.cpu().numpy().astype(np.float64)
+    wg = w.cpu().numpy().astype(np.float64)
+    assert np.array_equal(xg[:, nf:], u[:, nf:])                 # uniform share is the stream itself
+    assert np.abs(xg[:, :nf] - xr[:, :nf]).max() < 2e-3
+    rel = np.abs(wg / wr - 1.0)
+    print("defensive: max rel w %.3e p99 %.3e" % (rel.max(), np.quantile(rel, 0.99)))
+    assert rel.max() < 2e-2 and np.quantile(rel, 0.99) < 2e-3
+    assert np.all(wg <= 1.0 / a * (1 + 1e-6))
+
+
 def test_log_density_parity_and_consistency(api):
     F, blob = _flow(api)
     n = 2500
