@@ -209,7 +209,7 @@ def run_ours(args, rank, world, dist):
     G, tuned = autotune.tuned_jit_graph(order, roots, params[0])
     # algorithmic work: every leaf family computed once (no recomputation)
     flops_ps, sfu_ps = fdgraph.tape_work(api.tape_bytes(order, roots, budget=1 << 13, bundle=1, window=1))
-    exec_flops_ps, exec_sfu_ps = fdgraph.specialised_work(G.tape, tuned["root_units"])
+    exec_flops_ps, exec_sfu_ps = fdgraph.specialised_work(G.tape, tuned.get("root_units", True))
     V = api.Vegas(G.dim, WL["n_bins"])
     n = args.samples
     plan = api.EvalPlan([G], params, [0], n, maps=[V])
@@ -293,9 +293,7 @@ def run_ours(args, rank, world, dist):
                    "lam_over_kF": WL["lam_over_kF"], "T_over_TF": WL["T_over_TF"], "roots": len(roots),
                    "dim": G.dim, "samples_per_step": n, "sampler": "vegas", "n_bins": WL["n_bins"],
                    "tape_instr": G.n_instr,
-                   "kernel_variant": {k: tuned.get(k) for k in ("threads", "min_blocks", "root_units", "sync_every",
-                                                               "leaf_calls", "spt", "regs",
-                                                             "local_bytes")},
+                   "kernel_variant": {k: tuned.get(k) for k in autotune.JIT_KEYS + ("regs", "local_bytes")},
                    "l2": "256 MiB flush write between timed steps; inputs generated on device",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -89,29 +89,33 @@ fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_
 
 /* ---- specialised kernels (Sec. VI.A: graphs compiled once, evaluated in batches)
  * fd_graph_jit translates the graph's validated tape into straight-line CUDA
- * (one function per root-accumulate slice, intermediates in registers),
- * compiles it for the current device with NVRTC (modules compiled in
- * parallel and linked with nvJitLink when max_modules > 1 and the graph is
- * large) and from then on evaluates the graph's instances with it (one launch
- * per graph; graphs without one keep the interpreter).  threads in
- * {64, 128, 256}, min_blocks in 1..8 (launch bounds; registers are capped at
- * 65536 / (threads * min_blocks)).  root_units != 0: a split graph compiles
- * one function per root (the root's slices share their leaves) instead of
- * one function per slice.  sync_every > 0: a block barrier after about that
- * many generated arithmetic statements (the warps of a CTA then share
- * instruction-cache lines); 0 = none.  leaf_calls != 0: every leaf family
- * calls one out-of-line function per (Taylor order, d/dk) shape instead of
- * being inlined (smaller code, instruction-cache reuse, one call per leaf).
- * spt in 1..8: samples per thread per pass; with spt > 1 every compilation
- * unit (a root, or a slice of a large root) loops over the spt samples, so
- * its code is re-executed from the instruction cache.  cache_dir (may be NULL): directory for
- * compiled images, keyed by a hash of the generated source and options.
- * Synchronous; FD_ENOTSUP when the run-time compiler is unavailable or fails
- * (fd_last_error holds its log).  Results agree with the interpreter up to
- * FP32 rounding order. */
-fd_status fd_graph_jit(fd_graph *g, int32_t threads, int32_t min_blocks, int32_t max_modules,
-                       int32_t root_units, int32_t sync_every, int32_t leaf_calls, int32_t spt,
-                       const char *cache_dir);
+ * (the backward slice of every root-accumulate instruction, intermediates in
+ * registers), compiles it for the current device with NVRTC (modules
+ * compiled in parallel and linked with nvJitLink when the graph is large) and
+ * from then on evaluates the graph's instances with it (one launch per graph;
+ * graphs without one keep the interpreter).  Options:
+ *  threads      CTA size, 64, 128 or 256;
+ *  min_blocks   1..8, launch bounds; registers capped at 65536 / (threads * min_blocks);
+ *  max_modules  1..64, modules compiled in parallel for a large graph;
+ *  root_units   != 0: a split graph gets one function per root (its slices
+ *               share their leaves) instead of one per slice;
+ *  sync_every   > 0: a block barrier after about that many generated
+ *               arithmetic statements (warps share instruction-cache lines);
+ *  leaf_calls   != 0: leaf families are calls to one out-of-line function per
+ *               (Taylor order, d/dk) shape instead of inlined code;
+ *  spt          1..8 samples per thread per pass; with spt > 1 every
+ *               compilation unit loops over the spt samples, so its code is
+ *               re-executed from the instruction cache;
+ *  unit_cap     with spt > 1: consecutive slices of a root share a unit while
+ *               its cost (FMAs + 30 per distinct leaf) stays within the cap.
+ * cache_dir (may be NULL): directory for compiled images, keyed by a hash of
+ * the generated source and options.  Synchronous; FD_ENOTSUP when the
+ * run-time compiler is unavailable or fails (fd_last_error holds its log).
+ * Results agree with the interpreter up to FP32 rounding order. */
+typedef struct {
+    int32_t threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt, unit_cap;
+} fd_jit_options;
+fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const char *cache_dir);
 /* Switch evaluation of g between its specialised kernel (on != 0) and the interpreter. */
 fd_status fd_graph_jit_enable(fd_graph *g, int32_t on);
 /* info[6] = threads, min_blocks, registers per thread, local bytes per thread,
@@ -120,9 +124,8 @@ fd_status fd_graph_jit_info(const fd_graph *g, int32_t *info, double *compile_s)
 /* The generated source of module `module` for a serialised tape (no device
  * needed): copies at most cap - 1 bytes plus a terminating 0 into buf (may be
  * NULL), *len = full length, *n_modules = module count. */
-fd_status fd_jit_emit(const void *tape, size_t tape_len, int32_t threads, int32_t min_blocks,
-                      int32_t max_modules, int32_t root_units, int32_t sync_every, int32_t leaf_calls,
-                      int32_t spt, int32_t module, char *buf, int64_t cap, int64_t *len, int32_t *n_modules);
+fd_status fd_jit_emit(const void *tape, size_t tape_len, const fd_jit_options *opt, int32_t module, char *buf,
+                      int64_t cap, int64_t *len, int32_t *n_modules);
 
 /* ---- VEGAS map (Sec. IV, separable map q(x) = prod q_k(x_k)) ---------------
  * A map owns FP64 bin edges [dim][n_bins+1] (uniform at creation), their FP32

@@ -18,6 +18,11 @@ class FdError(RuntimeError):
         self.status = status
 
 
+class fd_jit_options(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("threads", "min_blocks", "max_modules", "root_units", "sync_every",
+                                              "leaf_calls", "spt", "unit_cap")]
+
+
 class fd_params(ctypes.Structure):
     _fields_ = [("k_ext", ctypes.c_double), ("k_F", ctypes.c_double), ("mu", ctypes.c_double),
                 ("beta", ctypes.c_double), ("Lambda", ctypes.c_double), ("k_cut", ctypes.c_double),
@@ -44,11 +49,11 @@ SIGNATURES = {
     "fd_graph_roots": (_i32, [_vp, _pi]),
     "fd_graph_free": (None, [_vp]),
     "fd_graph_set_launch": (_i32, [_vp, _i32, _i32]),
-    "fd_graph_jit": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _c.c_char_p]),
+    "fd_graph_jit": (_i32, [_vp, _c.POINTER(fd_jit_options), _c.c_char_p]),
     "fd_graph_jit_enable": (_i32, [_vp, _i32]),
     "fd_graph_jit_info": (_i32, [_vp, _pi, _c.POINTER(_c.c_double)]),
-    "fd_jit_emit": (_i32, [_vp, _c.c_size_t, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _c.c_char_p,
-                           _i64, _c.POINTER(_i64), _pi]),
+    "fd_jit_emit": (_i32, [_vp, _c.c_size_t, _c.POINTER(fd_jit_options), _i32, _c.c_char_p, _i64,
+                           _c.POINTER(_i64), _pi]),
     "fd_vegas_create": (_i32, [_i32, _i32, _c.POINTER(_vp)]),
     "fd_vegas_free": (None, [_vp]),
     "fd_vegas_set_edges": (_i32, [_vp, _pd]),

@@ -66,18 +66,25 @@ def tape_bytes(order, roots, budget=None, bundle=None, window=None):
     return data
 
 
-def jit_source(tape, threads=128, min_blocks=2, max_modules=1, module=0, root_units=True, sync_every=0,
-               leaf_calls=False, spt=1):
-    """Generated source of one module of the specialised kernel (no device needed)."""
+def jit_options(threads=128, min_blocks=2, max_modules=None, root_units=True, sync_every=0, leaf_calls=False, spt=1,
+                unit_cap=6000):
+    if max_modules is None:
+        max_modules = max(1, min(32, os.cpu_count() or 1))
+    return L.fd_jit_options(threads, min_blocks, max_modules, 1 if root_units else 0, sync_every,
+                            1 if leaf_calls else 0, spt, unit_cap)
+
+
+def jit_source(tape, module=0, **options):
+    """Generated source of one module of the specialised kernel (no device needed):
+    (text, module count).  Options as Graph.jit."""
+    opt = jit_options(**options)
     n = ctypes.c_int64()
     nm = ctypes.c_int32()
-    ru = 1 if root_units else 0
-    lc = 1 if leaf_calls else 0
-    L.check(L.lib().fd_jit_emit(tape, len(tape), threads, min_blocks, max_modules, ru, sync_every, lc, spt,
-                                module, None, 0, ctypes.byref(n), ctypes.byref(nm)))
+    L.check(L.lib().fd_jit_emit(tape, len(tape), ctypes.byref(opt), module, None, 0, ctypes.byref(n),
+                                ctypes.byref(nm)))
     buf = ctypes.create_string_buffer(n.value + 1)
-    L.check(L.lib().fd_jit_emit(tape, len(tape), threads, min_blocks, max_modules, ru, sync_every, lc, spt,
-                                module, buf, n.value + 1, ctypes.byref(n), ctypes.byref(nm)))
+    L.check(L.lib().fd_jit_emit(tape, len(tape), ctypes.byref(opt), module, buf, n.value + 1, ctypes.byref(n),
+                                ctypes.byref(nm)))
     return buf.value.decode(), nm.value
 
 
@@ -101,17 +108,16 @@ class Graph:
     def set_launch(self, threads=0, samples_per_thread=0):
         L.check(L.lib().fd_graph_set_launch(self.handle, threads, samples_per_thread))
 
-    def jit(self, threads=128, min_blocks=2, max_modules=None, root_units=True, sync_every=0, leaf_calls=False,
-            spt=1, cache=True):
+    def jit(self, cache=True, **options):
         """Compile the specialised straight-line kernel (cached under _build/jit)
-        and evaluate this graph with it from now on."""
-        if max_modules is None:
-            max_modules = max(1, min(32, os.cpu_count() or 1))
+        and evaluate this graph with it from now on.  Options (fd_jit_options):
+        threads, min_blocks, max_modules, root_units, sync_every, leaf_calls,
+        spt, unit_cap."""
+        opt = jit_options(**options)
         cdir = _JIT_DIR if cache else None
         if cdir:
             os.makedirs(cdir, exist_ok=True)
-        L.check(L.lib().fd_graph_jit(self.handle, threads, min_blocks, max_modules, 1 if root_units else 0,
-                                     sync_every, 1 if leaf_calls else 0, spt, cdir.encode() if cdir else None))
+        L.check(L.lib().fd_graph_jit(self.handle, ctypes.byref(opt), cdir.encode() if cdir else None))
         return self.jit_info()
 
     def jit_enable(self, on=True):

@@ -22,9 +22,11 @@ from . import api
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 SCHEDULES = [dict(budget=b, bundle=w, window=8 * w) for b in (96, 128, 160) for w in (4, 8)]
 SHAPES = [(128, 2), (256, 1), (128, 1), (64, 2)]
-# (threads, min_blocks, root_units, sync_every, leaf_calls, samples per thread)
-JIT_VARIANTS = [(256, 1, True, 0, False, 1), (256, 1, True, 0, False, 2), (256, 1, True, 0, False, 4),
-                (256, 1, False, 0, False, 4)]
+# specialised-kernel variants (fd_jit_options; unlisted options at their defaults)
+JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=1), dict(threads=256, min_blocks=1, spt=2, unit_cap=12000),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=6000)]
+JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap")
 
 
 def _key(order, roots):
@@ -102,21 +104,20 @@ def _store(key, best):
 
 def _jit_graph(order, roots, v):
     G = api.Graph(order, roots=roots, budget=1 << 13)
-    G.jit(threads=v["threads"], min_blocks=v["min_blocks"], root_units=v["root_units"],
-          sync_every=v.get("sync_every", 0), leaf_calls=v.get("leaf_calls", False), spt=v.get("spt", 1))
+    G.jit(**{k: v[k] for k in JIT_KEYS if k in v})
     return G
 
 
 def tune_jit(order, roots, params, n_samples=1 << 23, variants=None, force=False, log=None):
     """Best {'threads','min_blocks','root_units','sync_every','leaf_calls','spt','samples_per_s',...} for the
     specialised kernel."""
-    key = "jit2|" + _key(order, roots)
+    key = "jit3|" + _key(order, roots)
     cache = _load()
     if key in cache and not force:
         return cache[key]
     results = []
-    for (t, mb, ru, se, lc, spt) in variants or JIT_VARIANTS:
-        v = dict(threads=t, min_blocks=mb, root_units=ru, sync_every=se, leaf_calls=lc, spt=spt)
+    for v in variants or JIT_VARIANTS:
+        v = dict(v)
         try:
             G = _jit_graph(order, roots, v)
             ms = _time(G, params, n_samples)

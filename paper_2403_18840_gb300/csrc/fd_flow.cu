@@ -77,6 +77,17 @@ __device__ __forceinline__ void bfrag(const __nv_bfloat16 *W, int ld, int kt, in
     b0 = *reinterpret_cast<const uint32_t *>(p);
     b1 = *reinterpret_cast<const uint32_t *>(p + 8);
 }
+// B fragments of n-tiles nt0 and nt0 + 1 at k-step kt with one ldmatrix.x4
+// (W row-major [n][k], rows 16-byte aligned): lanes 8m..8m+7 address row r of
+// 8x8 matrix m = (n-tile nt0 + m/2, k half m%2); b[0..1] belong to nt0, b[2..3]
+// to nt0 + 1, in the register order of the m16n8k16 B operand.
+__device__ __forceinline__ void bfrag2(const __nv_bfloat16 *W, int ld, int kt, int nt0, int lane, uint32_t (&b)[4]) {
+    const int m = lane >> 3, r = lane & 7;
+    const __nv_bfloat16 *p = W + ((nt0 + (m >> 1)) * 8 + r) * ld + kt * 16 + (m & 1) * 8;
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
 // B fragment of B[k][n] = W[k][n] (W row-major [k][n]: transposed access)
 __device__ __forceinline__ void bfrag_t(const __nv_bfloat16 *W, int ld, int kt, int nt, int g, int t, uint32_t &b0,
                                         uint32_t &b1) {
@@ -113,14 +124,14 @@ __device__ __forceinline__ LayerSmem layer_view(const unsigned char *base) {
 // h1, h2 as A fragments (post-ReLU, BF16) and o = [s_raw | t] accumulators.
 __device__ __forceinline__ void mlp_forward(const LayerSmem &L, const uint32_t (&ain)[4], uint32_t (&h1a)[8][4],
                                             uint32_t (&h2a)[8][4], float (&o)[4][4], int g, int t) {
+    const int lane = g * 4 + t;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
-        uint32_t b0, b1;
-        bfrag(L.W1, W1_LD, 0, 2 * j, g, t, b0, b1);
-        mma16816(c0, ain, b0, b1);
-        bfrag(L.W1, W1_LD, 0, 2 * j + 1, g, t, b0, b1);
-        mma16816(c1, ain, b0, b1);
+        uint32_t b[4];
+        bfrag2(L.W1, W1_LD, 0, 2 * j, lane, b);
+        mma16816(c0, ain, b[0], b[1]);
+        mma16816(c1, ain, b[2], b[3]);
         const float u0 = L.b1[16 * j + 2 * t], u1 = L.b1[16 * j + 2 * t + 1];
         const float u2 = L.b1[16 * j + 8 + 2 * t], u3 = L.b1[16 * j + 9 + 2 * t];
         c0[0] = fmaxf(c0[0] + u0, 0.f);
@@ -133,19 +144,29 @@ __device__ __forceinline__ void mlp_forward(const LayerSmem &L, const uint32_t (
         c1[3] = fmaxf(c1[3] + u3, 0.f);
         c_to_a(c0, c1, h1a[j]);
     }
+    // second layer: k-steps outer, all 16 n-tiles accumulated side by side
+    // (16 independent MMA chains in flight per warp)
+    float c[16][4];
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[nt][q] = 0.f;
+    }
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            uint32_t b[4];
+            bfrag2(L.W2, W2_LD, kt, 2 * j, lane, b);
+            mma16816(c[2 * j], h1a[kt], b[0], b[1]);
+            mma16816(c[2 * j + 1], h1a[kt], b[2], b[3]);
+        }
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kt = 0; kt < 8; ++kt) {
-            uint32_t b0, b1;
-            bfrag(L.W2, W2_LD, kt, 2 * j, g, t, b0, b1);
-            mma16816(c0, h1a[kt], b0, b1);
-            bfrag(L.W2, W2_LD, kt, 2 * j + 1, g, t, b0, b1);
-            mma16816(c1, h1a[kt], b0, b1);
-        }
         const float u0 = L.b2[16 * j + 2 * t], u1 = L.b2[16 * j + 2 * t + 1];
         const float u2 = L.b2[16 * j + 8 + 2 * t], u3 = L.b2[16 * j + 9 + 2 * t];
+        float *c0 = c[2 * j], *c1 = c[2 * j + 1];
         c0[0] = fmaxf(c0[0] + u0, 0.f);
         c0[1] = fmaxf(c0[1] + u1, 0.f);
         c0[2] = fmaxf(c0[2] + u0, 0.f);
@@ -154,18 +175,25 @@ __device__ __forceinline__ void mlp_forward(const LayerSmem &L, const uint32_t (
         c1[1] = fmaxf(c1[1] + u3, 0.f);
         c1[2] = fmaxf(c1[2] + u2, 0.f);
         c1[3] = fmaxf(c1[3] + u3, 0.f);
-        c_to_a(c0, c1, h2a[j]);
+        c_to_a(c[2 * j], c[2 * j + 1], h2a[j]);
     }
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) o[nt][q] = 0.f;
+    }
 #pragma unroll
-        for (int kt = 0; kt < 8; ++kt) {
-            uint32_t b0, b1;
-            bfrag(L.W3, W3_LD, kt, nt, g, t, b0, b1);
-            mma16816(o[nt], h2a[kt], b0, b1);
-        }
+    for (int kt = 0; kt < 8; ++kt) {
+        uint32_t b[4];
+        bfrag2(L.W3, W3_LD, kt, 0, lane, b);
+        mma16816(o[0], h2a[kt], b[0], b[1]);
+        mma16816(o[1], h2a[kt], b[2], b[3]);
+        bfrag2(L.W3, W3_LD, kt, 2, lane, b);
+        mma16816(o[2], h2a[kt], b[0], b[1]);
+        mma16816(o[3], h2a[kt], b[2], b[3]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
         const float u0 = L.b3[nt * 8 + 2 * t], u1 = L.b3[nt * 8 + 2 * t + 1];
         o[nt][0] += u0;
         o[nt][1] += u1;

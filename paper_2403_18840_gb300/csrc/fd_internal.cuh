@@ -67,6 +67,7 @@ struct fd_graph {
     cudaLibrary_t jit_lib = nullptr;
     cudaKernel_t jit_kernel = nullptr;
     int jit_threads = 0, jit_min_blocks = 0, jit_regs = 0, jit_local_bytes = 0, jit_modules = 0, jit_per_sm = 1;
+    int jit_spt = 1;
     double jit_compile_s = 0.0;
     bool jit_enabled = false;       // evaluation uses the specialised kernel
 };

@@ -360,8 +360,8 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
                           int leaf_calls);
 
 Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units, int sync_every,
-                     int leaf_calls, int spt = 1) {
-    if (spt > 1) return emit_program_loop(g, T, min_blocks, max_modules, spt, root_units ? 6000.0 : 0.0, leaf_calls);
+                     int leaf_calls, int spt = 1, int unit_cap = 6000) {
+    if (spt > 1) return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls);
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -491,26 +491,36 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
     std::vector<Slice> sl = make_slices(ins, g.h_tape, (int)h.n_slots);
     double total = 0;
     for (auto &s : sl) total += s.cost();
-    // units: all slices of a root, unless the root costs more than unit_cap
+    // units: consecutive slices of one root packed while the unit's cost
+    // (FMAs + 30 per distinct leaf, the leaves shared inside the unit) stays
+    // within unit_cap; a unit's code is re-executed for the spt samples
     std::vector<Unit> units;
-    for (size_t i = 0; i < sl.size();) {
-        size_t j = i;
+    auto unit_cost = [&](const std::vector<int> &slices) {
+        std::vector<uint32_t> leaves;
         double c = 0;
-        while (j < sl.size() && sl[j].root == sl[i].root) c += sl[j++].cost();
-        if (c > unit_cap) {
-            for (size_t q = i; q < j; ++q) {
-                units.emplace_back();
-                units.back().root = sl[q].root;
-                units.back().slices.push_back((int)q);
-                units.back().cost = sl[q].cost();
-            }
-        } else {
-            units.emplace_back();
-            units.back().root = sl[i].root;
-            for (size_t q = i; q < j; ++q) units.back().slices.push_back((int)q);
-            units.back().cost = c;
+        for (int i : slices) {
+            c += sl[i].n_fma;
+            for (auto &kv : sl[i].keep)
+                if (ins[kv.first].op == OP_GLEAF || ins[kv.first].op == OP_VLEAF) leaves.push_back(kv.first);
         }
-        i = j;
+        std::sort(leaves.begin(), leaves.end());
+        return c + 30.0 * (double)(std::unique(leaves.begin(), leaves.end()) - leaves.begin());
+    };
+    for (size_t i = 0; i < sl.size(); ++i) {
+        if (!units.empty() && units.back().root == sl[i].root) {
+            std::vector<int> grown = units.back().slices;
+            grown.push_back((int)i);
+            const double c = unit_cost(grown);
+            if (c <= unit_cap) {
+                units.back().slices = grown;
+                units.back().cost = c;
+                continue;
+            }
+        }
+        units.emplace_back();
+        units.back().root = sl[i].root;
+        units.back().slices.push_back((int)i);
+        units.back().cost = unit_cost(units.back().slices);
     }
     int n_mod = 1;
     if (total > kSingleModuleCost && max_modules > 1)
@@ -684,20 +694,33 @@ fd_status jit_launch(const fd_graph *g, const EvalArgs &args, cudaStream_t strea
     return FD_OK;
 }
 
-extern "C" fd_status fd_jit_emit(const void *tape, size_t tape_len, int32_t threads, int32_t min_blocks,
-                                 int32_t max_modules, int32_t root_units, int32_t sync_every, int32_t leaf_calls,
-                                 int32_t spt, int32_t module, char *buf, int64_t cap, int64_t *len,
-                                 int32_t *n_modules) {
+namespace {
+fd_status check_options(const fd_jit_options *o) {
+    FD_REQUIRE(o, "options are required");
+    FD_REQUIRE(o->threads == 64 || o->threads == 128 || o->threads == 256, "threads must be 64, 128 or 256");
+    FD_REQUIRE(o->min_blocks >= 1 && o->min_blocks <= 8, "min_blocks must be in 1..8");
+    FD_REQUIRE(o->max_modules >= 1 && o->max_modules <= 64, "max_modules must be in 1..64");
+    FD_REQUIRE(o->sync_every >= 0, "sync_every must be >= 0");
+    FD_REQUIRE(o->spt >= 1 && o->spt <= 8, "samples per thread must be in 1..8");
+    FD_REQUIRE(o->unit_cap >= 0, "unit_cap must be >= 0");
+    return FD_OK;
+}
+
+Program emit(const fd_graph &g, const fd_jit_options &o) {
+    return emit_program(g, o.threads, o.min_blocks, o.max_modules, o.root_units, o.sync_every, o.leaf_calls, o.spt,
+                        o.unit_cap);
+}
+}  // namespace
+
+extern "C" fd_status fd_jit_emit(const void *tape, size_t tape_len, const fd_jit_options *opt, int32_t module,
+                                 char *buf, int64_t cap, int64_t *len, int32_t *n_modules) {
     FD_REQUIRE(tape, "tape is required");
-    FD_REQUIRE(threads == 64 || threads == 128 || threads == 256, "threads must be 64, 128 or 256");
-    FD_REQUIRE(min_blocks >= 1 && min_blocks <= 8, "min_blocks must be in 1..8");
-    FD_REQUIRE(max_modules >= 1 && max_modules <= 64, "max_modules must be in 1..64");
-    FD_REQUIRE(sync_every >= 0, "sync_every must be >= 0");
-    FD_REQUIRE(spt >= 1 && spt <= 8, "samples per thread must be in 1..8");
+    const fd_status so = check_options(opt);
+    if (so != FD_OK) return so;
     fd_graph g;
     const fd_status st = graph_from_tape(tape, tape_len, g);
     if (st != FD_OK) return st;
-    const Program P = emit_program(g, threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt);
+    const Program P = emit(g, *opt);
     if (n_modules) *n_modules = P.n_modules;
     FD_REQUIRE(module >= 0 && module < P.n_modules, "module out of range");
     const std::string &s = P.modules[module];
@@ -710,26 +733,22 @@ extern "C" fd_status fd_jit_emit(const void *tape, size_t tape_len, int32_t thre
     return FD_OK;
 }
 
-extern "C" fd_status fd_graph_jit(fd_graph *g, int32_t threads, int32_t min_blocks, int32_t max_modules,
-                                  int32_t root_units, int32_t sync_every, int32_t leaf_calls, int32_t spt,
-                                  const char *cache_dir) {
+extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const char *cache_dir) {
     FD_REQUIRE(g, "null graph");
-    FD_REQUIRE(threads == 64 || threads == 128 || threads == 256, "threads must be 64, 128 or 256");
-    FD_REQUIRE(min_blocks >= 1 && min_blocks <= 8, "min_blocks must be in 1..8");
-    FD_REQUIRE(max_modules >= 1 && max_modules <= 64, "max_modules must be in 1..64");
-    FD_REQUIRE(sync_every >= 0, "sync_every must be >= 0");
-    FD_REQUIRE(spt >= 1 && spt <= 8, "samples per thread must be in 1..8");
+    const fd_status so = check_options(opt);
+    if (so != FD_OK) return so;
+    const int threads = opt->threads, min_blocks = opt->min_blocks;
     int dev = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
     FD_REQUIRE(dev == g->device, "graph belongs to another device");
     const auto t0 = std::chrono::steady_clock::now();
     const int maxrreg = std::min(255, (65536 / (threads * min_blocks)) & ~7);
-    const Program P = emit_program(*g, threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt);
+    const Program P = emit(*g, *opt);
     // cache key: generator version, launch shape, register cap and every module's source
     uint64_t key = fnv1a(&kJitVersion, sizeof kJitVersion);
     key = fnv1a(kRuntimeHeader, sizeof kRuntimeHeader, key);
-    const int32_t shape[7] = {threads, min_blocks, maxrreg, root_units, sync_every, leaf_calls, spt};
-    key = fnv1a(shape, sizeof shape, key);
+    key = fnv1a(opt, sizeof *opt, key);
+    key = fnv1a(&maxrreg, sizeof maxrreg, key);
     for (const auto &m : P.modules) key = fnv1a(m.data(), m.size(), key);
     std::string path;
     std::vector<char> cubin;
@@ -775,6 +794,7 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, int32_t threads, int32_t min_bloc
     g->jit_regs = attr.numRegs;
     g->jit_local_bytes = (int)attr.localSizeBytes;
     g->jit_modules = P.n_modules;
+    g->jit_spt = opt->spt;
     g->jit_compile_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     g->jit_enabled = true;
     return FD_OK;

@@ -19,7 +19,7 @@ def _tape(order, with_dk):
 
 def test_small_graph_is_one_module_with_every_root_flushed():
     tape = _tape(2, True)
-    src, n_mod = api.jit_source(tape, 128, 2, 8, 0)
+    src, n_mod = api.jit_source(tape, 0, threads=128, min_blocks=2, max_modules=8)
     assert n_mod == 1
     roots = fdgraph.graph_roots(2, with_dk=True)
     flushes = re.findall(r"flush<(\d+), (\d+), (\d+)>", src)
@@ -31,7 +31,7 @@ def test_small_graph_is_one_module_with_every_root_flushed():
 
 @pytest.mark.skipif(shutil.which("nvcc") is None, reason="nvcc not available")
 def test_generated_source_compiles(tmp_path):
-    src, _ = api.jit_source(_tape(2, True), 128, 2, 1, 0)
+    src, _ = api.jit_source(_tape(2, True), 0, threads=128, min_blocks=2, max_modules=1)
     f = tmp_path / "m0.cu"
     f.write_text(src)
     r = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-cubin",
@@ -42,13 +42,13 @@ def test_generated_source_compiles(tmp_path):
 @pytest.mark.parametrize("root_units", [False, True])
 def test_large_graph_splits_into_linked_modules(root_units):
     tape = _tape(5, False)
-    _, n_mod = api.jit_source(tape, 128, 2, 8, 0, root_units)
+    _, n_mod = api.jit_source(tape, 0, threads=128, min_blocks=2, max_modules=8, root_units=root_units)
     assert 2 <= n_mod <= 8
     unit = "fd_r" if root_units else "fd_s"
     ret = "float2" if root_units else "float"
     defined, declared, slices = [], set(), []
     for m in range(n_mod):
-        src, _ = api.jit_source(tape, 128, 2, 8, m, root_units)
+        src, _ = api.jit_source(tape, m, threads=128, min_blocks=2, max_modules=8, root_units=root_units)
         defined += re.findall(r'extern "C" __device__ __noinline__ %s (%s\d+)\(' % (ret, unit), src)
         declared |= set(re.findall(r'extern "C" __device__ %s (%s\d+)\(const FdSV &V' % (ret, unit), src))
         slices += re.findall(r"__device__ __\w+__ float (fd_s\d+)\(const FdSV &V\) \{", src)
@@ -56,8 +56,31 @@ def test_large_graph_splits_into_linked_modules(root_units):
     assert len(defined) == len(set(defined))
     assert declared <= set(defined)
     assert len(slices) == len(set(slices))            # every slice emitted exactly once
-    body, _ = api.jit_source(tape, 128, 2, 8, 0, root_units)
+    body, _ = api.jit_source(tape, 0, threads=128, min_blocks=2, max_modules=8, root_units=root_units)
     called = set(re.findall(r"= (%s\d+)\(V" % unit, body))
     assert called == set(defined)
     if root_units:
         assert len(defined) == len(fdgraph.graph_roots(5))
+
+
+@pytest.mark.parametrize("unit_cap", [0, 6000, 100000])
+def test_sample_loop_units_cover_every_slice_once(unit_cap):
+    # spt > 1: units pack consecutive slices of one root; every slice emitted
+    # once, every unit called once, every root flushed once per sample
+    tape = _tape(5, False)
+    kw = dict(threads=256, min_blocks=1, max_modules=8, spt=4, unit_cap=unit_cap)
+    _, n_mod = api.jit_source(tape, 0, **kw)
+    slices, units = [], []
+    for m in range(n_mod):
+        src, _ = api.jit_source(tape, m, **kw)
+        slices += re.findall(r"__device__ __forceinline__ float (fd_s\d+)\(const FdSV &V\) \{", src)
+        units += re.findall(r"__device__ __noinline__ void (fd_u\d+)\(", src)
+    body, _ = api.jit_source(tape, 0, **kw)
+    assert len(slices) == len(set(slices))
+    assert sorted(re.findall(r"(fd_u\d+)\(V, cs, sn, re, im\)", body)) == sorted(units)
+    flushes = re.findall(r"flush<(\d+), ", body)
+    assert sorted(int(r) for r in flushes) == list(range(len(fdgraph.graph_roots(5))))
+    if unit_cap == 0:
+        assert len(units) == len(slices)             # one slice per unit
+    if unit_cap == 100000:
+        assert len(units) == len(fdgraph.graph_roots(5))   # one unit per root
