@@ -97,6 +97,19 @@ __device__ __forceinline__ void bfrag_t(const __nv_bfloat16 *W, int ld, int kt, 
 }
 
 // accumulator tiles (2j, 2j+1) -> A fragment of k-tile j
+// ReLU and round two FP32 values to a packed BF16 pair (lo in the low half)
+__device__ __forceinline__ uint32_t relu_pack(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+// accumulators of n-tiles (2j, 2j+1) -> A fragment of the next layer, with ReLU
+__device__ __forceinline__ void c_to_a_relu(const float (&c0)[4], const float (&c1)[4], uint32_t (&a)[4]) {
+    a[0] = relu_pack(c0[0], c0[1]);
+    a[1] = relu_pack(c0[2], c0[3]);
+    a[2] = relu_pack(c1[0], c1[1]);
+    a[3] = relu_pack(c1[2], c1[3]);
+}
 __device__ __forceinline__ void c_to_a(const float (&c0)[4], const float (&c1)[4], uint32_t (&a)[4]) {
     a[0] = pack_bf16(c0[0], c0[1]);
     a[1] = pack_bf16(c0[2], c0[3]);
@@ -122,35 +135,38 @@ __device__ __forceinline__ LayerSmem layer_view(const unsigned char *base) {
 
 // MLP on one 16-sample tile: input A fragment (16 x 16, zero-padded) ->
 // h1, h2 as A fragments (post-ReLU, BF16) and o = [s_raw | t] accumulators.
+// Forward MLP of one 16-row tile: accumulators start at the bias (the MMA adds
+// the products to it), ReLU and the BF16 rounding of the next layer's A
+// fragment are one cvt per pair.
 __device__ __forceinline__ void mlp_forward(const LayerSmem &L, const uint32_t (&ain)[4], uint32_t (&h1a)[8][4],
                                             uint32_t (&h2a)[8][4], float (&o)[4][4], int g, int t) {
     const int lane = g * 4 + t;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+        const float u0 = L.b1[16 * j + 2 * t], u1 = L.b1[16 * j + 2 * t + 1];
+        const float u2 = L.b1[16 * j + 8 + 2 * t], u3 = L.b1[16 * j + 9 + 2 * t];
+        float c0[4] = {u0, u1, u0, u1}, c1[4] = {u2, u3, u2, u3};
         uint32_t b[4];
         bfrag2(L.W1, W1_LD, 0, 2 * j, lane, b);
         mma16816(c0, ain, b[0], b[1]);
         mma16816(c1, ain, b[2], b[3]);
-        const float u0 = L.b1[16 * j + 2 * t], u1 = L.b1[16 * j + 2 * t + 1];
-        const float u2 = L.b1[16 * j + 8 + 2 * t], u3 = L.b1[16 * j + 9 + 2 * t];
-        c0[0] = fmaxf(c0[0] + u0, 0.f);
-        c0[1] = fmaxf(c0[1] + u1, 0.f);
-        c0[2] = fmaxf(c0[2] + u0, 0.f);
-        c0[3] = fmaxf(c0[3] + u1, 0.f);
-        c1[0] = fmaxf(c1[0] + u2, 0.f);
-        c1[1] = fmaxf(c1[1] + u3, 0.f);
-        c1[2] = fmaxf(c1[2] + u2, 0.f);
-        c1[3] = fmaxf(c1[3] + u3, 0.f);
-        c_to_a(c0, c1, h1a[j]);
+        c_to_a_relu(c0, c1, h1a[j]);
     }
     // second layer: k-steps outer, all 16 n-tiles accumulated side by side
     // (16 independent MMA chains in flight per warp)
     float c[16][4];
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) c[nt][q] = 0.f;
+    for (int j = 0; j < 8; ++j) {
+        const float u0 = L.b2[16 * j + 2 * t], u1 = L.b2[16 * j + 2 * t + 1];
+        const float u2 = L.b2[16 * j + 8 + 2 * t], u3 = L.b2[16 * j + 9 + 2 * t];
+        c[2 * j][0] = u0;
+        c[2 * j][1] = u1;
+        c[2 * j][2] = u0;
+        c[2 * j][3] = u1;
+        c[2 * j + 1][0] = u2;
+        c[2 * j + 1][1] = u3;
+        c[2 * j + 1][2] = u2;
+        c[2 * j + 1][3] = u3;
     }
 #pragma unroll
     for (int kt = 0; kt < 8; ++kt) {
@@ -163,24 +179,14 @@ __device__ __forceinline__ void mlp_forward(const LayerSmem &L, const uint32_t (
         }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float u0 = L.b2[16 * j + 2 * t], u1 = L.b2[16 * j + 2 * t + 1];
-        const float u2 = L.b2[16 * j + 8 + 2 * t], u3 = L.b2[16 * j + 9 + 2 * t];
-        float *c0 = c[2 * j], *c1 = c[2 * j + 1];
-        c0[0] = fmaxf(c0[0] + u0, 0.f);
-        c0[1] = fmaxf(c0[1] + u1, 0.f);
-        c0[2] = fmaxf(c0[2] + u0, 0.f);
-        c0[3] = fmaxf(c0[3] + u1, 0.f);
-        c1[0] = fmaxf(c1[0] + u2, 0.f);
-        c1[1] = fmaxf(c1[1] + u3, 0.f);
-        c1[2] = fmaxf(c1[2] + u2, 0.f);
-        c1[3] = fmaxf(c1[3] + u3, 0.f);
-        c_to_a(c[2 * j], c[2 * j + 1], h2a[j]);
-    }
+    for (int j = 0; j < 8; ++j) c_to_a_relu(c[2 * j], c[2 * j + 1], h2a[j]);
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) o[nt][q] = 0.f;
+        const float u0 = L.b3[nt * 8 + 2 * t], u1 = L.b3[nt * 8 + 2 * t + 1];
+        o[nt][0] = u0;
+        o[nt][1] = u1;
+        o[nt][2] = u0;
+        o[nt][3] = u1;
     }
 #pragma unroll
     for (int kt = 0; kt < 8; ++kt) {
@@ -191,14 +197,6 @@ __device__ __forceinline__ void mlp_forward(const LayerSmem &L, const uint32_t (
         bfrag2(L.W3, W3_LD, kt, 2, lane, b);
         mma16816(o[2], h2a[kt], b[0], b[1]);
         mma16816(o[3], h2a[kt], b[2], b[3]);
-    }
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const float u0 = L.b3[nt * 8 + 2 * t], u1 = L.b3[nt * 8 + 2 * t + 1];
-        o[nt][0] += u0;
-        o[nt][1] += u1;
-        o[nt][2] += u0;
-        o[nt][3] += u1;
     }
 }
 
