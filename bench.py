@@ -47,6 +47,8 @@ def _parse():
     ap.add_argument("--flow-steps", type=int, default=workloads.FLOW_ORDER5["train_steps"])
     ap.add_argument("--flow-batch", type=int, default=workloads.FLOW_ORDER5["batch"])
     ap.add_argument("--no-flow", action="store_true", help="skip the flow vs VEGAS section (profiling runs)")
+    ap.add_argument("--flow-tensor-path", type=int, default=0, choices=[0, 1],
+                    help="flow sampling / density on mma.sync (0) or tcgen05 (1)")
     return ap.parse_args()
 
 
@@ -176,6 +178,7 @@ def flow_vs_vegas(args, api, params, order, seed):
     Vs = api.Vegas(Gs.dim, FW["n_bins"])
     driver.adapt_vegas(Gs, params[0], Vs, 1 << 22, 12, seed=FW["seed"])
     F = api.Flow(Gs.dim, FW["n_layers"], FW["hidden"], seed=FW["seed"])
+    F.set_tensor_path(args.flow_tensor_path)
     t0 = time.perf_counter()
     losses = driver.train_flow(Gs, params[0], F, Vs, steps=max(1, args.flow_steps), batch=args.flow_batch,
                                lr=1e-3, seed=FW["seed"], vegas_steps=100, evals_per_batch=4, defensive=0.1)
@@ -189,6 +192,7 @@ def flow_vs_vegas(args, api, params, order, seed):
            "means_agree_sigma": cmp["means_agree_sigma"], "compare": "16 batches x %d samples per sampler" %
            FW["n_compare"], "proposal": "flow on the VEGAS grid's input coordinates, 10 % defensive uniform share",
            "flow_train_steps": max(1, args.flow_steps), "flow_batch": args.flow_batch,
+           "flow_tensor_path": ["mma.sync", "tcgen05"][args.flow_tensor_path],
            "flow_train_s": flow_train_s, "flow_loss_first_last": [losses[0], losses[-1]],
            "flow_train_note": "each integrand batch reused for 4 Adam steps; first 100 steps on VEGAS samples; "
                               "VEGAS adapted 12 iterations x 2^22 samples"}

@@ -267,7 +267,7 @@ fd_status fd_flow_sample(const fd_flow *f, uint64_t seed, uint64_t iter, int32_t
  * hypercube; Hesterberg's defensive importance sampling): samples
  * [0, n - n_u) as fd_flow_sample, samples [n - n_u, n) uniform from the same
  * Philox stream, where the flow share n - n_u is n - floor(alpha n) rounded up
- * to a multiple of 256 (at most n), and every sample weighted w = 1 / q_mix(x)
+ * to a multiple of 512 (at most n), and every sample weighted w = 1 / q_mix(x)
  * with a = n_u / n (written to *alpha_used, may be NULL).  The weights never exceed 1 / a, so the proposal's tails are
  * bounded by those of the uniform (or, on a VEGAS grid's coordinates, of
  * VEGAS).  alpha in [0, 0.5]. */
@@ -277,6 +277,15 @@ fd_status fd_flow_sample_defensive(const fd_flow *f, uint64_t seed, uint64_t ite
 /* log q(x) for given points (inverse pass).  x: device [dim][n], logq: device [n]. */
 fd_status fd_flow_log_density(const fd_flow *f, const float *x, int64_t n, float *logq,
                               void *stream);
+/* Tensor-core path of the sampling and density passes: 0 (default) =
+ * warp-level mma.sync m16n8k16 with the activations kept in registers between
+ * layers; 1 = tcgen05.mma with TMEM accumulators, 128-sample tiles, two tiles
+ * in flight, weights staged by TMA (measured ~7% slower on GB300 for this
+ * MLP: its K <= 128 chains spend their time in the per-element epilogues,
+ * which the tcgen05 path routes through TMEM loads and shared memory).  Both
+ * compute the same BF16 contract (BF16 weights and GEMM inputs, FP32
+ * accumulation); training always uses the mma.sync kernels. */
+fd_status fd_flow_set_tensor_path(fd_flow *f, int32_t path);
 /* Weighted forward-KL loss L = -sum w log q(x) / sum w and its gradient in
  * blob layout.  x: device [dim][n]; w: device [n] (>= 0); loss: device [1];
  * grad: device [param_count]. */

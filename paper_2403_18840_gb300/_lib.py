@@ -81,6 +81,7 @@ SIGNATURES = {
     "fd_flow_get_params": (_i32, [_vp, _pf, _i64]),
     "fd_flow_sample": (_i32, [_vp, _u64, _u64, _i32, _i64, _vp, _vp, _vp]),
     "fd_flow_sample_defensive": (_i32, [_vp, _u64, _u64, _i32, _i64, _f64, _vp, _vp, _c.POINTER(_c.c_double), _vp]),
+    "fd_flow_set_tensor_path": (_i32, [_vp, _i32]),
     "fd_flow_log_density": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "fd_flow_grad": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fd_flow_train": (_i32, [_vp, _vp, _vp, _i64, _i32, _f32, _pf, _vp]),

@@ -244,6 +244,10 @@ class Flow:
         L.check(L.lib().fd_flow_sample(self.handle, seed, it, inst, n, _ptr(x), _ptr(w), _stream_ptr(stream)))
         return x, w
 
+    def set_tensor_path(self, path):
+        """Sampling / density on mma.sync (0, default) or tcgen05 (1)."""
+        L.check(L.lib().fd_flow_set_tensor_path(self.handle, path))
+
     def sample_defensive(self, seed, it, inst, n, alpha, stream=None):
         """Mixture (1 - a) q_flow + a uniform: (x, w = 1/q_mix, a actually used)."""
         x = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")

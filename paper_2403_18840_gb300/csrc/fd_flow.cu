@@ -942,6 +942,416 @@ __global__ void sum_weights_kernel(const float *__restrict__ w, int64_t n, doubl
     if (threadIdx.x == 0) atomicAdd(out, sh[0]);
 }
 
+
+// ---- tcgen05 (5th-generation tensor core) sampling / density kernel ------------------
+// Thread pairs own the rows of 128-sample tiles (row = TMEM lane; the two
+// halves of the CTA split every epilogue's columns).  Per layer the three GEMMs
+// of the coupling MLP are single-thread-issued tcgen05.mma (kind::f16: BF16 x
+// BF16 -> FP32) on operands in shared memory in the no-swizzle K-major
+// core-matrix layout (8 rows x 16 bytes per core matrix; LBO = 128 bytes
+// between k-chunks, SBO between 8-row groups), with the accumulators in TMEM;
+// the epilogues (bias, ReLU, BF16 A operand of the next GEMM) and the affine
+// coupling read the rows back with tcgen05.ld.  Two tiles are in flight so that
+// one tile's GEMM runs while the threads work on the other's epilogue.  Layer
+// weights (46 KB) are staged by 1-D TMA bulk copies into a double buffer, the
+// next layer's copy overlapping the current layer.  Same inputs, outputs and
+// modes as flow_pass_kernel.
+namespace umma {
+constexpr int W1B = 128 * 16 * 2;             // W1 [128 n][16 k] BF16
+constexpr int W2B = 128 * 128 * 2;            // W2 [128 n][128 k]
+constexpr int W3B = 32 * 128 * 2;             // W3 [32 n][128 k]: rows 0..15 s, 16..31 t
+constexpr int OFF_W1 = 0, OFF_W2 = OFF_W1 + W1B, OFF_W3 = OFF_W2 + W2B;
+constexpr int OFF_B1 = OFF_W3 + W3B, OFF_B2 = OFF_B1 + 128 * 4, OFF_B3 = OFF_B2 + 128 * 4;
+constexpr int LAYER = OFF_B3 + 32 * 4;        // 46208 bytes per layer
+constexpr int TILES = 4;                      // tiles per block: one weight staging per layer and 512 samples
+constexpr int BLOCK_U = 128 * TILES;
+constexpr int THREADS = 256;                  // two threads per tile row: column halves of every epilogue
+constexpr int YSU = 25;                       // coordinate row stride in floats (odd: no bank conflicts)
+constexpr int S_W = 0;                        // shared memory: two layer buffers
+constexpr int S_A1 = S_W + 2 * LAYER;         // A of GEMM1 [128][16] (SBO 256), one per tile of a pair
+constexpr int S_A2 = S_A1 + 2 * W1B;          // A of GEMM2 / GEMM3 [128][128] (SBO 2048), one per tile of a pair
+constexpr int S_Y = S_A2 + 2 * W2B;           // coordinates [BLOCK_U][YSU] f32
+constexpr int S_LD = S_Y + BLOCK_U * YSU * 4; // log-Jacobian parts [2][BLOCK_U] (one per column half)
+constexpr int S_BAR = S_LD + 2 * BLOCK_U * 4; // weight barriers [2], MMA barriers [2], TMEM address
+constexpr int SMEM = S_BAR + 48;
+constexpr uint32_t TMEM_COLS = 512;           // per tile of a pair: D1 and D3 at +0, D2 at +128
+static_assert(LAYER % 16 == 0 && S_A1 % 16 == 0 && S_A2 % 16 == 0 && S_BAR % 8 == 0, "alignment");
+static_assert(SMEM <= 227 * 1024, "shared memory");
+
+// byte offset of element (row, k) in the core-matrix layout with 8-row-group stride sbo
+__host__ __device__ __forceinline__ uint32_t core_off(int row, int k, uint32_t sbo) {
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+// shared-memory matrix descriptor: start, LBO, SBO (bytes, 16-byte units), version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(const void *p, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = smem_addr(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both K-major, M = 128
+__host__ __device__ constexpr uint32_t idesc(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d), "l"(a), "l"(b), "r"(id),
+                 "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 32 consecutive FP32 columns of this thread's TMEM lane (asynchronous: wait_ld before use)
+__device__ __forceinline__ void ld32_async(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+    wait_ld();
+}
+// hidden-layer epilogue for columns [c_lo, c_lo + 64) of this thread's accumulator
+// row: + bias, ReLU, BF16 -> that row of A (SBO 2048)
+__device__ __forceinline__ void epi_hidden(uint32_t taddr, const float *bias, unsigned char *a, int row, int c_lo) {
+    uint32_t v[2][32];
+    ld32_async(taddr + (uint32_t)c_lo, v[0]);
+    ld32_async(taddr + (uint32_t)c_lo + 32u, v[1]);
+    wait_ld();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c0 = c_lo + 32 * h;
+        uint32_t pk[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            pk[j] = relu_pack(__uint_as_float(v[h][2 * j]) + bias[c0 + 2 * j],
+                              __uint_as_float(v[h][2 * j + 1]) + bias[c0 + 2 * j + 1]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4 *>(a + core_off(row, c0 + 8 * q, 2048)) =
+                make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    }
+}
+// S tanh(x / S) from one exponential: S (1 - 2 / (exp(2 x / S) + 1)), saturating to +-S
+__device__ __forceinline__ float soft_clamp(float x) {
+    const float e = __expf(fminf(fmaxf(x * (2.0f / S_CLAMP), -40.0f), 40.0f));
+    return S_CLAMP * (1.0f - __fdividef(2.0f, e + 1.0f));
+}
+}  // namespace umma
+
+// Weights of every layer in the tcgen05 operand layout (BF16 core matrices) + FP32 biases.
+__global__ void pack_umma_kernel(const float *__restrict__ blob, const LayerIdx *__restrict__ li, int K,
+                                 unsigned char *__restrict__ wu) {
+    const int l = blockIdx.y;
+    if (l >= K) return;
+    const LayerIdx L = li[l];
+    const float *W1 = blob + L.off;
+    const float *b1 = W1 + H * L.a;
+    const float *W2 = b1 + H;
+    const float *b2 = W2 + H * H;
+    const float *W3 = b2 + H;
+    const float *b3 = W3 + 2 * L.b * H;
+    unsigned char *out = wu + (size_t)l * umma::LAYER;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H * H; k += gridDim.x * blockDim.x) {
+        const int r = k / H, c = k % H;
+        *reinterpret_cast<__nv_bfloat16 *>(out + umma::OFF_W2 + umma::core_off(r, c, 2048)) =
+            __float2bfloat16_rn(W2[r * H + c]);
+        if (k < H * 16) {
+            const int r1 = k / 16, c1 = k % 16;
+            *reinterpret_cast<__nv_bfloat16 *>(out + umma::OFF_W1 + umma::core_off(r1, c1, 256)) =
+                __float2bfloat16_rn(c1 < L.a ? W1[r1 * L.a + c1] : 0.f);
+        }
+        if (k < 32 * H) {
+            const int r3 = k / H, c3 = k % H;
+            float v = 0.f;
+            if (r3 < 16 && r3 < L.b) v = W3[r3 * H + c3];                       // s rows
+            else if (r3 >= 16 && r3 - 16 < L.b) v = W3[(L.b + r3 - 16) * H + c3];  // t rows
+            *reinterpret_cast<__nv_bfloat16 *>(out + umma::OFF_W3 + umma::core_off(r3, c3, 2048)) =
+                __float2bfloat16_rn(v);
+        }
+        if (k < H) {
+            reinterpret_cast<float *>(out + umma::OFF_B1)[k] = b1[k];
+            reinterpret_cast<float *>(out + umma::OFF_B2)[k] = b2[k];
+        }
+        if (k < 32)
+            reinterpret_cast<float *>(out + umma::OFF_B3)[k] =
+                (k < 16) ? (k < L.b ? b3[k] : 0.f) : (k - 16 < L.b ? b3[L.b + k - 16] : 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(umma::THREADS, 1) flow_umma_kernel(
+    const unsigned char *__restrict__ wglob, FlowDims f, int mode, int64_t n, uint32_t seed_lo, uint32_t seed_hi,
+    uint32_t iter, uint32_t inst, const float *__restrict__ xin, float *__restrict__ xout, float *__restrict__ wout,
+    int *status, int64_t n_flow, float alpha) {
+    using umma::BLOCK_U;
+    using umma::LAYER;
+    using umma::TILES;
+    using umma::YSU;
+    using umma::core_off;
+    using umma::sdesc;
+    using umma::idesc;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *wb[2] = {smem + umma::S_W, smem + umma::S_W + LAYER};
+    unsigned char *a1[2] = {smem + umma::S_A1, smem + umma::S_A1 + umma::W1B};
+    unsigned char *a2[2] = {smem + umma::S_A2, smem + umma::S_A2 + umma::W2B};
+    float *ys = reinterpret_cast<float *>(smem + umma::S_Y);
+    float *ldj[2] = {reinterpret_cast<float *>(smem + umma::S_LD),
+                     reinterpret_cast<float *>(smem + umma::S_LD) + BLOCK_U};
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(smem + umma::S_BAR);
+    uint64_t *mbar = wbar + 2;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 4);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int half = warp >> 2;                    // column half of every epilogue
+    const int row = (warp & 3) * 32 + (tid & 31);  // tile row = TMEM lane
+    if (tid == 0) {
+        for (int k = 0; k < 4; ++k) mbar_init(&wbar[k], 1);
+        fence_mbarrier_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                     "r"(umma::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = *slot;
+    const uint32_t lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const int64_t nblocks = (n + BLOCK_U - 1) / BLOCK_U;
+    auto dens_of = [&](int64_t b) { return mode == 1 || b * BLOCK_U >= n_flow; };
+    auto layer_of = [&](bool d, int step) { return d ? f.K - 1 - step : step; };
+    auto stage = [&](int buf, int l) {   // thread 0: TMA of layer l into buffer buf
+        fence_proxy_async_smem();
+        mbar_expect_tx(&wbar[buf], LAYER);
+        bulk_g2s(wb[buf], wglob + (size_t)l * LAYER, LAYER, &wbar[buf]);
+    };
+    uint32_t wph[2] = {0u, 0u}, mph[2] = {0u, 0u};
+    bool wpending[2] = {false, false}, mpending[2] = {false, false}, failed = false, lfail = false;
+    int64_t blk = blockIdx.x;
+    if (tid == 0 && blk < nblocks) stage(0, layer_of(dens_of(blk), 0));
+    wpending[0] = blk < nblocks;
+    // generic shared-memory writes made visible to the tensor core, then a block
+    // barrier that also agrees on failure; true when every thread is healthy
+    auto publish = [&]() {
+        fence_proxy_async_smem();
+        umma::fence_before();
+        const bool bad = __syncthreads_or(lfail);
+        umma::fence_after();
+        if (bad) failed = true;
+        return !bad;
+    };
+    // wait for the MMAs committed to barrier p (a thread that gives up reports at the next barrier)
+    auto wait_mma = [&](int p) {
+        if (mbar_wait_bounded(&mbar[p], mph[p] & 1u, WAIT_LIMIT)) {
+            ++mph[p];
+            mpending[p] = false;
+        } else {
+            lfail = true;
+        }
+        umma::fence_after();
+    };
+    auto issue = [&](int p) {
+        umma::commit(&mbar[p]);
+        mpending[p] = true;
+    };
+    int gstep = 0;
+    for (; blk < nblocks && !failed; blk += gridDim.x) {
+        const int64_t base = blk * BLOCK_U;
+        const bool dens = dens_of(blk);
+        // coordinates of the block's samples: rows t * 128 + row, tiles split between the halves
+        for (int t = half; t < TILES; t += 2) {
+            const int r = t * 128 + row;
+            const int64_t i = base + r;
+            const bool valid = i < n;
+            float acc = 0.f;
+            float *y = ys + r * YSU;
+            const int64_t ii = valid ? i : base;
+            if (mode == 0) {
+                const uint32_t c0 = (uint32_t)(uint64_t)ii, c1 = (uint32_t)((uint64_t)ii >> 32);
+                for (int blk4 = 0; 4 * blk4 < f.D; ++blk4) {
+                    const u32x4 rr = philox4x32_10(u32x4{c0, c1, iter, (inst << 8) | (uint32_t)blk4}, seed_lo, seed_hi);
+                    const uint32_t wv[4] = {rr.x, rr.y, rr.z, rr.w};
+                    for (int q = 0; q < 4 && 4 * blk4 + q < f.D; ++q) {
+                        const float z = word_to_uniform(wv[q]);
+                        const float yy = __logf(z) - log1pf(-z);
+                        y[4 * blk4 + q] = yy;
+                        acc -= log_sig_deriv(yy);
+                        // defensive share: the uniform point itself is the sample
+                        if (dens && valid) xout[(int64_t)(4 * blk4 + q) * n + i] = z;
+                    }
+                }
+            } else {
+                for (int d = 0; d < f.D; ++d) {
+                    const float x = clamp_unit(valid ? xin[(int64_t)d * n + i] : 0.5f);
+                    const float yy = __logf(x) - log1pf(-x);
+                    y[d] = yy;
+                    acc -= log_sig_deriv(yy);
+                }
+            }
+            ldj[0][r] = acc;
+            ldj[1][r] = 0.f;
+        }
+        for (int step = 0; step < f.K && !failed; ++step, ++gstep) {
+            const int b = gstep & 1;
+            const int l = layer_of(dens, step);
+            // everyone is done with the other buffer (previous layer): prefetch into it
+            __syncthreads();
+            int nl = -1;
+            if (step + 1 < f.K) nl = layer_of(dens, step + 1);
+            else if (blk + gridDim.x < nblocks) nl = layer_of(dens_of(blk + gridDim.x), 0);
+            if (nl >= 0) {
+                if (tid == 0) stage(b ^ 1, nl);
+                wpending[b ^ 1] = true;
+            }
+            const bool ok = mbar_wait_bounded(&wbar[b], wph[b] & 1u, WAIT_LIMIT);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            ++wph[b];
+            wpending[b] = false;
+            const unsigned char *W = wb[b];
+            const float *b1 = reinterpret_cast<const float *>(W + umma::OFF_B1);
+            const float *b2 = reinterpret_cast<const float *>(W + umma::OFF_B2);
+            const float *b3 = reinterpret_cast<const float *>(W + umma::OFF_B3);
+            const int na = a_size(f, l), nb = b_size(f, l);
+            const float dir = dens ? -1.f : 1.f;
+            const uint64_t dW1 = sdesc(W + umma::OFF_W1, 128, 256);
+            // tiles in pairs: while the threads run one tile's epilogue, the
+            // tensor core runs the other tile's GEMM
+            for (int t0 = 0; t0 < TILES && !failed; t0 += 2) {
+                // A of GEMM1 for both tiles: k chunk `half` of this row's conditioning half
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const float *y = ys + ((t0 + p) * 128 + row) * YSU;
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int k0 = 8 * half + 2 * i;
+                        const float v0 = k0 < na ? y[a_idx(f, l, k0)] : 0.f;
+                        const float v1 = k0 + 1 < na ? y[a_idx(f, l, k0 + 1)] : 0.f;
+                        pk[i] = pack_bf16(v0, v1);
+                    }
+                    *reinterpret_cast<uint4 *>(a1[p] + core_off(row, 8 * half, 256)) =
+                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
+                if (!publish()) break;
+                if (tid == 0) {
+                    for (int p = 0; p < 2; ++p) {
+                        umma::mma(tmem + 256 * p, sdesc(a1[p], 128, 256), dW1, idesc(128), 0u);
+                        issue(p);
+                    }
+                }
+                // GEMM2 of each tile once its hidden layer 1 is written
+                for (int p = 0; p < 2; ++p) {
+                    wait_mma(p);
+                    umma::epi_hidden(lane + 256 * p, b1, a2[p], row, 64 * half);
+                    if (!publish()) break;
+                    if (tid == 0) {
+#pragma unroll
+                        for (int s2 = 0; s2 < 8; ++s2)
+                            umma::mma(tmem + 256 * p + 128, sdesc(a2[p] + s2 * 256, 128, 2048),
+                                      sdesc(W + umma::OFF_W2 + s2 * 256, 128, 2048), idesc(128), s2 > 0 ? 1u : 0u);
+                        issue(p);
+                    }
+                }
+                if (failed) break;
+                // GEMM3 (into the tile's first 32 columns: hidden layer 1 is consumed)
+                for (int p = 0; p < 2; ++p) {
+                    wait_mma(p);
+                    umma::epi_hidden(lane + 256 * p + 128, b2, a2[p], row, 64 * half);
+                    if (!publish()) break;
+                    if (tid == 0) {
+#pragma unroll
+                        for (int s2 = 0; s2 < 8; ++s2)
+                            umma::mma(tmem + 256 * p, sdesc(a2[p] + s2 * 256, 128, 2048),
+                                      sdesc(W + umma::OFF_W3 + s2 * 256, 128, 2048), idesc(32), s2 > 0 ? 1u : 0u);
+                        issue(p);
+                    }
+                }
+                if (failed) break;
+                // affine coupling: this thread's half of the pairs (s, t), j in [8 half, 8 half + 8)
+                for (int p = 0; p < 2; ++p) {
+                    wait_mma(p);
+                    // tcgen05.ld is warp-collective: a warp with a failed wait skips as a whole
+                    if (__any_sync(0xffffffffu, lfail)) {
+                        lfail = true;
+                        continue;
+                    }
+                    const int r = (t0 + p) * 128 + row;
+                    float *y = ys + r * YSU;
+                    uint32_t os[8], ot[8];
+                    umma::ld8(lane + 256 * p + 8 * half, os);
+                    umma::ld8(lane + 256 * p + 16 + 8 * half, ot);
+                    float part = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int j = 8 * half + q;
+                        if (j < nb) {
+                            const float sv = umma::soft_clamp(__uint_as_float(os[q]) + b3[j]);
+                            const float tt = __uint_as_float(ot[q]) + b3[16 + j];
+                            float &yy = y[b_idx(f, l, j)];
+                            yy = dir > 0.f ? fmaf(yy, __expf(sv), tt) : (yy - tt) * __expf(-sv);
+                            part += sv;
+                        }
+                    }
+                    ldj[half][r] += dir * part;
+                }
+            }
+            // rows of the next layer's A come from both halves' couplings
+            if (__syncthreads_or(lfail)) failed = true;
+        }
+        if (failed) break;
+        __syncthreads();
+        // outputs of the block (tiles split between the halves)
+        for (int t = half; t < TILES; t += 2) {
+            const int r = t * 128 + row;
+            const int64_t i = base + r;
+            if (i >= n) continue;
+            const float *y = ys + r * YSU;
+            float acc = ldj[0][r] + ldj[1][r];
+            for (int d = 0; d < f.D; ++d) {
+                acc += log_sig_deriv(y[d]);
+                if (mode == 0 && !dens) xout[(int64_t)d * n + i] = 1.0f / (1.0f + __expf(-y[d]));
+            }
+            if (mode == 1) {
+                wout[i] = acc;
+            } else if (alpha == 0.f) {
+                wout[i] = __expf(acc);
+            } else {
+                const float q = __expf(dens ? acc : -acc);
+                wout[i] = 1.0f / fmaf(1.0f - alpha, q, alpha);
+            }
+        }
+    }
+    if (failed) {
+        // report, let copies and MMAs in flight finish (bounded), then release TMEM
+        if (tid == 0 && status) atomicExch(status, DEV_ST_TIMEOUT);
+        for (int k = 0; k < 2; ++k) {
+            if (wpending[k]) (void)mbar_wait_bounded(&wbar[k], wph[k] & 1u, WAIT_LIMIT);
+            if (mpending[k]) (void)mbar_wait_bounded(&mbar[k], mph[k] & 1u, WAIT_LIMIT);
+        }
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(umma::TMEM_COLS)
+                     : "memory");
+}
+
 }  // namespace
 
 struct fd_flow {
@@ -952,6 +1362,8 @@ struct fd_flow {
     LayerIdx *d_idx = nullptr;
     float *d_blob = nullptr, *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr, *d_gpad = nullptr;
     unsigned char *d_wpack = nullptr;
+    unsigned char *d_wumma = nullptr;   // weights in the tcgen05 operand layout
+    int tensor_path = 0;                // sampling / density: 0 mma.sync (default, faster), 1 tcgen05
     double *d_wsum = nullptr;
     float *d_loss = nullptr;
     float *d_vbuf = nullptr, *d_gbuf = nullptr;
@@ -964,6 +1376,8 @@ FlowDims dims_of(const fd_flow *f) { return FlowDims{f->D, f->K, (f->D + 1) / 2}
 
 fd_status repack(fd_flow *f, cudaStream_t s) {
     pack_weights_kernel<<<dim3(32, f->K), 256, 0, s>>>(f->d_blob, f->d_idx, f->K, f->d_wpack);
+    FD_CHECK_CUDA(cudaGetLastError());
+    pack_umma_kernel<<<dim3(32, f->K), 256, 0, s>>>(f->d_blob, f->d_idx, f->K, f->d_wumma);
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
 }
@@ -988,6 +1402,26 @@ int grid_for(int64_t units, int per_sm_ctas) {
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int64_t g = std::min<int64_t>(units, (int64_t)n_sm * per_sm_ctas);
     return (int)std::max<int64_t>(g, 1);
+}
+
+// sampling (mode 0, flow share [0, n_flow), weights 1 / ((1 - alpha) q + alpha)) or density (mode 1)
+fd_status launch_pass(const fd_flow *f, int mode, int64_t n, uint64_t seed, uint64_t iter, int32_t inst,
+                      const float *xin, float *xout, float *wout, int64_t n_flow, float alpha, cudaStream_t st) {
+    if (f->tensor_path == 1) {
+        FD_CHECK_CUDA(cudaFuncSetAttribute(flow_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           umma::SMEM));
+        flow_umma_kernel<<<grid_for((n + umma::BLOCK_U - 1) / umma::BLOCK_U, 1), umma::THREADS, umma::SMEM, st>>>(
+            f->d_wumma, dims_of(f), mode, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)inst,
+            xin, xout, wout, fd::device_status_word(), n_flow, alpha);
+    } else {
+        const int sm = pass_smem();
+        FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, st>>>(
+            f->d_wpack, dims_of(f), mode, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)inst,
+            xin, xout, wout, fd::device_status_word(), n_flow, alpha);
+    }
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
 }
 
 // loss and gradient (padded per-layer, then blob layout in d_grad) of the batch
@@ -1022,7 +1456,7 @@ fd_status grad_impl(fd_flow *f, const float *x, const float *w, int64_t n, cudaS
 extern "C" fd_status fd_flow_create(int32_t dim, int32_t n_layers, int32_t hidden, uint64_t seed, fd_flow **out) {
     FD_REQUIRE(out, "out is required");
     *out = nullptr;
-    FD_REQUIRE(dim >= 2 && dim <= 32, "dim must be in [2, 32]");
+    FD_REQUIRE(dim >= 2 && dim <= YS, "dim must be in [2, 24] (coordinate rows of the flow kernels)");
     FD_REQUIRE(n_layers >= 1 && n_layers <= 64, "n_layers must be in [1, 64]");
     FD_REQUIRE(hidden == H, "hidden must be 128 (tensor-core tiling of this build)");
     fd_flow *f = new fd_flow();
@@ -1072,6 +1506,7 @@ extern "C" fd_status fd_flow_create(int32_t dim, int32_t n_layers, int32_t hidde
     al((void **)&f->d_grad, off * 4);
     al((void **)&f->d_gpad, (size_t)n_layers * GRAD_LAYER * 4);
     al((void **)&f->d_wpack, (size_t)n_layers * LAYER_BYTES);
+    al((void **)&f->d_wumma, (size_t)n_layers * umma::LAYER);
     al((void **)&f->d_idx, n_layers * sizeof(LayerIdx));
     al((void **)&f->d_wsum, sizeof(double));
     al((void **)&f->d_loss, sizeof(float));
@@ -1102,6 +1537,7 @@ extern "C" void fd_flow_free(fd_flow *f) {
     cudaFree(f->d_grad);
     cudaFree(f->d_gpad);
     cudaFree(f->d_wpack);
+    cudaFree(f->d_wumma);
     cudaFree(f->d_idx);
     cudaFree(f->d_wsum);
     cudaFree(f->d_loss);
@@ -1140,13 +1576,7 @@ extern "C" fd_status fd_flow_sample(const fd_flow *f, uint64_t seed, uint64_t it
     FD_REQUIRE(f && x && w, "flow, x and w are required");
     FD_REQUIRE(n > 0 && n <= (int64_t(1) << 34), "n out of range");
     FD_REQUIRE(inst >= 0 && inst < (1 << 24), "instance index out of range");
-    const int sm = pass_smem();
-    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, (cudaStream_t)stream>>>(
-        f->d_wpack, dims_of(f), 0, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)inst, nullptr, x,
-        w, fd::device_status_word(), n, 0.0f);
-    FD_CHECK_CUDA(cudaGetLastError());
-    return FD_OK;
+    return launch_pass(f, 0, n, seed, iter, inst, nullptr, x, w, n, 0.0f, (cudaStream_t)stream);
 }
 
 extern "C" fd_status fd_flow_sample_defensive(const fd_flow *f, uint64_t seed, uint64_t iter, int32_t inst,
@@ -1156,28 +1586,25 @@ extern "C" fd_status fd_flow_sample_defensive(const fd_flow *f, uint64_t seed, u
     FD_REQUIRE(n > 0 && n <= (int64_t(1) << 34), "n out of range");
     FD_REQUIRE(inst >= 0 && inst < (1 << 24), "instance index out of range");
     FD_REQUIRE(alpha >= 0.0 && alpha <= 0.5, "alpha must be in [0, 0.5]");
-    // the flow share ends on a block boundary, so every block is of one kind
-    const int64_t n_flow = std::min(n, (n - (int64_t)(alpha * (double)n) + BLOCK - 1) / BLOCK * BLOCK);
+    // the flow share ends on a block boundary of both sampling kernels, so every block is of one kind
+    constexpr int64_t UNIT = umma::BLOCK_U;
+    const int64_t n_flow = std::min(n, (n - (int64_t)(alpha * (double)n) + UNIT - 1) / UNIT * UNIT);
     const int64_t n_u = n - n_flow;
     const float a = (float)((double)n_u / (double)n);
     if (alpha_used) *alpha_used = (double)n_u / (double)n;
-    const int sm = pass_smem();
-    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, (cudaStream_t)stream>>>(
-        f->d_wpack, dims_of(f), 0, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)inst, nullptr, x,
-        w, fd::device_status_word(), n - n_u, a);
-    FD_CHECK_CUDA(cudaGetLastError());
-    return FD_OK;
+    return launch_pass(f, 0, n, seed, iter, inst, nullptr, x, w, n_flow, a, (cudaStream_t)stream);
 }
 
 extern "C" fd_status fd_flow_log_density(const fd_flow *f, const float *x, int64_t n, float *logq, void *stream) {
     FD_REQUIRE(f && x && logq, "flow, x and logq are required");
     FD_REQUIRE(n > 0 && n <= (int64_t(1) << 34), "n out of range");
-    const int sm = pass_smem();
-    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    flow_pass_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, 2), 128, sm, (cudaStream_t)stream>>>(
-        f->d_wpack, dims_of(f), 1, n, 0, 0, 0, 0, x, nullptr, logq, fd::device_status_word(), n, 0.0f);
-    FD_CHECK_CUDA(cudaGetLastError());
+    return launch_pass(f, 1, n, 0, 0, 0, x, nullptr, logq, n, 0.0f, (cudaStream_t)stream);
+}
+
+extern "C" fd_status fd_flow_set_tensor_path(fd_flow *f, int32_t path) {
+    FD_REQUIRE(f, "null flow");
+    FD_REQUIRE(path == 0 || path == 1, "path must be 0 (mma.sync) or 1 (tcgen05)");
+    f->tensor_path = path;
     return FD_OK;
 }
 

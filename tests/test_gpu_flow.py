@@ -62,7 +62,7 @@ def test_defensive_mixture_parity(api):
     n = 3000
     x, w, a = F.sample_defensive(21, 2, 3, n, 0.25)
     torch.cuda.synchronize()
-    n_u = n - 2304                      # flow share n - floor(0.25 n) = 2250 rounded up to 256s
+    n_u = n - 2560                      # flow share n - floor(0.25 n) = 2250 rounded up to 512s
     assert a == n_u / n
     nf = n - n_u
     u = ophilox.uniforms(21, 2, 3, np.arange(n), D)
@@ -79,6 +79,50 @@ def test_defensive_mixture_parity(api):
     print("defensive: max rel w %.3e p99 %.3e" % (rel.max(), np.quantile(rel, 0.99)))
     assert rel.max() < 2e-2 and np.quantile(rel, 0.99) < 2e-3
     assert np.all(wg <= 1.0 / a * (1 + 1e-6))
+
+
+def test_tensor_paths_agree(api):
+    # tcgen05 and mma.sync (default) sampling / density passes compute the same
+    # BF16 contract; n spans several 512-sample blocks and a ragged tail
+    F, blob = _flow(api)
+    n = 5000
+    out = {}
+    for path in (1, 0):
+        F.set_tensor_path(path)
+        x, w = F.sample(5, 1, 2, n)
+        lq = F.log_density(x)
+        xd, wd, _ = F.sample_defensive(5, 1, 2, n, 0.2)
+        torch.cuda.synchronize()
+        out[path] = [t.cpu().numpy().astype(np.float64) for t in (x, w, lq, xd, wd)]
+    F.set_tensor_path(0)
+    (x1, w1, l1, xd1, wd1), (x0, w0, l0, xd0, wd0) = out[1], out[0]
+    assert np.abs(x1 - x0).max() < 2e-3
+    assert np.abs(np.log(w1) - np.log(w0)).max() < 2e-2
+    assert np.abs(l1 - l0).max() < 2e-2
+    assert np.abs(xd1 - xd0).max() < 2e-3
+    assert np.abs(wd1 / wd0 - 1.0).max() < 2e-2
+    # the density pass inverts the sampling pass: log q(x) = -log w
+    assert np.quantile(np.abs(l1 + np.log(w1)), 0.99) < 2e-3
+
+
+def test_tcgen05_path_parity(api):
+    # the tcgen05 sampling and density passes against the FP64 oracle under the BF16 contract
+    F, blob = _flow(api)
+    F.set_tensor_path(1)
+    n = 3000
+    x, w = F.sample(21, 2, 3, n)
+    lq = F.log_density(x)
+    torch.cuda.synchronize()
+    F.set_tensor_path(0)
+    z = ophilox.uniforms(21, 2, 3, np.arange(n), D)
+    xr, lqr = oflow.forward(blob, z, D, K, H)
+    dx = np.abs(x.cpu().numpy().astype(np.float64) - xr)
+    dl = np.abs(np.log(w.cpu().numpy().astype(np.float64)) + lqr)
+    dd = np.abs(lq.cpu().numpy().astype(np.float64) - lqr)
+    print("tcgen05: max |dx| %.3e  max |dlogq| %.3e" % (dx.max(), dl.max()))
+    assert dx.max() < 2e-3 and np.quantile(dx, 0.99) < 2e-4
+    assert dl.max() < 2e-2 and np.quantile(dl, 0.99) < 2e-3
+    assert dd.max() < 2e-2 and np.quantile(dd, 0.99) < 2e-3
 
 
 def test_log_density_parity_and_consistency(api):
