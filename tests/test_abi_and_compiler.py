@@ -95,8 +95,11 @@ def test_tape_validation_rejects_malformed_tapes():
     assert len(L.lib().fd_last_error()) > 0
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 4])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, pytest.param(6, marks=pytest.mark.slow)])
 def test_compiler_topologies_match_oracle(n):
+    # order 6 (the effective-mass configuration): the oracle's brute force visits
+    # 12! contractions (about a minute); the compiler must produce the same
+    # 110410 connected and 31130 self-energy topologies
     mine = sorted(d.sigma for d in fdgraph.self_energy_diagrams(n))
     ref = sorted(t.sigma for t in odg.self_energy_topologies(n))
     assert mine == ref
