@@ -745,22 +745,37 @@ extern "C" fd_status fd_counter_add(uint32_t *d_counter, uint32_t v, void *strea
 
 // ---- fd_accumulate ---------------------------------------------------------------
 namespace {
+// One warp per (instance, root, part): lane j sums tiles j, j + 32, ... with
+// Neumaier compensation, then lane 0 combines the 32 lane sums in lane order
+// (fixed order: bitwise reproducible).
 __global__ void accumulate_kernel(const double *partials, int n_inst, int r_max, int tiles,
                                   int64_t n, double *out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;   // (inst, r, c)
+    const int k = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);   // (inst, r, c)
+    const int lane = threadIdx.x & 31;
     if (k >= n_inst * r_max * 2) return;
     const int inst = k / (r_max * 2), rc = k % (r_max * 2), r = rc / 2, c = rc % 2;
     double s = 0.0, sc = 0.0, q = 0.0, qc = 0.0;
-    for (int t = 0; t < tiles; ++t) {
+    for (int t = lane; t < tiles; t += 32) {
         const double *p = partials + (((int64_t)inst * tiles + t) * r_max + r) * 4 + c * 2;
         neumaier(s, sc, p[0]);
         neumaier(q, qc, p[1]);
     }
-    s += sc;
-    q += qc;
-    const double mean = s / (double)n;
+    double ls[4] = {s, sc, q, qc};
+    double S = 0.0, SC = 0.0, Q = 0.0, QC = 0.0;
+    for (int j = 0; j < 32; ++j) {
+        const double v0 = __shfl_sync(0xffffffffu, ls[0], j), v1 = __shfl_sync(0xffffffffu, ls[1], j);
+        const double v2 = __shfl_sync(0xffffffffu, ls[2], j), v3 = __shfl_sync(0xffffffffu, ls[3], j);
+        neumaier(S, SC, v0);
+        neumaier(S, SC, v1);
+        neumaier(Q, QC, v2);
+        neumaier(Q, QC, v3);
+    }
+    if (lane != 0) return;
+    S += SC;
+    Q += QC;
+    const double mean = S / (double)n;
     double var = 0.0;
-    if (n > 1) var = fmax((q - s * mean) / (double)(n - 1), 0.0) / (double)n;
+    if (n > 1) var = fmax((Q - S * mean) / (double)(n - 1), 0.0) / (double)n;
     out[(((int64_t)inst * r_max + r) * 2 + c) * 2] = mean;
     out[(((int64_t)inst * r_max + r) * 2 + c) * 2 + 1] = var;
 }
@@ -772,9 +787,9 @@ extern "C" fd_status fd_accumulate(const double *partials, int32_t n_inst, int32
     FD_REQUIRE(n_inst > 0 && r_max > 0 && n_per_inst > 0, "sizes must be positive");
     const int64_t tl = fd_tile_samples(n_per_inst);
     const int tiles = (int)((n_per_inst + tl - 1) / tl);
-    const int total = n_inst * r_max * 2;
-    accumulate_kernel<<<(total + 127) / 128, 128, 0, (cudaStream_t)stream>>>(partials, n_inst, r_max, tiles,
-                                                                          n_per_inst, out);
+    const int64_t threads = (int64_t)n_inst * r_max * 2 * 32;    // one warp per output
+    accumulate_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+        partials, n_inst, r_max, tiles, n_per_inst, out);
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
 }

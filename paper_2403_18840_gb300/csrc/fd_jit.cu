@@ -45,7 +45,7 @@ const char kRuntimeHeader[] =
 #include "fd_jit_rt.inc"
     ;
 
-constexpr int kJitVersion = 1;              // bump when the generated code changes meaning
+constexpr int kJitVersion = 2;              // bump when the generated code changes meaning
 constexpr double kSingleModuleCost = 3500;  // below this the graph compiles as one module
 
 // ---- run-time compiler entry points (resolved with dlopen on first use) ---------
@@ -580,8 +580,8 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
           << spt << "; ++p) re[p] = im[p] = 0.0f;\n";
         for (size_t u = 0; u < units.size(); ++u)
             if (units[u].root == r) b << "      fd_u" << u << "(V, cs, sn, re, im);\n";
-        b << "#pragma unroll\n      for (int p = 0; p < " << spt << "; ++p) k[p].template flush<" << r << ", "
-          << (rt & 255u) << ", " << (((rt >> 24) & 255u) ? 1 : 0) << ">(re[p], im[p]);\n    }\n";
+        b << "      flush_samples<" << r << ", " << (rt & 255u) << ", " << (((rt >> 24) & 255u) ? 1 : 0) << ", "
+          << spt << ", " << N << ">(k, re, im);\n    }\n";
     }
     b << "  }\n};\n";
     src[0] << b.str();

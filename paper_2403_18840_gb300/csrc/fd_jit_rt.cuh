@@ -328,6 +328,39 @@ struct FdSink {
     }
 };
 
+// Completed root R_IDX for the P samples of this thread: per-sample weights,
+// VEGAS sums and outputs, then one warp reduction of the thread's FP32 sums
+// over its samples and one FP64 accumulation per warp (instead of one per sample).
+template <int R_IDX, int ORD, int DK, int P, int N>
+__device__ __forceinline__ void flush_samples(FdSink<N> *K, const float *re, const float *im) {
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const float J = K[p].jac[ORD - 1];
+        const float fre = K[p].valid ? re[p] * J : 0.0f;
+        const float fim = K[p].valid ? im[p] * J : 0.0f;
+        if (!DK) K[p].hsum += fabsf(fre) + fabsf(fim);
+        if (K[p].ps && K[p].valid) {
+            K[p].ps[K[p].ps_row + (int64_t)(2 * R_IDX) * K[p].ps_n] = fre;
+            K[p].ps[K[p].ps_row + (int64_t)(2 * R_IDX + 1) * K[p].ps_n] = fim;
+        }
+        v[0] += fre;
+        v[1] = fmaf(fre, fre, v[1]);
+        v[2] += fim;
+        v[3] = fmaf(fim, fim, v[3]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        double *acc = K[0].acc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) neumaier(acc[(R_IDX * 4 + q) * 2], acc[(R_IDX * 4 + q) * 2 + 1], (double)v[q]);
+    }
+}
+
 // Persistent specialised kernel body: work items (instance, tile) from the
 // queue, one sample per thread per pass, Body::run contracts the graph, tile
 // partials combined over warps in a fixed order (bitwise reproducible).

@@ -78,7 +78,7 @@ def test_sample_loop_units_cover_every_slice_once(unit_cap):
     body, _ = api.jit_source(tape, 0, **kw)
     assert len(slices) == len(set(slices))
     assert sorted(re.findall(r"(fd_u\d+)\(V, cs, sn, re, im\)", body)) == sorted(units)
-    flushes = re.findall(r"flush<(\d+), ", body)
+    flushes = re.findall(r"flush(?:_samples)?<(\d+), ", body)
     assert sorted(int(r) for r in flushes) == list(range(len(fdgraph.graph_roots(5))))
     if unit_cap == 0:
         assert len(units) == len(slices)             # one slice per unit
