@@ -13,8 +13,8 @@ write) between timed steps.
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host
 cores on a bounded sample of the same workload.  Under torchrun (N > 1) every
-rank runs an independent replica with its own Philox instance index (weak
-scaling, no data-path collective); rank 0 prints.
+rank runs an independent replica with its own Philox seed (weak scaling, no
+data-path collective; `replicas.py`); rank 0 prints.
 """
 import argparse
 import json
@@ -203,7 +203,7 @@ def flow_vs_vegas(args, api, params, order, seed):
 def run_ours(args, rank, world, dist):
     import torch
 
-    from paper_2403_18840_gb300 import api, autotune, fdgraph
+    from paper_2403_18840_gb300 import api, autotune, fdgraph, replicas
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     order = WL["order"]
@@ -219,7 +219,7 @@ def run_ours(args, rank, world, dist):
     plan = api.EvalPlan([G], params, [0], n, maps=[V])
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    seed = WL["seed"] + 1000 * rank
+    seed = replicas.rank_seed(WL["seed"], rank)
 
     def step(it, ev=None):
         if ev is not None:
@@ -258,10 +258,7 @@ def run_ours(args, rank, world, dist):
     kern_ms = [e[0].elapsed_time(e[1]) for e in evs]
     t_step = float(np.sum(step_ms)) / 1e3
     t_kern = float(np.mean(kern_ms)) / 1e3
-    if dist:
-        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = replicas.max_over_ranks(dist, t_step, device="cuda")
     value = world * n * args.steps / t_step
 
     # end to end through the C-ABI with host buffers: grid in, estimates and grid out
