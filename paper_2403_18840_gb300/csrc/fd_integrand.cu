@@ -587,6 +587,7 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
     args.r_max = r_max;
     args.slots_total = slots_total;
     args.dim_max = dim_max;
+    args.hist_smem = 0;     // the specialised launcher sets its own
     for (int j = 0; j < n_inst; ++j) {
         const int gi = graph_of_inst[j];
         FD_REQUIRE(gi >= 0 && gi < n_graphs, "graph_of_inst out of range");

@@ -68,6 +68,7 @@ struct fd_graph {
     cudaKernel_t jit_kernel = nullptr;
     int jit_threads = 0, jit_min_blocks = 0, jit_regs = 0, jit_local_bytes = 0, jit_modules = 0, jit_per_sm = 1;
     int jit_spt = 1;
+    int jit_hist_cap = 0;           // floats of dynamic shared memory the kernel may take for a tile histogram
     double jit_compile_s = 0.0;
     bool jit_enabled = false;       // evaluation uses the specialised kernel
 };
@@ -77,7 +78,7 @@ fd_status graph_from_tape(const void *buf, size_t len, fd_graph &g);
 
 // launches the specialised kernel of graph g for the instances in `args`
 // (fd_jit.cu); the caller has reset the work counter
-fd_status jit_launch(const fd_graph *g, const EvalArgs &args, cudaStream_t stream);
+fd_status jit_launch(const fd_graph *g, EvalArgs &args, cudaStream_t stream);
 
 struct fd_vegas {
     int device;

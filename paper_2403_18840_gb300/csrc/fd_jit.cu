@@ -45,7 +45,7 @@ const char kRuntimeHeader[] =
 #include "fd_jit_rt.inc"
     ;
 
-constexpr int kJitVersion = 2;              // bump when the generated code changes meaning
+constexpr int kJitVersion = 3;              // bump when the generated code changes meaning
 constexpr double kSingleModuleCost = 3500;  // below this the graph compiles as one module
 
 // ---- run-time compiler entry points (resolved with dlopen on first use) ---------
@@ -681,16 +681,20 @@ fd_status build_cubin(const Program &P, int maxrreg, std::vector<char> &cubin) {
 
 }  // namespace
 
-fd_status jit_launch(const fd_graph *g, const EvalArgs &args, cudaStream_t stream) {
-    int dev = 0, n_sm = 0, per_sm = 0;
+fd_status jit_launch(const fd_graph *g, EvalArgs &args, cudaStream_t stream) {
+    int dev = 0, n_sm = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
-    (void)per_sm;
     FD_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    per_sm = g->jit_per_sm;
+    // tile histograms in shared memory when every adapting instance's grid fits
+    int hist_floats = 0;
+    for (int j = 0; j < args.n_inst; ++j)
+        if (args.inst[j].hist) hist_floats = std::max(hist_floats, args.inst[j].dim * args.inst[j].n_bins);
+    args.hist_smem = hist_floats <= g->jit_hist_cap ? hist_floats : 0;
     const int items = args.n_inst * args.tiles_per_inst;
-    const int grid = std::min(items, n_sm * per_sm);
+    const int grid = std::min(items, n_sm * g->jit_per_sm);
     void *params[1] = {(void *)&args};
-    FD_CHECK_CUDA(cudaLaunchKernel((const void *)g->jit_kernel, dim3(grid), dim3(g->jit_threads), params, 0, stream));
+    FD_CHECK_CUDA(cudaLaunchKernel((const void *)g->jit_kernel, dim3(grid), dim3(g->jit_threads), params,
+                                   (size_t)args.hist_smem * sizeof(float), stream));
     return FD_OK;
 }
 
@@ -785,8 +789,27 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const 
         (void)cudaGetLastError();
         per_sm = std::max(1, 65536 / (std::max(attr.numRegs, 1) * threads));
     }
+    per_sm = std::max(per_sm, 1);
+    // dynamic shared memory for tile histograms: what the resident CTAs leave
+    // free, at most 96 KB so that the rest of the unified L1 keeps the
+    // per-thread local arrays of the sample-loop variants
+    int sm_total = 0, optin = 0, reserved = 0, hist_cap = 0;
+    if (cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
+        const long free_b = std::min<long>((long)sm_total / per_sm - reserved, optin) - (long)attr.sharedSizeBytes;
+        const long cap_b = std::min<long>(free_b, 96 * 1024) & ~15L;
+        if (cap_b > 0) {
+            if (cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_b) ==
+                cudaSuccess)
+                hist_cap = (int)(cap_b / (long)sizeof(float));
+            else
+                (void)cudaGetLastError();   // no tile histograms: global atomics only
+        }
+    }
     if (g->jit_lib) cudaLibraryUnload(g->jit_lib);
-    g->jit_per_sm = std::max(per_sm, 1);
+    g->jit_per_sm = per_sm;
+    g->jit_hist_cap = hist_cap;
     g->jit_lib = lib;
     g->jit_kernel = kern;
     g->jit_threads = threads;

@@ -42,6 +42,7 @@ struct InstDesc {
 
 struct EvalArgs {
     int32_t n_inst, tiles_per_inst, r_max, slots_total, dim_max;
+    int32_t hist_smem;                 // floats of dynamic shared memory for the tile histogram (0: none)
     int64_t n_per_inst, tile;
     uint32_t seed_lo, seed_hi, iter;
     const uint32_t *iter_dev;          // optional: iteration += *iter_dev (read on the device)
@@ -361,6 +362,41 @@ __device__ __forceinline__ void flush_samples(FdSink<N> *K, const float *re, con
     }
 }
 
+// VEGAS histogram of one tile.  With hist_smem > 0 the launch provides
+// dim x n_bins floats of dynamic shared memory: each sample adds its squared
+// |f| sum to its bins there (FP32 shared atomics) and the tile's nonzero bins
+// go to the FP64 global histogram once at the end of the tile, instead of one
+// FP64 global atomic per sample and coordinate.  A square that overflows FP32
+// goes straight to the global histogram.
+template <int DIM>
+__device__ __forceinline__ void hist_sample(const InstDesc &D, float *hs, const int *bins, float hsum) {
+    const float h = hsum * hsum;
+    if (hs && h <= 3.40282347e38f) {      // finite in FP32
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) atomicAdd(hs + d * D.n_bins + bins[d], h);
+    } else {
+        const double hd = (double)hsum * (double)hsum;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) atomicAdd(D.hist + (int64_t)d * D.n_bins + bins[d], hd);
+    }
+}
+
+template <int DIM, int T>
+__device__ __forceinline__ void hist_tile_flush(const InstDesc &D, const float *hs) {
+    for (int k = threadIdx.x; k < DIM * D.n_bins; k += T) {
+        const float v = hs[k];
+        if (v != 0.0f) atomicAdd(D.hist + k, (double)v);
+    }
+}
+
+template <int DIM, int T>
+__device__ __forceinline__ float *hist_tile_begin(const InstDesc &D, const EvalArgs &A, float *smem) {
+    if (!D.hist || A.hist_smem < DIM * D.n_bins) return nullptr;
+    for (int k = threadIdx.x; k < DIM * D.n_bins; k += T) smem[k] = 0.0f;
+    __syncthreads();
+    return smem;
+}
+
 // Persistent specialised kernel body: work items (instance, tile) from the
 // queue, one sample per thread per pass, Body::run contracts the graph, tile
 // partials combined over warps in a fixed order (bitwise reproducible).
@@ -368,6 +404,7 @@ template <class Body, int N, int DIM, int R, int T>
 __device__ __forceinline__ void jit_main(const EvalArgs &A) {
     __shared__ double acc[T / 32][R * 8];
     __shared__ int next_item;
+    extern __shared__ float hist_smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = A.n_inst * A.tiles_per_inst;
     const uint32_t iter = A.iter + (A.iter_dev ? *A.iter_dev : 0u);
@@ -380,6 +417,7 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
         const int tile = item % A.tiles_per_inst;
         for (int k = lane; k < R * 8; k += 32) acc[warp][k] = 0.0;
         __syncwarp();
+        float *hs = hist_tile_begin<DIM, T>(D, A, hist_smem);
         const int64_t first = (int64_t)tile * A.tile;
         const int64_t last = min(first + A.tile, A.n_per_inst);
         for (int64_t base = first; base < last; base += T) {
@@ -398,13 +436,10 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
             FdSink<N> K{acc[warp], jac, valid, 0.0f, A.per_sample_f,
                         (int64_t)D.id * A.r_max * 2 * A.n_per_inst + idx, A.n_per_inst};
             Body::run(V, cs, sn, K);
-            if (D.hist && valid) {
-                const double h = (double)K.hsum * (double)K.hsum;
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) atomicAdd(D.hist + (int64_t)d * D.n_bins + bins[d], h);
-            }
+            if (D.hist && valid) hist_sample<DIM>(D, hs, bins, K.hsum);
         }
         __syncthreads();
+        if (hs) hist_tile_flush<DIM, T>(D, hs);
         for (int k = tid; k < R * 4; k += T) {
             double s = 0.0, c = 0.0;
             for (int wp = 0; wp < T / 32; ++wp) {
@@ -431,6 +466,7 @@ template <class Body, int N, int DIM, int R, int T, int P>
 __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
     __shared__ double acc[T / 32][R * 8];
     __shared__ int next_item;
+    extern __shared__ float hist_smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = A.n_inst * A.tiles_per_inst;
     const uint32_t iter = A.iter + (A.iter_dev ? *A.iter_dev : 0u);
@@ -443,6 +479,7 @@ __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
         const int tile = item % A.tiles_per_inst;
         for (int k = lane; k < R * 8; k += 32) acc[warp][k] = 0.0;
         __syncwarp();
+        float *hs = hist_tile_begin<DIM, T>(D, A, hist_smem);
         const int64_t first = (int64_t)tile * A.tile;
         const int64_t last = min(first + A.tile, A.n_per_inst);
         for (int64_t base = first; base < last; base += (int64_t)T * P) {
@@ -467,15 +504,12 @@ __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
             Body::run(V, cs, sn, K);
             if (D.hist) {
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    if (!K[p].valid) continue;
-                    const double h = (double)K[p].hsum * (double)K[p].hsum;
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) atomicAdd(D.hist + (int64_t)d * D.n_bins + bins[p][d], h);
-                }
+                for (int p = 0; p < P; ++p)
+                    if (K[p].valid) hist_sample<DIM>(D, hs, bins[p], K[p].hsum);
             }
         }
         __syncthreads();
+        if (hs) hist_tile_flush<DIM, T>(D, hs);
         for (int k = tid; k < R * 4; k += T) {
             double s = 0.0, c = 0.0;
             for (int wp = 0; wp < T / 32; ++wp) {
