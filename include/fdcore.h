@@ -57,10 +57,10 @@ typedef struct {
 } fd_params;
 
 /* Sample-tile size of the reduction: partial sums are kept per instance and
- * per tile of consecutive samples.  The tile holds FD_TILE_SAMPLES samples
- * when n_per_inst >= 512 * FD_TILE_SAMPLES, otherwise the smallest power of
- * two >= n_per_inst / 512 (at least 1024), so small launches still spread
- * over the GPU; fd_tile_samples(n) returns it. */
+ * per tile of consecutive samples.  The tile is the smallest power of two
+ * >= n_per_inst / 4096, at least 1024 and at most FD_TILE_SAMPLES: many work
+ * items per SM, so the last wave of the persistent CTAs leaves little idle
+ * time; fd_tile_samples(n) returns it. */
 #define FD_TILE_SAMPLES 16384
 int64_t fd_tile_samples(int64_t n_per_inst);
 
@@ -103,7 +103,7 @@ fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_
  *               arithmetic statements (warps share instruction-cache lines);
  *  leaf_calls   != 0: leaf families are calls to one out-of-line function per
  *               (Taylor order, d/dk) shape instead of inlined code;
- *  spt          1..8 samples per thread per pass; with spt > 1 every
+ *  spt          1..16 samples per thread per pass; with spt > 1 every
  *               compilation unit loops over the spt samples, so its code is
  *               re-executed from the instruction cache;
  *  unit_cap     with spt > 1: consecutive slices of a root share a unit while

@@ -23,9 +23,9 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 SCHEDULES = [dict(budget=b, bundle=w, window=8 * w) for b in (96, 128, 160) for w in (4, 8)]
 SHAPES = [(128, 2), (256, 1), (128, 1), (64, 2)]
 # specialised-kernel variants (fd_jit_options; unlisted options at their defaults)
-JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=1), dict(threads=256, min_blocks=1, spt=2, unit_cap=12000),
-                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000),
-                dict(threads=256, min_blocks=1, spt=4, unit_cap=6000)]
+JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=1), dict(threads=256, min_blocks=1, spt=4, unit_cap=12000),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=6000),
+                dict(threads=256, min_blocks=1, spt=8, unit_cap=12000)]
 JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap")
 
 
@@ -111,7 +111,7 @@ def _jit_graph(order, roots, v):
 def tune_jit(order, roots, params, n_samples=1 << 23, variants=None, force=False, log=None):
     """Best {'threads','min_blocks','root_units','sync_every','leaf_calls','spt','samples_per_s',...} for the
     specialised kernel."""
-    key = "jit3|" + _key(order, roots)
+    key = "jit4|" + _key(order, roots)
     cache = _load()
     if key in cache and not force:
         return cache[key]

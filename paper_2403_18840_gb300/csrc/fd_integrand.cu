@@ -531,9 +531,8 @@ extern "C" fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t s
 }
 
 extern "C" int64_t fd_tile_samples(int64_t n_per_inst) {
-    if (n_per_inst >= 512ll * FD_TILE_SAMPLES) return FD_TILE_SAMPLES;
     int64_t t = 1024;
-    while (t * 512 < n_per_inst) t *= 2;
+    while (t < FD_TILE_SAMPLES && t * 4096 < n_per_inst) t *= 2;
     return t;
 }
 

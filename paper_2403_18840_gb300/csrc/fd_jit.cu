@@ -685,11 +685,16 @@ fd_status jit_launch(const fd_graph *g, EvalArgs &args, cudaStream_t stream) {
     int dev = 0, n_sm = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
     FD_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    // tile histograms in shared memory when every adapting instance's grid fits
-    int hist_floats = 0;
+    // tile histograms in shared memory when every adapting instance's grid
+    // fits and a tile holds at least 4 samples per bin (the end-of-tile flush
+    // then costs at most a quarter of the per-sample global atomics it replaces)
+    int hist_floats = 0, bins_max = 0;
     for (int j = 0; j < args.n_inst; ++j)
-        if (args.inst[j].hist) hist_floats = std::max(hist_floats, args.inst[j].dim * args.inst[j].n_bins);
-    args.hist_smem = hist_floats <= g->jit_hist_cap ? hist_floats : 0;
+        if (args.inst[j].hist) {
+            hist_floats = std::max(hist_floats, args.inst[j].dim * args.inst[j].n_bins);
+            bins_max = std::max(bins_max, args.inst[j].n_bins);
+        }
+    args.hist_smem = (hist_floats <= g->jit_hist_cap && args.tile >= 4 * (int64_t)bins_max) ? hist_floats : 0;
     const int items = args.n_inst * args.tiles_per_inst;
     const int grid = std::min(items, n_sm * g->jit_per_sm);
     void *params[1] = {(void *)&args};
@@ -705,7 +710,7 @@ fd_status check_options(const fd_jit_options *o) {
     FD_REQUIRE(o->min_blocks >= 1 && o->min_blocks <= 8, "min_blocks must be in 1..8");
     FD_REQUIRE(o->max_modules >= 1 && o->max_modules <= 64, "max_modules must be in 1..64");
     FD_REQUIRE(o->sync_every >= 0, "sync_every must be >= 0");
-    FD_REQUIRE(o->spt >= 1 && o->spt <= 8, "samples per thread must be in 1..8");
+    FD_REQUIRE(o->spt >= 1 && o->spt <= 16, "samples per thread must be in 1..16");
     FD_REQUIRE(o->unit_cap >= 0, "unit_cap must be >= 0");
     return FD_OK;
 }
