@@ -112,6 +112,22 @@ def _peaks():
     return {}
 
 
+# DRAM bytes (read + write) per sample of fd_jit_kernel from one ncu capture
+# of the variant below (2^22 samples; the traffic is local-memory lines
+# evicted from L2 and grows with the samples).  Another variant, or a change
+# of the kernel's code, has no capture: traffic is then reported as null.
+NCU_TRAFFIC = dict(variant=dict(threads=256, min_blocks=1, spt=4, unit_cap=6000), bytes_per_sample=214.7,
+                   capture="profiles/fd_jit_kernel_order5_vegas_ncu_full.md")
+
+
+def ncu_traffic(tuned, n, keys=("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap")):
+    """Captured DRAM bytes of one launch of n samples, or None for an uncaptured variant."""
+    v = NCU_TRAFFIC["variant"]
+    if all(tuned.get(k) == v.get(k) for k in keys):
+        return NCU_TRAFFIC["bytes_per_sample"] * n
+    return None
+
+
 def fp32_peak_tflops(n_sm, mhz):
     """Non-tensor FP32 peak: 128 FP32 lanes per SM, FMA = 2 flops."""
     return n_sm * 128 * 2 * mhz * 1e6 / 1e12
@@ -298,7 +314,7 @@ def run_ours(args, rank, world, dist):
                    "l2": "256 MiB flush write between timed steps; inputs generated on device",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "fd_jit_kernel",
+                     "frac": achieved / peak, "traffic": ncu_traffic(tuned, n), "kernel": "fd_jit_kernel",
                      "flops_per_sample": flops_ps, "sfu_per_sample": sfu_ps,
                      "executed_flops_per_sample": exec_flops_ps, "executed_sfu_per_sample": exec_sfu_ps,
                      "sfu_achieved_tops": sfu_achieved,
