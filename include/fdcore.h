@@ -300,7 +300,8 @@ fd_status fd_flow_train(fd_flow *f, const float *x, const float *w, int64_t n, i
 /* ---- pipe throughput probes -------------------------------------------------
  * Measured throughput of one pipe of the current device, used as roofline
  * denominators next to the unit-count peaks: kind 0 = FP32 FMA (flops per
- * second, FMA = 2), 1 = SFU exp2 (results per second), 2 = SFU reciprocal.
+ * second, FMA = 2), 1 = SFU exp2 (results per second), 2 = SFU reciprocal,
+ * 3 = packed two-lane FP32 FMA (flops per second, 4 per instruction).
  * Synchronous; allocates a small scratch buffer. */
 fd_status fd_measure_peak(int32_t kind, double *ops_per_s);
 

@@ -284,7 +284,7 @@ class Flow:
 
 
 def measure_peak(kind):
-    """Measured pipe throughput: 0 FP32 FMA (flop/s), 1 SFU ex2, 2 SFU rcp (results/s)."""
+    """Measured pipe throughput: 0 FP32 FMA (flop/s), 1 SFU ex2, 2 SFU rcp (results/s), 3 packed FP32x2 FMA (flop/s)."""
     v = ctypes.c_double()
     L.check(L.lib().fd_measure_peak(kind, ctypes.byref(v)))
     return v.value

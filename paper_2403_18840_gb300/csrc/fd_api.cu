@@ -669,25 +669,43 @@ __global__ void peak_kernel(float *out, int iters, float seed) {
     for (int j = 0; j < 8; ++j) s += v[j];
     if (s == 12345.678f) out[threadIdx.x] = s;   // keeps the work alive
 }
+
+// packed FP32: 8 independent chains of two-lane FMAs (one instruction, 4 flops)
+__global__ void peak_kernel_f32x2(float *out, int iters, float seed) {
+    float2 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = make_float2(seed + 0.001f * (threadIdx.x + j), seed - 0.001f * j);
+    const float2 a = make_float2(0.9999999f, 0.9999998f), c = make_float2(1e-7f, 2e-7f);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __ffma2_rn(v[j], a, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += v[j].x + v[j].y;
+    if (s == 12345.678f) out[threadIdx.x] = s;
+}
 }  // namespace
 
 // Measured throughput of one pipe on the current device (synchronous):
-// kind 0 = FP32 FMA (flops, FMA = 2), 1 = SFU ex2, 2 = SFU rcp (results).
+// kind 0 = FP32 FMA (flops, FMA = 2), 1 = SFU ex2, 2 = SFU rcp (results),
+// 3 = packed two-lane FP32 FMA (flops, 4 per instruction).
 extern "C" fd_status fd_measure_peak(int32_t kind, double *ops_per_s) {
-    FD_REQUIRE(ops_per_s && kind >= 0 && kind <= 2, "kind in 0..2 and an output are required");
+    FD_REQUIRE(ops_per_s && kind >= 0 && kind <= 3, "kind in 0..3 and an output are required");
     int dev = 0, n_sm = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
     FD_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     float *out = nullptr;
     FD_CHECK_CUDA(cudaMalloc(&out, 1024 * sizeof(float)));
-    const int threads = 512, blocks = n_sm * 4, iters = kind == 0 ? 8192 : 2048;
+    const int threads = 512, blocks = n_sm * 4, iters = (kind == 0 || kind == 3) ? 8192 : 2048;
     cudaEvent_t a, b;
     FD_CHECK_CUDA(cudaEventCreate(&a));
     FD_CHECK_CUDA(cudaEventCreate(&b));
     auto launch = [&]() {
         if (kind == 0) peak_kernel<0><<<blocks, threads>>>(out, iters, 1.0f);
         else if (kind == 1) peak_kernel<1><<<blocks, threads>>>(out, iters, 0.5f);
-        else peak_kernel<2><<<blocks, threads>>>(out, iters, 1.5f);
+        else if (kind == 2) peak_kernel<2><<<blocks, threads>>>(out, iters, 1.5f);
+        else peak_kernel_f32x2<<<blocks, threads>>>(out, iters, 1.0f);
     };
     launch();
     FD_CHECK_CUDA(cudaGetLastError());
@@ -700,7 +718,7 @@ extern "C" fd_status fd_measure_peak(int32_t kind, double *ops_per_s) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(out);
-    const double ops = 5.0 * blocks * threads * (double)iters * 8.0 * (kind == 0 ? 2.0 : 1.0);
+    const double ops = 5.0 * blocks * threads * (double)iters * 8.0 * (kind == 0 ? 2.0 : kind == 3 ? 4.0 : 1.0);
     *ops_per_s = ops / (ms * 1e-3);
     return FD_OK;
 }
