@@ -26,7 +26,7 @@ SHAPES = [(128, 2), (256, 1), (128, 1), (64, 2)]
 JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=1), dict(threads=256, min_blocks=1, spt=4, unit_cap=12000),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=6000),
                 dict(threads=256, min_blocks=1, spt=8, unit_cap=12000)]
-JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap")
+JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap", "pair")
 
 
 def _key(order, roots):

@@ -242,19 +242,18 @@ std::string fnum(float f) {
 // signed momentum sums of a 2-bit-per-variable mask: (x, y, z, k_ext coefficient)
 void momentum_expr(uint32_t mask, int N, std::string &x, std::string &y, std::string &z, std::string &ks) {
     auto coef = [&](int j) { return (int)(((int32_t)(mask << (30 - 2 * j))) >> 30); };
+    // -a + b is written b - a (the same value bit for bit, and one operation
+    // fewer in the packed code); the order of the later terms is kept
     auto sum = [&](const char *comp, bool with_ext) {
-        std::string e;
-        if (with_ext && coef(0)) e = coef(0) > 0 ? "V.kext" : "-V.kext";
-        for (int j = 1; j <= N; ++j) {
-            const int c = coef(j);
-            if (!c) continue;
-            const std::string term = std::string("V.") + comp + "[" + std::to_string(j - 1) + "]";
-            if (e.empty())
-                e = (c > 0 ? "" : "-") + term;
-            else
-                e += (c > 0 ? " + " : " - ") + term;
-        }
-        return e.empty() ? std::string("0.0f") : e;
+        std::vector<std::pair<int, std::string>> terms;
+        if (with_ext && coef(0)) terms.push_back({coef(0), "V.kext"});
+        for (int j = 1; j <= N; ++j)
+            if (coef(j)) terms.push_back({coef(j), std::string("V.") + comp + "[" + std::to_string(j - 1) + "]"});
+        if (terms.empty()) return std::string("0.0f");
+        if (terms.size() >= 2 && terms[0].first < 0 && terms[1].first > 0) std::swap(terms[0], terms[1]);
+        std::string e = (terms[0].first > 0 ? "" : "-") + terms[0].second;
+        for (size_t i = 1; i < terms.size(); ++i) e += (terms[i].first > 0 ? " + " : " - ") + terms[i].second;
+        return e;
     };
     x = sum("kx", false);
     y = sum("ky", false);
@@ -267,14 +266,17 @@ void momentum_expr(uint32_t mask, int N, std::string &x, std::string &y, std::st
 // together and share the instruction-cache lines they fetch.  Every thread of
 // the block executes every statement, so the barriers are uniform.
 // leaf_calls: leaves call the out-of-line family functions instead of inlining them.
+// vt: value type of the generated code, "float" (one sample) or "FdF2" (two
+// samples in packed two-lane arithmetic; no out-of-line leaves).
 std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, const std::vector<uint64_t> &words,
-                       int N, int n_slots, const char *qual, int sync_every, int leaf_calls) {
+                       int N, int n_slots, const char *qual, int sync_every, int leaf_calls,
+                       const std::string &vt = "float") {
     std::ostringstream o;
     std::vector<std::string> cur(n_slots + 1);
     cur[0] = "0.0f";
     cur[1] = "1.0f";
     for (int j = 0; j < N; ++j) cur[2 + j] = "V.t[" + std::to_string(j) + "]";
-    o << qual << " float fd_s" << q << "(const FdSV &V) {\n";
+    o << qual << " " << vt << " fd_s" << q << "(const FdSVT<" << vt << "> &V) {\n";
     int k = 0, since_sync = 0;
     for (const auto &kv : s.keep) {
         const TIns &t = ins[kv.first];
@@ -293,11 +295,12 @@ std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, cons
                                c = (uint32_t)(mw >> 48);
                 const std::string nm = "v" + std::to_string(k++);
                 if (b == 1)
-                    o << "  const float " << nm << " = " << cur[a] << " + " << cur[c] << ";\n";
+                    o << "  const " << vt << " " << nm << " = " << cur[a] << " + " << cur[c] << ";\n";
                 else if (c == 0)
-                    o << "  const float " << nm << " = " << cur[a] << " * " << cur[b] << ";\n";
+                    o << "  const " << vt << " " << nm << " = " << cur[a] << " * " << cur[b] << ";\n";
                 else
-                    o << "  const float " << nm << " = fmaf(" << cur[a] << ", " << cur[b] << ", " << cur[c] << ");\n";
+                    o << "  const " << vt << " " << nm << " = fd_fma(" << cur[a] << ", " << cur[b] << ", " << cur[c]
+                      << ");\n";
                 upd.push_back({d, nm});
             }
             for (auto &u : upd) cur[u.first] = u.second;
@@ -321,15 +324,15 @@ std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, cons
                 for (int j = 0; j < no; ++j) cur[d + j] = nm + ".v[" + std::to_string(j) + "]";
                 continue;
             }
-            o << "  float " << nm << "[" << no << "];\n  {\n    const float px = " << x << ", py = " << y
-              << ", pz = " << z << ";\n    const float p2 = fmaf(px, px, fmaf(py, py, pz * pz));\n";
+            o << "  " << vt << " " << nm << "[" << no << "];\n  {\n    const " << vt << " px = " << x << ", py = " << y
+              << ", pz = " << z << ";\n    const " << vt << " p2 = fd_fma(px, px, fd_fma(py, py, pz * pz));\n";
             if (t.op == OP_GLEAF) {
                 const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
                 o << "    g_family(p2, pz, " << ks << ", V.t[" << la << "] - V.t[" << lb << "], V.beta, V.mu, " << M
-                  << ", " << dk << ", [&](int j, float v) { " << nm << "[j] = v; });\n  }\n";
+                  << ", " << dk << ", [&](int j, " << vt << " v) { " << nm << "[j] = v; });\n  }\n";
             } else {
-                o << "    v_family(p2, pz, " << ks << ", V.Lam, " << M << ", " << dk << ", [&](int j, float v) { "
-                  << nm << "[j] = v; });\n  }\n";
+                o << "    v_family(p2, pz, " << ks << ", V.Lam, " << M << ", " << dk << ", [&](int j, " << vt
+                  << " v) { " << nm << "[j] = v; });\n  }\n";
             }
             for (int j = 0; j < no; ++j) cur[d + j] = nm + "[" + std::to_string(j) + "]";
         } else if (t.op == OP_CONST) {
@@ -357,11 +360,11 @@ struct Unit {
 };
 
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls);
+                          int leaf_calls, int pair);
 
 Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units, int sync_every,
-                     int leaf_calls, int spt = 1, int unit_cap = 6000) {
-    if (spt > 1) return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls);
+                     int leaf_calls, int spt = 1, int unit_cap = 6000, int pair = 0) {
+    if (spt > 1) return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls, pair);
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -484,7 +487,7 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
 // Emission with P > 1 samples per thread: compilation units (a root, or one
 // slice of a root whose cost exceeds unit_cap) loop over the P samples.
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls) {
+                          int leaf_calls, int pair) {
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -553,15 +556,30 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
     std::vector<std::ostringstream> src(n_mod);
     for (int m = 0; m < n_mod; ++m)
         src[m] << "// generated from a validated fdcore tape: order " << N << ", " << R << " roots, " << sl.size()
-               << " root-accumulate slices, " << spt << " samples per thread\n#include \"fd_jit_rt.cuh\"\n";
+               << " root-accumulate slices, " << spt << " samples per thread" << (pair ? " in packed pairs" : "")
+               << "\n#include \"fd_jit_rt.cuh\"\n";
     const char *unit_qual = multi ? "extern \"C\" __device__ __noinline__" : "static __device__ __noinline__";
     const std::string sig = "(const FdSV *V, const float *cs, const float *sn, float *re, float *im)";
     for (size_t u = 0; u < units.size(); ++u) {
         const int m = mod_of[u];
         for (int i : units[u].slices)
             src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, "static __device__ __forceinline__", 0,
-                                 leaf_calls);
+                                 leaf_calls, pair ? "FdF2" : "float");
         if (multi && m != 0) src[0] << "extern \"C\" __device__ void fd_u" << u << sig << ";\n";
+        if (pair) {
+            // samples p and p + 1 in the two lanes of packed arithmetic
+            src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
+                   << "; p += 2) {\n    const FdSVT<FdF2> W = fd_pack(V[p], V[p + 1]);\n    FdF2 r = 0.0f, i = 0.0f, v;\n";
+            for (int i : units[u].slices) {
+                const std::string c0 = "p * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
+                const std::string c1 = "(p + 1) * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
+                src[m] << "    v = fd_s" << i << "(W); r = fd_fma(v, FdF2(cs[" << c0 << "], cs[" << c1
+                       << "]), r); i = fd_fma(v, FdF2(sn[" << c0 << "], sn[" << c1 << "]), i);\n";
+            }
+            src[m] << "    re[p] += r.v.x;\n    re[p + 1] += r.v.y;\n    im[p] += i.v.x;\n    im[p + 1] += i.v.y;\n"
+                      "  }\n}\n";
+            continue;
+        }
         src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
                << "; ++p) {\n    float r = 0.0f, i = 0.0f, v;\n";
         for (int i : units[u].slices)
@@ -712,12 +730,14 @@ fd_status check_options(const fd_jit_options *o) {
     FD_REQUIRE(o->sync_every >= 0, "sync_every must be >= 0");
     FD_REQUIRE(o->spt >= 1 && o->spt <= 16, "samples per thread must be in 1..16");
     FD_REQUIRE(o->unit_cap >= 0, "unit_cap must be >= 0");
+    FD_REQUIRE(o->pair == 0 || (o->spt >= 2 && o->spt % 2 == 0 && !o->leaf_calls),
+               "packed pairs need an even number of samples per thread and inlined leaves");
     return FD_OK;
 }
 
 Program emit(const fd_graph &g, const fd_jit_options &o) {
     return emit_program(g, o.threads, o.min_blocks, o.max_modules, o.root_units, o.sync_every, o.leaf_calls, o.spt,
-                        o.unit_cap);
+                        o.unit_cap, o.pair);
 }
 }  // namespace
 

@@ -96,6 +96,47 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Two samples' values in one register pair: every arithmetic operation is one
+// packed two-lane instruction (add, multiply, fused multiply-add; each lane
+// rounds exactly as the scalar operation), so the code of a compilation unit is
+// fetched and issued once for two samples.  Subtraction is a + (-1) b and
+// negation (-1) a, both exact.  Scalars convert implicitly (both lanes).
+struct FdF2 {
+    float2 v;
+    __device__ __forceinline__ FdF2() {}
+    __device__ __forceinline__ FdF2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ FdF2(float a, float b) : v(make_float2(a, b)) {}
+};
+struct FdM2 {
+    bool x, y;
+};
+__device__ __forceinline__ FdF2 fd_wrap(float2 v) {
+    FdF2 r;
+    r.v = v;
+    return r;
+}
+__device__ __forceinline__ FdF2 operator+(FdF2 a, FdF2 b) { return fd_wrap(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ FdF2 operator*(FdF2 a, FdF2 b) { return fd_wrap(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ FdF2 operator-(FdF2 a, FdF2 b) {
+    return fd_wrap(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v));
+}
+__device__ __forceinline__ FdF2 operator-(FdF2 a) { return fd_wrap(__fmul2_rn(a.v, make_float2(-1.0f, -1.0f))); }
+__device__ __forceinline__ float fd_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ FdF2 fd_fma(FdF2 a, FdF2 b, FdF2 c) { return fd_wrap(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ float fd_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ FdF2 fd_abs(FdF2 a) { return FdF2(fabsf(a.v.x), fabsf(a.v.y)); }
+__device__ __forceinline__ float fd_exp(float a) { return __expf(a); }
+__device__ __forceinline__ FdF2 fd_exp(FdF2 a) { return FdF2(__expf(a.v.x), __expf(a.v.y)); }
+__device__ __forceinline__ bool fd_gt0(float a) { return a > 0.0f; }
+__device__ __forceinline__ FdM2 fd_gt0(FdF2 a) { return FdM2{a.v.x > 0.0f, a.v.y > 0.0f}; }
+__device__ __forceinline__ bool fd_lt0(float a) { return a < 0.0f; }
+__device__ __forceinline__ FdM2 fd_lt0(FdF2 a) { return FdM2{a.v.x < 0.0f, a.v.y < 0.0f}; }
+__device__ __forceinline__ float fd_sel(bool c, float a, float b) { return c ? a : b; }
+__device__ __forceinline__ FdF2 fd_sel(FdM2 c, FdF2 a, FdF2 b) {
+    return FdF2(c.x ? a.v.x : b.v.x, c.y ? a.v.y : b.v.y);
+}
+__device__ __forceinline__ FdF2 rcp_approx(FdF2 x) { return FdF2(rcp_approx(x.v.x), rcp_approx(x.v.y)); }
+
 // 1 / (k + 1) for the Taylor recurrences (no division in the inner loops)
 __device__ __forceinline__ float inv_int(int k1) {
     return k1 == 1 ? 1.0f : k1 == 2 ? 0.5f : k1 == 3 ? 0.33333334f : k1 == 4 ? 0.25f
@@ -112,34 +153,34 @@ __device__ __forceinline__ float inv_int(int k1) {
 // phi(eps - d) follows from the logistic ODE d phi / d eps = +-beta phi (1 - phi)
 // (a Taylor-mode recurrence); the series of exp(d tau*) is tau*^k / k!.
 // out(j, value) receives the (M + 1) (1 + dk) values.
-template <class Out>
-__device__ __forceinline__ void g_family(float p2, float pz, float ks, float dx, float beta, float mu, int M,
-                                         int dk, Out &&out) {
-    const float eps = p2 - mu;
-    const float E = __expf(-beta * fabsf(eps));
-    const float phi = rcp_approx(1.0f + E);
-    const float psi = E * phi;
-    const bool pos = dx > 0.0f;
-    const float tau = beta * dx;
-    const bool occ = eps < 0.0f;
-    const float tstar = occ ? (pos ? tau - beta : tau) : (pos ? tau : tau + beta);
-    const float X = (pos ? -1.0f : 1.0f) * __expf(-eps * tstar) * phi;
+template <class T, class Out>
+__device__ __forceinline__ void g_family(T p2, T pz, float ks, T dx, float beta, float mu, int M, int dk,
+                                         Out &&out) {
+    const T eps = p2 - mu;
+    const T E = fd_exp(-beta * fd_abs(eps));
+    const T phi = rcp_approx(1.0f + E);
+    const T psi = E * phi;
+    const auto pos = fd_gt0(dx);
+    const T tau = beta * dx;
+    const auto occ = fd_lt0(eps);
+    const T tstar = fd_sel(occ, fd_sel(pos, tau - beta, tau), fd_sel(pos, tau, tau + beta));
+    const T X = fd_sel(pos, T(-1.0f), T(1.0f)) * fd_exp(-eps * tstar) * phi;
     if (M == 0 && !dk) {
         out(0, X);
         return;
     }
     const int Mx = M + dk;
-    float ph[FD_MAX_M + 1], ps[FD_MAX_M + 1], A[FD_MAX_M + 1], cf[FD_MAX_M + 1];
-    const float g = occ ? beta : -beta;
+    T ph[FD_MAX_M + 1], ps[FD_MAX_M + 1], A[FD_MAX_M + 1], cf[FD_MAX_M + 1];
+    const T g = fd_sel(occ, T(beta), T(-beta));
     ph[0] = 1.0f;
     ps[0] = psi;
     A[0] = 1.0f;
 #pragma unroll
     for (int k = 0; k < FD_MAX_M; ++k) {
         if (k < Mx) {
-            float s = 0.0f;
+            T s = 0.0f;
 #pragma unroll
-            for (int i = 0; i <= k; ++i) s = fmaf(ph[i], ps[k - i], s);
+            for (int i = 0; i <= k; ++i) s = fd_fma(ph[i], ps[k - i], s);
             ph[k + 1] = g * s * inv_int(k + 1);
             ps[k + 1] = -phi * ph[k + 1];
             A[k + 1] = A[k] * tstar * inv_int(k + 1);
@@ -148,9 +189,9 @@ __device__ __forceinline__ void g_family(float p2, float pz, float ks, float dx,
 #pragma unroll
     for (int j = 0; j <= FD_MAX_M; ++j) {
         if (j <= Mx) {
-            float s = 0.0f;
+            T s = 0.0f;
 #pragma unroll
-            for (int i = 0; i <= j; ++i) s = fmaf(A[j - i], ph[i], s);
+            for (int i = 0; i <= j; ++i) s = fd_fma(A[j - i], ph[i], s);
             cf[j] = X * s;
         }
     }
@@ -159,7 +200,7 @@ __device__ __forceinline__ void g_family(float p2, float pz, float ks, float dx,
         if (j <= M) out(j, cf[j]);
     if (dk) {
         // d eps / d k_ext = 2 p . e_z ks; d/dk c_j = -(j + 1) c_(j+1) d eps / dk
-        const float kz = -2.0f * ks * pz;
+        const T kz = -2.0f * ks * pz;
 #pragma unroll
         for (int j = 0; j < FD_MAX_M; ++j)
             if (j <= M) out(M + 1 + j, kz * (float)(j + 1) * cf[j + 1]);
@@ -168,11 +209,11 @@ __device__ __forceinline__ void g_family(float p2, float pz, float ks, float dx,
 
 // V Taylor family: c_l = (d/dLambda)^l V / l! = 8 pi (-1)^l w^(l+1), w = 1/(q^2+Lambda),
 // l <= L, then (when dk) d c_l / d k_ext.  out(l, value) receives (L + 1) (1 + dk) values.
-template <class Out>
-__device__ __forceinline__ void v_family(float q2, float qz, float ks, float Lambda, int L, int dk, Out &&out) {
-    const float inv = rcp_approx(q2 + Lambda);
-    float cl = FD_8PI * inv;
-    float cf[FD_MAX_M + 1];
+template <class T, class Out>
+__device__ __forceinline__ void v_family(T q2, T qz, float ks, float Lambda, int L, int dk, Out &&out) {
+    const T inv = rcp_approx(q2 + Lambda);
+    T cl = FD_8PI * inv;
+    T cf[FD_MAX_M + 1];
 #pragma unroll
     for (int l = 0; l <= FD_MAX_M; ++l) {
         if (l <= L + dk) {
@@ -184,7 +225,7 @@ __device__ __forceinline__ void v_family(float q2, float qz, float ks, float Lam
     for (int l = 0; l <= FD_MAX_M; ++l)
         if (l <= L) out(l, cf[l]);
     if (dk) {
-        const float kz = 2.0f * ks * qz;
+        const T kz = 2.0f * ks * qz;
 #pragma unroll
         for (int l = 0; l < FD_MAX_M; ++l)
             if (l <= L) out(L + 1 + l, kz * (float)(l + 1) * cf[l + 1]);
@@ -218,10 +259,29 @@ __device__ __noinline__ FdLeafOut<(L + 1) * (1 + DK)> v_leaf_fn(float q2, float 
 // ---- specialised kernels -------------------------------------------------------
 // Per-sample variables the generated code reads: loop momenta k_1..k_N,
 // hypercube times of the interaction lines (t[0] = 0) and the parameters.
-struct FdSV {
-    float kx[FD_MAX_ORDER], ky[FD_MAX_ORDER], kz[FD_MAX_ORDER], t[FD_MAX_ORDER];
+template <class T>
+struct FdSVT {
+    T kx[FD_MAX_ORDER], ky[FD_MAX_ORDER], kz[FD_MAX_ORDER], t[FD_MAX_ORDER];
     float kext, beta, mu, Lam;
 };
+using FdSV = FdSVT<float>;
+
+// two samples' variables for the packed code (the parameters are per instance)
+__device__ __forceinline__ FdSVT<FdF2> fd_pack(const FdSV &a, const FdSV &b) {
+    FdSVT<FdF2> w;
+#pragma unroll
+    for (int j = 0; j < FD_MAX_ORDER; ++j) {
+        w.kx[j] = FdF2(a.kx[j], b.kx[j]);
+        w.ky[j] = FdF2(a.ky[j], b.ky[j]);
+        w.kz[j] = FdF2(a.kz[j], b.kz[j]);
+        w.t[j] = FdF2(a.t[j], b.t[j]);
+    }
+    w.kext = a.kext;
+    w.beta = a.beta;
+    w.mu = a.mu;
+    w.Lam = a.Lam;
+    return w;
+}
 
 // Hypercube point of sample i (Philox stream or given point), VEGAS map (when
 // the instance has one), then loop momenta k_j, interaction-line times t_j

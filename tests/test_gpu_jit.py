@@ -209,18 +209,34 @@ def test_jit_captured_iteration(api):
     assert int(a.d_iter.item()) == 2
 
 
+@pytest.mark.parametrize("pair", [False, True])
 @pytest.mark.parametrize("order,with_dk,n", [(3, True, 2 * 1024 + 77), (5, False, 160)])
-def test_jit_sample_loop_variant(api, order, with_dk, n):
-    # spt samples per thread, each compilation unit looping over them; a pass
+def test_jit_sample_loop_variant(api, order, with_dk, n, pair):
+    # spt samples per thread, each compilation unit looping over them (with
+    # pair: two samples at a time in packed two-lane arithmetic); a pass
     # covers 256 x 4 samples, so n spans several passes and a ragged tail
     G = api.Graph(order, with_dk=with_dk, budget=8192)
-    info = G.jit(threads=256, min_blocks=1, spt=4)
+    info = G.jit(threads=256, min_blocks=1, spt=4, pair=pair)
     assert info["enabled"]
     f, st, _ = _run(api, G, order, n, 37)
     ref, mag = _oracle(order, G.roots, n, 37)
-    _compare(f[:len(G.roots)], ref, mag, "jit spt 4 order %d" % order)
+    _compare(f[:len(G.roots)], ref, mag, "jit spt 4 pair %s order %d" % (pair, order))
     for r in range(len(G.roots)):
         assert abs(st[r, 0, 0] - f[r, 0].mean()) <= 1e-6 * (np.abs(f[r, 0]).mean() + 1e-30)
+
+
+def test_jit_packed_pairs_match_scalar_loop(api):
+    # several tiles and a ragged tail; the packed code does per lane the
+    # operations of the scalar code, up to multiply-add contraction
+    order, n = 4, 3 * 16384 + 77
+    a = api.Graph(order, with_dk=True, budget=8192)
+    a.jit(threads=256, min_blocks=1, spt=4, unit_cap=6000, pair=True)
+    b = api.Graph(order, with_dk=True, budget=8192)
+    b.jit(threads=256, min_blocks=1, spt=4, unit_cap=6000)
+    fa, _, _ = _run(api, a, order, n, 5)
+    fb, _, _ = _run(api, b, order, n, 5)
+    scale = np.abs(fb).max(axis=2, keepdims=True) + 1e-30
+    assert np.max(np.abs(fa - fb) / scale) < 1e-5
 
 
 def test_jit_sample_loop_matches_one_sample_per_thread(api):

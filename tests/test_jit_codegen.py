@@ -51,11 +51,11 @@ def test_large_graph_splits_into_linked_modules(root_units):
         src, _ = api.jit_source(tape, m, threads=128, min_blocks=2, max_modules=8, root_units=root_units)
         defined += re.findall(r'extern "C" __device__ __noinline__ %s (%s\d+)\(' % (ret, unit), src)
         declared |= set(re.findall(r'extern "C" __device__ %s (%s\d+)\(const FdSV &V' % (ret, unit), src))
-        slices += re.findall(r"__device__ __\w+__ float (fd_s\d+)\(const FdSV &V\) \{", src)
+        slices += re.findall(r"__device__ __\w+__ float (fd_s\d+)\(const FdSVT<float> &V\) \{", src)
         assert ("fd_jit_kernel" in src) == (m == 0)
     assert len(defined) == len(set(defined))
     assert declared <= set(defined)
-    assert len(slices) == len(set(slices))            # every slice emitted exactly once
+    assert slices and len(slices) == len(set(slices))   # every slice emitted exactly once
     body, _ = api.jit_source(tape, 0, threads=128, min_blocks=2, max_modules=8, root_units=root_units)
     called = set(re.findall(r"= (%s\d+)\(V" % unit, body))
     assert called == set(defined)
@@ -63,20 +63,25 @@ def test_large_graph_splits_into_linked_modules(root_units):
         assert len(defined) == len(fdgraph.graph_roots(5))
 
 
+@pytest.mark.parametrize("pair", [False, True])
 @pytest.mark.parametrize("unit_cap", [0, 6000, 100000])
-def test_sample_loop_units_cover_every_slice_once(unit_cap):
+def test_sample_loop_units_cover_every_slice_once(unit_cap, pair):
     # spt > 1: units pack consecutive slices of one root; every slice emitted
-    # once, every unit called once, every root flushed once per sample
+    # once (in packed two-lane arithmetic with pair), every unit called once,
+    # every root flushed once per sample
     tape = _tape(5, False)
-    kw = dict(threads=256, min_blocks=1, max_modules=8, spt=4, unit_cap=unit_cap)
+    kw = dict(threads=256, min_blocks=1, max_modules=8, spt=4, unit_cap=unit_cap, pair=pair)
     _, n_mod = api.jit_source(tape, 0, **kw)
     slices, units = [], []
+    vt = "FdF2" if pair else "float"
     for m in range(n_mod):
         src, _ = api.jit_source(tape, m, **kw)
-        slices += re.findall(r"__device__ __forceinline__ float (fd_s\d+)\(const FdSV &V\) \{", src)
+        slices += re.findall(r"__device__ __forceinline__ %s (fd_s\d+)\(const FdSVT<%s> &V\) \{" % (vt, vt), src)
+        if pair:
+            assert "fd_pack(V[p], V[p + 1])" in src or "fd_u" not in src
         units += re.findall(r"__device__ __noinline__ void (fd_u\d+)\(", src)
     body, _ = api.jit_source(tape, 0, **kw)
-    assert len(slices) == len(set(slices))
+    assert slices and len(slices) == len(set(slices))
     assert sorted(re.findall(r"(fd_u\d+)\(V, cs, sn, re, im\)", body)) == sorted(units)
     flushes = re.findall(r"flush(?:_samples)?<(\d+), ", body)
     assert sorted(int(r) for r in flushes) == list(range(len(fdgraph.graph_roots(5))))
@@ -84,3 +89,10 @@ def test_sample_loop_units_cover_every_slice_once(unit_cap):
         assert len(units) == len(slices)             # one slice per unit
     if unit_cap == 100000:
         assert len(units) == len(fdgraph.graph_roots(5))   # one unit per root
+
+
+@pytest.mark.parametrize("kw", [dict(spt=3, pair=True), dict(spt=1, pair=True), dict(spt=4, pair=True, leaf_calls=True)])
+def test_packed_pairs_reject_invalid_options(kw):
+    # packed pairs need an even number of samples per thread and inlined leaves
+    with pytest.raises(api.L.FdError):
+        api.jit_source(_tape(2, False), 0, threads=256, min_blocks=1, **kw)
