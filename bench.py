@@ -113,15 +113,17 @@ def _peaks():
 
 
 # DRAM bytes (read + write) per sample of fd_jit_kernel from one ncu capture
-# of the variant below (2^22 samples; the traffic is local-memory lines
-# evicted from L2 and grows with the samples).  Another variant, or a change
-# of the kernel's code, has no capture: traffic is then reported as null.
-NCU_TRAFFIC = dict(variant=dict(threads=256, min_blocks=1, spt=4, unit_cap=6000), bytes_per_sample=214.7,
-                   capture="profiles/fd_jit_kernel_order5_vegas_ncu_full.md")
+# of the variant named here (the traffic is local-memory lines evicted from
+# L2 and grows with the samples).  Another variant, or a change of the
+# kernel's code since the capture, has none: traffic is then reported as null.
+NCU_TRAFFIC = None
 
 
-def ncu_traffic(tuned, n, keys=("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap")):
+def ncu_traffic(tuned, n, keys=("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap",
+                                "pair")):
     """Captured DRAM bytes of one launch of n samples, or None for an uncaptured variant."""
+    if NCU_TRAFFIC is None:
+        return None
     v = NCU_TRAFFIC["variant"]
     if all(tuned.get(k) == v.get(k) for k in keys):
         return NCU_TRAFFIC["bytes_per_sample"] * n

@@ -101,6 +101,7 @@ fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_
  *               share their leaves) instead of one per slice;
  *  sync_every   > 0: a block barrier after about that many generated
  *               arithmetic statements (warps share instruction-cache lines);
+ *               with spt > 1: a block barrier after every unit call;
  *  leaf_calls   != 0: leaf families are calls to one out-of-line function per
  *               (Taylor order, d/dk) shape instead of inlined code;
  *  spt          1..16 samples per thread per pass; with spt > 1 every

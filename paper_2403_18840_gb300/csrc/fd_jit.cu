@@ -360,11 +360,12 @@ struct Unit {
 };
 
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair);
+                          int leaf_calls, int pair, int sync_units);
 
 Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units, int sync_every,
                      int leaf_calls, int spt = 1, int unit_cap = 6000, int pair = 0) {
-    if (spt > 1) return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls, pair);
+    if (spt > 1)
+        return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls, pair, sync_every);
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -486,8 +487,11 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
 
 // Emission with P > 1 samples per thread: compilation units (a root, or one
 // slice of a root whose cost exceeds unit_cap) loop over the P samples.
+// sync_units != 0: a block barrier after every unit call, so that the warps of
+// a CTA run the same unit together and share its instruction-cache lines
+// (every thread calls every unit: the barriers are uniform).
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair) {
+                          int leaf_calls, int pair, int sync_units) {
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -597,7 +601,8 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         b << "    {\n      float re[" << spt << "], im[" << spt << "];\n#pragma unroll\n      for (int p = 0; p < "
           << spt << "; ++p) re[p] = im[p] = 0.0f;\n";
         for (size_t u = 0; u < units.size(); ++u)
-            if (units[u].root == r) b << "      fd_u" << u << "(V, cs, sn, re, im);\n";
+            if (units[u].root == r)
+                b << "      fd_u" << u << "(V, cs, sn, re, im);\n" << (sync_units ? "      __syncthreads();\n" : "");
         b << "      flush_samples<" << r << ", " << (rt & 255u) << ", " << (((rt >> 24) & 255u) ? 1 : 0) << ", "
           << spt << ", " << N << ">(k, re, im);\n    }\n";
     }
