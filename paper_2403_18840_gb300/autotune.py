@@ -118,13 +118,11 @@ def best_load(order, roots, v, params, copies=4, n_samples=1 << 22, reps=2):
     loads of one image in one process differ by up to ~10 %, each stable for
     the life of the load.  The image comes from the compile cache after the
     first load, so a further load costs a library load and a short launch."""
-    best = None
+    loads = []                       # all held until the choice, so each load gets new addresses
     for _ in range(copies):
         G = _jit_graph(order, roots, v)
-        ms = _time(G, params, n_samples, reps)
-        if best is None or ms < best[1]:
-            best = (G, ms)
-    return best
+        loads.append((G, _time(G, params, n_samples, reps)))
+    return min(loads, key=lambda gm: gm[1])
 
 
 def tune_jit(order, roots, params, n_samples=1 << 22, variants=None, force=False, log=None, copies=3):
