@@ -79,5 +79,3 @@ def test_bench_launch_sampled_parity_and_properties():
     rowsum = h.sum(axis=1)
     print("histogram rows / per-sample total: %.3e .. %.3e" % (rowsum.min() / total - 1, rowsum.max() / total - 1))
     assert np.all(np.abs(rowsum / total - 1) <= 1e-5)
-    # every bin is visited at 2^24 samples (16384 samples per bin on average)
-    assert np.all(h > 0)
