@@ -121,7 +121,7 @@ NCU_TRAFFIC = dict(variant=dict(threads=256, min_blocks=1, spt=4, unit_cap=12000
 
 
 def ncu_traffic(tuned, n, keys=("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap",
-                                "pair")):
+                                "pair", "sv_smem")):
     """Captured DRAM bytes of one launch of n samples, or None for an uncaptured variant."""
     if NCU_TRAFFIC is None:
         return None

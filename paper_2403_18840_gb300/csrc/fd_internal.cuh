@@ -69,6 +69,7 @@ struct fd_graph {
     int jit_threads = 0, jit_min_blocks = 0, jit_regs = 0, jit_local_bytes = 0, jit_modules = 0, jit_per_sm = 1;
     int jit_spt = 1;
     int jit_hist_cap = 0;           // floats of dynamic shared memory the kernel may take for a tile histogram
+    int jit_sv_bytes = 0;           // dynamic shared memory of the per-sample inputs (before the histogram)
     double jit_compile_s = 0.0;
     bool jit_enabled = false;       // evaluation uses the specialised kernel
 };

@@ -360,12 +360,13 @@ struct Unit {
 };
 
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair, int sync_units);
+                          int leaf_calls, int pair, int sync_units, int sv_smem);
 
 Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units, int sync_every,
-                     int leaf_calls, int spt = 1, int unit_cap = 6000, int pair = 0) {
+                     int leaf_calls, int spt = 1, int unit_cap = 6000, int pair = 0, int sv_smem = 0) {
     if (spt > 1)
-        return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls, pair, sync_every);
+        return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls, pair, sync_every,
+                                 sv_smem);
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -490,8 +491,11 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
 // sync_units != 0: a block barrier after every unit call, so that the warps of
 // a CTA run the same unit together and share its instruction-cache lines
 // (every thread calls every unit: the barriers are uniform).
+// sv_smem != 0: the per-sample inputs in shared memory, sample p of a thread
+// at V[p * T] (otherwise a local array, V[p]).
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair, int sync_units) {
+                          int leaf_calls, int pair, int sync_units, int sv_smem) {
+    const std::string vs = sv_smem ? " * " + std::to_string(T) : "";
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -573,7 +577,8 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         if (pair) {
             // samples p and p + 1 in the two lanes of packed arithmetic
             src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
-                   << "; p += 2) {\n    const FdSVT<FdF2> W = fd_pack(V[p], V[p + 1]);\n    FdF2 r = 0.0f, i = 0.0f, v;\n";
+                   << "; p += 2) {\n    const FdSVT<FdF2> W = fd_pack(V[p" << vs << "], V[(p + 1)" << vs
+                   << "]);\n    FdF2 r = 0.0f, i = 0.0f, v;\n";
             for (int i : units[u].slices) {
                 const std::string c0 = "p * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
                 const std::string c1 = "(p + 1) * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
@@ -587,7 +592,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
                << "; ++p) {\n    float r = 0.0f, i = 0.0f, v;\n";
         for (int i : units[u].slices)
-            src[m] << "    v = fd_s" << i << "(V[p]); r = fmaf(v, cs[p * " << N << " + " << sl[i].line
+            src[m] << "    v = fd_s" << i << "(V[p" << vs << "]); r = fmaf(v, cs[p * " << N << " + " << sl[i].line
                    << "], r); i = fmaf(v, sn[p * " << N << " + " << sl[i].line << "], i);\n";
         src[m] << "    re[p] += r;\n    im[p] += i;\n  }\n}\n";
     }
@@ -610,7 +615,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
     src[0] << b.str();
     src[0] << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks
            << ") fd_jit_kernel(const __grid_constant__ EvalArgs A) {\n  jit_main_loop<FdBody, " << N << ", " << DIM
-           << ", " << R << ", " << T << ", " << spt << ">(A);\n}\n";
+           << ", " << R << ", " << T << ", " << spt << ", " << (sv_smem ? T : 1) << ">(A);\n}\n";
     for (int m = 0; m < n_mod; ++m) Pg.modules[m] = src[m].str();
     return Pg;
 }
@@ -722,7 +727,7 @@ fd_status jit_launch(const fd_graph *g, EvalArgs &args, cudaStream_t stream) {
     const int grid = std::min(items, n_sm * g->jit_per_sm);
     void *params[1] = {(void *)&args};
     FD_CHECK_CUDA(cudaLaunchKernel((const void *)g->jit_kernel, dim3(grid), dim3(g->jit_threads), params,
-                                   (size_t)args.hist_smem * sizeof(float), stream));
+                                   (size_t)g->jit_sv_bytes + (size_t)args.hist_smem * sizeof(float), stream));
     return FD_OK;
 }
 
@@ -737,12 +742,13 @@ fd_status check_options(const fd_jit_options *o) {
     FD_REQUIRE(o->unit_cap >= 0, "unit_cap must be >= 0");
     FD_REQUIRE(o->pair == 0 || (o->spt >= 2 && o->spt % 2 == 0 && !o->leaf_calls),
                "packed pairs need an even number of samples per thread and inlined leaves");
+    FD_REQUIRE(o->sv_smem == 0 || o->spt >= 2, "per-sample inputs in shared memory need spt >= 2");
     return FD_OK;
 }
 
 Program emit(const fd_graph &g, const fd_jit_options &o) {
     return emit_program(g, o.threads, o.min_blocks, o.max_modules, o.root_units, o.sync_every, o.leaf_calls, o.spt,
-                        o.unit_cap, o.pair);
+                        o.unit_cap, o.pair, o.sv_smem);
 }
 }  // namespace
 
@@ -814,24 +820,42 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const 
         cudaLibraryUnload(lib);
         return fd::cuda_error(e, "loading the specialised kernel");
     }
+    // dynamic shared memory: the per-sample inputs (sv_smem: threads x spt rows
+    // of FdSV), then the tile histogram in what the resident CTAs leave free,
+    // at most 96 KB so that the rest of the unified L1 keeps the per-thread
+    // local arrays of the sample-loop variants
+    const long sv_b = opt->sv_smem ? (long)threads * opt->spt * (long)sizeof(FdSV) : 0;
+    int sm_total = 0, optin = 0, reserved = 0, hist_cap = 0;
+    const bool have_attrs =
+        cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess;
+    if (sv_b > 0) {
+        cudaError_t es = have_attrs ? cudaSuccess : cudaErrorInvalidValue;
+        if (es == cudaSuccess && sv_b + (long)attr.sharedSizeBytes > optin) es = cudaErrorInvalidValue;
+        if (es == cudaSuccess)
+            es = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv_b);
+        if (es != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaLibraryUnload(lib);
+            return fd::set_error(FD_EINVAL, "the per-sample inputs (" + std::to_string(sv_b) +
+                                                " bytes per block) do not fit in shared memory");
+        }
+    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kern, threads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kern, threads, (size_t)sv_b) !=
+        cudaSuccess) {
         (void)cudaGetLastError();
         per_sm = std::max(1, 65536 / (std::max(attr.numRegs, 1) * threads));
     }
     per_sm = std::max(per_sm, 1);
-    // dynamic shared memory for tile histograms: what the resident CTAs leave
-    // free, at most 96 KB so that the rest of the unified L1 keeps the
-    // per-thread local arrays of the sample-loop variants
-    int sm_total = 0, optin = 0, reserved = 0, hist_cap = 0;
-    if (cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
-        const long free_b = std::min<long>((long)sm_total / per_sm - reserved, optin) - (long)attr.sharedSizeBytes;
+    if (have_attrs) {
+        const long free_b =
+            std::min<long>((long)sm_total / per_sm - reserved, optin) - (long)attr.sharedSizeBytes - sv_b;
         const long cap_b = std::min<long>(free_b, 96 * 1024) & ~15L;
         if (cap_b > 0) {
-            if (cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_b) ==
-                cudaSuccess)
+            if (cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sv_b + cap_b)) == cudaSuccess)
                 hist_cap = (int)(cap_b / (long)sizeof(float));
             else
                 (void)cudaGetLastError();   // no tile histograms: global atomics only
@@ -840,6 +864,7 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const 
     if (g->jit_lib) cudaLibraryUnload(g->jit_lib);
     g->jit_per_sm = per_sm;
     g->jit_hist_cap = hist_cap;
+    g->jit_sv_bytes = (int)sv_b;
     g->jit_lib = lib;
     g->jit_kernel = kern;
     g->jit_threads = threads;

@@ -263,6 +263,7 @@ template <class T>
 struct FdSVT {
     T kx[FD_MAX_ORDER], ky[FD_MAX_ORDER], kz[FD_MAX_ORDER], t[FD_MAX_ORDER];
     float kext, beta, mu, Lam;
+    float pad;                 // 29 words for float: an odd stride, so [sample][thread] rows in shared memory are conflict-free
 };
 using FdSV = FdSVT<float>;
 
@@ -520,13 +521,17 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
 // Variant with P samples per thread per pass, handled one after another by
 // every compilation unit (Body::run loops over the samples inside each unit):
 // the unit's code is fetched once and then re-executed from the instruction
-// cache for the other P - 1 samples, at no cost in registers (the per-sample
-// inputs live in local memory).
-template <class Body, int N, int DIM, int R, int T, int P>
+// cache for the other P - 1 samples, at no cost in registers.  The per-sample
+// inputs live in local memory (SVS = 1) or, with SVS = T, in dynamic shared
+// memory as [sample][thread] rows of FdSV (sample p of this thread at
+// V[p * SVS]); the tile histogram, when the launch provides it, follows them.
+template <class Body, int N, int DIM, int R, int T, int P, int SVS = 1>
 __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
     __shared__ double acc[T / 32][R * 8];
     __shared__ int next_item;
-    extern __shared__ float hist_smem[];
+    extern __shared__ float dyn_smem[];
+    constexpr int SV_FLOATS = SVS > 1 ? T * P * (int)(sizeof(FdSV) / sizeof(float)) : 0;
+    float *const hist_smem = dyn_smem + SV_FLOATS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = A.n_inst * A.tiles_per_inst;
     const uint32_t iter = A.iter + (A.iter_dev ? *A.iter_dev : 0u);
@@ -543,7 +548,8 @@ __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
         const int64_t first = (int64_t)tile * A.tile;
         const int64_t last = min(first + A.tile, A.n_per_inst);
         for (int64_t base = first; base < last; base += (int64_t)T * P) {
-            FdSV V[P];
+            FdSV Vl[SVS > 1 ? 1 : P];
+            FdSV *const V = SVS > 1 ? reinterpret_cast<FdSV *>(dyn_smem) + tid : Vl;
             float jac[P][N];
             int bins[P][DIM];
             float cs[P * N], sn[P * N];
@@ -553,11 +559,11 @@ __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
                 const int64_t i = base + (int64_t)p * T + tid;
                 const bool valid = i < last;
                 const int64_t idx = valid ? i : first;
-                sample_point<N, DIM>(D, A, idx, iter, V[p], jac[p], bins[p]);
+                sample_point<N, DIM>(D, A, idx, iter, V[p * SVS], jac[p], bins[p]);
                 cs[p * N] = 1.0f;
                 sn[p * N] = 0.0f;
 #pragma unroll
-                for (int j = 1; j < N; ++j) sincospif(V[p].t[j], &sn[p * N + j], &cs[p * N + j]);
+                for (int j = 1; j < N; ++j) sincospif(V[p * SVS].t[j], &sn[p * N + j], &cs[p * N + j]);
                 K[p] = FdSink<N>{acc[warp], jac[p], valid, 0.0f, A.per_sample_f,
                                  (int64_t)D.id * A.r_max * 2 * A.n_per_inst + idx, A.n_per_inst};
             }

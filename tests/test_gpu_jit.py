@@ -209,18 +209,19 @@ def test_jit_captured_iteration(api):
     assert int(a.d_iter.item()) == 2
 
 
-@pytest.mark.parametrize("pair", [False, True])
+@pytest.mark.parametrize("pair,sv_smem", [(False, False), (True, False), (False, True)])
 @pytest.mark.parametrize("order,with_dk,n", [(3, True, 2 * 1024 + 77), (5, False, 160)])
-def test_jit_sample_loop_variant(api, order, with_dk, n, pair):
+def test_jit_sample_loop_variant(api, order, with_dk, n, pair, sv_smem):
     # spt samples per thread, each compilation unit looping over them (with
-    # pair: two samples at a time in packed two-lane arithmetic); a pass
-    # covers 256 x 4 samples, so n spans several passes and a ragged tail
+    # pair: two samples at a time in packed two-lane arithmetic; with sv_smem:
+    # the samples' inputs in shared memory); a pass covers 256 x 4 samples, so
+    # n spans several passes and a ragged tail
     G = api.Graph(order, with_dk=with_dk, budget=8192)
-    info = G.jit(threads=256, min_blocks=1, spt=4, pair=pair)
+    info = G.jit(threads=256, min_blocks=1, spt=4, pair=pair, sv_smem=sv_smem)
     assert info["enabled"]
     f, st, _ = _run(api, G, order, n, 37)
     ref, mag = _oracle(order, G.roots, n, 37)
-    _compare(f[:len(G.roots)], ref, mag, "jit spt 4 pair %s order %d" % (pair, order))
+    _compare(f[:len(G.roots)], ref, mag, "jit spt 4 pair %s sv_smem %s order %d" % (pair, sv_smem, order))
     for r in range(len(G.roots)):
         assert abs(st[r, 0, 0] - f[r, 0].mean()) <= 1e-6 * (np.abs(f[r, 0]).mean() + 1e-30)
 
@@ -249,3 +250,28 @@ def test_jit_sample_loop_matches_one_sample_per_thread(api):
     fb, _, _ = _run(api, b, order, n, 5)
     scale = np.abs(fb).max(axis=2, keepdims=True) + 1e-30
     assert np.max(np.abs(fa - fb) / scale) < 1e-5
+
+
+def test_jit_shared_inputs_bitwise_equal_to_local(api):
+    # the inputs' storage changes nothing in the arithmetic: several tiles and a
+    # ragged tail, VEGAS map and histogram, bitwise equal outputs and partials
+    order, n, nb = 3, 3 * 16384 + 77, 64
+    e = _fp32_edges(8, 4 * order - 1, nb)
+    out = []
+    for sv in (False, True):
+        G = api.Graph(order, with_dk=True, budget=8192)
+        G.jit(threads=256, min_blocks=1, spt=4, sv_smem=sv)
+        m = api.Vegas(G.dim, nb)
+        m.set_edges(e)
+        f, st, plan = _run(api, G, order, n, 6, maps=[m])
+        out.append((f, plan.partials.cpu().numpy(), m.hist()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.allclose(out[0][2], out[1][2], rtol=1e-12, atol=0)
+
+
+def test_jit_shared_inputs_too_large_is_rejected(api):
+    # 256 threads x 8 samples x 116 bytes exceed a block's shared memory
+    G = api.Graph(2, budget=8192)
+    with pytest.raises(api.L.FdError):
+        G.jit(threads=256, min_blocks=1, spt=8, sv_smem=True)

@@ -77,8 +77,8 @@ def test_sample_loop_units_cover_every_slice_once(unit_cap, pair):
     for m in range(n_mod):
         src, _ = api.jit_source(tape, m, **kw)
         slices += re.findall(r"__device__ __forceinline__ %s (fd_s\d+)\(const FdSVT<%s> &V\) \{" % (vt, vt), src)
-        if pair:
-            assert "fd_pack(V[p], V[p + 1])" in src or "fd_u" not in src
+        if pair:   # every unit defined here packs two samples per pass
+            assert src.count("fd_pack(") == len(re.findall(r"__noinline__ void fd_u\d+", src))
         units += re.findall(r"__device__ __noinline__ void (fd_u\d+)\(", src)
     body, _ = api.jit_source(tape, 0, **kw)
     assert slices and len(slices) == len(set(slices))
@@ -91,8 +91,10 @@ def test_sample_loop_units_cover_every_slice_once(unit_cap, pair):
         assert len(units) == len(fdgraph.graph_roots(5))   # one unit per root
 
 
-@pytest.mark.parametrize("kw", [dict(spt=3, pair=True), dict(spt=1, pair=True), dict(spt=4, pair=True, leaf_calls=True)])
-def test_packed_pairs_reject_invalid_options(kw):
-    # packed pairs need an even number of samples per thread and inlined leaves
+@pytest.mark.parametrize("kw", [dict(spt=3, pair=True), dict(spt=1, pair=True), dict(spt=4, pair=True, leaf_calls=True),
+                                dict(spt=1, sv_smem=True)])
+def test_sample_loop_options_reject_invalid_combinations(kw):
+    # packed pairs need an even number of samples per thread and inlined
+    # leaves; inputs in shared memory need the sample loop
     with pytest.raises(api.L.FdError):
         api.jit_source(_tape(2, False), 0, threads=256, min_blocks=1, **kw)
