@@ -255,6 +255,7 @@ def test_jit_sample_loop_matches_one_sample_per_thread(api):
 def test_jit_shared_inputs_bitwise_equal_to_local(api):
     # the inputs' storage changes nothing in the arithmetic: several tiles and a
     # ragged tail, VEGAS map and histogram, bitwise equal outputs and partials
+    # (the histogram's FP32 shared-memory atomics arrive in any order: FP32-level)
     order, n, nb = 3, 3 * 16384 + 77, 64
     e = _fp32_edges(8, 4 * order - 1, nb)
     out = []
@@ -267,7 +268,7 @@ def test_jit_shared_inputs_bitwise_equal_to_local(api):
         out.append((f, plan.partials.cpu().numpy(), m.hist()))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
-    assert np.allclose(out[0][2], out[1][2], rtol=1e-12, atol=0)
+    assert np.allclose(out[0][2], out[1][2], rtol=1e-5, atol=0)
 
 
 def test_jit_shared_inputs_too_large_is_rejected(api):
