@@ -24,10 +24,10 @@ SCHEDULES = [dict(budget=b, bundle=w, window=8 * w) for b in (96, 128, 160) for 
 SHAPES = [(128, 2), (256, 1), (128, 1), (64, 2)]
 # specialised-kernel variants (fd_jit_options; unlisted options at their defaults)
 JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=1), dict(threads=256, min_blocks=1, spt=4, unit_cap=12000),
-                dict(threads=256, min_blocks=1, spt=4, unit_cap=6000),
-                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1),
-                dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sync_every=1),
-                dict(threads=256, min_blocks=1, spt=8, unit_cap=12000, sync_every=1)]
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sv_smem=True),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sv_smem=True),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1, sv_smem=True),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sync_every=1, sv_smem=True)]
 JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap", "pair", "sv_smem")
 
 
@@ -45,8 +45,10 @@ def _load():
     return {}
 
 
-def _time(G, params, n, reps=2):
-    plan = api.EvalPlan([G], [params], [0], n)
+def _time(G, params, n, reps=2, n_bins=None):
+    """ms per launch of n samples (identity sampler, or a uniform VEGAS grid of n_bins with its histogram)."""
+    maps = [api.Vegas(G.dim, n_bins)] if n_bins else None
+    plan = api.EvalPlan([G], [params], [0], n, maps=maps)
     plan.run(7, 0)
     torch.cuda.synchronize()
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -110,25 +112,26 @@ def _jit_graph(order, roots, v):
     return G
 
 
-def best_load(order, roots, v, params, copies=4, n_samples=1 << 22, reps=2):
-    """(graph, ms) of the fastest of `copies` loads of the same specialised kernel.
+def best_load(order, roots, v, params, copies=4, n_samples=1 << 24, reps=2, n_bins=1024):
+    """(graph, ms) of the fastest of `copies` loads of the same specialised kernel,
+    timed on the production path (a VEGAS grid of n_bins with its histogram).
 
     The kernel's speed depends on where the driver places its code (it runs
-    ~30k straight-line instructions per sample out of the instruction cache):
-    loads of one image in one process differ by up to ~10 %, each stable for
+    ~26k straight-line instructions per sample out of the instruction cache):
+    loads of one image in one process differ by up to ~20 %, each stable for
     the life of the load.  The image comes from the compile cache after the
-    first load, so a further load costs a library load and a short launch."""
+    first load, so a further load costs a library load and a few launches."""
     loads = []                       # all held until the choice, so each load gets new addresses
     for _ in range(copies):
         G = _jit_graph(order, roots, v)
-        loads.append((G, _time(G, params, n_samples, reps)))
+        loads.append((G, _time(G, params, n_samples, reps, n_bins)))
     return min(loads, key=lambda gm: gm[1])
 
 
-def tune_jit(order, roots, params, n_samples=1 << 22, variants=None, force=False, log=None, copies=3):
-    """Best {'threads','min_blocks','root_units','sync_every','leaf_calls','spt','unit_cap','pair',
+def tune_jit(order, roots, params, n_samples=1 << 24, variants=None, force=False, log=None, copies=3):
+    """Best {'threads','min_blocks','root_units','sync_every','leaf_calls','spt','unit_cap','pair','sv_smem',
     'samples_per_s',...} for the specialised kernel, each variant scored at its best of `copies` loads."""
-    key = "jit5|" + _key(order, roots)
+    key = "jit6|" + _key(order, roots)
     cache = _load()
     if key in cache and not force:
         return cache[key]
