@@ -116,8 +116,8 @@ def _peaks():
 # of the variant named here (the traffic is local-memory lines evicted from
 # L2 and grows with the samples).  Another variant, or a change of the
 # kernel's code since the capture, has none: traffic is then reported as null.
-NCU_TRAFFIC = dict(variant=dict(threads=256, min_blocks=1, spt=4, unit_cap=12000), bytes_per_sample=403.1,
-                   capture="profiles/fd_jit_kernel_order5_vegas_ncu_full.md")
+NCU_TRAFFIC = dict(variant=dict(threads=256, min_blocks=1, sync_every=1, spt=4, unit_cap=12000, sv_smem=True),
+                   bytes_per_sample=235.1, capture="profiles/fd_jit_kernel_order5_vegas_ncu_full.md")
 
 
 def ncu_traffic(tuned, n, keys=("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap",
