@@ -121,7 +121,7 @@ NCU_TRAFFIC = dict(variant=dict(threads=256, min_blocks=1, sync_every=1, spt=4, 
 
 
 def ncu_traffic(tuned, n, keys=("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap",
-                                "pair", "sv_smem")):
+                                "pair", "sv_smem", "cross_roots")):
     """Captured DRAM bytes of one launch of n samples, or None for an uncaptured variant."""
     if NCU_TRAFFIC is None:
         return None
@@ -232,7 +232,10 @@ def run_ours(args, rank, world, dist):
     G, tuned = autotune.tuned_jit_graph(order, roots, params[0])
     # algorithmic work: every leaf family computed once (no recomputation)
     flops_ps, sfu_ps = fdgraph.tape_work(api.tape_bytes(order, roots, budget=1 << 13, bundle=1, window=1))
-    exec_flops_ps, exec_sfu_ps = fdgraph.specialised_work(G.tape, tuned.get("root_units", True))
+    loop = (tuned.get("spt") or 1) > 1
+    exec_flops_ps, exec_sfu_ps = fdgraph.specialised_work(
+        G.tape, tuned.get("root_units", True), unit_cap=(tuned.get("unit_cap") or 6000) if loop else None,
+        cross_roots=bool(tuned.get("cross_roots")) and loop)
     V = api.Vegas(G.dim, WL["n_bins"])
     n = args.samples
     plan = api.EvalPlan([G], params, [0], n, maps=[V])

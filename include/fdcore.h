@@ -115,13 +115,17 @@ fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_
  *               both samples);
  *  sv_smem      != 0 (spt > 1): the per-sample inputs of the thread's spt
  *               samples (momenta, times) in shared memory instead of local
- *               memory; FD_EINVAL from fd_graph_jit when they do not fit.
+ *               memory; FD_EINVAL from fd_graph_jit when they do not fit;
+ *  cross_roots  != 0 (spt > 1): units pack consecutive slices across root
+ *               boundaries, so leaves that neighbouring roots share are
+ *               computed once per unit.
  * cache_dir (may be NULL): directory for compiled images, keyed by a hash of
  * the generated source and options.  Synchronous; FD_ENOTSUP when the
  * run-time compiler is unavailable or fails (fd_last_error holds its log).
  * Results agree with the interpreter up to FP32 rounding order. */
 typedef struct {
-    int32_t threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt, unit_cap, pair, sv_smem;
+    int32_t threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt, unit_cap, pair, sv_smem,
+        cross_roots;
 } fd_jit_options;
 fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const char *cache_dir);
 /* Switch evaluation of g between its specialised kernel (on != 0) and the interpreter. */

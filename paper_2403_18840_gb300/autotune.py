@@ -28,7 +28,8 @@ JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=1), dict(threads=256, min_bl
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sync_every=1, sv_smem=True)]
-JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap", "pair", "sv_smem")
+JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap", "pair", "sv_smem",
+            "cross_roots")
 
 
 def _key(order, roots):

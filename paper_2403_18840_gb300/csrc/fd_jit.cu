@@ -360,13 +360,14 @@ struct Unit {
 };
 
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair, int sync_units, int sv_smem);
+                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots);
 
 Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units, int sync_every,
-                     int leaf_calls, int spt = 1, int unit_cap = 6000, int pair = 0, int sv_smem = 0) {
+                     int leaf_calls, int spt = 1, int unit_cap = 6000, int pair = 0, int sv_smem = 0,
+                     int cross_roots = 0) {
     if (spt > 1)
         return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls, pair, sync_every,
-                                 sv_smem);
+                                 sv_smem, cross_roots);
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -493,8 +494,12 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
 // (every thread calls every unit: the barriers are uniform).
 // sv_smem != 0: the per-sample inputs in shared memory, sample p of a thread
 // at V[p * T] (otherwise a local array, V[p]).
+// cross_roots != 0: units pack consecutive slices across root boundaries (the
+// leaves that neighbouring roots share are computed once per unit); each
+// unit adds into the accumulators of the roots it touches, and every root is
+// flushed after all units.
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair, int sync_units, int sv_smem) {
+                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots) {
     const std::string vs = sv_smem ? " * " + std::to_string(T) : "";
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
@@ -518,7 +523,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         return c + 30.0 * (double)(std::unique(leaves.begin(), leaves.end()) - leaves.begin());
     };
     for (size_t i = 0; i < sl.size(); ++i) {
-        if (!units.empty() && units.back().root == sl[i].root) {
+        if (!units.empty() && (cross_roots || units.back().root == sl[i].root)) {
             std::vector<int> grown = units.back().slices;
             grown.push_back((int)i);
             const double c = unit_cost(grown);
@@ -568,6 +573,65 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
                << "\n#include \"fd_jit_rt.cuh\"\n";
     const char *unit_qual = multi ? "extern \"C\" __device__ __noinline__" : "static __device__ __noinline__";
     const std::string sig = "(const FdSV *V, const float *cs, const float *sn, float *re, float *im)";
+    if (cross_roots) {
+        // re/im: [root][sample] accumulators of the whole graph
+        for (size_t u = 0; u < units.size(); ++u) {
+            const int m = mod_of[u];
+            for (int i : units[u].slices)
+                src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, "static __device__ __forceinline__",
+                                     0, leaf_calls, pair ? "FdF2" : "float");
+            if (multi && m != 0) src[0] << "extern \"C\" __device__ void fd_u" << u << sig << ";\n";
+            const std::vector<int> &us = units[u].slices;
+            src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
+                   << (pair ? "; p += 2) {\n    const FdSVT<FdF2> W = fd_pack(V[p" + vs + "], V[(p + 1)" + vs + "]);\n"
+                            : "; ++p) {\n")
+                   << "    " << (pair ? "FdF2" : "float") << " v;\n";
+            for (size_t a = 0; a < us.size();) {
+                const int r = sl[us[a]].root;
+                src[m] << "    {\n      " << (pair ? "FdF2" : "float") << " r = 0.0f, i = 0.0f;\n";
+                for (; a < us.size() && sl[us[a]].root == r; ++a) {
+                    const int i = us[a];
+                    const std::string c0 = "p * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
+                    if (pair) {
+                        const std::string c1 = "(p + 1) * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
+                        src[m] << "      v = fd_s" << i << "(W); r = fd_fma(v, FdF2(cs[" << c0 << "], cs[" << c1
+                               << "]), r); i = fd_fma(v, FdF2(sn[" << c0 << "], sn[" << c1 << "]), i);\n";
+                    } else {
+                        src[m] << "      v = fd_s" << i << "(V[p" << vs << "]); r = fmaf(v, cs[" << c0
+                               << "], r); i = fmaf(v, sn[" << c0 << "], i);\n";
+                    }
+                }
+                const std::string o = std::to_string(r * spt) + " + p";
+                if (pair)
+                    src[m] << "      re[" << o << "] += r.v.x;\n      re[" << o << " + 1] += r.v.y;\n      im[" << o
+                           << "] += i.v.x;\n      im[" << o << " + 1] += i.v.y;\n    }\n";
+                else
+                    src[m] << "      re[" << o << "] += r;\n      im[" << o << "] += i;\n    }\n";
+            }
+            src[m] << "  }\n}\n";
+        }
+        std::ostringstream b;
+        b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV *V, "
+             "const float *cs, const float *sn, K *k) {\n    float re["
+          << R * spt << "], im[" << R * spt << "];\n#pragma unroll\n    for (int q = 0; q < " << R * spt
+          << "; ++q) re[q] = im[q] = 0.0f;\n";
+        for (size_t u = 0; u < units.size(); ++u)
+            b << "    fd_u" << u << "(V, cs, sn, re, im);\n" << (sync_units ? "    __syncthreads();\n" : "");
+        for (const TIns &t : ins) {
+            if (t.op != OP_RFLUSH) continue;
+            const int r = (int)fd_(g.h_tape[t.w]);
+            const uint32_t rt = g.h_roots[2 * r];
+            b << "    flush_samples<" << r << ", " << (rt & 255u) << ", " << (((rt >> 24) & 255u) ? 1 : 0) << ", " << spt
+              << ", " << N << ">(k, re + " << r * spt << ", im + " << r * spt << ");\n";
+        }
+        b << "  }\n};\n";
+        src[0] << b.str();
+        src[0] << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks
+               << ") fd_jit_kernel(const __grid_constant__ EvalArgs A) {\n  jit_main_loop<FdBody, " << N << ", " << DIM
+               << ", " << R << ", " << T << ", " << spt << ", " << (sv_smem ? T : 1) << ">(A);\n}\n";
+        for (int m = 0; m < n_mod; ++m) Pg.modules[m] = src[m].str();
+        return Pg;
+    }
     for (size_t u = 0; u < units.size(); ++u) {
         const int m = mod_of[u];
         for (int i : units[u].slices)
@@ -743,12 +807,13 @@ fd_status check_options(const fd_jit_options *o) {
     FD_REQUIRE(o->pair == 0 || (o->spt >= 2 && o->spt % 2 == 0 && !o->leaf_calls),
                "packed pairs need an even number of samples per thread and inlined leaves");
     FD_REQUIRE(o->sv_smem == 0 || o->spt >= 2, "per-sample inputs in shared memory need spt >= 2");
+    FD_REQUIRE(o->cross_roots == 0 || o->spt >= 2, "units across roots need spt >= 2");
     return FD_OK;
 }
 
 Program emit(const fd_graph &g, const fd_jit_options &o) {
     return emit_program(g, o.threads, o.min_blocks, o.max_modules, o.root_units, o.sync_every, o.leaf_calls, o.spt,
-                        o.unit_cap, o.pair, o.sv_smem);
+                        o.unit_cap, o.pair, o.sv_smem, o.cross_roots);
 }
 }  // namespace
 

@@ -834,13 +834,16 @@ def _leaf_work(w):
     return flops + 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0), 1
 
 
-def specialised_work(data, root_units=True):
+def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False):
     """(fp32_flops, sfu_ops) per sample executed by the specialised kernel.
 
     The kernel evaluates every root-accumulate slice of the tape as straight-line
-    code; leaves shared between slices are recomputed in each compilation unit
-    (one unit per root with root_units, else one per slice), so the leaf work
-    exceeds the tape's.  Same counting rule as tape_work.
+    code; leaves shared between slices are recomputed in each compilation unit,
+    so the leaf work exceeds the tape's.  Units as the generator forms them: one
+    per root with root_units, else one per slice; with unit_cap (the sample-loop
+    kernels) consecutive slices of a root, or across roots with cross_roots,
+    packed while FMAs + 30 per distinct leaf stay within the cap.  Same counting
+    rule as tape_work.
     """
     hdr = struct.unpack("<16I", data[:64])
     order, dim, n_roots, n_instr, ins_off = hdr[2], hdr[3], hdr[4], hdr[6], hdr[8]
@@ -859,7 +862,7 @@ def specialised_work(data, root_units=True):
         if op != OP_NOP:
             ins.append((op, k, 0))
         k += 1
-    units = []                   # per unit: set of (instr, member) FMAs and set of leaf instrs
+    slices = []                  # per slice: root, set of (instr, member) FMAs, set of leaf instrs
     root = 0
     for i, (op, wk, _) in enumerate(ins):
         if op == OP_RFLUSH:
@@ -888,11 +891,19 @@ def specialised_work(data, root_units=True):
                     leaves.add(j)
             elif oj == OP_CONST:
                 need.discard((words[wj] >> 6) & 16383)
-        if root_units and units and units[-1][0] == root:
-            units[-1][1].update(fmas)
-            units[-1][2].update(leaves)
-        else:
-            units.append((root, fmas, leaves))
+        slices.append((root, fmas, leaves))
+    units = []                   # per unit: [root of its first slice, FMAs, leaves]
+    for r, fmas, leaves in slices:
+        if units and (cross_roots or units[-1][0] == r):
+            grown_f, grown_l = units[-1][1] | fmas, units[-1][2] | leaves
+            if unit_cap is None:
+                fits = root_units
+            else:
+                fits = len(grown_f) + 30 * len(grown_l) <= unit_cap
+            if fits:
+                units[-1][1], units[-1][2] = grown_f, grown_l
+                continue
+        units.append([r, set(fmas), set(leaves)])
     flops = sfu = 0
     for _, fmas, leaves in units:
         for (j, q) in fmas:
@@ -902,7 +913,7 @@ def specialised_work(data, root_units=True):
             f, u = _leaf_work(words[ins[j][1]])
             flops += f
             sfu += u
-    n_racc = sum(1 for op, _, _ in ins if op == OP_RACC)
+    n_racc = len(slices)
     flops += 4 * n_racc + 6 * dim + 14 * order + 3 * (order - 1) + 2 * n_roots
     sfu += 2 * order + (order - 1)
     return flops, sfu

@@ -209,19 +209,22 @@ def test_jit_captured_iteration(api):
     assert int(a.d_iter.item()) == 2
 
 
-@pytest.mark.parametrize("pair,sv_smem", [(False, False), (True, False), (False, True)])
+@pytest.mark.parametrize("pair,sv_smem,cross", [(False, False, False), (True, False, False), (False, True, False),
+                                                (False, True, True), (True, False, True)])
 @pytest.mark.parametrize("order,with_dk,n", [(3, True, 2 * 1024 + 77), (5, False, 160)])
-def test_jit_sample_loop_variant(api, order, with_dk, n, pair, sv_smem):
+def test_jit_sample_loop_variant(api, order, with_dk, n, pair, sv_smem, cross):
     # spt samples per thread, each compilation unit looping over them (with
     # pair: two samples at a time in packed two-lane arithmetic; with sv_smem:
-    # the samples' inputs in shared memory); a pass covers 256 x 4 samples, so
-    # n spans several passes and a ragged tail
+    # the samples' inputs in shared memory; with cross: units spanning roots);
+    # a pass covers 256 x 4 samples, so n spans several passes and a ragged tail
     G = api.Graph(order, with_dk=with_dk, budget=8192)
-    info = G.jit(threads=256, min_blocks=1, spt=4, pair=pair, sv_smem=sv_smem)
+    info = G.jit(threads=256, min_blocks=1, spt=4, unit_cap=6000, pair=pair, sv_smem=sv_smem, cross_roots=cross,
+                 sync_every=1 if cross else 0)
     assert info["enabled"]
     f, st, _ = _run(api, G, order, n, 37)
     ref, mag = _oracle(order, G.roots, n, 37)
-    _compare(f[:len(G.roots)], ref, mag, "jit spt 4 pair %s sv_smem %s order %d" % (pair, sv_smem, order))
+    _compare(f[:len(G.roots)], ref, mag, "jit spt 4 pair %s sv_smem %s cross %s order %d" % (pair, sv_smem, cross,
+                                                                                              order))
     for r in range(len(G.roots)):
         assert abs(st[r, 0, 0] - f[r, 0].mean()) <= 1e-6 * (np.abs(f[r, 0]).mean() + 1e-30)
 

@@ -63,14 +63,14 @@ def test_large_graph_splits_into_linked_modules(root_units):
         assert len(defined) == len(fdgraph.graph_roots(5))
 
 
-@pytest.mark.parametrize("pair", [False, True])
+@pytest.mark.parametrize("pair,cross", [(False, False), (True, False), (False, True)])
 @pytest.mark.parametrize("unit_cap", [0, 6000, 100000])
-def test_sample_loop_units_cover_every_slice_once(unit_cap, pair):
-    # spt > 1: units pack consecutive slices of one root; every slice emitted
-    # once (in packed two-lane arithmetic with pair), every unit called once,
-    # every root flushed once per sample
+def test_sample_loop_units_cover_every_slice_once(unit_cap, pair, cross):
+    # spt > 1: units pack consecutive slices of one root (of several roots with
+    # cross_roots); every slice emitted once (in packed two-lane arithmetic
+    # with pair), every unit called once, every root flushed once per sample
     tape = _tape(5, False)
-    kw = dict(threads=256, min_blocks=1, max_modules=8, spt=4, unit_cap=unit_cap, pair=pair)
+    kw = dict(threads=256, min_blocks=1, max_modules=8, spt=4, unit_cap=unit_cap, pair=pair, cross_roots=cross)
     _, n_mod = api.jit_source(tape, 0, **kw)
     slices, units = [], []
     vt = "FdF2" if pair else "float"
@@ -87,14 +87,27 @@ def test_sample_loop_units_cover_every_slice_once(unit_cap, pair):
     assert sorted(int(r) for r in flushes) == list(range(len(fdgraph.graph_roots(5))))
     if unit_cap == 0:
         assert len(units) == len(slices)             # one slice per unit
-    if unit_cap == 100000:
-        assert len(units) == len(fdgraph.graph_roots(5))   # one unit per root
+    if unit_cap == 100000:   # one unit per root; across roots, one unit for the whole graph
+        assert len(units) == (1 if cross else len(fdgraph.graph_roots(5)))
 
 
 @pytest.mark.parametrize("kw", [dict(spt=3, pair=True), dict(spt=1, pair=True), dict(spt=4, pair=True, leaf_calls=True),
-                                dict(spt=1, sv_smem=True)])
+                                dict(spt=1, sv_smem=True), dict(spt=1, cross_roots=True)])
 def test_sample_loop_options_reject_invalid_combinations(kw):
     # packed pairs need an even number of samples per thread and inlined
     # leaves; inputs in shared memory need the sample loop
     with pytest.raises(api.L.FdError):
         api.jit_source(_tape(2, False), 0, threads=256, min_blocks=1, **kw)
+
+
+@pytest.mark.parametrize("order", [3, 5])
+def test_executed_work_model(order):
+    # one unit across all roots computes every leaf once: the tape's own work;
+    # smaller units recompute leaves, more so when they may not span roots
+    data = fdgraph.compile_graph(order, fdgraph.graph_roots(order), budget=8192).to_bytes()
+    assert fdgraph.specialised_work(data, True, 10 ** 9, True) == fdgraph.tape_work(data)
+    for cap in (6000, 12000):
+        per_root = fdgraph.specialised_work(data, True, cap, False)
+        cross = fdgraph.specialised_work(data, True, cap, True)
+        assert fdgraph.tape_work(data)[0] <= cross[0] <= per_root[0]
+        assert fdgraph.tape_work(data)[1] <= cross[1] <= per_root[1]
