@@ -317,6 +317,39 @@ fd_status fd_flow_train(fd_flow *f, const float *x, const float *w, int64_t n, i
  * Synchronous; allocates a small scratch buffer. */
 fd_status fd_measure_peak(int32_t kind, double *ops_per_s);
 
+/* ---- NF-MCMC / VEGAS-MCMC chains (Sec. V, Eqs. target_distr and
+ * nf_mcmc_estimator) --------------------------------------------------------
+ * Independence Metropolis-Hastings over proposals x ~ q that were already
+ * evaluated.  w: device FP32 [n_out][ld], the importance weights
+ * w_o = f_o(x)/q(x) of the proposals (e.g. the per-sample output of
+ * fd_integrand_eval: on a VEGAS grid q = 1/J, for flow points on the grid
+ * q = q_flow/J; rows = (root, Re/Im)); proposal k of chain c is column
+ * k * n_chains + c, so ld >= n_chains * n_steps.  The chains sample
+ * pi = alpha q + (1 - alpha) |f| with |f| = sum over o < n_sel of |w_o|
+ * (0 < alpha <= 1), accept a proposal when u < g'/g_t with g = pi/q =
+ * alpha + (1 - alpha)|f|/q and u from Philox4x32-10 with counter
+ * (chain_lo, chain_hi, iter, 0x40000000 | (step >> 2)), word step & 3, key
+ * (seed_lo, seed_hi), u = ((word >> 9) + 0.5) 2^-23; a chain with g_t = 0
+ * has no state yet and accepts its first proposal.
+ * state: device FP64 [n_out + 1][n_chains], in/out: the chains' current
+ *        weights, then g (zero-fill it before the first call).
+ * sums:  device FP64 [n_out + 2][n_chains], out: per chain the sums over the
+ *        steps k >= n_therm of w_o/g (= f/pi) and of 1/g (= q/pi), then the
+ *        number of accepted proposals.
+ * FP64 throughout, each operation rounded as written (reproducible bit for
+ * bit).  Asynchronous on stream; FD_EINVAL for sizes or alpha out of range
+ * (n_out <= 32). */
+fd_status fd_mcmc_chains(const float *w, int32_t n_out, int64_t ld, int32_t n_sel, int64_t n_chains,
+                         int32_t n_steps, double alpha, uint64_t seed, uint64_t iter, int32_t n_therm,
+                         double *state, double *sums, void *stream);
+/* Estimates from the chains' sums (Eq. nf_mcmc_estimator): out (device FP64
+ * [n_out + 1][2]) row o = (I_o = sum_c A_oc / sum_c B_c, its variance by the
+ * delta method over the independent chains: sum_c (A_oc - I_o B_c)^2 /
+ * (C (C - 1)) / mean(B)^2), last row = (accepted fraction of the n_chains x
+ * n_steps proposals, 0).  Fixed reduction order.  Asynchronous on stream. */
+fd_status fd_mcmc_estimate(const double *sums, int32_t n_out, int64_t n_chains, int32_t n_steps, double *out,
+                           void *stream);
+
 /* ---- renormalisation post-processing (host, FP64; Sec. VI.A) -------------
  * sigma_re/sigma_im/dsigma_re: FP64 [N+1][N+1][N+1] indexed (n, m, l) holding
  * Sigma^(n,m,l)(k_F, i w0) and d_k Re Sigma^(n,m,l) for n + m + l <= N.

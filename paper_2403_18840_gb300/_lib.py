@@ -86,6 +86,8 @@ SIGNATURES = {
     "fd_flow_grad": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fd_flow_train": (_i32, [_vp, _vp, _vp, _i64, _i32, _f32, _pf, _vp]),
     "fd_measure_peak": (_i32, [_i32, _pd]),
+    "fd_mcmc_chains": (_i32, [_vp, _i32, _i64, _i32, _i64, _i32, _f64, _u64, _u64, _i32, _vp, _vp, _vp]),
+    "fd_mcmc_estimate": (_i32, [_vp, _i32, _i64, _i32, _vp, _vp]),
     "fd_postprocess": (_i32, [_i32, _pd, _pd, _pd, _f64, _f64, _f64, _pd, _pd, _pd, _pd]),
 }
 

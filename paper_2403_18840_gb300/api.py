@@ -284,6 +284,31 @@ class Flow:
             self.handle = None
 
 
+class Chains:
+    """Independence Metropolis-Hastings chains over evaluated proposals (NF-MCMC
+    with flow proposals, VEGAS-MCMC with VEGAS proposals; Sec. V).  Weights w
+    [n_out][ld] (device FP32, e.g. EvalPlan.per_sample[inst].reshape(-1, n)):
+    proposal k of chain c in column k * n_chains + c."""
+
+    def __init__(self, n_out, n_chains, n_sel=1, alpha=0.5):
+        self.n_out, self.n_chains, self.n_sel, self.alpha = n_out, n_chains, n_sel, alpha
+        self.state = torch.zeros((n_out + 1, n_chains), dtype=torch.float64, device="cuda")
+        self.sums = torch.zeros((n_out + 2, n_chains), dtype=torch.float64, device="cuda")
+        self.out = torch.zeros((n_out + 1, 2), dtype=torch.float64, device="cuda")
+
+    def run(self, w, n_steps, seed, it, n_therm=0, stream=None):
+        """Advance every chain by n_steps (sums of this call in .sums); returns the
+        estimates [n_out + 1][2]: (I, variance) per component, then (accepted fraction, 0)."""
+        assert w.dtype == torch.float32 and w.is_cuda and w.dim() == 2 and w.stride(1) == 1
+        assert w.shape[0] >= self.n_out
+        L.check(L.lib().fd_mcmc_chains(_ptr(w), self.n_out, w.stride(0), self.n_sel, self.n_chains, n_steps,
+                                       self.alpha, seed, it, n_therm, _ptr(self.state), _ptr(self.sums),
+                                       _stream_ptr(stream)))
+        L.check(L.lib().fd_mcmc_estimate(_ptr(self.sums), self.n_out, self.n_chains, n_steps, _ptr(self.out),
+                                         _stream_ptr(stream)))
+        return self.out
+
+
 def measure_peak(kind):
     """Measured pipe throughput: 0 FP32 FMA (flop/s), 1 SFU ex2, 2 SFU rcp (results/s), 3 packed FP32x2 FMA (flop/s)."""
     v = ctypes.c_double()

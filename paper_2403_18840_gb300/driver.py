@@ -86,6 +86,31 @@ def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, e
     return losses
 
 
+def mcmc(G, params, vegas, flow, n_chains, n_steps, alpha, seed, it, n_therm=0, chains=None, n_sel=1, plan=None):
+    """One call of NF-MCMC (flow given: proposals from the flow on the VEGAS
+    grid's coordinates) or VEGAS-MCMC (flow None: proposals from the VEGAS map),
+    Sec. V: n_chains x n_steps proposals drawn from q and evaluated by the
+    integrand kernel (their weights f/q per root and Re/Im), then n_steps
+    Metropolis-Hastings steps of every chain (target alpha q + (1 - alpha)|f|,
+    |f| from the first n_sel weight rows).  Pass the returned chains (and plan)
+    back in to continue the same chains.  Returns (chains, plan, estimates
+    [n_out + 1][2] on the device: (I, variance) per weight row, then the
+    accepted fraction)."""
+    n = n_chains * n_steps
+    if plan is None:
+        plan = api.EvalPlan([G], [params], [0], n, maps=[vegas] if vegas is not None else None, per_sample=True)
+    if flow is None:
+        plan.run(seed, it)
+    else:
+        x, w = flow.sample(seed, it, 3, n)
+        plan.run(seed, it, points=x, point_w=w)
+    weights = plan.per_sample[0].reshape(-1, n)[:2 * len(G.roots)]
+    if chains is None:
+        chains = api.Chains(weights.shape[0], n_chains, n_sel=n_sel, alpha=alpha)
+    out = chains.run(weights, n_steps, seed, it, n_therm)
+    return chains, plan, out
+
+
 def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3, defensive=0.0):
     """Per-sample variance of every root and seconds per sample for one sampler.
 

@@ -1,0 +1,104 @@
+"""NF-MCMC / VEGAS-MCMC (Sec. V, Eqs. target_distr and nf_mcmc_estimator) on
+the GPU: the chain kernel reproduces the oracle's chains bit for bit on the
+same proposal weights and uniforms (ragged chain count, several weight rows,
+two calls in a row), and the whole path (proposals from the VEGAS map or the
+flow, integrand weights, chains, estimator) recovers the Fock self-energy's
+closed form."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import conventions, mcmc as omcmc
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2403_18840_gb300 import api as A
+    assert torch.cuda.is_available()
+    return A
+
+
+def _weights(seed, n_out, n):
+    """Signed heavy-tailed FP32 weights, some exactly zero (points outside the cutoff)."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_cauchy((n_out, n)) * rng.choice([1e-3, 1.0, 30.0], size=(n_out, n))
+    w[:, rng.random(n) < 0.05] = 0.0
+    return w.astype(np.float32)
+
+
+def test_chains_bitwise_equal_to_oracle(api):
+    C, S, n_out, n_sel, alpha = 3000, 37, 4, 2, 0.35
+    w1, w2 = _weights(1, n_out, C * S), _weights(2, n_out, C * S)
+    ch = api.Chains(n_out, C, n_sel=n_sel, alpha=alpha)
+    ch.run(torch.tensor(w1, device="cuda"), S, 17, 0, n_therm=5)
+    sums1, st1 = ch.sums.cpu().numpy(), ch.state.cpu().numpy()
+    out2 = ch.run(torch.tensor(w2, device="cuda"), S, 17, 1).cpu().numpy()
+    sums2, st2 = ch.sums.cpu().numpy(), ch.state.cpu().numpy()
+    rs1, rst1 = omcmc.run_chains(w1, n_sel, alpha, C, S, 17, 0, n_therm=5)
+    rs2, rst2 = omcmc.run_chains(w2, n_sel, alpha, C, S, 17, 1, state=rst1)
+    assert np.array_equal(sums1, rs1) and np.array_equal(st1, rst1)
+    assert np.array_equal(sums2, rs2) and np.array_equal(st2, rst2)
+    I, var = omcmc.estimate(rs2, n_out)
+    assert np.allclose(out2[:n_out, 0], I, rtol=1e-12, atol=0)
+    assert np.allclose(out2[:n_out, 1], var, rtol=1e-10, atol=0)
+    assert out2[n_out, 0] == rs2[n_out + 1].sum() / (C * S)
+    assert 0.05 < out2[n_out, 0] < 0.95
+
+
+def test_alpha_one_is_importance_sampling(api):
+    C, S = 1000, 8
+    w = _weights(3, 2, C * S)
+    ch = api.Chains(2, C, n_sel=1, alpha=1.0)
+    out = ch.run(torch.tensor(w, device="cuda"), S, 1, 0).cpu().numpy()
+    assert out[2, 0] == 1.0
+    assert np.allclose(out[:2, 0], w.astype(np.float64).mean(axis=1), rtol=1e-12)
+
+
+@pytest.mark.parametrize("kw", [dict(alpha=0.0), dict(alpha=1.5), dict(n_out=33), dict(n_sel=3)])
+def test_invalid_arguments_are_rejected(api, kw):
+    a = dict(n_out=2, n_sel=1, alpha=0.5)
+    a.update(kw)
+    ch = api.Chains(a["n_out"], 64, n_sel=a["n_sel"], alpha=a["alpha"])
+    w = torch.zeros((a["n_out"], 64 * 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(api.L.FdError):
+        ch.run(w, 2, 0, 0)
+    with pytest.raises(api.L.FdError):                       # too few columns for chains x steps
+        api.Chains(2, 64).run(torch.zeros((2, 64), dtype=torch.float32, device="cuda"), 2, 0, 0)
+
+
+def _fock_quad(P, k):
+    from scipy import integrate
+    from scipy.special import expit
+    f = lambda q: q * expit(-P.beta * (q * q - P.mu)) * math.log(((k + q) ** 2 + P.Lambda) / ((k - q) ** 2 + P.Lambda))
+    v, _ = integrate.quad(f, 0, P.kc, limit=500, epsabs=1e-14, epsrel=1e-13, points=[P.kF, k])
+    return -v / (math.pi * k)
+
+
+@pytest.mark.parametrize("sampler", ["vegas", "flow"])
+def test_mcmc_recovers_the_fock_closed_form(api, sampler):
+    from paper_2403_18840_gb300 import driver
+    cfg = workloads.FOCK_ORDER1
+    G = api.Graph(1)
+    p = api.ueg_params(1, cfg["rs"], cfg["T_over_TF"], cfg["lam_over_kF"], 1.0)
+    V = api.Vegas(G.dim, 256)
+    driver.adapt_vegas(G, p, V, 1 << 18, 6, seed=3)
+    flow = api.Flow(G.dim, n_layers=4, hidden=128, seed=5) if sampler == "flow" else None   # untrained: any q is valid
+    C, S = 1 << 15, 32
+    ch, plan, out = driver.mcmc(G, p, V, flow, C, S, 0.5, seed=9, it=100, n_therm=4)
+    out = out.cpu().numpy()
+    P = conventions.ueg_params(cfg["rs"], cfg["T_over_TF"], cfg["lam_over_kF"], 1.0)
+    ref = _fock_quad(P, P.kext)
+    print(sampler, "MCMC Fock", out[0], "ref", ref, "accepted", out[2, 0])
+    assert abs(out[0, 0] - ref) < 5.0 * math.sqrt(out[0, 1]), (out[0], ref)
+    assert out[1, 0] == 0.0                                  # the Fock self-energy is static: Im = 0
+    assert 0.02 < out[2, 0] <= 1.0
+    # continuing the same chains: a second call, estimate again consistent
+    _, _, out2 = driver.mcmc(G, p, V, flow, C, S, 0.5, seed=9, it=101, chains=ch, plan=plan)
+    out2 = out2.cpu().numpy()
+    assert abs(out2[0, 0] - ref) < 5.0 * math.sqrt(out2[0, 1])
