@@ -204,6 +204,13 @@ def flow_vs_vegas(args, api, params, order, seed):
     torch.cuda.synchronize()
     flow_train_s = time.perf_counter() - t0
     cmp = driver.compare(Gs, params[0], Vs, F, FW["n_compare"], seed=seed + 7, batches=16, defensive=0.1)
+    # the paper's sampler: independence Metropolis-Hastings chains with the flow
+    # (NF-MCMC) or the VEGAS map (VEGAS-MCMC) as proposal, against the same
+    # VEGAS importance-sampling reference (figure of merit 1 / (variance x time))
+    mc = driver.mcmc_compare(Gs, params[0], Vs, F, FW["mcmc_chains"], FW["mcmc_steps"], FW["mcmc_alphas"],
+                             seed=seed + 31)
+    ref = {"pooled": cmp["vegas"]["samples_per_s"] / cmp["vegas"]["var_per_sample"],
+           "median": cmp["vegas"]["samples_per_s"] / cmp["vegas"]["var_median"]}
     eff = {"quantity": "Re Sigma^(5)(k_F, i w0), single-root order-5 graph", "vegas": cmp["vegas"],
            "flow": cmp["flow"], "flow_over_vegas": cmp["flow_over_vegas"],
            "flow_over_vegas_median": cmp["flow_over_vegas_median"],
@@ -213,6 +220,10 @@ def flow_vs_vegas(args, api, params, order, seed):
            "flow_train_steps": max(1, args.flow_steps), "flow_batch": args.flow_batch,
            "flow_tensor_path": ["mma.sync", "tcgen05"][args.flow_tensor_path],
            "flow_train_s": flow_train_s, "flow_loss_first_last": [losses[0], losses[-1]],
+           "mcmc": dict(mc, over_vegas={k: mc[k]["merit"] / ref["pooled"] for k in mc},
+                        over_vegas_median={k: mc[k]["merit"] / ref["median"] for k in mc},
+                        note="alpha chosen on one draw of proposals, efficiency measured on an independent "
+                             "draw; merit = 1 / (variance of the estimate x seconds of the call)"),
            "flow_train_note": "each integrand batch reused for 4 Adam steps; first 100 steps on VEGAS samples; "
                               "VEGAS adapted 12 iterations x 2^22 samples"}
 

@@ -30,13 +30,18 @@ __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict
                                                          int n_therm, double *state, double *sums) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_chains) return;
-    double cur[kMaxOut], acc_w[kMaxOut];
+    // cur: the state's weights; m_w = cur/g (f/pi) and m_q = 1/g (q/pi) of the
+    // state, computed when it is accepted (the same operands and rounding as
+    // at every later step, so measuring them from the cache changes no bit)
+    double cur[kMaxOut], acc_w[kMaxOut], m_w[kMaxOut];
+    double g = state[(int64_t)n_out * n_chains + c];
 #pragma unroll
     for (int o = 0; o < kMaxOut; ++o) {
         cur[o] = o < n_out ? state[(int64_t)o * n_chains + c] : 0.0;
+        m_w[o] = g != 0.0 ? __ddiv_rn(cur[o], g) : 0.0;
         acc_w[o] = 0.0;
     }
-    double g = state[(int64_t)n_out * n_chains + c];
+    double m_q = g != 0.0 ? __ddiv_rn(1.0, g) : 0.0;
     double acc_q = 0.0, n_acc = 0.0;
     const double one_m_alpha = __dadd_rn(1.0, -alpha);
     u32x4 words{0u, 0u, 0u, 0u};
@@ -52,17 +57,21 @@ __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict
         const double gp = __dadd_rn(alpha, __dmul_rn(one_m_alpha, s));      // pi/q of the proposal
         const bool accept = g == 0.0 || u < __ddiv_rn(gp, g);
         if (accept) {
+            g = gp;
 #pragma unroll
             for (int o = 0; o < kMaxOut; ++o)
-                if (o < n_out) cur[o] = (double)__ldg(col + (int64_t)o * ld);
-            g = gp;
+                if (o < n_out) {
+                    cur[o] = (double)__ldg(col + (int64_t)o * ld);
+                    m_w[o] = __ddiv_rn(cur[o], g);
+                }
+            m_q = __ddiv_rn(1.0, g);
             n_acc += 1.0;
         }
         if (k >= n_therm) {
 #pragma unroll
             for (int o = 0; o < kMaxOut; ++o)
-                if (o < n_out) acc_w[o] = __dadd_rn(acc_w[o], __ddiv_rn(cur[o], g));   // f/pi
-            acc_q = __dadd_rn(acc_q, __ddiv_rn(1.0, g));                              // q/pi
+                if (o < n_out) acc_w[o] = __dadd_rn(acc_w[o], m_w[o]);   // f/pi
+            acc_q = __dadd_rn(acc_q, m_q);                              // q/pi
         }
     }
 #pragma unroll

@@ -111,6 +111,41 @@ def mcmc(G, params, vegas, flow, n_chains, n_steps, alpha, seed, it, n_therm=0, 
     return chains, plan, out
 
 
+def mcmc_compare(G, params, vegas, flow, n_chains, n_steps, alphas, seed, n_therm=16):
+    """Efficiency of VEGAS-MCMC and NF-MCMC (Sec. V) for Re of root 0.
+
+    Per sampler: alpha is chosen on one draw of proposals (the smallest
+    variance of the estimate over `alphas`, the same weights reused), then an
+    independent draw with that alpha runs and a continuation of the same chains
+    is timed end to end (proposals, integrand, chains, estimate).  Returns per
+    sampler: alpha, estimate and error, accepted fraction, seconds of the timed
+    call, measured steps and the figure of merit 1 / (variance x seconds)."""
+    n = n_chains * n_steps
+    res = {}
+    for name, fl in (("vegas_mcmc", None), ("nf_mcmc", flow)):
+        _, plan, _ = mcmc(G, params, vegas, fl, n_chains, n_steps, alphas[0], seed, 1000, n_therm)
+        w = plan.per_sample[0].reshape(-1, n)[:2]
+        scan = []
+        for a in alphas:
+            out = api.Chains(2, n_chains, n_sel=1, alpha=a).run(w, n_steps, seed, 1000, n_therm).cpu().numpy()
+            scan.append((float(out[0, 1]), a))
+        a = min(scan)[1]
+        ch, plan, _ = mcmc(G, params, vegas, fl, n_chains, n_steps, a, seed + 1, 2000, n_therm)
+        torch.cuda.synchronize()
+        s, e = _events()
+        s.record()
+        _, _, out = mcmc(G, params, vegas, fl, n_chains, n_steps, a, seed + 1, 2001, 0, chains=ch, plan=plan)
+        e.record()
+        torch.cuda.synchronize()
+        t = s.elapsed_time(e) / 1e3
+        out = out.cpu().numpy()
+        res[name] = {"alpha": a, "alpha_scan": {str(b): v for v, b in sorted(scan, key=lambda x: x[1])},
+                     "mean": float(out[0, 0]), "err": float(math.sqrt(out[0, 1])), "accepted": float(out[2, 0]),
+                     "seconds": t, "proposals": n, "chains": n_chains, "steps": n_steps,
+                     "merit": 1.0 / (float(out[0, 1]) * t)}
+    return res
+
+
 def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3, defensive=0.0):
     """Per-sample variance of every root and seconds per sample for one sampler.
 
