@@ -326,7 +326,7 @@ fd_status fd_measure_peak(int32_t kind, double *ops_per_s);
  * q = q_flow/J; rows = (root, Re/Im)); proposal k of chain c is column
  * k * n_chains + c, so ld >= n_chains * n_steps.  The chains sample
  * pi = alpha q + (1 - alpha) |f| with |f| = sum over o < n_sel of |w_o|
- * (0 < alpha <= 1), accept a proposal when u < g'/g_t with g = pi/q =
+ * (0 < alpha <= 1), accept a proposal when u g_t < g' with g = pi/q =
  * alpha + (1 - alpha)|f|/q and u from Philox4x32-10 with counter
  * (chain_lo, chain_hi, iter, 0x40000000 | (step >> 2)), word step & 3, key
  * (seed_lo, seed_hi), u = ((word >> 9) + 0.5) 2^-23; a chain with g_t = 0

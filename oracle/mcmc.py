@@ -33,9 +33,10 @@ Acceptance uniforms: Philox4x32-10 (oracle.philox) with counter
 (seed_lo, seed_hi), u = ((word >> 9) + 0.5) 2^-23: a stream disjoint from the
 sample streams (whose last counter word is < 2^16).
 
-The arithmetic is FP64 with the operations in the order written below, so an
-implementation that rounds each operation the same way reproduces the chains
-bit for bit.
+The arithmetic is FP64 with the operations in the order written below (the
+acceptance test u < g'/g_t as u g_t < g', the same event in exact arithmetic),
+so an implementation that rounds each operation the same way reproduces the
+chains bit for bit.
 """
 import numpy as np
 
@@ -89,9 +90,9 @@ def run_chains(w, n_sel, alpha, n_chains, n_steps, seed, iteration, n_therm=0, s
     for k in range(n_steps):
         wp = w[:, k * C:(k + 1) * C].astype(np.float64)
         gp = g_of(wp, n_sel, alpha)
-        with np.errstate(divide="ignore", invalid="ignore"):
-            R = gp / g                                   # pi(x') q(x_t) / (pi(x_t) q(x'))
-        acc = (g == 0.0) | (u[k] < R)
+        # u < R = pi(x') q(x_t) / (pi(x_t) q(x')) = gp / g, written u g < gp
+        # (the same event; g > 0 once the chain has a state, since alpha > 0)
+        acc = (g == 0.0) | (u[k] * g < gp)
         cur = np.where(acc[None, :], wp, cur)
         g = np.where(acc, gp, g)
         sums[n_out + 1] += acc

@@ -24,6 +24,8 @@ namespace {
 constexpr int kMaxOut = 32;                  // weight components per proposal
 constexpr uint32_t kChainTag = 0x40000000u;  // acceptance-uniform stream: counter word 3 = tag | (step >> 2)
 
+// NO >= n_out: the size of the per-chain register arrays
+template <int NO>
 __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict__ w, int n_out, int64_t ld,
                                                          int n_sel, int64_t n_chains, int n_steps, double alpha,
                                                          uint32_t seed_lo, uint32_t seed_hi, uint32_t iter,
@@ -33,10 +35,10 @@ __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict
     // cur: the state's weights; m_w = cur/g (f/pi) and m_q = 1/g (q/pi) of the
     // state, computed when it is accepted (the same operands and rounding as
     // at every later step, so measuring them from the cache changes no bit)
-    double cur[kMaxOut], acc_w[kMaxOut], m_w[kMaxOut];
+    double cur[NO], acc_w[NO], m_w[NO];
     double g = state[(int64_t)n_out * n_chains + c];
 #pragma unroll
-    for (int o = 0; o < kMaxOut; ++o) {
+    for (int o = 0; o < NO; ++o) {
         cur[o] = o < n_out ? state[(int64_t)o * n_chains + c] : 0.0;
         m_w[o] = g != 0.0 ? __ddiv_rn(cur[o], g) : 0.0;
         acc_w[o] = 0.0;
@@ -55,11 +57,12 @@ __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict
         double s = 0.0;
         for (int o = 0; o < n_sel; ++o) s = __dadd_rn(s, fabs((double)__ldg(col + (int64_t)o * ld)));
         const double gp = __dadd_rn(alpha, __dmul_rn(one_m_alpha, s));      // pi/q of the proposal
-        const bool accept = g == 0.0 || u < __ddiv_rn(gp, g);
+        // u < R = g'/g_t, as u g_t < g' (g_t > 0 once the chain has a state)
+        const bool accept = g == 0.0 || __dmul_rn(u, g) < gp;
         if (accept) {
             g = gp;
 #pragma unroll
-            for (int o = 0; o < kMaxOut; ++o)
+            for (int o = 0; o < NO; ++o)
                 if (o < n_out) {
                     cur[o] = (double)__ldg(col + (int64_t)o * ld);
                     m_w[o] = __ddiv_rn(cur[o], g);
@@ -69,13 +72,13 @@ __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict
         }
         if (k >= n_therm) {
 #pragma unroll
-            for (int o = 0; o < kMaxOut; ++o)
+            for (int o = 0; o < NO; ++o)
                 if (o < n_out) acc_w[o] = __dadd_rn(acc_w[o], m_w[o]);   // f/pi
             acc_q = __dadd_rn(acc_q, m_q);                              // q/pi
         }
     }
 #pragma unroll
-    for (int o = 0; o < kMaxOut; ++o)
+    for (int o = 0; o < NO; ++o)
         if (o < n_out) {
             state[(int64_t)o * n_chains + c] = cur[o];
             sums[(int64_t)o * n_chains + c] = acc_w[o];
@@ -152,9 +155,22 @@ extern "C" fd_status fd_mcmc_chains(const float *w, int32_t n_out, int64_t ld, i
     FD_REQUIRE(ld >= n_chains * (int64_t)n_steps, "ld must hold n_chains * n_steps proposals");
     FD_REQUIRE(alpha > 0.0 && alpha <= 1.0, "alpha must be in (0, 1]");
     const unsigned blocks = (unsigned)((n_chains + 127) / 128);
-    mcmc_chain_kernel<<<blocks, 128, 0, (cudaStream_t)stream>>>(w, n_out, ld, n_sel, n_chains, n_steps, alpha,
-                                                                 (uint32_t)seed, (uint32_t)(seed >> 32),
-                                                                 (uint32_t)iter, n_therm, state, sums);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t lo = (uint32_t)seed, hi = (uint32_t)(seed >> 32), it = (uint32_t)iter;
+#define FD_MCMC_LAUNCH(NO)                                                                                      \
+    mcmc_chain_kernel<NO><<<blocks, 128, 0, st>>>(w, n_out, ld, n_sel, n_chains, n_steps, alpha, lo, hi, it, \
+                                                  n_therm, state, sums)
+    if (n_out <= 2)
+        FD_MCMC_LAUNCH(2);
+    else if (n_out <= 4)
+        FD_MCMC_LAUNCH(4);
+    else if (n_out <= 8)
+        FD_MCMC_LAUNCH(8);
+    else if (n_out <= 16)
+        FD_MCMC_LAUNCH(16);
+    else
+        FD_MCMC_LAUNCH(32);
+#undef FD_MCMC_LAUNCH
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
 }
