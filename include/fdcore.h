@@ -334,8 +334,8 @@ fd_status fd_measure_peak(int32_t kind, double *ops_per_s);
  * state: device FP64 [n_out + 1][n_chains], in/out: the chains' current
  *        weights, then g (zero-fill it before the first call).
  * sums:  device FP64 [n_out + 2][n_chains], out: per chain the sums over the
- *        steps k >= n_therm of w_o/g (= f/pi) and of 1/g (= q/pi), then the
- *        number of accepted proposals.
+ *        steps k >= n_therm of w_o (1/g) (= f/pi) and of 1/g (= q/pi), then
+ *        the number of accepted proposals.
  * FP64 throughout, each operation rounded as written (reproducible bit for
  * bit).  Asynchronous on stream; FD_EINVAL for sizes or alpha out of range
  * (n_out <= 32). */

@@ -34,9 +34,10 @@ Acceptance uniforms: Philox4x32-10 (oracle.philox) with counter
 sample streams (whose last counter word is < 2^16).
 
 The arithmetic is FP64 with the operations in the order written below (the
-acceptance test u < g'/g_t as u g_t < g', the same event in exact arithmetic),
-so an implementation that rounds each operation the same way reproduces the
-chains bit for bit.
+acceptance test u < g'/g_t as u g_t < g', the same event in exact arithmetic;
+the estimator's terms as q/pi = 1/g and f/pi = w (1/g)), so an
+implementation that rounds each operation the same way reproduces the chains
+bit for bit.
 """
 import numpy as np
 
@@ -97,8 +98,9 @@ def run_chains(w, n_sel, alpha, n_chains, n_steps, seed, iteration, n_therm=0, s
         g = np.where(acc, gp, g)
         sums[n_out + 1] += acc
         if k >= n_therm:
-            sums[:n_out] += cur / g[None, :]            # f/pi
-            sums[n_out] += 1.0 / g                       # q/pi
+            inv = 1.0 / g                                # q/pi
+            sums[:n_out] += cur * inv[None, :]           # f/pi = (f/q)(q/pi)
+            sums[n_out] += inv
     return sums, np.concatenate([cur, g[None, :]])
 
 

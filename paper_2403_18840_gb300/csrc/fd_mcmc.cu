@@ -32,18 +32,18 @@ __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict
                                                          int n_therm, double *state, double *sums) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_chains) return;
-    // cur: the state's weights; m_w = cur/g (f/pi) and m_q = 1/g (q/pi) of the
-    // state, computed when it is accepted (the same operands and rounding as
-    // at every later step, so measuring them from the cache changes no bit)
+    // cur: the state's weights; m_q = 1/g (q/pi) and m_w = cur m_q (f/pi) of
+    // the state, computed when it is accepted (the same operands and rounding
+    // as at every later step, so measuring them from the cache changes no bit)
     double cur[NO], acc_w[NO], m_w[NO];
     double g = state[(int64_t)n_out * n_chains + c];
+    double m_q = g != 0.0 ? __ddiv_rn(1.0, g) : 0.0;
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
         cur[o] = o < n_out ? state[(int64_t)o * n_chains + c] : 0.0;
-        m_w[o] = g != 0.0 ? __ddiv_rn(cur[o], g) : 0.0;
+        m_w[o] = __dmul_rn(cur[o], m_q);
         acc_w[o] = 0.0;
     }
-    double m_q = g != 0.0 ? __ddiv_rn(1.0, g) : 0.0;
     double acc_q = 0.0, n_acc = 0.0;
     const double one_m_alpha = __dadd_rn(1.0, -alpha);
     u32x4 words{0u, 0u, 0u, 0u};
@@ -61,13 +61,13 @@ __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict
         const bool accept = g == 0.0 || __dmul_rn(u, g) < gp;
         if (accept) {
             g = gp;
+            m_q = __ddiv_rn(1.0, g);
 #pragma unroll
             for (int o = 0; o < NO; ++o)
                 if (o < n_out) {
                     cur[o] = (double)__ldg(col + (int64_t)o * ld);
-                    m_w[o] = __ddiv_rn(cur[o], g);
+                    m_w[o] = __dmul_rn(cur[o], m_q);
                 }
-            m_q = __ddiv_rn(1.0, g);
             n_acc += 1.0;
         }
         if (k >= n_therm) {
