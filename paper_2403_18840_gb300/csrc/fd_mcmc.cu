@@ -47,34 +47,53 @@ __global__ void __launch_bounds__(128) mcmc_chain_kernel(const float *__restrict
     double acc_q = 0.0, n_acc = 0.0;
     const double one_m_alpha = __dadd_rn(1.0, -alpha);
     u32x4 words{0u, 0u, 0u, 0u};
-    for (int k = 0; k < n_steps; ++k) {
-        if ((k & 3) == 0)
-            words = philox4x32_10(u32x4{(uint32_t)c, (uint32_t)((uint64_t)c >> 32), iter, kChainTag | (uint32_t)(k >> 2)},
-                                  seed_lo, seed_hi);
-        const uint32_t word = (k & 3) == 0 ? words.x : (k & 3) == 1 ? words.y : (k & 3) == 2 ? words.z : words.w;
-        const double u = (double)word_to_uniform(word);
-        const float *col = w + (int64_t)k * n_chains + c;
-        double s = 0.0;
-        for (int o = 0; o < n_sel; ++o) s = __dadd_rn(s, fabs((double)__ldg(col + (int64_t)o * ld)));
-        const double gp = __dadd_rn(alpha, __dmul_rn(one_m_alpha, s));      // pi/q of the proposal
-        // u < R = g'/g_t, as u g_t < g' (g_t > 0 once the chain has a state)
-        const bool accept = g == 0.0 || __dmul_rn(u, g) < gp;
-        if (accept) {
-            g = gp;
-            m_q = __ddiv_rn(1.0, g);
+    // The proposals' weights do not depend on the chain: load those of the
+    // next B steps before stepping through them (a chain's steps are
+    // sequential, so this hides the loads' latency behind the FP64 work)
+    constexpr int B = NO <= 2 ? 8 : NO <= 4 ? 4 : NO <= 8 ? 2 : 1;
+    for (int k0 = 0; k0 < n_steps; k0 += B) {
+        float wb[B][NO];
+#pragma unroll
+        for (int j = 0; j < B; ++j)
 #pragma unroll
             for (int o = 0; o < NO; ++o)
-                if (o < n_out) {
-                    cur[o] = (double)__ldg(col + (int64_t)o * ld);
-                    m_w[o] = __dmul_rn(cur[o], m_q);
-                }
-            n_acc += 1.0;
-        }
-        if (k >= n_therm) {
+                wb[j][o] = (k0 + j < n_steps && o < n_out)
+                               ? __ldg(w + (int64_t)(k0 + j) * n_chains + c + (int64_t)o * ld)
+                               : 0.0f;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int k = k0 + j;
+            if (k >= n_steps) break;
+            if ((k & 3) == 0)
+                words = philox4x32_10(
+                    u32x4{(uint32_t)c, (uint32_t)((uint64_t)c >> 32), iter, kChainTag | (uint32_t)(k >> 2)}, seed_lo,
+                    seed_hi);
+            const uint32_t word = (k & 3) == 0 ? words.x : (k & 3) == 1 ? words.y : (k & 3) == 2 ? words.z : words.w;
+            const double u = (double)word_to_uniform(word);
+            double s = 0.0;
 #pragma unroll
             for (int o = 0; o < NO; ++o)
-                if (o < n_out) acc_w[o] = __dadd_rn(acc_w[o], m_w[o]);   // f/pi
-            acc_q = __dadd_rn(acc_q, m_q);                              // q/pi
+                if (o < n_sel) s = __dadd_rn(s, fabs((double)wb[j][o]));
+            const double gp = __dadd_rn(alpha, __dmul_rn(one_m_alpha, s));      // pi/q of the proposal
+            // u < R = g'/g_t, as u g_t < g' (g_t > 0 once the chain has a state)
+            const bool accept = g == 0.0 || __dmul_rn(u, g) < gp;
+            if (accept) {
+                g = gp;
+                m_q = __ddiv_rn(1.0, g);
+#pragma unroll
+                for (int o = 0; o < NO; ++o)
+                    if (o < n_out) {
+                        cur[o] = (double)wb[j][o];
+                        m_w[o] = __dmul_rn(cur[o], m_q);
+                    }
+                n_acc += 1.0;
+            }
+            if (k >= n_therm) {
+#pragma unroll
+                for (int o = 0; o < NO; ++o)
+                    if (o < n_out) acc_w[o] = __dadd_rn(acc_w[o], m_w[o]);   // f/pi
+                acc_q = __dadd_rn(acc_q, m_q);                              // q/pi
+            }
         }
     }
 #pragma unroll

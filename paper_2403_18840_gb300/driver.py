@@ -111,16 +111,23 @@ def mcmc(G, params, vegas, flow, n_chains, n_steps, alpha, seed, it, n_therm=0, 
     return chains, plan, out
 
 
-def mcmc_compare(G, params, vegas, flow, n_chains, n_steps, alphas, seed, n_therm=16):
+def mcmc_compare(G, params, vegas, flow, n_chains, n_steps, alphas, seed, n_therm=None):
     """Efficiency of VEGAS-MCMC and NF-MCMC (Sec. V) for Re of root 0.
 
     Per sampler: alpha is chosen on one draw of proposals (the smallest
-    variance of the estimate over `alphas`, the same weights reused), then an
-    independent draw with that alpha runs and a continuation of the same chains
-    is timed end to end (proposals, integrand, chains, estimate).  Returns per
-    sampler: alpha, estimate and error, accepted fraction, seconds of the timed
-    call, measured steps and the figure of merit 1 / (variance x seconds)."""
+    variance of the estimate over `alphas`, the same weights reused, the first
+    n_therm steps of each chain discarded; default a quarter), then an
+    independent draw with that alpha thermalises a fresh set of chains (one
+    whole call discarded) and a continuation of the same chains is timed end
+    to end (proposals, integrand, chains, estimate).  The chains must be long
+    enough to equilibrate: with heavy-tailed weights short chains stick in
+    high-weight states and give biased estimates with too small error bars.
+    Returns per sampler: alpha, estimate and error, accepted fraction,
+    seconds of the timed call, and the figure of merit 1 / (variance x
+    seconds) of the timed call (thermalisation not charged)."""
     n = n_chains * n_steps
+    if n_therm is None:
+        n_therm = n_steps // 4
     res = {}
     for name, fl in (("vegas_mcmc", None), ("nf_mcmc", flow)):
         _, plan, _ = mcmc(G, params, vegas, fl, n_chains, n_steps, alphas[0], seed, 1000, n_therm)
@@ -130,7 +137,7 @@ def mcmc_compare(G, params, vegas, flow, n_chains, n_steps, alphas, seed, n_ther
             out = api.Chains(2, n_chains, n_sel=1, alpha=a).run(w, n_steps, seed, 1000, n_therm).cpu().numpy()
             scan.append((float(out[0, 1]), a))
         a = min(scan)[1]
-        ch, plan, _ = mcmc(G, params, vegas, fl, n_chains, n_steps, a, seed + 1, 2000, n_therm)
+        ch, plan, _ = mcmc(G, params, vegas, fl, n_chains, n_steps, a, seed + 1, 2000, n_steps)
         torch.cuda.synchronize()
         s, e = _events()
         s.record()

@@ -22,7 +22,7 @@ import time
 from . import api, autotune, driver
 
 
-def run_order(order, flow_steps, batch=1 << 20, n_compare=1 << 24, n_chains=1 << 16, n_steps=256,
+def run_order(order, flow_steps, batch=1 << 20, n_compare=1 << 24, n_chains=1 << 12, n_steps=1 << 12,
               alphas=(0.1, 0.3, 0.5, 0.7, 0.9), T_over_TF=1.0 / 32.0, seed=41):
     t0 = time.perf_counter()
     params = api.ueg_params(order, 1.0, T_over_TF, 1.0, 1.0)
@@ -53,10 +53,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--orders", type=int, nargs="+", default=[1, 2, 3, 4, 5])
     ap.add_argument("--flow-steps", type=int, default=1000)
+    ap.add_argument("--chains", type=int, default=1 << 12)
+    ap.add_argument("--steps", type=int, default=1 << 12)
     args = ap.parse_args()
     rows = []
     for n in args.orders:
-        r = run_order(n, args.flow_steps)
+        r = run_order(n, args.flow_steps, n_chains=args.chains, n_steps=args.steps)
         rows.append(r)
         print(json.dumps(r), flush=True)
     print(json.dumps({"summary": [{"order": r["order"],

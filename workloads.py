@@ -37,13 +37,13 @@ BATCHED_240 = dict(
 # Learned proposal at order 5, r_s = 1 (D = 19): 8 affine coupling layers,
 # MLP hidden 128, trained 2000 steps on 2^20-sample batches, compared with
 # VEGAS at 2^24 samples; as the proposal of Metropolis-Hastings chains
-# (NF-MCMC, and VEGAS-MCMC with the grid): 2^16 chains x 256 steps, the
+# (NF-MCMC, and VEGAS-MCMC with the grid): 2^12 chains x 2^12 steps, the
 # mixing parameter from a scan.
 FLOW_ORDER5 = dict(
     name="flow_order5_rs1", order=5, rs=1.0, T_over_TF=1.0 / 25.0, lam_over_kF=1.0,
     kext_over_kF=1.0, kc_over_kF=6.0, n_layers=8, hidden=128, train_steps=2000,
     batch=1 << 20, n_compare=1 << 24, n_bins=1024, seed=2,
-    mcmc_chains=1 << 16, mcmc_steps=256, mcmc_alphas=(0.1, 0.3, 0.5, 0.7, 0.9))
+    mcmc_chains=1 << 12, mcmc_steps=1 << 12, mcmc_alphas=(0.1, 0.3, 0.5, 0.7, 0.9))
 
 # Order-6 effective mass: r_s in {1, 2}, D = 23, 2^26 samples x 50 iterations.
 ORDER6_MEFF = dict(
