@@ -173,11 +173,18 @@ extern "C" fd_status fd_mcmc_chains(const float *w, int32_t n_out, int64_t ld, i
     FD_REQUIRE(n_steps >= 1 && n_therm >= 0, "n_steps must be positive and n_therm non-negative");
     FD_REQUIRE(ld >= n_chains * (int64_t)n_steps, "ld must hold n_chains * n_steps proposals");
     FD_REQUIRE(alpha > 0.0 && alpha <= 1.0, "alpha must be in (0, 1]");
-    const unsigned blocks = (unsigned)((n_chains + 127) / 128);
+    // chains are sequential and FP64-bound: spread them over every SM (down to
+    // one warp per block) before stacking warps on one SM's FP64 pipe
+    int dev = 0, n_sm = 1;
+    FD_CHECK_CUDA(cudaGetDevice(&dev));
+    FD_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t per_sm = (n_chains + n_sm - 1) / n_sm;
+    const int threads = per_sm <= 32 ? 32 : per_sm <= 64 ? 64 : 128;
+    const unsigned blocks = (unsigned)((n_chains + threads - 1) / threads);
     const cudaStream_t st = (cudaStream_t)stream;
     const uint32_t lo = (uint32_t)seed, hi = (uint32_t)(seed >> 32), it = (uint32_t)iter;
 #define FD_MCMC_LAUNCH(NO)                                                                                      \
-    mcmc_chain_kernel<NO><<<blocks, 128, 0, st>>>(w, n_out, ld, n_sel, n_chains, n_steps, alpha, lo, hi, it, \
+    mcmc_chain_kernel<NO><<<blocks, threads, 0, st>>>(w, n_out, ld, n_sel, n_chains, n_steps, alpha, lo, hi, it, \
                                                   n_therm, state, sums)
     if (n_out <= 2)
         FD_MCMC_LAUNCH(2);
