@@ -919,6 +919,30 @@ def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False):
     return flops, sfu
 
 
+def contraction_ops(data):
+    """Operation count N_op of a serialised tape's contraction: products and
+    sums as written, an FMA counted as 2 (leaves and weighting excluded)."""
+    hdr = struct.unpack("<16I", data[:64])
+    n_instr, ins_off = hdr[6], hdr[8]
+    words = struct.unpack("<%dQ" % n_instr, data[ins_off:ins_off + 8 * n_instr])
+    ops = 0
+    k = 0
+    while k < n_instr:
+        w = words[k]
+        op = w & 63
+        if op == OP_BUNDLE:
+            n = (w >> 6) & 15
+            for q in range(n):
+                m = words[k + 1 + q]
+                ops += 1 if ((m >> 48) == 0 or ((m >> 32) & 0xFFFF) == 1) else 2
+            k += n + 1
+            continue
+        if op == OP_END:
+            break
+        k += 1
+    return ops
+
+
 def tape_work(data):
     """(fp32_flops, sfu_ops) per sample of a serialised tape, map and weighting included.
 

@@ -111,3 +111,16 @@ def test_executed_work_model(order):
         cross = fdgraph.specialised_work(data, True, cap, True)
         assert fdgraph.tape_work(data)[0] <= cross[0] <= per_root[0]
         assert fdgraph.tape_work(data)[1] <= cross[1] <= per_root[1]
+
+
+def test_contraction_ops_below_the_naive_diagram_sum():
+    # naive: every diagram a product of 2n - 1 G and n V leaves, then summed
+    diagrams = {2: 3, 3: 20, 4: 189}
+    ratios = []
+    for n, d in diagrams.items():
+        ops = fdgraph.contraction_ops(fdgraph.compile_graph(n, [(n, 0, 0, 0)], budget=8192).to_bytes())
+        naive = d * (3 * n - 2) + (d - 1)
+        assert ops < naive
+        ratios.append(naive / ops)
+    assert ratios == sorted(ratios)          # the compression grows with the order
+    assert fdgraph.contraction_ops(fdgraph.compile_graph(4, [(4, 0, 0, 0)], budget=8192).to_bytes()) == 721
