@@ -1,0 +1,166 @@
+"""Neural spline flow (oracle; test infrastructure, never imported by the
+product path): monotone rational-quadratic spline coupling layers on the unit
+hypercube (App. A: 8 bins, a residual conditioner with hidden width 32 and
+ReLU, uniform base distribution), plain FP64 numpy.
+
+The rational-quadratic spline is the construction of Durkan, Bekasov, Murray
+and Papamakarios ("Neural Spline Flows", NeurIPS 2019): K bins with widths
+w_k and heights h_k (softmax of the conditioner's outputs, each at least a
+minimum), knots (x_k, y_k) at their cumulative sums, positive derivatives
+d_k at the knots; inside bin k, with xi = (x - x_k)/w_k and s_k = h_k/w_k,
+
+    y = y_k + h_k (s_k xi^2 + d_k xi (1 - xi)) / (s_k + (d_{k+1} + d_k - 2 s_k) xi (1 - xi)),
+
+which is monotone, passes through the knots and has derivative d_k there.
+
+Readings where the paper is silent: the spline maps [0, 1] onto [0, 1] with
+derivative 1 at both ends (App. A learns the derivatives at the internal
+knots only); minimum bin width and height 1e-3 and minimum derivative 1e-3;
+internal derivatives d = 1e-3 + softplus(theta^d), so theta^d =
+log(e^(1 - 1e-3) - 1) gives d = 1; the conditioner is a linear map from the
+unchanged coordinates to width 32, two residual blocks (ReLU, linear 32x32,
+ReLU, linear 32x32, plus the block's input) and a linear map to the
+3K - 1 spline parameters of every transformed coordinate; coupling layers
+alternate which half of the coordinates (first floor(D/2), or the rest)
+stays unchanged.
+"""
+import numpy as np
+
+K_BINS = 8
+HIDDEN = 32
+MIN_W = MIN_H = MIN_D = 1e-3
+THETA_D_ONE = float(np.log(np.expm1(1.0 - MIN_D)))   # internal derivative 1
+
+
+def _softmax(a):
+    a = a - a.max(axis=-1, keepdims=True)
+    e = np.exp(a)
+    return e / e.sum(axis=-1, keepdims=True)
+
+
+def _softplus(a):
+    return np.logaddexp(0.0, a)
+
+
+def knots(theta_w, theta_h, theta_d):
+    """Knot positions x [.., K+1], y [.., K+1] and derivatives d [.., K+1]
+    from unnormalised parameters theta_w, theta_h [.., K] and theta_d [.., K-1]."""
+    K = theta_w.shape[-1]
+    w = MIN_W + (1.0 - MIN_W * K) * _softmax(theta_w)
+    h = MIN_H + (1.0 - MIN_H * K) * _softmax(theta_h)
+    zero = np.zeros(w.shape[:-1] + (1,))
+    x = np.concatenate([zero, np.cumsum(w, axis=-1)], axis=-1)
+    y = np.concatenate([zero, np.cumsum(h, axis=-1)], axis=-1)
+    x[..., -1] = 1.0
+    y[..., -1] = 1.0
+    one = np.ones(w.shape[:-1] + (1,))
+    d = np.concatenate([one, MIN_D + _softplus(theta_d), one], axis=-1)
+    return x, y, d
+
+
+def _bin(v, edges):
+    K = edges.shape[-1] - 1
+    k = (v[..., None] >= edges[..., 1:-1]).sum(axis=-1)
+    return np.clip(k, 0, K - 1)
+
+
+def _take(a, k):
+    return np.take_along_axis(a, k[..., None], axis=-1)[..., 0]
+
+
+def rq_forward(x, theta_w, theta_h, theta_d):
+    """y = g(x) and log g'(x) for x in [0, 1] (arrays broadcast over leading axes)."""
+    X, Y, D = knots(theta_w, theta_h, theta_d)
+    k = _bin(x, X)
+    xk, xk1, yk, yk1 = _take(X, k), _take(X, k + 1), _take(Y, k), _take(Y, k + 1)
+    dk, dk1 = _take(D, k), _take(D, k + 1)
+    w, h = xk1 - xk, yk1 - yk
+    s = h / w
+    xi = (x - xk) / w
+    t = xi * (1.0 - xi)
+    den = s + (dk1 + dk - 2.0 * s) * t
+    y = yk + h * (s * xi * xi + dk * t) / den
+    dy = s * s * (dk1 * xi * xi + 2.0 * s * t + dk * (1.0 - xi) ** 2) / (den * den)
+    return y, np.log(dy)
+
+
+def rq_inverse(y, theta_w, theta_h, theta_d):
+    """x = g^-1(y) and log (g^-1)'(y): the root in [0, 1] of the bin's quadratic in xi."""
+    X, Y, D = knots(theta_w, theta_h, theta_d)
+    k = _bin(y, Y)
+    xk, xk1, yk, yk1 = _take(X, k), _take(X, k + 1), _take(Y, k), _take(Y, k + 1)
+    dk, dk1 = _take(D, k), _take(D, k + 1)
+    w, h = xk1 - xk, yk1 - yk
+    s = h / w
+    dy = y - yk
+    a = h * (s - dk) + dy * (dk1 + dk - 2.0 * s)
+    b = h * dk - dy * (dk1 + dk - 2.0 * s)
+    c = -s * dy
+    disc = np.maximum(b * b - 4.0 * a * c, 0.0)
+    xi = (2.0 * c) / (-b - np.sqrt(disc))
+    x = xk + xi * w
+    _, logd = rq_forward(x, theta_w, theta_h, theta_d)
+    return x, -logd
+
+
+class Conditioner:
+    """Residual network: in -> 32, two residual blocks, 32 -> out (FP64)."""
+
+    def __init__(self, n_in, n_out, rng, scale=0.3):
+        def lin(a, b, s=scale):
+            return rng.normal(0.0, s / np.sqrt(a), (a, b)), rng.normal(0.0, 0.01, b)
+        self.w0, self.b0 = lin(n_in, HIDDEN)
+        self.blocks = [(lin(HIDDEN, HIDDEN), lin(HIDDEN, HIDDEN)) for _ in range(2)]
+        self.w1, self.b1 = lin(HIDDEN, n_out)
+
+    def __call__(self, u):
+        h = u @ self.w0 + self.b0
+        for (wa, ba), (wb, bb) in self.blocks:
+            t = np.maximum(h, 0.0) @ wa + ba
+            t = np.maximum(t, 0.0) @ wb + bb
+            h = h + t
+        return h @ self.w1 + self.b1
+
+
+class SplineFlow:
+    """x = T(z), z ~ U(0,1)^D, T a stack of rational-quadratic coupling layers."""
+
+    def __init__(self, dim, n_layers, seed, scale=0.3, zero=False):
+        rng = np.random.default_rng(seed)
+        self.dim, self.layers = dim, []
+        for layer in range(n_layers):
+            a = dim // 2
+            keep = np.arange(a) if layer % 2 == 0 else np.arange(a, dim)
+            move = np.setdiff1d(np.arange(dim), keep)
+            net = Conditioner(len(keep), len(move) * (3 * K_BINS - 1), rng, scale)
+            if zero:   # identity layer
+                net.w1[:] = 0.0
+                net.b1[:] = 0.0
+                net.b1.reshape(len(move), 3 * K_BINS - 1)[:, 2 * K_BINS:] = THETA_D_ONE
+            self.layers.append((keep, move, net))
+
+    def _params(self, net, u, n_move):
+        p = net(u).reshape(u.shape[0], n_move, 3 * K_BINS - 1)
+        return p[..., :K_BINS], p[..., K_BINS:2 * K_BINS], p[..., 2 * K_BINS:]
+
+    def forward(self, z):
+        """x = T(z) for z [N, D]; returns (x, log q(x)) with log q = -sum log |g'|."""
+        x = np.array(z, dtype=np.float64)
+        logq = np.zeros(x.shape[0])
+        for keep, move, net in self.layers:
+            tw, th, td = self._params(net, x[:, keep], len(move))
+            y, logd = rq_forward(x[:, move], tw, th, td)
+            x[:, move] = y
+            logq -= logd.sum(axis=1)
+        return x, logq
+
+    def log_density(self, x):
+        """log q(x) by the inverse pass."""
+        z = np.array(x, dtype=np.float64)
+        logq = np.zeros(z.shape[0])
+        for keep, move, net in reversed(self.layers):
+            tw, th, td = self._params(net, z[:, keep], len(move))
+            v, logd_inv = rq_inverse(z[:, move], tw, th, td)
+            z[:, move] = v
+            logq += logd_inv.sum(axis=1)
+        return logq, z

@@ -1,0 +1,108 @@
+"""Pins of the spline-flow oracle (App. A; rational-quadratic splines of
+Durkan et al.): identity at the identity parameters; the spline passes
+through its knots with the prescribed derivatives there (second-order
+one-sided finite differences from both sides); inverse(forward) = id;
+log-derivative vs finite differences; the flow's log-density vs a
+finite-difference Jacobian determinant; the forward and inverse passes'
+densities agree; the density integrates to 1 (grid, and E_z[1/q] = 1)."""
+import numpy as np
+import pytest
+
+from oracle import spline_flow as sf
+
+
+def _params(rng, n, scale=1.5):
+    K = sf.K_BINS
+    return (rng.normal(0, scale, (n, K)), rng.normal(0, scale, (n, K)), rng.normal(0, scale, (n, K - 1)))
+
+
+def test_identity_parameters_give_the_identity():
+    K = sf.K_BINS
+    x = np.linspace(0.0, 1.0, 101)
+    tw, th = np.zeros((101, K)), np.zeros((101, K))
+    td = np.full((101, K - 1), sf.THETA_D_ONE)
+    y, logd = sf.rq_forward(x, tw, th, td)
+    assert np.allclose(y, x, atol=1e-14) and np.allclose(logd, 0.0, atol=1e-12)
+    flow = sf.SplineFlow(5, 4, seed=1, zero=True)
+    z = np.random.default_rng(2).random((50, 5))
+    xf, logq = flow.forward(z)
+    assert np.allclose(xf, z, atol=1e-13) and np.allclose(logq, 0.0, atol=1e-12)
+
+
+def test_spline_through_knots_with_their_derivatives():
+    rng = np.random.default_rng(3)
+    tw, th, td = _params(rng, 1)
+    X, Y, D = sf.knots(tw, th, td)
+    assert np.all(np.diff(X) > 0) and np.all(np.diff(Y) > 0) and np.all(D > 0)
+    assert X[0, 0] == 0.0 and X[0, -1] == 1.0 and Y[0, 0] == 0.0 and Y[0, -1] == 1.0
+    for k in range(1, sf.K_BINS):
+        y, _ = sf.rq_forward(np.array([X[0, k]]), tw, th, td)
+        assert abs(y[0] - Y[0, k]) < 1e-13
+        # second-order one-sided differences, the step a small part of the bins
+        e = 1e-5 * min(X[0, k] - X[0, k - 1], X[0, k + 1] - X[0, k])
+        yl, _ = sf.rq_forward(X[0, k] - np.array([2 * e, e, 0.0]), tw, th, td)
+        yr, _ = sf.rq_forward(X[0, k] + np.array([0.0, e, 2 * e]), tw, th, td)
+        left = (3 * yl[2] - 4 * yl[1] + yl[0]) / (2 * e)
+        right = (-3 * yr[0] + 4 * yr[1] - yr[2]) / (2 * e)
+        assert abs(left - D[0, k]) < 1e-6 * D[0, k] and abs(right - D[0, k]) < 1e-6 * D[0, k]
+
+
+def test_monotone_inverse_and_log_derivative():
+    rng = np.random.default_rng(4)
+    n = 2000
+    tw, th, td = _params(rng, n)
+    x = rng.random(n)
+    y, logd = sf.rq_forward(x, tw, th, td)
+    assert np.all((y >= 0) & (y <= 1))
+    xs = np.sort(x)
+    ys, _ = sf.rq_forward(xs, tw[:1].repeat(n, 0), th[:1].repeat(n, 0), td[:1].repeat(n, 0))
+    assert np.all(np.diff(ys) > 0)                              # one spline: monotone
+    xb, logdi = sf.rq_inverse(y, tw, th, td)
+    assert np.max(np.abs(xb - x)) < 1e-11
+    assert np.allclose(logdi, -logd, atol=1e-9)
+    h = 1e-6
+    xp, xm = np.clip(x + h, 0, 1), np.clip(x - h, 0, 1)
+    yp, _ = sf.rq_forward(xp, tw, th, td)
+    ym, _ = sf.rq_forward(xm, tw, th, td)
+    fd = (yp - ym) / (xp - xm)
+    inner = (x > 2e-6) & (x < 1 - 2e-6)
+    X, _, _ = sf.knots(tw, th, td)
+    away = np.min(np.abs(X - x[:, None]), axis=1) > 1e-5        # finite differences across a knot
+    m = inner & away
+    assert np.allclose(np.log(fd[m]), logd[m], atol=1e-6)
+
+
+@pytest.mark.parametrize("dim", [3, 6])
+def test_flow_log_density_vs_jacobian_determinant(dim):
+    flow = sf.SplineFlow(dim, 4, seed=5, scale=0.8)
+    z = np.random.default_rng(6).uniform(0.05, 0.95, (6, dim))
+    x, logq = flow.forward(z)
+    h = 1e-6
+    for i in range(z.shape[0]):
+        J = np.zeros((dim, dim))
+        for j in range(dim):
+            zp, zm = z[i].copy(), z[i].copy()
+            zp[j] += h
+            zm[j] -= h
+            J[:, j] = (flow.forward(zp[None])[0][0] - flow.forward(zm[None])[0][0]) / (2 * h)
+        assert abs(-np.log(abs(np.linalg.det(J))) - logq[i]) < 1e-6
+    logq2, zb = flow.log_density(x)
+    assert np.max(np.abs(zb - z)) < 1e-10 and np.allclose(logq2, logq, atol=1e-9)
+
+
+def test_density_integrates_to_one():
+    # midpoint rule on a grid (a mild flow), and for a sharper one the exact
+    # identity E_z[1 / q(T(z))] = volume = 1 over uniform z
+    flow = sf.SplineFlow(2, 4, seed=7, scale=0.5)
+    m = 800
+    g = (np.arange(m) + 0.5) / m
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    logq, _ = flow.log_density(np.stack([X.ravel(), Y.ravel()], axis=1))
+    q = np.exp(logq)
+    assert q.max() / q.min() > 2.0                               # a non-trivial density
+    assert abs(q.mean() - 1.0) < 1e-3
+    sharp = sf.SplineFlow(4, 6, seed=8, scale=1.0)
+    z = np.random.default_rng(9).random((200000, 4))
+    _, logq = sharp.forward(z)
+    r = np.exp(-logq)
+    assert abs(r.mean() - 1.0) < 5 * r.std() / np.sqrt(r.size)
