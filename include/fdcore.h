@@ -317,6 +317,32 @@ fd_status fd_flow_train(fd_flow *f, const float *x, const float *w, int64_t n, i
  * Synchronous; allocates a small scratch buffer. */
 fd_status fd_measure_peak(int32_t kind, double *ops_per_s);
 
+/* ---- neural spline flow, sampling and density (App. A) --------------------
+ * x = T(z), z uniform on [0, 1]^dim, T = n_layers rational-quadratic coupling
+ * layers (K = 8 bins on [0, 1]: widths and heights from softmax of the
+ * conditioner's outputs, each at least 1e-3; derivative 1e-3 + softplus at the
+ * 7 internal knots, 1 at both ends), layer l keeping the first floor(dim/2)
+ * coordinates when l is even and the others when odd; the conditioner maps
+ * the kept coordinates linearly to width 32, applies two residual blocks
+ * h += W_b relu(W_a relu(h) + b_a) + b_b and maps linearly to 23 parameters
+ * per transformed coordinate (8 width, 8 height, 7 derivative logits).
+ * Parameters (host FP32, fd_nsf_param_count of them), layer after layer:
+ * W0 [n_keep][32], b0 [32], for each block W_a [32][32], b_a [32], W_b [32][32],
+ * b_b [32], then W1 [32][n_move * 23], b1 [n_move * 23] (row-major, inputs
+ * first).  The flow owns its device copy; create/free are synchronous. */
+typedef struct fd_nsf fd_nsf;
+fd_status fd_nsf_create(int32_t dim, int32_t n_layers, fd_nsf **out);   /* 2 <= dim <= 24; all parameters 0 */
+void fd_nsf_free(fd_nsf *f);
+int64_t fd_nsf_param_count(const fd_nsf *f);
+fd_status fd_nsf_set_params(fd_nsf *f, const float *params, int64_t n);  /* synchronous; FD_EINVAL if non-finite */
+/* x = T(z) for device z [dim][n]: x (device FP32 [dim][n]) and log q(x)
+ * (device FP32 [n]).  Asynchronous on stream. */
+fd_status fd_nsf_forward(const fd_nsf *f, const float *z, int64_t n, float *x, float *logq, void *stream);
+/* The same with z from the sample stream (Philox counter (i_lo, i_hi, iter,
+ * inst << 8 | block), u = ((w >> 9) + 0.5) 2^-23). */
+fd_status fd_nsf_sample(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n, float *x,
+                        float *logq, void *stream);
+
 /* ---- NF-MCMC / VEGAS-MCMC chains (Sec. V, Eqs. target_distr and
  * nf_mcmc_estimator) --------------------------------------------------------
  * Independence Metropolis-Hastings over proposals x ~ q that were already

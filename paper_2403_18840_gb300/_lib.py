@@ -87,6 +87,12 @@ SIGNATURES = {
     "fd_flow_train": (_i32, [_vp, _vp, _vp, _i64, _i32, _f32, _pf, _vp]),
     "fd_measure_peak": (_i32, [_i32, _pd]),
     "fd_mcmc_chains": (_i32, [_vp, _i32, _i64, _i32, _i64, _i32, _f64, _u64, _u64, _i32, _vp, _vp, _vp]),
+    "fd_nsf_create": (_i32, [_i32, _i32, _c.POINTER(_vp)]),
+    "fd_nsf_free": (None, [_vp]),
+    "fd_nsf_param_count": (_i64, [_vp]),
+    "fd_nsf_set_params": (_i32, [_vp, _pf, _i64]),
+    "fd_nsf_forward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "fd_nsf_sample": (_i32, [_vp, _u64, _u64, _i32, _i64, _vp, _vp, _vp]),
     "fd_mcmc_estimate": (_i32, [_vp, _i32, _i64, _i32, _vp, _vp]),
     "fd_postprocess": (_i32, [_i32, _pd, _pd, _pd, _f64, _f64, _f64, _pd, _pd, _pd, _pd]),
 }

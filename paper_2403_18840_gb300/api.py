@@ -284,6 +284,42 @@ class Flow:
             self.handle = None
 
 
+class SplineFlow:
+    """Neural spline flow (App. A): rational-quadratic coupling layers on the
+    unit hypercube; sampling and density on the device (fd_nsf_*)."""
+
+    def __init__(self, dim, n_layers=8):
+        h = ctypes.c_void_p()
+        L.check(L.lib().fd_nsf_create(dim, n_layers, ctypes.byref(h)))
+        self.handle, self.dim, self.n_layers = h, dim, n_layers
+        self.n_params = L.lib().fd_nsf_param_count(h)
+
+    def set_params(self, blob):
+        b = np.ascontiguousarray(blob, dtype=np.float32)
+        assert b.size == self.n_params
+        L.check(L.lib().fd_nsf_set_params(self.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), b.size))
+
+    def forward(self, z, stream=None):
+        n = z.shape[1]
+        x = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")
+        lq = torch.empty((n,), dtype=torch.float32, device="cuda")
+        assert z.dtype == torch.float32 and z.is_contiguous() and z.shape[0] == self.dim
+        L.check(L.lib().fd_nsf_forward(self.handle, _ptr(z), n, _ptr(x), _ptr(lq), _stream_ptr(stream)))
+        return x, lq
+
+    def sample(self, seed, it, inst, n, stream=None):
+        x = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")
+        lq = torch.empty((n,), dtype=torch.float32, device="cuda")
+        L.check(L.lib().fd_nsf_sample(self.handle, seed, it, inst, n, _ptr(x), _ptr(lq), _stream_ptr(stream)))
+        return x, lq
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.fd_nsf_free(h)
+            self.handle = None
+
+
 class Chains:
     """Independence Metropolis-Hastings chains over evaluated proposals (NF-MCMC
     with flow proposals, VEGAS-MCMC with VEGAS proposals; Sec. V).  Weights w

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfdcore.so")
-SOURCES = ["fd_api.cu", "fd_integrand.cu", "fd_flow.cu", "fd_jit.cu", "fd_mcmc.cu"]
+SOURCES = ["fd_api.cu", "fd_integrand.cu", "fd_flow.cu", "fd_jit.cu", "fd_mcmc.cu", "fd_nsf.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -1,0 +1,92 @@
+"""GPU parity of the spline flow's sampling and density pass (App. A) with the
+FP64 oracle on the same parameters: explicit points, the Philox sample
+stream, the identity flow, and a ragged sample count."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import philox as ophilox, spline_flow as osf
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2403_18840_gb300 import api as A
+    assert torch.cuda.is_available()
+    return A
+
+
+def _flatten(flow):
+    """The oracle's parameters in the library's order (fd_nsf_set_params)."""
+    parts = []
+    for _, _, net in flow.layers:
+        parts += [net.w0.ravel(), net.b0]
+        for (wa, ba), (wb, bb) in net.blocks:
+            parts += [wa.ravel(), ba, wb.ravel(), bb]
+        parts += [net.w1.ravel(), net.b1]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _as_fp32(flow):
+    """The oracle flow with its parameters rounded to FP32 (what the GPU holds)."""
+    for _, _, net in flow.layers:
+        for name in ("w0", "b0", "w1", "b1"):
+            setattr(net, name, getattr(net, name).astype(np.float32).astype(np.float64))
+        net.blocks = [tuple((w.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64))
+                            for (w, b) in blk) for blk in net.blocks]
+    return flow
+
+
+def _compare(x_gpu, lq_gpu, x_ref, lq_ref, label):
+    dx = np.abs(x_gpu - x_ref).max(axis=0)
+    dl = np.abs(lq_gpu - lq_ref)
+    print("%s: max |dx| %.3e (99%% %.3e), max |d log q| %.3e (99%% %.3e)" %
+          (label, dx.max(), np.quantile(dx, 0.99), dl.max(), np.quantile(dl, 0.99)))
+    assert np.quantile(dx, 0.99) < 1e-5 and dx.max() < 1e-3, label
+    assert np.quantile(dl, 0.99) < 1e-4 and dl.max() < 1e-2, label
+
+
+@pytest.mark.parametrize("dim", [19, 5])
+def test_forward_matches_oracle(api, dim):
+    flow = _as_fp32(osf.SplineFlow(dim, 8, seed=11, scale=0.8))
+    g = api.SplineFlow(dim, 8)
+    g.set_params(_flatten(flow))
+    n = 3 * 1000 + 77                                        # several blocks and a ragged tail
+    z = workloads.uniform_points(12, dim, n)
+    x, lq = g.forward(torch.tensor(z, dtype=torch.float32, device="cuda").contiguous())
+    x_ref, lq_ref = flow.forward(z.T)
+    _compare(x.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), x_ref.T, lq_ref,
+             "forward dim %d" % dim)
+
+
+def test_sample_stream_matches_oracle(api):
+    dim, n = 19, 2049
+    flow = _as_fp32(osf.SplineFlow(dim, 8, seed=13, scale=0.8))
+    g = api.SplineFlow(dim, 8)
+    g.set_params(_flatten(flow))
+    x, lq = g.sample(21, 4, 3, n)
+    z = ophilox.uniforms(21, 4, 3, np.arange(n), dim)
+    x_ref, lq_ref = flow.forward(z.T)
+    _compare(x.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), x_ref.T, lq_ref, "sample")
+
+
+def test_identity_flow(api):
+    dim, n = 7, 1000
+    flow = osf.SplineFlow(dim, 4, seed=1, zero=True)
+    g = api.SplineFlow(dim, 4)
+    g.set_params(_flatten(flow))
+    z = workloads.uniform_points(3, dim, n)
+    x, lq = g.forward(torch.tensor(z, dtype=torch.float32, device="cuda").contiguous())
+    assert np.max(np.abs(x.cpu().numpy() - z.astype(np.float32))) < 1e-6
+    assert np.max(np.abs(lq.cpu().numpy())) < 1e-5
+
+
+def test_invalid_arguments(api):
+    with pytest.raises(api.L.FdError):
+        api.SplineFlow(25, 8)
+    g = api.SplineFlow(3, 2)
+    with pytest.raises(api.L.FdError):
+        g.set_params(np.full(g.n_params, np.nan, dtype=np.float32))
