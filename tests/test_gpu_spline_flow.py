@@ -41,12 +41,14 @@ def _as_fp32(flow):
 
 
 def _compare(x_gpu, lq_gpu, x_ref, lq_ref, label):
+    # FP32 through 8 layers: a coordinate carries ~1e-6 absolute error; log q
+    # sums 8 x (D/2) log-derivatives of ~1e-6 each, ~1e-4 in the worst samples
     dx = np.abs(x_gpu - x_ref).max(axis=0)
     dl = np.abs(lq_gpu - lq_ref)
     print("%s: max |dx| %.3e (99%% %.3e), max |d log q| %.3e (99%% %.3e)" %
           (label, dx.max(), np.quantile(dx, 0.99), dl.max(), np.quantile(dl, 0.99)))
-    assert np.quantile(dx, 0.99) < 1e-5 and dx.max() < 1e-3, label
-    assert np.quantile(dl, 0.99) < 1e-4 and dl.max() < 1e-2, label
+    assert np.quantile(dx, 0.99) < 5e-6 and dx.max() < 5e-5, label
+    assert np.quantile(dl, 0.99) < 1e-4 and dl.max() < 1e-3, label
 
 
 @pytest.mark.parametrize("dim", [19, 5])
