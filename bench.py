@@ -225,9 +225,29 @@ def flow_vs_vegas(args, api, params, order, seed):
                         note="alpha chosen on one draw of proposals, efficiency measured on an independent "
                              "draw; merit = 1 / (variance of the estimate x seconds of the call)"),
            "flow_train_note": "each integrand batch reused for 4 Adam steps; first 100 steps on VEGAS samples; "
-                              "VEGAS adapted 12 iterations x 2^22 samples"}
+                              "VEGAS adapted 12 iterations x 2^22 samples",
+           "spline_flow_sampling": spline_flow_sampling(api, Gs.dim)}
 
     return eff
+
+
+def spline_flow_sampling(api, dim, layers=8, n=1 << 22, reps=3):
+    """Samples/s of the spline flow's sampling and density pass (App. A), seeded
+    untrained parameters (its training is not built yet)."""
+    import torch
+    g = api.SplineFlow(dim, layers)
+    g.set_params(workloads.small_params(7, g.n_params))
+    g.sample(1, 0, 0, n)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for r in range(reps):
+        g.sample(1, r + 1, 0, n)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / reps
+    return {"samples_per_s": n / ms * 1e3, "dim": dim, "layers": layers, "samples": n, "ms": ms,
+            "parameters": "seeded, untrained"}
 
 
 def run_ours(args, rank, world, dist):

@@ -58,6 +58,11 @@ BENCH_ORDER5 = dict(
     n_samples=1 << 24, seed=5)
 
 
+def small_params(seed, n, scale=0.05):
+    """Seeded FP32 parameter vector (normal, small): an untrained network's weights."""
+    return (np.random.default_rng(seed).standard_normal(n) * scale).astype(np.float32)
+
+
 def uniform_points(seed, dim, n, lo=1e-6, hi=1.0 - 1e-6):
     """Seeded points in (lo, hi)^dim as FP32-representable values, shape [dim, n]."""
     rng = np.random.default_rng(seed)
