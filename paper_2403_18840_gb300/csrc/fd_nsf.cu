@@ -28,6 +28,7 @@ constexpr int kHidden = 32;
 constexpr int kParamsPerDim = 3 * kBins - 1;
 constexpr int kMaxDim = 24;
 constexpr float kMinW = 1e-3f, kMinH = 1e-3f, kMinD = 1e-3f;
+constexpr int kPad = 24;                 // a coordinate's 23 spline parameters, padded for 16-byte loads
 
 // per layer: W0 [n_keep][32], b0 [32], two blocks of (Wa [32][32], ba [32],
 // Wb [32][32], bb [32]), W1 [32][n_move * 23], b1 [n_move * 23]
@@ -40,7 +41,7 @@ __device__ __forceinline__ float softplusf(float a) { return a > 20.0f ? a : log
 
 // rational-quadratic spline on [0, 1]: y = g(u) and log g'(u) from the 23
 // parameters (widths, heights, internal-knot derivatives)
-__device__ void rq_spline(const float (&p)[kParamsPerDim], float u, float &y, float &logd) {
+__device__ __forceinline__ void rq_spline(const float (&p)[kPad], float u, float &y, float &logd) {
     float mw = p[0], mh = p[kBins];
 #pragma unroll
     for (int k = 1; k < kBins; ++k) {
@@ -78,8 +79,14 @@ __device__ void rq_spline(const float (&p)[kParamsPerDim], float u, float &y, fl
             y0 = ys[k];
             y1 = ys[k + 1];
         }
-    const float d0 = bin > 0 ? kMinD + softplusf(p[2 * kBins + bin - 1]) : 1.0f;
-    const float d1 = bin < kBins - 1 ? kMinD + softplusf(p[2 * kBins + bin]) : 1.0f;
+    float pd0 = 0.0f, pd1 = 0.0f;                // the derivative logits at the bin's knots
+#pragma unroll
+    for (int k = 0; k < kBins - 1; ++k) {
+        if (k == bin - 1) pd0 = p[2 * kBins + k];
+        if (k == bin) pd1 = p[2 * kBins + k];
+    }
+    const float d0 = bin > 0 ? kMinD + softplusf(pd0) : 1.0f;
+    const float d1 = bin < kBins - 1 ? kMinD + softplusf(pd1) : 1.0f;
     const float wk = x1 - x0, hk = y1 - y0;
     const float s = hk / wk, xi = (u - x0) / wk, t = xi * (1.0f - xi);
     const float den = s + (d1 + d0 - 2.0f * s) * t;
@@ -98,8 +105,20 @@ struct NsfArgs {
     uint32_t seed_lo, seed_hi, iter, inst;
 };
 
+// shared-memory layout of a layer: as in global memory up to the residual
+// blocks; W1 and b1 re-laid as rows of kPad (23 parameters and a zero), so
+// every weight row starts on 16 bytes and is read as float4
+
+__host__ __device__ __forceinline__ int64_t head_floats(int n_keep) {
+    return (int64_t)n_keep * kHidden + kHidden + 2 * (2 * (kHidden * kHidden + kHidden));
+}
+
+__host__ __device__ __forceinline__ int64_t layer_smem_floats(int n_keep, int n_move) {
+    return head_floats(n_keep) + (int64_t)(kHidden + 1) * n_move * kPad;
+}
+
 __global__ void __launch_bounds__(128) nsf_forward_kernel(const NsfArgs a) {
-    extern __shared__ float wsm[];
+    extern __shared__ __align__(16) float wsm[];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < a.n;
     const int D = a.dim, half = D / 2;
@@ -125,12 +144,20 @@ __global__ void __launch_bounds__(128) nsf_forward_kernel(const NsfArgs a) {
     for (int layer = 0; layer < a.n_layers; ++layer) {
         const int keep0 = layer % 2 == 0 ? 0 : half, n_keep = layer % 2 == 0 ? half : D - half;
         const int move0 = layer % 2 == 0 ? half : 0, n_move = D - n_keep;
-        const int64_t nf = layer_floats(n_keep, n_move);
+        const int64_t nf = layer_floats(n_keep, n_move), head = head_floats(n_keep);
+        const int row = n_move * kParamsPerDim;                    // W1 row length in global memory
         __syncthreads();                                            // the previous layer's weights are consumed
-        for (int64_t k = threadIdx.x; k < nf; k += blockDim.x) wsm[k] = __ldg(lp + k);
+        for (int64_t k = threadIdx.x; k < head; k += blockDim.x) wsm[k] = __ldg(lp + k);
+        for (int64_t k = threadIdx.x; k < (int64_t)(kHidden + 1) * n_move * kPad; k += blockDim.x) {
+            // padded index k = (r n_move + m) 24 + q; r = 32 is b1
+            const int q = (int)(k % kPad);
+            const int64_t rm = k / kPad;
+            const int r = (int)(rm / n_move), m = (int)(rm % n_move);
+            wsm[head + k] = q < kParamsPerDim ? __ldg(lp + head + (int64_t)r * row + m * kParamsPerDim + q) : 0.0f;
+        }
         __syncthreads();
         const float *W0 = wsm, *b0 = W0 + n_keep * kHidden, *blk = b0 + kHidden;
-        const float *W1 = blk + 2 * (2 * (kHidden * kHidden + kHidden)), *b1 = W1 + kHidden * n_move * kParamsPerDim;
+        const float *W1 = wsm + head, *b1 = W1 + (int64_t)kHidden * n_move * kPad;
         float hdn[kHidden];
 #pragma unroll
         for (int c = 0; c < kHidden; ++c) hdn[c] = b0[c];
@@ -140,7 +167,13 @@ __global__ void __launch_bounds__(128) nsf_forward_kernel(const NsfArgs a) {
             for (int j = 0; j < kMaxDim; ++j)
                 if (j == keep0 + r) xv = v[j];
 #pragma unroll
-            for (int c = 0; c < kHidden; ++c) hdn[c] = fmaf(xv, W0[r * kHidden + c], hdn[c]);
+            for (int c4 = 0; c4 < kHidden / 4; ++c4) {
+                const float4 w = reinterpret_cast<const float4 *>(W0 + r * kHidden)[c4];
+                hdn[4 * c4] = fmaf(xv, w.x, hdn[4 * c4]);
+                hdn[4 * c4 + 1] = fmaf(xv, w.y, hdn[4 * c4 + 1]);
+                hdn[4 * c4 + 2] = fmaf(xv, w.z, hdn[4 * c4 + 2]);
+                hdn[4 * c4 + 3] = fmaf(xv, w.w, hdn[4 * c4 + 3]);
+            }
         }
 #pragma unroll 1
         for (int bk = 0; bk < 2; ++bk) {
@@ -153,7 +186,13 @@ __global__ void __launch_bounds__(128) nsf_forward_kernel(const NsfArgs a) {
             for (int r = 0; r < kHidden; ++r) {
                 const float hr = fmaxf(hdn[r], 0.0f);
 #pragma unroll
-                for (int c = 0; c < kHidden; ++c) t[c] = fmaf(hr, Wa[r * kHidden + c], t[c]);
+                for (int c4 = 0; c4 < kHidden / 4; ++c4) {
+                    const float4 w = reinterpret_cast<const float4 *>(Wa + r * kHidden)[c4];
+                    t[4 * c4] = fmaf(hr, w.x, t[4 * c4]);
+                    t[4 * c4 + 1] = fmaf(hr, w.y, t[4 * c4 + 1]);
+                    t[4 * c4 + 2] = fmaf(hr, w.z, t[4 * c4 + 2]);
+                    t[4 * c4 + 3] = fmaf(hr, w.w, t[4 * c4 + 3]);
+                }
             }
             float t2[kHidden];
 #pragma unroll
@@ -162,20 +201,38 @@ __global__ void __launch_bounds__(128) nsf_forward_kernel(const NsfArgs a) {
             for (int r = 0; r < kHidden; ++r) {
                 const float tr = fmaxf(t[r], 0.0f);
 #pragma unroll
-                for (int c = 0; c < kHidden; ++c) t2[c] = fmaf(tr, Wb[r * kHidden + c], t2[c]);
+                for (int c4 = 0; c4 < kHidden / 4; ++c4) {
+                    const float4 w = reinterpret_cast<const float4 *>(Wb + r * kHidden)[c4];
+                    t2[4 * c4] = fmaf(tr, w.x, t2[4 * c4]);
+                    t2[4 * c4 + 1] = fmaf(tr, w.y, t2[4 * c4 + 1]);
+                    t2[4 * c4 + 2] = fmaf(tr, w.z, t2[4 * c4 + 2]);
+                    t2[4 * c4 + 3] = fmaf(tr, w.w, t2[4 * c4 + 3]);
+                }
             }
 #pragma unroll
             for (int c = 0; c < kHidden; ++c) hdn[c] += t2[c];
         }
-        const int ldw1 = n_move * kParamsPerDim;
         for (int m = 0; m < n_move; ++m) {
-            float p[kParamsPerDim];
+            float p[kPad];
 #pragma unroll
-            for (int q = 0; q < kParamsPerDim; ++q) p[q] = b1[m * kParamsPerDim + q];
+            for (int q4 = 0; q4 < kPad / 4; ++q4) {
+                const float4 b = reinterpret_cast<const float4 *>(b1 + m * kPad)[q4];
+                p[4 * q4] = b.x;
+                p[4 * q4 + 1] = b.y;
+                p[4 * q4 + 2] = b.z;
+                p[4 * q4 + 3] = b.w;
+            }
 #pragma unroll
             for (int r = 0; r < kHidden; ++r) {
+                const float4 *w4 = reinterpret_cast<const float4 *>(W1 + ((int64_t)r * n_move + m) * kPad);
 #pragma unroll
-                for (int q = 0; q < kParamsPerDim; ++q) p[q] = fmaf(hdn[r], W1[r * ldw1 + m * kParamsPerDim + q], p[q]);
+                for (int q4 = 0; q4 < kPad / 4; ++q4) {
+                    const float4 w = w4[q4];
+                    p[4 * q4] = fmaf(hdn[r], w.x, p[4 * q4]);
+                    p[4 * q4 + 1] = fmaf(hdn[r], w.y, p[4 * q4 + 1]);
+                    p[4 * q4 + 2] = fmaf(hdn[r], w.z, p[4 * q4 + 2]);
+                    if (4 * q4 + 3 < kParamsPerDim) p[4 * q4 + 3] = fmaf(hdn[r], w.w, p[4 * q4 + 3]);
+                }
             }
             float u = 0.0f;
 #pragma unroll
@@ -211,9 +268,8 @@ fd_status nsf_sizes(int dim, int n_layers, int64_t &total, int64_t &max_layer) {
     max_layer = 0;
     for (int l = 0; l < n_layers; ++l) {
         const int n_keep = l % 2 == 0 ? dim / 2 : dim - dim / 2;
-        const int64_t f = layer_floats(n_keep, dim - n_keep);
-        total += f;
-        max_layer = std::max(max_layer, f);
+        total += layer_floats(n_keep, dim - n_keep);
+        max_layer = std::max(max_layer, layer_smem_floats(n_keep, dim - n_keep));
     }
     return FD_OK;
 }
