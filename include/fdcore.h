@@ -342,6 +342,11 @@ fd_status fd_nsf_forward(const fd_nsf *f, const float *z, int64_t n, float *x, f
  * inst << 8 | block), u = ((w >> 9) + 0.5) 2^-23). */
 fd_status fd_nsf_sample(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n, float *x,
                         float *logq, void *stream);
+/* Density at given points: z = T^-1(x) (device FP32 [dim][n], the layers in
+ * reverse order, each spline inverted through its bin's quadratic) and
+ * log q(x) (device FP32 [n]) for device x [dim][n] in [0, 1]^dim.
+ * Asynchronous on stream. */
+fd_status fd_nsf_log_density(const fd_nsf *f, const float *x, int64_t n, float *z, float *logq, void *stream);
 
 /* ---- NF-MCMC / VEGAS-MCMC chains (Sec. V, Eqs. target_distr and
  * nf_mcmc_estimator) --------------------------------------------------------

@@ -313,6 +313,15 @@ class SplineFlow:
         L.check(L.lib().fd_nsf_sample(self.handle, seed, it, inst, n, _ptr(x), _ptr(lq), _stream_ptr(stream)))
         return x, lq
 
+    def log_density(self, x, stream=None):
+        """(z = T^-1(x), log q(x)) for device points x [dim][n]."""
+        n = x.shape[1]
+        assert x.dtype == torch.float32 and x.is_contiguous() and x.shape[0] == self.dim
+        z = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")
+        lq = torch.empty((n,), dtype=torch.float32, device="cuda")
+        L.check(L.lib().fd_nsf_log_density(self.handle, _ptr(x), n, _ptr(z), _ptr(lq), _stream_ptr(stream)))
+        return z, lq
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h and L._lib is not None:

@@ -39,9 +39,13 @@ __host__ __device__ __forceinline__ int64_t layer_floats(int n_keep, int n_move)
 
 __device__ __forceinline__ float softplusf(float a) { return a > 20.0f ? a : log1pf(expf(a)); }
 
-// rational-quadratic spline on [0, 1]: y = g(u) and log g'(u) from the 23
-// parameters (widths, heights, internal-knot derivatives)
-__device__ __forceinline__ void rq_spline(const float (&p)[kPad], float u, float &y, float &logd) {
+// The bin of the rational-quadratic spline on [0, 1] that holds v (an input
+// coordinate, or with BY_Y an output coordinate) from the 23 parameters
+// (widths, heights, internal-knot derivative logits): its knots and the
+// derivatives there.
+template <bool BY_Y>
+__device__ __forceinline__ void rq_bin(const float (&p)[kPad], float v, float &x0, float &x1, float &y0, float &y1,
+                                       float &d0, float &d1) {
     float mw = p[0], mh = p[kBins];
 #pragma unroll
     for (int k = 1; k < kBins; ++k) {
@@ -67,10 +71,13 @@ __device__ __forceinline__ void rq_spline(const float (&p)[kPad], float u, float
     }
     xs[kBins] = 1.0f;
     ys[kBins] = 1.0f;
-    int bin = 0;                                   // the number of internal knots at or below u
+    int bin = 0;                                   // the number of internal knots at or below v
 #pragma unroll
-    for (int k = 1; k < kBins; ++k) bin += u >= xs[k] ? 1 : 0;
-    float x0 = 0.0f, x1 = 1.0f, y0 = 0.0f, y1 = 1.0f;
+    for (int k = 1; k < kBins; ++k) bin += v >= (BY_Y ? ys[k] : xs[k]) ? 1 : 0;
+    x0 = 0.0f;
+    x1 = 1.0f;
+    y0 = 0.0f;
+    y1 = 1.0f;
 #pragma unroll
     for (int k = 0; k < kBins; ++k)
         if (k == bin) {
@@ -85,14 +92,38 @@ __device__ __forceinline__ void rq_spline(const float (&p)[kPad], float u, float
         if (k == bin - 1) pd0 = p[2 * kBins + k];
         if (k == bin) pd1 = p[2 * kBins + k];
     }
-    const float d0 = bin > 0 ? kMinD + softplusf(pd0) : 1.0f;
-    const float d1 = bin < kBins - 1 ? kMinD + softplusf(pd1) : 1.0f;
+    d0 = bin > 0 ? kMinD + softplusf(pd0) : 1.0f;
+    d1 = bin < kBins - 1 ? kMinD + softplusf(pd1) : 1.0f;
+}
+
+// log g' at the bin's relative position xi
+__device__ __forceinline__ float rq_logd(float s, float xi, float d0, float d1) {
+    const float t = xi * (1.0f - xi), den = s + (d1 + d0 - 2.0f * s) * t;
+    const float num = s * s * (d1 * xi * xi + 2.0f * s * t + d0 * (1.0f - xi) * (1.0f - xi));
+    return logf(num) - 2.0f * logf(den);
+}
+
+// y = g(u) and log g'(u)
+__device__ __forceinline__ void rq_spline(const float (&p)[kPad], float u, float &y, float &logd) {
+    float x0, x1, y0, y1, d0, d1;
+    rq_bin<false>(p, u, x0, x1, y0, y1, d0, d1);
     const float wk = x1 - x0, hk = y1 - y0;
     const float s = hk / wk, xi = (u - x0) / wk, t = xi * (1.0f - xi);
     const float den = s + (d1 + d0 - 2.0f * s) * t;
     y = y0 + hk * (s * xi * xi + d0 * t) / den;
-    const float num = s * s * (d1 * xi * xi + 2.0f * s * t + d0 * (1.0f - xi) * (1.0f - xi));
-    logd = logf(num) - 2.0f * logf(den);
+    logd = rq_logd(s, xi, d0, d1);
+}
+
+// u = g^-1(y) (the root in [0, 1] of the bin's quadratic in xi) and log g'(u)
+__device__ __forceinline__ void rq_spline_inverse(const float (&p)[kPad], float y, float &u, float &logd) {
+    float x0, x1, y0, y1, d0, d1;
+    rq_bin<true>(p, y, x0, x1, y0, y1, d0, d1);
+    const float wk = x1 - x0, hk = y1 - y0, s = hk / wk, dy = y - y0, e = d1 + d0 - 2.0f * s;
+    const float qa = hk * (s - d0) + dy * e, qb = hk * d0 - dy * e, qc = -s * dy;
+    const float disc = fmaxf(qb * qb - 4.0f * qa * qc, 0.0f);
+    const float xi = (2.0f * qc) / (-qb - sqrtf(disc));
+    u = x0 + xi * wk;
+    logd = rq_logd(s, xi, d0, d1);
 }
 
 struct NsfArgs {
@@ -117,7 +148,10 @@ __host__ __device__ __forceinline__ int64_t layer_smem_floats(int n_keep, int n_
     return head_floats(n_keep) + (int64_t)(kHidden + 1) * n_move * kPad;
 }
 
-__global__ void __launch_bounds__(128) nsf_forward_kernel(const NsfArgs a) {
+// INV = false: z -> x = T(z); INV = true: x -> z = T^-1(x) (the layers in
+// reverse order).  Both return log q(x) = -sum of the log derivatives.
+template <bool INV>
+__global__ void __launch_bounds__(128) nsf_kernel(const NsfArgs a) {
     extern __shared__ __align__(16) float wsm[];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < a.n;
@@ -140,11 +174,13 @@ __global__ void __launch_bounds__(128) nsf_forward_kernel(const NsfArgs a) {
         }
     }
     float logq = 0.0f;
-    const float *lp = a.params;
-    for (int layer = 0; layer < a.n_layers; ++layer) {
+    for (int step = 0; step < a.n_layers; ++step) {
+        const int layer = INV ? a.n_layers - 1 - step : step;
+        const float *lp = a.params;
+        for (int l = 0; l < layer; ++l) lp += layer_floats(l % 2 == 0 ? half : D - half, l % 2 == 0 ? D - half : half);
         const int keep0 = layer % 2 == 0 ? 0 : half, n_keep = layer % 2 == 0 ? half : D - half;
         const int move0 = layer % 2 == 0 ? half : 0, n_move = D - n_keep;
-        const int64_t nf = layer_floats(n_keep, n_move), head = head_floats(n_keep);
+        const int64_t head = head_floats(n_keep);
         const int row = n_move * kParamsPerDim;                    // W1 row length in global memory
         __syncthreads();                                            // the previous layer's weights are consumed
         for (int64_t k = threadIdx.x; k < head; k += blockDim.x) wsm[k] = __ldg(lp + k);
@@ -239,13 +275,15 @@ __global__ void __launch_bounds__(128) nsf_forward_kernel(const NsfArgs a) {
             for (int j = 0; j < kMaxDim; ++j)
                 if (j == move0 + m) u = v[j];
             float y, logd;
-            rq_spline(p, fminf(fmaxf(u, 0.0f), 1.0f), y, logd);
+            if (INV)
+                rq_spline_inverse(p, fminf(fmaxf(u, 0.0f), 1.0f), y, logd);
+            else
+                rq_spline(p, fminf(fmaxf(u, 0.0f), 1.0f), y, logd);
 #pragma unroll
             for (int j = 0; j < kMaxDim; ++j)
                 if (j == move0 + m) v[j] = y;
             logq -= logd;
         }
-        lp += nf;
     }
     if (!valid) return;
 #pragma unroll
@@ -274,8 +312,8 @@ fd_status nsf_sizes(int dim, int n_layers, int64_t &total, int64_t &max_layer) {
     return FD_OK;
 }
 
-fd_status nsf_launch(const fd_nsf *f, const float *z, int64_t ldz, uint64_t seed, uint64_t iter, int32_t inst,
-                     int64_t n, float *x, int64_t ldx, float *logq, cudaStream_t stream) {
+fd_status nsf_launch(const fd_nsf *f, bool inverse, const float *z, int64_t ldz, uint64_t seed, uint64_t iter,
+                     int32_t inst, int64_t n, float *x, int64_t ldx, float *logq, cudaStream_t stream) {
     FD_REQUIRE(f && x && logq, "flow, x and logq are required");
     FD_REQUIRE(n > 0, "n must be positive");
     FD_REQUIRE(inst >= 0 && inst < (1 << 24), "inst out of range");
@@ -297,8 +335,13 @@ fd_status nsf_launch(const fd_nsf *f, const float *z, int64_t ldz, uint64_t seed
     a.iter = (uint32_t)iter;
     a.inst = (uint32_t)inst;
     const size_t smem = (size_t)f->max_layer * sizeof(float);
-    FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    nsf_forward_kernel<<<(unsigned)((n + 127) / 128), 128, smem, stream>>>(a);
+    if (inverse) {
+        FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        nsf_kernel<true><<<(unsigned)((n + 127) / 128), 128, smem, stream>>>(a);
+    } else {
+        FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        nsf_kernel<false><<<(unsigned)((n + 127) / 128), 128, smem, stream>>>(a);
+    }
     FD_CHECK_CUDA(cudaGetLastError());
     return FD_OK;
 }
@@ -343,10 +386,16 @@ extern "C" fd_status fd_nsf_set_params(fd_nsf *f, const float *params, int64_t n
 extern "C" fd_status fd_nsf_forward(const fd_nsf *f, const float *z, int64_t n, float *x, float *logq,
                                     void *stream) {
     FD_REQUIRE(z, "z is required");
-    return nsf_launch(f, z, n, 0, 0, 0, n, x, n, logq, (cudaStream_t)stream);
+    return nsf_launch(f, false, z, n, 0, 0, 0, n, x, n, logq, (cudaStream_t)stream);
+}
+
+extern "C" fd_status fd_nsf_log_density(const fd_nsf *f, const float *x, int64_t n, float *z, float *logq,
+                                        void *stream) {
+    FD_REQUIRE(x && z, "x and z are required");
+    return nsf_launch(f, true, x, n, 0, 0, 0, n, z, n, logq, (cudaStream_t)stream);
 }
 
 extern "C" fd_status fd_nsf_sample(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n, float *x,
                                    float *logq, void *stream) {
-    return nsf_launch(f, nullptr, 0, seed, iter, inst, n, x, n, logq, (cudaStream_t)stream);
+    return nsf_launch(f, false, nullptr, 0, seed, iter, inst, n, x, n, logq, (cudaStream_t)stream);
 }

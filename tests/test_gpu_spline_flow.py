@@ -1,6 +1,7 @@
-"""GPU parity of the spline flow's sampling and density pass (App. A) with the
-FP64 oracle on the same parameters: explicit points, the Philox sample
-stream, the identity flow, and a ragged sample count."""
+"""GPU parity of the spline flow's sampling and density passes (App. A) with
+the FP64 oracle on the same parameters: explicit points, the Philox sample
+stream, the density at given points (inverse pass), a sample -> density
+round trip, the identity flow, and ragged sample counts."""
 import numpy as np
 import pytest
 
@@ -73,6 +74,32 @@ def test_sample_stream_matches_oracle(api):
     z = ophilox.uniforms(21, 4, 3, np.arange(n), dim)
     x_ref, lq_ref = flow.forward(z.T)
     _compare(x.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), x_ref.T, lq_ref, "sample")
+
+
+@pytest.mark.parametrize("dim", [19, 6])
+def test_log_density_matches_oracle(api, dim):
+    flow = _as_fp32(osf.SplineFlow(dim, 8, seed=15, scale=0.8))
+    g = api.SplineFlow(dim, 8)
+    g.set_params(_flatten(flow))
+    n = 2 * 1000 + 33
+    z0 = workloads.uniform_points(16, dim, n)
+    x_ref, _ = flow.forward(z0.T)                            # points inside the flow's image
+    z, lq = g.log_density(torch.tensor(x_ref.T, dtype=torch.float32, device="cuda").contiguous())
+    lq_ref, z_ref = flow.log_density(x_ref.astype(np.float32).astype(np.float64))
+    _compare(z.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), z_ref.T, lq_ref,
+             "log density dim %d" % dim)
+
+
+def test_sample_then_density_round_trip(api):
+    dim, n = 19, 4096
+    flow = _as_fp32(osf.SplineFlow(dim, 8, seed=17, scale=0.8))
+    g = api.SplineFlow(dim, 8)
+    g.set_params(_flatten(flow))
+    x, lq = g.sample(5, 0, 1, n)
+    z, lq2 = g.log_density(x)
+    z0 = ophilox.uniforms(5, 0, 1, np.arange(n), dim)
+    _compare(z.cpu().numpy().astype(np.float64), lq2.cpu().numpy().astype(np.float64), z0,
+             lq.cpu().numpy().astype(np.float64), "round trip")
 
 
 def test_identity_flow(api):
