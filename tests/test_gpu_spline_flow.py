@@ -41,15 +41,19 @@ def _as_fp32(flow):
     return flow
 
 
-def _compare(x_gpu, lq_gpu, x_ref, lq_ref, label):
-    # FP32 through 8 layers: a coordinate carries ~1e-6 absolute error; log q
-    # sums 8 x (D/2) log-derivatives of ~1e-6 each, ~1e-4 in the worst samples
+def _compare(x_gpu, lq_gpu, x_ref, lq_ref, label, inverse=False):
+    # Forward: FP32 through 8 layers, a coordinate carries ~1e-6 absolute error
+    # and log q (a sum of 8 x D/2 log-derivatives) ~1e-4 in the worst samples.
+    # Inverse: each layer divides the error of its input by the spline's
+    # derivative there (down to ~0.1 for these parameters), so the errors are
+    # ~10x larger: ~2e-5 / 2e-4 for z, 3e-4 / 2e-3 for log q (99 % / max).
     dx = np.abs(x_gpu - x_ref).max(axis=0)
     dl = np.abs(lq_gpu - lq_ref)
     print("%s: max |dx| %.3e (99%% %.3e), max |d log q| %.3e (99%% %.3e)" %
           (label, dx.max(), np.quantile(dx, 0.99), dl.max(), np.quantile(dl, 0.99)))
-    assert np.quantile(dx, 0.99) < 5e-6 and dx.max() < 5e-5, label
-    assert np.quantile(dl, 0.99) < 1e-4 and dl.max() < 1e-3, label
+    bx, bl = ((5e-5, 5e-4), (1e-3, 1e-2)) if inverse else ((5e-6, 5e-5), (1e-4, 1e-3))
+    assert np.quantile(dx, 0.99) < bx[0] and dx.max() < bx[1], label
+    assert np.quantile(dl, 0.99) < bl[0] and dl.max() < bl[1], label
 
 
 @pytest.mark.parametrize("dim", [19, 5])
@@ -87,7 +91,7 @@ def test_log_density_matches_oracle(api, dim):
     z, lq = g.log_density(torch.tensor(x_ref.T, dtype=torch.float32, device="cuda").contiguous())
     lq_ref, z_ref = flow.log_density(x_ref.astype(np.float32).astype(np.float64))
     _compare(z.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), z_ref.T, lq_ref,
-             "log density dim %d" % dim)
+             "log density dim %d" % dim, inverse=True)
 
 
 def test_sample_then_density_round_trip(api):
@@ -99,7 +103,7 @@ def test_sample_then_density_round_trip(api):
     z, lq2 = g.log_density(x)
     z0 = ophilox.uniforms(5, 0, 1, np.arange(n), dim)
     _compare(z.cpu().numpy().astype(np.float64), lq2.cpu().numpy().astype(np.float64), z0,
-             lq.cpu().numpy().astype(np.float64), "round trip")
+             lq.cpu().numpy().astype(np.float64), "round trip", inverse=True)
 
 
 def test_identity_flow(api):
