@@ -336,7 +336,8 @@ void fd_nsf_free(fd_nsf *f);
 int64_t fd_nsf_param_count(const fd_nsf *f);
 fd_status fd_nsf_set_params(fd_nsf *f, const float *params, int64_t n);  /* synchronous; FD_EINVAL if non-finite */
 /* x = T(z) for device z [dim][n]: x (device FP32 [dim][n]) and log q(x)
- * (device FP32 [n]).  Asynchronous on stream. */
+ * (device FP32 [n]); 1 <= n <= 2^36 (FD_EINVAL otherwise).  Asynchronous on
+ * stream. */
 fd_status fd_nsf_forward(const fd_nsf *f, const float *z, int64_t n, float *x, float *logq, void *stream);
 /* The same with z from the sample stream (Philox counter (i_lo, i_hi, iter,
  * inst << 8 | block), u = ((w >> 9) + 0.5) 2^-23). */

@@ -315,7 +315,7 @@ fd_status nsf_sizes(int dim, int n_layers, int64_t &total, int64_t &max_layer) {
 fd_status nsf_launch(const fd_nsf *f, bool inverse, const float *z, int64_t ldz, uint64_t seed, uint64_t iter,
                      int32_t inst, int64_t n, float *x, int64_t ldx, float *logq, cudaStream_t stream) {
     FD_REQUIRE(f && x && logq, "flow, x and logq are required");
-    FD_REQUIRE(n > 0, "n must be positive");
+    FD_REQUIRE(n > 0 && n <= (int64_t(1) << 36), "n must be in [1, 2^36]");
     FD_REQUIRE(inst >= 0 && inst < (1 << 24), "inst out of range");
     int dev = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
