@@ -164,3 +164,54 @@ class SplineFlow:
             z[:, move] = v
             logq += logd_inv.sum(axis=1)
         return logq, z
+
+    # ---- parameters as one vector (the library's order) and the training loss
+
+    def flat(self):
+        """All parameters, layer after layer: W0, b0, (W_a, b_a, W_b, b_b) per
+        block, W1, b1 (row-major, inputs first)."""
+        parts = []
+        for _, _, net in self.layers:
+            parts += [net.w0.ravel(), net.b0]
+            for (wa, ba), (wb, bb) in net.blocks:
+                parts += [wa.ravel(), ba, wb.ravel(), bb]
+            parts += [net.w1.ravel(), net.b1]
+        return np.concatenate(parts)
+
+    def set_flat(self, vec):
+        vec = np.asarray(vec, dtype=np.float64)
+        k = 0
+
+        def take(shape):
+            nonlocal k
+            n = int(np.prod(shape))
+            out = vec[k:k + n].reshape(shape).copy()
+            k += n
+            return out
+        for _, _, net in self.layers:
+            net.w0, net.b0 = take(net.w0.shape), take(net.b0.shape)
+            net.blocks = [tuple((take(w.shape), take(b.shape)) for (w, b) in blk) for blk in net.blocks]
+            net.w1, net.b1 = take(net.w1.shape), take(net.b1.shape)
+        assert k == vec.size
+
+    def kl_loss(self, x, w):
+        """Forward KL to the target up to a constant (App. A): -sum w log q(x) / sum w
+        for points x [N, D] drawn from some proposal with weights w = p*/q_proposal."""
+        logq, _ = self.log_density(x)
+        return -float(np.sum(w * logq) / np.sum(w))
+
+    def kl_grad_fd(self, x, w, h=1e-6):
+        """Gradient of kl_loss over flat() by central differences (plain and slow)."""
+        theta = self.flat()
+        g = np.empty_like(theta)
+        for j in range(theta.size):
+            tp, tm = theta.copy(), theta.copy()
+            tp[j] += h
+            tm[j] -= h
+            self.set_flat(tp)
+            lp = self.kl_loss(x, w)
+            self.set_flat(tm)
+            lm = self.kl_loss(x, w)
+            g[j] = (lp - lm) / (2 * h)
+        self.set_flat(theta)
+        return g

@@ -22,13 +22,7 @@ def api():
 
 def _flatten(flow):
     """The oracle's parameters in the library's order (fd_nsf_set_params)."""
-    parts = []
-    for _, _, net in flow.layers:
-        parts += [net.w0.ravel(), net.b0]
-        for (wa, ba), (wb, bb) in net.blocks:
-            parts += [wa.ravel(), ba, wb.ravel(), bb]
-        parts += [net.w1.ravel(), net.b1]
-    return np.concatenate(parts).astype(np.float32)
+    return flow.flat().astype(np.float32)
 
 
 def _as_fp32(flow):

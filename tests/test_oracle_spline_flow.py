@@ -106,3 +106,42 @@ def test_density_integrates_to_one():
     _, logq = sharp.forward(z)
     r = np.exp(-logq)
     assert abs(r.mean() - 1.0) < 5 * r.std() / np.sqrt(r.size)
+
+
+def test_flat_parameters_round_trip_and_loss_gradient():
+    # a small flow: the parameter vector round-trips, the finite-difference
+    # gradient of the forward-KL loss is step-consistent, and a descent step
+    # along it lowers the loss
+    flow = sf.SplineFlow(2, 1, seed=21, scale=0.8)
+    theta = flow.flat()
+    z = np.random.default_rng(22).random((40, 2))
+    x0, _ = flow.forward(z)
+    flow.set_flat(theta)
+    x1, _ = flow.forward(z)
+    assert np.array_equal(x0, x1) and np.array_equal(flow.flat(), theta)
+    rng = np.random.default_rng(23)
+    x = rng.uniform(0.02, 0.98, (16, 2))
+    w = np.exp(-8 * ((x - 0.3) ** 2).sum(axis=1))              # a peaked target
+    g = flow.kl_grad_fd(x, w, h=1e-5)
+    assert np.linalg.norm(g) > 0
+    # step consistency on the output layer (the parameters the loss moves most)
+    out = slice(theta.size - 23 * 9, theta.size)
+    sub = sf.SplineFlow(2, 1, seed=21, scale=0.8)
+    g2 = np.array([_fd_one(sub, x, w, j, 5e-6) for j in range(out.start, out.stop)])
+    assert np.allclose(g[out], g2, rtol=1e-5, atol=1e-9)
+    l0 = flow.kl_loss(x, w)
+    flow.set_flat(theta - 1e-2 * g / np.linalg.norm(g))
+    assert flow.kl_loss(x, w) < l0
+
+
+def _fd_one(flow, x, w, j, h):
+    theta = flow.flat()
+    tp, tm = theta.copy(), theta.copy()
+    tp[j] += h
+    tm[j] -= h
+    flow.set_flat(tp)
+    lp = flow.kl_loss(x, w)
+    flow.set_flat(tm)
+    lm = flow.kl_loss(x, w)
+    flow.set_flat(theta)
+    return (lp - lm) / (2 * h)
