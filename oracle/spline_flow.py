@@ -218,12 +218,13 @@ class SplineFlow:
 
     # ---- reverse-mode gradient of the loss through the inverse pass
 
-    def kl_grad(self, x, w, h_local=1e-6):
+    def kl_grad(self, x, w, h_local=1e-6, analytic=False):
         """Gradient of kl_loss over flat() by the chain rule through the inverse
         pass: exact through the conditioner (linear maps, ReLU, residual sums);
         each spline's partial derivatives with respect to its 23 parameters and
         its input by FP64 central differences of the spline alone (step
-        h_local).  Checked against kl_grad_fd."""
+        h_local), or in closed form with analytic.  Checked against
+        kl_grad_fd."""
         x = np.asarray(x, dtype=np.float64)
         N = x.shape[0]
         c = -np.asarray(w, dtype=np.float64) / np.sum(w)          # d loss / d log q_i
@@ -248,7 +249,8 @@ class SplineFlow:
         grads = {}
         vbar = np.zeros_like(v)                                    # d loss / d (the layer's output)
         for keep, move, net, k, hs, acts, P, u in reversed(tape):  # layers 0, 1, ... of the flow
-            g_P, l_P, l_u, lg = _spline_partials(u, P, h_local)   # dg/dP, dl/dP, dl/du, l = log g'
+            g_P, l_P, l_u, lg = (_spline_partials_analytic(u, P) if analytic
+                                 else _spline_partials(u, P, h_local))  # dg/dP, dl/dP, dl/du, l = log g'
             # loss = ... + c * (-sum_m l_m): sources at u and P
             ubar = vbar[:, move] - c[:, None] * l_u
             gprime = np.exp(lg)
@@ -309,3 +311,78 @@ def _spline_partials(u, P, h):
     l_u = (lp - lm) / (up - um)
     _, l0 = _spline_eval(u, P)
     return g_P, l_P, l_u, l0
+
+
+def _spline_partials_analytic(u, P):
+    """Closed-form partials of one spline each, the same quantities as
+    _spline_partials: dg/dP [.., 23], dl/dP [.., 23], dl/du [..] and l = log g'.
+
+    Inside bin k (w, h its width and height, s = h/w, xi = (u - x_k)/w,
+    t = xi (1 - xi), d0, d1 the knot derivatives): g = y_k + h N/E with
+    N = s xi^2 + d0 t, E = s + (d1 + d0 - 2 s) t, and l = 2 log s + log M -
+    2 log E with M = d1 xi^2 + 2 s t + d0 (1 - xi)^2.  The local variables
+    depend on the raw parameters through the softmax (w_i = m + (1 - K m)
+    softmax_i), the cumulative sums x_k = sum_{i<k} w_i (heights alike) and
+    the softplus of the internal-knot derivative logits."""
+    K = K_BINS
+    tw, th, td = P[..., :K], P[..., K:2 * K], P[..., 2 * K:]
+    sw, sh = _softmax(tw), _softmax(th)
+    X, Y, D = knots(tw, th, td)
+    k = _bin(u, X)
+    xk, yk = _take(X, k), _take(Y, k)
+    w, h = _take(X, k + 1) - xk, _take(Y, k + 1) - yk
+    d0, d1 = _take(D, k), _take(D, k + 1)
+    s = h / w
+    xi = (u - xk) / w
+    t = xi * (1.0 - xi)
+    tp = 1.0 - 2.0 * xi
+    N = s * xi * xi + d0 * t
+    E = s + (d1 + d0 - 2.0 * s) * t
+    M = d1 * xi * xi + 2.0 * s * t + d0 * (1.0 - xi) ** 2
+    l = 2.0 * np.log(s) + np.log(M) - 2.0 * np.log(E)
+    # partials of (N, E, M) in (xi, s, d0, d1)
+    N_xi, N_s, N_d0 = 2.0 * s * xi + d0 * tp, xi * xi, t
+    E_xi, E_s, E_d0, E_d1 = (d1 + d0 - 2.0 * s) * tp, 1.0 - 2.0 * t, t, t
+    M_xi, M_s, M_d0, M_d1 = 2.0 * d1 * xi + 2.0 * s * tp - 2.0 * d0 * (1.0 - xi), 2.0 * t, (1.0 - xi) ** 2, xi * xi
+    R = N / E
+
+    def dR(Nv, Ev):
+        return (Nv * E - N * Ev) / (E * E)
+    g_xi, g_s, g_d0, g_d1 = h * dR(N_xi, E_xi), h * dR(N_s, E_s), h * dR(N_d0, E_d0), h * dR(0.0, E_d1)
+    l_xi = M_xi / M - 2.0 * E_xi / E
+    l_s = 2.0 / s + M_s / M - 2.0 * E_s / E
+    l_d0 = M_d0 / M - 2.0 * E_d0 / E
+    l_d1 = M_d1 / M - 2.0 * E_d1 / E
+    # local variables in terms of (x_k, w, y_k, h): xi(u, x_k, w), s(h, w)
+    g_xk, l_xk = -g_xi / w, -l_xi / w
+    g_w = g_xi * (-xi / w) + g_s * (-s / w)
+    l_w = l_xi * (-xi / w) + l_s * (-s / w)
+    g_yk, g_h = 1.0, R + g_s / w
+    l_yk, l_h = 0.0, l_s / w
+    l_u = l_xi / w
+    # widths and heights: dw_i / dtheta_a = (1 - K m) s_i (delta_ia - s_a)
+    cw, ch = 1.0 - MIN_W * K, 1.0 - MIN_H * K
+    idx = np.arange(K)
+    below = (idx < k[..., None]).astype(float)                 # i < k: in x_k
+    at = (idx == k[..., None]).astype(float)                   # i = k: the bin itself
+    # d x_k / d theta_a = sum_{i<k} cw s_i (delta_ia - s_a); d w_k / d theta_a = cw s_k (delta_ka - s_a)
+    sum_below_w = (below * sw).sum(axis=-1, keepdims=True)
+    dxk_dtw = cw * (below * sw - sum_below_w * sw)
+    dw_dtw = cw * (at * sw - (at * sw).sum(axis=-1, keepdims=True) * sw)
+    sum_below_h = (below * sh).sum(axis=-1, keepdims=True)
+    dyk_dth = ch * (below * sh - sum_below_h * sh)
+    dh_dth = ch * (at * sh - (at * sh).sum(axis=-1, keepdims=True) * sh)
+    g_P = np.zeros(P.shape)
+    l_P = np.zeros(P.shape)
+    g_P[..., :K] = g_xk[..., None] * dxk_dtw + g_w[..., None] * dw_dtw
+    l_P[..., :K] = l_xk[..., None] * dxk_dtw + l_w[..., None] * dw_dtw
+    g_P[..., K:2 * K] = g_yk * dyk_dth + g_h[..., None] * dh_dth
+    l_P[..., K:2 * K] = l_yk * dyk_dth + l_h[..., None] * dh_dth
+    # knot derivatives: d0 = m + softplus(theta_d[k - 1]) for k >= 1, d1 = ... theta_d[k] for k <= K - 2
+    sig = 1.0 / (1.0 + np.exp(-td))
+    jd = np.arange(K - 1)
+    at0 = (jd == (k - 1)[..., None]).astype(float)
+    at1 = (jd == k[..., None]).astype(float)
+    g_P[..., 2 * K:] = (g_d0[..., None] * at0 + g_d1[..., None] * at1) * sig
+    l_P[..., 2 * K:] = (l_d0[..., None] * at0 + l_d1[..., None] * at1) * sig
+    return g_P, l_P, l_u, l

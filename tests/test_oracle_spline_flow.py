@@ -164,3 +164,25 @@ def test_reverse_mode_gradient_matches_finite_differences():
     idx = rng.choice(g.size, 120, replace=False)
     gf = np.array([_fd_one(flow, x, w, j, 1e-5) for j in idx])
     assert np.max(np.abs(g[idx] - gf)) < 1e-6 * max(np.max(np.abs(gf)), 1e-3)
+
+
+
+def test_closed_form_spline_partials():
+    # the closed-form partials of one spline (what a GPU backward pass would
+    # evaluate) against central differences: the gap shrinks as the step
+    # squared, to ~2e-6 of the scale at step 1e-6
+    rng = np.random.default_rng(5)
+    P = rng.normal(0, 1.2, (500, sf.K_BINS * 3 - 1))
+    u = rng.uniform(0.01, 0.99, 500)
+    a = sf._spline_partials_analytic(u, P)
+    f5 = sf._spline_partials(u, P, 1e-5)
+    f6 = sf._spline_partials(u, P, 1e-6)
+    for x, y5, y6 in zip(a, f5, f6):
+        e5 = np.max(np.abs(x - y5) / (np.abs(y5) + 1.0))
+        e6 = np.max(np.abs(x - y6) / (np.abs(y6) + 1.0))
+        assert e6 < 1e-5 and (e6 < 1e-13 or e6 < 0.05 * e5)     # exact, or second-order convergence
+    rng = np.random.default_rng(24)
+    flow = sf.SplineFlow(3, 2, seed=31, scale=0.8)
+    x = rng.uniform(0.02, 0.98, (12, 3))
+    w = rng.random(12)
+    assert np.allclose(flow.kl_grad(x, w, analytic=True), flow.kl_grad(x, w), rtol=1e-5, atol=1e-9)
