@@ -348,6 +348,19 @@ fd_status fd_nsf_sample(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t i
  * log q(x) (device FP32 [n]) for device x [dim][n] in [0, 1]^dim.
  * Asynchronous on stream. */
 fd_status fd_nsf_log_density(const fd_nsf *f, const float *x, int64_t n, float *z, float *logq, void *stream);
+/* Forward-KL training loss of the flow (App. A) and its gradient:
+ * loss = -sum_i w_i log q(x_i) / sum_i w_i over device points x [dim][n] in
+ * [0, 1]^dim with device weights w [n] (e.g. |f|/q of the proposal that drew
+ * them; sum w > 0), and grad = d loss / d parameters (device FP32
+ * [fd_nsf_param_count], the parameter layout above, overwritten).  Reverse
+ * mode through the inverse pass with the splines' closed-form partials, FP32
+ * per sample; loss (device FP64 [1], overwritten) and grad are sums over
+ * samples by atomics, so their last bits depend on the order of arrival.
+ * n_layers <= 16 (FD_EINVAL otherwise); 1 <= n <= 2^36.  Asynchronous on
+ * stream; calls on one flow must not overlap on different streams (they share
+ * the flow's weight-sum scratch word). */
+fd_status fd_nsf_kl_grad(const fd_nsf *f, const float *x, const float *w, int64_t n, float *grad, double *loss,
+                         void *stream);
 
 /* ---- NF-MCMC / VEGAS-MCMC chains (Sec. V, Eqs. target_distr and
  * nf_mcmc_estimator) --------------------------------------------------------

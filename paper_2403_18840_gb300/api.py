@@ -286,7 +286,8 @@ class Flow:
 
 class SplineFlow:
     """Neural spline flow (App. A): rational-quadratic coupling layers on the
-    unit hypercube; sampling and density on the device (fd_nsf_*)."""
+    unit hypercube; sampling, density and the training loss's gradient on the
+    device (fd_nsf_*)."""
 
     def __init__(self, dim, n_layers=8):
         h = ctypes.c_void_p()
@@ -321,6 +322,19 @@ class SplineFlow:
         lq = torch.empty((n,), dtype=torch.float32, device="cuda")
         L.check(L.lib().fd_nsf_log_density(self.handle, _ptr(x), n, _ptr(z), _ptr(lq), _stream_ptr(stream)))
         return z, lq
+
+    def kl_grad(self, x, w, stream=None):
+        """(loss, grad): the forward-KL loss -sum w log q(x) / sum w over device
+        points x [dim][n] with weights w [n], and its gradient over the
+        parameters (device FP64 [1], device FP32 [n_params])."""
+        n = x.shape[1]
+        assert x.dtype == torch.float32 and x.is_contiguous() and x.shape[0] == self.dim
+        assert w.dtype == torch.float32 and w.is_contiguous() and w.shape == (n,)
+        grad = torch.empty((self.n_params,), dtype=torch.float32, device="cuda")
+        loss = torch.empty((1,), dtype=torch.float64, device="cuda")
+        L.check(L.lib().fd_nsf_kl_grad(self.handle, _ptr(x), _ptr(w), n, _ptr(grad), _ptr(loss),
+                                       _stream_ptr(stream)))
+        return loss, grad
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -16,6 +16,7 @@
 // more than 23 registers.  FP32 arithmetic with IEEE exp/log (the parameters
 // pass through softmax and softplus).
 #include "fd_internal.cuh"
+#include "fd_nsf_math.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -23,108 +24,7 @@
 
 namespace {
 
-constexpr int kBins = 8;
-constexpr int kHidden = 32;
-constexpr int kParamsPerDim = 3 * kBins - 1;
-constexpr int kMaxDim = 24;
-constexpr float kMinW = 1e-3f, kMinH = 1e-3f, kMinD = 1e-3f;
-constexpr int kPad = 24;                 // a coordinate's 23 spline parameters, padded for 16-byte loads
-
-// per layer: W0 [n_keep][32], b0 [32], two blocks of (Wa [32][32], ba [32],
-// Wb [32][32], bb [32]), W1 [32][n_move * 23], b1 [n_move * 23]
-__host__ __device__ __forceinline__ int64_t layer_floats(int n_keep, int n_move) {
-    return (int64_t)n_keep * kHidden + kHidden + 2 * (2 * (kHidden * kHidden + kHidden)) +
-           (int64_t)kHidden * n_move * kParamsPerDim + (int64_t)n_move * kParamsPerDim;
-}
-
-__device__ __forceinline__ float softplusf(float a) { return a > 20.0f ? a : log1pf(expf(a)); }
-
-// The bin of the rational-quadratic spline on [0, 1] that holds v (an input
-// coordinate, or with BY_Y an output coordinate) from the 23 parameters
-// (widths, heights, internal-knot derivative logits): its knots and the
-// derivatives there.
-template <bool BY_Y>
-__device__ __forceinline__ void rq_bin(const float (&p)[kPad], float v, float &x0, float &x1, float &y0, float &y1,
-                                       float &d0, float &d1) {
-    float mw = p[0], mh = p[kBins];
-#pragma unroll
-    for (int k = 1; k < kBins; ++k) {
-        mw = fmaxf(mw, p[k]);
-        mh = fmaxf(mh, p[kBins + k]);
-    }
-    float ew[kBins], eh[kBins], sw = 0.0f, sh = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kBins; ++k) {
-        ew[k] = expf(p[k] - mw);
-        eh[k] = expf(p[kBins + k] - mh);
-        sw += ew[k];
-        sh += eh[k];
-    }
-    const float cw = (1.0f - kMinW * kBins) / sw, ch = (1.0f - kMinH * kBins) / sh;
-    float xs[kBins + 1], ys[kBins + 1];
-    xs[0] = 0.0f;
-    ys[0] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kBins; ++k) {
-        xs[k + 1] = xs[k] + (kMinW + cw * ew[k]);
-        ys[k + 1] = ys[k] + (kMinH + ch * eh[k]);
-    }
-    xs[kBins] = 1.0f;
-    ys[kBins] = 1.0f;
-    int bin = 0;                                   // the number of internal knots at or below v
-#pragma unroll
-    for (int k = 1; k < kBins; ++k) bin += v >= (BY_Y ? ys[k] : xs[k]) ? 1 : 0;
-    x0 = 0.0f;
-    x1 = 1.0f;
-    y0 = 0.0f;
-    y1 = 1.0f;
-#pragma unroll
-    for (int k = 0; k < kBins; ++k)
-        if (k == bin) {
-            x0 = xs[k];
-            x1 = xs[k + 1];
-            y0 = ys[k];
-            y1 = ys[k + 1];
-        }
-    float pd0 = 0.0f, pd1 = 0.0f;                // the derivative logits at the bin's knots
-#pragma unroll
-    for (int k = 0; k < kBins - 1; ++k) {
-        if (k == bin - 1) pd0 = p[2 * kBins + k];
-        if (k == bin) pd1 = p[2 * kBins + k];
-    }
-    d0 = bin > 0 ? kMinD + softplusf(pd0) : 1.0f;
-    d1 = bin < kBins - 1 ? kMinD + softplusf(pd1) : 1.0f;
-}
-
-// log g' at the bin's relative position xi
-__device__ __forceinline__ float rq_logd(float s, float xi, float d0, float d1) {
-    const float t = xi * (1.0f - xi), den = s + (d1 + d0 - 2.0f * s) * t;
-    const float num = s * s * (d1 * xi * xi + 2.0f * s * t + d0 * (1.0f - xi) * (1.0f - xi));
-    return logf(num) - 2.0f * logf(den);
-}
-
-// y = g(u) and log g'(u)
-__device__ __forceinline__ void rq_spline(const float (&p)[kPad], float u, float &y, float &logd) {
-    float x0, x1, y0, y1, d0, d1;
-    rq_bin<false>(p, u, x0, x1, y0, y1, d0, d1);
-    const float wk = x1 - x0, hk = y1 - y0;
-    const float s = hk / wk, xi = (u - x0) / wk, t = xi * (1.0f - xi);
-    const float den = s + (d1 + d0 - 2.0f * s) * t;
-    y = y0 + hk * (s * xi * xi + d0 * t) / den;
-    logd = rq_logd(s, xi, d0, d1);
-}
-
-// u = g^-1(y) (the root in [0, 1] of the bin's quadratic in xi) and log g'(u)
-__device__ __forceinline__ void rq_spline_inverse(const float (&p)[kPad], float y, float &u, float &logd) {
-    float x0, x1, y0, y1, d0, d1;
-    rq_bin<true>(p, y, x0, x1, y0, y1, d0, d1);
-    const float wk = x1 - x0, hk = y1 - y0, s = hk / wk, dy = y - y0, e = d1 + d0 - 2.0f * s;
-    const float qa = hk * (s - d0) + dy * e, qb = hk * d0 - dy * e, qc = -s * dy;
-    const float disc = fmaxf(qb * qb - 4.0f * qa * qc, 0.0f);
-    const float xi = (2.0f * qc) / (-qb - sqrtf(disc));
-    u = x0 + xi * wk;
-    logd = rq_logd(s, xi, d0, d1);
-}
+using namespace nsf;
 
 struct NsfArgs {
     const float *params;      // all layers, in order
@@ -135,18 +35,6 @@ struct NsfArgs {
     int dim, n_layers;
     uint32_t seed_lo, seed_hi, iter, inst;
 };
-
-// shared-memory layout of a layer: as in global memory up to the residual
-// blocks; W1 and b1 re-laid as rows of kPad (23 parameters and a zero), so
-// every weight row starts on 16 bytes and is read as float4
-
-__host__ __device__ __forceinline__ int64_t head_floats(int n_keep) {
-    return (int64_t)n_keep * kHidden + kHidden + 2 * (2 * (kHidden * kHidden + kHidden));
-}
-
-__host__ __device__ __forceinline__ int64_t layer_smem_floats(int n_keep, int n_move) {
-    return head_floats(n_keep) + (int64_t)(kHidden + 1) * n_move * kPad;
-}
 
 // INV = false: z -> x = T(z); INV = true: x -> z = T^-1(x) (the layers in
 // reverse order).  Both return log q(x) = -sum of the log derivatives.
@@ -176,8 +64,7 @@ __global__ void __launch_bounds__(128) nsf_kernel(const NsfArgs a) {
     float logq = 0.0f;
     for (int step = 0; step < a.n_layers; ++step) {
         const int layer = INV ? a.n_layers - 1 - step : step;
-        const float *lp = a.params;
-        for (int l = 0; l < layer; ++l) lp += layer_floats(l % 2 == 0 ? half : D - half, l % 2 == 0 ? D - half : half);
+        const float *lp = a.params + layer_offset(layer, D);
         const int keep0 = layer % 2 == 0 ? 0 : half, n_keep = layer % 2 == 0 ? half : D - half;
         const int move0 = layer % 2 == 0 ? half : 0, n_move = D - n_keep;
         const int64_t head = head_floats(n_keep);
@@ -292,12 +179,106 @@ __global__ void __launch_bounds__(128) nsf_kernel(const NsfArgs a) {
     a.logq[i] = logq;
 }
 
+
+// ---- gradient of the forward-KL loss (App. A) ------------------------------
+// loss = -sum_i w_i log q(x_i) / sum_i w_i over given points x_i and weights
+// w_i, and its gradient in every parameter by reverse mode through the
+// inverse pass.  One thread per sample: the inverse pass (layers L-1 .. 0)
+// keeps each layer's input in local memory; the backward sweep then walks the
+// layers in the flow's order (0 .. L-1), recomputing each conditioner from
+// the kept input (layer_backward).  A parameter's gradient is summed over the
+// warp's samples by shuffles and added to global memory by lane 0.
+
+constexpr int kGradMaxLayers = 16;
+
+struct WarpAtomicAcc {
+    float *g;                                 // the layer's slice of the gradient
+    __device__ __forceinline__ void operator()(int64_t k, float v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(g + k, v);
+    }
+};
+
+struct NsfGradArgs {
+    const float *params, *x, *w;   // x [dim][n], w [n]
+    const double *wsum;            // sum of w
+    float *grad;                   // [n_params], zeroed
+    double *loss;                  // zeroed
+    int64_t n;
+    int dim, n_layers;
+};
+
+__global__ void nsf_wsum_kernel(const float *w, int64_t n, double *wsum) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += w[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(wsum, s);
+}
+
+// one layer's weights into shared memory in the staged layout (layer_at)
+__device__ void stage_layer(const float *lp, int n_keep, int n_move, float *wsm) {
+    const int64_t head = head_floats(n_keep);
+    const int row = n_move * kParamsPerDim;
+    __syncthreads();                                         // the previous layer's weights are consumed
+    for (int64_t k = threadIdx.x; k < head; k += blockDim.x) wsm[k] = __ldg(lp + k);
+    for (int64_t k = threadIdx.x; k < (int64_t)(kHidden + 1) * n_move * kPad; k += blockDim.x) {
+        const int q = (int)(k % kPad);
+        const int64_t rm = k / kPad;
+        const int r = (int)(rm / n_move), m = (int)(rm % n_move);
+        wsm[head + k] = q < kParamsPerDim ? __ldg(lp + head + (int64_t)r * row + m * kParamsPerDim + q) : 0.0f;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) nsf_grad_kernel(const NsfGradArgs a) {
+    extern __shared__ __align__(16) float wsm[];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < a.n;
+    const int D = a.dim, half = D / 2;
+    const float c = valid ? (float)(-(double)a.w[i] / *a.wsum) : 0.0f;     // d loss / d log q_i
+    float v[kMaxDim];
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) v[j] = (valid && j < D) ? a.x[(int64_t)j * a.n + i] : 0.5f;
+    float vin[kGradMaxLayers][kMaxDim];
+    float logq = 0.0f;
+    for (int layer = a.n_layers - 1; layer >= 0; --layer) {
+        const int n_keep = layer % 2 == 0 ? half : D - half;
+        stage_layer(a.params + layer_offset(layer, D), n_keep, D - n_keep, wsm);
+#pragma unroll
+        for (int j = 0; j < kMaxDim; ++j) vin[layer][j] = v[j];
+        logq -= layer_inverse(layer_at(wsm, layer, D), v);
+    }
+    {
+        float l = valid ? c * logq : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(a.loss, (double)l);
+    }
+    float vbar[kMaxDim];
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j) vbar[j] = 0.0f;       // z does not enter the loss
+    for (int layer = 0; layer < a.n_layers; ++layer) {
+        const int n_keep = layer % 2 == 0 ? half : D - half;
+        const int64_t off = layer_offset(layer, D);
+        stage_layer(a.params + off, n_keep, D - n_keep, wsm);
+        float xin[kMaxDim];
+#pragma unroll
+        for (int j = 0; j < kMaxDim; ++j) xin[j] = vin[layer][j];
+        WarpAtomicAcc acc{a.grad + off};
+        layer_backward(layer_at(wsm, layer, D), xin, vbar, c, acc);
+    }
+}
+
 }  // namespace
 
 struct fd_nsf {
     int dim = 0, n_layers = 0, device = 0;
     int64_t n_params = 0, max_layer = 0;
     float *d_params = nullptr;
+    double *d_wsum = nullptr;      // the loss's weight normaliser (fd_nsf_kl_grad)
 };
 
 namespace {
@@ -358,8 +339,10 @@ extern "C" fd_status fd_nsf_create(int32_t dim, int32_t n_layers, fd_nsf **out) 
     cudaError_t e = cudaGetDevice(&f->device);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_params, (size_t)f->n_params * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(f->d_params, 0, (size_t)f->n_params * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_wsum, sizeof(double));
     if (e != cudaSuccess) {
         if (f->d_params) cudaFree(f->d_params);
+        if (f->d_wsum) cudaFree(f->d_wsum);
         delete f;
         return fd::cuda_error(e, "creating a spline flow");
     }
@@ -370,6 +353,7 @@ extern "C" fd_status fd_nsf_create(int32_t dim, int32_t n_layers, fd_nsf **out) 
 extern "C" void fd_nsf_free(fd_nsf *f) {
     if (!f) return;
     if (f->d_params) cudaFree(f->d_params);
+    if (f->d_wsum) cudaFree(f->d_wsum);
     delete f;
 }
 
@@ -398,4 +382,35 @@ extern "C" fd_status fd_nsf_log_density(const fd_nsf *f, const float *x, int64_t
 extern "C" fd_status fd_nsf_sample(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n, float *x,
                                    float *logq, void *stream) {
     return nsf_launch(f, false, nullptr, 0, seed, iter, inst, n, x, n, logq, (cudaStream_t)stream);
+}
+
+extern "C" fd_status fd_nsf_kl_grad(const fd_nsf *f, const float *x, const float *w, int64_t n, float *grad,
+                                    double *loss, void *stream) {
+    FD_REQUIRE(f && x && w && grad && loss, "flow, x, w, grad and loss are required");
+    FD_REQUIRE(n > 0 && n <= (int64_t(1) << 36), "n must be in [1, 2^36]");
+    FD_REQUIRE(f->n_layers <= kGradMaxLayers, "the gradient pass supports at most 16 layers");
+    int dev = 0;
+    FD_CHECK_CUDA(cudaGetDevice(&dev));
+    FD_REQUIRE(dev == f->device, "flow belongs to another device");
+    const cudaStream_t st = (cudaStream_t)stream;
+    FD_CHECK_CUDA(cudaMemsetAsync(grad, 0, (size_t)f->n_params * sizeof(float), st));
+    FD_CHECK_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), st));
+    FD_CHECK_CUDA(cudaMemsetAsync(f->d_wsum, 0, sizeof(double), st));
+    nsf_wsum_kernel<<<256, 256, 0, st>>>(w, n, f->d_wsum);
+    FD_CHECK_CUDA(cudaGetLastError());
+    NsfGradArgs a;
+    a.params = f->d_params;
+    a.x = x;
+    a.w = w;
+    a.wsum = f->d_wsum;
+    a.grad = grad;
+    a.loss = loss;
+    a.n = n;
+    a.dim = f->dim;
+    a.n_layers = f->n_layers;
+    const size_t smem = (size_t)f->max_layer * sizeof(float);
+    FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    nsf_grad_kernel<<<(unsigned)((n + 127) / 128), 128, smem, st>>>(a);
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
 }
