@@ -226,14 +226,15 @@ def flow_vs_vegas(args, api, params, order, seed):
                              "draw; merit = 1 / (variance of the estimate x seconds of the call)"),
            "flow_train_note": "each integrand batch reused for 4 Adam steps; first 100 steps on VEGAS samples; "
                               "VEGAS adapted 12 iterations x 2^22 samples",
-           "spline_flow_sampling": spline_flow_sampling(api, Gs.dim)}
+           "spline_flow_sampling": spline_flow_sampling(api, Gs.dim),
+           "spline_flow_training": spline_flow_training(api, Gs.dim)}
 
     return eff
 
 
 def spline_flow_sampling(api, dim, layers=8, n=1 << 22, reps=3):
     """Samples/s of the spline flow's sampling and density pass (App. A), seeded
-    untrained parameters (its training is not built yet)."""
+    untrained parameters."""
     import torch
     g = api.SplineFlow(dim, layers)
     g.set_params(workloads.small_params(7, g.n_params))
@@ -248,6 +249,28 @@ def spline_flow_sampling(api, dim, layers=8, n=1 << 22, reps=3):
     ms = s.elapsed_time(e) / reps
     return {"samples_per_s": n / ms * 1e3, "dim": dim, "layers": layers, "samples": n, "ms": ms,
             "parameters": "seeded, untrained"}
+
+
+def spline_flow_training(api, dim, layers=8, n=1 << 16, reps=3):
+    """Samples/s of the spline flow's training gradient (fd_nsf_kl_grad: the
+    inverse pass and reverse mode through it) on n of the flow's own samples
+    with unit weights, seeded untrained parameters."""
+    import torch
+    g = api.SplineFlow(dim, layers)
+    g.set_params(workloads.small_params(7, g.n_params))
+    x, _ = g.sample(1, 0, 0, n)
+    w = torch.ones(n, dtype=torch.float32, device="cuda")
+    g.kl_grad(x, w)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        loss, _ = g.kl_grad(x, w)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / reps
+    return {"samples_per_s": n / ms * 1e3, "dim": dim, "layers": layers, "samples": n, "ms": ms,
+            "loss": float(loss.item()), "parameters": "seeded, untrained"}
 
 
 def run_ours(args, rank, world, dist):

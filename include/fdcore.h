@@ -334,7 +334,12 @@ typedef struct fd_nsf fd_nsf;
 fd_status fd_nsf_create(int32_t dim, int32_t n_layers, fd_nsf **out);   /* 2 <= dim <= 24; all parameters 0 */
 void fd_nsf_free(fd_nsf *f);
 int64_t fd_nsf_param_count(const fd_nsf *f);
-fd_status fd_nsf_set_params(fd_nsf *f, const float *params, int64_t n);  /* synchronous; FD_EINVAL if non-finite */
+/* Synchronous; FD_EINVAL if any is non-finite.  Also resets the training
+ * state (Adam moments and step count, fd_nsf_train). */
+fd_status fd_nsf_set_params(fd_nsf *f, const float *params, int64_t n);
+/* The current parameters into host params [n == fd_nsf_param_count];
+ * synchronous (waits for the device). */
+fd_status fd_nsf_get_params(const fd_nsf *f, float *params, int64_t n);
 /* x = T(z) for device z [dim][n]: x (device FP32 [dim][n]) and log q(x)
  * (device FP32 [n]); 1 <= n <= 2^36 (FD_EINVAL otherwise).  Asynchronous on
  * stream. */
@@ -361,6 +366,14 @@ fd_status fd_nsf_log_density(const fd_nsf *f, const float *x, int64_t n, float *
  * the flow's weight-sum scratch word). */
 fd_status fd_nsf_kl_grad(const fd_nsf *f, const float *x, const float *w, int64_t n, float *grad, double *loss,
                          void *stream);
+/* Training on one batch (App. A): `steps` Adam steps (Kingma and Ba: beta =
+ * (0.9, 0.999), eps = 1e-8, bias-corrected; the moments live in the flow and
+ * persist across calls), each on the gradient of fd_nsf_kl_grad over (x, w)
+ * at the current parameters.  loss_out: host FP64 [steps], the loss before
+ * each step, or NULL; with it the call waits for the stream.
+ * 1 <= steps <= 4096, lr > 0 (FD_EINVAL otherwise). */
+fd_status fd_nsf_train(fd_nsf *f, const float *x, const float *w, int64_t n, int32_t steps, float lr,
+                       double *loss_out, void *stream);
 
 /* ---- NF-MCMC / VEGAS-MCMC chains (Sec. V, Eqs. target_distr and
  * nf_mcmc_estimator) --------------------------------------------------------

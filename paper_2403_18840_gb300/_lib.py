@@ -95,6 +95,8 @@ SIGNATURES = {
     "fd_nsf_sample": (_i32, [_vp, _u64, _u64, _i32, _i64, _vp, _vp, _vp]),
     "fd_nsf_log_density": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "fd_nsf_kl_grad": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "fd_nsf_train": (_i32, [_vp, _vp, _vp, _i64, _i32, _f32, _vp, _vp]),
+    "fd_nsf_get_params": (_i32, [_vp, _pf, _i64]),
     "fd_mcmc_estimate": (_i32, [_vp, _i32, _i64, _i32, _vp, _vp]),
     "fd_postprocess": (_i32, [_i32, _pd, _pd, _pd, _f64, _f64, _f64, _pd, _pd, _pd, _pd]),
 }

@@ -300,6 +300,12 @@ class SplineFlow:
         assert b.size == self.n_params
         L.check(L.lib().fd_nsf_set_params(self.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), b.size))
 
+    def params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        L.check(L.lib().fd_nsf_get_params(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          out.size))
+        return out
+
     def forward(self, z, stream=None):
         n = z.shape[1]
         x = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")
@@ -335,6 +341,15 @@ class SplineFlow:
         L.check(L.lib().fd_nsf_kl_grad(self.handle, _ptr(x), _ptr(w), n, _ptr(grad), _ptr(loss),
                                        _stream_ptr(stream)))
         return loss, grad
+
+    def train(self, x, w, steps, lr, stream=None):
+        """`steps` Adam steps on the batch (x, w); returns the loss before each step."""
+        assert x.dtype == torch.float32 and x.is_contiguous() and x.shape[0] == self.dim
+        assert w.dtype == torch.float32 and w.is_contiguous() and w.shape == (x.shape[1],)
+        out = np.empty(steps, dtype=np.float64)
+        L.check(L.lib().fd_nsf_train(self.handle, _ptr(x), _ptr(w), x.shape[1], steps, lr,
+                                     out.ctypes.data, _stream_ptr(stream)))
+        return out
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(128) nsf_kernel(const NsfArgs a) {
 // warp's samples by shuffles and added to global memory by lane 0.
 
 constexpr int kGradMaxLayers = 16;
+constexpr int kNsfMaxTrainSteps = 4096;      // losses kept per fd_nsf_train call
 
 struct WarpAtomicAcc {
     float *g;                                 // the layer's slice of the gradient
@@ -279,6 +280,10 @@ struct fd_nsf {
     int64_t n_params = 0, max_layer = 0;
     float *d_params = nullptr;
     double *d_wsum = nullptr;      // the loss's weight normaliser (fd_nsf_kl_grad)
+    // training state (fd_nsf_train): gradient, Adam moments, loss of each step
+    float *d_grad = nullptr, *d_m = nullptr, *d_v = nullptr;
+    double *d_loss = nullptr;
+    int64_t step = 0;
 };
 
 namespace {
@@ -340,9 +345,16 @@ extern "C" fd_status fd_nsf_create(int32_t dim, int32_t n_layers, fd_nsf **out) 
     if (e == cudaSuccess) e = cudaMalloc(&f->d_params, (size_t)f->n_params * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(f->d_params, 0, (size_t)f->n_params * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->d_wsum, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_grad, (size_t)f->n_params * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_m, (size_t)f->n_params * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_v, (size_t)f->n_params * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(f->d_m, 0, (size_t)f->n_params * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(f->d_v, 0, (size_t)f->n_params * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_loss, kNsfMaxTrainSteps * sizeof(double));
     if (e != cudaSuccess) {
-        if (f->d_params) cudaFree(f->d_params);
-        if (f->d_wsum) cudaFree(f->d_wsum);
+        for (void *q : {(void *)f->d_params, (void *)f->d_wsum, (void *)f->d_grad, (void *)f->d_m, (void *)f->d_v,
+                        (void *)f->d_loss})
+            if (q) cudaFree(q);
         delete f;
         return fd::cuda_error(e, "creating a spline flow");
     }
@@ -352,8 +364,9 @@ extern "C" fd_status fd_nsf_create(int32_t dim, int32_t n_layers, fd_nsf **out) 
 
 extern "C" void fd_nsf_free(fd_nsf *f) {
     if (!f) return;
-    if (f->d_params) cudaFree(f->d_params);
-    if (f->d_wsum) cudaFree(f->d_wsum);
+    for (void *q : {(void *)f->d_params, (void *)f->d_wsum, (void *)f->d_grad, (void *)f->d_m, (void *)f->d_v,
+                    (void *)f->d_loss})
+        if (q) cudaFree(q);
     delete f;
 }
 
@@ -364,6 +377,9 @@ extern "C" fd_status fd_nsf_set_params(fd_nsf *f, const float *params, int64_t n
     FD_REQUIRE(n == f->n_params, "parameter count differs from fd_nsf_param_count");
     for (int64_t k = 0; k < n; ++k) FD_REQUIRE(std::isfinite(params[k]), "non-finite parameter");
     FD_CHECK_CUDA(cudaMemcpy(f->d_params, params, (size_t)n * sizeof(float), cudaMemcpyHostToDevice));
+    FD_CHECK_CUDA(cudaMemset(f->d_m, 0, (size_t)n * sizeof(float)));     // a fresh Adam state
+    FD_CHECK_CUDA(cudaMemset(f->d_v, 0, (size_t)n * sizeof(float)));
+    f->step = 0;
     return FD_OK;
 }
 
@@ -384,15 +400,15 @@ extern "C" fd_status fd_nsf_sample(const fd_nsf *f, uint64_t seed, uint64_t iter
     return nsf_launch(f, false, nullptr, 0, seed, iter, inst, n, x, n, logq, (cudaStream_t)stream);
 }
 
-extern "C" fd_status fd_nsf_kl_grad(const fd_nsf *f, const float *x, const float *w, int64_t n, float *grad,
-                                    double *loss, void *stream) {
+namespace {
+fd_status kl_grad_impl(const fd_nsf *f, const float *x, const float *w, int64_t n, float *grad, double *loss,
+                       cudaStream_t st) {
     FD_REQUIRE(f && x && w && grad && loss, "flow, x, w, grad and loss are required");
     FD_REQUIRE(n > 0 && n <= (int64_t(1) << 36), "n must be in [1, 2^36]");
     FD_REQUIRE(f->n_layers <= kGradMaxLayers, "the gradient pass supports at most 16 layers");
     int dev = 0;
     FD_CHECK_CUDA(cudaGetDevice(&dev));
     FD_REQUIRE(dev == f->device, "flow belongs to another device");
-    const cudaStream_t st = (cudaStream_t)stream;
     FD_CHECK_CUDA(cudaMemsetAsync(grad, 0, (size_t)f->n_params * sizeof(float), st));
     FD_CHECK_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), st));
     FD_CHECK_CUDA(cudaMemsetAsync(f->d_wsum, 0, sizeof(double), st));
@@ -412,5 +428,53 @@ extern "C" fd_status fd_nsf_kl_grad(const fd_nsf *f, const float *x, const float
     FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     nsf_grad_kernel<<<(unsigned)((n + 127) / 128), 128, smem, st>>>(a);
     FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
+}
+
+// Adam (Kingma and Ba, 2015) with bias correction; b1t = b1^step, b2t = b2^step
+__global__ void nsf_adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                                float *__restrict__ v, int64_t n, float lr, float b1, float b2, float b1t, float b2t,
+                                float eps) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float gk = g[k];
+    const float mk = b1 * m[k] + (1.0f - b1) * gk, vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    p[k] -= lr * (mk / (1.0f - b1t)) / (sqrtf(vk / (1.0f - b2t)) + eps);
+}
+}  // namespace
+
+extern "C" fd_status fd_nsf_kl_grad(const fd_nsf *f, const float *x, const float *w, int64_t n, float *grad,
+                                    double *loss, void *stream) {
+    return kl_grad_impl(f, x, w, n, grad, loss, (cudaStream_t)stream);
+}
+
+extern "C" fd_status fd_nsf_train(fd_nsf *f, const float *x, const float *w, int64_t n, int32_t steps, float lr,
+                                  double *loss_out, void *stream) {
+    FD_REQUIRE(f && x && w, "flow, x and w are required");
+    FD_REQUIRE(steps >= 1 && steps <= kNsfMaxTrainSteps, "steps must be in [1, 4096]");
+    FD_REQUIRE(lr > 0.0f && std::isfinite(lr), "a positive learning rate is required");
+    const cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < steps; ++k) {
+        const fd_status s = kl_grad_impl(f, x, w, n, f->d_grad, f->d_loss + k, st);
+        if (s != FD_OK) return s;
+        f->step += 1;
+        const float b1t = (float)std::pow(0.9, (double)f->step), b2t = (float)std::pow(0.999, (double)f->step);
+        nsf_adam_kernel<<<(unsigned)((f->n_params + 255) / 256), 256, 0, st>>>(
+            f->d_params, f->d_grad, f->d_m, f->d_v, f->n_params, lr, 0.9f, 0.999f, b1t, b2t, 1e-8f);
+        FD_CHECK_CUDA(cudaGetLastError());
+    }
+    if (loss_out) {
+        FD_CHECK_CUDA(cudaMemcpyAsync(loss_out, f->d_loss, steps * sizeof(double), cudaMemcpyDeviceToHost, st));
+        FD_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_nsf_get_params(const fd_nsf *f, float *params, int64_t n) {
+    FD_REQUIRE(f && params && n == f->n_params, "params must hold fd_nsf_param_count floats");
+    FD_CHECK_CUDA(cudaDeviceSynchronize());
+    FD_CHECK_CUDA(cudaMemcpy(params, f->d_params, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
     return FD_OK;
 }

@@ -157,3 +157,41 @@ def test_kl_grad_rejects_deep_flows(api):
     w = torch.ones(4, device="cuda")
     with pytest.raises(api.L.FdError):
         g.kl_grad(x, w)
+
+
+def test_training_first_adam_step_and_descent(api):
+    # from zero moments the first bias-corrected Adam step moves every
+    # parameter by lr g / (|g| + eps), i.e. -lr sign(g) wherever |g| >> eps;
+    # the sign is taken from the oracle's gradient where it is unambiguous
+    # (|g| above 1e-3 of the largest, far above the GPU/oracle difference),
+    # elsewhere only |step| <= lr is required
+    dim, n_layers, n, lr = 5, 4, 1000, 1e-3
+    flow = _as_fp32(osf.SplineFlow(dim, n_layers, seed=51, scale=0.8))
+    theta = _flatten(flow)
+    g = api.SplineFlow(dim, n_layers)
+    g.set_params(theta)
+    z = workloads.uniform_points(52, dim, n)
+    x_ref, _ = flow.forward(z.T)
+    x32 = x_ref.astype(np.float32)
+    w32 = np.exp(-6.0 * ((x32.astype(np.float64) - 0.3) ** 2).sum(axis=1)).astype(np.float32)
+    x = torch.tensor(x32.T, device="cuda").contiguous()
+    w = torch.tensor(w32, device="cuda")
+    losses = g.train(x, w, 1, lr)
+    gr = flow.kl_grad(x32.astype(np.float64), w32.astype(np.float64), analytic=True)
+    lr_ref = flow.kl_loss(x32.astype(np.float64), w32.astype(np.float64))
+    assert abs(losses[0] - lr_ref) < 1e-5 * (1.0 + abs(lr_ref))
+    d = g.params().astype(np.float64) - theta.astype(np.float64)
+    ulp = 2.0 ** -23 * (1.0 + np.abs(theta.astype(np.float64)))   # rounding of the FP32 update
+    big = np.abs(gr) > 1e-3 * np.abs(gr).max()
+    assert big.sum() > 0.3 * gr.size
+    assert np.all(np.abs(d[big] + lr * np.sign(gr[big])) <= 1e-3 * lr + ulp[big])
+    assert np.all(np.abs(d) <= lr * (1.0 + 1e-3) + ulp)
+    more = g.train(x, w, 40, lr)
+    print("spline flow training: loss %.6f -> %.6f after 41 Adam steps" % (losses[0], more[-1]))
+    # the oracle's own Adam on its FP64 gradient goes -0.776 -> -1.885 here
+    # (the first sign-sized step overshoots: -0.718)
+    assert more[-1] < losses[0] - 0.5
+    g.set_params(theta)                                  # a fresh Adam state: the same first step
+    assert abs(g.train(x, w, 1, lr)[0] - losses[0]) < 1e-6 * (1.0 + abs(losses[0]))
+    d2 = g.params().astype(np.float64) - theta.astype(np.float64)
+    assert np.all(np.abs(d2[big] - d[big]) <= 1e-3 * lr + 2 * ulp[big])
