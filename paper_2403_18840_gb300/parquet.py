@@ -43,9 +43,11 @@ The equations, in these terms (each diagram must come out exactly once):
   R.out2), with weight 1/2 (each diagram arises from both assignments of
   the two parallel lines to L's out-legs).  Choosing R irreducible makes the
   join unique (the cut nearest R's external legs).
-* I^(N), the fully irreducible vertex: the bare vertex at order 0, none at
-  orders 1 and 2, and at order 3 the envelope diagrams, found here by
-  brute force over all order-3 vertices (the irreducible remainder).
+* I^(N), the fully irreducible vertex: the bare vertex at order 0; above it,
+  the order-N vertices that no channel's reducible part contains, found by
+  enumerating all order-N vertices (none at orders 1 and 2, the 64 envelope
+  diagrams at order 3).  The paper builds I bottom-up as well (Fig.
+  envelope_diag) but only sketches the rule, so the remainder stands in.
 
 Multiplicities are carried as exact fractions; every generated diagram must
 end with weight 1, which the tests check against the enumerator.
@@ -214,6 +216,97 @@ def brute_gamma4(n_lines):
     return out
 
 
+def enumerate_gamma4(n_lines):
+    """The same set as brute_gamma4, built by following fermion lines: from
+    in-leg 1's vertex, each step sends the current vertex's line to an out-leg,
+    to a vertex already named (the free end of an introduced interaction
+    line) or to the first end of a new interaction line; a finished path or
+    loop continues at in-leg 2's vertex (any named or new vertex) and then at
+    the smallest named vertex not yet passed.  Duplicates are removed by the
+    canonical key."""
+    nv = 2 * n_lines
+    succ = [None] * nv
+    pred = [None] * nv
+    partner = tuple(v ^ 1 for v in range(nv))
+    out = {}
+
+    def finish():
+        piece = (tuple(succ), tuple(pred), partner)
+        key = canonical(piece)
+        if key is not None and key not in out:
+            p = from_key(key)
+            if amputated(p) and tadpole_free(p):
+                out[key] = p
+
+    def named_free(nl):
+        return [w for w in range(2 * nl) if pred[w] is None]
+
+    def next_start(nl, outs_used, in2_done):
+        """Continue after a path or loop ends."""
+        if not in2_done:
+            cands = named_free(nl) + ([2 * nl] if nl < n_lines else [])
+            for w in cands:
+                nl2 = nl + 1 if w == 2 * nl else nl
+                pred[w] = -2
+                walk(w, nl2, outs_used, True, None)
+                pred[w] = None
+            return
+        free = [w for w in range(2 * nl) if pred[w] is None]
+        if not free:
+            if nl == n_lines and len(outs_used) == 2:
+                finish()
+            return
+        st = free[0]
+        walk(st, nl, outs_used, True, st)
+
+    def walk(v, nl, outs_used, in2_done, loop_start):
+        # v has its pred set (or is a loop start); choose succ[v]
+        choices = []
+        if loop_start is None:
+            choices += [-(j + 1) for j in (0, 1) if (j not in outs_used)]
+        for w in range(2 * nl):
+            if pred[w] is None and w != loop_start:
+                choices.append(w)
+        if loop_start is not None:
+            choices.append(loop_start)
+        if nl < n_lines:
+            choices.append(2 * nl)
+        for w in choices:
+            if w < 0:
+                succ[v] = w
+                next_start(nl, outs_used | {-w - 1}, in2_done)
+                succ[v] = None
+                continue
+            nl2 = nl + 1 if (nl < n_lines and w == 2 * nl) else nl
+            succ[v] = w
+            if w == loop_start:
+                pred[w] = v
+                next_start(nl2, outs_used, in2_done)
+                pred[w] = None
+            else:
+                pred[w] = v
+                walk(w, nl2, outs_used, in2_done, loop_start)
+                pred[w] = None
+            succ[v] = None
+
+    pred[0] = -1
+    walk(0, 1, frozenset(), False, None)
+    return out
+
+
+def irreducible_remainder(N, reducible_parts):
+    """I^(N): the order-N vertices (N + 1 interaction lines, enumerated) that
+    no channel's reducible part contains.  The reducible parts must cover each
+    of their diagrams exactly once and only enumerated diagrams."""
+    full = enumerate_gamma4(N + 1)
+    red = collections.defaultdict(Fraction)
+    for part in reducible_parts:
+        for k, w in part.items():
+            red[k] += w
+    assert all(w == 1 for w in red.values()) and set(red) <= set(full)
+    return {k: Fraction(1) for k in full if k not in red}
+
+
 # ---- joining pieces ------------------------------------------------------------
 
 class _Builder:
@@ -293,8 +386,9 @@ class Construction:
     each a {canonical key: weight} multiset."""
 
     def __init__(self, irreducible=None):
-        # fully irreducible vertex by order (order 0 is the bare vertex)
-        self._irr = irreducible or {}
+        # fully irreducible vertex by order (order 0 is the bare vertex);
+        # orders not given are found as the irreducible remainder
+        self._irr = dict(irreducible or {})
 
     # Sigma^(N)
     @functools.lru_cache(maxsize=None)
@@ -367,7 +461,9 @@ class Construction:
             direct = ((-1, -2), (-1, -2), (1, 0))
             exchange = ((-2, -1), (-1, -2), (1, 0))
             return {canonical(direct): Fraction(1), canonical(exchange): Fraction(1)}
-        return dict(self._irr.get(N, {}))
+        if N in self._irr:
+            return dict(self._irr[N])
+        return irreducible_remainder(N, [self.phi(c, N) for c in ("ph", "phbar", "pp")])
 
     @functools.lru_cache(maxsize=None)
     def gamma4_irreducible_in(self, join, N):
