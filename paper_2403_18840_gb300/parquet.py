@@ -381,6 +381,18 @@ def _add_to(acc, piece, w):
 
 # ---- the equations ---------------------------------------------------------------
 
+def _memo(method):
+    """Memoise a method on its instance (the cache dies with the instance)."""
+    @functools.wraps(method)
+    def wrapper(self, *args):
+        cache = self.__dict__.setdefault("_cache", {})
+        key = (method.__name__,) + args
+        if key not in cache:
+            cache[key] = method(self, *args)
+        return cache[key]
+    return wrapper
+
+
 class Construction:
     """Pieces of every kind and order, built from lower orders and memoised:
     each a {canonical key: weight} multiset."""
@@ -391,7 +403,7 @@ class Construction:
         self._irr = dict(irreducible or {})
 
     # Sigma^(N)
-    @functools.lru_cache(maxsize=None)
+    @_memo
     def sigma(self, N):
         acc = collections.defaultdict(Fraction)
         for i in range(N):
@@ -409,7 +421,7 @@ class Construction:
         return dict(acc)
 
     # G^(k): chains of self-energy insertions of total order k
-    @functools.lru_cache(maxsize=None)
+    @_memo
     def chains(self, k):
         if k == 0:
             return ((), Fraction(1)),
@@ -421,7 +433,7 @@ class Construction:
         return tuple(out)
 
     # Gamma3^(N)
-    @functools.lru_cache(maxsize=None)
+    @_memo
     def gamma3(self, N):
         if N == 0:
             return {canonical(((-1,), (-1,), (-1,))): Fraction(1)}
@@ -445,7 +457,7 @@ class Construction:
         return dict(acc)
 
     # Gamma4^(N) and its channel parts
-    @functools.lru_cache(maxsize=None)
+    @_memo
     def gamma4(self, N):
         acc = collections.defaultdict(Fraction)
         for k, w in self.irreducible(N).items():
@@ -455,7 +467,7 @@ class Construction:
                 acc[k] += w
         return {k: w for k, w in acc.items() if w != 0}
 
-    @functools.lru_cache(maxsize=None)
+    @_memo
     def irreducible(self, N):
         if N == 0:
             direct = ((-1, -2), (-1, -2), (1, 0))
@@ -465,7 +477,7 @@ class Construction:
             return dict(self._irr[N])
         return irreducible_remainder(N, [self.phi(c, N) for c in ("ph", "phbar", "pp")])
 
-    @functools.lru_cache(maxsize=None)
+    @_memo
     def gamma4_irreducible_in(self, join, N):
         """Gamma4 minus its part reducible in the channel of the join (ph for
         the ph and phbar joins, pp for the pp join), in the piece's own legs."""
@@ -474,7 +486,7 @@ class Construction:
             acc[k] -= w
         return {k: w for k, w in acc.items() if w != 0}
 
-    @functools.lru_cache(maxsize=None)
+    @_memo
     def phi(self, c, N):
         acc = collections.defaultdict(Fraction)
         if N == 0:
