@@ -1,0 +1,98 @@
+"""Host analysis of the effective-mass series (App. B): error propagation
+through the post-process (closed form at order 1, Monte Carlo resampling at
+order 3), the three-order truncation estimate, the screening-parameter
+choice, and the weighted linear-T extrapolation (exact lines, the textbook
+least-squares errors, and coverage on seeded noisy data)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2403_18840_gb300 import analysis as A
+from paper_2403_18840_gb300 import api
+
+
+def test_order_one_errors_closed_form():
+    kF, beta, Lam = 1.9, 6.8, 0.9
+    s = {(1, 0, 0): complex(-0.63, 0.11)}
+    ds = {(1, 0, 0): complex(0.377, 0.0)}
+    se = {(1, 0, 0): complex(0.01, 0.004)}
+    dse = {(1, 0, 0): 0.02}
+    m, dm = A.meff_with_errors(1, s, se, ds, dse, kF, beta, Lam)
+    w0 = math.pi / beta
+    assert math.isclose(m[1], 1 - 0.377 / (2 * kF) - 0.11 / w0, rel_tol=1e-12)
+    want = math.hypot(0.02 / (2 * kF), 0.004 / w0)
+    assert math.isclose(dm[1], want, rel_tol=1e-6)
+    assert dm[0] == 0.0
+
+
+def _toy_inputs(N, seed):
+    rng = np.random.default_rng(seed)
+    sig, dsig, se, dse = {}, {}, {}, {}
+    for n in range(1, N + 1):
+        for m in range(N - n + 1):
+            for l in range(N - n - m + 1):
+                sig[(n, m, l)] = complex(rng.normal(0, 0.5), rng.normal(0, 0.1))
+                dsig[(n, m, l)] = complex(rng.normal(0, 0.3), 0.0)
+                se[(n, m, l)] = complex(0.01 * abs(sig[(n, m, l)].real) + 1e-3, 0.01 * abs(sig[(n, m, l)].imag) + 1e-3)
+                dse[(n, m, l)] = 0.01 * abs(dsig[(n, m, l)].real) + 1e-3
+    return sig, dsig, se, dse
+
+
+def test_error_propagation_matches_resampling():
+    N, kF, beta, Lam = 3, 1.3, 5.0, 0.7
+    sig, dsig, se, dse = _toy_inputs(N, 3)
+    m, dm = A.meff_with_errors(N, sig, se, dsig, dse, kF, beta, Lam)
+    rng = np.random.default_rng(4)
+    draws = []
+    for _ in range(3000):
+        s = {k: complex(v.real + rng.normal() * se[k].real, v.imag + rng.normal() * se[k].imag) for k, v in sig.items()}
+        d = {k: complex(v.real + rng.normal() * dse[k], 0.0) for k, v in dsig.items()}
+        draws.append(api.postprocess(N, s, d, kF, beta, Lam)["meff"])
+    sd = np.std(np.array(draws), axis=0)
+    # 3000 draws: the sample standard deviation is within ~4 % (3 sigma ~ 4 %)
+    assert np.allclose(dm[1:], sd[1:], rtol=0.08)
+
+
+def test_truncation_estimate():
+    est, sys = A.truncation_estimate([1.0, 0.9, 0.95, 0.97, 0.975, 0.979])
+    assert est == 0.979 and math.isclose(sys, 0.009)
+    with pytest.raises(ValueError):
+        A.truncation_estimate([1.0, 0.9])
+
+
+def test_choose_screening_prefers_fast_convergence():
+    # partial sums converging to 0.98 with ratios r(Lambda): fastest at 1.5
+    scan = {}
+    for L, r in ((1.0, 0.6), (1.25, 0.4), (1.5, 0.1), (1.75, 0.3), (2.0, 0.5)):
+        scan[L] = [0.98 + 0.1 * r ** k for k in range(7)]
+    L, est, sys = A.choose_screening(scan)
+    assert L == 1.5
+    assert math.isclose(est, 0.98 + 0.1 * 0.1 ** 6)
+    # the neighbours' three-order variation (ratio 0.4 at 1.25) sets the uncertainty
+    assert math.isclose(sys, 0.1 * (0.4 ** 4 - 0.4 ** 6))
+
+
+def test_extrapolation_exact_line_and_textbook_errors():
+    t = np.array([1 / 40, 1 / 30, 1 / 20, 1 / 10])
+    y = 0.98 * (1 + 0.3 * t)
+    r = A.extrapolate_linear_T(t, y, np.full(4, 1e-3))
+    assert math.isclose(r["y0"], 0.98, rel_tol=1e-12) and math.isclose(r["alpha"], 0.3, rel_tol=1e-10)
+    assert r["chi2_dof"] < 1e-20
+    # equal weights: var(intercept) = s^2 sum t^2 / (n sum t^2 - (sum t)^2)
+    n = t.size
+    want = 1e-3 * math.sqrt((t * t).sum() / (n * (t * t).sum() - t.sum() ** 2))
+    assert math.isclose(r["dy0"], want, rel_tol=1e-12)
+
+
+def test_extrapolation_coverage_on_noisy_data():
+    rng = np.random.default_rng(9)
+    t = np.linspace(0.02, 0.1, 6)
+    dy = np.full(t.size, 2e-3)
+    pulls = []
+    for _ in range(400):
+        y = 0.95 * (1 - 0.5 * t) + rng.normal(0, 2e-3, t.size)
+        r = A.extrapolate_linear_T(t, y, dy)
+        pulls.append((r["y0"] - 0.95) / r["dy0"])
+    pulls = np.array(pulls)
+    assert abs(pulls.mean()) < 0.2 and 0.85 < pulls.std() < 1.15
