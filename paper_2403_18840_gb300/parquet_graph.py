@@ -1,0 +1,355 @@
+"""Evaluation graph of the Dyson-Schwinger / parquet construction and its
+operation count (Sec. II.B-C, Figs. parquet_graph and parquet_benchmark).
+
+The construction of `parquet.py` is evaluated per sample as a graph of
+shared nodes.  Each node is a group of sub-diagrams with the same order,
+kind, external momenta and internal variables: its own loop momenta and
+interaction-line times.  Each join takes a new loop momentum and hands
+contiguous blocks of variables to its parts, in a fixed order: the join's
+own loop first, then the left part, the right part and the two dressed
+lines.  A node is a tensor over the times of the lines its external legs
+sit on, because the bare lines that join it to other nodes depend on those
+times.  Joins contract these indices.
+
+The recursion runs over an algebra:
+
+* `Scalar`: values are numbers, nodes are memoised, and every multiply and
+  add in a node's evaluation is counted once.  This is the compact graph's
+  N_op (leaves excluded, as in `fdgraph.contraction_ops`).
+* `Expanded`: values are lists of weighted monomials over leaves
+  ('G', momentum, from vertex, to vertex) and ('V', momentum, vertex,
+  vertex).  The expansion is the plain sum over diagrams, each with the
+  momentum routing the construction gives it.
+
+Momenta are integer coefficient tuples over (k_ext, p_1, ..., p_n).  Each
+interaction line l has time variable l; its two ends are vertices 2l and
+2l + 1.
+"""
+import collections
+from fractions import Fraction
+
+from . import parquet as P
+
+
+def _vec(n, i=None):
+    v = [0] * (n + 1)
+    if i is not None:
+        v[i] = 1
+    return tuple(v)
+
+
+def _add(a, b):
+    return tuple(x + y for x, y in zip(a, b))
+
+
+def _sub(a, b):
+    return tuple(x - y for x, y in zip(a, b))
+
+
+class Scalar:
+    """Numbers; multiplies and adds counted in `ops`."""
+
+    def __init__(self, g0, v):
+        self.g0, self.v = g0, v          # leaf functions: g0(mom, from_line, to_line), v(mom)
+        self.ops = 0
+
+    def index(self, vertex):
+        return vertex // 2                # a node's tensor index: the line (its time)
+
+    def leaf_g(self, mom, x, y):
+        return self.g0(mom, x, y)
+
+    def leaf_v(self, mom, a, b):
+        return self.v(mom)
+
+    def mul(self, *xs):
+        r = xs[0]
+        for x in xs[1:]:
+            r = r * x
+        self.ops += len(xs) - 1
+        return r
+
+    def scale(self, w, x):
+        if w == 1:
+            return x
+        self.ops += 1
+        return float(w) * x
+
+    def acc(self, d, key, x):
+        if key in d:
+            d[key] = d[key] + x
+            self.ops += 1
+        else:
+            d[key] = x
+
+
+class Expanded:
+    """Weighted monomials over vertex-level leaves."""
+
+    def index(self, vertex):
+        return vertex
+
+    def leaf_g(self, mom, x, y):
+        return [(Fraction(1), (("G", mom, x, y),))]
+
+    def leaf_v(self, mom, a, b):
+        return [(Fraction(1), (("V", mom, a, b),))]
+
+    def mul(self, *xs):
+        out = [(Fraction(1), ())]
+        for x in xs:
+            out = [(w1 * w2, m1 + m2) for (w1, m1) in out for (w2, m2) in x]
+        return out
+
+    def scale(self, w, x):
+        return [(w * c, m) for (c, m) in x]
+
+    def acc(self, d, key, x):
+        d.setdefault(key, []).extend(x)
+
+
+def route_piece(piece, leg_moms, n_var, ms, line_of):
+    """Momentum routing of one diagram piece: leg momenta given
+    ({('in'|'out', j): mom}), chords of a spanning tree carry the loop
+    variables ms, ms+1, ..., tree lines follow from conservation.  Returns
+    the leaves [('G', mom, x, y) / ('V', mom, a, b)] with vertices mapped by
+    line_of (piece vertex -> global vertex)."""
+    succ, pred, partner = piece
+    nv = len(succ)
+    edges = [("G", v, succ[v]) for v in range(nv) if succ[v] >= 0]
+    edges += [("V", v, partner[v]) for v in range(nv) if 0 <= v < partner[v]]
+    parent = list(range(nv))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+    tree, chords = [], []
+    for e in edges:
+        ra, rb = find(e[1]), find(e[2])
+        if ra != rb:
+            parent[ra] = rb
+            tree.append(e)
+        else:
+            chords.append(e)
+    mom = {}
+    for k, e in enumerate(chords):
+        mom[e] = _vec(n_var, ms + k)
+    # net momentum entering each vertex from legs and known lines
+    need = [_vec(n_var) for _ in range(nv)]
+    legs = P._leg_vertices(piece)
+    for (kind, j), v in legs.items():
+        m = leg_moms[(kind, j)]
+        need[v] = _add(need[v], m) if kind == "in" else _sub(need[v], m)
+    for e, m in mom.items():
+        need[e[1]] = _sub(need[e[1]], m)
+        need[e[2]] = _add(need[e[2]], m)
+    rest = list(tree)
+    while rest:
+        deg = collections.Counter()
+        for e in rest:
+            deg[e[1]] += 1
+            deg[e[2]] += 1
+        for e in rest:
+            a, b = e[1], e[2]
+            if deg[a] == 1:           # a's balance fixes e (leaving a)
+                m = need[a]
+                mom[e] = m
+                need[a] = _sub(need[a], m)
+                need[b] = _add(need[b], m)
+                rest.remove(e)
+                break
+            if deg[b] == 1:           # b's balance fixes e (entering b)
+                m = _vec(n_var)
+                m = _sub(m, need[b])
+                mom[e] = m
+                need[b] = _add(need[b], m)
+                need[a] = _sub(need[a], m)
+                rest.remove(e)
+                break
+    leaves = []
+    for e, m in mom.items():
+        leaves.append((e[0], m, line_of(e[1]), line_of(e[2])))
+    return leaves
+
+
+class Evaluator:
+    """The construction as a recursion over an algebra (Scalar or Expanded),
+    memoised on (node, arguments)."""
+
+    def __init__(self, order, alg, construction=None):
+        self.n = order
+        self.alg = alg
+        self.C = construction or P.Construction()
+        self.memo = {}
+
+    def _m(self, key, fn):
+        if key not in self.memo:
+            self.memo[key] = fn()
+        return self.memo[key]
+
+    # a dressed line from vertex x to vertex y, momentum K, k orders of insertions
+    # x, y, and every tensor key below, are vertex indices of the algebra
+    # (lines for Scalar, vertices for Expanded)
+    def chain(self, k, K, x, y, ms, ts):
+        return self._m(("chain", k, K, x, y, ms, ts), lambda: self._chain(k, K, x, y, ms, ts))
+
+    def _chain(self, k, K, x, y, ms, ts):
+        A = self.alg
+        if k == 0:
+            return A.leaf_g(K, x, y)
+        total = None
+        for p in range(1, k + 1):
+            a = A.index(2 * ts)
+            for o, s in self.sigma(p, K, ms, ts).items():
+                term = A.mul(A.leaf_g(K, x, a), s, self.chain(k - p, K, o, y, ms + p, ts + p))
+                total = term if total is None else self._plus(total, term)
+        return total
+
+    def _plus(self, a, b):
+        d = {}
+        self.alg.acc(d, 0, a)
+        self.alg.acc(d, 0, b)
+        return d[0]
+
+    # Sigma^(N)(K) over its out-vertex; in-vertex 2 ts, loop q = ms
+    def sigma(self, N, K, ms, ts):
+        return self._m(("sigma", N, K, ms, ts), lambda: self._sigma(N, K, ms, ts))
+
+    def _sigma(self, N, K, ms, ts):
+        A = self.alg
+        q = _vec(self.n, ms)
+        a, b = A.index(2 * ts), A.index(2 * ts + 1)
+        out = {}
+        for i in range(N):
+            g3 = self.gamma3(i, _sub(K, q), K, ms + 1, ts + 1, b)
+            for (x, o), val in g3.items():
+                ch = self.chain(N - i - 1, _sub(K, q), a, x, ms + 1 + i, ts + 1 + i)
+                A.acc(out, o, A.mul(A.leaf_v(q, a, b), ch, val))
+        return out
+
+    # Gamma3 over (in-vertex, out-vertex); b its interaction end (outside)
+    def gamma3(self, N, Kin, Kout, ms, ts, b):
+        return self._m(("g3", N, Kin, Kout, ms, ts, b), lambda: self._gamma3(N, Kin, Kout, ms, ts, b))
+
+    def _gamma3(self, N, Kin, Kout, ms, ts, b):
+        A = self.alg
+        if N == 0:
+            return {(b, b): self._one()}             # the bare vertex: b itself
+        # b takes in the boson momentum Kout - Kin; Gamma4 legs (in1, out1, in2, out2)
+        p = _vec(self.n, ms)
+        out = {}
+        for i in range(N):
+            M = N - i - 1
+            legs = (Kin, Kout, _add(p, _sub(Kout, Kin)), p)
+            g4 = self.gamma4(i, legs, ms + 1, ts, None)
+            for j in range(M + 1):
+                m1, t1 = ms + 1 + i, ts + i + 1
+                for (x, o, u, w), val in g4.items():
+                    c1 = self.chain(j, legs[2], b, u, m1, t1)
+                    c2 = self.chain(M - j, p, w, b, m1 + j, t1 + j)
+                    A.acc(out, (x, o), A.mul(val, c1, c2))
+        return out
+
+    def _one(self):
+        return 1.0 if isinstance(self.alg, Scalar) else [(Fraction(1), ())]
+
+    # Gamma4 over (in1, out1, in2, out2) vertices; irr: None, 'ph' or 'pp'
+    def gamma4(self, N, legs, ms, ts, irr):
+        return self._m(("g4", N, legs, ms, ts, irr), lambda: self._gamma4(N, legs, ms, ts, irr))
+
+    def _gamma4(self, N, legs, ms, ts, irr):
+        A = self.alg
+        out = {}
+        for k, v in self.irreducible(N, legs, ms, ts).items():
+            A.acc(out, k, v)
+        for c in ("ph", "phbar", "pp"):
+            if irr == "ph" and c == "ph":
+                continue
+            if irr == "pp" and c == "pp":
+                continue
+            for k, v in self.phi(c, N, legs, ms, ts).items():
+                A.acc(out, k, v)
+        return out
+
+    def irreducible(self, N, legs, ms, ts):
+        return self._m(("irr", N, legs, ms, ts), lambda: self._irreducible(N, legs, ms, ts))
+
+    def _irreducible(self, N, legs, ms, ts):
+        A = self.alg
+        K1, K3, K2, K4 = legs
+        out = {}
+        if N == 0:
+            a, b = A.index(2 * ts), A.index(2 * ts + 1)
+            A.acc(out, (a, a, b, b), A.leaf_v(_sub(K1, K3), a, b))     # direct
+            A.acc(out, (a, b, b, a), A.leaf_v(_sub(K1, K4), a, b))     # exchanged
+            return out
+        leg_moms = {("in", 0): K1, ("out", 0): K3, ("in", 1): K2, ("out", 1): K4}
+        for key, w in self.C.irreducible(N).items():
+            piece = P.from_key(key)
+            # the piece's interaction lines in order of first vertex -> lines ts, ts+1, ...
+            succ, pred, partner = piece
+            lines = {}
+            for v in range(len(succ)):
+                lo = min(v, partner[v])
+                if lo not in lines:
+                    lines[lo] = len(lines)
+            glob = {v: 2 * (ts + lines[min(v, partner[v])]) + (0 if v < partner[v] else 1) for v in range(len(succ))}
+            leaves = route_piece(piece, leg_moms, self.n, ms, lambda v: A.index(glob[v]))
+            vals = [A.leaf_g(m, x, y) if kind == "G" else A.leaf_v(m, x, y) for (kind, m, x, y) in leaves]
+            lg = P._leg_vertices(piece)
+            idx = tuple(A.index(glob[lg[k]]) for k in (("in", 0), ("out", 0), ("in", 1), ("out", 1)))
+            A.acc(out, idx, A.scale(w, A.mul(*vals)))
+        return out
+
+    def phi(self, c, N, legs, ms, ts):
+        return self._m(("phi", c, N, legs, ms, ts), lambda: self._phi(c, N, legs, ms, ts))
+
+    def _phi(self, c, N, legs, ms, ts):
+        A = self.alg
+        out = {}
+        if N == 0:
+            return out
+        K1, K3, K2, K4 = legs
+        if c == "phbar":
+            # the ph join with the composite's out-legs exchanged
+            inner = self.phi("ph", N, (K1, K4, K2, K3), ms, ts)
+            return {(a, d, cc, b): v for (a, b, cc, d), v in inner.items()}
+        p = _vec(self.n, ms)
+        half = Fraction(1, 2) if c == "pp" else Fraction(1)
+        for i in range(N):
+            for j in range(N - i):
+                for k in range(N - i - j):
+                    l = N - 1 - i - j - k
+                    mL, tL = ms + 1, ts
+                    mR, tR = mL + i, tL + i + 1
+                    m1, t1 = mR + j, tR + j + 1
+                    m2, t2 = m1 + k, t1 + k
+                    if c == "ph":
+                        P1, P2 = p, _add(p, _sub(K3, K1))
+                        Lg = (K1, K3, P2, P1)
+                        Rg = (P1, P2, K2, K4)
+                        L = self.gamma4(i, Lg, mL, tL, None)
+                        R = self.gamma4(j, Rg, mR, tR, "ph")
+                        for (a, b, x, y), lv in L.items():
+                            for (u, v, cc, d), rv in R.items():
+                                g1 = self.chain(k, P1, y, u, m1, t1)
+                                g2 = self.chain(l, P2, v, x, m2, t2)
+                                A.acc(out, (a, b, cc, d), A.mul(lv, g1, g2, rv))
+                    else:
+                        P1, P2 = p, _sub(_add(K1, K2), p)
+                        Lg = (K1, P1, K2, P2)
+                        Rg = (P1, K3, P2, K4)
+                        L = self.gamma4(i, Lg, mL, tL, None)
+                        R = self.gamma4(j, Rg, mR, tR, "pp")
+                        for (a, x, b, y), lv in L.items():
+                            for (u, cc, v, d), rv in R.items():
+                                g1 = self.chain(k, P1, x, u, m1, t1)
+                                g2 = self.chain(l, P2, y, v, m2, t2)
+                                A.acc(out, (a, cc, b, d), A.scale(half, A.mul(lv, g1, g2, rv)))
+        return out
+
+    def root(self):
+        """Sigma^(n)(k_ext) over its out-vertex (index)."""
+        return self.sigma(self.n, _vec(self.n, 0), 1, 0)

@@ -1,0 +1,111 @@
+"""The evaluation graph of the Dyson-Schwinger / parquet construction (Sec.
+II.B-C): expanded into monomials it is exactly the set of self-energy
+diagrams (each with total weight 1), every monomial conserves momentum at
+every vertex with n independent loop momenta, and the compact evaluation
+(shared nodes, tensors over leg times) equals the expanded sum per sample
+for arbitrary leaf functions; its operation count is below the plain sum
+over diagrams."""
+import collections
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2403_18840_gb300 import parquet as P
+from paper_2403_18840_gb300 import parquet_graph as PG
+
+
+@pytest.fixture(scope="module")
+def construction():
+    return P.Construction()
+
+
+def _piece(n, out_v, mono):
+    nv = 2 * n
+    succ, pred, partner = [None] * nv, [None] * nv, [None] * nv
+    for leaf in mono:
+        if leaf[0] == "G":
+            _, _, x, y = leaf
+            assert succ[x] is None and pred[y] is None
+            succ[x], pred[y] = y, x
+        else:
+            _, _, a, b = leaf
+            partner[a], partner[b] = b, a
+    assert pred[0] is None and succ[out_v] is None
+    pred[0], succ[out_v] = -1, -1
+    assert None not in succ + pred + partner
+    return tuple(succ), tuple(pred), tuple(partner)
+
+
+def _conserves(n, out_v, mono):
+    net = np.zeros((2 * n, n + 1), dtype=int)
+    net[0, 0] += 1                       # k_ext enters at the in-vertex
+    net[out_v, 0] -= 1
+    for _, m, x, y in mono:
+        net[x] -= m
+        net[y] += m
+    loops = np.array([m for _, m, _, _ in mono])[:, 1:]
+    return not net.any() and np.linalg.matrix_rank(loops) == n
+
+
+def _leaf_functions(n, seed):
+    rng = np.random.default_rng(seed)
+    var, tau = rng.normal(0, 1, n + 1), rng.uniform(0, 1, n)
+
+    def mv(m):
+        return float(np.dot(m, var))
+
+    def g0(m, x, y):
+        return math.exp(-0.3 * mv(m) ** 2) * (1 + 0.5 * math.sin(tau[y] - tau[x] + mv(m)))
+
+    def v(m):
+        return 1.0 / (mv(m) ** 2 + 0.5)
+    return g0, v
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_graph_expands_to_the_diagrams_and_evaluates_them(construction, n):
+    root = PG.Evaluator(n, PG.Expanded(), construction).root()
+    weights = collections.defaultdict(Fraction)
+    for o, monos in root.items():
+        for w, mono in monos:
+            assert len(mono) == 3 * n - 1
+            assert _conserves(n, o, mono)
+            weights[P.canonical(_piece(n, o, mono))] += w
+    assert dict(weights) == construction.sigma(n)
+    g0, v = _leaf_functions(n, n)
+    S = PG.Scalar(g0, v)
+    compact = PG.Evaluator(n, S, construction).root()
+    naive = collections.defaultdict(float)
+    for o, monos in root.items():
+        for w, mono in monos:
+            val = float(w)
+            for leaf in mono:
+                val *= g0(leaf[1], leaf[2] // 2, leaf[3] // 2) if leaf[0] == "G" else v(leaf[1])
+            naive[o // 2] += val
+    scale = max(abs(x) for x in naive.values())
+    assert set(compact) == set(naive)
+    assert max(abs(compact[k] - naive[k]) for k in naive) < 1e-12 * scale
+    D = len(construction.sigma(n))
+    if n >= 2:
+        assert S.ops < D * (3 * n - 2) + D - 1
+
+
+def test_routing_of_a_fully_irreducible_vertex(construction):
+    # the envelope diagrams: spanning-tree routing conserves momentum at every
+    # vertex, the four legs' momenta given, with three independent loop momenta
+    legs = {("in", 0): (0, 1, 0, 0, 0, 0, 0), ("out", 0): (0, 0, 1, 0, 0, 0, 0),
+            ("in", 1): (0, 0, 0, 1, 0, 0, 0), ("out", 1): (0, 1, -1, 1, 0, 0, 0)}
+    for key in construction.irreducible(3):
+        piece = P.from_key(key)
+        leaves = PG.route_piece(piece, legs, 6, 4, lambda v: v)
+        assert len(leaves) == 6 + 4                 # 6 bare lines, 4 interaction lines
+        net = np.zeros((len(piece[0]), 7), dtype=int)
+        for (kind, j), vtx in P._leg_vertices(piece).items():
+            net[vtx] += np.array(legs[(kind, j)]) * (1 if kind == "in" else -1)
+        for _, m, x, y in leaves:
+            net[x] -= m
+            net[y] += m
+        assert not net.any()
+        assert np.linalg.matrix_rank(np.array([m for _, m, _, _ in leaves])[:, 4:]) == 3
