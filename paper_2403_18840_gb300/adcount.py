@@ -152,6 +152,23 @@ def scaling_table(n, l_max):
     return rows
 
 
+def parquet_scaling_table(n, l_max, construction=None):
+    """Rows (l, Taylor ops, nested ops) for Sigma^(n,0,l) on the Dyson-Schwinger
+    / parquet evaluation graph (`parquet_graph`), the graph the paper's
+    comparison uses; V-leaf series included."""
+    from . import parquet as P
+    from . import parquet_graph as PG
+    C = construction or P.Construction()
+    rows = []
+    for l in range(l_max + 1):
+        t = PG.DerivativeCount(l, "taylor")
+        PG.Evaluator(n, t, C).root()
+        d = PG.DerivativeCount(l, "nested")
+        PG.Evaluator(n, d, C).root()
+        rows.append((l, t.total(), d.total()))
+    return rows
+
+
 # ---- numerical evaluation of the same three routes ---------------------------
 
 def leaf_values(dag, seed):

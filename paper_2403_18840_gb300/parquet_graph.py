@@ -62,6 +62,9 @@ class Scalar:
     def leaf_v(self, mom, a, b):
         return self.v(mom)
 
+    def one(self):
+        return 1.0
+
     def mul(self, *xs):
         r = xs[0]
         for x in xs[1:]:
@@ -83,6 +86,102 @@ class Scalar:
             d[key] = x
 
 
+class DerivativeCount:
+    """Operation counts of derivatives in the screening shift Lambda, which
+    enters through the interaction leaves only: values are True when they
+    depend on Lambda.  Taylor mode to order L (mode 'taylor') or forward
+    mode nested L times (mode 'nested'), with the costs of `adcount`: a
+    product of two dependent values (L + 1)^2 or 2 3^L - 2^L, a product with
+    an independent value L + 1 or 2^L, a sum of two dependent values L + 1 or
+    2^L, anything else 1; each distinct interaction leaf L (its series)."""
+
+    def __init__(self, L, mode):
+        self.L = L
+        if mode == "taylor":
+            self.dd, self.di, self.add = (L + 1) ** 2, L + 1, L + 1
+        else:
+            self.dd, self.di, self.add = 2 * 3 ** L - 2 ** L, 2 ** L, 2 ** L
+        self.ops = 0
+        self.v_leaves = set()
+
+    def index(self, vertex):
+        return vertex // 2
+
+    def leaf_g(self, mom, x, y):
+        return False
+
+    def leaf_v(self, mom, a, b):
+        self.v_leaves.add(mom)
+        return True
+
+    def one(self):
+        return False
+
+    def mul(self, *xs):
+        r = xs[0]
+        for x in xs[1:]:
+            self.ops += self.dd if (r and x) else self.di if (r or x) else 1
+            r = r or x
+        return r
+
+    def scale(self, w, x):
+        if w == 1:
+            return x
+        self.ops += self.di if x else 1
+        return x
+
+    def acc(self, d, key, x):
+        if key in d:
+            self.ops += self.add if (d[key] and x) else 1
+            d[key] = d[key] or x
+        else:
+            d[key] = x
+
+    def total(self):
+        return self.ops + len(self.v_leaves) * self.L
+
+
+class Series:
+    """Truncated Taylor series in the screening shift Lambda (numpy arrays of
+    length L + 1): the interaction leaves carry c / (q^2 + Lambda) expanded
+    at lam, everything else is constant in Lambda.  v(mom) returns (c, q^2)."""
+
+    def __init__(self, g0, v, lam, L):
+        import numpy as np
+        self.np, self.g0, self.v, self.lam, self.L = np, g0, v, lam, L
+
+    def index(self, vertex):
+        return vertex // 2
+
+    def _const(self, x):
+        s = self.np.zeros(self.L + 1)
+        s[0] = x
+        return s
+
+    def leaf_g(self, mom, x, y):
+        return self._const(self.g0(mom, x, y))
+
+    def leaf_v(self, mom, a, b):
+        c, q2 = self.v(mom)
+        r = 1.0 / (q2 + self.lam)
+        return self.np.array([c * r * (-r) ** k for k in range(self.L + 1)])
+
+    def one(self):
+        return self._const(1.0)
+
+    def mul(self, *xs):
+        r = xs[0]
+        for x in xs[1:]:
+            r = self.np.array([sum(r[i] * x[k - i] for i in range(k + 1)) for k in range(self.L + 1)])
+        return r
+
+    def scale(self, w, x):
+        return float(w) * x
+
+    def acc(self, d, key, x):
+        d[key] = d[key] + x if key in d else x
+
+
 class Expanded:
     """Weighted monomials over vertex-level leaves."""
 
@@ -94,6 +193,9 @@ class Expanded:
 
     def leaf_v(self, mom, a, b):
         return [(Fraction(1), (("V", mom, a, b),))]
+
+    def one(self):
+        return [(Fraction(1), ())]
 
     def mul(self, *xs):
         out = [(Fraction(1), ())]
@@ -236,7 +338,7 @@ class Evaluator:
     def _gamma3(self, N, Kin, Kout, ms, ts, b):
         A = self.alg
         if N == 0:
-            return {(b, b): self._one()}             # the bare vertex: b itself
+            return {(b, b): A.one()}                 # the bare vertex: b itself
         # b takes in the boson momentum Kout - Kin; Gamma4 legs (in1, out1, in2, out2)
         p = _vec(self.n, ms)
         out = {}
@@ -251,9 +353,6 @@ class Evaluator:
                     c2 = self.chain(M - j, p, w, b, m1 + j, t1 + j)
                     A.acc(out, (x, o), A.mul(val, c1, c2))
         return out
-
-    def _one(self):
-        return 1.0 if isinstance(self.alg, Scalar) else [(Fraction(1), ())]
 
     # Gamma4 over (in1, out1, in2, out2) vertices; irr: None, 'ph' or 'pp'
     def gamma4(self, N, legs, ms, ts, irr):

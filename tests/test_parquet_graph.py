@@ -109,3 +109,42 @@ def test_routing_of_a_fully_irreducible_vertex(construction):
             net[y] += m
         assert not net.any()
         assert np.linalg.matrix_rank(np.array([m for _, m, _, _ in leaves])[:, 4:]) == 3
+
+
+def test_counterterm_derivatives_on_the_graph(construction):
+    # Taylor series in Lambda through the graph: coefficient l times l! equals
+    # central differences of the plain graph in Lambda (l = 1, 2)
+    n, lam, h = 3, 0.6, 1e-3
+    g0, _ = _leaf_functions(n, 7)
+    rng = np.random.default_rng(8)
+    cq = {}
+
+    def v(m):
+        if m not in cq:
+            cq[m] = (rng.uniform(0.5, 2.0), rng.uniform(0.5, 3.0))
+        return cq[m]
+    ser = PG.Evaluator(n, PG.Series(g0, v, lam, 2), construction).root()
+
+    def plain(x):
+        out = PG.Evaluator(n, PG.Series(g0, v, x, 0), construction).root()
+        return {k: s[0] for k, s in out.items()}
+    p0, pp, pm = plain(lam), plain(lam + h), plain(lam - h)
+    scale1 = max(abs(s[1]) for s in ser.values())
+    scale2 = max(abs(2 * s[2]) for s in ser.values())
+    for k, s in ser.items():
+        assert abs(s[0] - p0[k]) < 1e-12 * (abs(p0[k]) + 1e-300)
+        assert abs((pp[k] - pm[k]) / (2 * h) - s[1]) < 1e-5 * scale1
+        assert abs((pp[k] - 2 * p0[k] + pm[k]) / h ** 2 - 2 * s[2]) < 1e-5 * scale2
+
+
+def test_taylor_and_nested_counts_on_the_graph(construction):
+    from paper_2403_18840_gb300 import adcount
+    rows = adcount.parquet_scaling_table(4, 6, construction)
+    g0, v = _leaf_functions(4, 1)
+    S = PG.Scalar(g0, v)
+    PG.Evaluator(4, S, construction).root()
+    assert rows[0][1] == rows[0][2] == S.ops
+    t = np.array([r[1] for r in rows], dtype=float)
+    assert np.all(np.abs(np.diff(t, 3)) < 1e-9)          # a quadratic in l
+    d = np.array([r[2] for r in rows], dtype=float)
+    assert 2.5 < d[6] / d[5] < 3.0 and d[6] > 15 * t[6]
