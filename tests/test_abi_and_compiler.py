@@ -156,3 +156,17 @@ def _load_ok_or_nodevice(data):
     st = _load(data)
     # validation passes; the upload needs a device (FD_ECUDA on a CPU-only host)
     return st in (L.FD_OK, L.FD_ECUDA)
+
+
+def test_spline_flow_entry_points_validate_arguments_before_any_device_work():
+    # null handles and pointers are rejected on the host with FD_EINVAL and a
+    # message, without touching a device (this runs without one)
+    lib = L.lib()
+    f32 = np.zeros(4, dtype=np.float32)
+    p = f32.ctypes.data
+    loss = np.zeros(4, dtype=np.float64)
+    assert lib.fd_nsf_kl_grad(None, p, p, 4, p, loss.ctypes.data, None) == 1
+    assert b"required" in lib.fd_last_error()
+    assert lib.fd_nsf_train(None, p, p, 4, 1, 1e-3, None, None) == 1
+    assert lib.fd_nsf_get_params(None, f32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 4) == 1
+    assert lib.fd_nsf_param_count(None) == 0
