@@ -28,6 +28,7 @@ interaction line l has time variable l; its two ends are vertices 2l and
 import collections
 from fractions import Fraction
 
+from . import fdgraph
 from . import parquet as P
 
 
@@ -301,19 +302,21 @@ class Evaluator:
         A = self.alg
         if k == 0:
             return A.leaf_g(K, x, y)
-        total = None
-        for p in range(1, k + 1):
-            a = A.index(2 * ts)
-            for o, s in self.sigma(p, K, ms, ts).items():
-                term = A.mul(A.leaf_g(K, x, a), s, self.chain(k - p, K, o, y, ms + p, ts + p))
-                total = term if total is None else self._plus(total, term)
-        return total
+        # G0(x -> first insertion) times the rest, which does not depend on x
+        return A.mul(A.leaf_g(K, x, A.index(2 * ts)), self.chain_tail(k, K, y, ms, ts))
 
-    def _plus(self, a, b):
-        d = {}
-        self.alg.acc(d, 0, a)
-        self.alg.acc(d, 0, b)
-        return d[0]
+    def chain_tail(self, k, K, y, ms, ts):
+        """sum over the first insertion Sigma^(p) and its out-vertex o of
+        Sigma^(p)[o] times the dressed line of order k - p from o to y."""
+        return self._m(("tail", k, K, y, ms, ts), lambda: self._chain_tail(k, K, y, ms, ts))
+
+    def _chain_tail(self, k, K, y, ms, ts):
+        A = self.alg
+        out = {}
+        for p in range(1, k + 1):
+            for o, s in self.sigma(p, K, ms, ts).items():
+                A.acc(out, 0, A.mul(s, self.chain(k - p, K, o, y, ms + p, ts + p)))
+        return out[0]
 
     # Sigma^(N)(K) over its out-vertex; in-vertex 2 ts, loop q = ms
     def sigma(self, N, K, ms, ts):
@@ -326,9 +329,10 @@ class Evaluator:
         out = {}
         for i in range(N):
             g3 = self.gamma3(i, _sub(K, q), K, ms + 1, ts + 1, b)
+            vline = {x: A.mul(A.leaf_v(q, a, b), self.chain(N - i - 1, _sub(K, q), a, x, ms + 1 + i, ts + 1 + i))
+                     for x in {x for (x, _) in g3}}
             for (x, o), val in g3.items():
-                ch = self.chain(N - i - 1, _sub(K, q), a, x, ms + 1 + i, ts + 1 + i)
-                A.acc(out, o, A.mul(A.leaf_v(q, a, b), ch, val))
+                A.acc(out, o, A.mul(vline[x], val))
         return out
 
     # Gamma3 over (in-vertex, out-vertex); b its interaction end (outside)
@@ -346,12 +350,15 @@ class Evaluator:
             M = N - i - 1
             legs = (Kin, Kout, _add(p, _sub(Kout, Kin)), p)
             g4 = self.gamma4(i, legs, ms + 1, ts, None)
-            for j in range(M + 1):
-                m1, t1 = ms + 1 + i, ts + i + 1
-                for (x, o, u, w), val in g4.items():
-                    c1 = self.chain(j, legs[2], b, u, m1, t1)
-                    c2 = self.chain(M - j, p, w, b, m1 + j, t1 + j)
-                    A.acc(out, (x, o), A.mul(val, c1, c2))
+            m1, t1 = ms + 1 + i, ts + i + 1
+            pairs = {(u, w) for (_, _, u, w) in g4}
+            bubble = {}                          # [G G]^(M) from b to u and from w back to b
+            for (u, w) in pairs:
+                for j in range(M + 1):
+                    A.acc(bubble, (u, w), A.mul(self.chain(j, legs[2], b, u, m1, t1),
+                                                self.chain(M - j, p, w, b, m1 + j, t1 + j)))
+            for (x, o, u, w), val in g4.items():
+                A.acc(out, (x, o), A.mul(val, bubble[(u, w)]))
         return out
 
     # Gamma4 over (in1, out1, in2, out2) vertices; irr: None, 'ph' or 'pp'
@@ -385,6 +392,7 @@ class Evaluator:
             A.acc(out, (a, b, b, a), A.leaf_v(_sub(K1, K4), a, b))     # exchanged
             return out
         leg_moms = {("in", 0): K1, ("out", 0): K3, ("in", 1): K2, ("out", 1): K4}
+        polys = {}
         for key, w in self.C.irreducible(N).items():
             piece = P.from_key(key)
             # the piece's interaction lines in order of first vertex -> lines ts, ts+1, ...
@@ -396,11 +404,47 @@ class Evaluator:
                     lines[lo] = len(lines)
             glob = {v: 2 * (ts + lines[min(v, partner[v])]) + (0 if v < partner[v] else 1) for v in range(len(succ))}
             leaves = route_piece(piece, leg_moms, self.n, ms, lambda v: A.index(glob[v]))
-            vals = [A.leaf_g(m, x, y) if kind == "G" else A.leaf_v(m, x, y) for (kind, m, x, y) in leaves]
             lg = P._leg_vertices(piece)
             idx = tuple(A.index(glob[lg[k]]) for k in (("in", 0), ("out", 0), ("in", 1), ("out", 1)))
-            A.acc(out, idx, A.scale(w, A.mul(*vals)))
+            poly = polys.setdefault(idx, {})
+            mono = tuple(sorted(leaves))
+            poly[mono] = poly.get(mono, 0) + w
+        # the node's diagrams factorised together (greedy Horner, hash-consed)
+        dag = fdgraph.DAG()
+        dag.scope = None
+        memo = {}
+        for idx, poly in polys.items():
+            A.acc(out, idx, self._dag_value(dag, fdgraph.horner(dag, poly), memo))
         return out
+
+    def _dag_value(self, dag, u, memo):
+        if u in memo:
+            return memo[u]
+        A = self.alg
+        node = dag.nodes[u]
+        kind = node[0]
+        if kind == "var":
+            kd, m, x, y = node[1]
+            val = A.leaf_g(m, x, y) if kd == "G" else A.leaf_v(m, x, y)
+        elif kind == "mul":
+            val = A.mul(self._dag_value(dag, node[1], memo), self._dag_value(dag, node[2], memo))
+        elif kind == "mulc":
+            val = A.scale(node[2], self._dag_value(dag, node[1], memo))
+        elif kind in ("add", "fma"):
+            if kind == "add":
+                first = self._dag_value(dag, node[1], memo)
+                second = self._dag_value(dag, node[2], memo)
+            else:
+                first = A.mul(self._dag_value(dag, node[1], memo), self._dag_value(dag, node[2], memo))
+                second = self._dag_value(dag, node[3], memo)
+            d = {}
+            A.acc(d, 0, first)
+            A.acc(d, 0, second)
+            val = d[0]
+        else:
+            raise ValueError("unexpected node %r" % (node,))
+        memo[u] = val
+        return val
 
     def phi(self, c, N, legs, ms, ts):
         return self._m(("phi", c, N, legs, ms, ts), lambda: self._phi(c, N, legs, ms, ts))
@@ -427,26 +471,42 @@ class Evaluator:
                     m2, t2 = m1 + k, t1 + k
                     if c == "ph":
                         P1, P2 = p, _add(p, _sub(K3, K1))
-                        Lg = (K1, K3, P2, P1)
-                        Rg = (P1, P2, K2, K4)
-                        L = self.gamma4(i, Lg, mL, tL, None)
-                        R = self.gamma4(j, Rg, mR, tR, "ph")
+                        L = self.gamma4(i, (K1, K3, P2, P1), mL, tL, None)
+                        R = self.gamma4(j, (P1, P2, K2, K4), mR, tR, "ph")
+                        # L[a,b,x,y] G(y->u) G(v->x) R[u,v,c,d]
+                        us = {u for (u, _, _, _) in R}
+                        vs = {v for (_, v, _, _) in R}
+                        M1 = {}
                         for (a, b, x, y), lv in L.items():
-                            for (u, v, cc, d), rv in R.items():
-                                g1 = self.chain(k, P1, y, u, m1, t1)
-                                g2 = self.chain(l, P2, v, x, m2, t2)
-                                A.acc(out, (a, b, cc, d), A.mul(lv, g1, g2, rv))
+                            for u in us:
+                                A.acc(M1, (a, b, x, u), A.mul(lv, self.chain(k, P1, y, u, m1, t1)))
+                        M2 = {}
+                        for (a, b, x, u), mv in M1.items():
+                            for v in vs:
+                                A.acc(M2, (a, b, u, v), A.mul(mv, self.chain(l, P2, v, x, m2, t2)))
+                        for (u, v, cc, d), rv in R.items():
+                            for (a, b, u2, v2), nv in M2.items():
+                                if (u2, v2) == (u, v):
+                                    A.acc(out, (a, b, cc, d), A.mul(nv, rv))
                     else:
                         P1, P2 = p, _sub(_add(K1, K2), p)
-                        Lg = (K1, P1, K2, P2)
-                        Rg = (P1, K3, P2, K4)
-                        L = self.gamma4(i, Lg, mL, tL, None)
-                        R = self.gamma4(j, Rg, mR, tR, "pp")
+                        L = self.gamma4(i, (K1, P1, K2, P2), mL, tL, None)
+                        R = self.gamma4(j, (P1, K3, P2, K4), mR, tR, "pp")
+                        # L[a,x,b,y] G(x->u) G(y->v) R[u,c,v,d] / 2
+                        us = {u for (u, _, _, _) in R}
+                        vs = {v for (_, _, v, _) in R}
+                        M1 = {}
                         for (a, x, b, y), lv in L.items():
-                            for (u, cc, v, d), rv in R.items():
-                                g1 = self.chain(k, P1, x, u, m1, t1)
-                                g2 = self.chain(l, P2, y, v, m2, t2)
-                                A.acc(out, (a, cc, b, d), A.scale(half, A.mul(lv, g1, g2, rv)))
+                            for u in us:
+                                A.acc(M1, (a, b, y, u), A.mul(lv, self.chain(k, P1, x, u, m1, t1)))
+                        M2 = {}
+                        for (a, b, y, u), mv in M1.items():
+                            for v in vs:
+                                A.acc(M2, (a, b, u, v), A.mul(mv, self.chain(l, P2, y, v, m2, t2)))
+                        for (u, cc, v, d), rv in R.items():
+                            for (a, b, u2, v2), nv in M2.items():
+                                if (u2, v2) == (u, v):
+                                    A.acc(out, (a, cc, b, d), A.scale(half, A.mul(nv, rv)))
         return out
 
     def root(self):
