@@ -169,6 +169,23 @@ def parquet_scaling_table(n, l_max, construction=None):
     return rows
 
 
+def parquet_all_roots_ops(order, construction=None):
+    """Contraction ops of every root (n, m, l) with n + m + l = order from the
+    Dyson-Schwinger / parquet graphs of Sigma^(1..order), each in Taylor mode
+    in (mu, Lambda) to total degree order - n; leaves excluded.  Returns
+    {n: ops} and the total."""
+    from . import parquet as P
+    from . import parquet_graph as PG
+    C = construction or P.Construction()
+    per = {}
+    for n in range(1, order + 1):
+        alg = PG.BiTaylorCount(order - n)
+        ev = PG.Evaluator(n, alg, C)
+        ev.root()
+        per[n] = alg.ops
+    return per, sum(per.values())
+
+
 # ---- numerical evaluation of the same three routes ---------------------------
 
 def leaf_values(dag, seed):

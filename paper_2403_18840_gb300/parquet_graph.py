@@ -183,6 +183,110 @@ class Series:
         d[key] = d[key] + x if key in d else x
 
 
+def _support(kind, D):
+    """Exponents (i, j) of mu^i Lambda^j a series of this kind carries to total degree D."""
+    if kind == "const":
+        return frozenset({(0, 0)})
+    if kind == "mu":
+        return frozenset((i, 0) for i in range(D + 1))
+    if kind == "lam":
+        return frozenset((0, j) for j in range(D + 1))
+    return frozenset((i, j) for i in range(D + 1) for j in range(D + 1 - i))
+
+
+class BiSeries:
+    """Truncated Taylor series in (mu, Lambda) to total degree D, as dicts
+    {(i, j): coefficient}: the bare lines depend on mu, the interaction lines
+    on Lambda.  g0(mom, x, y, i) is the i-th mu-Taylor coefficient of a bare
+    line, v(mom) = (c, q^2) an interaction c / (q^2 + Lambda) at lam."""
+
+    def __init__(self, g0, v, lam, D):
+        self.g0, self.v, self.lam, self.D = g0, v, lam, D
+
+    def index(self, vertex):
+        return vertex // 2
+
+    def leaf_g(self, mom, x, y):
+        return {(i, 0): self.g0(mom, x, y, i) for i in range(self.D + 1)}
+
+    def leaf_v(self, mom, a, b):
+        c, q2 = self.v(mom)
+        r = 1.0 / (q2 + self.lam)
+        return {(0, j): c * r * (-r) ** j for j in range(self.D + 1)}
+
+    def one(self):
+        return {(0, 0): 1.0}
+
+    def mul(self, *xs):
+        r = xs[0]
+        for x in xs[1:]:
+            out = {}
+            for (i1, j1), a in r.items():
+                for (i2, j2), b in x.items():
+                    if i1 + i2 + j1 + j2 <= self.D:
+                        k = (i1 + i2, j1 + j2)
+                        out[k] = out.get(k, 0.0) + a * b
+            r = out
+        return r
+
+    def scale(self, w, x):
+        return {k: float(w) * v for k, v in x.items()}
+
+    def acc(self, d, key, x):
+        if key in d:
+            y = dict(d[key])
+            for k, v in x.items():
+                y[k] = y.get(k, 0.0) + v
+            d[key] = y
+        else:
+            d[key] = x
+
+
+class BiTaylorCount:
+    """Operation count of Taylor mode in (mu, Lambda) to total degree D (all
+    counterterm orders of one Sigma^(n) at once): values are the exponent
+    supports; a product costs one multiply per pair of exponents within the
+    degree plus the adds that merge equal exponents, a sum one add per common
+    exponent.  Leaves excluded, as in `fdgraph.contraction_ops`."""
+
+    def __init__(self, D):
+        self.D = D
+        self.ops = 0
+
+    def index(self, vertex):
+        return vertex // 2
+
+    def leaf_g(self, mom, x, y):
+        return _support("mu", self.D)
+
+    def leaf_v(self, mom, a, b):
+        return _support("lam", self.D)
+
+    def one(self):
+        return _support("const", self.D)
+
+    def mul(self, *xs):
+        r = xs[0]
+        for x in xs[1:]:
+            pairs = [(a[0] + b[0], a[1] + b[1]) for a in r for b in x if sum(a) + sum(b) <= self.D]
+            out = frozenset(pairs)
+            self.ops += len(pairs) + (len(pairs) - len(out))
+            r = out
+        return r
+
+    def scale(self, w, x):
+        if w != 1:
+            self.ops += len(x)
+        return x
+
+    def acc(self, d, key, x):
+        if key in d:
+            self.ops += len(d[key] & x)
+            d[key] = d[key] | x
+        else:
+            d[key] = x
+
+
 class Expanded:
     """Weighted monomials over vertex-level leaves."""
 

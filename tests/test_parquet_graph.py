@@ -148,3 +148,53 @@ def test_taylor_and_nested_counts_on_the_graph(construction):
     assert np.all(np.abs(np.diff(t, 3)) < 1e-9)          # a quadratic in l
     d = np.array([r[2] for r in rows], dtype=float)
     assert 2.5 < d[6] / d[5] < 3.0 and d[6] > 15 * t[6]
+
+
+def test_taylor_mode_in_mu_and_lambda_on_the_graph(construction):
+    # every counterterm root from one graph: the (mu, Lambda) series through
+    # the graph against mixed central differences of the plain graph
+    n, D, mu0, lam0, h = 3, 2, 0.2, 0.6, 1e-3
+    rng = np.random.default_rng(12)
+    var, tau = rng.normal(0, 1, n + 1), rng.uniform(0, 1, n)
+    cq = {}
+
+    def v(m):
+        if m not in cq:
+            cq[m] = (rng.uniform(0.5, 2.0), rng.uniform(0.5, 3.0))
+        return cq[m]
+
+    def g_at(mu):
+        # a bare line exp(-0.3 (p^2 - mu)) (1 + 0.5 sin(...)): its i-th mu-Taylor
+        # coefficient is the value times 0.3^i / i!
+        def g0(m, x, y, i):
+            pm = float(np.dot(m, var))
+            base = math.exp(-0.3 * (pm * pm - mu)) * (1 + 0.5 * math.sin(tau[y] - tau[x] + pm))
+            return base * 0.3 ** i / math.factorial(i)
+        return g0
+
+    ser = PG.Evaluator(n, PG.BiSeries(g_at(mu0), v, lam0, D), construction).root()
+
+    def plain(mu, lam):
+        out = PG.Evaluator(n, PG.BiSeries(g_at(mu), v, lam, 0), construction).root()
+        return {k: s[(0, 0)] for k, s in out.items()}
+    f = {(a, b): plain(mu0 + a * h, lam0 + b * h) for a in (-1, 0, 1) for b in (-1, 0, 1)}
+    for k, s in ser.items():
+        fd = {(1, 0): (f[1, 0][k] - f[-1, 0][k]) / (2 * h),
+              (0, 1): (f[0, 1][k] - f[0, -1][k]) / (2 * h),
+              (2, 0): (f[1, 0][k] - 2 * f[0, 0][k] + f[-1, 0][k]) / h ** 2 / 2,
+              (0, 2): (f[0, 1][k] - 2 * f[0, 0][k] + f[0, -1][k]) / h ** 2 / 2,
+              (1, 1): (f[1, 1][k] - f[1, -1][k] - f[-1, 1][k] + f[-1, -1][k]) / (4 * h * h)}
+        scale = max(abs(x) for x in s.values())
+        assert abs(s[(0, 0)] - f[0, 0][k]) < 1e-12 * scale
+        for e, d in fd.items():
+            assert abs(s[e] - d) < 1e-5 * scale, (k, e)
+
+
+def test_all_roots_counts(construction):
+    from paper_2403_18840_gb300 import adcount
+    g0, v = _leaf_functions(4, 1)
+    S = PG.Scalar(g0, v)
+    PG.Evaluator(4, S, construction).root()
+    per, total = adcount.parquet_all_roots_ops(4, construction)
+    assert per[4] == S.ops                      # degree 0: the plain graph
+    assert total == sum(per.values()) and all(per[n] > 0 for n in per)
