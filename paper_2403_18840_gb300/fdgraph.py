@@ -522,6 +522,17 @@ def compile_graph(order, roots, budget=96, bundle=4, window=32):
     for (r, o) in sorted(polys):
         dag.scope = (r, o)
         outputs.append((r, o, horner(dag, polys[(r, o)])))
+    return compile_dag(order, roots, dag, outputs, budget, bundle, window)
+
+
+def compile_dag(order, roots, dag, outputs, budget=96, bundle=4, window=32):
+    """Schedule, allocate and serialise a built DAG: outputs [(root index, out
+    line, node)] accumulate into the roots [(n, m, l, dk)]; leaves are
+    ('G', mom, line_dst, line_src, j) / ('Gd', ...) / ('V', mom, j) /
+    ('Vd', mom, j) with mom over (k_ext, k_1..k_order) up to overall sign."""
+    assert 1 <= bundle <= MAX_BUNDLE
+    sys.setrecursionlimit(max(sys.getrecursionlimit(), 100000))
+    N = order
 
     # ---- pass 1: linear schedule (post-order, largest-need child first) ------
     need = {}

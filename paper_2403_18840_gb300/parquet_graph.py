@@ -287,6 +287,96 @@ class BiTaylorCount:
             d[key] = x
 
 
+class DagEmit:
+    """Emits Taylor mode in (mu, Lambda) to total degree D as nodes of a
+    shared `fdgraph.DAG`, in the compiler's leaf vocabulary: ('G', mom,
+    line_dst, line_src, i) for the i-th mu-coefficient of a bare line and
+    ('V', mom, j) for the j-th Lambda-coefficient of an interaction line,
+    momenta padded to the tape's order and taken up to overall sign.
+    Values are {(i, j): node}."""
+
+    def __init__(self, dag, D, order):
+        self.dag, self.D, self.order = dag, D, order
+
+    def index(self, vertex):
+        return vertex // 2
+
+    def _mom(self, mom):
+        m = tuple(mom) + (0,) * (self.order + 1 - len(mom))
+        return fdgraph._canon_mom(m)[0]
+
+    def leaf_g(self, mom, x, y):
+        cm = self._mom(mom)
+        return {(i, 0): self.dag.var(("G", cm, y, x, i)) for i in range(self.D + 1)}
+
+    def leaf_v(self, mom, a, b):
+        cm = self._mom(mom)
+        return {(0, j): self.dag.var(("V", cm, j)) for j in range(self.D + 1)}
+
+    def one(self):
+        return {(0, 0): self.dag.const(1.0)}
+
+    def mul(self, *xs):
+        r = xs[0]
+        for x in xs[1:]:
+            out = {}
+            for (i1, j1), a in sorted(r.items()):
+                for (i2, j2), b in sorted(x.items()):
+                    if i1 + i2 + j1 + j2 > self.D:
+                        continue
+                    k = (i1 + i2, j1 + j2)
+                    out[k] = self.dag.make("fma", a, b, out[k]) if k in out else self.dag.make("mul", a, b)
+            r = out
+        return r
+
+    def scale(self, w, x):
+        if w == 1:
+            return x
+        return {k: self.dag.make("mulc", u, float(w)) for k, u in x.items()}
+
+    def acc(self, d, key, x):
+        if key in d:
+            y = dict(d[key])
+            for k, u in x.items():
+                y[k] = self.dag.make("add", y[k], u) if k in y else u
+            d[key] = y
+        else:
+            d[key] = x
+
+
+def parquet_outputs(order, roots, construction=None):
+    """(dag, outputs) for roots [(n, m, l, 0)] of an order-`order` tape from
+    the Dyson-Schwinger / parquet graphs: Sigma^(n) in Taylor mode to total
+    degree order - n, root (n, m, l) = m! l! times the (m, l) coefficient, one
+    output per out line; one DAG shared by all roots."""
+    import math
+    C = construction or P.Construction()
+    dag = fdgraph.DAG()
+    dag.scope = None
+    series = {}
+    outputs = []
+    for r, (n, m, l, dk) in enumerate(roots):
+        if dk:
+            raise ValueError("k-derivative roots are not built on the parquet graph")
+        if n not in series:
+            series[n] = Evaluator(n, DagEmit(dag, order - n, order), C).root()
+        for o, coefs in sorted(series[n].items()):
+            if (m, l) not in coefs:
+                continue
+            node = coefs[(m, l)]
+            f = math.factorial(m) * math.factorial(l)
+            if f != 1:
+                node = dag.make("mulc", node, float(f))
+            outputs.append((r, o, node))
+    return dag, outputs
+
+
+def parquet_tape(order, roots, budget=96, bundle=4, window=32, construction=None):
+    """The parquet graphs of the roots compiled into the tape format."""
+    dag, outputs = parquet_outputs(order, roots, construction)
+    return fdgraph.compile_dag(order, roots, dag, outputs, budget, bundle, window)
+
+
 class Expanded:
     """Weighted monomials over vertex-level leaves."""
 
