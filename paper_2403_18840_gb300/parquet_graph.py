@@ -293,10 +293,12 @@ class DagEmit:
     line_dst, line_src, i) for the i-th mu-coefficient of a bare line and
     ('V', mom, j) for the j-th Lambda-coefficient of an interaction line,
     momenta padded to the tape's order and taken up to overall sign.
-    Values are {(i, j): node}."""
+    Values are {(i, j, e): node}; e = 1 is the first derivative in the
+    external momentum (with dk: the leaves 'Gd' / 'Vd' of lines that carry
+    k_ext, products by the Leibniz rule), e = 0 otherwise."""
 
-    def __init__(self, dag, D, order):
-        self.dag, self.D, self.order = dag, D, order
+    def __init__(self, dag, D, order, dk=False):
+        self.dag, self.D, self.order, self.dk = dag, D, order, dk
 
     def index(self, vertex):
         return vertex // 2
@@ -307,24 +309,30 @@ class DagEmit:
 
     def leaf_g(self, mom, x, y):
         cm = self._mom(mom)
-        return {(i, 0): self.dag.var(("G", cm, y, x, i)) for i in range(self.D + 1)}
+        out = {(i, 0, 0): self.dag.var(("G", cm, y, x, i)) for i in range(self.D + 1)}
+        if self.dk and cm[0] != 0:
+            out.update({(i, 0, 1): self.dag.var(("Gd", cm, y, x, i)) for i in range(self.D + 1)})
+        return out
 
     def leaf_v(self, mom, a, b):
         cm = self._mom(mom)
-        return {(0, j): self.dag.var(("V", cm, j)) for j in range(self.D + 1)}
+        out = {(0, j, 0): self.dag.var(("V", cm, j)) for j in range(self.D + 1)}
+        if self.dk and cm[0] != 0:
+            out.update({(0, j, 1): self.dag.var(("Vd", cm, j)) for j in range(self.D + 1)})
+        return out
 
     def one(self):
-        return {(0, 0): self.dag.const(1.0)}
+        return {(0, 0, 0): self.dag.const(1.0)}
 
     def mul(self, *xs):
         r = xs[0]
         for x in xs[1:]:
             out = {}
-            for (i1, j1), a in sorted(r.items()):
-                for (i2, j2), b in sorted(x.items()):
-                    if i1 + i2 + j1 + j2 > self.D:
+            for (i1, j1, e1), a in sorted(r.items()):
+                for (i2, j2, e2), b in sorted(x.items()):
+                    if i1 + i2 + j1 + j2 > self.D or e1 + e2 > 1:
                         continue
-                    k = (i1 + i2, j1 + j2)
+                    k = (i1 + i2, j1 + j2, e1 + e2)
                     out[k] = self.dag.make("fma", a, b, out[k]) if k in out else self.dag.make("mul", a, b)
             r = out
         return r
@@ -345,25 +353,25 @@ class DagEmit:
 
 
 def parquet_outputs(order, roots, construction=None):
-    """(dag, outputs) for roots [(n, m, l, 0)] of an order-`order` tape from
+    """(dag, outputs) for roots [(n, m, l, dk)] of an order-`order` tape from
     the Dyson-Schwinger / parquet graphs: Sigma^(n) in Taylor mode to total
-    degree order - n, root (n, m, l) = m! l! times the (m, l) coefficient, one
-    output per out line; one DAG shared by all roots."""
+    degree order - n (and first order in k_ext when any root has dk), root
+    (n, m, l, dk) = m! l! times the (m, l, dk) coefficient, one output per
+    out line; one DAG shared by all roots."""
     import math
     C = construction or P.Construction()
     dag = fdgraph.DAG()
     dag.scope = None
+    with_dk = any(r[3] for r in roots)
     series = {}
     outputs = []
     for r, (n, m, l, dk) in enumerate(roots):
-        if dk:
-            raise ValueError("k-derivative roots are not built on the parquet graph")
         if n not in series:
-            series[n] = Evaluator(n, DagEmit(dag, order - n, order), C).root()
+            series[n] = Evaluator(n, DagEmit(dag, order - n, order, with_dk), C).root()
         for o, coefs in sorted(series[n].items()):
-            if (m, l) not in coefs:
+            if (m, l, dk) not in coefs:
                 continue
-            node = coefs[(m, l)]
+            node = coefs[(m, l, dk)]
             f = math.factorial(m) * math.factorial(l)
             if f != 1:
                 node = dag.make("mulc", node, float(f))

@@ -19,11 +19,12 @@ def decode_mask(mask, n_var):
     return tuple(out)
 
 
-def run(data, g_leaf, v_leaf):
+def run(data, g_leaf, v_leaf, gd_leaf=None, vd_leaf=None):
     """Execute a serialised tape.  g_leaf(mom, line_dst, line_src, j) and
     v_leaf(mom, j) give the j-th Taylor coefficient of a leaf (mom with the
-    tape's sign).  Returns {root index: {out line: accumulated value}} (the
-    out line's phase left out)."""
+    tape's sign), gd_leaf / vd_leaf its derivative in k_ext for families
+    with the d/dk flag.  Returns {root index: {out line: accumulated value}}
+    (the out line's phase left out)."""
     hdr = struct.unpack("<16I", data[:64])
     order, n_slots, n_instr, ins_off = hdr[2], hdr[5], hdr[6], hdr[8]
     words = struct.unpack("<%dQ" % n_instr, data[ins_off:ins_off + 8 * n_instr])
@@ -48,10 +49,11 @@ def run(data, g_leaf, v_leaf):
         if op in (OP_GLEAF, OP_VLEAF):
             d, mask = (w >> 6) & 0x3FFF, (w >> 20) & 0x3FFF
             la, lb, M, dk = (w >> 34) & 7, (w >> 37) & 7, (w >> 40) & 7, (w >> 43) & 1
-            assert not dk
             mom = decode_mask(mask, order + 1)
             for j in range(M + 1):
                 S[d + j] = g_leaf(mom, la, lb, j) if op == OP_GLEAF else v_leaf(mom, j)
+                if dk:
+                    S[d + M + 1 + j] = gd_leaf(mom, la, lb, j) if op == OP_GLEAF else vd_leaf(mom, j)
         elif op == OP_RACC:
             a, line = (w >> 20) & 0x3FFF, (w >> 34) & 7
             current[line] += S[a]

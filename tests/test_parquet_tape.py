@@ -76,3 +76,74 @@ def test_parquet_tape_needs_fewer_operations(construction):
     pq = fdgraph.contraction_ops(PG.parquet_tape(5, roots, construction=construction).to_bytes())
     present = fdgraph.contraction_ops(fdgraph.compile_graph(5, roots).to_bytes())
     assert pq < present / 3
+
+
+def _leaf_functions_dk(order, seed, lam=0.6):
+    # leaves that depend on the momentum through p^2 = (mom . var)^2, var[0]
+    # the external momentum; their k_ext-derivatives in closed form
+    rng = np.random.default_rng(seed)
+    tau = rng.uniform(0, 1, order)
+    var0 = rng.normal(0, 1, order + 1)
+
+    def make(var):
+        def p(mom):
+            return float(np.dot(mom, var[:len(mom)]))
+
+        def base(p2, dst, src):
+            return math.exp(-0.3 * p2) * (1 + 0.5 * math.sin(tau[dst] - tau[src] + p2))
+
+        def dbase(p2, dst, src):
+            return -0.3 * base(p2, dst, src) + math.exp(-0.3 * p2) * 0.5 * math.cos(tau[dst] - tau[src] + p2)
+
+        def g_leaf(mom, dst, src, j):
+            return base(p(mom) ** 2, dst, src) * 0.3 ** j / math.factorial(j)
+
+        def gd_leaf(mom, dst, src, j):
+            return dbase(p(mom) ** 2, dst, src) * 2 * p(mom) * mom[0] * 0.3 ** j / math.factorial(j)
+
+        def v_cq(mom):
+            return 1.0 + 0.1 * p(mom) ** 2, 0.5 + p(mom) ** 2
+
+        def v_leaf(mom, j):
+            c, q2 = v_cq(mom)
+            r = 1.0 / (q2 + lam)
+            return c * (-1) ** j * r ** (j + 1)
+
+        def vd_leaf(mom, j):
+            c, q2 = v_cq(mom)
+            r = 1.0 / (q2 + lam)
+            d_dp2 = (-1) ** j * (0.1 * r ** (j + 1) - c * (j + 1) * r ** (j + 2))
+            return d_dp2 * 2 * p(mom) * mom[0]
+        return g_leaf, gd_leaf, v_leaf, vd_leaf, v_cq
+    return make, var0, lam
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_parquet_tape_k_derivative_roots(construction, order):
+    roots = fdgraph.graph_roots(order, with_dk=True)
+    data = PG.parquet_tape(order, roots, construction=construction).to_bytes()
+    assert _load_ok_or_nodevice(data)
+    make, var0, lam = _leaf_functions_dk(order, 20 + order)
+    g_leaf, gd_leaf, v_leaf, vd_leaf, _ = make(var0)
+    got = tape_exec.run(data, g_leaf, v_leaf, gd_leaf, vd_leaf)
+    h = 1e-5
+
+    def series_at(shift, n):
+        var = var0.copy()
+        var[0] += shift
+        g, _, _, _, v_cq = make(var)
+        return PG.Evaluator(n, PG.BiSeries(lambda mom, x, y, i: g(mom, y, x, i), v_cq, lam, order - n),
+                            construction).root()
+    cache = {}
+    for r, (n, m, l, dk) in enumerate(roots):
+        f = math.factorial(m) * math.factorial(l)
+        if n not in cache:
+            cache[n] = (series_at(0.0, n), series_at(h, n), series_at(-h, n))
+        s0, sp, sm = cache[n]
+        if dk == 0:
+            want = {o: s[(m, l)] * f for o, s in s0.items() if (m, l) in s}
+        else:
+            want = {o: (sp[o][(m, l)] - sm[o][(m, l)]) / (2 * h) * f for o in s0 if (m, l) in s0[o]}
+        scale = max(abs(x) for x in want.values()) + 1e-300
+        for o in want:
+            assert abs(got[r].get(o, 0.0) - want[o]) < (1e-10 if dk == 0 else 1e-6) * scale, (n, m, l, dk, o)
