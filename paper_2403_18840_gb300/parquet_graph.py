@@ -413,6 +413,39 @@ class Expanded:
         d.setdefault(key, []).extend(x)
 
 
+DIRECT, EXCHANGED = 0, 1       # a 4-point piece's fermion paths: in1 -> out1, or in1 -> out2
+LOOP = -2                      # a closed fermion loop: its sign and its spin sum
+
+
+def path_class(piece):
+    """(DIRECT or EXCHANGED, closed fermion loops inside) of a 4-point piece."""
+    succ, pred, _ = piece
+    v = pred.index(-1)
+    on_path = set()
+    while True:
+        on_path.add(v)
+        if succ[v] < 0:
+            cls = DIRECT if succ[v] == -1 else EXCHANGED
+            break
+        v = succ[v]
+    v = pred.index(-2)
+    while True:
+        on_path.add(v)
+        if succ[v] < 0:
+            break
+        v = succ[v]
+    loops, seen = 0, set(on_path)
+    for s0 in range(len(succ)):
+        if s0 in seen:
+            continue
+        loops += 1
+        v = s0
+        while v not in seen:
+            seen.add(v)
+            v = succ[v]
+    return cls, loops
+
+
 def route_piece(piece, leg_moms, n_var, ms, line_of):
     """Momentum routing of one diagram piece: leg momenta given
     ({('in'|'out', j): mom}), chords of a spanning tree carry the loop
@@ -553,14 +586,20 @@ class Evaluator:
             legs = (Kin, Kout, _add(p, _sub(Kout, Kin)), p)
             g4 = self.gamma4(i, legs, ms + 1, ts, None)
             m1, t1 = ms + 1 + i, ts + i + 1
-            pairs = {(u, w) for (_, _, u, w) in g4}
+            pairs = {(u, w) for (_, _, _, u, w) in g4}
             bubble = {}                          # [G G]^(M) from b to u and from w back to b
             for (u, w) in pairs:
                 for j in range(M + 1):
                     A.acc(bubble, (u, w), A.mul(self.chain(j, legs[2], b, u, m1, t1),
                                                 self.chain(M - j, p, w, b, m1 + j, t1 + j)))
-            for (x, o, u, w), val in g4.items():
-                A.acc(out, (x, o), A.mul(val, bubble[(u, w)]))
+            # a direct vertex (in2 -> out2) closes a fermion loop through b: -2
+            loop, through = {}, {}
+            for (cls, x, o, u, w), val in g4.items():
+                A.acc(loop if cls == DIRECT else through, (x, o), A.mul(val, bubble[(u, w)]))
+            for k, v in loop.items():
+                A.acc(out, k, A.scale(LOOP, v))
+            for k, v in through.items():
+                A.acc(out, k, v)
         return out
 
     # Gamma4 over (in1, out1, in2, out2) vertices; irr: None, 'ph' or 'pp'
@@ -590,8 +629,8 @@ class Evaluator:
         out = {}
         if N == 0:
             a, b = A.index(2 * ts), A.index(2 * ts + 1)
-            A.acc(out, (a, a, b, b), A.leaf_v(_sub(K1, K3), a, b))     # direct
-            A.acc(out, (a, b, b, a), A.leaf_v(_sub(K1, K4), a, b))     # exchanged
+            A.acc(out, (DIRECT, a, a, b, b), A.leaf_v(_sub(K1, K3), a, b))
+            A.acc(out, (EXCHANGED, a, b, b, a), A.leaf_v(_sub(K1, K4), a, b))
             return out
         leg_moms = {("in", 0): K1, ("out", 0): K3, ("in", 1): K2, ("out", 1): K4}
         polys = {}
@@ -607,10 +646,11 @@ class Evaluator:
             glob = {v: 2 * (ts + lines[min(v, partner[v])]) + (0 if v < partner[v] else 1) for v in range(len(succ))}
             leaves = route_piece(piece, leg_moms, self.n, ms, lambda v: A.index(glob[v]))
             lg = P._leg_vertices(piece)
-            idx = tuple(A.index(glob[lg[k]]) for k in (("in", 0), ("out", 0), ("in", 1), ("out", 1)))
+            cls, loops = path_class(piece)
+            idx = (cls,) + tuple(A.index(glob[lg[k]]) for k in (("in", 0), ("out", 0), ("in", 1), ("out", 1)))
             poly = polys.setdefault(idx, {})
             mono = tuple(sorted(leaves))
-            poly[mono] = poly.get(mono, 0) + w
+            poly[mono] = poly.get(mono, 0) + w * LOOP ** loops
         # the node's diagrams factorised together (greedy Horner, hash-consed)
         dag = fdgraph.DAG()
         dag.scope = None
@@ -660,7 +700,7 @@ class Evaluator:
         if c == "phbar":
             # the ph join with the composite's out-legs exchanged
             inner = self.phi("ph", N, (K1, K4, K2, K3), ms, ts)
-            return {(a, d, cc, b): v for (a, b, cc, d), v in inner.items()}
+            return {(1 - cls, a, d, cc, b): v for (cls, a, b, cc, d), v in inner.items()}
         p = _vec(self.n, ms)
         half = Fraction(1, 2) if c == "pp" else Fraction(1)
         for i in range(N):
@@ -676,41 +716,56 @@ class Evaluator:
                         L = self.gamma4(i, (K1, K3, P2, P1), mL, tL, None)
                         R = self.gamma4(j, (P1, P2, K2, K4), mR, tR, "ph")
                         # L[a,b,x,y] G(y->u) G(v->x) R[u,v,c,d]
-                        us = {u for (u, _, _, _) in R}
-                        vs = {v for (_, v, _, _) in R}
+                        us = {u for (_, u, _, _, _) in R}
+                        vs = {v for (_, _, v, _, _) in R}
                         M1 = {}
-                        for (a, b, x, y), lv in L.items():
+                        for (cl, a, b, x, y), lv in L.items():
                             for u in us:
-                                A.acc(M1, (a, b, x, u), A.mul(lv, self.chain(k, P1, y, u, m1, t1)))
+                                A.acc(M1, (cl, a, b, x, u), A.mul(lv, self.chain(k, P1, y, u, m1, t1)))
                         M2 = {}
-                        for (a, b, x, u), mv in M1.items():
+                        for (cl, a, b, x, u), mv in M1.items():
                             for v in vs:
-                                A.acc(M2, (a, b, u, v), A.mul(mv, self.chain(l, P2, v, x, m2, t2)))
-                        for (u, v, cc, d), rv in R.items():
-                            for (a, b, u2, v2), nv in M2.items():
-                                if (u2, v2) == (u, v):
-                                    A.acc(out, (a, b, cc, d), A.mul(nv, rv))
+                                A.acc(M2, (cl, a, b, u, v), A.mul(mv, self.chain(l, P2, v, x, m2, t2)))
+                        # both direct: L.in2 -> L.out2 -> R.in1 -> R.out1 -> L.in2 is a loop (-2);
+                        # both exchanged: exchanged; otherwise direct
+                        loop = {}
+                        for (cr, u, v, cc, d), rv in R.items():
+                            for (cl, a, b, u2, v2), nv in M2.items():
+                                if (u2, v2) != (u, v):
+                                    continue
+                                if cl == DIRECT and cr == DIRECT:
+                                    A.acc(loop, (DIRECT, a, b, cc, d), A.mul(nv, rv))
+                                else:
+                                    cls = EXCHANGED if (cl == EXCHANGED and cr == EXCHANGED) else DIRECT
+                                    A.acc(out, (cls, a, b, cc, d), A.mul(nv, rv))
+                        for key, v in loop.items():
+                            A.acc(out, key, A.scale(LOOP, v))
                     else:
                         P1, P2 = p, _sub(_add(K1, K2), p)
                         L = self.gamma4(i, (K1, P1, K2, P2), mL, tL, None)
                         R = self.gamma4(j, (P1, K3, P2, K4), mR, tR, "pp")
-                        # L[a,x,b,y] G(x->u) G(y->v) R[u,c,v,d] / 2
-                        us = {u for (u, _, _, _) in R}
-                        vs = {v for (_, _, v, _) in R}
+                        # L[a,x,b,y] G(x->u) G(y->v) R[u,c,v,d] / 2; no loop forms,
+                        # the composite is exchanged when exactly one part is
+                        us = {u for (_, u, _, _, _) in R}
+                        vs = {v for (_, _, _, v, _) in R}
                         M1 = {}
-                        for (a, x, b, y), lv in L.items():
+                        for (cl, a, x, b, y), lv in L.items():
                             for u in us:
-                                A.acc(M1, (a, b, y, u), A.mul(lv, self.chain(k, P1, x, u, m1, t1)))
+                                A.acc(M1, (cl, a, b, y, u), A.mul(lv, self.chain(k, P1, x, u, m1, t1)))
                         M2 = {}
-                        for (a, b, y, u), mv in M1.items():
+                        for (cl, a, b, y, u), mv in M1.items():
                             for v in vs:
-                                A.acc(M2, (a, b, u, v), A.mul(mv, self.chain(l, P2, y, v, m2, t2)))
-                        for (u, cc, v, d), rv in R.items():
-                            for (a, b, u2, v2), nv in M2.items():
+                                A.acc(M2, (cl, a, b, u, v), A.mul(mv, self.chain(l, P2, y, v, m2, t2)))
+                        for (cr, u, cc, v, d), rv in R.items():
+                            for (cl, a, b, u2, v2), nv in M2.items():
                                 if (u2, v2) == (u, v):
-                                    A.acc(out, (a, cc, b, d), A.scale(half, A.mul(nv, rv)))
+                                    A.acc(out, (cl ^ cr, a, cc, b, d), A.scale(half, A.mul(nv, rv)))
         return out
 
     def root(self):
-        """Sigma^(n)(k_ext) over its out-vertex (index)."""
-        return self.sigma(self.n, _vec(self.n, 0), 1, 0)
+        """Sigma^(n)(k_ext) over its out-vertex (index), with the sign
+        (-1)^n of its n interaction lines (the loops' -2 are inside)."""
+        out = self.sigma(self.n, _vec(self.n, 0), 1, 0)
+        if self.n % 2 == 0:
+            return out
+        return {k: self.alg.scale(-1, v) for k, v in out.items()}

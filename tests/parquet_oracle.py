@@ -6,6 +6,8 @@ the per-sample reference for a tape compiled from the construction, whose
 routing differs from the oracle's convention.  Only the line-to-momentum
 assignment comes from the construction, and the tests check it for
 momentum conservation at every vertex."""
+from fractions import Fraction
+
 import numpy as np
 
 from oracle import diagrams as od
@@ -65,8 +67,15 @@ def routed_diagrams(n, construction):
                 a, b, m = vl[i]
                 assert (a, b) == (2 * i, 2 * i + 1)
                 v_mom[i] = m
-            d = od.RoutedDiagram(n=n, sigma=tuple(succ), sign=float((-1) ** (n + F) * 2 ** F), out_vertex=out_v,
+            sign = (-1) ** (n + F) * 2 ** F
+            d = od.RoutedDiagram(n=n, sigma=tuple(succ), sign=float(sign), out_vertex=out_v,
                                  g_src=g_src, g_dst=g_dst, g_mom=g_mom, v_mom=v_mom, g_tau=g_tau)
             assert od.check_conservation(d) == 0
-            out.append((float(w), d))
+            # the graph's weight is the diagram's sign and spin factor times
+            # its share: 1, or 2^-k for the 2^k routings of a diagram with k
+            # nested pp joins
+            share = Fraction(w) / sign
+            assert share > 0 and (1 / share).denominator == 1 and ((1 / share).numerator & ((1 / share).numerator - 1)) == 0, \
+                (w, sign)
+            out.append((float(share), d))
     return out

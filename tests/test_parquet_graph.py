@@ -38,6 +38,24 @@ def _piece(n, out_v, mono):
     return tuple(succ), tuple(pred), tuple(partner)
 
 
+def _loops(piece):
+    """Closed fermion loops of a self-energy piece (cycles off the external path)."""
+    succ, pred, _ = piece
+    v, seen = pred.index(-1), set()
+    while v >= 0:
+        seen.add(v)
+        v = succ[v]
+    loops = 0
+    for s0 in range(len(succ)):
+        if s0 not in seen:
+            loops += 1
+            v = s0
+            while v not in seen:
+                seen.add(v)
+                v = succ[v]
+    return loops
+
+
 def _conserves(n, out_v, mono):
     net = np.zeros((2 * n, n + 1), dtype=int)
     net[0, 0] += 1                       # k_ext enters at the in-vertex
@@ -73,7 +91,10 @@ def test_graph_expands_to_the_diagrams_and_evaluates_them(construction, n):
             assert len(mono) == 3 * n - 1
             assert _conserves(n, o, mono)
             weights[P.canonical(_piece(n, o, mono))] += w
-    assert dict(weights) == construction.sigma(n)
+    # every diagram once, with its sign and spin factor (-1)^(n+F) 2^F
+    assert set(weights) == set(construction.sigma(n))
+    for key, w in weights.items():
+        assert w == (-1) ** (n + _loops(P.from_key(key))) * 2 ** _loops(P.from_key(key))
     g0, v = _leaf_functions(n, n)
     S = PG.Scalar(g0, v)
     compact = PG.Evaluator(n, S, construction).root()
