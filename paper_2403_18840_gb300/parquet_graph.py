@@ -727,19 +727,20 @@ class Evaluator:
                             for v in vs:
                                 A.acc(M2, (cl, a, b, u, v), A.mul(mv, self.chain(l, P2, v, x, m2, t2)))
                         # both direct: L.in2 -> L.out2 -> R.in1 -> R.out1 -> L.in2 is a loop (-2);
-                        # both exchanged: exchanged; otherwise direct
-                        loop = {}
+                        # both exchanged: exchanged; otherwise direct.  A direct L
+                        # therefore meets -2 R_direct + R_exchanged (formed once)
+                        rd = {}
                         for (cr, u, v, cc, d), rv in R.items():
-                            for (cl, a, b, u2, v2), nv in M2.items():
-                                if (u2, v2) != (u, v):
-                                    continue
-                                if cl == DIRECT and cr == DIRECT:
-                                    A.acc(loop, (DIRECT, a, b, cc, d), A.mul(nv, rv))
-                                else:
-                                    cls = EXCHANGED if (cl == EXCHANGED and cr == EXCHANGED) else DIRECT
-                                    A.acc(out, (cls, a, b, cc, d), A.mul(nv, rv))
-                        for key, v in loop.items():
-                            A.acc(out, key, A.scale(LOOP, v))
+                            A.acc(rd, (u, v, cc, d), A.scale(LOOP, rv) if cr == DIRECT else rv)
+                        for (cl, a, b, u, v), nv in M2.items():
+                            if cl == DIRECT:
+                                for (u2, v2, cc, d), rv in rd.items():
+                                    if (u2, v2) == (u, v):
+                                        A.acc(out, (DIRECT, a, b, cc, d), A.mul(nv, rv))
+                            else:
+                                for (cr, u2, v2, cc, d), rv in R.items():
+                                    if (u2, v2) == (u, v):
+                                        A.acc(out, (cr, a, b, cc, d), A.mul(nv, rv))
                     else:
                         P1, P2 = p, _sub(_add(K1, K2), p)
                         L = self.gamma4(i, (K1, P1, K2, P2), mL, tL, None)
