@@ -352,23 +352,28 @@ class DagEmit:
             d[key] = x
 
 
-def parquet_outputs(order, roots, construction=None):
+def parquet_outputs(order, roots, construction=None, share="root"):
     """(dag, outputs) for roots [(n, m, l, dk)] of an order-`order` tape from
     the Dyson-Schwinger / parquet graphs: Sigma^(n) in Taylor mode to total
     degree order - n (and first order in k_ext when any root has dk), root
     (n, m, l, dk) = m! l! times the (m, l, dk) coefficient, one output per
-    out line; one DAG shared by all roots."""
+    out line.  share: "root" (default) builds each root's graph on its own
+    (products and sums shared within the root only, as the compiler's own
+    tapes do; each root keeps only the Taylor coefficients it needs, so its
+    leaf families stay narrow and its temporaries die with it), "n" shares
+    within the roots of one Sigma^(n), "all" across every root."""
     import math
     C = construction or P.Construction()
     dag = fdgraph.DAG()
-    dag.scope = None
     with_dk = any(r[3] for r in roots)
     series = {}
     outputs = []
     for r, (n, m, l, dk) in enumerate(roots):
-        if n not in series:
-            series[n] = Evaluator(n, DagEmit(dag, order - n, order, with_dk), C).root()
-        for o, coefs in sorted(series[n].items()):
+        scope = {"root": (n, r), "n": n, "all": None}[share]
+        if (n, scope) not in series:
+            dag.scope = scope
+            series[(n, scope)] = Evaluator(n, DagEmit(dag, order - n, order, with_dk), C).root()
+        for o, coefs in sorted(series[(n, scope)].items()):
             if (m, l, dk) not in coefs:
                 continue
             node = coefs[(m, l, dk)]
@@ -379,9 +384,9 @@ def parquet_outputs(order, roots, construction=None):
     return dag, outputs
 
 
-def parquet_tape(order, roots, budget=96, bundle=4, window=32, construction=None):
+def parquet_tape(order, roots, budget=96, bundle=4, window=32, construction=None, share="root"):
     """The parquet graphs of the roots compiled into the tape format."""
-    dag, outputs = parquet_outputs(order, roots, construction)
+    dag, outputs = parquet_outputs(order, roots, construction, share)
     return fdgraph.compile_dag(order, roots, dag, outputs, budget, bundle, window)
 
 
