@@ -33,6 +33,8 @@ import math
 import numpy as np
 
 from . import fdgraph
+from . import parquet as P
+from . import parquet_graph as PG
 
 
 def sigma_dag(n, l=0):
@@ -156,8 +158,6 @@ def parquet_scaling_table(n, l_max, construction=None):
     """Rows (l, Taylor ops, nested ops) for Sigma^(n,0,l) on the Dyson-Schwinger
     / parquet evaluation graph (`parquet_graph`), the graph the paper's
     comparison uses; V-leaf series included."""
-    from . import parquet as P
-    from . import parquet_graph as PG
     C = construction or P.Construction()
     rows = []
     for l in range(l_max + 1):
@@ -174,8 +174,6 @@ def parquet_all_roots_ops(order, construction=None):
     Dyson-Schwinger / parquet graphs of Sigma^(1..order), each in Taylor mode
     in (mu, Lambda) to total degree order - n; leaves excluded.  Returns
     {n: ops} and the total."""
-    from . import parquet as P
-    from . import parquet_graph as PG
     C = construction or P.Construction()
     per = {}
     for n in range(1, order + 1):

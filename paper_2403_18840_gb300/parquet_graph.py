@@ -26,7 +26,10 @@ interaction line l has time variable l; its two ends are vertices 2l and
 2l + 1.
 """
 import collections
+import math
 from fractions import Fraction
+
+import numpy as np
 
 from . import fdgraph
 from . import parquet as P
@@ -148,7 +151,6 @@ class Series:
     at lam, everything else is constant in Lambda.  v(mom) returns (c, q^2)."""
 
     def __init__(self, g0, v, lam, L):
-        import numpy as np
         self.np, self.g0, self.v, self.lam, self.L = np, g0, v, lam, L
 
     def index(self, vertex):
@@ -362,7 +364,6 @@ def parquet_outputs(order, roots, construction=None, share="root"):
     tapes do; each root keeps only the Taylor coefficients it needs, so its
     leaf families stay narrow and its temporaries die with it), "n" shares
     within the roots of one Sigma^(n), "all" across every root."""
-    import math
     C = construction or P.Construction()
     dag = fdgraph.DAG()
     with_dk = any(r[3] for r in roots)
