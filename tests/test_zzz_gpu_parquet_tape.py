@@ -50,7 +50,7 @@ def _reference(order, roots, x, construction):
     return out, mag
 
 
-@pytest.mark.parametrize("order,with_dk,n", [(2, True, 3001), (3, True, 2049), (4, False, 700)])
+@pytest.mark.parametrize("order,with_dk,n", [(2, True, 3001), (3, True, 2049), (4, False, 700), (5, False, 513)])
 def test_parquet_tape_per_sample_parity(api, construction, order, with_dk, n):
     roots = fdgraph.graph_roots(order, with_dk=with_dk)
     tape = PG.parquet_tape(order, roots, construction=construction).to_bytes()
