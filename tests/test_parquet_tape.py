@@ -205,3 +205,22 @@ def test_parquet_tape_with_oracle_leaves_equals_the_oracle(construction, order, 
             # the terms cancel: compare on the scale of their L1 magnitude
             for line, v in want.items():
                 assert abs(got[r].get(line, 0.0) - v) <= 1e-12 * l1, (s, n, m, l, dk, line)
+
+
+def test_parquet_tape_specialised_source_compiles(construction, tmp_path):
+    # the run-time code generator accepts a parquet tape and its kernel
+    # source compiles for sm_103a (cross-compiled here)
+    import os
+    import shutil
+    import subprocess
+    from paper_2403_18840_gb300 import api
+    if shutil.which("nvcc") is None:
+        pytest.skip("nvcc not available")
+    tape = PG.parquet_tape(3, fdgraph.graph_roots(3, with_dk=True), construction=construction).to_bytes()
+    src, _ = api.jit_source(tape, 0, threads=128, min_blocks=2, max_modules=1)
+    f = tmp_path / "m0.cu"
+    f.write_text(src)
+    csrc = os.path.join(os.path.dirname(os.path.abspath(PG.__file__)), "csrc")
+    r = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-cubin",
+                        "-I", csrc, "-o", str(tmp_path / "m0.cubin"), str(f)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
