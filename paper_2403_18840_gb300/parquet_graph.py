@@ -569,8 +569,10 @@ class Evaluator:
         a, b = A.index(2 * ts), A.index(2 * ts + 1)
         out = {}
         for i in range(N):
-            g3 = self.gamma3(i, _sub(K, q), K, ms + 1, ts + 1, b)
-            vline = {x: A.mul(A.leaf_v(q, a, b), self.chain(N - i - 1, _sub(K, q), a, x, ms + 1 + i, ts + 1 + i))
+            # the loop momentum runs on the bare line into Gamma3, the
+            # interaction line a -> b carries the rest
+            g3 = self.gamma3(i, q, K, ms + 1, ts + 1, b)
+            vline = {x: A.mul(A.leaf_v(_sub(K, q), a, b), self.chain(N - i - 1, q, a, x, ms + 1 + i, ts + 1 + i))
                      for x in {x for (x, _) in g3}}
             for (x, o), val in g3.items():
                 A.acc(out, o, A.mul(vline[x], val))
