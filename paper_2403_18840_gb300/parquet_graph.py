@@ -599,7 +599,7 @@ class Evaluator:
             for (u, w) in pairs:
                 for j in range(M + 1):
                     A.acc(bubble, (u, w), A.mul(self.chain(j, legs[2], b, u, m1, t1),
-                                                self.chain(M - j, p, w, b, m1 + j, t1 + j)))
+                                                self.chain(M - j, legs[3], w, b, m1 + j, t1 + j)))
             # a direct vertex (in2 -> out2) closes a fermion loop through b: -2
             loop, through = {}, {}
             for (cls, x, o, u, w), val in g4.items():
