@@ -126,6 +126,9 @@ fd_status validate_tape(const uint8_t *buf, size_t len, TapeHeader &h) {
                     ok = f != 2u && (j <= N || f == 0u);
                 }
                 if (op == OP_GLEAF) ok = ok && la < N && lb < N;
+                // above the d/dk flag: only a G leaf's FP64 flag
+                ok = ok && (w >> (FD_LEAF_PRECISE_BIT + 1)) == 0 &&
+                     (op == OP_GLEAF || ((w >> FD_LEAF_PRECISE_BIT) & 1u) == 0);
                 break;
             }
             case OP_RACC: ok = a < S && b < N; break;
@@ -188,6 +191,16 @@ extern "C" fd_status fd_graph_load(const void *buf, size_t len, fd_graph **out) 
         cudaFree(g->d_roots);
         delete g;
         return fd::cuda_error(e, "graph upload");
+    }
+    // the sampler map's table on this device, filled here (before any stream
+    // capture of an evaluation)
+    const FdTab4 *tab = nullptr;
+    const fd_status ts = fd::sc_table(&tab);
+    if (ts != FD_OK) {
+        cudaFree(g->d_tape);
+        cudaFree(g->d_roots);
+        delete g;
+        return ts;
     }
     *out = g;
     return FD_OK;

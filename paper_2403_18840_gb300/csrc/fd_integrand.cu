@@ -86,7 +86,9 @@ struct Slots {
 // register-resident per-sample variables
 template <int P>
 struct Vars {
-    float kx[NK][P], ky[NK][P], kz[NK][P];     // loop momenta k_1..k_N
+    float kx[NK][P], ky[NK][P], kz[NK][P];     // loop momenta k_1..k_N: grid parts
+    float kxl[NK][P], kyl[NK][P], kzl[NK][P];  // and remainders
+    float tl[NK][P];                           // remainders of the times of interaction lines 0..N-1 (hi: slots 2..)
     float re[P], im[P], hsum[P];               // root accumulator and |f| sum for VEGAS
 };
 
@@ -103,26 +105,33 @@ __device__ __forceinline__ uint32_t f_a(uint64_t w) { return (uint32_t)(w >> 20)
 __device__ __forceinline__ uint32_t f_b(uint64_t w) { return (uint32_t)(w >> 34) & 16383u; }
 __device__ __forceinline__ uint32_t f_c(uint64_t w) { return (uint32_t)(w >> 48) & 16383u; }
 
-// signed momentum sum from a 2-bit-per-variable mask; k_ext is (0, 0, kext)
+// signed momentum sums from a 2-bit-per-variable mask, grid parts (h) and
+// remainders (l); k_ext is (0, 0, kext + kext_l)
 template <int P>
-__device__ __forceinline__ void momentum(const Vars<P> &V, uint32_t mask, float kext, float (&px)[P],
-                                         float (&py)[P], float (&pz)[P], float &ks) {
+__device__ __forceinline__ void momentum(const Vars<P> &V, uint32_t mask, const InstDesc &D, float (&h)[3][P],
+                                         float (&l)[3][P], float &ks) {
     float cf[NK + 1];
 #pragma unroll
     for (int j = 0; j <= NK; ++j) cf[j] = (float)(((int)(mask << (30 - 2 * j))) >> 30);   // signed 2-bit field
     ks = cf[0];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        float x = 0.0f, y = 0.0f, z = cf[0] * kext;
+        float x = 0.0f, y = 0.0f, z = cf[0] * D.kext, xl = 0.0f, yl = 0.0f, zl = cf[0] * D.kext_l;
 #pragma unroll
         for (int j = 0; j < NK; ++j) {
-            x = fmaf(cf[j + 1], V.kx[j][p], x);
+            x = fmaf(cf[j + 1], V.kx[j][p], x);                 // exact: grid values, coefficients 0, +-1
             y = fmaf(cf[j + 1], V.ky[j][p], y);
             z = fmaf(cf[j + 1], V.kz[j][p], z);
+            xl = fmaf(cf[j + 1], V.kxl[j][p], xl);
+            yl = fmaf(cf[j + 1], V.kyl[j][p], yl);
+            zl = fmaf(cf[j + 1], V.kzl[j][p], zl);
         }
-        px[p] = x;
-        py[p] = y;
-        pz[p] = z;
+        h[0][p] = x;
+        h[1][p] = y;
+        h[2][p] = z;
+        l[0][p] = xl;
+        l[1][p] = yl;
+        l[2][p] = zl;
     }
 }
 
@@ -134,16 +143,25 @@ __device__ __forceinline__ void g_leaf(const Slots<T, P> &S, const Vars<P> &V, u
     const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
     const int M = (int)((w >> 40) & 7u);
     const int dk = (int)((w >> 43) & 1u);
-    float px[P], py[P], pz[P], ks;
-    momentum(V, mask, D.kext, px, py, pz, ks);
+    const bool precise = (w >> FD_LEAF_PRECISE_BIT) & 1u;
+    float h[3][P], l[3][P], ks;
+    momentum(V, mask, D, h, l, ks);
     float ta[P], tb[P];
     S.load(2 + la, ta);                        // hypercube time of the two lines
     S.load(2 + lb, tb);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const float p2 = fmaf(px[p], px[p], fmaf(py[p], py[p], pz[p] * pz[p]));
-        g_family(p2, pz[p], ks, ta[p] - tb[p], D.beta, D.mu, M, dk,
-                 [&](int j, float v) { S.store1(d + j, p, v); });
+        float dxh, dxl;
+        fd_time_diff(ta[p], pick(V.tl, la, p), tb[p], pick(V.tl, lb, p), dxh, dxl);
+        if (precise) {
+            g_family_precise((double)h[0][p], (double)h[1][p], (double)h[2][p], (double)l[0][p], (double)l[1][p],
+                             (double)l[2][p], ks, dxh, dxl, (double)D.beta + (double)D.beta_l,
+                             (double)D.mu + (double)D.mu_l, M, dk, [&](int j, float v) { S.store1(d + j, p, v); });
+            continue;
+        }
+        const float eps = fd_eps(h[0][p], h[1][p], h[2][p], l[0][p], l[1][p], l[2][p], D.mu, D.mu_l);
+        g_family<float>(eps, h[2][p] + l[2][p], ks, dxh, dxl, D.beta, M, dk,
+                        [&](int j, float v) { S.store1(d + j, p, v); });
     }
 }
 
@@ -152,12 +170,13 @@ __device__ __forceinline__ void v_leaf(const Slots<T, P> &S, const Vars<P> &V, u
     const uint32_t d = f_d(w), mask = f_a(w);
     const int L = (int)((w >> 40) & 7u);
     const int dk = (int)((w >> 43) & 1u);
-    float px[P], py[P], pz[P], ks;
-    momentum(V, mask, D.kext, px, py, pz, ks);
+    float h[3][P], l[3][P], ks;
+    momentum(V, mask, D, h, l, ks);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const float q2 = fmaf(px[p], px[p], fmaf(py[p], py[p], pz[p] * pz[p]));
-        v_family(q2, pz[p], ks, D.Lambda, L, dk, [&](int j, float v) { S.store1(d + j, p, v); });
+        const float qx = h[0][p] + l[0][p], qy = h[1][p] + l[1][p], qz = h[2][p] + l[2][p];
+        const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+        v_family<float>(q2, qz, ks, D.Lambda, L, dk, [&](int j, float v) { S.store1(d + j, p, v); });
     }
 }
 
@@ -294,12 +313,12 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int64_t i = idx[p];
-        float x[FD_MAX_DIM];
+        FdDF x[FD_MAX_DIM];
         float wgt = 1.0f;
         if (D.points) {
 #pragma unroll
             for (int d = 0; d < FD_MAX_DIM; ++d)
-                if (d < dim) x[d] = D.points[(int64_t)d * A.n_per_inst + i];
+                if (d < dim) x[d] = FdDF{D.points[(int64_t)d * A.n_per_inst + i], 0.0f};
             wgt = D.point_w ? D.point_w[i] : 1.0f;
         } else {
             const uint32_t c0 = (uint32_t)(uint64_t)i, c1 = (uint32_t)((uint64_t)i >> 32);
@@ -311,7 +330,7 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
                     const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (4 * blk + q < FD_MAX_DIM) x[4 * blk + q] = word_to_uniform(wv[q]);
+                        if (4 * blk + q < FD_MAX_DIM) x[4 * blk + q] = FdDF{word_to_uniform(wv[q]), 0.0f};
                 }
             }
         }
@@ -320,39 +339,36 @@ __device__ __forceinline__ void prologue(const Slots<T, P> &S, Vars<P> &V, const
         for (int d = 0; d < FD_MAX_DIM; ++d) {
             jd[d] = 1.0f;
             if (d < dim && D.edges) {
-                const int nb = D.n_bins;
-                const float y = x[d] * (float)nb;
-                const int bin = min((int)y, nb - 1);
-                const float *e = D.edges + (int64_t)d * (nb + 1);
-                const float lo = __ldg(e + bin), hi = __ldg(e + bin + 1);
-                x[d] = fmaf(y - (float)bin, hi - lo, lo);
-                jd[d] = (float)nb * (hi - lo);
+                const int bin = fd_vegas_df(x[d].hi, D.n_bins, D.edges + (int64_t)d * (D.n_bins + 1), x[d], jd[d]);
                 S.store1(D.n_slots + d, p, __int_as_float(bin));
             }
         }
+        const float g = D.grid, ginv = 1.0f / D.grid;
         float jac = wgt;
+        V.tl[0][p] = 0.0f;
 #pragma unroll
         for (int j = 0; j < NK; ++j) {
-            V.kx[j][p] = 0.0f;
-            V.ky[j][p] = 0.0f;
-            V.kz[j][p] = 0.0f;
+            V.kx[j][p] = V.ky[j][p] = V.kz[j][p] = 0.0f;
+            V.kxl[j][p] = V.kyl[j][p] = V.kzl[j][p] = 0.0f;
+            if (j >= 1) V.tl[j][p] = 0.0f;
             const int jj = j + 1;                       // loop momentum k_jj
             if (jj <= N) {
                 const int c0 = (jj == 1) ? 0 : 4 * jj - 5;
-                const float xa = x[c0], xb = x[c0 + 1], xc = x[c0 + 2];
-                const float r = D.kc * xa;
-                const float cth = fmaf(2.0f, xb, -1.0f);
-                const float sth = 2.0f * sqrtf(xb * (1.0f - xb));
-                float sp, cp;
-                sincospif(2.0f * xc, &sp, &cp);
-                V.kx[j][p] = r * sth * cp;
-                V.ky[j][p] = r * sth * sp;
-                V.kz[j][p] = r * cth;
+                float kh[3], kl[3];
+                const float r =
+                    fd_loop_momentum(x[c0], x[c0 + 1], x[c0 + 2], FdDF{D.kc, D.kc_l}, A.sc_tab, g, ginv, kh, kl);
+                V.kx[j][p] = kh[0];
+                V.ky[j][p] = kh[1];
+                V.kz[j][p] = kh[2];
+                V.kxl[j][p] = kl[0];
+                V.kyl[j][p] = kl[1];
+                V.kzl[j][p] = kl[2];
                 jac *= D.kc * r * r * FD_INV_2PI2;
                 jac *= jd[c0] * jd[c0 + 1] * jd[c0 + 2];   // 1 without a map
                 if (jj >= 2) {
                     // time of interaction line jj - 1
-                    S.store1(2 + jj - 1, p, x[4 * jj - 2]);   // time of interaction line jj - 1
+                    S.store1(2 + jj - 1, p, x[4 * jj - 2].hi);
+                    V.tl[jj - 1][p] = x[4 * jj - 2].lo;
                     jac *= D.beta;
                     jac *= jd[4 * jj - 2];
                 }
@@ -549,21 +565,46 @@ int dev_of_call() {
     return cudaGetDevice(&d) == cudaSuccess ? d : -1;
 }
 
-// Shared body of the evaluation entry points: validate, build the launch
-// descriptors and launch the integrand kernel.  `status` is the device word a
-// kernel sets when a bounded wait gives up (may be null).
-fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_params *params,
-                    const int32_t *graph_of_inst, int32_t n_inst, fd_vegas *const *maps,
-                    const float *points, const float *point_w, uint64_t seed, uint64_t iter,
-                    const uint32_t *iter_dev, int64_t n_per_inst, double *partials, float *per_sample_f,
-                    int *status, cudaStream_t stream) {
+// The instance's FP64 parameters as FP32 parts for the kernels' double-float
+// kinematics: the grid g is the power of two with max(K_c, k_ext) / g in
+// [2^12, 2^13), so every loop-momentum component and k_ext is a multiple of g
+// plus a remainder |.| <= g / 2, and sums of up to eight grid parts are exact
+// in FP32; mu is split on the grid g^2 (its grid part is exact in FP32 for the
+// electron gas, mu = k_F^2 = (K_c / 6)^2), beta and K_c into FP32 roundings
+// and remainders.
+void set_kinematics(InstDesc &D, const fd_params &p) {
+    int e = 0;
+    (void)std::frexp(std::max(p.k_cut, p.k_ext), &e);
+    const double g = std::ldexp(1.0, e - 13), g2 = g * g;
+    const double kh = std::rint(p.k_ext / g) * g;
+    const double mh = (double)(float)(std::rint(p.mu / g2) * g2);
+    D.grid = (float)g;
+    D.kext = (float)kh;
+    D.kext_l = (float)(p.k_ext - kh);
+    D.mu = (float)mh;
+    D.mu_l = (float)(p.mu - mh);
+    D.beta = (float)p.beta;
+    D.beta_l = (float)(p.beta - (double)D.beta);
+    D.kc = (float)p.k_cut;
+    D.kc_l = (float)(p.k_cut - (double)D.kc);
+    D.Lambda = (float)p.Lambda;
+}
+
+// Validation and launch descriptors of an evaluation call (no CUDA work
+// beyond device queries): every argument error is reported here, before the
+// caller touches any device memory.  `status` is the device word a kernel sets
+// when a bounded wait gives up (may be null).
+fd_status eval_build(const fd_graph *const *graphs, int32_t n_graphs, const fd_params *params,
+                     const int32_t *graph_of_inst, int32_t n_inst, fd_vegas *const *maps,
+                     const float *points, const float *point_w, uint64_t seed, uint64_t iter,
+                     const uint32_t *iter_dev, int64_t n_per_inst, double *partials, float *per_sample_f,
+                     int *status, EvalArgs &args) {
     FD_REQUIRE(graphs && n_graphs > 0, "graphs must be a non-empty array");
     FD_REQUIRE(params && graph_of_inst, "params and graph_of_inst are required");
     FD_REQUIRE(n_inst > 0 && n_inst <= FD_MAX_INST, "n_inst must be in [1, 256]");
     FD_REQUIRE(n_per_inst > 0 && n_per_inst <= (int64_t(1) << 40), "n_per_inst out of range");
     FD_REQUIRE(partials, "partials buffer is required");
     FD_REQUIRE(point_w == nullptr || points != nullptr, "point_w needs points");
-    static EvalArgs args;   // large (kernel parameter space); built on the host per call
     args.n_inst = n_inst;
     args.n_per_inst = n_per_inst;
     args.tile = fd_tile_samples(n_per_inst);
@@ -606,11 +647,7 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
         D.order = (int32_t)G->hdr.order;
         D.dim = (int32_t)G->hdr.dim;
         D.n_roots = (int32_t)G->hdr.n_roots;
-        D.kext = (float)p.k_ext;
-        D.mu = (float)p.mu;
-        D.beta = (float)p.beta;
-        D.Lambda = (float)p.Lambda;
-        D.kc = (float)p.k_cut;
+        set_kinematics(D, p);
         D.id = j;
         D.edges = nullptr;
         D.hist = nullptr;
@@ -631,13 +668,24 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
     }
     args.queue = reinterpret_cast<unsigned long long *>(
         partials + fd_partials_count(n_inst, r_max, n_per_inst) - 1);
-    // instances whose graph has a specialised kernel run as one launch per
-    // graph (stream-ordered, so they can share the work counter); the rest go
-    // through the interpreter in one launch
+    for (int g = 0; g < n_graphs; ++g)
+        if (graphs[g]->jit_enabled && graphs[g]->jit_kernel)
+            FD_REQUIRE(graphs[g]->device == dev_of_call(), "graph belongs to another device");
+    return fd::sc_table(&args.sc_tab);
+}
+
+// Launches of a built call: instances whose graph has a specialised kernel
+// run as one launch per graph (stream-ordered, so they can share the work
+// counter); the rest go through the interpreter in one launch.  The
+// descriptors live in per-host-thread storage, so calls from several host
+// threads do not share them.
+fd_status eval_run(const fd_graph *const *graphs, int32_t n_graphs, const int32_t *graph_of_inst, EvalArgs &args,
+                   cudaStream_t stream) {
+    const int32_t n_inst = args.n_inst;
     bool any_jit = false;
     for (int g = 0; g < n_graphs; ++g) any_jit = any_jit || (graphs[g]->jit_enabled && graphs[g]->jit_kernel);
     if (any_jit) {
-        static EvalArgs sub;
+        static thread_local EvalArgs sub;
         std::vector<int> rest;
         for (int g = 0; g < n_graphs; ++g) {
             std::vector<int> members;
@@ -649,7 +697,6 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
                 rest.insert(rest.end(), members.begin(), members.end());
                 continue;
             }
-            FD_REQUIRE(G->device == dev_of_call(), "graph belongs to another device");
             sub = args;
             sub.n_inst = (int32_t)members.size();
             for (size_t k = 0; k < members.size(); ++k) {
@@ -709,6 +756,19 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
     if (bt == 64 && bp == 1) return launch_eval<64, 1>(args, stream, items);
     return fd::set_error(FD_ENOTSUP, "per-sample state of " + std::to_string(args.slots_total) +
                                          " slots does not fit in shared memory with any CTA shape");
+}
+
+// Shared body of the evaluation entry points: validate and build, then launch.
+fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_params *params,
+                    const int32_t *graph_of_inst, int32_t n_inst, fd_vegas *const *maps,
+                    const float *points, const float *point_w, uint64_t seed, uint64_t iter,
+                    const uint32_t *iter_dev, int64_t n_per_inst, double *partials, float *per_sample_f,
+                    int *status, cudaStream_t stream) {
+    static thread_local EvalArgs args;   // large (kernel parameter space)
+    const fd_status st = eval_build(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed,
+                                    iter, iter_dev, n_per_inst, partials, per_sample_f, status, args);
+    if (st != FD_OK) return st;
+    return eval_run(graphs, n_graphs, graph_of_inst, args, stream);
 }
 }  // namespace
 
@@ -794,6 +854,43 @@ extern "C" fd_status fd_accumulate(const double *partials, int32_t n_inst, int32
     return FD_OK;
 }
 
+// ---- the sampler map's cosine / sine table ---------------------------------------
+// cos and sin of 2 pi n / 256, n = 0..256, each as a double-float pair (FP64
+// libm values split into FP32 hi + lo), in every device's global memory; the
+// double-float map (fd_sincos2pi_df) reads it.  Filled once per device, at
+// the first graph load on that device (before any stream capture).
+namespace {
+__device__ __align__(16) FdTab4 g_sc_tab[257];
+const FdTab4 *g_sc_tab_dev[64];
+std::mutex g_sc_mu;
+}  // namespace
+
+namespace fd {
+fd_status sc_table(const FdTab4 **out) {
+    int dev = 0;
+    FD_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fd::set_error(FD_ENOTSUP, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_sc_mu);
+    if (!g_sc_tab_dev[dev]) {
+        FdTab4 h[257];
+        for (int n = 0; n <= 256; ++n) {
+            const double a = 2.0 * M_PI * (double)n / 256.0;
+            const double c = std::cos(a), sn = std::sin(a);
+            h[n].x = (float)c;
+            h[n].y = (float)(c - (double)h[n].x);
+            h[n].z = (float)sn;
+            h[n].w = (float)(sn - (double)h[n].z);
+        }
+        FD_CHECK_CUDA(cudaMemcpyToSymbol(g_sc_tab, h, sizeof h));
+        void *p = nullptr;
+        FD_CHECK_CUDA(cudaGetSymbolAddress(&p, g_sc_tab));
+        g_sc_tab_dev[dev] = static_cast<const FdTab4 *>(p);
+    }
+    *out = g_sc_tab_dev[dev];
+    return FD_OK;
+}
+}  // namespace fd
+
 // ---- evaluation without device allocation ---------------------------------------
 // Callers that cannot allocate device memory themselves (a host process whose
 // allocations must all be made up front, a CUDA-graph replay that may not add
@@ -854,11 +951,16 @@ extern "C" fd_status fd_integrand_eval_stats_noalloc(
     fd_status st = noalloc_setup(&partials);
     if (st != FD_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    // every argument is checked before the shared array is written: a rejected
+    // call leaves an earlier call's partial sums alone
+    static thread_local EvalArgs args;
+    st = eval_build(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, nullptr,
+                    n_per_inst, partials, per_sample_f, nullptr, args);
+    if (st != FD_OK) return st;
     // every byte 0xFF is a NaN double: a tile the kernel failed to write shows up
     // as NaN in `out` instead of a stale value from an earlier call
     FD_CHECK_CUDA(cudaMemsetAsync(partials, 0xFF, (size_t)need * sizeof(double), s));
-    st = eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, nullptr,
-                   n_per_inst, partials, per_sample_f, nullptr, s);
+    st = eval_run(graphs, n_graphs, graph_of_inst, args, s);
     if (st != FD_OK) return st;
     return fd_accumulate(partials, n_inst, r_max, n_per_inst, out, stream);
 }

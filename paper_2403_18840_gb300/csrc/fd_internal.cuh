@@ -29,9 +29,12 @@ fd_status cuda_error(cudaError_t e, const char *what);
 // device-side status word (one per device, zero when healthy)
 int *device_status_word();
 
+// the sampler map's cos / sin table on the current device (filled on first use)
+fd_status sc_table(const FdTab4 **out);
+
 }  // namespace fd
 
-// ---- tape format, version 3 (mirrors paper_2403_18840_gb300/fdgraph.py) ----------
+// ---- tape format, version 4 (mirrors paper_2403_18840_gb300/fdgraph.py) ----------
 enum : uint32_t {
     OP_FMA = 1,      // reserved (products and sums travel in bundles)
     OP_GLEAF = 2,    // G0 Taylor family from a momentum mask and two interaction lines
@@ -45,7 +48,7 @@ enum : uint32_t {
 };
 
 constexpr uint32_t TAPE_MAGIC = 0x50544446u;  // 'FDTP'
-constexpr uint32_t TAPE_VERSION = 3;
+constexpr uint32_t TAPE_VERSION = 4;
 constexpr int FD_CHUNK_WORDS = 1024;  // tape chunk staged in shared memory; bundles never straddle one
 constexpr int FD_MAX_BUNDLE = 8;
 

@@ -45,7 +45,7 @@ const char kRuntimeHeader[] =
 #include "fd_jit_rt.inc"
     ;
 
-constexpr int kJitVersion = 3;              // bump when the generated code changes meaning
+constexpr int kJitVersion = 4;              // bump when the generated code changes meaning
 constexpr double kSingleModuleCost = 3500;  // below this the graph compiles as one module
 
 // ---- run-time compiler entry points (resolved with dlopen on first use) ---------
@@ -239,26 +239,47 @@ std::string fnum(float f) {
     return buf;
 }
 
-// signed momentum sums of a 2-bit-per-variable mask: (x, y, z, k_ext coefficient)
-void momentum_expr(uint32_t mask, int N, std::string &x, std::string &y, std::string &z, std::string &ks) {
+// signed momentum sums of a 2-bit-per-variable mask: grid parts (x, y, z),
+// remainders (xl, yl, zl) and the k_ext coefficient.  cast: a prefix for the
+// remainder terms ("(double)" in the FP64 families).
+struct MomExpr {
+    std::string x, y, z, xl, yl, zl, ks;
+};
+
+MomExpr momentum_expr(uint32_t mask, int N, const std::string &cast = "") {
     auto coef = [&](int j) { return (int)(((int32_t)(mask << (30 - 2 * j))) >> 30); };
     // -a + b is written b - a (the same value bit for bit, and one operation
     // fewer in the packed code); the order of the later terms is kept
-    auto sum = [&](const char *comp, bool with_ext) {
+    auto sum = [&](const char *comp, const char *ext, const std::string &pre) {
         std::vector<std::pair<int, std::string>> terms;
-        if (with_ext && coef(0)) terms.push_back({coef(0), "V.kext"});
+        if (ext && coef(0)) terms.push_back({coef(0), pre + ext});
         for (int j = 1; j <= N; ++j)
-            if (coef(j)) terms.push_back({coef(j), std::string("V.") + comp + "[" + std::to_string(j - 1) + "]"});
+            if (coef(j)) terms.push_back({coef(j), pre + "V." + comp + "[" + std::to_string(j - 1) + "]"});
         if (terms.empty()) return std::string("0.0f");
         if (terms.size() >= 2 && terms[0].first < 0 && terms[1].first > 0) std::swap(terms[0], terms[1]);
         std::string e = (terms[0].first > 0 ? "" : "-") + terms[0].second;
         for (size_t i = 1; i < terms.size(); ++i) e += (terms[i].first > 0 ? " + " : " - ") + terms[i].second;
         return e;
     };
-    x = sum("kx", false);
-    y = sum("ky", false);
-    z = sum("kz", true);
-    ks = coef(0) > 0 ? "1.0f" : coef(0) < 0 ? "-1.0f" : "0.0f";
+    MomExpr m;
+    m.x = sum("kx", nullptr, "");
+    m.y = sum("ky", nullptr, "");
+    m.z = sum("kz", "Q.kexth", "");
+    m.xl = sum("kxl", nullptr, cast);
+    m.yl = sum("kyl", nullptr, cast);
+    m.zl = sum("kzl", "Q.kextl", cast);
+    m.ks = coef(0) > 0 ? "1.0f" : coef(0) < 0 ? "-1.0f" : "0.0f";
+    return m;
+}
+
+// time difference t_a - t_b of a G leaf's interaction lines as (dxh, dxl)
+std::string time_diff_expr(uint32_t la, uint32_t lb, const std::string &vt) {
+    const std::string a = std::to_string(la), b = std::to_string(lb);
+    if (la == lb) return "    const " + vt + " dxh = 0.0f, dxl = 0.0f;\n";
+    if (lb == 0) return "    const " + vt + " dxh = V.t[" + a + "], dxl = V.tl[" + a + "];\n";
+    if (la == 0) return "    const " + vt + " dxh = -V.t[" + b + "], dxl = -V.tl[" + b + "];\n";
+    return "    " + vt + " dxh, dxl;\n    fd_time_diff(V.t[" + a + "], V.tl[" + a + "], V.t[" + b + "], V.tl[" + b +
+           "], dxh, dxl);\n";
 }
 
 // sync_every > 0: a block barrier after every sync_every arithmetic
@@ -276,7 +297,7 @@ std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, cons
     cur[0] = "0.0f";
     cur[1] = "1.0f";
     for (int j = 0; j < N; ++j) cur[2 + j] = "V.t[" + std::to_string(j) + "]";
-    o << qual << " " << vt << " fd_s" << q << "(const FdSVT<" << vt << "> &V) {\n";
+    o << qual << " " << vt << " fd_s" << q << "(const FdSVT<" << vt << ", " << N << "> &V, const FdPar &Q) {\n";
     int k = 0, since_sync = 0;
     for (const auto &kv : s.keep) {
         const TIns &t = ins[kv.first];
@@ -308,31 +329,75 @@ std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, cons
             const uint32_t d = fd_(w), mask = fa(w);
             const int no = leaf_outputs(w);
             const int M = (int)((w >> 40) & 7u), dk = (int)((w >> 43) & 1u);
-            std::string x, y, z, ks;
-            momentum_expr(mask, N, x, y, z, ks);
+            const bool precise = t.op == OP_GLEAF && ((w >> FD_LEAF_PRECISE_BIT) & 1u);
+            const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
+            const MomExpr me = momentum_expr(mask, N, precise ? "(double)" : "");
             const std::string nm = "l" + std::to_string(k++);
+            const std::string hi = "    const " + vt + " pxh = " + me.x + ", pyh = " + me.y + ", pzh = " + me.z + ";\n";
+            if (precise) {
+                // FP64 family (the single G line of the order-1 diagram), per sample (packed: per lane)
+                o << "  " << vt << " " << nm << "[" << no << "];\n  {\n" << hi << time_diff_expr(la, lb, vt)
+                  << "    const double bt = (double)Q.beta + (double)Q.betal, mu = (double)Q.muh + (double)Q.mul;\n";
+                const int lanes = vt == "float" ? 1 : 2;
+                for (int q = 0; q < lanes; ++q) {
+                    const std::string L = vt == "float" ? "" : ".v." + std::string(q ? "y" : "x");
+                    const MomExpr ml = momentum_expr(mask, N, "(double)");
+                    auto lane = [&](const std::string &e) {
+                        if (vt == "float") return e;
+                        // packed operands: take this lane of every V member
+                        std::string r = e, out;
+                        size_t pos = 0;
+                        while (true) {
+                            const size_t a = r.find("]", pos);
+                            if (a == std::string::npos) break;
+                            out += r.substr(pos, a + 1 - pos) + L;
+                            pos = a + 1;
+                        }
+                        return out + r.substr(pos);
+                    };
+                    o << "    g_family_precise((double)" << (vt == "float" ? "pxh" : "pxh" + L) << ", (double)"
+                      << (vt == "float" ? "pyh" : "pyh" + L) << ", (double)" << (vt == "float" ? "pzh" : "pzh" + L)
+                      << ", " << lane(ml.xl) << ", " << lane(ml.yl) << ", " << lane(ml.zl) << ", " << me.ks << ", "
+                      << (vt == "float" ? "dxh" : "dxh" + L) << ", " << (vt == "float" ? "dxl" : "dxl" + L)
+                      << ", bt, mu, " << M << ", " << dk << ", [&](int j, float v) { ";
+                    if (vt == "float")
+                        o << nm << "[j] = v; });\n";
+                    else
+                        o << nm << "[j].v." << (q ? "y" : "x") << " = v; });\n";
+                }
+                o << "  }\n";
+                for (int j = 0; j < no; ++j) cur[d + j] = nm + "[" + std::to_string(j) + "]";
+                continue;
+            }
+            const std::string lo =
+                "    const " + vt + " pxl = " + me.xl + ", pyl = " + me.yl + ", pzl = " + me.zl + ";\n";
             if (leaf_calls) {
-                o << "  FdLeafOut<" << no << "> " << nm << ";\n  {\n    const float px = " << x << ", py = " << y
-                  << ", pz = " << z << ";\n    const float p2 = fmaf(px, px, fmaf(py, py, pz * pz));\n";
+                o << "  FdLeafOut<" << no << "> " << nm << ";\n  {\n" << hi << lo;
                 if (t.op == OP_GLEAF) {
-                    const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
-                    o << "    " << nm << " = g_leaf_fn<" << M << ", " << dk << ">(p2, pz, " << ks << ", V.t[" << la
-                      << "] - V.t[" << lb << "], V.beta, V.mu);\n  }\n";
+                    o << time_diff_expr(la, lb, "float")
+                      << "    const float eps = fd_eps(pxh, pyh, pzh, pxl, pyl, pzl, Q.muh, Q.mul);\n"
+                      << "    " << nm << " = g_leaf_fn<" << M << ", " << dk << ">(eps, pzh + pzl, " << me.ks
+                      << ", dxh, dxl, Q.beta);\n  }\n";
                 } else {
-                    o << "    " << nm << " = v_leaf_fn<" << M << ", " << dk << ">(p2, pz, " << ks << ", V.Lam);\n  }\n";
+                    o << "    const float qx = pxh + pxl, qy = pyh + pyl, qz = pzh + pzl;\n"
+                      << "    const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));\n"
+                      << "    " << nm << " = v_leaf_fn<" << M << ", " << dk << ">(q2, qz, " << me.ks
+                      << ", Q.Lam);\n  }\n";
                 }
                 for (int j = 0; j < no; ++j) cur[d + j] = nm + ".v[" + std::to_string(j) + "]";
                 continue;
             }
-            o << "  " << vt << " " << nm << "[" << no << "];\n  {\n    const " << vt << " px = " << x << ", py = " << y
-              << ", pz = " << z << ";\n    const " << vt << " p2 = fd_fma(px, px, fd_fma(py, py, pz * pz));\n";
+            o << "  " << vt << " " << nm << "[" << no << "];\n  {\n" << hi << lo;
             if (t.op == OP_GLEAF) {
-                const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
-                o << "    g_family(p2, pz, " << ks << ", V.t[" << la << "] - V.t[" << lb << "], V.beta, V.mu, " << M
+                o << time_diff_expr(la, lb, vt) << "    const " << vt
+                  << " eps = fd_eps(pxh, pyh, pzh, pxl, pyl, pzl, Q.muh, Q.mul);\n"
+                  << "    g_family<" << vt << ">(eps, pzh + pzl, " << me.ks << ", dxh, dxl, " << vt << "(Q.beta), " << M
                   << ", " << dk << ", [&](int j, " << vt << " v) { " << nm << "[j] = v; });\n  }\n";
             } else {
-                o << "    v_family(p2, pz, " << ks << ", V.Lam, " << M << ", " << dk << ", [&](int j, " << vt
-                  << " v) { " << nm << "[j] = v; });\n  }\n";
+                o << "    const " << vt << " qx = pxh + pxl, qy = pyh + pyl, qz = pzh + pzl;\n"
+                  << "    const " << vt << " q2 = fd_fma(qx, qx, fd_fma(qy, qy, qz * qz));\n"
+                  << "    v_family<" << vt << ">(q2, qz, " << me.ks << ", Q.Lam, " << M << ", " << dk << ", [&](int j, "
+                  << vt << " v) { " << nm << "[j] = v; });\n  }\n";
             }
             for (int j = 0; j < no; ++j) cur[d + j] = nm + "[" + std::to_string(j) + "]";
         } else if (t.op == OP_CONST) {
@@ -434,30 +499,31 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
     std::vector<std::ostringstream> src(n_mod);
     for (int m = 0; m < n_mod; ++m)
         src[m] << "// generated from a validated fdcore tape: order " << N << ", " << R << " roots, " << sl.size()
-               << " root-accumulate slices\n#include \"fd_jit_rt.cuh\"\n";
+               << " root-accumulate slices\n#include \"fd_jit_rt.cuh\"\nusing FdSV = FdSVT<float, " << N << ">;\n";
     const char *slice_qual = (multi && !by_root) ? "extern \"C\" __device__ __noinline__" : "static __device__ __forceinline__";
     for (size_t u = 0; u < units.size(); ++u) {
         const int m = mod_of[u];
         for (int i : units[u].slices) {
             if (multi && !by_root && m != 0)
-                src[0] << "extern \"C\" __device__ float fd_s" << i << "(const FdSV &V);\n";
+                src[0] << "extern \"C\" __device__ float fd_s" << i << "(const FdSV &V, const FdPar &Q);\n";
             src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, slice_qual, sync_every, leaf_calls);
         }
         if (by_root) {
             const int r = units[u].root;
             if (m != 0)
-                src[0] << "extern \"C\" __device__ float2 fd_r" << r << "(const FdSV &V, const float *cs, const float *sn);\n";
+                src[0] << "extern \"C\" __device__ float2 fd_r" << r
+                       << "(const FdSV &V, const FdPar &Q, const float *cs, const float *sn);\n";
             src[m] << "extern \"C\" __device__ __noinline__ float2 fd_r" << r
-                   << "(const FdSV &V, const float *cs, const float *sn) {\n  float re = 0.0f, im = 0.0f, v;\n";
+                   << "(const FdSV &V, const FdPar &Q, const float *cs, const float *sn) {\n  float re = 0.0f, im = 0.0f, v;\n";
             for (int i : units[u].slices)
-                src[m] << "  v = fd_s" << i << "(V); re = fmaf(v, cs[" << sl[i].line << "], re); im = fmaf(v, sn["
+                src[m] << "  v = fd_s" << i << "(V, Q); re = fmaf(v, cs[" << sl[i].line << "], re); im = fmaf(v, sn["
                        << sl[i].line << "], im);\n";
             src[m] << "  return make_float2(re, im);\n}\n";
         }
     }
     // body: roots in flush order, each the sum of its slices times exp(i pi x_line)
     std::ostringstream b;
-    b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV &V, const float (&cs)["
+    b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV &V, const FdPar &Q, const float (&cs)["
       << N << "], const float (&sn)[" << N << "], K &k) {\n";
     size_t si = 0;
     for (const TIns &t : ins) {
@@ -468,13 +534,13 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
                                (((rt >> 24) & 255u) ? "1" : "0") + ">";
         const bool has = si < sl.size() && sl[si].root == r;
         if (by_root && has) {
-            b << "    {\n      const float2 z = fd_r" << r << "(V, cs, sn);\n      " << fl << "(z.x, z.y);\n    }\n";
+            b << "    {\n      const float2 z = fd_r" << r << "(V, Q, cs, sn);\n      " << fl << "(z.x, z.y);\n    }\n";
             while (si < sl.size() && sl[si].root == r) ++si;
             continue;
         }
         b << "    {\n      float re = 0.0f, im = 0.0f, v;\n";
         for (; si < sl.size() && sl[si].root == r; ++si)
-            b << "      v = fd_s" << si << "(V); re = fmaf(v, cs[" << sl[si].line << "], re); im = fmaf(v, sn["
+            b << "      v = fd_s" << si << "(V, Q); re = fmaf(v, cs[" << sl[si].line << "], re); im = fmaf(v, sn["
               << sl[si].line << "], im);\n";
         b << "      " << fl << "(re, im);\n    }\n";
     }
@@ -570,9 +636,9 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
     for (int m = 0; m < n_mod; ++m)
         src[m] << "// generated from a validated fdcore tape: order " << N << ", " << R << " roots, " << sl.size()
                << " root-accumulate slices, " << spt << " samples per thread" << (pair ? " in packed pairs" : "")
-               << "\n#include \"fd_jit_rt.cuh\"\n";
+               << "\n#include \"fd_jit_rt.cuh\"\nusing FdSV = FdSVT<float, " << N << ">;\n";
     const char *unit_qual = multi ? "extern \"C\" __device__ __noinline__" : "static __device__ __noinline__";
-    const std::string sig = "(const FdSV *V, const float *cs, const float *sn, float *re, float *im)";
+    const std::string sig = "(const FdSV *V, FdPar Q, const float *cs, const float *sn, float *re, float *im)";
     if (cross_roots) {
         // re/im: [root][sample] accumulators of the whole graph
         for (size_t u = 0; u < units.size(); ++u) {
@@ -583,7 +649,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
             if (multi && m != 0) src[0] << "extern \"C\" __device__ void fd_u" << u << sig << ";\n";
             const std::vector<int> &us = units[u].slices;
             src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
-                   << (pair ? "; p += 2) {\n    const FdSVT<FdF2> W = fd_pack(V[p" + vs + "], V[(p + 1)" + vs + "]);\n"
+                   << (pair ? "; p += 2) {\n    const auto W = fd_pack(V[p" + vs + "], V[(p + 1)" + vs + "]);\n"
                             : "; ++p) {\n")
                    << "    " << (pair ? "FdF2" : "float") << " v;\n";
             for (size_t a = 0; a < us.size();) {
@@ -594,10 +660,10 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
                     const std::string c0 = "p * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
                     if (pair) {
                         const std::string c1 = "(p + 1) * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
-                        src[m] << "      v = fd_s" << i << "(W); r = fd_fma(v, FdF2(cs[" << c0 << "], cs[" << c1
+                        src[m] << "      v = fd_s" << i << "(W, Q); r = fd_fma(v, FdF2(cs[" << c0 << "], cs[" << c1
                                << "]), r); i = fd_fma(v, FdF2(sn[" << c0 << "], sn[" << c1 << "]), i);\n";
                     } else {
-                        src[m] << "      v = fd_s" << i << "(V[p" << vs << "]); r = fmaf(v, cs[" << c0
+                        src[m] << "      v = fd_s" << i << "(V[p" << vs << "], Q); r = fmaf(v, cs[" << c0
                                << "], r); i = fmaf(v, sn[" << c0 << "], i);\n";
                     }
                 }
@@ -612,11 +678,11 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         }
         std::ostringstream b;
         b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV *V, "
-             "const float *cs, const float *sn, K *k) {\n    float re["
+             "const FdPar &Q, const float *cs, const float *sn, K *k) {\n    float re["
           << R * spt << "], im[" << R * spt << "];\n#pragma unroll\n    for (int q = 0; q < " << R * spt
           << "; ++q) re[q] = im[q] = 0.0f;\n";
         for (size_t u = 0; u < units.size(); ++u)
-            b << "    fd_u" << u << "(V, cs, sn, re, im);\n" << (sync_units ? "    __syncthreads();\n" : "");
+            b << "    fd_u" << u << "(V, Q, cs, sn, re, im);\n" << (sync_units ? "    __syncthreads();\n" : "");
         for (const TIns &t : ins) {
             if (t.op != OP_RFLUSH) continue;
             const int r = (int)fd_(g.h_tape[t.w]);
@@ -641,12 +707,12 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         if (pair) {
             // samples p and p + 1 in the two lanes of packed arithmetic
             src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
-                   << "; p += 2) {\n    const FdSVT<FdF2> W = fd_pack(V[p" << vs << "], V[(p + 1)" << vs
+                   << "; p += 2) {\n    const auto W = fd_pack(V[p" << vs << "], V[(p + 1)" << vs
                    << "]);\n    FdF2 r = 0.0f, i = 0.0f, v;\n";
             for (int i : units[u].slices) {
                 const std::string c0 = "p * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
                 const std::string c1 = "(p + 1) * " + std::to_string(N) + " + " + std::to_string(sl[i].line);
-                src[m] << "    v = fd_s" << i << "(W); r = fd_fma(v, FdF2(cs[" << c0 << "], cs[" << c1
+                src[m] << "    v = fd_s" << i << "(W, Q); r = fd_fma(v, FdF2(cs[" << c0 << "], cs[" << c1
                        << "]), r); i = fd_fma(v, FdF2(sn[" << c0 << "], sn[" << c1 << "]), i);\n";
             }
             src[m] << "    re[p] += r.v.x;\n    re[p + 1] += r.v.y;\n    im[p] += i.v.x;\n    im[p + 1] += i.v.y;\n"
@@ -656,13 +722,13 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
                << "; ++p) {\n    float r = 0.0f, i = 0.0f, v;\n";
         for (int i : units[u].slices)
-            src[m] << "    v = fd_s" << i << "(V[p" << vs << "]); r = fmaf(v, cs[p * " << N << " + " << sl[i].line
+            src[m] << "    v = fd_s" << i << "(V[p" << vs << "], Q); r = fmaf(v, cs[p * " << N << " + " << sl[i].line
                    << "], r); i = fmaf(v, sn[p * " << N << " + " << sl[i].line << "], i);\n";
         src[m] << "    re[p] += r;\n    im[p] += i;\n  }\n}\n";
     }
     std::ostringstream b;
-    b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV *V, const float *cs, "
-         "const float *sn, K *k) {\n";
+    b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV *V, const FdPar &Q, "
+         "const float *cs, const float *sn, K *k) {\n";
     for (const TIns &t : ins) {
         if (t.op != OP_RFLUSH) continue;
         const int r = (int)fd_(g.h_tape[t.w]);
@@ -671,7 +737,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
           << spt << "; ++p) re[p] = im[p] = 0.0f;\n";
         for (size_t u = 0; u < units.size(); ++u)
             if (units[u].root == r)
-                b << "      fd_u" << u << "(V, cs, sn, re, im);\n" << (sync_units ? "      __syncthreads();\n" : "");
+                b << "      fd_u" << u << "(V, Q, cs, sn, re, im);\n" << (sync_units ? "      __syncthreads();\n" : "");
         b << "      flush_samples<" << r << ", " << (rt & 255u) << ", " << (((rt >> 24) & 255u) ? 1 : 0) << ", "
           << spt << ", " << N << ">(k, re, im);\n    }\n";
     }
@@ -889,7 +955,7 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const 
     // of FdSV), then the tile histogram in what the resident CTAs leave free,
     // at most 96 KB so that the rest of the unified L1 keeps the per-thread
     // local arrays of the sample-loop variants
-    const long sv_b = opt->sv_smem ? (long)threads * opt->spt * (long)sizeof(FdSV) : 0;
+    const long sv_b = opt->sv_smem ? (long)threads * opt->spt * (long)sizeof(float) * fd_sv_words((int)g->hdr.order) : 0;
     int sm_total = 0, optin = 0, reserved = 0, hist_cap = 0;
     const bool have_attrs =
         cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&

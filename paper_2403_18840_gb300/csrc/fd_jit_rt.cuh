@@ -17,12 +17,35 @@ typedef unsigned int uint32_t;
 typedef long long int64_t;
 typedef unsigned long long uint64_t;
 #else
+#include <math.h>
 #include <stdint.h>
 #endif
+
+// Functions marked FD_HD are plain FP32/FP64 arithmetic: the kernels call
+// them, and a host build of this header runs the same code on the CPU.
+#define FD_HD __host__ __device__ __forceinline__
+
+// rounded sum and product that the compiler may not fuse into an FMA (the
+// error-free transformations below depend on the rounding of each step)
+FD_HD float fd_add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+FD_HD float fd_mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
 
 constexpr int FD_MAX_ORDER = 6;
 constexpr int FD_MAX_DIM = 4 * FD_MAX_ORDER - 1;
 constexpr int FD_MAX_M = 7;         // largest Taylor order of a leaf family (incl. d/dk)
+constexpr int FD_LEAF_PRECISE_BIT = 44;   // G leaf word: evaluate the family in FP64 (g_family_precise)
 constexpr int FD_MAX_INST = 256;    // instances per launch (kernel-parameter descriptors)
 constexpr float FD_INV_2PI2 = 0.050660591821168885f;   // 1 / (2 pi^2)
 constexpr float FD_8PI = 25.132741228718345f;
@@ -36,9 +59,15 @@ struct InstDesc {
     const float *points;       // explicit points [dim_max][n] or null
     const float *point_w;      // explicit weights [n] or null
     int32_t n_instr, n_slots, order, dim, n_roots, n_bins;
+    // k_ext and mu as grid parts (multiples of g and g^2), beta and K_c rounded
+    // to FP32; with the remainders below they carry the FP64 parameters
     float kext, mu, beta, Lambda, kc;
+    float kext_l, mu_l, beta_l, kc_l;
+    float grid;                // g: a power of two, the grid of the loop-momentum components
     int32_t id;                // instance index of the call (partials, per-sample rows, Philox stream)
 };
+
+struct FdTab4;
 
 struct EvalArgs {
     int32_t n_inst, tiles_per_inst, r_max, slots_total, dim_max;
@@ -50,6 +79,7 @@ struct EvalArgs {
     double *partials;
     float *per_sample_f;
     int *status;
+    const FdTab4 *sc_tab;              // cos / sin of 2 pi n / 256 as double-float pairs, n = 0..256
     uint8_t perm[FD_MAX_INST];         // descriptors in decreasing cost: work items go heaviest first
     InstDesc inst[FD_MAX_INST];
 };
@@ -78,6 +108,139 @@ __device__ __forceinline__ float word_to_uniform(uint32_t w) {
     return __uint2float_rn(w >> 9) * 1.1920928955078125e-07f + 5.9604644775390625e-08f;
 }
 
+// ---- accurate kinematics (double-float arithmetic in FP32) ------------------------
+// A G0 coefficient of Eq. taylor_node depends on eps = |p|^2 - mu through
+// exp(-eps tau*) and the Fermi factor; near the Fermi surface eps is a small
+// difference of O(mu) numbers, and a derivative coefficient (d/dmu)^j G0 can
+// vanish there (the equal-time line: f''(0) = 0).  Momenta rounded to FP32
+// move eps by ~1e-6 and the coefficient by that much relative to its scale,
+// so the sampler map, the loop momenta and eps are computed as unevaluated
+// sums hi + lo of FP32 numbers (error-free transformations: Knuth's TwoSum,
+// Dekker's product through an FMA) and eps is rounded to FP32 only at the end.
+// Each loop-momentum component is stored as a "grid" part, a multiple of the
+// instance's power of two g (so that the signed momentum sums of a leaf, and
+// their squares near the Fermi surface, are exact in FP32), plus a small
+// remainder |lo| <= g/2 carried in FP32.
+struct FdDF {
+    float hi, lo;
+};
+
+FD_HD FdDF fd_two_sum(float a, float b) {
+    const float s = fd_add_rn(a, b);
+    const float bb = fd_add_rn(s, -a);
+    const float e = fd_add_rn(fd_add_rn(a, -fd_add_rn(s, -bb)), fd_add_rn(b, -bb));
+    return FdDF{s, e};
+}
+// |a| >= |b| (or a == 0)
+FD_HD FdDF fd_fast_two_sum(float a, float b) {
+    const float s = fd_add_rn(a, b);
+    return FdDF{s, fd_add_rn(b, -fd_add_rn(s, -a))};
+}
+FD_HD FdDF fd_two_prod(float a, float b) {
+    const float p = fd_mul_rn(a, b);
+    return FdDF{p, fmaf(a, b, -p)};
+}
+FD_HD FdDF fd_df_mul(FdDF a, FdDF b) {
+    const FdDF p = fd_two_prod(a.hi, b.hi);
+    return fd_fast_two_sum(p.hi, p.lo + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+
+// cos(2 pi c), sin(2 pi c) for c = c.hi + c.lo in [0, 1], relative accuracy
+// ~1e-13.  tab[n] = (cos hi, cos lo, sin hi, sin lo) of 2 pi n / 256,
+// n = 0..256, as double-float pairs; the remainder angle b = 2 pi (c - n/256),
+// |b| <= pi/256, enters through sin b = b (1 - b^2/6 + b^4/120) and
+// cos b = 1 + d, d = -b^2/2 + b^4/24 (the next terms are below 1e-14).
+struct FdTab4 {
+    float x, y, z, w;
+};
+
+FD_HD void fd_sincos2pi_df(FdDF c, const FdTab4 *tab, FdDF &cs, FdDF &sn) {
+    const float n = rintf(c.hi * 256.0f);
+    const float rh = fd_add_rn(c.hi, -n * 0.00390625f);          // exact (Sterbenz)
+    const float kH = 6.28318548202514648f, kL = -1.7484555314695172e-07f;   // 2 pi = kH + kL
+    const FdDF bp = fd_two_prod(kH, rh);
+    const FdDF b = fd_fast_two_sum(bp.hi, bp.lo + fmaf(kH, c.lo, kL * rh));
+    const float u = b.hi * b.hi;
+    const float sb_hi = b.hi;
+    const float sb_lo = fmaf(b.hi, u * fmaf(u, 1.0f / 120.0f, -1.0f / 6.0f), b.lo);
+    const FdDF q = fd_two_prod(b.hi, b.hi);
+    const float d_hi = -0.5f * q.hi;                                // exact
+    const float d_lo = fmaf(q.hi * q.hi, 1.0f / 24.0f, -0.5f * fmaf(2.0f * b.hi, b.lo, q.lo));
+    const FdTab4 t = tab[(int)n];
+    // cos(a + b) = ca + ca d - sa sin b
+    {
+        const FdDF p1 = fd_two_prod(t.x, d_hi), p2 = fd_two_prod(t.z, sb_hi);
+        const float rest = t.y + fmaf(t.x, d_lo, t.y * d_hi) + p1.lo - p2.lo - fmaf(t.z, sb_lo, t.w * sb_hi);
+        const FdDF x = fd_two_sum(p1.hi, -p2.hi);
+        const FdDF y = fd_two_sum(t.x, x.hi);
+        cs = fd_two_sum(y.hi, y.lo + x.lo + rest);
+    }
+    // sin(a + b) = sa + sa d + ca sin b
+    {
+        const FdDF p3 = fd_two_prod(t.z, d_hi), p4 = fd_two_prod(t.x, sb_hi);
+        const float rest = t.w + fmaf(t.z, d_lo, t.w * d_hi) + p3.lo + p4.lo + fmaf(t.x, sb_lo, t.y * sb_hi);
+        const FdDF x = fd_two_sum(p3.hi, p4.hi);
+        const FdDF y = fd_two_sum(t.z, x.hi);
+        sn = fd_two_sum(y.hi, y.lo + x.lo + rest);
+    }
+}
+
+// VEGAS map of one coordinate (Lepage): y = u nb, bin i = floor(y),
+// x = e_i + (y - i) (e_(i+1) - e_i) from the FP32 edges, as hi + lo; returns
+// the bin and the map's Jacobian nb (e_(i+1) - e_i).
+FD_HD int fd_vegas_df(float u, int nb, const float *e, FdDF &x, float &jd) {
+    const FdDF y = fd_two_prod(u, (float)nb);                       // y.lo = 0 for a power-of-two nb
+    int bin = (int)y.hi;
+    float fh = y.hi - (float)bin;                                   // exact
+    if (fh == 0.0f && y.lo < 0.0f && bin > 0) {                     // just below the integer y.hi
+        bin -= 1;
+        fh = 1.0f;
+    }
+    if (bin > nb - 1) {                                             // u rounded up to 1: last bin
+        bin = nb - 1;
+        fh = 1.0f;
+    }
+    const float lo = e[bin], hi = e[bin + 1];
+    const FdDF w = fd_two_sum(hi, -lo);
+    const FdDF t = fd_two_prod(fh, w.hi);
+    const FdDF s = fd_two_sum(lo, t.hi);
+    x = fd_fast_two_sum(s.hi, s.lo + fmaf(fh, w.lo, fmaf(y.lo, w.hi, t.lo)));
+    jd = (float)nb * w.hi;
+    return bin;
+}
+
+// grid part and remainder of a double-float number: v = hi + lo with hi a
+// multiple of g (g, ginv powers of two)
+FD_HD void fd_grid_split(FdDF v, float g, float ginv, float &hi, float &lo) {
+    hi = rintf(v.hi * ginv) * g;
+    lo = fd_add_rn(v.hi, -hi) + v.lo;                               // v.hi - hi exact
+}
+
+// Loop momentum from its three hypercube coordinates (Sec. IV, spherical
+// coordinates with cutoff K_c): r = K_c a, cos(theta) = 2 b - 1,
+// sin(theta) = 2 sqrt(b (1 - b)), phi = 2 pi c; components split onto the
+// grid g.  kc = K_c as hi + lo.  Returns r (FP32) for the Jacobian.
+FD_HD float fd_loop_momentum(FdDF a, FdDF b, FdDF c, FdDF kc, const FdTab4 *tab, float g, float ginv,
+                             float (&kh)[3], float (&kl)[3]) {
+    const FdDF rp = fd_two_prod(kc.hi, a.hi);
+    const FdDF r = FdDF{rp.hi, rp.lo + fmaf(kc.hi, a.lo, kc.lo * a.hi)};
+    const FdDF c2 = fd_two_sum(2.0f * b.hi, -1.0f);
+    const FdDF cth = FdDF{c2.hi, fmaf(2.0f, b.lo, c2.lo)};
+    const FdDF om = fd_two_sum(1.0f, -b.hi);
+    const FdDF wp = fd_two_prod(b.hi, om.hi);
+    const float w_lo = wp.lo + fmaf(b.hi, om.lo - b.lo, b.lo * om.hi);
+    const float sq = sqrtf(wp.hi);
+    const float sq_lo = (fmaf(-sq, sq, wp.hi) + w_lo) * (0.5f / sq);
+    const FdDF sth = FdDF{2.0f * sq, 2.0f * sq_lo};
+    FdDF cp, sp;
+    fd_sincos2pi_df(c, tab, cp, sp);
+    const FdDF rs = fd_df_mul(r, sth);
+    fd_grid_split(fd_df_mul(rs, cp), g, ginv, kh[0], kl[0]);
+    fd_grid_split(fd_df_mul(rs, sp), g, ginv, kh[1], kl[1]);
+    fd_grid_split(fd_df_mul(r, cth), g, ginv, kh[2], kl[2]);
+    return r.hi;
+}
+
 // Neumaier compensated addition: (s, c) += v
 __device__ __forceinline__ void neumaier(double &s, double &c, double v) {
     const double t = s + v;
@@ -90,11 +253,16 @@ __device__ __forceinline__ void neumaier(double &s, double &c, double v) {
 
 // one MUFU reciprocal (relative error about 1 ulp); the arguments here are
 // normal numbers well inside the FP32 range
-__device__ __forceinline__ float rcp_approx(float x) {
+FD_HD float rcp_approx(float x) {
+#ifdef __CUDA_ARCH__
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+#else
+    return 1.0f / x;
+#endif
 }
+FD_HD double rcp_approx(double x) { return 1.0 / x; }
 
 // Two samples' values in one register pair: every arithmetic operation is one
 // packed two-lane instruction (add, multiply, fused multiply-add; each lane
@@ -121,49 +289,96 @@ __device__ __forceinline__ FdF2 operator-(FdF2 a, FdF2 b) {
     return fd_wrap(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v));
 }
 __device__ __forceinline__ FdF2 operator-(FdF2 a) { return fd_wrap(__fmul2_rn(a.v, make_float2(-1.0f, -1.0f))); }
-__device__ __forceinline__ float fd_fma(float a, float b, float c) { return fmaf(a, b, c); }
+FD_HD float fd_fma(float a, float b, float c) { return fmaf(a, b, c); }
+FD_HD double fd_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ FdF2 fd_fma(FdF2 a, FdF2 b, FdF2 c) { return fd_wrap(__ffma2_rn(a.v, b.v, c.v)); }
-__device__ __forceinline__ float fd_abs(float a) { return fabsf(a); }
+FD_HD float fd_abs(float a) { return fabsf(a); }
+FD_HD double fd_abs(double a) { return fabs(a); }
 __device__ __forceinline__ FdF2 fd_abs(FdF2 a) { return FdF2(fabsf(a.v.x), fabsf(a.v.y)); }
-__device__ __forceinline__ float fd_exp(float a) { return __expf(a); }
+FD_HD float fd_exp(float a) {
+#ifdef __CUDA_ARCH__
+    return __expf(a);
+#else
+    return expf(a);
+#endif
+}
+FD_HD double fd_exp(double a) { return exp(a); }
 __device__ __forceinline__ FdF2 fd_exp(FdF2 a) { return FdF2(__expf(a.v.x), __expf(a.v.y)); }
-__device__ __forceinline__ bool fd_gt0(float a) { return a > 0.0f; }
+FD_HD bool fd_gt0(float a) { return a > 0.0f; }
+FD_HD bool fd_gt0(double a) { return a > 0.0; }
 __device__ __forceinline__ FdM2 fd_gt0(FdF2 a) { return FdM2{a.v.x > 0.0f, a.v.y > 0.0f}; }
-__device__ __forceinline__ bool fd_lt0(float a) { return a < 0.0f; }
+FD_HD bool fd_lt0(float a) { return a < 0.0f; }
+FD_HD bool fd_lt0(double a) { return a < 0.0; }
 __device__ __forceinline__ FdM2 fd_lt0(FdF2 a) { return FdM2{a.v.x < 0.0f, a.v.y < 0.0f}; }
-__device__ __forceinline__ float fd_sel(bool c, float a, float b) { return c ? a : b; }
+FD_HD float fd_sel(bool c, float a, float b) { return c ? a : b; }
+FD_HD double fd_sel(bool c, double a, double b) { return c ? a : b; }
 __device__ __forceinline__ FdF2 fd_sel(FdM2 c, FdF2 a, FdF2 b) {
     return FdF2(c.x ? a.v.x : b.v.x, c.y ? a.v.y : b.v.y);
 }
 __device__ __forceinline__ FdF2 rcp_approx(FdF2 x) { return FdF2(rcp_approx(x.v.x), rcp_approx(x.v.y)); }
 
 // 1 / (k + 1) for the Taylor recurrences (no division in the inner loops)
-__device__ __forceinline__ float inv_int(int k1) {
+FD_HD float inv_int(int k1) {
     return k1 == 1 ? 1.0f : k1 == 2 ? 0.5f : k1 == 3 ? 0.33333334f : k1 == 4 ? 0.25f
          : k1 == 5 ? 0.2f : k1 == 6 ? 0.16666667f : k1 == 7 ? 0.14285715f : 0.125f;
 }
+template <class T>
+FD_HD T fd_inv_int(int k1) {
+    return T(inv_int(k1));
+}
+template <>
+FD_HD double fd_inv_int<double>(int k1) {
+    return 1.0 / (double)k1;
+}
+
+// eps = |p|^2 - mu from a leaf's grid sums (ph: exact in FP32) and remainder
+// sums (pl): the grid part sum ph^2 - mu_h is exact near the Fermi surface
+// (ph on the grid g, mu_h on the grid g^2), the rest
+// sum (2 ph + pl) pl - mu_l is small and rounds at ~1e-10.
+template <class T>
+FD_HD T fd_eps(T pxh, T pyh, T pzh, T pxl, T pyl, T pzl, float muh, float mul) {
+    const T s = fd_fma(pxh, pxh, fd_fma(pyh, pyh, pzh * pzh)) - T(muh);
+    const T L = fd_fma(fd_fma(T(2.0f), pxh, pxl), pxl,
+                       fd_fma(fd_fma(T(2.0f), pyh, pyl), pyl, fd_fma(fd_fma(T(2.0f), pzh, pzl), pzl, T(-mul))));
+    return s + L;
+}
+
+// hypercube time difference t_a - t_b of two interaction lines as hi + lo,
+// normalised so that hi == 0 only for equal times
+template <class T>
+FD_HD void fd_time_diff(T tah, T tal, T tbh, T tbl, T &dh, T &dl) {
+    const T s = tah - tbh;
+    const T bb = s - tah;
+    const T e = (tah - (s - bb)) + ((T(0.0f) - tbh) - bb);
+    const T lo = e + (tal - tbl);
+    dh = s + lo;
+    dl = lo - (dh - s);
+}
+
+
 
 // ---- leaf families (Eq. taylor_node) -------------------------------------------
-// G0 Taylor family at momentum p (|p|^2 = p2, p_z = pz; ks = coefficient of
-// k_ext in p) and hypercube time difference dx of its two interaction lines:
-// c_j = (d/dmu)^j G0 / j!, j <= M, then (when dk) d c_j / d k_ext, j <= M.
+// G0 Taylor family at eps = |p|^2 - mu (pz = p_z; ks = coefficient of k_ext in
+// p) and hypercube time difference dx = dxh + dxl of its two interaction
+// lines: c_j = (d/dmu)^j G0 / j!, j <= M, then (when dk) d c_j / d k_ext, j <= M.
 // Written as sign * exp(-eps tau*) * phi(eps - dmu) with the Fermi factor
-// phi >= 1/2 (phi = 1 - f for eps >= 0, f for eps < 0) and tau* the matching
-// antiperiodic time, so the exponent is never positive.  The series of
-// phi(eps - d) follows from the logistic ODE d phi / d eps = +-beta phi (1 - phi)
-// (a Taylor-mode recurrence); the series of exp(d tau*) is tau*^k / k!.
-// out(j, value) receives the (M + 1) (1 + dk) values.
+// phi >= 1/2 (phi = 1 - f for eps >= 0, f for eps < 0) and tau* = beta dx* the
+// matching antiperiodic time, dx* = dx - 1, dx or dx + 1 (exact in FP32 for
+// the dyadic times of the hypercube), so the exponent is never positive.  The
+// series of phi(eps - d) follows from the logistic ODE
+// d phi / d eps = +-beta phi (1 - phi) (a Taylor-mode recurrence); the series
+// of exp(d tau*) is tau*^k / k!.  T = float (the kernels' precision) or
+// double (the families whose value is the only term of a root, see
+// g_family_precise).  out(j, value) receives the (M + 1) (1 + dk) values.
 template <class T, class Out>
-__device__ __forceinline__ void g_family(T p2, T pz, float ks, T dx, float beta, float mu, int M, int dk,
-                                         Out &&out) {
-    const T eps = p2 - mu;
+FD_HD void g_family(T eps, T pz, float ks, T dxh, T dxl, T beta, int M, int dk, Out &&out) {
     const T E = fd_exp(-beta * fd_abs(eps));
-    const T phi = rcp_approx(1.0f + E);
+    const T phi = rcp_approx(T(1.0f) + E);
     const T psi = E * phi;
-    const auto pos = fd_gt0(dx);
-    const T tau = beta * dx;
+    const auto pos = fd_gt0(dxh);
     const auto occ = fd_lt0(eps);
-    const T tstar = fd_sel(occ, fd_sel(pos, tau - beta, tau), fd_sel(pos, tau, tau + beta));
+    const T dstar = fd_sel(occ, fd_sel(pos, dxh - T(1.0f), dxh), fd_sel(pos, dxh, dxh + T(1.0f))) + dxl;
+    const T tstar = beta * dstar;
     const T X = fd_sel(pos, T(-1.0f), T(1.0f)) * fd_exp(-eps * tstar) * phi;
     if (M == 0 && !dk) {
         out(0, X);
@@ -171,25 +386,25 @@ __device__ __forceinline__ void g_family(T p2, T pz, float ks, T dx, float beta,
     }
     const int Mx = M + dk;
     T ph[FD_MAX_M + 1], ps[FD_MAX_M + 1], A[FD_MAX_M + 1], cf[FD_MAX_M + 1];
-    const T g = fd_sel(occ, T(beta), T(-beta));
-    ph[0] = 1.0f;
+    const T g = fd_sel(occ, beta, T(0.0f) - beta);
+    ph[0] = T(1.0f);
     ps[0] = psi;
-    A[0] = 1.0f;
+    A[0] = T(1.0f);
 #pragma unroll
     for (int k = 0; k < FD_MAX_M; ++k) {
         if (k < Mx) {
-            T s = 0.0f;
+            T s = T(0.0f);
 #pragma unroll
             for (int i = 0; i <= k; ++i) s = fd_fma(ph[i], ps[k - i], s);
-            ph[k + 1] = g * s * inv_int(k + 1);
-            ps[k + 1] = -phi * ph[k + 1];
-            A[k + 1] = A[k] * tstar * inv_int(k + 1);
+            ph[k + 1] = g * s * fd_inv_int<T>(k + 1);
+            ps[k + 1] = (T(0.0f) - phi) * ph[k + 1];
+            A[k + 1] = A[k] * tstar * fd_inv_int<T>(k + 1);
         }
     }
 #pragma unroll
     for (int j = 0; j <= FD_MAX_M; ++j) {
         if (j <= Mx) {
-            T s = 0.0f;
+            T s = T(0.0f);
 #pragma unroll
             for (int i = 0; i <= j; ++i) s = fd_fma(A[j - i], ph[i], s);
             cf[j] = X * s;
@@ -200,35 +415,50 @@ __device__ __forceinline__ void g_family(T p2, T pz, float ks, T dx, float beta,
         if (j <= M) out(j, cf[j]);
     if (dk) {
         // d eps / d k_ext = 2 p . e_z ks; d/dk c_j = -(j + 1) c_(j+1) d eps / dk
-        const T kz = -2.0f * ks * pz;
+        const T kz = T(-2.0f * ks) * pz;
 #pragma unroll
         for (int j = 0; j < FD_MAX_M; ++j)
-            if (j <= M) out(M + 1 + j, kz * (float)(j + 1) * cf[j + 1]);
+            if (j <= M) out(M + 1 + j, kz * T((float)(j + 1)) * cf[j + 1]);
     }
+}
+
+// The G0 family of a line whose coefficients are, alone, the value of a root
+// (the single line of the order-1 diagram): a coefficient (d/dmu)^j G0 of the
+// equal-time line has zeros in eps (f''(0) = 0 and the nonzero roots of the
+// higher logistic derivatives), near which an FP32 evaluation has a large
+// error relative to the value itself.  This variant takes eps, p_z and tau*
+// from the grid and remainder sums in FP64 and evaluates the family in FP64.
+template <class Out>
+FD_HD void g_family_precise(double pxh, double pyh, double pzh, double pxl, double pyl, double pzl, float ks,
+                            float dxh, float dxl, double beta, double mu, int M, int dk, Out &&out) {
+    const double px = pxh + pxl, py = pyh + pyl, pz = pzh + pzl;
+    const double eps = fma(px, px, fma(py, py, pz * pz)) - mu;
+    g_family<double>(eps, pz, ks, (double)dxh, (double)dxl, beta, M, dk,
+                     [&](int j, double v) { out(j, (float)v); });
 }
 
 // V Taylor family: c_l = (d/dLambda)^l V / l! = 8 pi (-1)^l w^(l+1), w = 1/(q^2+Lambda),
 // l <= L, then (when dk) d c_l / d k_ext.  out(l, value) receives (L + 1) (1 + dk) values.
 template <class T, class Out>
-__device__ __forceinline__ void v_family(T q2, T qz, float ks, float Lambda, int L, int dk, Out &&out) {
-    const T inv = rcp_approx(q2 + Lambda);
-    T cl = FD_8PI * inv;
+FD_HD void v_family(T q2, T qz, float ks, float Lambda, int L, int dk, Out &&out) {
+    const T inv = rcp_approx(q2 + T(Lambda));
+    T cl = T(FD_8PI) * inv;
     T cf[FD_MAX_M + 1];
 #pragma unroll
     for (int l = 0; l <= FD_MAX_M; ++l) {
         if (l <= L + dk) {
             cf[l] = cl;
-            cl = -inv * cl;
+            cl = (T(0.0f) - inv) * cl;
         }
     }
 #pragma unroll
     for (int l = 0; l <= FD_MAX_M; ++l)
         if (l <= L) out(l, cf[l]);
     if (dk) {
-        const T kz = 2.0f * ks * qz;
+        const T kz = T(2.0f * ks) * qz;
 #pragma unroll
         for (int l = 0; l < FD_MAX_M; ++l)
-            if (l <= L) out(L + 1 + l, kz * (float)(l + 1) * cf[l + 1]);
+            if (l <= L) out(L + 1 + l, kz * T((float)(l + 1)) * cf[l + 1]);
     }
 }
 
@@ -242,62 +472,80 @@ struct FdLeafOut {
 };
 
 template <int M, int DK>
-__device__ __noinline__ FdLeafOut<(M + 1) * (1 + DK)> g_leaf_fn(float p2, float pz, float ks, float dx, float beta,
-                                                                 float mu) {
+__device__ __noinline__ FdLeafOut<(M + 1) * (1 + DK)> g_leaf_fn(float eps, float pz, float ks, float dxh, float dxl,
+                                                                 float beta) {
     FdLeafOut<(M + 1) * (1 + DK)> o;
-    g_family(p2, pz, ks, dx, beta, mu, M, DK, [&](int j, float v) { o.v[j] = v; });
+    g_family<float>(eps, pz, ks, dxh, dxl, beta, M, DK, [&](int j, float v) { o.v[j] = v; });
     return o;
 }
 
 template <int L, int DK>
 __device__ __noinline__ FdLeafOut<(L + 1) * (1 + DK)> v_leaf_fn(float q2, float qz, float ks, float Lambda) {
     FdLeafOut<(L + 1) * (1 + DK)> o;
-    v_family(q2, qz, ks, Lambda, L, DK, [&](int j, float v) { o.v[j] = v; });
+    v_family<float>(q2, qz, ks, Lambda, L, DK, [&](int j, float v) { o.v[j] = v; });
     return o;
 }
 
 // ---- specialised kernels -------------------------------------------------------
-// Per-sample variables the generated code reads: loop momenta k_1..k_N,
-// hypercube times of the interaction lines (t[0] = 0) and the parameters.
-template <class T>
+// Per-sample variables the generated code reads: loop momenta k_1..k_N as grid
+// parts (kx, ky, kz) and remainders (kxl, kyl, kzl), hypercube times of the
+// interaction lines (t[0] = 0) as hi + lo.  8 N + 1 words for float: an odd
+// stride, so [sample][thread] rows in shared memory are conflict-free.
+template <class T, int N>
 struct FdSVT {
-    T kx[FD_MAX_ORDER], ky[FD_MAX_ORDER], kz[FD_MAX_ORDER], t[FD_MAX_ORDER];
-    float kext, beta, mu, Lam;
-    float pad;                 // 29 words for float: an odd stride, so [sample][thread] rows in shared memory are conflict-free
+    T kx[N], ky[N], kz[N], kxl[N], kyl[N], kzl[N], t[N], tl[N];
+    float pad;
 };
-using FdSV = FdSVT<float>;
+__host__ __device__ constexpr int fd_sv_words(int N) { return 8 * N + 1; }
 
-// two samples' variables for the packed code (the parameters are per instance)
-__device__ __forceinline__ FdSVT<FdF2> fd_pack(const FdSV &a, const FdSV &b) {
-    FdSVT<FdF2> w;
+// Per-instance parameters of the generated code: k_ext and mu as grid part +
+// remainder (grid g and g^2), beta (and its FP64 remainder for the precise
+// families), Lambda.
+struct FdPar {
+    float kexth, kextl, beta, betal, muh, mul, Lam;
+};
+
+__device__ __forceinline__ FdPar fd_par(const InstDesc &D) {
+    return FdPar{D.kext, D.kext_l, D.beta, D.beta_l, D.mu, D.mu_l, D.Lambda};
+}
+
+// two samples' variables for the packed code
+template <int N>
+__device__ __forceinline__ FdSVT<FdF2, N> fd_pack(const FdSVT<float, N> &a, const FdSVT<float, N> &b) {
+    FdSVT<FdF2, N> w;
 #pragma unroll
-    for (int j = 0; j < FD_MAX_ORDER; ++j) {
+    for (int j = 0; j < N; ++j) {
         w.kx[j] = FdF2(a.kx[j], b.kx[j]);
         w.ky[j] = FdF2(a.ky[j], b.ky[j]);
         w.kz[j] = FdF2(a.kz[j], b.kz[j]);
+        w.kxl[j] = FdF2(a.kxl[j], b.kxl[j]);
+        w.kyl[j] = FdF2(a.kyl[j], b.kyl[j]);
+        w.kzl[j] = FdF2(a.kzl[j], b.kzl[j]);
         w.t[j] = FdF2(a.t[j], b.t[j]);
+        w.tl[j] = FdF2(a.tl[j], b.tl[j]);
     }
-    w.kext = a.kext;
-    w.beta = a.beta;
-    w.mu = a.mu;
-    w.Lam = a.Lam;
     return w;
 }
+
+// lane q of a packed value (the precise families run per sample in FP64)
+__device__ __forceinline__ float fd_lane(FdF2 v, int q) { return q ? v.v.y : v.v.x; }
+__device__ __forceinline__ float fd_lane(float v, int) { return v; }
 
 // Hypercube point of sample i (Philox stream or given point), VEGAS map (when
 // the instance has one), then loop momenta k_j, interaction-line times t_j
 // (hypercube units, t_0 = 0) and the weight jac[n - 1] of the roots of order
 // n (Jacobians of the roots' own coordinates, times the point weight).
-// bins[d] receives the VEGAS bin of coordinate d (histogram).
+// bins[d] receives the VEGAS bin of coordinate d (histogram).  Mapped
+// coordinates, momenta and times are double-float (hi + lo); the weights FP32.
 // Layout: k_1 <- x[0:3]; k_j <- x[4j-5 : 4j-2] and the time of line j - 1 <- x[4j-2] for j >= 2.
 template <int N, int DIM>
 __device__ __forceinline__ void sample_point(const InstDesc &D, const EvalArgs &A, int64_t i, uint32_t iter,
-                                             FdSV &V, float (&jac)[N], int (&bins)[DIM]) {
-    float x[DIM];
+                                             FdSVT<float, N> &V, float (&jac)[N], int (&bins)[DIM]) {
+    FdDF x[DIM];
     float wgt = 1.0f;
     if (D.points) {
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) x[d] = D.points[(int64_t)d * A.n_per_inst + i];
+        for (int d = 0; d < DIM; ++d) x[d] = FdDF{D.points[(int64_t)d * A.n_per_inst + i], 0.0f};
         wgt = D.point_w ? D.point_w[i] : 1.0f;
     } else {
         const uint32_t c0 = (uint32_t)(uint64_t)i, c1 = (uint32_t)((uint64_t)i >> 32);
@@ -308,7 +556,7 @@ __device__ __forceinline__ void sample_point(const InstDesc &D, const EvalArgs &
             const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (4 * blk + q < DIM) x[4 * blk + q] = word_to_uniform(wv[q]);
+                if (4 * blk + q < DIM) x[4 * blk + q] = FdDF{word_to_uniform(wv[q]), 0.0f};
         }
     }
     float jd[DIM];
@@ -316,43 +564,32 @@ __device__ __forceinline__ void sample_point(const InstDesc &D, const EvalArgs &
     for (int d = 0; d < DIM; ++d) {
         jd[d] = 1.0f;
         bins[d] = 0;
-        if (D.edges) {
-            const int nb = D.n_bins;
-            const float y = x[d] * (float)nb;
-            const int bin = min((int)y, nb - 1);
-            const float *e = D.edges + (int64_t)d * (nb + 1);
-            const float lo = __ldg(e + bin), hi = __ldg(e + bin + 1);
-            x[d] = fmaf(y - (float)bin, hi - lo, lo);
-            jd[d] = (float)nb * (hi - lo);
-            bins[d] = bin;
-        }
+        if (D.edges) bins[d] = fd_vegas_df(x[d].hi, D.n_bins, D.edges + (int64_t)d * (D.n_bins + 1), x[d], jd[d]);
     }
+    const float g = D.grid, ginv = 1.0f / D.grid;
     float w = wgt;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const int c0 = (j == 0) ? 0 : 4 * j - 1;
-        const float xa = x[c0], xb = x[c0 + 1], xc = x[c0 + 2];
-        const float r = D.kc * xa;
-        const float cth = fmaf(2.0f, xb, -1.0f);
-        const float sth = 2.0f * sqrtf(xb * (1.0f - xb));
-        float sp, cp;
-        sincospif(2.0f * xc, &sp, &cp);
-        V.kx[j] = r * sth * cp;
-        V.ky[j] = r * sth * sp;
-        V.kz[j] = r * cth;
+        float kh[3], kl[3];
+        const float r = fd_loop_momentum(x[c0], x[c0 + 1], x[c0 + 2], FdDF{D.kc, D.kc_l}, A.sc_tab, g, ginv, kh, kl);
+        V.kx[j] = kh[0];
+        V.ky[j] = kh[1];
+        V.kz[j] = kh[2];
+        V.kxl[j] = kl[0];
+        V.kyl[j] = kl[1];
+        V.kzl[j] = kl[2];
         w *= D.kc * r * r * FD_INV_2PI2;
         w *= jd[c0] * jd[c0 + 1] * jd[c0 + 2];
         V.t[j] = 0.0f;
+        V.tl[j] = 0.0f;
         if (j >= 1) {
-            V.t[j] = x[4 * j + 2];
+            V.t[j] = x[4 * j + 2].hi;
+            V.tl[j] = x[4 * j + 2].lo;
             w *= D.beta * jd[4 * j + 2];
         }
         jac[j] = w;
     }
-    V.kext = D.kext;
-    V.beta = D.beta;
-    V.mu = D.mu;
-    V.Lam = D.Lambda;
 }
 
 // Completed roots of one sample: weight, optional per-sample output, warp
@@ -476,6 +713,7 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
         if (item >= n_items) break;
         const InstDesc &D = A.inst[A.perm[item / A.tiles_per_inst]];
         const int tile = item % A.tiles_per_inst;
+        const FdPar Q = fd_par(D);
         for (int k = lane; k < R * 8; k += 32) acc[warp][k] = 0.0;
         __syncwarp();
         float *hs = hist_tile_begin<DIM, T>(D, A, hist_smem);
@@ -485,7 +723,7 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
             const int64_t i = base + tid;
             const bool valid = i < last;
             const int64_t idx = valid ? i : first;
-            FdSV V;
+            FdSVT<float, N> V;
             float jac[N];
             int bins[DIM];
             sample_point<N, DIM>(D, A, idx, iter, V, jac, bins);
@@ -496,7 +734,7 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
             for (int j = 1; j < N; ++j) sincospif(V.t[j], &sn[j], &cs[j]);   // exp(i pi x_line)
             FdSink<N> K{acc[warp], jac, valid, 0.0f, A.per_sample_f,
                         (int64_t)D.id * A.r_max * 2 * A.n_per_inst + idx, A.n_per_inst};
-            Body::run(V, cs, sn, K);
+            Body::run(V, Q, cs, sn, K);
             if (D.hist && valid) hist_sample<DIM>(D, hs, bins, K.hsum);
         }
         __syncthreads();
@@ -523,14 +761,15 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
 // the unit's code is fetched once and then re-executed from the instruction
 // cache for the other P - 1 samples, at no cost in registers.  The per-sample
 // inputs live in local memory (SVS = 1) or, with SVS = T, in dynamic shared
-// memory as [sample][thread] rows of FdSV (sample p of this thread at
+// memory as [sample][thread] rows of FdSVT (sample p of this thread at
 // V[p * SVS]); the tile histogram, when the launch provides it, follows them.
 template <class Body, int N, int DIM, int R, int T, int P, int SVS = 1>
 __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
     __shared__ double acc[T / 32][R * 8];
     __shared__ int next_item;
     extern __shared__ float dyn_smem[];
-    constexpr int SV_FLOATS = SVS > 1 ? T * P * (int)(sizeof(FdSV) / sizeof(float)) : 0;
+    using FdSV = FdSVT<float, N>;
+    constexpr int SV_FLOATS = SVS > 1 ? T * P * fd_sv_words(N) : 0;
     float *const hist_smem = dyn_smem + SV_FLOATS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = A.n_inst * A.tiles_per_inst;
@@ -542,6 +781,7 @@ __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
         if (item >= n_items) break;
         const InstDesc &D = A.inst[A.perm[item / A.tiles_per_inst]];
         const int tile = item % A.tiles_per_inst;
+        const FdPar Q = fd_par(D);
         for (int k = lane; k < R * 8; k += 32) acc[warp][k] = 0.0;
         __syncwarp();
         float *hs = hist_tile_begin<DIM, T>(D, A, hist_smem);
@@ -567,7 +807,7 @@ __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
                 K[p] = FdSink<N>{acc[warp], jac[p], valid, 0.0f, A.per_sample_f,
                                  (int64_t)D.id * A.r_max * 2 * A.n_per_inst + idx, A.n_per_inst};
             }
-            Body::run(V, cs, sn, K);
+            Body::run(V, Q, cs, sn, K);
             if (D.hist) {
 #pragma unroll
                 for (int p = 0; p < P; ++p)

@@ -28,7 +28,7 @@ Pipeline
 5. Schedule the DAG depth-first, compute each leaf family just before its
    first use, allocate per-sample slots by liveness, and serialise.
 
-Tape format, version 2 (little endian; sections 16-byte aligned):
+Tape format, version 4 (little endian; sections 16-byte aligned):
   header  16 x u32: magic 'FDTP', version, order, dim, n_roots, n_slots,
           n_instr, root_table_off, instr_off, total_bytes, n_g_leaves,
           n_v_leaves, n_arith, n_consts, reserved x2
@@ -37,8 +37,10 @@ Tape format, version 2 (little endian; sections 16-byte aligned):
           the words that follow a BUNDLE header (four u16 slot indices each).
           Leaf ops keep in `a` a signed 2-bit coefficient per momentum
           variable (k_ext, k_1..k_N; 1 = +1, 3 = -1) and in the upper bits the
-          two interaction lines (3 bits each), the Taylor order (3 bits) and
-          the d/dk flag.  RACC: `a` = value slot, `b` = out-line; RFLUSH:
+          two interaction lines (3 bits each), the Taylor order (3 bits),
+          the d/dk flag and (G leaves, bit 44) the FP64 flag: the family is
+          the only G line of a root's value (the order-1 diagram), evaluated
+          in FP64.  RACC: `a` = value slot, `b` = out-line; RFLUSH:
           `d` = root index; CONST: float in the high 32 bits.
 Per-sample state: slot 0 = 0.0, slot 1 = 1.0 and slots 2..N+1 = hypercube time
 of interaction lines 0..N-1 (written by the kernel), then constants, leaf
@@ -52,7 +54,7 @@ import struct
 import sys
 
 MAGIC = 0x50544446  # 'FDTP'
-VERSION = 3
+VERSION = 4
 
 # opcodes (keep in sync with csrc/fd_internal.cuh)
 OP_FMA = 1      # (reserved; products and sums travel in bundles)
@@ -389,9 +391,14 @@ def _enc_fma(d, a, b, c):
     return d | (a << 16) | (b << 32) | (c << 48)
 
 
-def _enc_leaf(op, d, mask, la, lb, M, dk):
+LEAF_PRECISE_BIT = 44
+
+
+def _enc_leaf(op, d, mask, la, lb, M, dk, precise=False):
     assert 0 <= d < 16384 and 0 <= mask < 16384 and 0 <= la < 8 and 0 <= lb < 8 and 0 <= M < 8
-    return op | (d << 6) | (mask << 20) | (la << 34) | (lb << 37) | (M << 40) | (int(dk) << 43)
+    assert not precise or op == OP_GLEAF
+    return (op | (d << 6) | (mask << 20) | (la << 34) | (lb << 37) | (M << 40) | (int(dk) << 43)
+            | (int(precise) << LEAF_PRECISE_BIT))
 
 
 def _enc_racc(a, line):
@@ -632,6 +639,24 @@ def compile_dag(order, roots, dag, outputs, budget=96, bundle=4, window=32):
     def fam_of(v):
         return ("G", v[1], v[2], v[3]) if v[0] in ("G", "Gd") else ("V", v[1])
 
+    # G families evaluated in FP64: those reachable from an order-1 root, whose
+    # value is one diagram with one G line (no other line's terms share its
+    # magnitude, so the zeros of its mu-derivatives need FP64)
+    precise = set()
+    stk = [node for (r, _, node) in outputs if roots[r][0] == 1]
+    seen = set()
+    while stk:
+        u = stk.pop()
+        if u in seen:
+            continue
+        seen.add(u)
+        key = dag.nodes[u]
+        if key[0] == "var":
+            if key[1][0] in ("G", "Gd"):
+                precise.add(fam_of(key[1]))
+            continue
+        stk.extend(_kids(key))
+
     def width(fk):
         M, dk = gfam[fk] if fk[0] == "G" else vfam[fk]
         return (M + 1) * (2 if dk else 1)
@@ -705,7 +730,7 @@ def compile_dag(order, roots, dag, outputs, budget=96, bundle=4, window=32):
         if fk[0] == "G":
             _, mom, la, lb = fk
             M, dk = gfam[fk]
-            words.append(_enc_leaf(OP_GLEAF, d, mom_mask(mom), la, lb, M, dk))
+            words.append(_enc_leaf(OP_GLEAF, d, mom_mask(mom), la, lb, M, dk, fk in precise))
             stats["g_leaves"] += 1
         else:
             _, mom = fk
@@ -821,7 +846,7 @@ def graph_roots(order, with_dk=False):
 
 def _g_family_flops(M, dk):
     """FP32 flops of one G family (FMA = 2) as written in the kernel's recurrence."""
-    f = 5                                   # dx, tau, tau*, -eps tau*, times phi
+    f = 6                                   # dx* (2), tau*, -eps tau*, sign and phi factors (2)
     Mx = M + dk
     for k in range(Mx):
         f += 2 * (k + 1) + 4                # Phi_hat convolution, scale, Psi, A
@@ -833,16 +858,45 @@ def _g_family_flops(M, dk):
     return f
 
 
+# per-sample map in double-float arithmetic (counted from the kernel's code):
+# a VEGAS coordinate, a loop momentum (radius, polar and azimuthal factors with
+# the table-based cos / sin, three double-float products, the grid split,
+# Jacobian), the phase and weight of an interaction-line time
+MAP_VEGAS_FLOPS = 28
+MAP_MOMENTUM_FLOPS, MAP_MOMENTUM_SFU = 190, 2
+MAP_TIME_FLOPS, MAP_TIME_SFU = 3, 1
+
+
 def _leaf_work(w):
+    """(fp32 flops, sfu ops, fp64 ops) of one leaf word.
+
+    Momentum: grid and remainder sums, 6 (t - 1) for t terms.  G: eps from the
+    sums (fd_eps) 19, p_z 1, the time difference of two nonzero lines 12,
+    Fermi factor 3 + 2 SFU, then the family (_g_family_flops + 1 SFU).  A G
+    family with the FP64 flag counts its arithmetic as FP64 operations
+    instead.  V: q = grid + remainder 3, |q|^2 5, 1 / (q^2 + Lambda) 1 + 1 SFU,
+    8 pi 1, the powers (L + dk), the d/dk outputs 2 + 2 (L + 1).
+    """
     op = w & 63
     mask = (w >> 20) & 16383
     terms = sum(1 for j in range(7) if (mask >> (2 * j)) & 3)
     M = (w >> 40) & 7
     dk = (w >> 43) & 1
-    flops = 3 * max(terms - 1, 0) + 5
+    sums = 6 * max(terms - 1, 0)
     if op == OP_GLEAF:
-        return flops + 1 + 4 + _g_family_flops(M, dk), 3
-    return flops + 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0), 1
+        la, lb = (w >> 34) & 7, (w >> 37) & 7
+        td = 12 if (la != lb and la and lb) else 0
+        fam = 19 + 1 + 3 + _g_family_flops(M, dk)
+        if (w >> LEAF_PRECISE_BIT) & 1:
+            return sums + td, 0, fam + 6
+        return sums + td + fam, 3, 0
+    return sums + 3 + 5 + 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0), 1, 0
+
+
+def _map_work(dim, order, n_roots):
+    flops = MAP_VEGAS_FLOPS * dim + MAP_MOMENTUM_FLOPS * order + MAP_TIME_FLOPS * (order - 1) + 2 * n_roots
+    sfu = MAP_MOMENTUM_SFU * order + MAP_TIME_SFU * (order - 1)
+    return flops, sfu
 
 
 def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False):
@@ -921,13 +975,12 @@ def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False):
             m = words[ins[j][1] + 1 + q]
             flops += 1 if ((m >> 48) == 0 or ((m >> 32) & 0xFFFF) == 1) else 2
         for j in leaves:
-            f, u = _leaf_work(words[ins[j][1]])
+            f, u, _ = _leaf_work(words[ins[j][1]])
             flops += f
             sfu += u
     n_racc = len(slices)
-    flops += 4 * n_racc + 6 * dim + 14 * order + 3 * (order - 1) + 2 * n_roots
-    sfu += 2 * order + (order - 1)
-    return flops, sfu
+    mf, mu = _map_work(dim, order, n_roots)
+    return flops + 4 * n_racc + mf, sfu + mu
 
 
 def contraction_ops(data):
@@ -954,22 +1007,22 @@ def contraction_ops(data):
     return ops
 
 
-def tape_work(data):
-    """(fp32_flops, sfu_ops) per sample of a serialised tape, map and weighting included.
+def tape_work(data, fp64=False):
+    """(fp32_flops, sfu_ops) per sample of a serialised tape, map and weighting
+    included (with fp64=True: the FP64 operations of the flagged families).
 
     Counting rule (FMA = 2 flops, other arithmetic 1): tape FMA as written
-    (a multiply by slot 1 = 1.0 or an add of slot 0 = 0.0 counts 1); a leaf's
-    momentum 3 (t - 1) for t terms plus |p|^2 5; G family: eps 1, Fermi factor
-    4 + 2 SFU (exp, rcp), the time part and series per _g_family_flops + 1 SFU
-    (exp); V family: 1 + 1 SFU (rcp) + 1 + (L + dk) + (dk: 2 + 2 (L + 1));
-    RACC 4; per sample the map: 6 per VEGAS dimension, 14 + 2 SFU (sincospi,
-    sqrt) per loop momentum, 3 + 1 SFU per time, 2 per root for the Jacobian.
+    (a multiply by slot 1 = 1.0 or an add of slot 0 = 0.0 counts 1); leaves
+    per _leaf_work; RACC 4; per sample the double-float map per _map_work
+    (28 per VEGAS dimension, 190 + 2 SFU (sqrt, reciprocal) per loop
+    momentum, 3 + 1 SFU per time), 2 per root for the Jacobian.
     """
     hdr = struct.unpack("<16I", data[:64])
     order, dim, n_roots, n_instr, ins_off = hdr[2], hdr[3], hdr[4], hdr[6], hdr[8]
     words = struct.unpack("<%dQ" % n_instr, data[ins_off:ins_off + 8 * n_instr])
     flops = 0
     sfu = 0
+    f64 = 0
     k = 0
     while k < len(words):
         w = words[k]
@@ -983,12 +1036,14 @@ def tape_work(data):
             k += 1 + n
             continue
         if op in (OP_GLEAF, OP_VLEAF):
-            f, u = _leaf_work(w)
+            f, u, d = _leaf_work(w)
             flops += f
             sfu += u
+            f64 += d
         elif op == OP_RACC:
             flops += 4
         k += 1
-    flops += 6 * dim + 14 * order + 3 * (order - 1) + 2 * n_roots
-    sfu += 2 * order + (order - 1)
-    return flops, sfu
+    if fp64:
+        return f64
+    mf, mu = _map_work(dim, order, n_roots)
+    return flops + mf, sfu + mu

@@ -2,6 +2,8 @@
 import numpy as np
 import pytest
 
+import parity
+
 import workloads
 from oracle import conventions, integrand as oig, philox as ophilox
 
@@ -40,7 +42,7 @@ def test_batched_launch_matches_oracle_per_sample():
         ref, mag = oig.eval_roots(x, graphs[gi[j]].roots, P, with_l1=True)
         R = len(graphs[gi[j]].roots)
         err = np.abs(f[j, :R, 0] - ref.real) + np.abs(f[j, :R, 1] - ref.imag)
-        assert np.all(err <= 2e-4 * mag + 1e-30), (j, o)
+        assert np.all(err <= parity.bound(mag)), (j, o)
 
 
 def test_cuda_graph_replay_matches_direct_calls():

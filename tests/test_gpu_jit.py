@@ -3,6 +3,8 @@ kernels against the FP64 oracle, and their agreement with the interpreter."""
 import numpy as np
 import pytest
 
+import parity
+
 import workloads
 from oracle import conventions, integrand as oig, philox as ophilox, vegas as ovegas
 
@@ -41,16 +43,8 @@ def _oracle(order, roots, n, seed, inst=0, kk=1.0, rs=1.0, it=0):
 
 
 def _compare(f, ref, mag, label):
-    # same bound as the interpreter's parity tests: 2e-4 of the oracle's L1
-    # magnitude per sample (FP32 map rounding amplified through eps tau), and
-    # at least 95% of the samples within 1e-5
-    err = np.abs(f[:, 0, :] - ref.real) + np.abs(f[:, 1, :] - ref.imag)
-    err = np.maximum(err - 1e-30, 0.0)
-    rel = err / np.maximum(mag, 1e-30)
-    frac = float(np.mean(rel <= 1e-5))
-    print("%s: max err/M %.3e, frac <= 1e-5: %.4f" % (label, rel.max(), frac))
-    assert np.all(rel <= 2e-4), (label, rel.max())
-    assert frac >= 0.95, (label, frac)
+    # the interpreter's criterion (tests/parity.py)
+    parity.check(parity.rel_error(f, ref, mag), label)
 
 
 def _run(api, G, order, n, seed, maps=None, points=None, point_w=None, kk=1.0):
@@ -113,7 +107,7 @@ def test_jit_tiny_sample_counts(api):
         f, _, _ = _run(api, G, 2, n, 3)
         ref, mag = _oracle(2, G.roots, n, 3)
         err = np.abs(f[:, 0, :] - ref.real) + np.abs(f[:, 1, :] - ref.imag)
-        assert np.all(err <= 2e-4 * mag + 1e-30)
+        assert np.all(err <= parity.bound(mag))
 
 
 def _fp32_edges(seed, dim, nb):

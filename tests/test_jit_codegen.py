@@ -51,7 +51,7 @@ def test_large_graph_splits_into_linked_modules(root_units):
         src, _ = api.jit_source(tape, m, threads=128, min_blocks=2, max_modules=8, root_units=root_units)
         defined += re.findall(r'extern "C" __device__ __noinline__ %s (%s\d+)\(' % (ret, unit), src)
         declared |= set(re.findall(r'extern "C" __device__ %s (%s\d+)\(const FdSV &V' % (ret, unit), src))
-        slices += re.findall(r"__device__ __\w+__ float (fd_s\d+)\(const FdSVT<float> &V\) \{", src)
+        slices += re.findall(r"__device__ __\w+__ float (fd_s\d+)\(const FdSVT<float, \d+> &V, const FdPar &Q\) \{", src)
         assert ("fd_jit_kernel" in src) == (m == 0)
     assert len(defined) == len(set(defined))
     assert declared <= set(defined)
@@ -76,13 +76,14 @@ def test_sample_loop_units_cover_every_slice_once(unit_cap, pair, cross):
     vt = "FdF2" if pair else "float"
     for m in range(n_mod):
         src, _ = api.jit_source(tape, m, **kw)
-        slices += re.findall(r"__device__ __forceinline__ %s (fd_s\d+)\(const FdSVT<%s> &V\) \{" % (vt, vt), src)
+        slices += re.findall(r"__device__ __forceinline__ %s (fd_s\d+)\(const FdSVT<%s, \d+> &V, const FdPar &Q\) \{"
+                             % (vt, vt), src)
         if pair:   # every unit defined here packs two samples per pass
             assert src.count("fd_pack(") == len(re.findall(r"__noinline__ void fd_u\d+", src))
         units += re.findall(r"__device__ __noinline__ void (fd_u\d+)\(", src)
     body, _ = api.jit_source(tape, 0, **kw)
     assert slices and len(slices) == len(set(slices))
-    assert sorted(re.findall(r"(fd_u\d+)\(V, cs, sn, re, im\)", body)) == sorted(units)
+    assert sorted(re.findall(r"(fd_u\d+)\(V, Q, cs, sn, re, im\)", body)) == sorted(units)
     flushes = re.findall(r"flush(?:_samples)?<(\d+), ", body)
     assert sorted(int(r) for r in flushes) == list(range(len(fdgraph.graph_roots(5))))
     if unit_cap == 0:
