@@ -112,25 +112,6 @@ def _peaks():
     return {}
 
 
-# DRAM bytes (read + write) per sample of fd_jit_kernel from one ncu capture
-# of the variant named here (the traffic is local-memory lines evicted from
-# L2 and grows with the samples).  Another variant, or a change of the
-# kernel's code since the capture, has none: traffic is then reported as null.
-NCU_TRAFFIC = dict(variant=dict(threads=256, min_blocks=1, sync_every=1, spt=4, unit_cap=12000, sv_smem=True),
-                   bytes_per_sample=235.1, capture="profiles/fd_jit_kernel_order5_vegas_ncu_full.md")
-
-
-def ncu_traffic(tuned, n, keys=("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap",
-                                "pair", "sv_smem", "cross_roots")):
-    """Captured DRAM bytes of one launch of n samples, or None for an uncaptured variant."""
-    if NCU_TRAFFIC is None:
-        return None
-    v = NCU_TRAFFIC["variant"]
-    if all(tuned.get(k) == v.get(k) for k in keys):
-        return NCU_TRAFFIC["bytes_per_sample"] * n
-    return None
-
-
 def fp32_peak_tflops(n_sm, mhz):
     """Non-tensor FP32 peak: 128 FP32 lanes per SM, FMA = 2 flops."""
     return n_sm * 128 * 2 * mhz * 1e6 / 1e12
@@ -141,46 +122,91 @@ def sfu_peak_tops(n_sm, mhz, per_clk=16):
     return n_sm * per_clk * mhz * 1e6 / 1e12
 
 
-def cpu_baseline(n_sample=48, budget_s=20.0):
-    """The FP64 oracle (as it stands) on a bounded sample of the same workload."""
+def _oracle_chunk(job):
+    """Worker: the FP64 oracle's 15 order-5 roots on the Philox points [lo, hi)."""
+    lo, hi = job
     from oracle import conventions, integrand, philox
     order = WL["order"]
     P = conventions.ueg_params(WL["rs"], WL["T_over_TF"], WL["lam_over_kF"], WL["kext_over_kF"])
-    roots = integrand.graph_roots(order)
-    integrand.eval_roots(philox.uniforms(WL["seed"], 0, 0, np.arange(2), 4 * order - 1), roots, P)  # warm caches
-    done, t0 = 0, time.perf_counter()
-    while done == 0 or (time.perf_counter() - t0 < budget_s and done < 4 * n_sample):
-        x = philox.uniforms(WL["seed"], 0, 0, np.arange(done, done + n_sample), 4 * order - 1)
-        integrand.eval_roots(x, roots, P)
-        done += n_sample
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d order-5 samples (15 roots, 2232 diagrams each), single-threaded numpy FP64" % done,
-            "seconds": dt}
+    x = philox.uniforms(WL["seed"], 0, 0, np.arange(lo, hi), 4 * order - 1)
+    integrand.eval_roots(x, integrand.graph_roots(order), P)
+    return hi - lo
+
+
+class OracleTimer:
+    """The FP64 oracle as it stands (numpy, vectorised over a batch of
+    samples) timed on the host: one thread, and every core through a pool of
+    worker processes (spawn) that each evaluate their own batch."""
+
+    def __init__(self, batch=512):
+        self.batch = batch
+        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        self.pool = None
+
+    def single(self, budget_s):
+        _oracle_chunk((0, 8))                                  # imports, diagram caches
+        done, t0 = 0, time.perf_counter()
+        while done == 0 or time.perf_counter() - t0 < budget_s:
+            done += _oracle_chunk((done, done + self.batch))
+        dt = time.perf_counter() - t0
+        return done, dt
+
+    def parallel(self, rounds=1):
+        import multiprocessing as mp
+        if self.pool is None:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+            self.pool.map(_oracle_chunk, [(0, 8)] * self.cores)   # imports, diagram caches
+        jobs = [(k * self.batch, (k + 1) * self.batch) for k in range(self.cores * rounds)]
+        t0 = time.perf_counter()
+        done = sum(self.pool.map(_oracle_chunk, jobs, chunksize=1))
+        return done, time.perf_counter() - t0
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle on a bounded sample of the same workload: all host cores
+    and one thread (about budget_s of CPU work for each)."""
+    T = OracleTimer()
+    n1, dt1 = T.single(budget_s)
+    rate1 = n1 / dt1
+    rounds = max(1, int(round(budget_s * rate1 / (T.batch * T.cores))))
+    nA, dtA = T.parallel(rounds)
+    T.close()
+    return {"value": nA / dtA, "unit": UNIT, "cores": T.cores, "kind": "oracle",
+            "sample": "%d order-5 samples (15 roots, 2232 diagrams each), numpy FP64, batches of %d, one worker "
+                      "process per core" % (nA, T.batch), "seconds": dtA,
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": "%d order-5 samples, one thread" % n1, "seconds": dt1}}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cb = cpu_baseline()
-    steps_done = []
+    T = OracleTimer()
     for _ in range(args.warmup):
-        cpu_baseline(n_sample=16, budget_s=1.0)
-    t0 = time.perf_counter()
+        T.parallel(1)
+    done, t0 = 0, time.perf_counter()
     for _ in range(args.steps):
-        steps_done.append(cpu_baseline(n_sample=16, budget_s=2.0)["value"])
+        done += T.parallel(1)[0]
     dt = time.perf_counter() - t0
-    value = float(np.mean(steps_done))
+    T.close()
+    value = done / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WL["name"], "order": WL["order"], "rs": WL["rs"],
                                             "kext_over_kF": WL["kext_over_kF"], "roots": 15,
-                                            "step": "bounded CPU sample of the order-5 workload"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "16 samples per step, oracle FP64 single thread"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "reference_full_sample": cb}
+                                            "step": "bounded CPU sample of the order-5 workload: %d samples "
+                                                    "(%d per core)" % (T.batch * T.cores, T.batch)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": T.cores, "kind": "oracle",
+                             "sample": "%d samples per step, oracle FP64, one worker process per core"
+                                       % (T.batch * T.cores)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -290,6 +316,10 @@ def run_ours(args, rank, world, dist):
     exec_flops_ps, exec_sfu_ps = fdgraph.specialised_work(
         G.tape, tuned.get("root_units", True), unit_cap=(tuned.get("unit_cap") or 6000) if loop else None,
         cross_roots=bool(tuned.get("cross_roots")) and loop)
+    exec_instr_ps, _ = fdgraph.specialised_work(
+        G.tape, tuned.get("root_units", True), unit_cap=(tuned.get("unit_cap") or 6000) if loop else None,
+        cross_roots=bool(tuned.get("cross_roots")) and loop, instr=True)
+    fp64_ps = fdgraph.tape_work(G.tape, fp64=True)
     V = api.Vegas(G.dim, WL["n_bins"])
     n = args.samples
     plan = api.EvalPlan([G], params, [0], n, maps=[V])
@@ -374,9 +404,13 @@ def run_ours(args, rank, world, dist):
                    "l2": "256 MiB flush write between timed steps; inputs generated on device",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(tuned, n), "kernel": "fd_jit_kernel",
-                     "flops_per_sample": flops_ps, "sfu_per_sample": sfu_ps,
+                     "frac": achieved / peak, "traffic": None,
+                     "traffic_note": "no DRAM counters in a timed run; ncu figures in profiles/",
+                     "kernel": "fd_jit_kernel",
+                     "flops_per_sample": flops_ps, "sfu_per_sample": sfu_ps, "fp64_per_sample": fp64_ps,
                      "executed_flops_per_sample": exec_flops_ps, "executed_sfu_per_sample": exec_sfu_ps,
+                     "executed_fp32_instr_per_sample": exec_instr_ps,
+                     "fp32_issue_frac": exec_instr_ps * n / t_kern / (n_sm * 128 * mhz_max * 1e6),
                      "sfu_achieved_tops": sfu_achieved,
                      "peak_basis": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (n_sm, mhz_max),
                      "measured_pipe_peaks": measured,

@@ -216,6 +216,18 @@ fd_status fd_counter_add(uint32_t *d_counter, uint32_t v, void *stream);
  * that gave up since the last call (the record is cleared). */
 fd_status fd_device_status(void *stream);
 
+/* Test hook for the bounded waits (the paper has no counterpart; failure
+ * handling of this library).  The tape interpreter stages its instruction
+ * chunks into shared memory with bulk copies and waits on an mbarrier for
+ * each, polling at most a fixed number of times (2^24) before it gives up,
+ * records FD_ETIMEOUT for fd_device_status, waits (at the full limit) for the
+ * copies still in flight and returns early, leaving its unfinished tiles
+ * unwritten.  This call sets that poll count for the evaluations issued
+ * after it from any host thread: polls = 0 gives up at the first wait (the
+ * timeout path runs without a fault or a hang), polls < 0 restores the
+ * default.  FD_EINVAL for polls >= 2^32. */
+fd_status fd_debug_set_wait_polls(int64_t polls);
+
 /* Number of doubles of the `partials` buffer for this launch shape: the tile
  * partial sums followed by one word the launch uses as its work counter. */
 int64_t fd_partials_count(int32_t n_inst, int32_t r_max, int64_t n_per_inst);

@@ -147,8 +147,13 @@ def inverse(blob, x, dim, n_layers, hidden, keep=False):
     return z, logq
 
 
-def loss_and_grad(blob, x, w, dim, n_layers, hidden):
-    """Weighted forward-KL loss -sum w log q(x) / sum w and its gradient (blob layout)."""
+def loss_and_grad(blob, x, w, dim, n_layers, hidden, with_l1=False):
+    """Weighted forward-KL loss -sum w log q(x) / sum w and its gradient (blob layout).
+
+    with_l1: also the gradient's L1 magnitude per parameter, the same backward
+    pass with every term replaced by its absolute value (|W|^T |g| for a
+    product, |g_a| + |g_b| for a sum): the scale against which the rounding
+    of a lower-precision evaluation of that gradient entry is measured."""
     layers = unpack(blob, dim, n_layers, hidden)
     w = np.asarray(w, dtype=np.float64)
     wn = w / w.sum()
@@ -156,6 +161,8 @@ def loss_and_grad(blob, x, w, dim, n_layers, hidden):
     loss = -float(np.sum(wn * logq))
     # dL/dv^(0): L_i contains -log(z(1-z)) with z = sigmoid(v0)
     g = -(1.0 - 2.0 * z) * wn[None, :]
+    G = np.abs(g)
+    mags = []
     grads = []
     for l in range(n_layers):
         W1, b1, W2, b2, W3, b3 = layers[l]
@@ -182,8 +189,22 @@ def loss_and_grad(blob, x, w, dim, n_layers, hidden):
         g_new = g.copy()
         g_new[B] = gB * es
         g_new[A] = g[A] + g_a
+        if with_l1:
+            GB = G[B]
+            G_o = np.concatenate([(GB * np.abs(vB) + wn[None, :]) * np.abs(1.0 - (s / S_CLAMP) ** 2),
+                                  GB * es], axis=0)
+            G_h2 = (np.abs(W3).T @ G_o) * (h2 > 0)
+            G_h1 = (np.abs(W2).T @ G_h2) * (h1 > 0)
+            mags.append([G_h1 @ np.abs(a).T, G_h1.sum(axis=1),
+                         G_h2 @ np.abs(h1).T, G_h2.sum(axis=1), G_o @ np.abs(h2).T, G_o.sum(axis=1)])
+            G_new = G.copy()
+            G_new[B] = GB * es
+            G_new[A] = G[A] + np.abs(W1).T @ G_h1
+            G = G_new
         g = g_new
         grads.append([dW1, db1, dW2, db2, dW3, db3])
+    if with_l1:
+        return loss, pack(grads), pack(mags)
     return loss, pack(grads)
 
 

@@ -33,11 +33,12 @@ Acceptance uniforms: Philox4x32-10 (oracle.philox) with counter
 (seed_lo, seed_hi), u = ((word >> 9) + 0.5) 2^-23: a stream disjoint from the
 sample streams (whose last counter word is < 2^16).
 
-The arithmetic is FP64 with the operations in the order written below (the
-acceptance test u < g'/g_t as u g_t < g', the same event in exact arithmetic;
-the estimator's terms as q/pi = 1/g and f/pi = w (1/g)), so an
-implementation that rounds each operation the same way reproduces the chains
-bit for bit.
+The arithmetic is FP64 and follows the equations as written: a proposal is
+accepted when u < R = g'/g_t, and the estimator sums f/pi = w/g and q/pi = 1/g.
+An implementation may reorder this arithmetic (test u g_t < g', multiply by
+1/g); it then takes the same decisions except where u lies within a few
+rounding steps of g'/g_t (near_ties reports those steps), and its sums agree
+to rounding.
 """
 import numpy as np
 
@@ -69,14 +70,16 @@ def g_of(w, n_sel, alpha):
     return alpha + (1.0 - alpha) * s
 
 
-def run_chains(w, n_sel, alpha, n_chains, n_steps, seed, iteration, n_therm=0, state=None):
+def run_chains(w, n_sel, alpha, n_chains, n_steps, seed, iteration, n_therm=0, state=None, near_ties=None):
     """Advance n_chains chains by n_steps steps.
 
     w: proposal weights [n_out, n_chains * n_steps]; proposal k of chain c in
     column k * n_chains + c.  state: [n_out + 1, n_chains] (current weights, then
     g; g = 0: no state yet) or None.  Returns (sums, state): sums [n_out + 2,
     n_chains] holds, per chain, the sums over the measured steps of w_o/g and of
-    1/g, then the number of accepted proposals.
+    1/g, then the number of accepted proposals.  near_ties: an optional boolean
+    array [n_chains], set for chains with a step where u is within 8 rounding
+    steps of g'/g_t (a decision that reordered arithmetic may take otherwise).
     """
     assert 0.0 < alpha <= 1.0
     w = np.asarray(w)
@@ -91,16 +94,19 @@ def run_chains(w, n_sel, alpha, n_chains, n_steps, seed, iteration, n_therm=0, s
     for k in range(n_steps):
         wp = w[:, k * C:(k + 1) * C].astype(np.float64)
         gp = g_of(wp, n_sel, alpha)
-        # u < R = pi(x') q(x_t) / (pi(x_t) q(x')) = gp / g, written u g < gp
-        # (the same event; g > 0 once the chain has a state, since alpha > 0)
-        acc = (g == 0.0) | (u[k] * g < gp)
+        # R = pi(x') q(x_t) / (pi(x_t) q(x')) = gp / g (g > 0 once the chain has a
+        # state, since alpha > 0); a chain without a state accepts
+        has = g > 0.0
+        R = gp / np.where(has, g, 1.0)
+        acc = ~has | (u[k] < R)
+        if near_ties is not None:
+            near_ties |= has & (np.abs(u[k] - R) <= 8.0 * np.finfo(np.float64).eps * np.maximum(R, u[k]))
         cur = np.where(acc[None, :], wp, cur)
         g = np.where(acc, gp, g)
         sums[n_out + 1] += acc
         if k >= n_therm:
-            inv = 1.0 / g                                # q/pi
-            sums[:n_out] += cur * inv[None, :]           # f/pi = (f/q)(q/pi)
-            sums[n_out] += inv
+            sums[:n_out] += cur / g[None, :]             # f/pi = (f/q) / (pi/q)
+            sums[n_out] += 1.0 / g                       # q/pi
     return sums, np.concatenate([cur, g[None, :]])
 
 

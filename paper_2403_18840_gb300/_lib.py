@@ -44,6 +44,7 @@ _pi = _c.POINTER(_c.c_int32)
 SIGNATURES = {
     "fd_last_error": (_c.c_char_p, []),
     "fd_device_status": (_i32, [_vp]),
+    "fd_debug_set_wait_polls": (_i32, [_i64]),
     "fd_graph_load": (_i32, [_vp, _c.c_size_t, _c.POINTER(_vp)]),
     "fd_graph_info": (_i32, [_vp, _pi, _pi, _c.POINTER(_i64), _pi]),
     "fd_graph_roots": (_i32, [_vp, _pi]),

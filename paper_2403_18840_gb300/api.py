@@ -394,6 +394,12 @@ def device_status(stream=None):
     L.check(L.lib().fd_device_status(_stream_ptr(stream)))
 
 
+def set_wait_polls(polls):
+    """Test hook: the interpreter's tape waits give up after `polls` polls
+    (0: at once; negative: the default)."""
+    L.check(L.lib().fd_debug_set_wait_polls(int(polls)))
+
+
 def postprocess(N, sigma, dsigma, kF, beta, Lam):
     """Host FP64 post-process: dict (n,m,l)->complex estimates -> dmu, a, b, meff series."""
     shape = (N + 1, N + 1, N + 1)

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
     }
     __syncthreads();
     uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};   // (thread 0) a bulk copy into buffer b has not been waited for
     bool failed = false;
     Vars<P> V;
     const uint32_t iter = A.iter + (A.iter_dev ? *A.iter_dev : 0u);
@@ -431,6 +433,7 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
                 const uint32_t bytes = (uint32_t)((cnt * 8 + 15) & ~15);
                 mbar_expect_tx(&bars[g], bytes);
                 bulk_g2s(buf[g], D.tape + (int64_t)ch * CHUNK_INSTR, bytes, &bars[g]);
+                pending[g] = true;
             }
         }
         int64_t g = 0;
@@ -447,15 +450,17 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
             for (int ch = 0; ch < n_chunks; ++ch, ++g) {
                 const int b = resident ? ch : (int)(g & 1);
                 if (!resident || pass == 0) {
-                    const bool ok = mbar_wait_bounded(&bars[b], phase[b] & 1u, WAIT_LIMIT);
+                    const bool ok = mbar_wait_bounded(&bars[b], phase[b] & 1u, A.wait_polls);
+                    if (ok) {
+                        ++phase[b];
+                        pending[b] = false;
+                    }
                     // block-uniform decision: every thread takes the same branch
                     if (__syncthreads_or(!ok)) {
                         failed = true;
                         if (tid == 0 && A.status) atomicExch(A.status, DEV_ST_TIMEOUT);
-                        if (ok) ++phase[b];
                         break;
                     }
-                    ++phase[b];
                 }
                 const int cnt = min(CHUNK_INSTR, D.n_instr - ch * CHUNK_INSTR);
                 run_chunk<T, P>(S, V, buf[b], cnt, D, A, acc, inst, idx, valid);
@@ -469,6 +474,7 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
                         const uint32_t bytes = (uint32_t)((ncnt * 8 + 15) & ~15);
                         mbar_expect_tx(&bars[b], bytes);
                         bulk_g2s(buf[b], D.tape + (int64_t)nch * CHUNK_INSTR, bytes, &bars[b]);
+                        pending[b] = true;
                     }
                 }
             }
@@ -505,8 +511,12 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
         }
         __syncthreads();
     }
+    // after a wait that gave up: thread 0 waits (bounded, at the full limit)
+    // for the bulk copies it issued and no wait has consumed, so none is
+    // still writing into this CTA's shared memory when it exits
     if (failed && tid == 0) {
-        for (int b = 0; b < 2; ++b) (void)mbar_wait_bounded(&bars[b], phase[b] & 1u, WAIT_LIMIT);
+        for (int b = 0; b < 2; ++b)
+            if (pending[b]) (void)mbar_wait_bounded(&bars[b], phase[b] & 1u, WAIT_LIMIT);
     }
 }
 
@@ -565,6 +575,9 @@ int dev_of_call() {
     return cudaGetDevice(&d) == cudaSuccess ? d : -1;
 }
 
+// polls before a tape wait of the interpreter gives up (fd_debug_set_wait_polls)
+std::atomic<uint32_t> g_wait_polls{WAIT_LIMIT};
+
 // The instance's FP64 parameters as FP32 parts for the kernels' double-float
 // kinematics: the grid g is the power of two with max(K_c, k_ext) / g in
 // [2^12, 2^13), so every loop-momentum component and k_ext is a multiple of g
@@ -612,6 +625,7 @@ fd_status eval_build(const fd_graph *const *graphs, int32_t n_graphs, const fd_p
     args.seed_lo = (uint32_t)seed;
     args.seed_hi = (uint32_t)(seed >> 32);
     args.iter = (uint32_t)iter;
+    args.wait_polls = g_wait_polls.load();
     args.iter_dev = iter_dev;
     args.partials = partials;
     args.per_sample_f = per_sample_f;
@@ -771,6 +785,12 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
     return eval_run(graphs, n_graphs, graph_of_inst, args, stream);
 }
 }  // namespace
+
+extern "C" fd_status fd_debug_set_wait_polls(int64_t polls) {
+    FD_REQUIRE(polls < (int64_t(1) << 32), "polls must be below 2^32");
+    g_wait_polls.store(polls < 0 ? WAIT_LIMIT : (uint32_t)polls);
+    return FD_OK;
+}
 
 extern "C" fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_graphs,
                                        const fd_params *params, const int32_t *graph_of_inst,

@@ -74,6 +74,7 @@ struct EvalArgs {
     int32_t hist_smem;                 // floats of dynamic shared memory for the tile histogram (0: none)
     int64_t n_per_inst, tile;
     uint32_t seed_lo, seed_hi, iter;
+    uint32_t wait_polls;               // tape waits of the interpreter give up after this many polls
     const uint32_t *iter_dev;          // optional: iteration += *iter_dev (read on the device)
     unsigned long long *queue;         // work counter (reset to 0 before the launch)
     double *partials;

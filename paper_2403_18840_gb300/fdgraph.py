@@ -844,18 +844,26 @@ def graph_roots(order, with_dk=False):
 # algorithmic work per sample (roofline accounting)
 # --------------------------------------------------------------------------
 
-def _g_family_flops(M, dk):
-    """FP32 flops of one G family (FMA = 2) as written in the kernel's recurrence."""
-    f = 6                                   # dx* (2), tau*, -eps tau*, sign and phi factors (2)
+def _g_family_work(M, dk):
+    """(FP32 flops, FP32 instructions) of one G family as written in the
+    kernel's recurrence (an FMA is 2 flops and 1 instruction)."""
+    f = i = 6                               # dx* (2), tau*, -eps tau*, sign and phi factors (2)
     Mx = M + dk
     for k in range(Mx):
-        f += 2 * (k + 1) + 4                # Phi_hat convolution, scale, Psi, A
+        f += 2 * (k + 1) + 4                # Phi_hat convolution (k + 1 FMAs), scale, Psi, A
+        i += (k + 1) + 4
     if Mx:
         for j in range(Mx + 1):
             f += 2 * (j + 1)                # c_j convolution
+            i += j + 1
     if dk:
         f += 2 * (M + 1) + 1
-    return f
+        i += 2 * (M + 1) + 1
+    return f, i
+
+
+def _g_family_flops(M, dk):
+    return _g_family_work(M, dk)[0]
 
 
 # per-sample map in double-float arithmetic (counted from the kernel's code):
@@ -867,15 +875,17 @@ MAP_MOMENTUM_FLOPS, MAP_MOMENTUM_SFU = 190, 2
 MAP_TIME_FLOPS, MAP_TIME_SFU = 3, 1
 
 
-def _leaf_work(w):
-    """(fp32 flops, sfu ops, fp64 ops) of one leaf word.
+def _leaf_work(w, instr=False):
+    """(fp32 flops, sfu ops, fp64 ops) of one leaf word (with instr: FP32
+    instructions in place of flops, an FMA counting once).
 
     Momentum: grid and remainder sums, 6 (t - 1) for t terms.  G: eps from the
-    sums (fd_eps) 19, p_z 1, the time difference of two nonzero lines 12,
-    Fermi factor 3 + 2 SFU, then the family (_g_family_flops + 1 SFU).  A G
-    family with the FP64 flag counts its arithmetic as FP64 operations
-    instead.  V: q = grid + remainder 3, |q|^2 5, 1 / (q^2 + Lambda) 1 + 1 SFU,
-    8 pi 1, the powers (L + dk), the d/dk outputs 2 + 2 (L + 1).
+    sums (fd_eps: 6 FMAs, a product and 3 sums: 19 flops, 10 instructions),
+    p_z 1, the time difference of two nonzero lines 12, Fermi factor 3 + 2 SFU,
+    then the family (_g_family_work + 1 SFU).  A G family with the FP64 flag
+    counts its arithmetic as FP64 operations instead.  V: q = grid +
+    remainder 3, |q|^2 5 (3 instructions), 1 / (q^2 + Lambda) 1 + 1 SFU, 8 pi 1,
+    the powers (L + dk), the d/dk outputs 2 + 2 (L + 1).
     """
     op = w & 63
     mask = (w >> 20) & 16383
@@ -886,11 +896,12 @@ def _leaf_work(w):
     if op == OP_GLEAF:
         la, lb = (w >> 34) & 7, (w >> 37) & 7
         td = 12 if (la != lb and la and lb) else 0
-        fam = 19 + 1 + 3 + _g_family_flops(M, dk)
+        gf, gi = _g_family_work(M, dk)
+        fam = (10 if instr else 19) + 1 + 3 + (gi if instr else gf)
         if (w >> LEAF_PRECISE_BIT) & 1:
-            return sums + td, 0, fam + 6
+            return sums + td, 0, 19 + 1 + 3 + gf + 6
         return sums + td + fam, 3, 0
-    return sums + 3 + 5 + 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0), 1, 0
+    return sums + 3 + (3 if instr else 5) + 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0), 1, 0
 
 
 def _map_work(dim, order, n_roots):
@@ -899,7 +910,7 @@ def _map_work(dim, order, n_roots):
     return flops, sfu
 
 
-def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False):
+def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False, instr=False):
     """(fp32_flops, sfu_ops) per sample executed by the specialised kernel.
 
     The kernel evaluates every root-accumulate slice of the tape as straight-line
@@ -908,7 +919,7 @@ def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False):
     per root with root_units, else one per slice; with unit_cap (the sample-loop
     kernels) consecutive slices of a root, or across roots with cross_roots,
     packed while FMAs + 30 per distinct leaf stay within the cap.  Same counting
-    rule as tape_work.
+    rule as tape_work (with instr: FP32 instructions, an FMA counting once).
     """
     hdr = struct.unpack("<16I", data[:64])
     order, dim, n_roots, n_instr, ins_off = hdr[2], hdr[3], hdr[4], hdr[6], hdr[8]
@@ -973,9 +984,9 @@ def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False):
     for _, fmas, leaves in units:
         for (j, q) in fmas:
             m = words[ins[j][1] + 1 + q]
-            flops += 1 if ((m >> 48) == 0 or ((m >> 32) & 0xFFFF) == 1) else 2
+            flops += 1 if (instr or (m >> 48) == 0 or ((m >> 32) & 0xFFFF) == 1) else 2
         for j in leaves:
-            f, u, _ = _leaf_work(words[ins[j][1]])
+            f, u, _ = _leaf_work(words[ins[j][1]], instr)
             flops += f
             sfu += u
     n_racc = len(slices)

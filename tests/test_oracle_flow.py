@@ -84,3 +84,21 @@ def test_adam_first_step_is_signed_lr():
     new, m, v = flow.adam_step(blob, grad, np.zeros(5), np.zeros(5), 1, 0.01)
     expect = -0.01 * grad / (np.abs(grad) + 1e-8)
     assert np.allclose(new, expect, rtol=1e-6, atol=1e-12)
+
+
+def test_gradient_magnitude_bounds_the_gradient():
+    # the absolute-value backward pass dominates |gradient| entry by entry, and
+    # equals it where an entry is one product chain (a bias of the t half of
+    # the first layer processed, from one sample)
+    D, K, H = 7, 3, 16
+    blob = workloads.normal_blob(4, flow.n_params(D, K, H), 0.3)
+    x = workloads.uniform_points(5, D, 40, 0.05, 0.95)
+    w = workloads.positive_weights(6, 40)
+    _, g, M = flow.loss_and_grad(blob, x, w, D, K, H, with_l1=True)
+    assert np.all(M >= np.abs(g) * (1 - 1e-12))
+    _, g1, M1 = flow.loss_and_grad(blob, x[:, :1], w[:1], D, K, H, with_l1=True)
+    b3_g = flow.unpack(g1, D, K, H)[0][5]
+    b3_m = flow.unpack(M1, D, K, H)[0][5]
+    nb = len(flow.layer_split(D, 0)[1])
+    assert np.allclose(b3_m[nb:], np.abs(b3_g[nb:]), rtol=1e-12, atol=0)
+    assert np.any(b3_m[:nb] > np.abs(b3_g[:nb]) * (1 + 1e-9)) or np.allclose(b3_m[:nb], np.abs(b3_g[:nb]))
