@@ -209,6 +209,19 @@ fd_status fd_integrand_eval_iter_dev(const fd_graph *const *graphs, int32_t n_gr
                                      int32_t n_inst, fd_vegas *const *maps, uint64_t seed,
                                      uint64_t iter_base, const uint32_t *d_iter, int64_t n_per_inst,
                                      double *partials, void *stream);
+/* As fd_integrand_eval without the per-sample roots, writing instead the
+ * learned proposal's training target (App. A: the flow is fitted by forward
+ * KL to |f| on points the method itself draws, each weighted by 1/q of the
+ * sampler that drew it): abs_f [n_inst][n_per_inst] (device FP32) receives,
+ * per sample, the sum over the value roots (no d/dk) of |Re| + |Im| of the
+ * weighted integrand (the point weight, e.g. 1/q, and the map's Jacobian
+ * included), 0 where that sum is not finite.  The same sum feeds the VEGAS
+ * histogram.  FD_EINVAL for a null abs_f, otherwise as fd_integrand_eval. */
+fd_status fd_integrand_eval_target(const fd_graph *const *graphs, int32_t n_graphs, const fd_params *params,
+                                   const int32_t *graph_of_inst, int32_t n_inst, fd_vegas *const *maps,
+                                   const float *points, const float *point_w, uint64_t seed, uint64_t iter,
+                                   int64_t n_per_inst, double *partials, float *abs_f, void *stream);
+
 /* *d_counter += v on the device (async). */
 fd_status fd_counter_add(uint32_t *d_counter, uint32_t v, void *stream);
 

@@ -70,6 +70,8 @@ SIGNATURES = {
     "fd_map_samples": (_i32, [_vp, _u64, _u64, _i32, _i64, _i32, _vp, _vp, _vp]),
     "fd_integrand_eval": (_i32, [_c.POINTER(_vp), _i32, _c.POINTER(fd_params), _pi, _i32,
                                  _c.POINTER(_vp), _vp, _vp, _u64, _u64, _i64, _vp, _vp, _vp]),
+    "fd_integrand_eval_target": (_i32, [_c.POINTER(_vp), _i32, _c.POINTER(fd_params), _pi, _i32,
+                                        _c.POINTER(_vp), _vp, _vp, _u64, _u64, _i64, _vp, _vp, _vp]),
     "fd_partials_count": (_i64, [_i32, _i32, _i64]),
     "fd_tile_samples": (_i64, [_i64]),
     "fd_integrand_eval_stats_noalloc": (_i32, [_c.POINTER(_vp), _i32, _c.POINTER(fd_params), _pi, _i32,

@@ -219,6 +219,16 @@ class EvalPlan:
                                       _ptr(self.stats), _stream_ptr(stream)))
         return self.stats
 
+    def run_target(self, seed, it, abs_f, points=None, point_w=None, stream=None):
+        """Evaluate and write the training target (sum over value roots of
+        |Re| + |Im|, weighted) per sample into abs_f [n_inst][n] (device FP32)."""
+        L.check(L.lib().fd_integrand_eval_target(self._g, len(self.graphs), self._p, self._gi, self.n_inst, self._m,
+                                                 _ptr(points), _ptr(point_w), seed, it, self.n_per_inst,
+                                                 _ptr(self.partials), _ptr(abs_f), _stream_ptr(stream)))
+        L.check(L.lib().fd_accumulate(_ptr(self.partials), self.n_inst, self.r_max, self.n_per_inst,
+                                      _ptr(self.stats), _stream_ptr(stream)))
+        return self.stats
+
 
 class Flow:
     """Affine coupling flow with BF16 tensor-core kernels (FP32 master weights)."""

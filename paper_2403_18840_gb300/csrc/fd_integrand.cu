@@ -479,6 +479,12 @@ __global__ void __launch_bounds__(T) integrand_kernel(const __grid_constant__ Ev
                 }
             }
             if (failed) break;
+            if (A.abs_f) {
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    if (valid[p])
+                        A.abs_f[(int64_t)D.id * A.n_per_inst + idx[p]] = isfinite(V.hsum[p]) ? V.hsum[p] : 0.0f;
+            }
             if (D.hist && !D.points) {
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
@@ -611,7 +617,7 @@ fd_status eval_build(const fd_graph *const *graphs, int32_t n_graphs, const fd_p
                      const int32_t *graph_of_inst, int32_t n_inst, fd_vegas *const *maps,
                      const float *points, const float *point_w, uint64_t seed, uint64_t iter,
                      const uint32_t *iter_dev, int64_t n_per_inst, double *partials, float *per_sample_f,
-                     int *status, EvalArgs &args) {
+                     float *abs_f, int *status, EvalArgs &args) {
     FD_REQUIRE(graphs && n_graphs > 0, "graphs must be a non-empty array");
     FD_REQUIRE(params && graph_of_inst, "params and graph_of_inst are required");
     FD_REQUIRE(n_inst > 0 && n_inst <= FD_MAX_INST, "n_inst must be in [1, 256]");
@@ -629,6 +635,7 @@ fd_status eval_build(const fd_graph *const *graphs, int32_t n_graphs, const fd_p
     args.iter_dev = iter_dev;
     args.partials = partials;
     args.per_sample_f = per_sample_f;
+    args.abs_f = abs_f;
     args.status = status;
     int r_max = 0, slots_total = 0, dim_max = 0;
     for (int g = 0; g < n_graphs; ++g) {
@@ -777,10 +784,10 @@ fd_status eval_impl(const fd_graph *const *graphs, int32_t n_graphs, const fd_pa
                     const int32_t *graph_of_inst, int32_t n_inst, fd_vegas *const *maps,
                     const float *points, const float *point_w, uint64_t seed, uint64_t iter,
                     const uint32_t *iter_dev, int64_t n_per_inst, double *partials, float *per_sample_f,
-                    int *status, cudaStream_t stream) {
+                    int *status, cudaStream_t stream, float *abs_f = nullptr) {
     static thread_local EvalArgs args;   // large (kernel parameter space)
     const fd_status st = eval_build(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed,
-                                    iter, iter_dev, n_per_inst, partials, per_sample_f, status, args);
+                                    iter, iter_dev, n_per_inst, partials, per_sample_f, abs_f, status, args);
     if (st != FD_OK) return st;
     return eval_run(graphs, n_graphs, graph_of_inst, args, stream);
 }
@@ -800,6 +807,17 @@ extern "C" fd_status fd_integrand_eval(const fd_graph *const *graphs, int32_t n_
                                        void *stream) {
     return eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, nullptr,
                      n_per_inst, partials, per_sample_f, fd::device_status_word(), (cudaStream_t)stream);
+}
+
+extern "C" fd_status fd_integrand_eval_target(const fd_graph *const *graphs, int32_t n_graphs,
+                                              const fd_params *params, const int32_t *graph_of_inst,
+                                              int32_t n_inst, fd_vegas *const *maps, const float *points,
+                                              const float *point_w, uint64_t seed, uint64_t iter,
+                                              int64_t n_per_inst, double *partials, float *abs_f,
+                                              void *stream) {
+    FD_REQUIRE(abs_f, "abs_f is required");
+    return eval_impl(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, nullptr,
+                     n_per_inst, partials, nullptr, fd::device_status_word(), (cudaStream_t)stream, abs_f);
 }
 
 extern "C" fd_status fd_integrand_eval_iter_dev(const fd_graph *const *graphs, int32_t n_graphs,
@@ -975,7 +993,7 @@ extern "C" fd_status fd_integrand_eval_stats_noalloc(
     // call leaves an earlier call's partial sums alone
     static thread_local EvalArgs args;
     st = eval_build(graphs, n_graphs, params, graph_of_inst, n_inst, maps, points, point_w, seed, iter, nullptr,
-                    n_per_inst, partials, per_sample_f, nullptr, args);
+                    n_per_inst, partials, per_sample_f, nullptr, nullptr, args);
     if (st != FD_OK) return st;
     // every byte 0xFF is a NaN double: a tile the kernel failed to write shows up
     // as NaN in `out` instead of a stale value from an earlier call

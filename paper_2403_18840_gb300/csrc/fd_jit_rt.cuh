@@ -79,6 +79,7 @@ struct EvalArgs {
     unsigned long long *queue;         // work counter (reset to 0 before the launch)
     double *partials;
     float *per_sample_f;
+    float *abs_f;                      // optional [inst][n]: sum over value roots of |Re| + |Im| (0 if not finite)
     int *status;
     const FdTab4 *sc_tab;              // cos / sin of 2 pi n / 256 as double-float pairs, n = 0..256
     uint8_t perm[FD_MAX_INST];         // descriptors in decreasing cost: work items go heaviest first
@@ -231,7 +232,7 @@ FD_HD float fd_loop_momentum(FdDF a, FdDF b, FdDF c, FdDF kc, const FdTab4 *tab,
     const FdDF wp = fd_two_prod(b.hi, om.hi);
     const float w_lo = wp.lo + fmaf(b.hi, om.lo - b.lo, b.lo * om.hi);
     const float sq = sqrtf(wp.hi);
-    const float sq_lo = (fmaf(-sq, sq, wp.hi) + w_lo) * (0.5f / sq);
+    const float sq_lo = sq > 0.0f ? (fmaf(-sq, sq, wp.hi) + w_lo) * (0.5f / sq) : 0.0f;   // b = 0 or 1: sin = 0
     const FdDF sth = FdDF{2.0f * sq, 2.0f * sq_lo};
     FdDF cp, sp;
     fd_sincos2pi_df(c, tab, cp, sp);
@@ -737,6 +738,7 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
                         (int64_t)D.id * A.r_max * 2 * A.n_per_inst + idx, A.n_per_inst};
             Body::run(V, Q, cs, sn, K);
             if (D.hist && valid) hist_sample<DIM>(D, hs, bins, K.hsum);
+            if (A.abs_f && valid) A.abs_f[(int64_t)D.id * A.n_per_inst + idx] = isfinite(K.hsum) ? K.hsum : 0.0f;
         }
         __syncthreads();
         if (hs) hist_tile_flush<DIM, T>(D, hs);
@@ -809,6 +811,13 @@ __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
                                  (int64_t)D.id * A.r_max * 2 * A.n_per_inst + idx, A.n_per_inst};
             }
             Body::run(V, Q, cs, sn, K);
+            if (A.abs_f) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const int64_t i = base + (int64_t)p * T + tid;
+                    if (K[p].valid) A.abs_f[(int64_t)D.id * A.n_per_inst + i] = isfinite(K[p].hsum) ? K[p].hsum : 0.0f;
+                }
+            }
             if (D.hist) {
 #pragma unroll
                 for (int p = 0; p < P; ++p)

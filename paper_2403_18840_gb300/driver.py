@@ -41,12 +41,6 @@ def adapt_vegas(G, params, vegas, n, iters, seed, alpha=0.5, first_iter=0):
     return torch.stack(out).cpu().numpy()
 
 
-def training_weights(per_sample, value_roots):
-    """Target |f| / q_s per sample: sum over value roots of |Re| + |Im| of the weighted integrand."""
-    ps = per_sample[0, value_roots]            # [Rv][2][n]
-    return ps.abs().sum(dim=(0, 1)).contiguous()
-
-
 def _flow_draw(flow, seed, it, inst, n, defensive):
     if defensive > 0:
         x, w, _ = flow.sample_defensive(seed, it, inst, n, defensive)
@@ -62,8 +56,8 @@ def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, e
     kernel (points mode, weights 1/q), and used for `evals_per_batch` Adam steps.
     Returns the list of losses.
     """
-    value_roots = [r for r, (n, m, l, dk) in enumerate(G.roots) if dk == 0]
-    plan = api.EvalPlan([G], [params], [0], batch, maps=[vegas] if on_vegas else None, per_sample=True)
+    plan = api.EvalPlan([G], [params], [0], batch, maps=[vegas] if on_vegas else None)
+    tw = torch.empty(batch, dtype=torch.float32, device="cuda")
     losses = []
     k = 0
     while k < steps:
@@ -72,9 +66,8 @@ def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, e
             x, w = api.map_samples(None if on_vegas else vegas, seed, 1000 + k, 1, batch, G.dim)
         else:
             x, w = _flow_draw(flow, seed, 1000 + k, 2, batch, defensive)
-        plan.run(seed, 1000 + k, points=x, point_w=w)
-        tw = training_weights(plan.per_sample, value_roots)
-        tw = torch.nan_to_num(tw, nan=0.0, posinf=0.0)
+        # target |f| / q_s per sample, formed by the integrand kernel
+        plan.run_target(seed, 1000 + k, tw, points=x, point_w=w)
         m = min(evals_per_batch, steps - k)
         step_losses = flow.train(x, tw, m, lr).tolist()
         losses.extend(step_losses)

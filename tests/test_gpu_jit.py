@@ -269,7 +269,7 @@ def test_jit_shared_inputs_bitwise_equal_to_local(api):
 
 
 def test_jit_shared_inputs_too_large_is_rejected(api):
-    # 256 threads x 8 samples x 116 bytes exceed a block's shared memory
+    # 256 threads x 16 samples x 68 bytes (order 2: 8 N + 1 words) exceed a block's shared memory
     G = api.Graph(2, budget=8192)
     with pytest.raises(api.L.FdError):
-        G.jit(threads=256, min_blocks=1, spt=8, sv_smem=True)
+        G.jit(threads=256, min_blocks=1, spt=16, sv_smem=True)

@@ -127,6 +127,8 @@ def test_loop_momenta_double_float(kin_exe, tmp_path):
     # the corners of the angles: c at the table nodes and halfway, b near 0 and 1
     x[2, :8] = np.array([0.0, 0.25, 0.5, 0.75, 1.0 / 512, 3.0 / 512, 0.9999999, 2.0 ** -24])
     x[1, 8:12] = np.array([2.0 ** -24, 1.0 - 2.0 ** -24, 0.5, 0.25])
+    # points on the cube's faces (a flow's FP32 samples can saturate to 0 or 1)
+    x[1, 12], x[1, 13], x[0, 14], x[2, 15], x[0, 16] = 0.0, 1.0, 0.0, 1.0, 1.0
     x = x.astype(np.float32)
     src, dst = str(tmp_path / "k.in"), str(tmp_path / "k.out")
     with open(src, "wb") as f:
@@ -135,6 +137,7 @@ def test_loop_momenta_double_float(kin_exe, tmp_path):
         x.tofile(f)
     subprocess.run([kin_exe, src, dst], check=True)
     k = np.fromfile(dst, np.float64).reshape(order, 3, n)
+    assert np.all(np.isfinite(k))
     kref, _, _ = oig.map_hypercube(x.astype(np.float64), order, P)
     err = np.abs(k - kref[1:])
     print("double-float momenta: max err %.2e" % err.max())
