@@ -119,13 +119,19 @@ fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_
  *  cross_roots  != 0 (spt > 1): units pack consecutive slices across root
  *               boundaries, so leaves that neighbouring roots share are
  *               computed once per unit.
+ *  leaf_cache   0..4096 floats per sample (scalar, inlined leaves): leaf
+ *               families used by several units are computed once per sample
+ *               into shared memory ([float][sample][thread], threads x spt x
+ *               4 bytes per float) and read there by the units, the families
+ *               that save the most work per float first, up to this many
+ *               floats; any spt (spt = 1 takes the sample-loop kernel).
  * cache_dir (may be NULL): directory for compiled images, keyed by a hash of
  * the generated source and options.  Synchronous; FD_ENOTSUP when the
  * run-time compiler is unavailable or fails (fd_last_error holds its log).
  * Results agree with the interpreter up to FP32 rounding order. */
 typedef struct {
     int32_t threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt, unit_cap, pair, sv_smem,
-        cross_roots;
+        cross_roots, leaf_cache;
 } fd_jit_options;
 fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const char *cache_dir);
 /* Switch evaluation of g between its specialised kernel (on != 0) and the interpreter. */

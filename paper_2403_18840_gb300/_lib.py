@@ -20,7 +20,8 @@ class FdError(RuntimeError):
 
 class fd_jit_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("threads", "min_blocks", "max_modules", "root_units", "sync_every",
-                                              "leaf_calls", "spt", "unit_cap", "pair", "sv_smem", "cross_roots")]
+                                              "leaf_calls", "spt", "unit_cap", "pair", "sv_smem", "cross_roots",
+                                              "leaf_cache")]
 
 
 class fd_params(ctypes.Structure):

@@ -7,9 +7,10 @@ device by timing real launches:
     trades recomputed leaves against shared-memory occupancy;
   * the CTA shape (threads x samples per thread).
 Specialised kernels: CTA size, launch-bounds occupancy (which caps the
-registers per thread and so trades spills against resident warps) and the
-compilation unit (one function per root, whose slices share leaves, or one
-per slice, which keeps live ranges short).
+registers per thread and so trades spills against resident warps), samples
+per thread, the compilation unit's size, where the samples' inputs live and
+how many floats per sample of leaf families shared by several units are
+computed once into shared memory (the leaf cache) rather than per unit.
 Results are cached per (graph, device) in _build/autotune.json.
 """
 import json
@@ -23,13 +24,15 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 SCHEDULES = [dict(budget=b, bundle=w, window=8 * w) for b in (96, 128, 160) for w in (4, 8)]
 SHAPES = [(128, 2), (256, 1), (128, 1), (64, 2)]
 # specialised-kernel variants (fd_jit_options; unlisted options at their defaults)
-JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=1), dict(threads=256, min_blocks=1, spt=4, unit_cap=12000),
-                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sv_smem=True),
+JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sv_smem=True),
-                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1, sv_smem=True),
-                dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sync_every=1, sv_smem=True)]
+                dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True),
+                dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True, leaf_cache=24),
+                dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, leaf_cache=64),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1, leaf_cache=24),
+                dict(threads=256, min_blocks=1, spt=1, unit_cap=12000, leaf_cache=128)]
 JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap", "pair", "sv_smem",
-            "cross_roots")
+            "cross_roots", "leaf_cache")
 
 
 def _key(order, roots):
@@ -132,7 +135,7 @@ def best_load(order, roots, v, params, copies=4, n_samples=1 << 24, reps=2, n_bi
 def tune_jit(order, roots, params, n_samples=1 << 24, variants=None, force=False, log=None, copies=3):
     """Best {'threads','min_blocks','root_units','sync_every','leaf_calls','spt','unit_cap','pair','sv_smem',
     'samples_per_s',...} for the specialised kernel, each variant scored at its best of `copies` loads."""
-    key = "jit6|" + _key(order, roots)
+    key = "jit7|" + _key(order, roots)
     cache = _load()
     if key in cache and not force:
         return cache[key]

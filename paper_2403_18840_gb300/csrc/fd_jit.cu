@@ -31,6 +31,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <map>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -282,6 +283,104 @@ std::string time_diff_expr(uint32_t la, uint32_t lb, const std::string &vt) {
            "], dxh, dxl);\n";
 }
 
+// Code computing the Taylor family of leaf word w into `nm` (an array of its
+// (M + 1)(1 + dk) values, or an FdLeafOut with leaf_calls); acc receives the
+// access prefix of value j ("nm[" or "nm.v[").
+std::string leaf_block(uint64_t w, const std::string &nm, uint32_t op, int N, const std::string &vt, int leaf_calls,
+                       std::string &acc) {
+    std::ostringstream o;
+    const uint32_t mask = fa(w);
+    const int no = leaf_outputs(w);
+    const int M = (int)((w >> 40) & 7u), dk = (int)((w >> 43) & 1u);
+    const bool precise = op == OP_GLEAF && ((w >> FD_LEAF_PRECISE_BIT) & 1u);
+    const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
+    const MomExpr me = momentum_expr(mask, N, precise ? "(double)" : "");
+    const std::string hi = "    const " + vt + " pxh = " + me.x + ", pyh = " + me.y + ", pzh = " + me.z + ";\n";
+    acc = nm + "[";
+    if (precise) {
+        // FP64 family (the single G line of the order-1 diagram), per sample (packed: per lane)
+        o << "  " << vt << " " << nm << "[" << no << "];\n  {\n" << hi << time_diff_expr(la, lb, vt)
+          << "    const double bt = (double)Q.beta + (double)Q.betal, mu = (double)Q.muh + (double)Q.mul;\n";
+        const int lanes = vt == "float" ? 1 : 2;
+        for (int q = 0; q < lanes; ++q) {
+            const std::string L = vt == "float" ? "" : ".v." + std::string(q ? "y" : "x");
+            const MomExpr ml = momentum_expr(mask, N, "(double)");
+            auto lane = [&](const std::string &e) {
+                if (vt == "float") return e;
+                // packed operands: take this lane of every V member
+                std::string r = e, out;
+                size_t pos = 0;
+                while (true) {
+                    const size_t a = r.find("]", pos);
+                    if (a == std::string::npos) break;
+                    out += r.substr(pos, a + 1 - pos) + L;
+                    pos = a + 1;
+                }
+                return out + r.substr(pos);
+            };
+            o << "    g_family_precise((double)" << (vt == "float" ? "pxh" : "pxh" + L) << ", (double)"
+              << (vt == "float" ? "pyh" : "pyh" + L) << ", (double)" << (vt == "float" ? "pzh" : "pzh" + L)
+              << ", " << lane(ml.xl) << ", " << lane(ml.yl) << ", " << lane(ml.zl) << ", " << me.ks << ", "
+              << (vt == "float" ? "dxh" : "dxh" + L) << ", " << (vt == "float" ? "dxl" : "dxl" + L)
+              << ", bt, mu, " << M << ", " << dk << ", [&](int j, float v) { ";
+            if (vt == "float")
+                o << nm << "[j] = v; });\n";
+            else
+                o << nm << "[j].v." << (q ? "y" : "x") << " = v; });\n";
+        }
+        o << "  }\n";
+        return o.str();
+    }
+    const std::string lo = "    const " + vt + " pxl = " + me.xl + ", pyl = " + me.yl + ", pzl = " + me.zl + ";\n";
+    if (leaf_calls) {
+        acc = nm + ".v[";
+        o << "  FdLeafOut<" << no << "> " << nm << ";\n  {\n" << hi << lo;
+        if (op == OP_GLEAF) {
+            o << time_diff_expr(la, lb, "float")
+              << "    const float eps = fd_eps(pxh, pyh, pzh, pxl, pyl, pzl, Q.muh, Q.mul);\n"
+              << "    " << nm << " = g_leaf_fn<" << M << ", " << dk << ">(eps, pzh + pzl, " << me.ks
+              << ", dxh, dxl, Q.beta);\n  }\n";
+        } else {
+            o << "    const float qx = pxh + pxl, qy = pyh + pyl, qz = pzh + pzl;\n"
+              << "    const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));\n"
+              << "    " << nm << " = v_leaf_fn<" << M << ", " << dk << ">(q2, qz, " << me.ks << ", Q.Lam);\n  }\n";
+        }
+        return o.str();
+    }
+    o << "  " << vt << " " << nm << "[" << no << "];\n  {\n" << hi << lo;
+    if (op == OP_GLEAF) {
+        o << time_diff_expr(la, lb, vt) << "    const " << vt
+          << " eps = fd_eps(pxh, pyh, pzh, pxl, pyl, pzl, Q.muh, Q.mul);\n"
+          << "    g_family<" << vt << ">(eps, pzh + pzl, " << me.ks << ", dxh, dxl, " << vt << "(Q.beta), " << M << ", "
+          << dk << ", [&](int j, " << vt << " v) { " << nm << "[j] = v; });\n  }\n";
+    } else {
+        o << "    const " << vt << " qx = pxh + pxl, qy = pyh + pyl, qz = pzh + pzl;\n"
+          << "    const " << vt << " q2 = fd_fma(qx, qx, fd_fma(qy, qy, qz * qz));\n"
+          << "    v_family<" << vt << ">(q2, qz, " << me.ks << ", Q.Lam, " << M << ", " << dk << ", [&](int j, " << vt
+          << " v) { " << nm << "[j] = v; });\n  }\n";
+    }
+    return o.str();
+}
+
+// Executed FP32 work of one leaf family (for ranking the leaf cache's
+// candidates): momentum sums, eps, Fermi factor and exponentials, the series.
+double leaf_cost(uint64_t w) {
+    const uint32_t mask = fa(w);
+    int terms = 0;
+    for (int j = 0; j < 7; ++j) terms += ((mask >> (2 * j)) & 3u) != 0;
+    const int M = (int)((w >> 40) & 7u), dk = (int)((w >> 43) & 1u), Mx = M + dk;
+    double c = 6.0 * std::max(terms - 1, 0);
+    if ((w & 63u) == OP_GLEAF) {
+        c += 36.0 + 3.0 * 8.0;                       // eps, Fermi factor, exponentials (an SFU op ~ 8)
+        for (int k = 0; k < Mx; ++k) c += (k + 1) + 4;
+        if (Mx)
+            for (int j = 0; j <= Mx; ++j) c += j + 1;
+    } else {
+        c += 12.0 + 8.0 + Mx;
+    }
+    return c;
+}
+
 // sync_every > 0: a block barrier after every sync_every arithmetic
 // statements, so that the warps of a CTA walk the (long, straight-line) code
 // together and share the instruction-cache lines they fetch.  Every thread of
@@ -289,15 +388,20 @@ std::string time_diff_expr(uint32_t la, uint32_t lb, const std::string &vt) {
 // leaf_calls: leaves call the out-of-line family functions instead of inlining them.
 // vt: value type of the generated code, "float" (one sample) or "FdF2" (two
 // samples in packed two-lane arithmetic; no out-of-line leaves).
+using LeafCache = std::map<uint32_t, int>;   // leaf instruction -> first float of its values in the cache
+
 std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, const std::vector<uint64_t> &words,
                        int N, int n_slots, const char *qual, int sync_every, int leaf_calls,
-                       const std::string &vt = "float") {
+                       const std::string &vt = "float", const LeafCache *cache = nullptr, int lc_stride = 0) {
+    static const LeafCache empty;
+    const auto cache_end = empty.end();
     std::ostringstream o;
     std::vector<std::string> cur(n_slots + 1);
     cur[0] = "0.0f";
     cur[1] = "1.0f";
     for (int j = 0; j < N; ++j) cur[2 + j] = "V.t[" + std::to_string(j) + "]";
-    o << qual << " " << vt << " fd_s" << q << "(const FdSVT<" << vt << ", " << N << "> &V, const FdPar &Q) {\n";
+    o << qual << " " << vt << " fd_s" << q << "(const FdSVT<" << vt << ", " << N << "> &V, const FdPar &Q"
+      << (cache ? ", const float *L" : "") << ") {\n";
     int k = 0, since_sync = 0;
     for (const auto &kv : s.keep) {
         const TIns &t = ins[kv.first];
@@ -326,80 +430,22 @@ std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, cons
             }
             for (auto &u : upd) cur[u.first] = u.second;
         } else if (t.op == OP_GLEAF || t.op == OP_VLEAF) {
-            const uint32_t d = fd_(w), mask = fa(w);
+            const uint32_t d = fd_(w);
             const int no = leaf_outputs(w);
-            const int M = (int)((w >> 40) & 7u), dk = (int)((w >> 43) & 1u);
-            const bool precise = t.op == OP_GLEAF && ((w >> FD_LEAF_PRECISE_BIT) & 1u);
-            const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
-            const MomExpr me = momentum_expr(mask, N, precise ? "(double)" : "");
             const std::string nm = "l" + std::to_string(k++);
-            const std::string hi = "    const " + vt + " pxh = " + me.x + ", pyh = " + me.y + ", pzh = " + me.z + ";\n";
-            if (precise) {
-                // FP64 family (the single G line of the order-1 diagram), per sample (packed: per lane)
-                o << "  " << vt << " " << nm << "[" << no << "];\n  {\n" << hi << time_diff_expr(la, lb, vt)
-                  << "    const double bt = (double)Q.beta + (double)Q.betal, mu = (double)Q.muh + (double)Q.mul;\n";
-                const int lanes = vt == "float" ? 1 : 2;
-                for (int q = 0; q < lanes; ++q) {
-                    const std::string L = vt == "float" ? "" : ".v." + std::string(q ? "y" : "x");
-                    const MomExpr ml = momentum_expr(mask, N, "(double)");
-                    auto lane = [&](const std::string &e) {
-                        if (vt == "float") return e;
-                        // packed operands: take this lane of every V member
-                        std::string r = e, out;
-                        size_t pos = 0;
-                        while (true) {
-                            const size_t a = r.find("]", pos);
-                            if (a == std::string::npos) break;
-                            out += r.substr(pos, a + 1 - pos) + L;
-                            pos = a + 1;
-                        }
-                        return out + r.substr(pos);
-                    };
-                    o << "    g_family_precise((double)" << (vt == "float" ? "pxh" : "pxh" + L) << ", (double)"
-                      << (vt == "float" ? "pyh" : "pyh" + L) << ", (double)" << (vt == "float" ? "pzh" : "pzh" + L)
-                      << ", " << lane(ml.xl) << ", " << lane(ml.yl) << ", " << lane(ml.zl) << ", " << me.ks << ", "
-                      << (vt == "float" ? "dxh" : "dxh" + L) << ", " << (vt == "float" ? "dxl" : "dxl" + L)
-                      << ", bt, mu, " << M << ", " << dk << ", [&](int j, float v) { ";
-                    if (vt == "float")
-                        o << nm << "[j] = v; });\n";
-                    else
-                        o << nm << "[j].v." << (q ? "y" : "x") << " = v; });\n";
-                }
-                o << "  }\n";
+            const auto hit = cache ? cache->find(kv.first) : cache_end;
+            if (cache && hit != cache->end()) {
+                // computed once per sample by fd_leaves: read from the leaf cache
+                o << "  const float " << nm << "[" << no << "] = {";
+                for (int j = 0; j < no; ++j)
+                    o << (j ? ", " : "") << "L[" << (hit->second + j) * lc_stride << "]";
+                o << "};\n";
                 for (int j = 0; j < no; ++j) cur[d + j] = nm + "[" + std::to_string(j) + "]";
                 continue;
             }
-            const std::string lo =
-                "    const " + vt + " pxl = " + me.xl + ", pyl = " + me.yl + ", pzl = " + me.zl + ";\n";
-            if (leaf_calls) {
-                o << "  FdLeafOut<" << no << "> " << nm << ";\n  {\n" << hi << lo;
-                if (t.op == OP_GLEAF) {
-                    o << time_diff_expr(la, lb, "float")
-                      << "    const float eps = fd_eps(pxh, pyh, pzh, pxl, pyl, pzl, Q.muh, Q.mul);\n"
-                      << "    " << nm << " = g_leaf_fn<" << M << ", " << dk << ">(eps, pzh + pzl, " << me.ks
-                      << ", dxh, dxl, Q.beta);\n  }\n";
-                } else {
-                    o << "    const float qx = pxh + pxl, qy = pyh + pyl, qz = pzh + pzl;\n"
-                      << "    const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));\n"
-                      << "    " << nm << " = v_leaf_fn<" << M << ", " << dk << ">(q2, qz, " << me.ks
-                      << ", Q.Lam);\n  }\n";
-                }
-                for (int j = 0; j < no; ++j) cur[d + j] = nm + ".v[" + std::to_string(j) + "]";
-                continue;
-            }
-            o << "  " << vt << " " << nm << "[" << no << "];\n  {\n" << hi << lo;
-            if (t.op == OP_GLEAF) {
-                o << time_diff_expr(la, lb, vt) << "    const " << vt
-                  << " eps = fd_eps(pxh, pyh, pzh, pxl, pyl, pzl, Q.muh, Q.mul);\n"
-                  << "    g_family<" << vt << ">(eps, pzh + pzl, " << me.ks << ", dxh, dxl, " << vt << "(Q.beta), " << M
-                  << ", " << dk << ", [&](int j, " << vt << " v) { " << nm << "[j] = v; });\n  }\n";
-            } else {
-                o << "    const " << vt << " qx = pxh + pxl, qy = pyh + pyl, qz = pzh + pzl;\n"
-                  << "    const " << vt << " q2 = fd_fma(qx, qx, fd_fma(qy, qy, qz * qz));\n"
-                  << "    v_family<" << vt << ">(q2, qz, " << me.ks << ", Q.Lam, " << M << ", " << dk << ", [&](int j, "
-                  << vt << " v) { " << nm << "[j] = v; });\n  }\n";
-            }
-            for (int j = 0; j < no; ++j) cur[d + j] = nm + "[" + std::to_string(j) + "]";
+            std::string acc;
+            o << leaf_block(w, nm, t.op, N, vt, leaf_calls, acc);
+            for (int j = 0; j < no; ++j) cur[d + j] = acc + std::to_string(j) + "]";
         } else if (t.op == OP_CONST) {
             uint32_t bits = (uint32_t)(w >> 32);
             float f;
@@ -414,6 +460,7 @@ std::string emit_slice(const Slice &s, int q, const std::vector<TIns> &ins, cons
 struct Program {
     std::vector<std::string> modules;   // module 0 holds the kernel
     int n_modules = 1;
+    int lc_floats = 0;                  // leaf-cache floats per sample (shared memory: x threads x spt)
 };
 
 // A compilation unit: one slice, or every slice of one root (the slices are
@@ -425,14 +472,14 @@ struct Unit {
 };
 
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots);
+                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots, int leaf_cache);
 
 Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units, int sync_every,
                      int leaf_calls, int spt = 1, int unit_cap = 6000, int pair = 0, int sv_smem = 0,
-                     int cross_roots = 0) {
-    if (spt > 1)
+                     int cross_roots = 0, int leaf_cache = 0) {
+    if (spt > 1 || leaf_cache > 0)
         return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls, pair, sync_every,
-                                 sv_smem, cross_roots);
+                                 sv_smem, cross_roots, leaf_cache);
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -565,7 +612,7 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
 // unit adds into the accumulators of the roots it touches, and every root is
 // flushed after all units.
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots) {
+                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots, int leaf_cache) {
     const std::string vs = sv_smem ? " * " + std::to_string(T) : "";
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
@@ -604,6 +651,47 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         units.back().slices.push_back((int)i);
         units.back().cost = unit_cost(units.back().slices);
     }
+    // leaf cache: families used by several units, computed once per sample
+    // by fd_leaves into shared memory [float][sample][thread] (stride spt T)
+    // and read by the units, the most work saved per float first, up to
+    // leaf_cache floats per sample
+    LeafCache cache;
+    int lc_floats = 0;
+    std::vector<uint32_t> cached;
+    if (leaf_cache > 0) {
+        std::map<uint32_t, int> uses;
+        for (const Unit &u : units) {
+            std::vector<uint32_t> ls;
+            for (int i : u.slices)
+                for (auto &kv : sl[i].keep)
+                    if (ins[kv.first].op == OP_GLEAF || ins[kv.first].op == OP_VLEAF) ls.push_back(kv.first);
+            std::sort(ls.begin(), ls.end());
+            ls.erase(std::unique(ls.begin(), ls.end()), ls.end());
+            for (uint32_t l : ls) ++uses[l];
+        }
+        std::vector<std::pair<double, uint32_t>> cand;
+        for (auto &kv : uses) {
+            if (kv.second < 2) continue;
+            const uint64_t w = g.h_tape[ins[kv.first].w];
+            cand.push_back({leaf_cost(w) * (kv.second - 1) / leaf_outputs(w), kv.first});
+        }
+        std::sort(cand.begin(), cand.end(), [](const std::pair<double, uint32_t> &a,
+                                               const std::pair<double, uint32_t> &b) { return a.first > b.first; });
+        for (auto &c : cand) {
+            const int wd = leaf_outputs(g.h_tape[ins[c.second].w]);
+            if (lc_floats + wd > leaf_cache) continue;
+            cached.push_back(c.second);
+            lc_floats += wd;
+        }
+        std::sort(cached.begin(), cached.end());
+        int off = 0;
+        for (uint32_t c : cached) {
+            cache[c] = off;
+            off += leaf_outputs(g.h_tape[ins[c].w]);
+        }
+    }
+    const LeafCache *cp = lc_floats ? &cache : nullptr;
+    const int lc_stride = spt * T;
     int n_mod = 1;
     if (total > kSingleModuleCost && max_modules > 1)
         n_mod = std::max(2, std::min(max_modules, (int)(total / 2500.0) + 1));
@@ -631,6 +719,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
     const bool multi = n_mod > 1;
     Program Pg;
     Pg.n_modules = n_mod;
+    Pg.lc_floats = lc_floats;
     Pg.modules.assign(n_mod, std::string());
     std::vector<std::ostringstream> src(n_mod);
     for (int m = 0; m < n_mod; ++m)
@@ -638,14 +727,35 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
                << " root-accumulate slices, " << spt << " samples per thread" << (pair ? " in packed pairs" : "")
                << "\n#include \"fd_jit_rt.cuh\"\nusing FdSV = FdSVT<float, " << N << ">;\n";
     const char *unit_qual = multi ? "extern \"C\" __device__ __noinline__" : "static __device__ __noinline__";
-    const std::string sig = "(const FdSV *V, FdPar Q, const float *cs, const float *sn, float *re, float *im)";
+    const std::string sig =
+        "(const FdSV *V, FdPar Q, const float *LC, const float *cs, const float *sn, float *re, float *im)";
+    const std::string lcarg = cp ? ", LC + p * " + std::to_string(T) : "";
+    // the leaf phase: every cached family of the thread's spt samples
+    if (cp) {
+        std::ostringstream lf;
+        lf << "static __device__ __noinline__ void fd_leaves(const FdSV *Vb, FdPar Q, float *LC) {\n#pragma unroll 1\n"
+              "  for (int p = 0; p < " << spt << "; ++p) {\n    const FdSV &V = Vb[p" << vs << "];\n    float *L = LC + p * "
+           << T << ";\n";
+        int k = 0;
+        for (uint32_t c : cached) {
+            const uint64_t w = g.h_tape[ins[c].w];
+            const std::string nm = "c" + std::to_string(k++);
+            std::string acc;
+            lf << leaf_block(w, nm, ins[c].op, N, "float", 0, acc);
+            const int off = cache.at(c);
+            for (int j = 0; j < leaf_outputs(w); ++j)
+                lf << "  L[" << (off + j) * lc_stride << "] = " << acc << j << "];\n";
+        }
+        lf << "  }\n}\n";
+        src[0] << lf.str();
+    }
     if (cross_roots) {
         // re/im: [root][sample] accumulators of the whole graph
         for (size_t u = 0; u < units.size(); ++u) {
             const int m = mod_of[u];
             for (int i : units[u].slices)
                 src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, "static __device__ __forceinline__",
-                                     0, leaf_calls, pair ? "FdF2" : "float");
+                                     0, leaf_calls, pair ? "FdF2" : "float", cp, lc_stride);
             if (multi && m != 0) src[0] << "extern \"C\" __device__ void fd_u" << u << sig << ";\n";
             const std::vector<int> &us = units[u].slices;
             src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
@@ -663,7 +773,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
                         src[m] << "      v = fd_s" << i << "(W, Q); r = fd_fma(v, FdF2(cs[" << c0 << "], cs[" << c1
                                << "]), r); i = fd_fma(v, FdF2(sn[" << c0 << "], sn[" << c1 << "]), i);\n";
                     } else {
-                        src[m] << "      v = fd_s" << i << "(V[p" << vs << "], Q); r = fmaf(v, cs[" << c0
+                        src[m] << "      v = fd_s" << i << "(V[p" << vs << "], Q" << lcarg << "); r = fmaf(v, cs[" << c0
                                << "], r); i = fmaf(v, sn[" << c0 << "], i);\n";
                     }
                 }
@@ -678,11 +788,12 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         }
         std::ostringstream b;
         b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV *V, "
-             "const FdPar &Q, const float *cs, const float *sn, K *k) {\n    float re["
+             "const FdPar &Q, float *LC, const float *cs, const float *sn, K *k) {\n"
+          << (cp ? "    fd_leaves(V, Q, LC);\n" : "") << "    float re["
           << R * spt << "], im[" << R * spt << "];\n#pragma unroll\n    for (int q = 0; q < " << R * spt
           << "; ++q) re[q] = im[q] = 0.0f;\n";
         for (size_t u = 0; u < units.size(); ++u)
-            b << "    fd_u" << u << "(V, Q, cs, sn, re, im);\n" << (sync_units ? "    __syncthreads();\n" : "");
+            b << "    fd_u" << u << "(V, Q, LC, cs, sn, re, im);\n" << (sync_units ? "    __syncthreads();\n" : "");
         for (const TIns &t : ins) {
             if (t.op != OP_RFLUSH) continue;
             const int r = (int)fd_(g.h_tape[t.w]);
@@ -694,7 +805,8 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         src[0] << b.str();
         src[0] << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks
                << ") fd_jit_kernel(const __grid_constant__ EvalArgs A) {\n  jit_main_loop<FdBody, " << N << ", " << DIM
-               << ", " << R << ", " << T << ", " << spt << ", " << (sv_smem ? T : 1) << ">(A);\n}\n";
+               << ", " << R << ", " << T << ", " << spt << ", " << (sv_smem ? T : 1) << ", " << lc_floats
+               << ">(A);\n}\n";
         for (int m = 0; m < n_mod; ++m) Pg.modules[m] = src[m].str();
         return Pg;
     }
@@ -702,7 +814,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         const int m = mod_of[u];
         for (int i : units[u].slices)
             src[m] << emit_slice(sl[i], i, ins, g.h_tape, N, (int)h.n_slots, "static __device__ __forceinline__", 0,
-                                 leaf_calls, pair ? "FdF2" : "float");
+                                 leaf_calls, pair ? "FdF2" : "float", cp, lc_stride);
         if (multi && m != 0) src[0] << "extern \"C\" __device__ void fd_u" << u << sig << ";\n";
         if (pair) {
             // samples p and p + 1 in the two lanes of packed arithmetic
@@ -722,13 +834,15 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         src[m] << unit_qual << " void fd_u" << u << sig << " {\n#pragma unroll 1\n  for (int p = 0; p < " << spt
                << "; ++p) {\n    float r = 0.0f, i = 0.0f, v;\n";
         for (int i : units[u].slices)
-            src[m] << "    v = fd_s" << i << "(V[p" << vs << "], Q); r = fmaf(v, cs[p * " << N << " + " << sl[i].line
+            src[m] << "    v = fd_s" << i << "(V[p" << vs << "], Q" << lcarg << "); r = fmaf(v, cs[p * " << N << " + "
+                   << sl[i].line
                    << "], r); i = fmaf(v, sn[p * " << N << " + " << sl[i].line << "], i);\n";
         src[m] << "    re[p] += r;\n    im[p] += i;\n  }\n}\n";
     }
     std::ostringstream b;
     b << "struct FdBody {\n  template <class K>\n  static __device__ __forceinline__ void run(const FdSV *V, const FdPar &Q, "
-         "const float *cs, const float *sn, K *k) {\n";
+         "float *LC, const float *cs, const float *sn, K *k) {\n"
+      << (cp ? "    fd_leaves(V, Q, LC);\n" : "");
     for (const TIns &t : ins) {
         if (t.op != OP_RFLUSH) continue;
         const int r = (int)fd_(g.h_tape[t.w]);
@@ -737,7 +851,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
           << spt << "; ++p) re[p] = im[p] = 0.0f;\n";
         for (size_t u = 0; u < units.size(); ++u)
             if (units[u].root == r)
-                b << "      fd_u" << u << "(V, Q, cs, sn, re, im);\n" << (sync_units ? "      __syncthreads();\n" : "");
+                b << "      fd_u" << u << "(V, Q, LC, cs, sn, re, im);\n" << (sync_units ? "      __syncthreads();\n" : "");
         b << "      flush_samples<" << r << ", " << (rt & 255u) << ", " << (((rt >> 24) & 255u) ? 1 : 0) << ", "
           << spt << ", " << N << ">(k, re, im);\n    }\n";
     }
@@ -745,7 +859,8 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
     src[0] << b.str();
     src[0] << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks
            << ") fd_jit_kernel(const __grid_constant__ EvalArgs A) {\n  jit_main_loop<FdBody, " << N << ", " << DIM
-           << ", " << R << ", " << T << ", " << spt << ", " << (sv_smem ? T : 1) << ">(A);\n}\n";
+           << ", " << R << ", " << T << ", " << spt << ", " << (sv_smem ? T : 1) << ", " << lc_floats
+           << ">(A);\n}\n";
     for (int m = 0; m < n_mod; ++m) Pg.modules[m] = src[m].str();
     return Pg;
 }
@@ -874,12 +989,14 @@ fd_status check_options(const fd_jit_options *o) {
                "packed pairs need an even number of samples per thread and inlined leaves");
     FD_REQUIRE(o->sv_smem == 0 || o->spt >= 2, "per-sample inputs in shared memory need spt >= 2");
     FD_REQUIRE(o->cross_roots == 0 || o->spt >= 2, "units across roots need spt >= 2");
+    FD_REQUIRE(o->leaf_cache >= 0 && o->leaf_cache <= 4096, "leaf_cache must be in 0..4096 floats per sample");
+    FD_REQUIRE(o->leaf_cache == 0 || (!o->pair && !o->leaf_calls), "the leaf cache needs scalar, inlined leaves");
     return FD_OK;
 }
 
 Program emit(const fd_graph &g, const fd_jit_options &o) {
     return emit_program(g, o.threads, o.min_blocks, o.max_modules, o.root_units, o.sync_every, o.leaf_calls, o.spt,
-                        o.unit_cap, o.pair, o.sv_smem, o.cross_roots);
+                        o.unit_cap, o.pair, o.sv_smem, o.cross_roots, o.leaf_cache);
 }
 }  // namespace
 
@@ -955,7 +1072,9 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const 
     // of FdSV), then the tile histogram in what the resident CTAs leave free,
     // at most 96 KB so that the rest of the unified L1 keeps the per-thread
     // local arrays of the sample-loop variants
-    const long sv_b = opt->sv_smem ? (long)threads * opt->spt * (long)sizeof(float) * fd_sv_words((int)g->hdr.order) : 0;
+    const long sv_b = (opt->sv_smem ? (long)threads * opt->spt * (long)sizeof(float) * fd_sv_words((int)g->hdr.order)
+                                    : 0) +
+                      (long)threads * opt->spt * (long)sizeof(float) * P.lc_floats;
     int sm_total = 0, optin = 0, reserved = 0, hist_cap = 0;
     const bool have_attrs =
         cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&

@@ -760,20 +760,24 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
 }
 
 // Variant with P samples per thread per pass, handled one after another by
-// every compilation unit (Body::run loops over the samples inside each unit):
+// every compilation unit (Body::run loops over the samples inside each unit;
+// with a leaf cache, Body::run first computes the cached leaf families of the
+// P samples into shared memory, where every unit reads them):
 // the unit's code is fetched once and then re-executed from the instruction
 // cache for the other P - 1 samples, at no cost in registers.  The per-sample
 // inputs live in local memory (SVS = 1) or, with SVS = T, in dynamic shared
 // memory as [sample][thread] rows of FdSVT (sample p of this thread at
 // V[p * SVS]); the tile histogram, when the launch provides it, follows them.
-template <class Body, int N, int DIM, int R, int T, int P, int SVS = 1>
+template <class Body, int N, int DIM, int R, int T, int P, int SVS = 1, int LCW = 0>
 __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
     __shared__ double acc[T / 32][R * 8];
     __shared__ int next_item;
     extern __shared__ float dyn_smem[];
     using FdSV = FdSVT<float, N>;
     constexpr int SV_FLOATS = SVS > 1 ? T * P * fd_sv_words(N) : 0;
-    float *const hist_smem = dyn_smem + SV_FLOATS;
+    // leaf cache: LCW floats per sample, [float][sample p][thread], this thread's column
+    float *const LC = LCW > 0 ? dyn_smem + SV_FLOATS + threadIdx.x : nullptr;
+    float *const hist_smem = dyn_smem + SV_FLOATS + T * P * LCW;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = A.n_inst * A.tiles_per_inst;
     const uint32_t iter = A.iter + (A.iter_dev ? *A.iter_dev : 0u);
@@ -810,7 +814,7 @@ __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
                 K[p] = FdSink<N>{acc[warp], jac[p], valid, 0.0f, A.per_sample_f,
                                  (int64_t)D.id * A.r_max * 2 * A.n_per_inst + idx, A.n_per_inst};
             }
-            Body::run(V, Q, cs, sn, K);
+            Body::run(V, Q, LC, cs, sn, K);
             if (A.abs_f) {
 #pragma unroll
                 for (int p = 0; p < P; ++p) {

@@ -1,9 +1,9 @@
 """Per-sample parity at 2^16 samples per order (Eq. sigma_integration with
 the counterterm roots of Eq. sigma_xi_dmu_dlambda) on both contraction
 paths: the tape interpreter and the specialised kernel (one sample per
-thread, and the sample-loop variant the benchmark runs: 4 samples per
-thread with their inputs in shared memory, units of cost <= 12000, a
-barrier after every unit).  Orders 3 and 4 with every k-derivative root,
+thread; the sample-loop variant with 4 samples per thread, their inputs in
+shared memory, units of cost <= 12000 and a barrier after every unit; and
+with 2 samples per thread and a 32-float leaf cache).  Orders 3 and 4 with every k-derivative root,
 order 5 with the 15 roots of the benchmark; the oracle runs in worker
 processes.  Criterion in tests/parity.py."""
 import numpy as np
@@ -20,7 +20,9 @@ N = 1 << 16
 CASES = [(3, True, 81), (4, True, 82), (5, False, 83)]
 VARIANTS = {"interpreter": None,
             "specialised": dict(),
-            "specialised_loop": dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sv_smem=True, sync_every=1)}
+            "specialised_loop": dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sv_smem=True, sync_every=1),
+            "specialised_leaf_cache": dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sv_smem=True,
+                                           sync_every=1, leaf_cache=32)}
 
 
 @pytest.fixture(scope="module")

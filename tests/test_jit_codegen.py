@@ -83,7 +83,7 @@ def test_sample_loop_units_cover_every_slice_once(unit_cap, pair, cross):
         units += re.findall(r"__device__ __noinline__ void (fd_u\d+)\(", src)
     body, _ = api.jit_source(tape, 0, **kw)
     assert slices and len(slices) == len(set(slices))
-    assert sorted(re.findall(r"(fd_u\d+)\(V, Q, cs, sn, re, im\)", body)) == sorted(units)
+    assert sorted(re.findall(r"(fd_u\d+)\(V, Q, LC, cs, sn, re, im\)", body)) == sorted(units)
     flushes = re.findall(r"flush(?:_samples)?<(\d+), ", body)
     assert sorted(int(r) for r in flushes) == list(range(len(fdgraph.graph_roots(5))))
     if unit_cap == 0:
@@ -125,3 +125,42 @@ def test_contraction_ops_below_the_naive_diagram_sum():
         ratios.append(naive / ops)
     assert ratios == sorted(ratios)          # the compression grows with the order
     assert fdgraph.contraction_ops(fdgraph.compile_graph(4, [(4, 0, 0, 0)], budget=8192).to_bytes()) == 721
+
+
+@pytest.mark.parametrize("kw", [dict(spt=2, sv_smem=True, leaf_cache=32), dict(spt=1, leaf_cache=96)])
+def test_leaf_cache_stores_each_family_once_and_units_read_it(kw):
+    # fd_leaves computes every cached family once per sample and stores its
+    # values at distinct offsets [float][sample][thread]; the units read those
+    # offsets instead of computing the family (at most leaf_cache floats)
+    tape = _tape(4, True)
+    T, spt = 256, kw["spt"]
+    src, n_mod = api.jit_source(tape, 0, threads=T, min_blocks=1, max_modules=1, unit_cap=6000, **kw)
+    assert n_mod == 1
+    head = src[src.index("fd_leaves(const FdSV *Vb"):src.index("static __device__ __forceinline__ float fd_s")]
+    stores = [int(m) for m in re.findall(r"  L\[(\d+)\] = c\d+\[\d+\];", head)]
+    assert stores and len(stores) == len(set(stores)) <= kw["leaf_cache"]
+    assert all(s % (T * spt) == 0 for s in stores)
+    body = src.replace(head, "")
+    loads = set(int(m) for m in re.findall(r"[{ ]L\[(\d+)\]", body))
+    assert loads and loads <= set(stores)
+    assert "fd_leaves(V, Q, LC);" in src
+    assert re.search(r"jit_main_loop<FdBody, 4, 15, \d+, 256, %d, %d, %d>" % (spt, T if kw.get("sv_smem") else 1,
+                                                                              len(stores)), src)
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None, reason="nvcc not available")
+def test_leaf_cache_source_compiles(tmp_path):
+    src, _ = api.jit_source(_tape(3, True), 0, threads=256, min_blocks=1, max_modules=1, spt=2, sv_smem=True,
+                            leaf_cache=24)
+    f = tmp_path / "lc.cu"
+    f.write_text(src)
+    r = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-cubin",
+                        "-I", CSRC, "-o", str(tmp_path / "lc.cubin"), str(f)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("kw", [dict(leaf_cache=-1), dict(leaf_cache=8, spt=2, pair=True),
+                                dict(leaf_cache=8, leaf_calls=True)])
+def test_leaf_cache_rejects_invalid_options(kw):
+    with pytest.raises(api.L.FdError):
+        api.jit_source(_tape(2, False), 0, threads=256, min_blocks=1, **kw)
