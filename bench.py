@@ -229,7 +229,7 @@ def flow_vs_vegas(args, api, params, order, seed):
                                lr=1e-3, seed=FW["seed"], vegas_steps=100, evals_per_batch=4, defensive=0.1)
     torch.cuda.synchronize()
     flow_train_s = time.perf_counter() - t0
-    cmp = driver.compare(Gs, params[0], Vs, F, FW["n_compare"], seed=seed + 7, batches=16, defensive=0.1)
+    cmp = driver.compare(Gs, params[0], Vs, F, FW["n_compare"], seed=seed + 7, batches=64, defensive=0.1)
     # the paper's sampler: independence Metropolis-Hastings chains with the flow
     # (NF-MCMC) or the VEGAS map (VEGAS-MCMC) as proposal, against the same
     # VEGAS importance-sampling reference (figure of merit 1 / (variance x time))
@@ -239,9 +239,9 @@ def flow_vs_vegas(args, api, params, order, seed):
            "median": cmp["vegas"]["samples_per_s"] / cmp["vegas"]["var_median"]}
     eff = {"quantity": "Re Sigma^(5)(k_F, i w0), single-root order-5 graph", "vegas": cmp["vegas"],
            "flow": cmp["flow"], "flow_over_vegas": cmp["flow_over_vegas"],
-           "flow_over_vegas_median": cmp["flow_over_vegas_median"],
+           "flow_over_vegas_median": cmp["flow_over_vegas_median"], "ci95": cmp["ci95"],
            "per_sample_variance_gain": cmp["vegas"]["var_per_sample"] / cmp["flow"]["var_per_sample"],
-           "means_agree_sigma": cmp["means_agree_sigma"], "compare": "16 batches x %d samples per sampler" %
+           "means_agree_sigma": cmp["means_agree_sigma"], "compare": "64 batches x %d samples per sampler" %
            FW["n_compare"], "proposal": "flow on the VEGAS grid's input coordinates, 10 % defensive uniform share",
            "flow_train_steps": max(1, args.flow_steps), "flow_batch": args.flow_batch,
            "flow_tensor_path": ["mma.sync", "tcgen05"][args.flow_tensor_path],

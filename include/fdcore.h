@@ -379,6 +379,13 @@ fd_status fd_nsf_forward(const fd_nsf *f, const float *z, int64_t n, float *x, f
  * inst << 8 | block), u = ((w >> 9) + 0.5) 2^-23). */
 fd_status fd_nsf_sample(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n, float *x,
                         float *logq, void *stream);
+/* The sampler's draws as importance-sampling proposals (App. A: the flow
+ * proposes configurations for the integral of Sec. IV and for the NF-MCMC
+ * chains of Sec. V): the same stream and points as fd_nsf_sample, with w
+ * (device FP32 [n]) = 1 / q(x), the weight fd_integrand_eval takes as
+ * point_w and the chains take through the integrand's weighted values. */
+fd_status fd_nsf_sample_w(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n, float *x,
+                          float *w, void *stream);
 /* Density at given points: z = T^-1(x) (device FP32 [dim][n], the layers in
  * reverse order, each spline inverted through its bin's quadratic) and
  * log q(x) (device FP32 [n]) for device x [dim][n] in [0, 1]^dim.

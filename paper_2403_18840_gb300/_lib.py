@@ -97,6 +97,7 @@ SIGNATURES = {
     "fd_nsf_set_params": (_i32, [_vp, _pf, _i64]),
     "fd_nsf_forward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "fd_nsf_sample": (_i32, [_vp, _u64, _u64, _i32, _i64, _vp, _vp, _vp]),
+    "fd_nsf_sample_w": (_i32, [_vp, _u64, _u64, _i32, _i64, _vp, _vp, _vp]),
     "fd_nsf_log_density": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "fd_nsf_kl_grad": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fd_nsf_train": (_i32, [_vp, _vp, _vp, _i64, _i32, _f32, _vp, _vp]),

@@ -255,6 +255,10 @@ class Flow:
         L.check(L.lib().fd_flow_sample(self.handle, seed, it, inst, n, _ptr(x), _ptr(w), _stream_ptr(stream)))
         return x, w
 
+    def draw(self, seed, it, inst, n, stream=None):
+        """Proposals: (x [dim][n], w = 1/q(x) [n]) (the flow's own sample stream)."""
+        return self.sample(seed, it, inst, n, stream)
+
     def set_tensor_path(self, path):
         """Sampling / density on mma.sync (0, default) or tcgen05 (1)."""
         L.check(L.lib().fd_flow_set_tensor_path(self.handle, path))
@@ -329,6 +333,14 @@ class SplineFlow:
         lq = torch.empty((n,), dtype=torch.float32, device="cuda")
         L.check(L.lib().fd_nsf_sample(self.handle, seed, it, inst, n, _ptr(x), _ptr(lq), _stream_ptr(stream)))
         return x, lq
+
+    def draw(self, seed, it, inst, n, stream=None):
+        """Proposals for the integrand and the chains: (x [dim][n], w = 1/q(x) [n]),
+        the same stream as sample()."""
+        x = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")
+        w = torch.empty((n,), dtype=torch.float32, device="cuda")
+        L.check(L.lib().fd_nsf_sample_w(self.handle, seed, it, inst, n, _ptr(x), _ptr(w), _stream_ptr(stream)))
+        return x, w
 
     def log_density(self, x, stream=None):
         """(z = T^-1(x), log q(x)) for device points x [dim][n]."""

@@ -30,8 +30,9 @@ struct NsfArgs {
     const float *params;      // all layers, in order
     const float *z;           // [dim][ldz] or null: Philox stream
     float *x;                 // [dim][ldx]
-    float *logq;              // [n]
+    float *logq;              // [n]: log q(x), or with inv_q the importance weight 1 / q(x)
     int64_t n, ldz, ldx;
+    int inv_q;
     int dim, n_layers;
     uint32_t seed_lo, seed_hi, iter, inst;
 };
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(128) nsf_kernel(const NsfArgs a) {
 #pragma unroll
     for (int j = 0; j < kMaxDim; ++j)
         if (j < D) a.x[(int64_t)j * a.ldx + i] = v[j];
-    a.logq[i] = logq;
+    a.logq[i] = a.inv_q ? expf(-logq) : logq;
 }
 
 
@@ -299,7 +300,8 @@ fd_status nsf_sizes(int dim, int n_layers, int64_t &total, int64_t &max_layer) {
 }
 
 fd_status nsf_launch(const fd_nsf *f, bool inverse, const float *z, int64_t ldz, uint64_t seed, uint64_t iter,
-                     int32_t inst, int64_t n, float *x, int64_t ldx, float *logq, cudaStream_t stream) {
+                     int32_t inst, int64_t n, float *x, int64_t ldx, float *logq, cudaStream_t stream,
+                     bool inv_q = false) {
     FD_REQUIRE(f && x && logq, "flow, x and logq are required");
     FD_REQUIRE(n > 0 && n <= (int64_t(1) << 36), "n must be in [1, 2^36]");
     FD_REQUIRE(inst >= 0 && inst < (1 << 24), "inst out of range");
@@ -311,6 +313,7 @@ fd_status nsf_launch(const fd_nsf *f, bool inverse, const float *z, int64_t ldz,
     a.z = z;
     a.x = x;
     a.logq = logq;
+    a.inv_q = inv_q ? 1 : 0;
     a.n = n;
     a.ldz = ldz;
     a.ldx = ldx;
@@ -398,6 +401,11 @@ extern "C" fd_status fd_nsf_log_density(const fd_nsf *f, const float *x, int64_t
 extern "C" fd_status fd_nsf_sample(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n, float *x,
                                    float *logq, void *stream) {
     return nsf_launch(f, false, nullptr, 0, seed, iter, inst, n, x, n, logq, (cudaStream_t)stream);
+}
+
+extern "C" fd_status fd_nsf_sample_w(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t inst, int64_t n, float *x,
+                                     float *w, void *stream) {
+    return nsf_launch(f, false, nullptr, 0, seed, iter, inst, n, x, n, w, (cudaStream_t)stream, true);
 }
 
 namespace {

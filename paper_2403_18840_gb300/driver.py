@@ -42,22 +42,29 @@ def adapt_vegas(G, params, vegas, n, iters, seed, alpha=0.5, first_iter=0):
 
 
 def _flow_draw(flow, seed, it, inst, n, defensive):
+    """Proposals (x, 1/q) of an affine flow (optionally with its defensive
+    uniform share) or a spline flow."""
     if defensive > 0:
         x, w, _ = flow.sample_defensive(seed, it, inst, n, defensive)
         return x, w
-    return flow.sample(seed, it, inst, n)
+    return flow.draw(seed, it, inst, n)
 
 
 def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, evals_per_batch=1, log=None,
-               on_vegas=True, defensive=0.0):
-    """Forward-KL training of `flow` on |f|; the first `vegas_steps` batches come from VEGAS.
+               on_vegas=True, defensive=0.0, anneal=None):
+    """Forward-KL training of `flow` (affine or spline) on |f|; the first
+    `vegas_steps` batches come from VEGAS.
 
     Every batch is drawn from the current sampler, evaluated by the integrand
     kernel (points mode, weights 1/q), and used for `evals_per_batch` Adam steps.
-    Returns the list of losses.
+    anneal = (factor, n_steps): App. A's annealing in the temperature, the
+    training target taken at factor x T at the first step and lowered
+    geometrically to T over the first n_steps steps (a smoother integrand
+    first).  Returns the list of losses.
     """
     plan = api.EvalPlan([G], [params], [0], batch, maps=[vegas] if on_vegas else None)
     tw = torch.empty(batch, dtype=torch.float32, device="cuda")
+    beta0 = plan._p[0].beta
     losses = []
     k = 0
     while k < steps:
@@ -66,6 +73,9 @@ def train_flow(G, params, flow, vegas, steps, batch, lr, seed, vegas_steps=50, e
             x, w = api.map_samples(None if on_vegas else vegas, seed, 1000 + k, 1, batch, G.dim)
         else:
             x, w = _flow_draw(flow, seed, 1000 + k, 2, batch, defensive)
+        if anneal is not None:
+            factor, n_anneal = anneal
+            plan._p[0].beta = beta0 / factor ** max(0.0, 1.0 - k / n_anneal)
         # target |f| / q_s per sample, formed by the integrand kernel
         plan.run_target(seed, 1000 + k, tw, points=x, point_w=w)
         m = min(evals_per_batch, steps - k)
@@ -95,7 +105,7 @@ def mcmc(G, params, vegas, flow, n_chains, n_steps, alpha, seed, it, n_therm=0, 
     if flow is None:
         plan.run(seed, it)
     else:
-        x, w = flow.sample(seed, it, 3, n)
+        x, w = flow.draw(seed, it, 3, n)
         plan.run(seed, it, points=x, point_w=w)
     weights = plan.per_sample[0].reshape(-1, n)[:2 * len(G.roots)]
     if chains is None:
@@ -179,6 +189,18 @@ def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3, defen
     return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
 
 
+def bootstrap_ratio(num, den, stat, resamples=4000, seed=0, level=0.95):
+    """Percentile bootstrap interval of stat(num) / stat(den), the batches of
+    the two samplers resampled independently with replacement."""
+    rng = np.random.default_rng(seed)
+    num, den = np.asarray(num, dtype=np.float64), np.asarray(den, dtype=np.float64)
+    a = stat(num[rng.integers(0, num.size, (resamples, num.size))], axis=1)
+    b = stat(den[rng.integers(0, den.size, (resamples, den.size))], axis=1)
+    q = (1.0 - level) / 2.0
+    r = a / b
+    return [float(np.quantile(r, q)), float(np.quantile(r, 1.0 - q))]
+
+
 def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True, defensive=0.0):
     """Variance-adjusted efficiency of flow vs VEGAS for the real part of `root`.
 
@@ -187,7 +209,8 @@ def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True, d
     the batch estimates) and, as a robust companion, by the median of the
     batch estimates: the order-5 integrand is heavy-tailed, so a single rare
     sample can dominate a batch's estimate.  The batch means give the combined
-    estimate and its error.
+    estimate and its error.  Both time-adjusted ratios come with a 95 %
+    percentile-bootstrap interval over the batches (ci95).
     """
     res = {}
     flow_kw = dict(flow=flow, vegas=vegas if on_vegas else None, defensive=defensive)
@@ -213,6 +236,11 @@ def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True, d
                                      res["vegas"]["var_median"] / res["flow"]["var_median"])
     res["means_agree_sigma"] = abs(res["flow"]["mean"] - res["vegas"]["mean"]) / math.sqrt(
         res["flow"]["err"] ** 2 + res["vegas"]["err"] ** 2)
+    speed = res["flow"]["samples_per_s"] / res["vegas"]["samples_per_s"]
+    vv, fv = res["vegas"]["var_batches"], res["flow"]["var_batches"]
+    res["ci95"] = {"flow_over_vegas": [speed * x for x in bootstrap_ratio(vv, fv, np.mean)],
+                   "flow_over_vegas_median": [speed * x for x in bootstrap_ratio(vv, fv, np.median)],
+                   "batches": batches, "samples_per_batch": n, "resamples": 4000}
     res["defensive_share"] = defensive
     return res
 

@@ -98,7 +98,7 @@ def _fock_quad(P, k):
     return -v / (math.pi * k)
 
 
-@pytest.mark.parametrize("sampler", ["vegas", "flow"])
+@pytest.mark.parametrize("sampler", ["vegas", "flow", "spline"])
 def test_mcmc_recovers_the_fock_closed_form(api, sampler):
     from paper_2403_18840_gb300 import driver
     cfg = workloads.FOCK_ORDER1
@@ -106,7 +106,12 @@ def test_mcmc_recovers_the_fock_closed_form(api, sampler):
     p = api.ueg_params(1, cfg["rs"], cfg["T_over_TF"], cfg["lam_over_kF"], 1.0)
     V = api.Vegas(G.dim, 256)
     driver.adapt_vegas(G, p, V, 1 << 18, 6, seed=3)
-    flow = api.Flow(G.dim, n_layers=4, hidden=128, seed=5) if sampler == "flow" else None   # untrained: any q is valid
+    flow = None                                              # untrained flows: any q is valid
+    if sampler == "flow":
+        flow = api.Flow(G.dim, n_layers=4, hidden=128, seed=5)
+    elif sampler == "spline":
+        flow = api.SplineFlow(G.dim, 4)
+        flow.set_params(workloads.small_params(5, flow.n_params))
     C, S = 1 << 15, 32
     ch, plan, out = driver.mcmc(G, p, V, flow, C, S, 0.5, seed=9, it=100, n_therm=4)
     out = out.cpu().numpy()

@@ -5,6 +5,7 @@ round trip, the identity flow, and ragged sample counts."""
 import numpy as np
 import pytest
 
+import parity
 import workloads
 from oracle import philox as ophilox, spline_flow as osf
 
@@ -195,3 +196,29 @@ def test_training_first_adam_step_and_descent(api):
     assert abs(g.train(x, w, 1, lr)[0] - losses[0]) < 1e-6 * (1.0 + abs(losses[0]))
     d2 = g.params().astype(np.float64) - theta.astype(np.float64)
     assert np.all(np.abs(d2[big] - d[big]) <= 1e-3 * lr + 2 * ulp[big])
+
+
+def test_sampler_weights_and_integrand_points(api):
+    """fd_nsf_sample_w: the sample stream's points with w = 1/q(x) (App. A's
+    flow as the proposal): the same points as fd_nsf_sample, w = exp(-log q),
+    and as point weights of the integrand they give the oracle's weighted
+    integrand at those points."""
+    from oracle import conventions, integrand as oig
+    g = api.SplineFlow(7, 4)
+    g.set_params(workloads.small_params(21, g.n_params))
+    n = 3001
+    x, lq = g.sample(5, 1, 2, n)
+    x2, w = g.draw(5, 1, 2, n)
+    torch.cuda.synchronize()
+    assert torch.equal(x, x2)
+    lqn = lq.cpu().numpy().astype(np.float64)
+    assert np.allclose(w.cpu().numpy(), np.exp(-lqn), rtol=2e-6, atol=0)
+    G = api.Graph(2, with_dk=True)
+    plan = api.EvalPlan([G], [api.ueg_params(2, 1.0, 1.0 / 25.0, 1.0, 1.0)], [0], n, per_sample=True)
+    plan.run(5, 1, points=x2, point_w=w)
+    torch.cuda.synchronize()
+    f = plan.per_sample[0].cpu().numpy().astype(np.float64)[:len(G.roots)]
+    P = conventions.ueg_params(1.0, 1.0 / 25.0, 1.0, 1.0)
+    ref, mag = oig.eval_roots(x2.cpu().numpy().astype(np.float64), G.roots, P, with_l1=True)
+    wd = w.cpu().numpy().astype(np.float64)
+    parity.check(parity.rel_error(f, ref * wd, mag * wd), "integrand on spline-flow points")
