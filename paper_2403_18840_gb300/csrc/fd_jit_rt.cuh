@@ -372,7 +372,9 @@ FD_HD void fd_time_diff(T tah, T tal, T tbh, T tbl, T &dh, T &dl) {
 // of exp(d tau*) is tau*^k / k!.  T = float (the kernels' precision) or
 // double (the families whose value is the only term of a root, see
 // g_family_precise).  out(j, value) receives the (M + 1) (1 + dk) values.
-template <class T, class Out>
+// ET (scalar T only): the two lines have equal times (0^-), so tau* = 0 or
+// beta and exp(-eps tau*) is 1 or the Fermi factor's exponential.
+template <class T, bool ET = false, class Out>
 FD_HD void g_family(T eps, T pz, float ks, T dxh, T dxl, T beta, int M, int dk, Out &&out) {
     const T E = fd_exp(-beta * fd_abs(eps));
     const T phi = rcp_approx(T(1.0f) + E);
@@ -381,7 +383,11 @@ FD_HD void g_family(T eps, T pz, float ks, T dxh, T dxl, T beta, int M, int dk, 
     const auto occ = fd_lt0(eps);
     const T dstar = fd_sel(occ, fd_sel(pos, dxh - T(1.0f), dxh), fd_sel(pos, dxh, dxh + T(1.0f))) + dxl;
     const T tstar = beta * dstar;
-    const T X = fd_sel(pos, T(-1.0f), T(1.0f)) * fd_exp(-eps * tstar) * phi;
+    T X;
+    if constexpr (ET)
+        X = occ ? phi : E * phi;
+    else
+        X = fd_sel(pos, T(-1.0f), T(1.0f)) * fd_exp(-eps * tstar) * phi;
     if (M == 0 && !dk) {
         out(0, X);
         return;
@@ -435,8 +441,11 @@ FD_HD void g_family_precise(double pxh, double pyh, double pzh, double pxl, doub
                             float dxh, float dxl, double beta, double mu, int M, int dk, Out &&out) {
     const double px = pxh + pxl, py = pyh + pyl, pz = pzh + pzl;
     const double eps = fma(px, px, fma(py, py, pz * pz)) - mu;
-    g_family<double>(eps, pz, ks, (double)dxh, (double)dxl, beta, M, dk,
-                     [&](int j, double v) { out(j, (float)v); });
+    if (dxh == 0.0f && dxl == 0.0f)
+        g_family<double, true>(eps, pz, ks, 0.0, 0.0, beta, M, dk, [&](int j, double v) { out(j, (float)v); });
+    else
+        g_family<double>(eps, pz, ks, (double)dxh, (double)dxl, beta, M, dk,
+                         [&](int j, double v) { out(j, (float)v); });
 }
 
 // V Taylor family: c_l = (d/dLambda)^l V / l! = 8 pi (-1)^l w^(l+1), w = 1/(q^2+Lambda),
