@@ -313,12 +313,14 @@ def run_ours(args, rank, world, dist):
     # algorithmic work: every leaf family computed once (no recomputation)
     flops_ps, sfu_ps = fdgraph.tape_work(api.tape_bytes(order, roots, budget=1 << 13, bundle=1, window=1))
     loop = (tuned.get("spt") or 1) > 1
+    lc = tuned.get("leaf_cache") or 0
+    loop = loop or lc > 0
     exec_flops_ps, exec_sfu_ps = fdgraph.specialised_work(
         G.tape, tuned.get("root_units", True), unit_cap=(tuned.get("unit_cap") or 6000) if loop else None,
-        cross_roots=bool(tuned.get("cross_roots")) and loop)
+        cross_roots=bool(tuned.get("cross_roots")) and loop, leaf_cache=lc)
     exec_instr_ps, _ = fdgraph.specialised_work(
         G.tape, tuned.get("root_units", True), unit_cap=(tuned.get("unit_cap") or 6000) if loop else None,
-        cross_roots=bool(tuned.get("cross_roots")) and loop, instr=True)
+        cross_roots=bool(tuned.get("cross_roots")) and loop, instr=True, leaf_cache=lc)
     fp64_ps = fdgraph.tape_work(G.tape, fp64=True)
     V = api.Vegas(G.dim, WL["n_bins"])
     n = args.samples

@@ -675,8 +675,9 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
             const uint64_t w = g.h_tape[ins[kv.first].w];
             cand.push_back({leaf_cost(w) * (kv.second - 1) / leaf_outputs(w), kv.first});
         }
-        std::sort(cand.begin(), cand.end(), [](const std::pair<double, uint32_t> &a,
-                                               const std::pair<double, uint32_t> &b) { return a.first > b.first; });
+        std::sort(cand.begin(), cand.end(), [](const std::pair<double, uint32_t> &a, const std::pair<double, uint32_t> &b) {
+            return a.first > b.first || (a.first == b.first && a.second < b.second);
+        });
         for (auto &c : cand) {
             const int wd = leaf_outputs(g.h_tape[ins[c.second].w]);
             if (lc_floats + wd > leaf_cache) continue;

@@ -910,7 +910,28 @@ def _map_work(dim, order, n_roots):
     return flops, sfu
 
 
-def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False, instr=False):
+def _leaf_rank_cost(w):
+    """The generator's cost of a leaf family for ranking leaf-cache candidates
+    (csrc/fd_jit.cu leaf_cost, the same arithmetic)."""
+    mask = (w >> 20) & 16383
+    terms = sum(1 for j in range(7) if (mask >> (2 * j)) & 3)
+    M, dk = (w >> 40) & 7, (w >> 43) & 1
+    Mx = M + dk
+    c = 6.0 * max(terms - 1, 0)
+    if (w & 63) == OP_GLEAF:
+        c += 36.0 + 3.0 * 8.0
+        for k in range(Mx):
+            c += (k + 1) + 4
+        if Mx:
+            for j in range(Mx + 1):
+                c += j + 1
+    else:
+        c += 12.0 + 8.0 + Mx
+    return c
+
+
+def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False, instr=False, leaf_cache=0,
+                     return_cache=False):
     """(fp32_flops, sfu_ops) per sample executed by the specialised kernel.
 
     The kernel evaluates every root-accumulate slice of the tape as straight-line
@@ -920,6 +941,10 @@ def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False, in
     kernels) consecutive slices of a root, or across roots with cross_roots,
     packed while FMAs + 30 per distinct leaf stay within the cap.  Same counting
     rule as tape_work (with instr: FP32 instructions, an FMA counting once).
+    leaf_cache = K: the families the generator caches (used by two or more
+    units, the most recomputation saved per float first, up to K floats per
+    sample) are computed once per sample and read by the units.  With
+    return_cache: the number of cached floats instead.
     """
     hdr = struct.unpack("<16I", data[:64])
     order, dim, n_roots, n_instr, ins_off = hdr[2], hdr[3], hdr[4], hdr[6], hdr[8]
@@ -980,12 +1005,38 @@ def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False, in
                 units[-1][1], units[-1][2] = grown_f, grown_l
                 continue
         units.append([r, set(fmas), set(leaves)])
+    cached = set()
+    if return_cache:
+        leaf_cache = leaf_cache or 0
+    if leaf_cache > 0:
+        uses = collections.Counter()
+        for _, _, leaves in units:
+            for j in leaves:
+                uses[j] += 1
+
+        def width(j):
+            w = words[ins[j][1]]
+            return (((w >> 40) & 7) + 1) * (2 if (w >> 43) & 1 else 1)
+        cand = sorted(((-_leaf_rank_cost(words[ins[j][1]]) * (c - 1) / width(j), j) for j, c in uses.items() if c >= 2))
+        used = 0
+        for _, j in cand:
+            if used + width(j) <= leaf_cache:
+                cached.add(j)
+                used += width(j)
+    if return_cache:
+        return sum((((words[ins[j][1]] >> 40) & 7) + 1) * (2 if (words[ins[j][1]] >> 43) & 1 else 1) for j in cached)
     flops = sfu = 0
+    for j in cached:
+        f, u, _ = _leaf_work(words[ins[j][1]], instr)
+        flops += f
+        sfu += u
     for _, fmas, leaves in units:
         for (j, q) in fmas:
             m = words[ins[j][1] + 1 + q]
             flops += 1 if (instr or (m >> 48) == 0 or ((m >> 32) & 0xFFFF) == 1) else 2
         for j in leaves:
+            if j in cached:
+                continue
             f, u, _ = _leaf_work(words[ins[j][1]], instr)
             flops += f
             sfu += u

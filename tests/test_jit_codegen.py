@@ -164,3 +164,15 @@ def test_leaf_cache_source_compiles(tmp_path):
 def test_leaf_cache_rejects_invalid_options(kw):
     with pytest.raises(api.L.FdError):
         api.jit_source(_tape(2, False), 0, threads=256, min_blocks=1, **kw)
+
+
+@pytest.mark.parametrize("cap,K", [(6000, 32), (12000, 96), (0, 48)])
+def test_work_model_caches_what_the_generator_caches(cap, K):
+    # fdgraph.specialised_work's leaf-cache selection (the executed-work model
+    # the benchmark reports) picks the same families as the generator
+    tape = _tape(4, True)
+    src, _ = api.jit_source(tape, 0, threads=256, min_blocks=1, max_modules=1, spt=2, unit_cap=cap, leaf_cache=K)
+    head = src[src.index("fd_leaves(const FdSV *Vb"):src.index("static __device__ __forceinline__ float fd_s")]
+    stores = len(re.findall(r"  L\[\d+\] = c\d+\[\d+\];", head))
+    assert stores == fdgraph.specialised_work(tape, True, cap, leaf_cache=K, return_cache=True)
+    assert fdgraph.specialised_work(tape, True, cap, leaf_cache=K)[0] < fdgraph.specialised_work(tape, True, cap)[0]
