@@ -30,8 +30,8 @@ def test_flow_beats_vegas_at_order5():
     V = api.Vegas(G.dim, 1024)
     driver.adapt_vegas(G, p, V, 1 << 22, 12, seed=11)
     F = api.Flow(G.dim, 8, 128, seed=3)
-    losses = driver.train_flow(G, p, F, V, steps=600, batch=1 << 18, lr=1e-3, seed=12, vegas_steps=100,
-                               evals_per_batch=2, defensive=0.1)
+    losses = driver.train_flow(G, p, F, V, steps=2000, batch=1 << 18, lr=1e-3, seed=12, vegas_steps=100,
+                               evals_per_batch=4, defensive=0.1)
     cmp = driver.compare(G, p, V, F, 1 << 22, seed=13, batches=64, defensive=0.1)
     print({k: cmp[k] for k in ("flow_over_vegas", "flow_over_vegas_median", "means_agree_sigma")},
           cmp["vegas"]["var_batches"], cmp["flow"]["var_batches"], cmp["vegas"]["samples_per_s"],

@@ -1,5 +1,5 @@
 """End to end to the effective mass (Sec. VI.A): GPU estimates of
-Sigma^(n,m,l)(k_F, i w0) and d Sigma / dk for all n + m + l <= 3 from the
+Sigma^(n,m,l)(k_F, i w0) and d Sigma / dk for all n + m + l <= 4 from the
 compiled graphs (integrand kernel, tile partials, fixed-order accumulation),
 renormalised by the library's host post-process, against the oracle's
 estimates on the same Philox points renormalised by the oracle's
@@ -10,15 +10,16 @@ post-process with its central-difference derivatives."""
 import numpy as np
 import pytest
 
+import oracle_pool
 import parity
 
-from oracle import conventions, integrand as oig, philox as ophilox, postprocess as opp
+from oracle import conventions, postprocess as opp
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-N = 3
+N = 4
 RS, T, LAM = 1.0, 1.0 / 25.0, 1.0
 
 
@@ -31,8 +32,7 @@ def _estimates(api, n, seed, jit):
             G.jit()
         plan = api.EvalPlan([G], [api.ueg_params(order, RS, T, LAM, 1.0)], [0], n)
         st = plan.run(seed, order).cpu().numpy()[0]                  # [R][2][2]
-        x = ophilox.uniforms(seed, order, 0, np.arange(n), 4 * order - 1)
-        ref, mag = oig.eval_roots(x, G.roots, P, with_l1=True)
+        ref, mag = oracle_pool.eval_roots(order, G.roots, seed, n, prm=(RS, T, LAM, 1.0), iteration=order)
         for r, (nn, m, l, dk) in enumerate(G.roots):
             g = complex(st[r, 0, 0], st[r, 1, 0])
             o = complex(ref[r].real.mean(), ref[r].imag.mean())
