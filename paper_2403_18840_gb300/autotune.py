@@ -26,6 +26,8 @@ SHAPES = [(128, 2), (256, 1), (128, 1), (64, 2)]
 # specialised-kernel variants (fd_jit_options; unlisted options at their defaults)
 JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sv_smem=True),
+                dict(threads=256, min_blocks=1, spt=3, unit_cap=12000, sync_every=1, sv_smem=True),
+                dict(threads=256, min_blocks=1, spt=3, unit_cap=12000, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True)]
 # (leaf-cache variants -- spt 1, 2, 4 with 24 - 128 cached floats -- were 15 - 31 %
