@@ -31,22 +31,24 @@ def combine_estimates(dist, mean, var, n, device="cpu"):
     """Pool the ranks' estimates of the same quantities.
 
     mean, var: arrays (any shape) of a rank's mean and variance of the mean
-    over its n samples, as fd_accumulate returns them
-    (var = (sum f^2 - n mean^2) / ((n - 1) n)).  Returns the mean and the
-    variance of the mean over all ranks' samples together (n times the number
-    of ranks), computed from the summed sums and sums of squares.
+    over its n samples, as fd_accumulate returns them (var = sum (f - mean)^2
+    / ((n - 1) n)).  Returns the mean and the variance of the mean over all
+    ranks' samples together (n times the number of ranks).  Pairwise
+    combination (Chan, Golub and LeVeque): the pooled mean first, then the
+    ranks' sums of squared deviations plus n (mean_r - mean)^2, so no large
+    sums of squares are subtracted from each other.
     """
     m = torch.as_tensor(mean, dtype=torch.float64, device=device)
     v = torch.as_tensor(var, dtype=torch.float64, device=device)
     s = m * n
-    q = v * n * (n - 1) + s * m
-    if dist is None:
-        world = 1
-    else:
-        world = dist.get_world_size()
+    world = 1 if dist is None else dist.get_world_size()
+    if dist is not None:
         dist.all_reduce(s)
-        dist.all_reduce(q)
     N = n * world
     mean_all = s / N
-    var_all = torch.clamp((q - s * mean_all) / (N - 1), min=0.0) / N
+    d = m - mean_all
+    q = v * n * (n - 1) + n * d * d                    # this rank's sum of (f - mean_all)^2
+    if dist is not None:
+        dist.all_reduce(q)
+    var_all = torch.clamp(q / (N - 1), min=0.0) / N
     return mean_all.cpu().numpy(), var_all.cpu().numpy()

@@ -18,13 +18,17 @@ N = 5000
 def _samples(rank):
     from paper_2403_18840_gb300 import replicas
     rng = np.random.default_rng(replicas.rank_seed(7, rank))
-    return rng.standard_normal((3, N)) * np.array([[1.0], [0.1], [5.0]]) + np.array([[0.5], [-2.0], [0.0]])
+    # the last row: a large offset with a small spread (sum f^2 - N mean^2
+    # would cancel ~16 digits)
+    return (rng.standard_normal((4, N)) * np.array([[1.0], [0.1], [5.0], [1e-3]])
+            + np.array([[0.5], [-2.0], [0.0], [1e8]]) + rank * np.array([[0.0], [0.0], [0.0], [1e-3]]))
 
 
 def _stats(f):
+    """Mean and variance of the mean, two-pass."""
     n = f.shape[-1]
     mean = f.mean(axis=-1)
-    var = np.maximum((np.sum(f * f, axis=-1) - n * mean * mean) / (n - 1), 0.0) / n
+    var = np.sum((f - mean[..., None]) ** 2, axis=-1) / (n - 1) / n
     return mean, var
 
 
@@ -59,6 +63,10 @@ def test_two_gloo_ranks_combine_like_one_pool():
     for r in range(WORLD):
         m_all, v_all, t_max, seed = res[r]
         assert np.allclose(m_all, ref_mean, rtol=1e-12, atol=1e-15)
-        assert np.allclose(v_all, ref_var, rtol=1e-9, atol=1e-18)
+        assert np.allclose(v_all[:3], ref_var[:3], rtol=1e-9, atol=1e-18)
+        # offset 1e8, spread 1e-3: the pooled mean carries FP64's 1e-16 relative
+        # rounding, 1e-8 absolute, ~1e-5 of the spread, and the variance that
+        # much relatively; subtracting sums of squares would lose every digit
+        assert abs(v_all[3] / ref_var[3] - 1.0) < 1e-4
         assert t_max == float(WORLD)                 # slowest rank's time
     assert res[0][3] != res[1][3]                    # independent streams
