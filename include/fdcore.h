@@ -124,14 +124,19 @@ fd_status fd_graph_set_launch(fd_graph *g, int32_t threads, int32_t samples_per_
  *               into shared memory ([float][sample][thread], threads x spt x
  *               4 bytes per float) and read there by the units, the families
  *               that save the most work per float first, up to this many
- *               floats; any spt (spt = 1 takes the sample-loop kernel).
+ *               floats; any spt (spt = 1 takes the sample-loop kernel);
+ *  lc_global    != 0 (leaf_cache > 0): the leaf cache in a global scratch
+ *               array the graph owns (one region per resident CTA, freed
+ *               with the graph or the next fd_graph_jit) instead of shared
+ *               memory; evaluations of such a graph must not overlap on the
+ *               GPU (they share the array).
  * cache_dir (may be NULL): directory for compiled images, keyed by a hash of
  * the generated source and options.  Synchronous; FD_ENOTSUP when the
  * run-time compiler is unavailable or fails (fd_last_error holds its log).
  * Results agree with the interpreter up to FP32 rounding order. */
 typedef struct {
     int32_t threads, min_blocks, max_modules, root_units, sync_every, leaf_calls, spt, unit_cap, pair, sv_smem,
-        cross_roots, leaf_cache;
+        cross_roots, leaf_cache, lc_global;
 } fd_jit_options;
 fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const char *cache_dir);
 /* Switch evaluation of g between its specialised kernel (on != 0) and the interpreter. */

@@ -21,7 +21,7 @@ class FdError(RuntimeError):
 class fd_jit_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("threads", "min_blocks", "max_modules", "root_units", "sync_every",
                                               "leaf_calls", "spt", "unit_cap", "pair", "sv_smem", "cross_roots",
-                                              "leaf_cache")]
+                                              "leaf_cache", "lc_global")]
 
 
 class fd_params(ctypes.Structure):

@@ -67,12 +67,12 @@ def tape_bytes(order, roots, budget=None, bundle=None, window=None):
 
 
 def jit_options(threads=128, min_blocks=2, max_modules=None, root_units=True, sync_every=0, leaf_calls=False, spt=1,
-                unit_cap=6000, pair=False, sv_smem=False, cross_roots=False, leaf_cache=0):
+                unit_cap=6000, pair=False, sv_smem=False, cross_roots=False, leaf_cache=0, lc_global=False):
     if max_modules is None:
         max_modules = max(1, min(32, os.cpu_count() or 1))
     return L.fd_jit_options(threads, min_blocks, max_modules, 1 if root_units else 0, sync_every,
                             1 if leaf_calls else 0, spt, unit_cap, 1 if pair else 0, 1 if sv_smem else 0,
-                            1 if cross_roots else 0, int(leaf_cache))
+                            1 if cross_roots else 0, int(leaf_cache), 1 if lc_global else 0)
 
 
 def jit_source(tape, module=0, **options):
@@ -113,7 +113,7 @@ class Graph:
         """Compile the specialised straight-line kernel (cached under _build/jit)
         and evaluate this graph with it from now on.  Options (fd_jit_options):
         threads, min_blocks, max_modules, root_units, sync_every, leaf_calls,
-        spt, unit_cap, pair, sv_smem, cross_roots, leaf_cache."""
+        spt, unit_cap, pair, sv_smem, cross_roots, leaf_cache, lc_global."""
         opt = jit_options(**options)
         cdir = _JIT_DIR if cache else None
         if cdir:

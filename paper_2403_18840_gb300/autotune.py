@@ -29,11 +29,15 @@ JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_ever
                 dict(threads=256, min_blocks=1, spt=3, unit_cap=12000, sync_every=1, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=3, unit_cap=12000, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sv_smem=True),
-                dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True)]
+                dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True),
+                dict(threads=256, min_blocks=1, spt=3, unit_cap=12000, sync_every=1, sv_smem=True, leaf_cache=320,
+                     lc_global=True),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1, sv_smem=True, leaf_cache=320,
+                     lc_global=True)]
 # (leaf-cache variants -- spt 1, 2, 4 with 24 - 128 cached floats -- were 15 - 31 %
 # slower than the best of these at order 5 on GB300 and are not tried by default)
 JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap", "pair", "sv_smem",
-            "cross_roots", "leaf_cache")
+            "cross_roots", "leaf_cache", "lc_global")
 
 
 def _key(order, roots):

@@ -231,6 +231,7 @@ extern "C" fd_status fd_graph_roots(const fd_graph *g, int32_t *roots) {
 extern "C" void fd_graph_free(fd_graph *g) {
     if (!g) return;
     if (g->jit_lib) cudaLibraryUnload(g->jit_lib);
+    if (g->jit_lc) cudaFree(g->jit_lc);
     cudaFree(g->d_tape);
     cudaFree(g->d_roots);
     delete g;

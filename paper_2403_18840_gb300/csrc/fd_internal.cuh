@@ -73,6 +73,8 @@ struct fd_graph {
     int jit_spt = 1;
     int jit_hist_cap = 0;           // floats of dynamic shared memory the kernel may take for a tile histogram
     int jit_sv_bytes = 0;           // dynamic shared memory of the per-sample inputs (before the histogram)
+    float *jit_lc = nullptr;        // global leaf cache (lc_global): one region per resident CTA
+    int64_t jit_lc_floats = 0;      // its size in floats
     double jit_compile_s = 0.0;
     bool jit_enabled = false;       // evaluation uses the specialised kernel
 };

@@ -472,14 +472,15 @@ struct Unit {
 };
 
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots, int leaf_cache);
+                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots, int leaf_cache,
+                          int lc_global);
 
 Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, int root_units, int sync_every,
                      int leaf_calls, int spt = 1, int unit_cap = 6000, int pair = 0, int sv_smem = 0,
-                     int cross_roots = 0, int leaf_cache = 0) {
+                     int cross_roots = 0, int leaf_cache = 0, int lc_global = 0) {
     if (spt > 1 || leaf_cache > 0)
         return emit_program_loop(g, T, min_blocks, max_modules, spt, (double)unit_cap, leaf_calls, pair, sync_every,
-                                 sv_smem, cross_roots, leaf_cache);
+                                 sv_smem, cross_roots, leaf_cache, lc_global);
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
     const std::vector<TIns> ins = decode(g.h_tape);
@@ -612,7 +613,8 @@ Program emit_program(const fd_graph &g, int T, int min_blocks, int max_modules, 
 // unit adds into the accumulators of the roots it touches, and every root is
 // flushed after all units.
 Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modules, int spt, double unit_cap,
-                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots, int leaf_cache) {
+                          int leaf_calls, int pair, int sync_units, int sv_smem, int cross_roots, int leaf_cache,
+                          int lc_global) {
     const std::string vs = sv_smem ? " * " + std::to_string(T) : "";
     const TapeHeader &h = g.hdr;
     const int N = (int)h.order, DIM = (int)h.dim, R = (int)h.n_roots;
@@ -807,6 +809,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
         src[0] << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks
                << ") fd_jit_kernel(const __grid_constant__ EvalArgs A) {\n  jit_main_loop<FdBody, " << N << ", " << DIM
                << ", " << R << ", " << T << ", " << spt << ", " << (sv_smem ? T : 1) << ", " << lc_floats
+               << ", " << (lc_global && lc_floats ? "true" : "false")
                << ">(A);\n}\n";
         for (int m = 0; m < n_mod; ++m) Pg.modules[m] = src[m].str();
         return Pg;
@@ -861,6 +864,7 @@ Program emit_program_loop(const fd_graph &g, int T, int min_blocks, int max_modu
     src[0] << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks
            << ") fd_jit_kernel(const __grid_constant__ EvalArgs A) {\n  jit_main_loop<FdBody, " << N << ", " << DIM
            << ", " << R << ", " << T << ", " << spt << ", " << (sv_smem ? T : 1) << ", " << lc_floats
+               << ", " << (lc_global && lc_floats ? "true" : "false")
            << ">(A);\n}\n";
     for (int m = 0; m < n_mod; ++m) Pg.modules[m] = src[m].str();
     return Pg;
@@ -970,7 +974,8 @@ fd_status jit_launch(const fd_graph *g, EvalArgs &args, cudaStream_t stream) {
         }
     args.hist_smem = (hist_floats <= g->jit_hist_cap && args.tile >= 4 * (int64_t)bins_max) ? hist_floats : 0;
     const int items = args.n_inst * args.tiles_per_inst;
-    const int grid = std::min(items, n_sm * g->jit_per_sm);
+    const int grid = std::min(items, n_sm * g->jit_per_sm);   // <= the CTAs the global leaf cache holds
+    args.lc_global = g->jit_lc;
     void *params[1] = {(void *)&args};
     FD_CHECK_CUDA(cudaLaunchKernel((const void *)g->jit_kernel, dim3(grid), dim3(g->jit_threads), params,
                                    (size_t)g->jit_sv_bytes + (size_t)args.hist_smem * sizeof(float), stream));
@@ -992,12 +997,13 @@ fd_status check_options(const fd_jit_options *o) {
     FD_REQUIRE(o->cross_roots == 0 || o->spt >= 2, "units across roots need spt >= 2");
     FD_REQUIRE(o->leaf_cache >= 0 && o->leaf_cache <= 4096, "leaf_cache must be in 0..4096 floats per sample");
     FD_REQUIRE(o->leaf_cache == 0 || (!o->pair && !o->leaf_calls), "the leaf cache needs scalar, inlined leaves");
+    FD_REQUIRE(o->lc_global == 0 || o->leaf_cache > 0, "lc_global needs a leaf cache");
     return FD_OK;
 }
 
 Program emit(const fd_graph &g, const fd_jit_options &o) {
     return emit_program(g, o.threads, o.min_blocks, o.max_modules, o.root_units, o.sync_every, o.leaf_calls, o.spt,
-                        o.unit_cap, o.pair, o.sv_smem, o.cross_roots, o.leaf_cache);
+                        o.unit_cap, o.pair, o.sv_smem, o.cross_roots, o.leaf_cache, o.lc_global);
 }
 }  // namespace
 
@@ -1075,7 +1081,7 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const 
     // local arrays of the sample-loop variants
     const long sv_b = (opt->sv_smem ? (long)threads * opt->spt * (long)sizeof(float) * fd_sv_words((int)g->hdr.order)
                                     : 0) +
-                      (long)threads * opt->spt * (long)sizeof(float) * P.lc_floats;
+                      (opt->lc_global ? 0L : (long)threads * opt->spt * (long)sizeof(float) * P.lc_floats);
     int sm_total = 0, optin = 0, reserved = 0, hist_cap = 0;
     const bool have_attrs =
         cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
@@ -1112,7 +1118,23 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const 
                 (void)cudaGetLastError();   // no tile histograms: global atomics only
         }
     }
+    // global leaf cache: one region of threads x spt x floats per CTA the launch can place
+    float *lcg = nullptr;
+    int64_t lcg_floats = 0;
+    if (opt->lc_global && P.lc_floats > 0) {
+        int n_sm = 0;
+        (void)cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        lcg_floats = (int64_t)n_sm * per_sm * threads * opt->spt * P.lc_floats;
+        const cudaError_t ea = cudaMalloc(&lcg, (size_t)lcg_floats * sizeof(float));
+        if (ea != cudaSuccess) {
+            cudaLibraryUnload(lib);
+            return fd::cuda_error(ea, "allocating the global leaf cache");
+        }
+    }
     if (g->jit_lib) cudaLibraryUnload(g->jit_lib);
+    if (g->jit_lc) cudaFree(g->jit_lc);
+    g->jit_lc = lcg;
+    g->jit_lc_floats = lcg_floats;
     g->jit_per_sm = per_sm;
     g->jit_hist_cap = hist_cap;
     g->jit_sv_bytes = (int)sv_b;

@@ -80,6 +80,7 @@ struct EvalArgs {
     double *partials;
     float *per_sample_f;
     float *abs_f;                      // optional [inst][n]: sum over value roots of |Re| + |Im| (0 if not finite)
+    float *lc_global;                  // global leaf cache (one region of T x P x LCW floats per CTA) or null
     int *status;
     const FdTab4 *sc_tab;              // cos / sin of 2 pi n / 256 as double-float pairs, n = 0..256
     uint8_t perm[FD_MAX_INST];         // descriptors in decreasing cost: work items go heaviest first
@@ -787,16 +788,20 @@ __device__ __forceinline__ void jit_main(const EvalArgs &A) {
 // inputs live in local memory (SVS = 1) or, with SVS = T, in dynamic shared
 // memory as [sample][thread] rows of FdSVT (sample p of this thread at
 // V[p * SVS]); the tile histogram, when the launch provides it, follows them.
-template <class Body, int N, int DIM, int R, int T, int P, int SVS = 1, int LCW = 0>
+template <class Body, int N, int DIM, int R, int T, int P, int SVS = 1, int LCW = 0, bool LCG = false>
 __device__ __forceinline__ void jit_main_loop(const EvalArgs &A) {
     __shared__ double acc[T / 32][R * 8];
     __shared__ int next_item;
     extern __shared__ float dyn_smem[];
     using FdSV = FdSVT<float, N>;
     constexpr int SV_FLOATS = SVS > 1 ? T * P * fd_sv_words(N) : 0;
-    // leaf cache: LCW floats per sample, [float][sample p][thread], this thread's column
-    float *const LC = LCW > 0 ? dyn_smem + SV_FLOATS + threadIdx.x : nullptr;
-    float *const hist_smem = dyn_smem + SV_FLOATS + T * P * LCW;
+    // leaf cache: LCW floats per sample, [float][sample p][thread], this thread's
+    // column; in shared memory after the inputs, or (LCG) in this CTA's region
+    // of a global scratch array (L2-resident)
+    float *const LC = LCW == 0 ? nullptr
+                    : LCG ? A.lc_global + (int64_t)blockIdx.x * (T * P * LCW) + threadIdx.x
+                          : dyn_smem + SV_FLOATS + threadIdx.x;
+    float *const hist_smem = dyn_smem + SV_FLOATS + (LCG ? 0 : T * P * LCW);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = A.n_inst * A.tiles_per_inst;
     const uint32_t iter = A.iter + (A.iter_dev ? *A.iter_dev : 0u);

@@ -22,7 +22,9 @@ VARIANTS = {"interpreter": None,
             "specialised": dict(),
             "specialised_loop": dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sv_smem=True, sync_every=1),
             "specialised_leaf_cache": dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sv_smem=True,
-                                           sync_every=1, leaf_cache=32)}
+                                           sync_every=1, leaf_cache=32),
+            "specialised_global_leaf_cache": dict(threads=256, min_blocks=1, spt=3, unit_cap=12000, sv_smem=True,
+                                                  sync_every=1, leaf_cache=320, lc_global=True)}
 
 
 @pytest.fixture(scope="module")
