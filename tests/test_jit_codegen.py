@@ -144,7 +144,7 @@ def test_leaf_cache_stores_each_family_once_and_units_read_it(kw):
     loads = set(int(m) for m in re.findall(r"[{ ]L\[(\d+)\]", body))
     assert loads and loads <= set(stores)
     assert "fd_leaves(V, Q, LC);" in src
-    assert re.search(r"jit_main_loop<FdBody, 4, 15, \d+, 256, %d, %d, %d>" % (spt, T if kw.get("sv_smem") else 1,
+    assert re.search(r"jit_main_loop<FdBody, 4, 15, \d+, 256, %d, %d, %d, false>" % (spt, T if kw.get("sv_smem") else 1,
                                                                               len(stores)), src)
 
 
