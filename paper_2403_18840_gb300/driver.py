@@ -240,6 +240,8 @@ def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True, d
     vv, fv = res["vegas"]["var_batches"], res["flow"]["var_batches"]
     res["ci95"] = {"flow_over_vegas": [speed * x for x in bootstrap_ratio(vv, fv, np.mean)],
                    "flow_over_vegas_median": [speed * x for x in bootstrap_ratio(vv, fv, np.median)],
+                   "variance_gain_median": bootstrap_ratio(vv, fv, np.median),
+                   "variance_gain_pooled": bootstrap_ratio(vv, fv, np.mean),
                    "batches": batches, "samples_per_batch": n, "resamples": 4000}
     res["defensive_share"] = defensive
     return res
