@@ -47,8 +47,9 @@ def _parse():
     ap.add_argument("--flow-steps", type=int, default=workloads.FLOW_ORDER5["train_steps"])
     ap.add_argument("--flow-batch", type=int, default=workloads.FLOW_ORDER5["batch"])
     ap.add_argument("--no-flow", action="store_true", help="skip the flow vs VEGAS section (profiling runs)")
-    ap.add_argument("--flow-tensor-path", type=int, default=0, choices=[0, 1],
-                    help="flow sampling / density on mma.sync (0) or tcgen05 (1)")
+    ap.add_argument("--flow-tensor-path", type=int, default=2, choices=[0, 1, 2],
+                    help="flow sampling / density on mma.sync (0), tcgen05 with tile pairs (1) or "
+                         "tcgen05 warp-specialised (2)")
     return ap.parse_args()
 
 
@@ -244,7 +245,7 @@ def flow_vs_vegas(args, api, params, order, seed):
            "means_agree_sigma": cmp["means_agree_sigma"], "compare": "64 batches x %d samples per sampler" %
            FW["n_compare"], "proposal": "flow on the VEGAS grid's input coordinates, 10 % defensive uniform share",
            "flow_train_steps": max(1, args.flow_steps), "flow_batch": args.flow_batch,
-           "flow_tensor_path": ["mma.sync", "tcgen05"][args.flow_tensor_path],
+           "flow_tensor_path": ["mma.sync", "tcgen05", "tcgen05 warp-specialised"][args.flow_tensor_path],
            "flow_train_s": flow_train_s, "flow_loss_first_last": [losses[0], losses[-1]],
            "mcmc": dict(mc, over_vegas={k: mc[k]["merit"] / ref["pooled"] for k in mc},
                         over_vegas_median={k: mc[k]["merit"] / ref["median"] for k in mc},
@@ -252,10 +253,41 @@ def flow_vs_vegas(args, api, params, order, seed):
                              "draw; merit = 1 / (variance of the estimate x seconds of the call)"),
            "flow_train_note": "each integrand batch reused for 4 Adam steps; first 100 steps on VEGAS samples; "
                               "VEGAS adapted 12 iterations x 2^22 samples",
+           "flow_sampling": affine_flow_sampling(api, F, args.flow_tensor_path),
            "spline_flow_sampling": spline_flow_sampling(api, Gs.dim),
            "spline_flow_training": spline_flow_training(api, Gs.dim)}
 
     return eff
+
+
+def affine_flow_sampling(api, F, default_path, n=1 << 24, reps=5):
+    """Samples/s of the trained affine flow's sampling pass (x and w = 1/q) on
+    each tensor-core path, and its tensor roofline: 2 (16 x 128 + 128 x 128 +
+    128 x 32) flops per layer and sample as padded on the tensor cores, against
+    the measured BF16 burst peak (the kernel is timed alone)."""
+    import torch
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = json.load(open(path)).get("bf16_tflops") if os.path.exists(path) else None
+    flops = 2 * (16 * 128 + 128 * 128 + 128 * 32) * F.n_layers
+    out = {"samples": n, "padded_flops_per_sample": flops, "peak_tflops": peak,
+           "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst)"}
+    names = {0: "mma.sync", 1: "tcgen05 tile pairs", 2: "tcgen05 warp-specialised"}
+    for path in (2, 0, 1):
+        F.set_tensor_path(path)
+        F.sample(3, 0, 0, n)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for r in range(reps):
+            F.sample(3, r + 1, 0, n)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / reps
+        tf = flops * n / ms * 1e-9
+        out[names[path]] = {"ms": ms, "samples_per_s": n / ms * 1e3, "tflops": tf,
+                            "frac": tf / peak if peak else None}
+    F.set_tensor_path(default_path)
+    return out
 
 
 def spline_flow_sampling(api, dim, layers=8, n=1 << 22, reps=3):

@@ -325,14 +325,16 @@ fd_status fd_flow_sample_defensive(const fd_flow *f, uint64_t seed, uint64_t ite
 /* log q(x) for given points (inverse pass).  x: device [dim][n], logq: device [n]. */
 fd_status fd_flow_log_density(const fd_flow *f, const float *x, int64_t n, float *logq,
                               void *stream);
-/* Tensor-core path of the sampling and density passes: 0 (default) =
- * warp-level mma.sync m16n8k16 with the activations kept in registers between
- * layers; 1 = tcgen05.mma with TMEM accumulators, 128-sample tiles, two tiles
- * in flight, weights staged by TMA (measured ~7% slower on GB300 for this
- * MLP: its K <= 128 chains spend their time in the per-element epilogues,
- * which the tcgen05 path routes through TMEM loads and shared memory).  Both
+/* Tensor-core path of the sampling and density passes: 2 (default) =
+ * tcgen05.mma with TMEM accumulators, warp-specialised: four 128-sample tiles
+ * in flight per SM, one thread issuing the GEMMs, one streaming the layers'
+ * weights by bulk copies, epilogue warps owning one sample per thread (the
+ * hidden biases enter the accumulators on the tensor core); 1 = tcgen05.mma
+ * with two tiles in flight and block barriers between the GEMMs; 0 =
+ * warp-level mma.sync m16n8k16 with the activations kept in registers.  All
  * compute the same BF16 contract (BF16 weights and GEMM inputs, FP32
- * accumulation); training always uses the mma.sync kernels. */
+ * accumulation); training always uses the mma.sync kernels.  FD_EINVAL for
+ * another path. */
 fd_status fd_flow_set_tensor_path(fd_flow *f, int32_t path);
 /* Weighted forward-KL loss L = -sum w log q(x) / sum w and its gradient in
  * blob layout.  x: device [dim][n]; w: device [n] (>= 0); loss: device [1];

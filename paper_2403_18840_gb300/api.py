@@ -260,7 +260,8 @@ class Flow:
         return self.sample(seed, it, inst, n, stream)
 
     def set_tensor_path(self, path):
-        """Sampling / density on mma.sync (0, default) or tcgen05 (1)."""
+        """Sampling / density on tcgen05, warp-specialised (2, default), tcgen05
+        with tile pairs (1) or mma.sync (0)."""
         L.check(L.lib().fd_flow_set_tensor_path(self.handle, path))
 
     def sample_defensive(self, seed, it, inst, n, alpha, stream=None):

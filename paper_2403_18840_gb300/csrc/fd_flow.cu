@@ -1069,9 +1069,18 @@ __global__ void pack_umma_kernel(const float *__restrict__ blob, const LayerIdx 
         *reinterpret_cast<__nv_bfloat16 *>(out + umma::OFF_W2 + umma::core_off(r, c, 2048)) =
             __float2bfloat16_rn(W2[r * H + c]);
         if (k < H * 16) {
+            // columns [0, a): W1; 12, 13: b2 as BF16 hi + lo; 14, 15: b1 as hi + lo
+            // (a <= 12; the warp-specialised kernel adds the biases on the tensor
+            // core through these columns, the other kernels read the FP32 biases)
             const int r1 = k / 16, c1 = k % 16;
+            float v = c1 < L.a ? W1[r1 * L.a + c1] : 0.f;
+            if (c1 >= 12) {
+                const float b = c1 < 14 ? b2[r1] : b1[r1];
+                const float hi = __bfloat162float(__float2bfloat16_rn(b));
+                v = (c1 & 1) ? b - hi : hi;
+            }
             *reinterpret_cast<__nv_bfloat16 *>(out + umma::OFF_W1 + umma::core_off(r1, c1, 256)) =
-                __float2bfloat16_rn(c1 < L.a ? W1[r1 * L.a + c1] : 0.f);
+                __float2bfloat16_rn(v);
         }
         if (k < 32 * H) {
             const int r3 = k / H, c3 = k % H;
@@ -1352,6 +1361,457 @@ __global__ void __launch_bounds__(umma::THREADS, 1) flow_umma_kernel(
                      : "memory");
 }
 
+
+// ---- warp-specialised tcgen05 sampling / density kernel (the default path) -------------
+// Roles within a CTA (one CTA per SM):
+//   * epilogue warps 0 .. 4 S - 1: slot s = warp / 4 owns one 128-sample tile
+//     of the current group; warp % 4 selects the warp's 32 TMEM lanes (tile
+//     rows), so every thread owns one sample, whose coordinates stay in
+//     registers through all layers;
+//   * warp 4 S: one thread issues the slots' GEMMs (tcgen05.mma, kind::f16:
+//     BF16 operands in shared memory in the no-swizzle K-major core-matrix
+//     layout, FP32 accumulators in TMEM) and owns the TMEM allocation;
+//   * warp 4 S + 1: one thread streams the layers' weights (bulk copies into a
+//     double buffer, the next layer's copy overlapping the current layer).
+// Per layer and slot: GEMM1 (A = the conditioning half, K = 16; b1 enters
+// through two columns of ones) -> ReLU, BF16 -> GEMM2 (a K = 16 step that
+// puts b2 into the accumulator, then K = 128) -> ReLU, BF16 -> GEMM3
+// (N = 32: s | t) -> affine coupling.  Each hand-off goes through one mbarrier
+// per direction and slot (a_full: the slot's A operand is written and its
+// accumulator read; d_full: the slot's GEMM has completed); the slot's 128
+// accumulator columns serve all three GEMMs.  The MMA thread issues the
+// slots' GEMMs stage by stage in slot order, so while one slot's warps run an
+// epilogue the tensor core runs the other slots' GEMMs.  Same inputs,
+// outputs and modes as flow_pass_kernel; every wait is bounded, a timeout is
+// reported through the status word, and then every role leaves its loop and
+// TMEM is freed.
+namespace ws {
+constexpr uint32_t tmem_cols(int c) { return c <= 32 ? 32u : c <= 64 ? 64u : c <= 128 ? 128u : c <= 256 ? 256u : 512u; }
+
+// A slot's operand buffer holds, at different times, the A of GEMM2 / GEMM3
+// ([128][128], from the hidden epilogues) and the A of GEMM1 ([128][16], at
+// offset 0, written by the coupling after GEMM3 has completed and read before
+// the next hidden epilogue writes) together with the row scratch (from
+// SCRATCH: a thread's coordinates by dimension between groups).
+constexpr int A_BYTES = umma::W2B;
+constexpr int SCRATCH = umma::W1B;
+constexpr int ROW_FLOATS = 33;   // odd: conflict-free rows
+static_assert(SCRATCH + 128 * ROW_FLOATS * 4 <= A_BYTES, "GEMM1 operand and row scratch fit a slot's buffer");
+
+template <int S_, int CW_>
+struct Cfg {
+    static constexpr int S = S_;                          // tiles in flight (slots)
+    static constexpr int CW = CW_;                        // hidden columns per TMEM wait
+    static constexpr int GROUP = 128 * S;                 // samples per group: all slots run the same layers
+    static constexpr int EPI_WARPS = 4 * S;
+    static constexpr int MMA_WARP = EPI_WARPS, LOAD_WARP = EPI_WARPS + 1;
+    static constexpr int THREADS = 32 * (EPI_WARPS + 2);
+    static constexpr int NE = 12;                         // coordinate pairs per half (dim <= 24)
+    static constexpr int S_W = 0;                         // two layer buffers
+    static constexpr int S_ONES = S_W + 2 * umma::LAYER;  // A of GEMM2's bias step [128][16]
+    static constexpr int S_A = S_ONES + umma::W1B;        // per slot: the A operands (A_BYTES)
+    static constexpr int S_BAR = S_A + S * A_BYTES;       // a_full[S], d_full[S], wfull[2], wempty[2], mdone
+    static constexpr int N_BAR = 2 * S + 5;
+    static constexpr int S_MISC = S_BAR + 8 * N_BAR;      // TMEM address, failure flag
+    static constexpr int SMEM = S_MISC + 16;
+    static constexpr uint32_t TMEM_COLS = tmem_cols(128 * S);
+    static constexpr uint32_t A_COUNT = 128;              // a_full: every thread of the slot arrives
+    static constexpr uint32_t E_COUNT = 1 + 128 * S;      // wempty: the MMA commit + every epilogue thread
+    static_assert(S_ONES % 128 == 0 && S_A % 128 == 0 && S_BAR % 8 == 0, "alignment");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(128 * S <= 512, "TMEM columns");
+    static_assert(CW == 16 || CW % 32 == 0, "whole TMEM loads per wait");
+};
+using Default = Cfg<4, 16>;
+
+__device__ __forceinline__ void arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// every lane waits for completion k of `bar` (bounded); the warp agrees on the outcome
+__device__ __forceinline__ bool wait_warp(uint64_t *bar, uint32_t k) {
+    const bool ok = mbar_wait_bounded(bar, k & 1u, WAIT_LIMIT);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// 8 / 16 consecutive FP32 columns of this thread's TMEM lane (asynchronous: wait_ld before use)
+__device__ __forceinline__ void ld8_async(uint32_t taddr, uint32_t *v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void ld16_async(uint32_t taddr, uint32_t *v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+// y = logit(z) and log(z (1 - z)) = log |dz/dy|, from two logarithms
+// (1 - z is exact for z >= 1/2)
+__device__ __forceinline__ float logit_lsd(float z, float &lsd) {
+    const float a = __logf(z), b = __logf(1.0f - z);
+    lsd = a + b;
+    return a - b;
+}
+// x = sigmoid(y) and log(x (1 - x)) = -|y| - 2 log(1 + exp(-|y|))
+__device__ __forceinline__ float sigmoid_lsd(float y, float &lsd) {
+    const float ay = fabsf(y), e = __expf(-ay), r = __fdividef(1.0f, 1.0f + e);
+    lsd = -ay - 2.0f * __logf(1.0f + e);
+    return y >= 0.f ? r : e * r;
+}
+
+// hidden-layer epilogue of this thread's accumulator row (the bias is already
+// in it): ReLU, BF16 -> that row of the slot's A operand (SBO 2048), CW
+// columns per TMEM wait
+template <int CW>
+__device__ __forceinline__ void hidden(uint32_t taddr, unsigned char *a, int row) {
+    constexpr int LW = CW < 32 ? CW : 32;   // columns per TMEM load
+#pragma unroll
+    for (int h = 0; h < 128 / CW; ++h) {
+        const int c0 = CW * h;
+        uint32_t v[CW];
+#pragma unroll
+        for (int g = 0; g < CW / LW; ++g) {
+            if constexpr (LW == 32) umma::ld32_async(taddr + (uint32_t)(c0 + 32 * g), *reinterpret_cast<uint32_t(*)[32]>(v + 32 * g));
+            else ld16_async(taddr + (uint32_t)(c0 + 16 * g), v + 16 * g);
+        }
+        umma::wait_ld();
+#pragma unroll
+        for (int q = 0; q < CW / 8; ++q) {
+            const uint32_t *u = v + 8 * q;
+            *reinterpret_cast<uint4 *>(a + umma::core_off(row, c0 + 8 * q, 2048)) =
+                make_uint4(relu_pack(__uint_as_float(u[0]), __uint_as_float(u[1])),
+                           relu_pack(__uint_as_float(u[2]), __uint_as_float(u[3])),
+                           relu_pack(__uint_as_float(u[4]), __uint_as_float(u[5])),
+                           relu_pack(__uint_as_float(u[6]), __uint_as_float(u[7])));
+        }
+    }
+}
+
+// One layer for this thread's row.  c: the conditioning half, t: the half the
+// coupling transforms (forward: t e^s + shift; inverse: (t - shift) e^-s).
+// kd counts the completions of the slot's d_full consumed so far.  Returns
+// false (warp-uniform) when a wait gave up.
+template <int CW, int NE>
+__device__ __forceinline__ bool epi_layer(float (&c)[NE], float (&t)[NE], int na, int nb, bool fwd, float &acc,
+                                          const unsigned char *W, unsigned char *a, int row, uint32_t taddr,
+                                          uint64_t *a_full, uint64_t *d_full, uint64_t *wempty, uint32_t &kd) {
+    const float *b3 = reinterpret_cast<const float *>(W + umma::OFF_B3);
+    // GEMM1 operand row: the conditioning half below na, 1 in columns 14 and 15
+    // (W1's b1 hi and lo), else 0 (the accumulator's previous contents were read
+    // before: wait_ld)
+    auto a1v = [&](int k) { return k < NE && k < na ? c[k < NE ? k : 0] : k >= 14 ? 1.0f : 0.f; };
+    uint32_t pk[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) pk[k] = pack_bf16(a1v(2 * k), a1v(2 * k + 1));
+    *reinterpret_cast<uint4 *>(a + umma::core_off(row, 0, 256)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4 *>(a + umma::core_off(row, 8, 256)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    fence_proxy_async_smem();
+    umma::fence_before();
+    arrive(a_full);
+    if (!wait_warp(d_full, kd++)) return false;
+    umma::fence_after();
+    hidden<CW>(taddr, a, row);
+    fence_proxy_async_smem();
+    umma::fence_before();
+    arrive(a_full);
+    if (!wait_warp(d_full, kd++)) return false;
+    umma::fence_after();
+    hidden<CW>(taddr, a, row);
+    fence_proxy_async_smem();
+    umma::fence_before();
+    arrive(a_full);
+    if (!wait_warp(d_full, kd++)) return false;
+    umma::fence_after();
+    // GEMM3: s in columns j, the shift in columns 16 + j (j < nb <= 12)
+    uint32_t os[16], ot[16];
+    ld16_async(taddr, os);
+    ld16_async(taddr + 16u, ot);
+    umma::wait_ld();
+    float part = 0.f;
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+        if (j >= nb) break;   // uniform over the CTA
+        const float sv = umma::soft_clamp(__uint_as_float(os[j]) + b3[j]);
+        const float sh = __uint_as_float(ot[j]) + b3[16 + j];
+        t[j] = fwd ? fmaf(t[j], __expf(sv), sh) : (t[j] - sh) * __expf(-sv);
+        part += sv;
+    }
+    acc += fwd ? part : -part;
+    arrive(wempty);   // this thread is done with the layer's weight buffer
+    return true;
+}
+
+// the GEMM of `stage` (0, 1, 2) for one slot, issued by the MMA thread.
+// GEMM1 takes b1 through columns 14, 15 of its operands; GEMM2 starts with
+// D = ones x W1^T, the ones tile selecting W1's columns 12, 13 (b2 hi and lo).
+__device__ __forceinline__ void issue_stage(int stage, uint32_t d, const unsigned char *W, const unsigned char *a,
+                                            const unsigned char *ones) {
+    if (stage == 0) {
+        umma::mma(d, umma::sdesc(a, 128, 256), umma::sdesc(W + umma::OFF_W1, 128, 256), umma::idesc(128), 0u);
+    } else {
+        const unsigned char *wb = W + (stage == 1 ? umma::OFF_W2 : umma::OFF_W3);
+        const uint32_t id = stage == 1 ? umma::idesc(128) : umma::idesc(32);
+        if (stage == 1)
+            umma::mma(d, umma::sdesc(ones, 128, 256), umma::sdesc(W + umma::OFF_W1, 128, 256), id, 0u);
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks)
+            umma::mma(d, umma::sdesc(a + ks * 256, 128, 2048), umma::sdesc(wb + ks * 256, 128, 2048), id,
+                      (ks > 0 || stage == 1) ? 1u : 0u);
+    }
+}
+}  // namespace ws
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1) flow_ws_kernel(
+    const unsigned char *__restrict__ wglob, FlowDims f, int mode, int64_t n, uint32_t seed_lo, uint32_t seed_hi,
+    uint32_t iter, uint32_t inst, const float *__restrict__ xin, float *__restrict__ xout, float *__restrict__ wout,
+    int *status, int64_t n_flow, float alpha) {
+    constexpr int S = C::S, NE = C::NE;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::S_BAR);
+    uint64_t *a_full = bars, *d_full = bars + S, *wfull = bars + 2 * S, *wempty = bars + 2 * S + 2;
+    uint64_t *mdone = bars + 2 * S + 4;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + C::S_MISC);
+    volatile int *fail = reinterpret_cast<volatile int *>(smem + C::S_MISC + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&a_full[s], C::A_COUNT);
+            mbar_init(&d_full[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&wfull[b], 1);
+            mbar_init(&wempty[b], C::E_COUNT);
+        }
+        mbar_init(mdone, 1);
+        *fail = 0;
+        fence_mbarrier_init();
+    }
+    // the ones tile of GEMM2's bias step: 1 in columns 12 and 13 of every row
+    for (int r = tid; r < 128; r += C::THREADS) {
+        const uint32_t one2 = pack_bf16(1.0f, 1.0f);
+        *reinterpret_cast<uint4 *>(smem + C::S_ONES + umma::core_off(r, 0, 256)) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(smem + C::S_ONES + umma::core_off(r, 8, 256)) = make_uint4(0u, 0u, one2, 0u);
+    }
+    fence_proxy_async_smem();
+    if (warp == C::MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = *tslot;
+    const int64_t ngroups = (n + C::GROUP - 1) / C::GROUP;
+    const int64_t my_groups = ngroups > (int64_t)blockIdx.x ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto dens_of = [&](int64_t g) { return mode == 1 || g * C::GROUP >= n_flow; };
+    auto give_up = [&]() {
+        *fail = 1;
+        if (status) atomicExch(status, DEV_ST_TIMEOUT);
+    };
+
+    if (warp < C::EPI_WARPS) {
+        // ---- epilogue: slot s, TMEM lanes 32 (warp % 4) ..., one sample per lane
+        const int s = warp >> 2, row = 32 * (warp & 3) + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)s;
+        unsigned char *a = smem + C::S_A + s * ws::A_BYTES;
+        float *scratch = reinterpret_cast<float *>(a + ws::SCRATCH) + row * ws::ROW_FLOATS;
+        const int h = f.h, D = f.D;
+        uint32_t kd = 0;
+        int64_t gs = 0;
+        bool ok = true;
+        for (int64_t k = 0; k < my_groups && ok; ++k) {
+            if (__any_sync(0xffffffffu, *fail != 0)) {
+                ok = false;
+                break;
+            }
+            const int64_t g = blockIdx.x + k * gridDim.x;
+            const int64_t base = g * C::GROUP;
+            const int64_t i = base + s * 128 + row;
+            const bool valid = i < n;
+            const bool dens = dens_of(g);
+            const int64_t ii = valid ? i : base;
+            float acc = 0.f;
+            // the row's coordinates y = logit(x), by dimension into the scratch row
+            if (mode == 0) {
+                const uint32_t c0 = (uint32_t)(uint64_t)ii, c1 = (uint32_t)((uint64_t)ii >> 32);
+                for (int b4 = 0; 4 * b4 < D; ++b4) {
+                    const u32x4 rr = philox4x32_10(u32x4{c0, c1, iter, (inst << 8) | (uint32_t)b4}, seed_lo, seed_hi);
+                    const uint32_t wv[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int d = 4 * b4 + q;
+                        if (d < D) {
+                            const float z = word_to_uniform(wv[q]);
+                            float lsd;
+                            scratch[d] = ws::logit_lsd(z, lsd);
+                            acc -= lsd;
+                            // defensive share: the uniform point itself is the sample
+                            if (dens && valid) xout[(int64_t)d * n + i] = z;
+                        }
+                    }
+                }
+            } else {
+                // all loads of the row issued before the first use
+                float xv[2 * NE];
+#pragma unroll
+                for (int q = 0; q < 2 * NE; ++q) xv[q] = valid && q < D ? xin[(int64_t)q * n + i] : 0.5f;
+#pragma unroll
+                for (int q = 0; q < 2 * NE; ++q) {
+                    if (q < D) {
+                        float lsd;
+                        scratch[q] = ws::logit_lsd(clamp_unit(xv[q]), lsd);
+                        acc -= lsd;
+                    }
+                }
+            }
+            // cnd / trn: the conditioning and the transformed half of the current
+            // layer (the first h coordinates for an even layer, the rest for an
+            // odd one), swapped after every layer: one copy of the layer code
+            const int l0 = dens ? f.K - 1 : 0;
+            const int hc = (l0 & 1) ? h : 0, ht = (l0 & 1) ? 0 : h;   // offsets of cnd and trn in the row
+            float cnd[NE], trn[NE];
+#pragma unroll
+            for (int q = 0; q < NE; ++q) {
+                cnd[q] = q < ((l0 & 1) ? D - h : h) ? scratch[hc + q] : 0.f;
+                trn[q] = q < ((l0 & 1) ? h : D - h) ? scratch[ht + q] : 0.f;
+            }
+            for (int step = 0; step < f.K; ++step, ++gs) {
+                const int l = dens ? f.K - 1 - step : step;
+                const int b = (int)(gs & 1);
+                if (!ws::wait_warp(&wfull[b], (uint32_t)(gs >> 1))) {
+                    ok = false;
+                    break;
+                }
+                if (!ws::epi_layer<C::CW, NE>(cnd, trn, a_size(f, l), b_size(f, l), !dens, acc,
+                                              smem + C::S_W + b * umma::LAYER, a, row, taddr, &a_full[s], &d_full[s],
+                                              &wempty[b], kd)) {
+                    ok = false;
+                    break;
+                }
+#pragma unroll
+                for (int q = 0; q < NE; ++q) {
+                    const float tq = cnd[q];
+                    cnd[q] = trn[q];
+                    trn[q] = tq;
+                }
+            }
+            if (!ok) break;
+            // after K layers cnd is the half a layer of parity l0 + K would
+            // condition on; back into the scratch row by dimension (the slot's
+            // last GEMM has completed)
+            const bool odd = (l0 + f.K) & 1;
+#pragma unroll
+            for (int q = 0; q < NE; ++q) {
+                if (q < (odd ? D - h : h)) scratch[(odd ? h : 0) + q] = cnd[q];
+                if (q < (odd ? h : D - h)) scratch[(odd ? 0 : h) + q] = trn[q];
+            }
+            if (valid) {
+                for (int d = 0; d < D; ++d) {
+                    float lsd;
+                    const float x = ws::sigmoid_lsd(scratch[d], lsd);
+                    acc += lsd;
+                    if (mode == 0 && !dens) xout[(int64_t)d * n + i] = x;
+                }
+                // forward: acc = log |det dx/dz| = -log q; inverse: acc = log q(x)
+                if (mode == 1) {
+                    wout[i] = acc;
+                } else if (alpha == 0.f) {
+                    wout[i] = __expf(acc);
+                } else {
+                    const float q = __expf(dens ? acc : -acc);
+                    wout[i] = 1.0f / fmaf(1.0f - alpha, q, alpha);
+                }
+            }
+        }
+        if (!ok) give_up();
+    } else if (warp == C::MMA_WARP) {
+        // ---- MMA issue, in the slots' common order: stage by stage, slot by slot
+        if (lane == 0) {
+            uint32_t ka[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) ka[s] = 0;
+            int64_t gs = 0;
+            bool ok = true;
+            for (int64_t k = 0; k < my_groups && ok; ++k) {
+                for (int step = 0; step < f.K; ++step, ++gs) {
+                    const int b = (int)(gs & 1);
+                    if (!mbar_wait_bounded(&wfull[b], (uint32_t)(gs >> 1) & 1u, WAIT_LIMIT)) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned char *W = smem + C::S_W + b * umma::LAYER;
+                    for (int st = 0; st < 3 && ok; ++st) {
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            if (!mbar_wait_bounded(&a_full[s], ka[s] & 1u, WAIT_LIMIT)) {
+                                ok = false;
+                                break;
+                            }
+                            ++ka[s];
+                            umma::fence_after();
+                            ws::issue_stage(st, tmem + 128u * (uint32_t)s, W, smem + C::S_A + s * ws::A_BYTES,
+                                            smem + C::S_ONES);
+                            umma::commit(&d_full[s]);
+                        }
+                    }
+                    if (!ok) break;
+                    // the weight buffer is free once every slot's last GEMM of the step has completed
+                    umma::commit(&wempty[b]);
+                }
+            }
+            if (!ok) give_up();
+            // every MMA issued by this thread completes before TMEM is released
+            umma::commit(mdone);
+            (void)mbar_wait_bounded(mdone, 0u, WAIT_LIMIT);
+        }
+        __syncwarp();
+    } else if (warp == C::LOAD_WARP) {
+        // ---- weights: one bulk copy per step into the buffer of the step's parity
+        if (lane == 0) {
+            uint32_t issued[2] = {0u, 0u};
+            int64_t gs = 0;
+            bool ok = true;
+            for (int64_t k = 0; k < my_groups && ok; ++k) {
+                const bool dens = dens_of(blockIdx.x + k * gridDim.x);
+                for (int step = 0; step < f.K; ++step, ++gs) {
+                    const int b = (int)(gs & 1);
+                    const int l = dens ? f.K - 1 - step : step;
+                    if (gs >= 2 && !mbar_wait_bounded(&wempty[b], (uint32_t)((gs >> 1) - 1) & 1u, WAIT_LIMIT)) {
+                        ok = false;
+                        break;
+                    }
+                    if (*fail) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async_smem();
+                    mbar_expect_tx(&wfull[b], umma::LAYER);
+                    bulk_g2s(smem + C::S_W + b * umma::LAYER, wglob + (size_t)l * umma::LAYER, umma::LAYER,
+                             &wfull[b]);
+                    ++issued[b];
+                }
+            }
+            if (!ok) give_up();
+            // copies in flight land before the CTA's shared memory goes away
+            for (int b = 0; b < 2; ++b)
+                if (issued[b]) (void)mbar_wait_bounded(&wfull[b], (issued[b] - 1u) & 1u, WAIT_LIMIT);
+        }
+        __syncwarp();
+    }
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    if (warp == C::MMA_WARP)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS)
+                     : "memory");
+}
+
 }  // namespace
 
 struct fd_flow {
@@ -1363,7 +1823,7 @@ struct fd_flow {
     float *d_blob = nullptr, *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr, *d_gpad = nullptr;
     unsigned char *d_wpack = nullptr;
     unsigned char *d_wumma = nullptr;   // weights in the tcgen05 operand layout
-    int tensor_path = 0;                // sampling / density: 0 mma.sync (default, faster), 1 tcgen05
+    int tensor_path = 2;                // sampling / density: 0 mma.sync, 1 tcgen05 (tile pairs), 2 tcgen05 warp-specialised
     double *d_wsum = nullptr;
     float *d_loss = nullptr;
     float *d_vbuf = nullptr, *d_gbuf = nullptr;
@@ -1404,10 +1864,23 @@ int grid_for(int64_t units, int per_sm_ctas) {
     return (int)std::max<int64_t>(g, 1);
 }
 
+template <class C>
+fd_status launch_ws(const fd_flow *f, int mode, int64_t n, uint64_t seed, uint64_t iter, int32_t inst,
+                    const float *xin, float *xout, float *wout, int64_t n_flow, float alpha, cudaStream_t st) {
+    FD_CHECK_CUDA(cudaFuncSetAttribute(flow_ws_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    flow_ws_kernel<C><<<grid_for((n + C::GROUP - 1) / C::GROUP, 1), C::THREADS, C::SMEM, st>>>(
+        f->d_wumma, dims_of(f), mode, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)inst, xin,
+        xout, wout, fd::device_status_word(), n_flow, alpha);
+    FD_CHECK_CUDA(cudaGetLastError());
+    return FD_OK;
+}
+
 // sampling (mode 0, flow share [0, n_flow), weights 1 / ((1 - alpha) q + alpha)) or density (mode 1)
 fd_status launch_pass(const fd_flow *f, int mode, int64_t n, uint64_t seed, uint64_t iter, int32_t inst,
                       const float *xin, float *xout, float *wout, int64_t n_flow, float alpha, cudaStream_t st) {
-    if (f->tensor_path == 1) {
+    if (f->tensor_path == 2) {
+        return launch_ws<ws::Default>(f, mode, n, seed, iter, inst, xin, xout, wout, n_flow, alpha, st);
+    } else if (f->tensor_path == 1) {
         FD_CHECK_CUDA(cudaFuncSetAttribute(flow_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            umma::SMEM));
         flow_umma_kernel<<<grid_for((n + umma::BLOCK_U - 1) / umma::BLOCK_U, 1), umma::THREADS, umma::SMEM, st>>>(
@@ -1588,6 +2061,8 @@ extern "C" fd_status fd_flow_sample_defensive(const fd_flow *f, uint64_t seed, u
     FD_REQUIRE(alpha >= 0.0 && alpha <= 0.5, "alpha must be in [0, 0.5]");
     // the flow share ends on a block boundary of both sampling kernels, so every block is of one kind
     constexpr int64_t UNIT = umma::BLOCK_U;
+    static_assert(UNIT % BLOCK == 0 && UNIT % ws::Default::GROUP == 0,
+                  "the flow share ends on every kernel's block boundary");
     const int64_t n_flow = std::min(n, (n - (int64_t)(alpha * (double)n) + UNIT - 1) / UNIT * UNIT);
     const int64_t n_u = n - n_flow;
     const float a = (float)((double)n_u / (double)n);
@@ -1603,7 +2078,7 @@ extern "C" fd_status fd_flow_log_density(const fd_flow *f, const float *x, int64
 
 extern "C" fd_status fd_flow_set_tensor_path(fd_flow *f, int32_t path) {
     FD_REQUIRE(f, "null flow");
-    FD_REQUIRE(path == 0 || path == 1, "path must be 0 (mma.sync) or 1 (tcgen05)");
+    FD_REQUIRE(path >= 0 && path <= 2, "path must be 0 (mma.sync), 1 (tcgen05) or 2 (tcgen05, warp-specialised)");
     f->tensor_path = path;
     return FD_OK;
 }

@@ -81,21 +81,23 @@ def test_defensive_mixture_parity(api):
     assert np.all(wg <= 1.0 / a * (1 + 1e-6))
 
 
-def test_tensor_paths_agree(api):
-    # tcgen05 and mma.sync (default) sampling / density passes compute the same
-    # BF16 contract; n spans several 512-sample blocks and a ragged tail
+@pytest.mark.parametrize("path", [1, 2])
+def test_tensor_paths_agree(api, path):
+    # the tcgen05 paths (1: tiles in pairs; 2: warp-specialised) and mma.sync
+    # (path 0) compute the same BF16 contract; n spans several 512-sample
+    # blocks and a ragged tail
     F, blob = _flow(api)
     n = 5000
     out = {}
-    for path in (1, 0):
-        F.set_tensor_path(path)
+    for p in (path, 0):
+        F.set_tensor_path(p)
         x, w = F.sample(5, 1, 2, n)
         lq = F.log_density(x)
         xd, wd, _ = F.sample_defensive(5, 1, 2, n, 0.2)
         torch.cuda.synchronize()
-        out[path] = [t.cpu().numpy().astype(np.float64) for t in (x, w, lq, xd, wd)]
-    F.set_tensor_path(0)
-    (x1, w1, l1, xd1, wd1), (x0, w0, l0, xd0, wd0) = out[1], out[0]
+        out[p] = [t.cpu().numpy().astype(np.float64) for t in (x, w, lq, xd, wd)]
+    F.set_tensor_path(2)
+    (x1, w1, l1, xd1, wd1), (x0, w0, l0, xd0, wd0) = out[path], out[0]
     assert np.abs(x1 - x0).max() < 2e-3
     assert np.abs(np.log(w1) - np.log(w0)).max() < 2e-2
     assert np.abs(l1 - l0).max() < 2e-2
@@ -105,15 +107,16 @@ def test_tensor_paths_agree(api):
     assert np.quantile(np.abs(l1 + np.log(w1)), 0.99) < 2e-3
 
 
-def test_tcgen05_path_parity(api):
+@pytest.mark.parametrize("path", [1, 2])
+def test_tcgen05_path_parity(api, path):
     # the tcgen05 sampling and density passes against the FP64 oracle under the BF16 contract
     F, blob = _flow(api)
-    F.set_tensor_path(1)
+    F.set_tensor_path(path)
     n = 3000
     x, w = F.sample(21, 2, 3, n)
     lq = F.log_density(x)
     torch.cuda.synchronize()
-    F.set_tensor_path(0)
+    F.set_tensor_path(2)
     z = ophilox.uniforms(21, 2, 3, np.arange(n), D)
     xr, lqr = oflow.forward(blob, z, D, K, H)
     dx = np.abs(x.cpu().numpy().astype(np.float64) - xr)
@@ -189,3 +192,42 @@ def test_training_reduces_loss_and_first_adam_step(api):
     more = F.train(x, w, 60, 3e-3)
     print("train losses", losses[0], more[0], more[-1])
     assert more[-1] < more[0] - 0.05
+
+
+@pytest.mark.parametrize("dim,layers", [(19, 8), (7, 3), (24, 2)])
+def test_default_path_many_groups_per_cta(api, dim, layers):
+    # n above 152 SMs x 512 samples, so every CTA of the warp-specialised kernel
+    # runs several groups (the weight buffers' phases carry over from group to
+    # group) and the last group is ragged; odd layer counts end on the other
+    # half.  Sampled rows against the oracle, all rows against mma.sync.
+    F = api.Flow(dim, layers, H, seed=0)
+    blob = workloads.normal_blob(7, F.n_params, 0.06)
+    F.set_params(blob)
+    n = (1 << 18) + 333
+    x, w = F.sample(9, 4, 1, n)
+    lq = F.log_density(x)
+    xd, wd, a = F.sample_defensive(9, 4, 1, n, 0.3)
+    F.set_tensor_path(0)
+    x0, w0 = F.sample(9, 4, 1, n)
+    lq0 = F.log_density(x)
+    F.set_tensor_path(2)
+    torch.cuda.synchronize()
+    xg, wg, lg = (t.cpu().numpy().astype(np.float64) for t in (x, w, lq))
+    assert np.abs(xg - x0.cpu().numpy()).max() < 2e-3
+    assert np.abs(np.log(wg) - np.log(w0.cpu().numpy().astype(np.float64))).max() < 2e-2
+    assert np.abs(lg - lq0.cpu().numpy()).max() < 2e-2
+    assert np.quantile(np.abs(lg + np.log(wg)), 0.99) < 2e-3
+    rows = np.unique(np.concatenate([np.arange(64), np.random.default_rng(3).integers(0, n, 1500), np.arange(n - 64, n)]))
+    z = ophilox.uniforms(9, 4, 1, rows, dim)
+    xr, lqr = oflow.forward(blob, z, dim, layers, H)
+    dx = np.abs(xg[:, rows] - xr)
+    dl = np.abs(np.log(wg[rows]) + lqr)
+    assert dx.max() < 2e-3 and np.quantile(dx, 0.99) < 2e-4
+    assert dl.max() < 2e-2 and np.quantile(dl, 0.99) < 2e-3
+    # defensive mixture: the flow share ends on a 512-sample boundary
+    nf = n - int(round(a * n))
+    assert nf % 512 == 0 or nf == n
+    xdg = xd.cpu().numpy()
+    u = ophilox.uniforms(9, 4, 1, np.arange(nf, n), dim)
+    assert np.array_equal(xdg[:, nf:], u.astype(np.float32))
+    assert np.abs(xdg[:, :nf] - xg[:, :nf]).max() == 0.0

@@ -52,14 +52,21 @@ def _reference(order, roots, x, construction):
     return out, mag
 
 
-@pytest.mark.parametrize("jit", [False, True])
+# specialised-kernel variants: the small shared-memory leaf cache of the
+# lower orders and the large global one of the order-6 effective-mass graph
+JIT = {"lc24": dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sv_smem=True, leaf_cache=24),
+       "lc2048_global": dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True,
+                             leaf_cache=2048, lc_global=True)}
+
+
+@pytest.mark.parametrize("jit", [None, "lc24", "lc2048_global"])
 @pytest.mark.parametrize("order,with_dk,n", [(2, True, 3001), (3, True, 2049), (4, False, 700), (5, False, 513)])
 def test_parquet_tape_per_sample_parity(api, construction, order, with_dk, n, jit):
     roots = fdgraph.graph_roots(order, with_dk=with_dk)
     tape = PG.parquet_tape(order, roots, budget=8192 if jit else 96, construction=construction).to_bytes()
     G = api.Graph(order, roots, tape=tape)
     if jit:
-        G.jit(threads=256, min_blocks=1, spt=2, unit_cap=12000, sv_smem=True, leaf_cache=24)
+        G.jit(**JIT[jit])
     plan = api.EvalPlan([G], [api.ueg_params(order, 1.0, 1.0 / 25.0, 1.0, 1.0)], [0], n, per_sample=True)
     seed = 61 + order
     plan.run(seed, 0)
