@@ -124,8 +124,11 @@ def run(rs, max_order, n, iters, adapt, T_over_TF=1.0 / 25.0, lam_over_kF=1.0, s
     Lam = (lam_over_kF * kF) ** 2
     meff, err = analysis.meff_with_errors(max_order, sig, sig_e, dsig, dsig_e, kF, beta, Lam)
     pp = api.postprocess(max_order, sig, dsig, kF, beta, Lam)
+    est, trunc = analysis.truncation_estimate(meff[1:]) if max_order >= 3 else (float(meff[-1]), None)
     return {"rs": rs, "T_over_TF": T_over_TF, "lam_over_kF": lam_over_kF, "samples_per_iter": n, "iters": iters,
             "meff": [float(v) for v in meff[1:]], "meff_err": [float(v) for v in err[1:]],
+            "estimate": {"meff": est, "stat": float(err[-1]), "truncation": trunc,
+                         "rule": "highest-order partial sum; truncation = largest deviation of the last three"},
             "dmu": [float(v) for v in pp["dmu"][1:]], "a": [float(v) for v in pp["a"][1:]],
             "b": [float(v) for v in pp["b"][1:]], "orders": infos}
 
