@@ -26,13 +26,16 @@ SHAPES = [(128, 2), (256, 1), (128, 1), (64, 2)]
 # specialised-kernel variants (fd_jit_options; unlisted options at their defaults)
 JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_every=1, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sv_smem=True),
+                dict(threads=256, min_blocks=1, spt=4, unit_cap=9000, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=4, unit_cap=6000, sv_smem=True),
                 dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True)]
 # Not tried by default, all slower than the best of these at order 5 on GB300:
 # leaf caches in shared memory (spt 1, 2, 4 with 24 - 128 cached floats: 15 - 31 %
 # slower), the leaf cache in a global L2 scratch (320 floats per sample at spt 3
 # and 4: 3.2e8 and 2.7e8 against 4.0e8 samples/s) and 3 samples per thread,
-# which leaves room for the tile histogram (3.3e8 - 3.4e8).
+# which leaves room for the tile histogram (3.3e8 - 3.4e8); two CTAs of 256
+# threads per SM (128 registers, 2 samples per thread: 2.6e8), three of 128
+# threads (3.2e8 - 3.5e8) and units of cost 16000 (3.4e8).
 JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap", "pair", "sv_smem",
             "cross_roots", "leaf_cache", "lc_global")
 
