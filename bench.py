@@ -291,22 +291,27 @@ def affine_flow_sampling(api, F, default_path, n=1 << 24, reps=5):
 
 
 def spline_flow_sampling(api, dim, layers=8, n=1 << 22, reps=3):
-    """Samples/s of the spline flow's sampling and density pass (App. A), seeded
-    untrained parameters."""
+    """Samples/s of the spline flow's sampling pass (App. A), seeded untrained
+    parameters: the default conditioner on BF16 tensor cores, and on FP32 CUDA
+    cores."""
     import torch
     g = api.SplineFlow(dim, layers)
     g.set_params(workloads.small_params(7, g.n_params))
-    g.sample(1, 0, 0, n)
-    torch.cuda.synchronize()
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.record()
-    for r in range(reps):
-        g.sample(1, r + 1, 0, n)
-    e.record()
-    torch.cuda.synchronize()
-    ms = s.elapsed_time(e) / reps
-    return {"samples_per_s": n / ms * 1e3, "dim": dim, "layers": layers, "samples": n, "ms": ms,
-            "parameters": "seeded, untrained"}
+    out = {"dim": dim, "layers": layers, "samples": n, "parameters": "seeded, untrained"}
+    for path, name in ((1, "tensor"), (0, "fp32")):
+        g.set_tensor_path(path)
+        g.sample(1, 0, 0, n)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for r in range(reps):
+            g.sample(1, r + 1, 0, n)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / reps
+        out[name] = {"samples_per_s": n / ms * 1e3, "ms": ms}
+    out["samples_per_s"] = out["tensor"]["samples_per_s"]
+    return out
 
 
 def spline_flow_training(api, dim, layers=8, n=1 << 16, reps=3):

@@ -398,6 +398,14 @@ fd_status fd_nsf_sample_w(const fd_nsf *f, uint64_t seed, uint64_t iter, int32_t
  * log q(x) (device FP32 [n]) for device x [dim][n] in [0, 1]^dim.
  * Asynchronous on stream. */
 fd_status fd_nsf_log_density(const fd_nsf *f, const float *x, int64_t n, float *z, float *logq, void *stream);
+/* Where the sampling and density passes (fd_nsf_forward, fd_nsf_sample,
+ * fd_nsf_sample_w, fd_nsf_log_density) evaluate the conditioner: 1 (default)
+ * = BF16 tensor cores (mma.sync tiles; the weights and every GEMM input
+ * rounded to BF16, FP32 accumulation and residual stream: the BF16 contract
+ * of the affine flow's sampler), 0 = FP32 CUDA cores.  The splines are FP32
+ * on both paths; the training gradient (fd_nsf_kl_grad, fd_nsf_train) is
+ * FP32.  FD_EINVAL for another path. */
+fd_status fd_nsf_set_tensor_path(fd_nsf *f, int32_t path);
 /* Forward-KL training loss of the flow (App. A) and its gradient:
  * loss = -sum_i w_i log q(x_i) / sum_i w_i over device points x [dim][n] in
  * [0, 1]^dim with device weights w [n] (e.g. |f|/q of the proposal that drew

@@ -26,6 +26,8 @@ stays unchanged.
 """
 import numpy as np
 
+from .flow import bf16
+
 K_BINS = 8
 HIDDEN = 32
 MIN_W = MIN_H = MIN_D = 1e-3
@@ -103,6 +105,18 @@ def rq_inverse(y, theta_w, theta_h, theta_d):
     return x, -logd
 
 
+_PREC = {"mode": "f64"}
+
+
+def set_precision(mode):
+    """'f64' (default) or 'bf16': the conditioner under the BF16 contract of
+    the tensor-core sampler (the weights and every GEMM input -- the kept
+    coordinates, relu(h), relu(t), the last hidden vector -- rounded to BF16;
+    biases, sums and the residual stream in FP64)."""
+    assert mode in ("f64", "bf16")
+    _PREC["mode"] = mode
+
+
 class Conditioner:
     """Residual network: in -> 32, two residual blocks, 32 -> out (FP64)."""
 
@@ -114,12 +128,13 @@ class Conditioner:
         self.w1, self.b1 = lin(HIDDEN, n_out)
 
     def __call__(self, u):
-        h = u @ self.w0 + self.b0
+        r = bf16 if _PREC["mode"] == "bf16" else (lambda a: a)
+        h = r(u) @ r(self.w0) + self.b0
         for (wa, ba), (wb, bb) in self.blocks:
-            t = np.maximum(h, 0.0) @ wa + ba
-            t = np.maximum(t, 0.0) @ wb + bb
+            t = r(np.maximum(h, 0.0)) @ r(wa) + ba
+            t = r(np.maximum(t, 0.0)) @ r(wb) + bb
             h = h + t
-        return h @ self.w1 + self.b1
+        return r(h) @ r(self.w1) + self.b1
 
 
 class SplineFlow:

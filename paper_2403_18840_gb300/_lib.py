@@ -96,6 +96,7 @@ SIGNATURES = {
     "fd_nsf_param_count": (_i64, [_vp]),
     "fd_nsf_set_params": (_i32, [_vp, _pf, _i64]),
     "fd_nsf_forward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "fd_nsf_set_tensor_path": (_i32, [_vp, _i32]),
     "fd_nsf_sample": (_i32, [_vp, _u64, _u64, _i32, _i64, _vp, _vp, _vp]),
     "fd_nsf_sample_w": (_i32, [_vp, _u64, _u64, _i32, _i64, _vp, _vp, _vp]),
     "fd_nsf_log_density": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),

@@ -321,6 +321,11 @@ class SplineFlow:
                                           out.size))
         return out
 
+    def set_tensor_path(self, path):
+        """Conditioner of the sampling / density passes on BF16 tensor cores (1,
+        default) or FP32 CUDA cores (0)."""
+        L.check(L.lib().fd_nsf_set_tensor_path(self.handle, path))
+
     def forward(self, z, stream=None):
         n = z.shape[1]
         x = torch.empty((self.dim, n), dtype=torch.float32, device="cuda")

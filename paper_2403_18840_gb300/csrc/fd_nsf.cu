@@ -15,6 +15,8 @@
 // spline parameters are computed just before its spline, so they never need
 // more than 23 registers.  FP32 arithmetic with IEEE exp/log (the parameters
 // pass through softmax and softplus).
+#include <cuda_bf16.h>
+
 #include "fd_internal.cuh"
 #include "fd_nsf_math.cuh"
 
@@ -181,6 +183,288 @@ __global__ void __launch_bounds__(128) nsf_kernel(const NsfArgs a) {
 }
 
 
+// ---- sampling and density with the conditioner on the tensor cores ----------------
+// The conditioner's GEMMs as warp-level mma.sync m16n8k16 tiles: BF16 weights
+// and GEMM inputs (the kept coordinates, relu(h), relu(t), h2), FP32
+// accumulation and an FP32 residual stream (the BF16 contract of the affine
+// flow's sampler).  A warp takes 32 samples (two 16-row tiles); a CTA of four
+// warps takes ROUNDS tiles of 128 samples per staging of a layer's weights.
+// Per layer: h = W0 x_keep + b0 and the two residual blocks stay in
+// registers (accumulators become the next GEMM's A fragments); the 24
+// outputs of every moved coordinate (23 spline parameters and a zero) go
+// through a per-warp scratch to the sample's own thread, which evaluates the
+// spline in FP32 as in nsf_kernel.  A sample's coordinates live in a shared
+// memory row.
+namespace nsf_tc {
+constexpr int ROUNDS = 2;
+constexpr int WARPS = 4, THREADS = 32 * WARPS, BLOCK = THREADS * ROUNDS;
+constexpr int LD16 = 24, LD32 = 40;     // BF16 row pitches of the staged W^T (conflict-free fragment loads)
+constexpr int VROW = 25, PROW = 25;     // floats per coordinate row and per parameter row (odd)
+constexpr int MAXMOVE = kMaxDim / 2;    // at most 12 moved coordinates per layer
+// staged layer, BF16 part: W0^T [32][LD16], Wa^T, Wb^T of both blocks [32][LD32], W1^T [n_move * 24][LD32]
+constexpr int OFF_W0 = 0, OFF_WA = OFF_W0 + kHidden * LD16, OFF_WB = OFF_WA + 2 * kHidden * LD32;
+constexpr int OFF_W1 = OFF_WB + 2 * kHidden * LD32;
+constexpr int BF_ELEMS = OFF_W1 + MAXMOVE * kPad * LD32;
+// FP32 part: b0 [32], ba [2][32], bb [2][32], b1 [n_move * 24]
+constexpr int F_B0 = 0, F_BA = kHidden, F_BB = 3 * kHidden, F_B1 = 5 * kHidden;
+constexpr int F_ELEMS = F_B1 + MAXMOVE * kPad;
+constexpr size_t SMEM = (size_t)BF_ELEMS * 2 + (size_t)F_ELEMS * 4 + (size_t)BLOCK * VROW * 4 +
+                        (size_t)WARPS * 32 * PROW * 4;
+static_assert((BF_ELEMS * 2) % 16 == 0, "alignment of the FP32 part");
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ uint32_t relu2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// B fragment (k-tile kt, n-tile nt) of B = W (K x N) from W^T rows of pitch ld
+__device__ __forceinline__ void bfrag(const __nv_bfloat16 *WT, int ld, int kt, int nt, int g, int t, uint32_t &b0,
+                                      uint32_t &b1) {
+    const __nv_bfloat16 *p = WT + (nt * 8 + g) * ld + kt * 16 + 2 * t;
+    b0 = *reinterpret_cast<const uint32_t *>(p);
+    b1 = *reinterpret_cast<const uint32_t *>(p + 8);
+}
+// accumulators of n-tiles (2j, 2j+1) -> the A fragment of k-tile j (ReLU or not)
+template <bool RELU>
+__device__ __forceinline__ void c_to_a(const float (&c0)[4], const float (&c1)[4], uint32_t (&a)[4]) {
+    if (RELU) {
+        a[0] = relu2(c0[0], c0[1]);
+        a[1] = relu2(c0[2], c0[3]);
+        a[2] = relu2(c1[0], c1[1]);
+        a[3] = relu2(c1[2], c1[3]);
+    } else {
+        a[0] = pack2(c0[0], c0[1]);
+        a[1] = pack2(c0[2], c0[3]);
+        a[2] = pack2(c1[0], c1[1]);
+        a[3] = pack2(c1[2], c1[3]);
+    }
+}
+
+// one layer's weights, BF16 and transposed (outputs by rows), from the parameter vector
+__device__ void stage(const float *lp, int n_keep, int n_move, __nv_bfloat16 *bw, float *fw) {
+    const int row = n_move * kParamsPerDim;                 // W1 row length in the parameter vector
+    const float *W0 = lp, *b0 = W0 + n_keep * kHidden, *blk = b0 + kHidden;
+    const float *W1 = lp + head_floats(n_keep), *b1 = W1 + (int64_t)kHidden * row;
+    __syncthreads();                                        // the previous layer's weights are consumed
+    for (int k = threadIdx.x; k < kHidden * 16; k += THREADS) {
+        const int nn = k / 16, kk = k % 16;
+        bw[OFF_W0 + nn * LD16 + kk] = __float2bfloat16_rn(kk < n_keep ? W0[kk * kHidden + nn] : 0.0f);
+    }
+    for (int k = threadIdx.x; k < 4 * kHidden * kHidden; k += THREADS) {
+        const int mat = k / (kHidden * kHidden), e = k % (kHidden * kHidden), nn = e / kHidden, kk = e % kHidden;
+        const int bk = mat >> 1, second = mat & 1;         // Wa0, Wb0, Wa1, Wb1
+        const float *W = blk + bk * 2 * (kHidden * kHidden + kHidden) + second * (kHidden * kHidden + kHidden);
+        bw[(second ? OFF_WB : OFF_WA) + bk * kHidden * LD32 + nn * LD32 + kk] = __float2bfloat16_rn(W[kk * kHidden + nn]);
+    }
+    for (int k = threadIdx.x; k < n_move * kPad * kHidden; k += THREADS) {
+        const int nn = k / kHidden, kk = k % kHidden, m = nn / kPad, q = nn % kPad;
+        bw[OFF_W1 + nn * LD32 + kk] =
+            __float2bfloat16_rn(q < kParamsPerDim ? W1[(int64_t)kk * row + m * kParamsPerDim + q] : 0.0f);
+    }
+    for (int k = threadIdx.x; k < kHidden; k += THREADS) {
+        fw[F_B0 + k] = b0[k];
+        for (int bk = 0; bk < 2; ++bk) {
+            const float *Wa = blk + bk * 2 * (kHidden * kHidden + kHidden);
+            fw[F_BA + bk * kHidden + k] = Wa[kHidden * kHidden + k];
+            fw[F_BB + bk * kHidden + k] = Wa[2 * kHidden * kHidden + kHidden + k];
+        }
+    }
+    for (int k = threadIdx.x; k < n_move * kPad; k += THREADS) {
+        const int m = k / kPad, q = k % kPad;
+        fw[F_B1 + k] = q < kParamsPerDim ? b1[m * kParamsPerDim + q] : 0.0f;
+    }
+    __syncthreads();
+}
+}  // namespace nsf_tc
+
+template <bool INV>
+__global__ void __launch_bounds__(nsf_tc::THREADS) nsf_tc_kernel(const NsfArgs a) {
+    using namespace nsf_tc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16 *bw = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+    float *fw = reinterpret_cast<float *>(smem_raw + (size_t)BF_ELEMS * 2);
+    float *V = fw + F_ELEMS;                                // [BLOCK][VROW] coordinates
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float *P = V + BLOCK * VROW + warp * 32 * PROW;         // this warp's [32][PROW] spline parameters
+    const int D = a.dim, half = D / 2;
+    const int64_t base = (int64_t)blockIdx.x * BLOCK;
+    // the coordinates of the block's samples (sample r of the block in row r)
+    float logq[ROUNDS];
+    for (int r = 0; r < ROUNDS; ++r) {
+        const int row = r * THREADS + threadIdx.x;
+        const int64_t i = base + row;
+        const bool valid = i < a.n;
+        float *v = V + row * VROW;
+        logq[r] = 0.0f;
+        if (a.z) {
+            for (int j = 0; j < D; ++j) v[j] = valid ? a.z[(int64_t)j * a.ldz + i] : 0.5f;
+        } else {
+            for (int b = 0; 4 * b < D; ++b) {
+                const u32x4 rr = philox4x32_10(u32x4{(uint32_t)i, (uint32_t)((uint64_t)i >> 32), a.iter,
+                                                     (a.inst << 8) | (uint32_t)b},
+                                               a.seed_lo, a.seed_hi);
+                const uint32_t ws[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (4 * b + q < D) v[4 * b + q] = word_to_uniform(ws[q]);
+            }
+        }
+    }
+    for (int step = 0; step < a.n_layers; ++step) {
+        const int layer = INV ? a.n_layers - 1 - step : step;
+        const int keep0 = layer % 2 == 0 ? 0 : half, n_keep = layer % 2 == 0 ? half : D - half;
+        const int move0 = layer % 2 == 0 ? half : 0, n_move = D - n_keep;
+        stage(a.params + layer_offset(layer, D), n_keep, n_move, bw, fw);
+        for (int r = 0; r < ROUNDS; ++r) {
+            const float *Vt = V + (r * THREADS + warp * 32) * VROW;   // this warp's 32 rows
+            // input fragments: the kept coordinates (K = 16, zero beyond n_keep)
+            uint32_t ax[2][4];
+#pragma unroll
+            for (int rt = 0; rt < 2; ++rt) {
+                const float *r0 = Vt + (16 * rt + g) * VROW + keep0, *r1 = r0 + 8 * VROW;
+                auto kv = [&](const float *rw, int k) { return k < n_keep ? rw[k] : 0.0f; };
+                ax[rt][0] = pack2(kv(r0, 2 * t), kv(r0, 2 * t + 1));
+                ax[rt][1] = pack2(kv(r1, 2 * t), kv(r1, 2 * t + 1));
+                ax[rt][2] = pack2(kv(r0, 2 * t + 8), kv(r0, 2 * t + 9));
+                ax[rt][3] = pack2(kv(r1, 2 * t + 8), kv(r1, 2 * t + 9));
+            }
+            // h = W0 x + b0
+            float h[2][4][4];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const float u0 = fw[F_B0 + nt * 8 + 2 * t], u1 = fw[F_B0 + nt * 8 + 2 * t + 1];
+                uint32_t b0, b1;
+                bfrag(bw + OFF_W0, LD16, 0, nt, g, t, b0, b1);
+#pragma unroll
+                for (int rt = 0; rt < 2; ++rt) {
+                    h[rt][nt][0] = u0;
+                    h[rt][nt][1] = u1;
+                    h[rt][nt][2] = u0;
+                    h[rt][nt][3] = u1;
+                    mma(h[rt][nt], ax[rt], b0, b1);
+                }
+            }
+            // two residual blocks: h += Wb relu(Wa relu(h) + ba) + bb
+#pragma unroll
+            for (int bk = 0; bk < 2; ++bk) {
+                const __nv_bfloat16 *WaT = bw + OFF_WA + bk * kHidden * LD32, *WbT = bw + OFF_WB + bk * kHidden * LD32;
+                uint32_t ah[2][2][4];
+#pragma unroll
+                for (int rt = 0; rt < 2; ++rt)
+#pragma unroll
+                    for (int kt = 0; kt < 2; ++kt) c_to_a<true>(h[rt][2 * kt], h[rt][2 * kt + 1], ah[rt][kt]);
+                float tt[2][4][4];
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const float u0 = fw[F_BA + bk * kHidden + nt * 8 + 2 * t];
+                    const float u1 = fw[F_BA + bk * kHidden + nt * 8 + 2 * t + 1];
+#pragma unroll
+                    for (int rt = 0; rt < 2; ++rt) {
+                        tt[rt][nt][0] = u0;
+                        tt[rt][nt][1] = u1;
+                        tt[rt][nt][2] = u0;
+                        tt[rt][nt][3] = u1;
+                    }
+#pragma unroll
+                    for (int kt = 0; kt < 2; ++kt) {
+                        uint32_t b0, b1;
+                        bfrag(WaT, LD32, kt, nt, g, t, b0, b1);
+#pragma unroll
+                        for (int rt = 0; rt < 2; ++rt) mma(tt[rt][nt], ah[rt][kt], b0, b1);
+                    }
+                }
+                uint32_t at[2][2][4];
+#pragma unroll
+                for (int rt = 0; rt < 2; ++rt)
+#pragma unroll
+                    for (int kt = 0; kt < 2; ++kt) c_to_a<true>(tt[rt][2 * kt], tt[rt][2 * kt + 1], at[rt][kt]);
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const float u0 = fw[F_BB + bk * kHidden + nt * 8 + 2 * t];
+                    const float u1 = fw[F_BB + bk * kHidden + nt * 8 + 2 * t + 1];
+#pragma unroll
+                    for (int rt = 0; rt < 2; ++rt) {
+                        h[rt][nt][0] += u0;
+                        h[rt][nt][1] += u1;
+                        h[rt][nt][2] += u0;
+                        h[rt][nt][3] += u1;
+                    }
+#pragma unroll
+                    for (int kt = 0; kt < 2; ++kt) {
+                        uint32_t b0, b1;
+                        bfrag(WbT, LD32, kt, nt, g, t, b0, b1);
+#pragma unroll
+                        for (int rt = 0; rt < 2; ++rt) mma(h[rt][nt], at[rt][kt], b0, b1);
+                    }
+                }
+            }
+            uint32_t a2[2][2][4];
+#pragma unroll
+            for (int rt = 0; rt < 2; ++rt)
+#pragma unroll
+                for (int kt = 0; kt < 2; ++kt) c_to_a<false>(h[rt][2 * kt], h[rt][2 * kt + 1], a2[rt][kt]);
+            // every moved coordinate: its 24 outputs through the warp's scratch to its sample's thread
+            float *vme = V + (r * THREADS + threadIdx.x) * VROW;
+            for (int m = 0; m < n_move; ++m) {
+#pragma unroll
+                for (int nt = 0; nt < 3; ++nt) {
+                    const int c0 = m * kPad + nt * 8 + 2 * t;
+                    const float u0 = fw[F_B1 + c0], u1 = fw[F_B1 + c0 + 1];
+                    float pc[2][4] = {{u0, u1, u0, u1}, {u0, u1, u0, u1}};
+#pragma unroll
+                    for (int kt = 0; kt < 2; ++kt) {
+                        uint32_t b0, b1;
+                        bfrag(bw + OFF_W1 + m * kPad * LD32, LD32, kt, nt, g, t, b0, b1);
+#pragma unroll
+                        for (int rt = 0; rt < 2; ++rt) mma(pc[rt], a2[rt][kt], b0, b1);
+                    }
+#pragma unroll
+                    for (int rt = 0; rt < 2; ++rt) {
+                        float *p0 = P + (16 * rt + g) * PROW + nt * 8 + 2 * t, *p1 = p0 + 8 * PROW;
+                        p0[0] = pc[rt][0];
+                        p0[1] = pc[rt][1];
+                        p1[0] = pc[rt][2];
+                        p1[1] = pc[rt][3];
+                    }
+                }
+                __syncwarp();
+                float p[kPad];
+#pragma unroll
+                for (int q = 0; q < kPad; ++q) p[q] = P[lane * PROW + q];
+                __syncwarp();                                   // the scratch is free for the next coordinate
+                float y, logd;
+                const float u = fminf(fmaxf(vme[move0 + m], 0.0f), 1.0f);
+                if (INV)
+                    rq_spline_inverse(p, u, y, logd);
+                else
+                    rq_spline(p, u, y, logd);
+                vme[move0 + m] = y;
+                logq[r] -= logd;
+            }
+            __syncwarp();                                       // coordinates written before the next layer reads them
+        }
+    }
+    for (int r = 0; r < ROUNDS; ++r) {
+        const int row = r * THREADS + threadIdx.x;
+        const int64_t i = base + row;
+        if (i >= a.n) continue;
+        const float *v = V + row * VROW;
+        for (int j = 0; j < D; ++j) a.x[(int64_t)j * a.ldx + i] = v[j];
+        a.logq[i] = a.inv_q ? expf(-logq[r]) : logq[r];
+    }
+}
+
 // ---- gradient of the forward-KL loss (App. A) ------------------------------
 // loss = -sum_i w_i log q(x_i) / sum_i w_i over given points x_i and weights
 // w_i, and its gradient in every parameter by reverse mode through the
@@ -188,19 +472,68 @@ __global__ void __launch_bounds__(128) nsf_kernel(const NsfArgs a) {
 // keeps each layer's input in local memory; the backward sweep then walks the
 // layers in the flow's order (0 .. L-1), recomputing each conditioner from
 // the kept input (layer_backward).  A parameter's gradient is summed over the
-// warp's samples by shuffles and added to global memory by lane 0.
+// warp's samples through shared memory and added to global memory once per
+// warp (WarpAtomicAcc).
 
 constexpr int kGradMaxLayers = 16;
 constexpr int kNsfMaxTrainSteps = 4096;      // losses kept per fd_nsf_train call
 
+// The warp's accumulator: a rank-one update G[r][q] += a[r] b[q] summed over
+// the warp's 32 samples is a small matrix product, computed by writing the
+// lanes' a and b rows to the warp's shared-memory scratch (rows of 33
+// floats: conflict-free) and letting lane r sum row r of G over the samples
+// (b read as broadcasts); one atomic per entry and warp.  About 30
+// instructions per 23 entries against 11 per entry for a per-entry warp
+// reduction.
+constexpr int kAccRow = 33;
 struct WarpAtomicAcc {
     float *g;                                 // the layer's slice of the gradient
-    __device__ __forceinline__ void operator()(int64_t k, float v) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(g + k, v);
-    }
+    float *s;                                 // this warp's scratch: [32][kAccRow] a rows, then b rows
 };
+
+template <int NA, int NB>
+__device__ __forceinline__ void acc_outer(WarpAtomicAcc &acc, int64_t off, int64_t stride, const float (&a)[NA],
+                                          int na, const float (&b)[NB], int nb) {
+    const int lane = threadIdx.x & 31;
+    float *A = acc.s, *B = acc.s + 32 * kAccRow;
+    __syncwarp();                                            // the scratch's previous use is over
+#pragma unroll
+    for (int r = 0; r < NA; ++r)
+        if (r < na) A[lane * kAccRow + r] = a[r];
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+        if (q < nb) B[lane * kAccRow + q] = b[q];
+    __syncwarp();
+    if (lane < na) {
+        float sum[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) sum[q] = 0.0f;
+        for (int smp = 0; smp < 32; ++smp) {
+            const float ar = A[smp * kAccRow + lane];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) sum[q] = fmaf(ar, B[smp * kAccRow + q], sum[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+            if (q < nb && sum[q] != 0.0f) atomicAdd(acc.g + off + lane * stride + q, sum[q]);
+    }
+}
+
+template <int NB>
+__device__ __forceinline__ void acc_vec(WarpAtomicAcc &acc, int64_t off, const float (&b)[NB], int nb) {
+    const int lane = threadIdx.x & 31;
+    float *B = acc.s + 32 * kAccRow;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+        if (q < nb) B[lane * kAccRow + q] = b[q];
+    __syncwarp();
+    if (lane < nb) {
+        float sum = 0.0f;
+        for (int smp = 0; smp < 32; ++smp) sum += B[smp * kAccRow + lane];
+        if (sum != 0.0f) atomicAdd(acc.g + off + lane, sum);
+    }
+}
 
 struct NsfGradArgs {
     const float *params, *x, *w;   // x [dim][n], w [n]
@@ -208,6 +541,7 @@ struct NsfGradArgs {
     float *grad;                   // [n_params], zeroed
     double *loss;                  // zeroed
     int64_t n;
+    int64_t max_layer;             // floats of the largest staged layer (the scratch follows)
     int dim, n_layers;
 };
 
@@ -237,6 +571,8 @@ __device__ void stage_layer(const float *lp, int n_keep, int n_move, float *wsm)
 
 __global__ void __launch_bounds__(128) nsf_grad_kernel(const NsfGradArgs a) {
     extern __shared__ __align__(16) float wsm[];
+    // the warps' accumulation scratch after the layer's weights (max_layer floats)
+    float *acc_scratch = wsm + a.max_layer + (threadIdx.x >> 5) * 2 * 32 * kAccRow;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < a.n;
     const int D = a.dim, half = D / 2;
@@ -269,7 +605,7 @@ __global__ void __launch_bounds__(128) nsf_grad_kernel(const NsfGradArgs a) {
         float xin[kMaxDim];
 #pragma unroll
         for (int j = 0; j < kMaxDim; ++j) xin[j] = vin[layer][j];
-        WarpAtomicAcc acc{a.grad + off};
+        WarpAtomicAcc acc{a.grad + off, acc_scratch};
         layer_backward(layer_at(wsm, layer, D), xin, vbar, c, acc);
     }
 }
@@ -285,6 +621,7 @@ struct fd_nsf {
     float *d_grad = nullptr, *d_m = nullptr, *d_v = nullptr;
     double *d_loss = nullptr;
     int64_t step = 0;
+    int tensor_path = 1;           // sampling / density: 1 conditioner on BF16 tensor cores, 0 FP32 CUDA cores
 };
 
 namespace {
@@ -323,6 +660,20 @@ fd_status nsf_launch(const fd_nsf *f, bool inverse, const float *z, int64_t ldz,
     a.seed_hi = (uint32_t)(seed >> 32);
     a.iter = (uint32_t)iter;
     a.inst = (uint32_t)inst;
+    if (f->tensor_path == 1) {
+        const unsigned grid = (unsigned)((n + nsf_tc::BLOCK - 1) / nsf_tc::BLOCK);
+        if (inverse) {
+            FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)nsf_tc::SMEM));
+            nsf_tc_kernel<true><<<grid, nsf_tc::THREADS, nsf_tc::SMEM, stream>>>(a);
+        } else {
+            FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)nsf_tc::SMEM));
+            nsf_tc_kernel<false><<<grid, nsf_tc::THREADS, nsf_tc::SMEM, stream>>>(a);
+        }
+        FD_CHECK_CUDA(cudaGetLastError());
+        return FD_OK;
+    }
     const size_t smem = (size_t)f->max_layer * sizeof(float);
     if (inverse) {
         FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -386,6 +737,13 @@ extern "C" fd_status fd_nsf_set_params(fd_nsf *f, const float *params, int64_t n
     return FD_OK;
 }
 
+extern "C" fd_status fd_nsf_set_tensor_path(fd_nsf *f, int32_t path) {
+    FD_REQUIRE(f, "null flow");
+    FD_REQUIRE(path == 0 || path == 1, "path must be 0 (FP32 CUDA cores) or 1 (BF16 tensor cores)");
+    f->tensor_path = path;
+    return FD_OK;
+}
+
 extern "C" fd_status fd_nsf_forward(const fd_nsf *f, const float *z, int64_t n, float *x, float *logq,
                                     void *stream) {
     FD_REQUIRE(z, "z is required");
@@ -430,9 +788,10 @@ fd_status kl_grad_impl(const fd_nsf *f, const float *x, const float *w, int64_t 
     a.grad = grad;
     a.loss = loss;
     a.n = n;
+    a.max_layer = (f->max_layer + 3) / 4 * 4;
     a.dim = f->dim;
     a.n_layers = f->n_layers;
-    const size_t smem = (size_t)f->max_layer * sizeof(float);
+    const size_t smem = ((size_t)a.max_layer + 4 * 2 * 32 * kAccRow) * sizeof(float);
     FD_CHECK_CUDA(cudaFuncSetAttribute(nsf_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     nsf_grad_kernel<<<(unsigned)((n + 127) / 128), 128, smem, st>>>(a);
     FD_CHECK_CUDA(cudaGetLastError());

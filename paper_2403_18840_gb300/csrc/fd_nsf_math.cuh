@@ -329,13 +329,29 @@ __host__ __device__ __forceinline__ float layer_inverse(const Layer &L, float (&
     return sum;
 }
 
+// Gradient accumulation of layer_backward: the rank-one updates
+// G[r][q] += a[r] b[q] (r < na, q < nb) at offset off + r stride + q and the
+// vector updates G[q] += b[q] at off + q, by default through the accumulator's
+// scalar call acc(k, value); an accumulator type may overload these two (the
+// device one sums a warp's 32 samples through shared memory).
+template <class Acc, int NA, int NB>
+__host__ __device__ __forceinline__ void acc_outer(Acc &acc, int64_t off, int64_t stride, const float (&a)[NA],
+                                                   int na, const float (&b)[NB], int nb) {
+    for (int r = 0; r < na; ++r)
+        for (int q = 0; q < nb; ++q) acc(off + r * stride + q, a[r] * b[q]);
+}
+template <class Acc, int NB>
+__host__ __device__ __forceinline__ void acc_vec(Acc &acc, int64_t off, const float (&b)[NB], int nb) {
+    for (int q = 0; q < nb; ++q) acc(off + q, b[q]);
+}
+
 // Reverse mode through one layer's inverse on one sample.  xin is the
 // layer's input (the point on the x side), vbar on entry the loss's adjoint
 // of the layer's output and on exit that of its input; c = d loss / d log q
 // (the sample's -w / sum w, 0 for a padding thread).  Every parameter
-// gradient goes to acc(k, value), k the offset within the layer's slice of
-// the parameter vector.  On the device all lanes of a warp call acc with the
-// same k sequence.
+// gradient goes to the accumulator (acc_outer / acc_vec above), offsets
+// within the layer's slice of the parameter vector.  On the device all lanes
+// of a warp make the same sequence of accumulator calls.
 #pragma nv_exec_check_disable
 template <class Acc>
 __host__ __device__ __forceinline__ void layer_backward(const Layer &L, const float (&xin)[kMaxDim],
@@ -355,13 +371,12 @@ __host__ __device__ __forceinline__ void layer_backward(const Layer &L, const fl
         float pbar[kPad];
         for (int q = 0; q < kPad; ++q) pbar[q] = c == 0.0f ? 0.0f : -c * lpp[q] - ubar * inv_g * gp[q];
         put(vbar, L.move0 + m, ubar * inv_g);
-        for (int q = 0; q < kParamsPerDim; ++q) acc(ob1 + m * kParamsPerDim + q, pbar[q]);
+        acc_vec(acc, ob1 + m * kParamsPerDim, pbar, kParamsPerDim);
+        acc_outer(acc, oW1 + m * kParamsPerDim, (int64_t)L.n_move * kParamsPerDim, h2, kHidden, pbar,
+                  kParamsPerDim);
         for (int r = 0; r < kHidden; ++r) {
             float s = 0.0f;
-            for (int q = 0; q < kParamsPerDim; ++q) {
-                acc(oW1 + (int64_t)r * L.n_move * kParamsPerDim + m * kParamsPerDim + q, h2[r] * pbar[q]);
-                s = fmaf(pbar[q], L.W1[(r * L.n_move + m) * kPad + q], s);
-            }
+            for (int q = 0; q < kParamsPerDim; ++q) s = fmaf(pbar[q], L.W1[(r * L.n_move + m) * kPad + q], s);
             hbar[r] += s;
         }
     }
@@ -372,39 +387,36 @@ __host__ __device__ __forceinline__ void layer_backward(const Layer &L, const fl
         const float *Wa = L.W0 + oWa, *Wb = L.W0 + oWb;
         const float(&hin)[kHidden] = bk == 0 ? h0 : h1;
         const float(&tt)[kHidden] = bk == 0 ? t0 : t1;
-        float tbar[kHidden], hadd[kHidden];
-        for (int q = 0; q < kHidden; ++q) acc(obb + q, hbar[q]);
+        float tbar[kHidden], hadd[kHidden], relu_t[kHidden], relu_h[kHidden];
+        for (int q = 0; q < kHidden; ++q) {
+            relu_t[q] = fmaxf(tt[q], 0.0f);
+            relu_h[q] = fmaxf(hin[q], 0.0f);
+        }
+        acc_vec(acc, obb, hbar, kHidden);
+        acc_outer(acc, oWb, kHidden, relu_t, kHidden, hbar, kHidden);
         for (int r = 0; r < kHidden; ++r) {
-            const float b = fmaxf(tt[r], 0.0f);
             float s = 0.0f;
-            for (int q = 0; q < kHidden; ++q) {
-                acc(oWb + r * kHidden + q, b * hbar[q]);
-                s = fmaf(hbar[q], Wb[r * kHidden + q], s);
-            }
+            for (int q = 0; q < kHidden; ++q) s = fmaf(hbar[q], Wb[r * kHidden + q], s);
             tbar[r] = tt[r] > 0.0f ? s : 0.0f;
         }
-        for (int q = 0; q < kHidden; ++q) acc(oba + q, tbar[q]);
+        acc_vec(acc, oba, tbar, kHidden);
+        acc_outer(acc, oWa, kHidden, relu_h, kHidden, tbar, kHidden);
         for (int r = 0; r < kHidden; ++r) {
-            const float a = fmaxf(hin[r], 0.0f);
             float s = 0.0f;
-            for (int q = 0; q < kHidden; ++q) {
-                acc(oWa + r * kHidden + q, a * tbar[q]);
-                s = fmaf(tbar[q], Wa[r * kHidden + q], s);
-            }
+            for (int q = 0; q < kHidden; ++q) s = fmaf(tbar[q], Wa[r * kHidden + q], s);
             hadd[r] = hin[r] > 0.0f ? s : 0.0f;
         }
         for (int q = 0; q < kHidden; ++q) hbar[q] += hadd[q];
     }
     // the input map: kept coordinates pass through and feed h0
     const int64_t ob0 = (int64_t)L.n_keep * kHidden;
-    for (int q = 0; q < kHidden; ++q) acc(ob0 + q, hbar[q]);
+    float xk[kMaxDim / 2];
+    for (int r = 0; r < kMaxDim / 2; ++r) xk[r] = r < L.n_keep ? sel(xin, L.keep0 + r) : 0.0f;
+    acc_vec(acc, ob0, hbar, kHidden);
+    acc_outer(acc, 0, kHidden, xk, L.n_keep, hbar, kHidden);
     for (int r = 0; r < L.n_keep; ++r) {
-        const float xv = sel(xin, L.keep0 + r);
         float s = 0.0f;
-        for (int q = 0; q < kHidden; ++q) {
-            acc((int64_t)r * kHidden + q, xv * hbar[q]);
-            s = fmaf(hbar[q], L.W0[r * kHidden + q], s);
-        }
+        for (int q = 0; q < kHidden; ++q) s = fmaf(hbar[q], L.W0[r * kHidden + q], s);
         put(vbar, L.keep0 + r, sel(vbar, L.keep0 + r) + s);
     }
 }

@@ -1,7 +1,11 @@
 """GPU parity of the spline flow's sampling and density passes (App. A) with
 the FP64 oracle on the same parameters: explicit points, the Philox sample
 stream, the density at given points (inverse pass), a sample -> density
-round trip, the identity flow, and ragged sample counts."""
+round trip, the identity flow, and ragged sample counts.  Both conditioner
+paths: FP32 CUDA cores against the FP64 oracle, BF16 tensor cores (the
+default) against the oracle under the same BF16 contract."""
+import contextlib
+
 import numpy as np
 import pytest
 
@@ -36,76 +40,117 @@ def _as_fp32(flow):
     return flow
 
 
-def _compare(x_gpu, lq_gpu, x_ref, lq_ref, label, inverse=False):
+def _compare(x_gpu, lq_gpu, x_ref, lq_ref, label, inverse=False, bf16=False):
     # Forward: FP32 through 8 layers, a coordinate carries ~1e-6 absolute error
     # and log q (a sum of 8 x D/2 log-derivatives) ~1e-4 in the worst samples.
     # Inverse: each layer divides the error of its input by the spline's
     # derivative there (down to ~0.1 for these parameters), so the errors are
     # ~10x larger: ~2e-5 / 2e-4 for z, 3e-4 / 2e-3 for log q (99 % / max).
+    # BF16 conditioner (against the oracle under the same contract, or its
+    # own round trip): a value that the GPU sums in FP32 and the oracle in
+    # FP64 can round to the neighbouring BF16 value when it lies within its
+    # ~1e-7 difference of a rounding boundary -- about 5e-5 of the ~1400
+    # roundings of a sample at D = 19 and 8 layers, so ~7 % of the samples
+    # carry one such flip (2^-8 in one activation, through the softmax knots
+    # up to ~1e-3 in a coordinate and ~0.1 in log q, 10x for the inverse).
+    # So 90 % of the samples must meet the FP32 path's 99 % bounds, and every
+    # sample the bound of a flip.
     dx = np.abs(x_gpu - x_ref).max(axis=0)
     dl = np.abs(lq_gpu - lq_ref)
-    print("%s: max |dx| %.3e (99%% %.3e), max |d log q| %.3e (99%% %.3e)" %
-          (label, dx.max(), np.quantile(dx, 0.99), dl.max(), np.quantile(dl, 0.99)))
+    print("%s: max |dx| %.3e (99%% %.3e, 90%% %.3e), max |d log q| %.3e (99%% %.3e, 90%% %.3e)" %
+          (label, dx.max(), np.quantile(dx, 0.99), np.quantile(dx, 0.9), dl.max(), np.quantile(dl, 0.99),
+           np.quantile(dl, 0.9)))
     bx, bl = ((5e-5, 5e-4), (1e-3, 1e-2)) if inverse else ((5e-6, 5e-5), (1e-4, 1e-3))
-    assert np.quantile(dx, 0.99) < bx[0] and dx.max() < bx[1], label
-    assert np.quantile(dl, 0.99) < bl[0] and dl.max() < bl[1], label
+    if bf16:
+        flip = (1e-1, 1.0) if inverse else (1e-2, 0.2)
+        assert np.quantile(dx, 0.9) < bx[0] and dx.max() < flip[0], label
+        assert np.quantile(dl, 0.9) < bl[0] and dl.max() < flip[1], label
+    else:
+        assert np.quantile(dx, 0.99) < bx[0] and dx.max() < bx[1], label
+        assert np.quantile(dl, 0.99) < bl[0] and dl.max() < bl[1], label
 
 
-@pytest.mark.parametrize("dim", [19, 5])
-def test_forward_matches_oracle(api, dim):
-    flow = _as_fp32(osf.SplineFlow(dim, 8, seed=11, scale=0.8))
-    g = api.SplineFlow(dim, 8)
+@contextlib.contextmanager
+def _oracle_precision(path):
+    osf.set_precision("bf16" if path == 1 else "f64")
+    try:
+        yield
+    finally:
+        osf.set_precision("f64")
+
+
+def _gpu_flow(api, dim, n_layers, flow, path):
+    g = api.SplineFlow(dim, n_layers)
     g.set_params(_flatten(flow))
+    g.set_tensor_path(path)
+    return g
+
+
+PATHS = [0, 1]
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("dim", [19, 5])
+def test_forward_matches_oracle(api, dim, path):
+    flow = _as_fp32(osf.SplineFlow(dim, 8, seed=11, scale=0.8))
+    g = _gpu_flow(api, dim, 8, flow, path)
     n = 3 * 1000 + 77                                        # several blocks and a ragged tail
     z = workloads.uniform_points(12, dim, n)
     x, lq = g.forward(torch.tensor(z, dtype=torch.float32, device="cuda").contiguous())
-    x_ref, lq_ref = flow.forward(z.T)
+    with _oracle_precision(path):
+        x_ref, lq_ref = flow.forward(z.T)
     _compare(x.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), x_ref.T, lq_ref,
-             "forward dim %d" % dim)
+             "forward dim %d path %d" % (dim, path), bf16=path == 1)
 
 
-def test_sample_stream_matches_oracle(api):
+@pytest.mark.parametrize("path", PATHS)
+def test_sample_stream_matches_oracle(api, path):
     dim, n = 19, 2049
     flow = _as_fp32(osf.SplineFlow(dim, 8, seed=13, scale=0.8))
-    g = api.SplineFlow(dim, 8)
-    g.set_params(_flatten(flow))
+    g = _gpu_flow(api, dim, 8, flow, path)
     x, lq = g.sample(21, 4, 3, n)
     z = ophilox.uniforms(21, 4, 3, np.arange(n), dim)
-    x_ref, lq_ref = flow.forward(z.T)
-    _compare(x.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), x_ref.T, lq_ref, "sample")
+    with _oracle_precision(path):
+        x_ref, lq_ref = flow.forward(z.T)
+    _compare(x.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), x_ref.T, lq_ref,
+             "sample path %d" % path, bf16=path == 1)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("dim", [19, 6])
-def test_log_density_matches_oracle(api, dim):
+def test_log_density_matches_oracle(api, dim, path):
     flow = _as_fp32(osf.SplineFlow(dim, 8, seed=15, scale=0.8))
-    g = api.SplineFlow(dim, 8)
-    g.set_params(_flatten(flow))
+    g = _gpu_flow(api, dim, 8, flow, path)
     n = 2 * 1000 + 33
     z0 = workloads.uniform_points(16, dim, n)
-    x_ref, _ = flow.forward(z0.T)                            # points inside the flow's image
-    z, lq = g.log_density(torch.tensor(x_ref.T, dtype=torch.float32, device="cuda").contiguous())
-    lq_ref, z_ref = flow.log_density(x_ref.astype(np.float32).astype(np.float64))
+    with _oracle_precision(path):
+        x_ref, _ = flow.forward(z0.T)                        # points inside the flow's image
+        z, lq = g.log_density(torch.tensor(x_ref.T, dtype=torch.float32, device="cuda").contiguous())
+        lq_ref, z_ref = flow.log_density(x_ref.astype(np.float32).astype(np.float64))
     _compare(z.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64), z_ref.T, lq_ref,
-             "log density dim %d" % dim, inverse=True)
+             "log density dim %d path %d" % (dim, path), inverse=True, bf16=path == 1)
 
 
-def test_sample_then_density_round_trip(api):
+@pytest.mark.parametrize("path", PATHS)
+def test_sample_then_density_round_trip(api, path):
+    # the kept half a layer conditions on is the same in both directions up to
+    # FP32 rounding, so the round trip holds to the splines' FP32 arithmetic
+    # on the FP32 path and, but for BF16 rounding flips, on the tensor path
     dim, n = 19, 4096
     flow = _as_fp32(osf.SplineFlow(dim, 8, seed=17, scale=0.8))
-    g = api.SplineFlow(dim, 8)
-    g.set_params(_flatten(flow))
+    g = _gpu_flow(api, dim, 8, flow, path)
     x, lq = g.sample(5, 0, 1, n)
     z, lq2 = g.log_density(x)
     z0 = ophilox.uniforms(5, 0, 1, np.arange(n), dim)
     _compare(z.cpu().numpy().astype(np.float64), lq2.cpu().numpy().astype(np.float64), z0,
-             lq.cpu().numpy().astype(np.float64), "round trip", inverse=True)
+             lq.cpu().numpy().astype(np.float64), "round trip path %d" % path, inverse=True, bf16=path == 1)
 
 
-def test_identity_flow(api):
+@pytest.mark.parametrize("path", PATHS)
+def test_identity_flow(api, path):
     dim, n = 7, 1000
     flow = osf.SplineFlow(dim, 4, seed=1, zero=True)
-    g = api.SplineFlow(dim, 4)
-    g.set_params(_flatten(flow))
+    g = _gpu_flow(api, dim, 4, flow, path)
     z = workloads.uniform_points(3, dim, n)
     x, lq = g.forward(torch.tensor(z, dtype=torch.float32, device="cuda").contiguous())
     assert np.max(np.abs(x.cpu().numpy() - z.astype(np.float32))) < 1e-6

@@ -186,3 +186,46 @@ def test_closed_form_spline_partials():
     x = rng.uniform(0.02, 0.98, (12, 3))
     w = rng.random(12)
     assert np.allclose(flow.kl_grad(x, w, analytic=True), flow.kl_grad(x, w), rtol=1e-5, atol=1e-9)
+
+
+def test_bf16_contract_rounds_only_the_conditioner_inputs():
+    # Under the BF16 contract a layer's spline parameters come from BF16
+    # weights and BF16 GEMM inputs: with weights, biases and inputs that are
+    # exact in BF16 and a conditioner whose hidden values stay BF16-exact (one
+    # nonzero W0 entry of 1, identity-like blocks switched off), both modes
+    # agree exactly; with general parameters they differ by ~2^-8 relative in
+    # the parameters but the flow stays invertible: forward then inverse under
+    # the contract returns the input, as the kept half is the same both ways.
+    rng = np.random.default_rng(5)
+    flow = sf.SplineFlow(6, 4, seed=3, scale=0.8)
+    z = rng.uniform(0.05, 0.95, (200, 6))
+    try:
+        sf.set_precision("bf16")
+        x, lq = flow.forward(z)
+        lq2, z2 = flow.log_density(x)
+    finally:
+        sf.set_precision("f64")
+    assert np.abs(z2 - z).max() < 1e-9 and np.abs(lq2 - lq).max() < 1e-9
+    x64, lq64 = flow.forward(z)
+    d = np.abs(x - x64).max()
+    assert 1e-6 < d < 5e-2, d                       # the contract changes the flow a little, not a lot
+    # exact agreement when nothing needs rounding
+    net = flow.layers[0][2]
+    net.w0[:] = 0.0
+    net.w0[0, 0] = 1.0
+    net.b0[:] = 0.0
+    for (wa, ba), (wb, bb) in net.blocks:
+        wa[:] = 0.0
+        ba[:] = 0.0
+        wb[:] = 0.0
+        bb[:] = 0.0
+    net.w1[:] = sf.bf16(net.w1)
+    net.b1[:] = 0.0
+    u = sf.bf16(rng.uniform(0.0, 1.0, (50, net.w0.shape[0])))
+    ref = net(u)
+    try:
+        sf.set_precision("bf16")
+        got = net(u)
+    finally:
+        sf.set_precision("f64")
+    assert np.array_equal(got, ref)
