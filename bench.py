@@ -9,7 +9,7 @@ kernel), then the fixed-order reduction and the FP64 grid update (two
 kernels).  Inputs are generated on the device; L2 is flushed (a 256 MiB
 write) between timed steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-flow]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-flow] [--no-batched]
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host
 cores on a bounded sample of the same workload.  Under torchrun (N > 1) every
@@ -47,6 +47,7 @@ def _parse():
     ap.add_argument("--flow-steps", type=int, default=workloads.FLOW_ORDER5["train_steps"])
     ap.add_argument("--flow-batch", type=int, default=workloads.FLOW_ORDER5["batch"])
     ap.add_argument("--no-flow", action="store_true", help="skip the flow vs VEGAS section (profiling runs)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 240-instance batched configuration")
     ap.add_argument("--flow-tensor-path", type=int, default=2, choices=[0, 1, 2],
                     help="flow sampling / density on mma.sync (0), tcgen05 with tile pairs (1) or "
                          "tcgen05 warp-specialised (2)")
@@ -423,6 +424,12 @@ def run_ours(args, rank, world, dist):
     d2h = int(e_host.nbytes + stats_host.numel() * 8)
 
     eff = None if args.no_flow else flow_vs_vegas(args, api, params, order, seed)
+    batched = None
+    if not args.no_batched:
+        # the batched configuration of many uneven instances (orders 1-5 x r_s x
+        # 16 k, 240 instances, CUDA-graph iterations), outside the timed region
+        from paper_2403_18840_gb300 import batched_run
+        batched = batched_run.run(iters=3, warmup=1, n_per_inst=1 << 22, seed=seed)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     mhz_max = _peaks().get("sm_max_mhz", 2070.0)
@@ -457,6 +464,7 @@ def run_ours(args, rank, world, dist):
                      "kernel_ms": 1e3 * t_kern},
         "e2e": {"value": n / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "eff_samples_per_s": eff,
+        "batched_240": batched,
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "wall_s": t_wall,
