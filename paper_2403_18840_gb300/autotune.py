@@ -35,7 +35,8 @@ JIT_VARIANTS = [dict(threads=256, min_blocks=1, spt=4, unit_cap=12000, sync_ever
 # and 4: 3.2e8 and 2.7e8 against 4.0e8 samples/s) and 3 samples per thread,
 # which leaves room for the tile histogram (3.3e8 - 3.4e8); two CTAs of 256
 # threads per SM (128 registers, 2 samples per thread: 2.6e8), three of 128
-# threads (3.2e8 - 3.5e8) and units of cost 16000 (3.4e8).
+# threads (3.2e8 - 3.5e8), units of cost 16000 (3.4e8) and samples in packed
+# pairs (1.5e8 - 2.0e8 at costs 1500 - 6000: 4 KB of local memory at every cost).
 JIT_KEYS = ("threads", "min_blocks", "root_units", "sync_every", "leaf_calls", "spt", "unit_cap", "pair", "sv_smem",
             "cross_roots", "leaf_cache", "lc_global")
 

@@ -231,3 +231,34 @@ def test_default_path_many_groups_per_cta(api, dim, layers):
     u = ophilox.uniforms(9, 4, 1, np.arange(nf, n), dim)
     assert np.array_equal(xdg[:, nf:], u.astype(np.float32))
     assert np.abs(xdg[:, :nf] - xg[:, :nf]).max() == 0.0
+
+
+def test_default_path_at_the_bench_size(api):
+    # the launch the flow-vs-VEGAS comparison times: 2^24 samples of the
+    # defensive mixture (10 % uniform) on the default path; sampled rows of
+    # both shares against the oracle (forward for the flow share, the inverse
+    # density for the uniform share), the last rows included
+    F, blob = _flow(api)
+    n = 1 << 24
+    x, w, a = F.sample_defensive(13, 60000, 3, n, 0.1)
+    torch.cuda.synchronize()
+    nf = n - int(round(a * n))
+    rng = np.random.default_rng(8)
+    rows_f = np.unique(np.concatenate([np.arange(32), rng.integers(0, nf, 1200), np.arange(nf - 32, nf)]))
+    rows_u = np.unique(np.concatenate([np.arange(nf, nf + 32), rng.integers(nf, n, 400), np.arange(n - 32, n)]))
+    xs = x[:, torch.as_tensor(np.concatenate([rows_f, rows_u]), device="cuda")].cpu().numpy().astype(np.float64)
+    ws = w[torch.as_tensor(np.concatenate([rows_f, rows_u]), device="cuda")].cpu().numpy().astype(np.float64)
+    uf = ophilox.uniforms(13, 60000, 3, rows_f, D)
+    xr, lq_f = oflow.forward(blob, uf, D, K, H)
+    uu = ophilox.uniforms(13, 60000, 3, rows_u, D)
+    _, lq_u = oflow.inverse(blob, uu, D, K, H)
+    kf = len(rows_f)
+    assert np.array_equal(xs[:, kf:], uu)                    # the uniform share is the stream itself
+    dx = np.abs(xs[:, :kf] - xr)
+    lq = np.concatenate([lq_f, lq_u])
+    wr = 1.0 / ((1.0 - a) * np.exp(lq) + a)
+    rel = np.abs(ws / wr - 1.0)
+    print("bench size: max |dx| %.3e (99%% %.3e), max rel w %.3e (99%% %.3e)" %
+          (dx.max(), np.quantile(dx, 0.99), rel.max(), np.quantile(rel, 0.99)))
+    assert dx.max() < 2e-3 and np.quantile(dx, 0.99) < 2e-4
+    assert rel.max() < 2e-2 and np.quantile(rel, 0.99) < 2e-3
