@@ -288,6 +288,26 @@ def affine_flow_sampling(api, F, default_path, n=1 << 24, reps=5):
         out[names[path]] = {"ms": ms, "samples_per_s": n / ms * 1e3, "tflops": tf,
                             "frac": tf / peak if peak else None}
     F.set_tensor_path(default_path)
+    # the training gradient (forward-KL loss and its gradient on given points:
+    # the inverse pass, then reverse mode layer by layer, mma.sync tiles): its
+    # GEMMs are the forward's three per layer plus two per GEMM backward
+    # (input adjoints and weight gradients), 3x the padded forward flops
+    m = 1 << 20
+    x, _ = F.sample(5, 0, 0, m)
+    wts = torch.ones(m, dtype=torch.float32, device="cuda")
+    F.grad(x, wts)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for r in range(reps):
+        F.grad(x, wts)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / reps
+    tf = 3 * flops * m / ms * 1e-9
+    out["training_gradient"] = {"samples": m, "ms": ms, "samples_per_s": m / ms * 1e3, "tflops": tf,
+                                "frac": tf / peak if peak else None,
+                                "padded_flops_per_sample": 3 * flops}
     return out
 
 
