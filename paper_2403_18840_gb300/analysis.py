@@ -17,7 +17,10 @@ Readings where the paper gives the procedure in words only:
   largest three-order variation among it and its neighbours in the scan;
 * temperature: y(T) = y(0) (1 + alpha T/T_F) fitted by weighted least
   squares in T/T_F; y(0), alpha, their errors and chi^2 per degree of
-  freedom are returned.
+  freedom are returned;
+* iterations: independent estimates of one integral (VEGAS iterations, each
+  on its own grid) are combined with inverse-variance weights, with chi^2
+  per degree of freedom as the consistency check (Lepage 1978).
 """
 import math
 
@@ -126,3 +129,26 @@ def extrapolate_linear_T(t, y, dy):
     dalpha = math.sqrt(float(ga @ cov @ ga))
     return {"y0": float(c0), "dy0": math.sqrt(cov[0, 0]), "alpha": float(alpha), "dalpha": dalpha,
             "slope": float(c1), "cov": cov, "chi2_dof": chi2}
+
+
+def combine_iterations(means, variances):
+    """Inverse-variance weighted combination of K independent estimates.
+
+    means, variances: arrays [K, ...] (iterations first; the variance of each
+    estimate, > 0).  Returns (mean, variance, chi2_per_dof) with
+    mean = sum(I_k / s_k^2) / sum(1 / s_k^2), variance = 1 / sum(1 / s_k^2) and
+    chi2_per_dof = sum((I_k - mean)^2 / s_k^2) / (K - 1) (NaN for K = 1), each
+    of the shape of one estimate.
+    """
+    m = np.asarray(means, dtype=np.float64)
+    v = np.asarray(variances, dtype=np.float64)
+    if m.shape != v.shape or m.shape[0] < 1:
+        raise ValueError("means and variances need the same shape, iterations first")
+    if not np.all(v > 0.0):
+        raise ValueError("every variance must be positive")
+    w = 1.0 / v
+    wsum = w.sum(axis=0)
+    mean = (w * m).sum(axis=0) / wsum
+    K = m.shape[0]
+    chi2 = ((m - mean) ** 2 * w).sum(axis=0) / (K - 1) if K > 1 else np.full(mean.shape, np.nan)
+    return mean, 1.0 / wsum, chi2

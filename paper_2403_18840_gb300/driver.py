@@ -29,7 +29,10 @@ def _events():
 
 
 def adapt_vegas(G, params, vegas, n, iters, seed, alpha=0.5, first_iter=0):
-    """`iters` VEGAS iterations of n samples; returns the per-iteration stats [iters][R][2][2]."""
+    """`iters` VEGAS iterations of n samples; returns the per-iteration stats
+    [iters][R][2][2] (root, Re/Im, mean/variance of the mean), which
+    `analysis.combine_iterations(stats[..., 0], stats[..., 1])` combines with
+    inverse-variance weights."""
     plan = api.EvalPlan([G], [params], [0], n, maps=[vegas])
     out = []
     for it in range(iters):

@@ -96,3 +96,25 @@ def test_extrapolation_coverage_on_noisy_data():
         pulls.append((r["y0"] - 0.95) / r["dy0"])
     pulls = np.array(pulls)
     assert abs(pulls.mean()) < 0.2 and 0.85 < pulls.std() < 1.15
+
+
+def test_combine_iterations():
+    # hand example: weights 1 and 1/4
+    m, v, c = A.combine_iterations([1.0, 2.0], [1.0, 4.0])
+    assert abs(m - 1.2) < 1e-15 and abs(v - 0.8) < 1e-15 and abs(c - 0.2) < 1e-15
+    # equal variances: the plain mean, s^2 / K, and chi^2 = sample variance / s^2
+    x = np.array([0.3, -0.1, 0.7, 0.2])
+    m, v, c = A.combine_iterations(x, np.full(4, 0.5))
+    assert abs(m - x.mean()) < 1e-15 and abs(v - 0.5 / 4) < 1e-15
+    assert abs(c - x.var(ddof=1) / 0.5) < 1e-14
+    # independent draws with different errors around one value: unbiased,
+    # unit pull scale and chi^2 per degree of freedom near 1
+    rng = np.random.default_rng(4)
+    sig = rng.uniform(0.5, 3.0, (200, 1000))
+    draws = 2.0 + sig * rng.standard_normal(sig.shape)
+    m, v, c = A.combine_iterations(draws, sig ** 2)
+    pull = (m - 2.0) / np.sqrt(v)
+    assert abs(pull.mean()) < 0.15 and abs(pull.std() - 1.0) < 0.08
+    assert abs(c.mean() - 1.0) < 0.02
+    with pytest.raises(ValueError):
+        A.combine_iterations([1.0, 2.0], [1.0, 0.0])
