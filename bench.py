@@ -243,6 +243,7 @@ def flow_vs_vegas(args, api, params, order, seed):
            "flow": cmp["flow"], "flow_over_vegas": cmp["flow_over_vegas"],
            "flow_over_vegas_median": cmp["flow_over_vegas_median"], "ci95": cmp["ci95"],
            "per_sample_variance_gain": cmp["vegas"]["var_per_sample"] / cmp["flow"]["var_per_sample"],
+           "kish_ess_fraction": cmp["kish_ess_fraction"],
            "means_agree_sigma": cmp["means_agree_sigma"], "compare": "64 batches x %d samples per sampler" %
            FW["n_compare"], "proposal": "flow on the VEGAS grid's input coordinates, 10 % defensive uniform share",
            "flow_train_steps": max(1, args.flow_steps), "flow_batch": args.flow_batch,

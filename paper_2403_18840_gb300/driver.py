@@ -192,6 +192,22 @@ def measure_sampler(G, params, n, seed, it, vegas=None, flow=None, reps=3, defen
     return st[0].cpu().numpy(), s.elapsed_time(e) / 1e3 / reps / n
 
 
+def kish_ess(G, params, n, seed, it, root=0, vegas=None, flow=None, defensive=0.0):
+    """Kish effective sample size fraction (sum |wf|)^2 / (n sum (wf)^2) of the
+    real part of `root` over one batch of n weighted samples of a sampler
+    (VEGAS map, or the flow's points with 1/q on top of `vegas`), from the
+    integrand's per-sample values."""
+    plan = api.EvalPlan([G], [params], [0], n, maps=[vegas] if vegas is not None else None, per_sample=True)
+    if flow is None:
+        plan.run(seed, it)
+    else:
+        x, w = _flow_draw(flow, seed, it, 3, n, defensive)
+        plan.run(seed, it, points=x, point_w=w)
+    f = plan.per_sample[0, root, 0].double()
+    a1, a2 = float(f.abs().sum().item()), float((f * f).sum().item())
+    return a1 * a1 / (n * a2) if a2 > 0 else 0.0
+
+
 def bootstrap_ratio(num, den, stat, resamples=4000, seed=0, level=0.95):
     """Percentile bootstrap interval of stat(num) / stat(den), the batches of
     the two samplers resampled independently with replacement."""
@@ -247,6 +263,10 @@ def compare(G, params, vegas, flow, n, seed, root=0, batches=4, on_vegas=True, d
                    "variance_gain_pooled": bootstrap_ratio(vv, fv, np.mean),
                    "batches": batches, "samples_per_batch": n, "resamples": 4000}
     res["defensive_share"] = defensive
+    # Kish effective sample size fraction of one batch of each sampler
+    res["kish_ess_fraction"] = {"vegas": kish_ess(G, params, n, seed, 70000, root, vegas=vegas),
+                                "flow": kish_ess(G, params, n, seed, 70000, root, **flow_kw),
+                                "samples": n}
     return res
 
 
