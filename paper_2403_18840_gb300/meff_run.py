@@ -39,10 +39,12 @@ from . import parquet_graph as _pg
 # thread, their inputs in shared memory, a leaf cache; no tuning per graph).
 # The order-6 parquet graph shares its leaf families across many units, so
 # its kernel computes 2048 floats of them once per sample into a global (L2)
-# scratch: 9.8e6 against 5.9e6 samples/s with the small cache on GB300
-# (4096 floats: 1.1e7, but a 15-minute compile).
+# scratch: 1.0e7 against 5.9e6 samples/s with the small cache on GB300
+# (4096 floats: 1.1e7, but a 15-minute compile).  One sample per thread;
+# the unit cost cap hardly matters there, as its largest root-accumulate
+# slices (up to 18k FMAs over 1 100 leaf families) are units by themselves.
 JIT_VARIANT = dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True, leaf_cache=24)
-JIT_VARIANT_PARQUET = dict(JIT_VARIANT, leaf_cache=2048, lc_global=True)
+JIT_VARIANT_PARQUET = dict(threads=256, min_blocks=1, spt=1, unit_cap=4000, leaf_cache=2048, lc_global=True)
 
 
 def _kf(rs):
