@@ -55,8 +55,7 @@ def _reference(order, roots, x, construction):
 # specialised-kernel variants: the small shared-memory leaf cache of the
 # lower orders and the large global one of the order-6 effective-mass graph
 JIT = {"lc24": dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sv_smem=True, leaf_cache=24),
-       "lc2048_global": dict(threads=256, min_blocks=1, spt=2, unit_cap=12000, sync_every=1, sv_smem=True,
-                             leaf_cache=2048, lc_global=True)}
+       "lc2048_global": dict(threads=256, min_blocks=1, spt=1, unit_cap=4000, leaf_cache=2048, lc_global=True)}
 
 
 @pytest.mark.parametrize("jit", [None, "lc24", "lc2048_global"])
