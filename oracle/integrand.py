@@ -195,3 +195,14 @@ def mean_var(values):
     s2 = math.fsum(((v - mean) ** 2).tolist())
     var = s2 / (N - 1) / N if N > 1 else 0.0
     return mean, var
+
+
+def kish_ess(values):
+    """Kish effective sample size (sum |v|)^2 / sum v^2 of weighted values v
+    (w f per sample), with exactly rounded sums; 0 when every value is 0."""
+    v = np.abs(np.asarray(values, dtype=np.float64)).ravel()
+    s2 = math.fsum((v * v).tolist())
+    if s2 == 0.0:
+        return 0.0
+    s1 = math.fsum(v.tolist())
+    return s1 * s1 / s2

@@ -201,3 +201,15 @@ def test_counterterm_roots_match_finite_differences(n):
     fd = rich(lambda d: W(dataclasses.replace(P, mu=P.mu + d), (n, 1, 0, 0)), h)
     scale = np.maximum(np.abs(got), 1e-3 * np.max(np.abs(got)))
     assert np.all(np.abs(got - fd) <= 1e-6 * scale)
+
+
+def test_kish_effective_sample_size():
+    # N equal weights count fully, one nonzero weight counts once, signs do not matter
+    assert ig.kish_ess(np.full(1000, 0.37)) == pytest.approx(1000.0, rel=1e-14)
+    assert ig.kish_ess(np.r_[np.zeros(99), 5.0]) == pytest.approx(1.0, rel=1e-14)
+    assert ig.kish_ess(np.tile([1.0, -1.0], 50)) == pytest.approx(100.0, rel=1e-14)
+    assert ig.kish_ess(np.zeros(10)) == 0.0
+    # two populations: (a n1 + b n2)^2 / (a^2 n1 + b^2 n2)
+    a, b, n1, n2 = 1.0, 10.0, 900, 100
+    v = np.r_[np.full(n1, a), np.full(n2, b)]
+    assert ig.kish_ess(v) == pytest.approx((a * n1 + b * n2) ** 2 / (a * a * n1 + b * b * n2), rel=1e-14)
