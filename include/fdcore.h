@@ -39,7 +39,7 @@ typedef enum {
     FD_ENOMEM = 3,    /* device or host allocation failed */
     FD_ECUDA = 4,     /* CUDA runtime error */
     FD_ETIMEOUT = 5,  /* a bounded device wait gave up (kernel returned early) */
-    FD_ENOTSUP = 6    /* valid request this build does not support */
+    FD_ENOTSUP = 6    /* valid request the library does not support */
 } fd_status;
 
 typedef struct fd_graph fd_graph;

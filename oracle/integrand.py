@@ -19,8 +19,8 @@ Loop momentum from (a, b, c): r = K_c a, cos(theta) = 2b - 1, phi = 2 pi c,
 d^3k / (2 pi)^3 = K_c r^2 / (2 pi^2) da db dc.  Roots with n below the graph's
 order use the leading 4n - 1 coordinates.
 
-Reduction (BASELINE accumulator contract): mean and variance of W over samples
-with exactly rounded sums (math.fsum).
+Reduction: mean and variance of W over samples with exactly rounded sums
+(math.fsum), and the Kish effective sample size of the weighted values.
 """
 import itertools
 import math

@@ -126,7 +126,7 @@ def best_load(order, roots, v, params, copies=4, n_samples=1 << 24, reps=2, n_bi
     """(graph, ms) of the fastest of `copies` loads of the same specialised kernel,
     timed on the production path (a VEGAS grid of n_bins with its histogram).
 
-    The kernel's speed depends on where the driver places its code (it runs
+    The kernel's speed depends on where the CUDA driver places its code (it runs
     ~26k straight-line instructions per sample out of the instruction cache):
     loads of one image in one process differ by up to ~20 %, each stable for
     the life of the load.  The image comes from the compile cache after the

@@ -1931,7 +1931,7 @@ extern "C" fd_status fd_flow_create(int32_t dim, int32_t n_layers, int32_t hidde
     *out = nullptr;
     FD_REQUIRE(dim >= 2 && dim <= YS, "dim must be in [2, 24] (coordinate rows of the flow kernels)");
     FD_REQUIRE(n_layers >= 1 && n_layers <= 64, "n_layers must be in [1, 64]");
-    FD_REQUIRE(hidden == H, "hidden must be 128 (tensor-core tiling of this build)");
+    FD_REQUIRE(hidden == H, "hidden must be 128 (the tensor-core kernels' tiling)");
     fd_flow *f = new fd_flow();
     f->D = dim;
     f->K = n_layers;

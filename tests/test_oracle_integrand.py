@@ -178,7 +178,7 @@ def test_second_order_quasiparticle_weight_below_one():
 
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_counterterm_roots_match_finite_differences(n):
-    # the BASELINE invariant: counterterm derivatives equal finite differences in mu and Lambda
+    # counterterm derivatives equal finite differences in mu and Lambda
     P = conventions.ueg_params(1.0, 1.0 / 25.0, 1.0, 1.0)
     x = workloads.uniform_points(31 + n, 4 * n - 1, 16)
     h = 1e-3

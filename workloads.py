@@ -7,7 +7,8 @@ its own code.
 
 The workloads mirror the paper's uniform-electron-gas calculations
 (Sec. VI.A: r_s, T/T_F, screening lambda, external momentum), at the sizes of
-the five benchmark configurations of this build.  No dataset is involved: the
+the benchmark configurations (the order-1 exchange case to the order-6
+effective mass).  No dataset is involved: the
 paper's inputs are synthetic by nature.
 """
 import numpy as np
