@@ -380,7 +380,6 @@ def run_ours(args, rank, world, dist):
     exec_instr_ps, _ = fdgraph.specialised_work(
         G.tape, tuned.get("root_units", True), unit_cap=(tuned.get("unit_cap") or 6000) if loop else None,
         cross_roots=bool(tuned.get("cross_roots")) and loop, instr=True, leaf_cache=lc)
-    fp64_ps = fdgraph.tape_work(G.tape, fp64=True)
     V = api.Vegas(G.dim, WL["n_bins"])
     n = args.samples
     plan = api.EvalPlan([G], params, [0], n, maps=[V])
@@ -474,7 +473,7 @@ def run_ours(args, rank, world, dist):
                      "frac": achieved / peak, "traffic": None,
                      "traffic_note": "no DRAM counters in a timed run; ncu figures in profiles/",
                      "kernel": "fd_jit_kernel",
-                     "flops_per_sample": flops_ps, "sfu_per_sample": sfu_ps, "fp64_per_sample": fp64_ps,
+                     "flops_per_sample": flops_ps, "sfu_per_sample": sfu_ps,
                      "executed_flops_per_sample": exec_flops_ps, "executed_sfu_per_sample": exec_sfu_ps,
                      "executed_fp32_instr_per_sample": exec_instr_ps,
                      "fp32_issue_frac": exec_instr_ps * n / t_kern / (n_sm * 128 * mhz_max * 1e6),

@@ -155,9 +155,9 @@ __device__ __forceinline__ void g_leaf(const Slots<T, P> &S, const Vars<P> &V, u
         float dxh, dxl;
         fd_time_diff(ta[p], pick(V.tl, la, p), tb[p], pick(V.tl, lb, p), dxh, dxl);
         if (precise) {
-            g_family_precise((double)h[0][p], (double)h[1][p], (double)h[2][p], (double)l[0][p], (double)l[1][p],
-                             (double)l[2][p], ks, dxh, dxl, (double)D.beta + (double)D.beta_l,
-                             (double)D.mu + (double)D.mu_l, M, dk, [&](int j, float v) { S.store1(d + j, p, v); });
+            g_family_df(h[0][p], h[1][p], h[2][p], FdDF{l[0][p], 0.0f}, FdDF{l[1][p], 0.0f}, FdDF{l[2][p], 0.0f},
+                        ks, dxh, dxl, D.beta, D.beta_l, D.mu, D.mu_l, M, dk,
+                        [&](int j, float v) { S.store1(d + j, p, v); });
             continue;
         }
         const float eps = fd_eps(h[0][p], h[1][p], h[2][p], l[0][p], l[1][p], l[2][p], D.mu, D.mu_l);

@@ -242,7 +242,7 @@ std::string fnum(float f) {
 
 // signed momentum sums of a 2-bit-per-variable mask: grid parts (x, y, z),
 // remainders (xl, yl, zl) and the k_ext coefficient.  cast: a prefix for the
-// remainder terms ("(double)" in the FP64 families).
+// remainder terms.
 struct MomExpr {
     std::string x, y, z, xl, yl, zl, ks;
 };
@@ -273,6 +273,28 @@ MomExpr momentum_expr(uint32_t mask, int N, const std::string &cast = "") {
     return m;
 }
 
+// the remainder sums of momentum_expr as exact double-float expressions
+// (FdDF; one error-free addition per further term)
+MomExpr momentum_df_expr(uint32_t mask, int N) {
+    auto coef = [&](int j) { return (int)(((int32_t)(mask << (30 - 2 * j))) >> 30); };
+    auto sum = [&](const char *comp, const char *ext) {
+        std::vector<std::pair<int, std::string>> terms;
+        if (ext && coef(0)) terms.push_back({coef(0), ext});
+        for (int j = 1; j <= N; ++j)
+            if (coef(j)) terms.push_back({coef(j), std::string("V.") + comp + "[" + std::to_string(j - 1) + "]"});
+        if (terms.empty()) return std::string("FdDF{0.0f, 0.0f}");
+        std::string e = std::string("FdDF{") + (terms[0].first > 0 ? "" : "-") + terms[0].second + ", 0.0f}";
+        for (size_t i = 1; i < terms.size(); ++i)
+            e = "fd_df_addf(" + e + ", " + (terms[i].first > 0 ? "" : "-") + terms[i].second + ")";
+        return e;
+    };
+    MomExpr m;
+    m.xl = sum("kxl", nullptr);
+    m.yl = sum("kyl", nullptr);
+    m.zl = sum("kzl", "Q.kextl");
+    return m;
+}
+
 // time difference t_a - t_b of a G leaf's interaction lines as (dxh, dxl)
 std::string time_diff_expr(uint32_t la, uint32_t lb, const std::string &vt) {
     const std::string a = std::to_string(la), b = std::to_string(lb);
@@ -294,17 +316,17 @@ std::string leaf_block(uint64_t w, const std::string &nm, uint32_t op, int N, co
     const int M = (int)((w >> 40) & 7u), dk = (int)((w >> 43) & 1u);
     const bool precise = op == OP_GLEAF && ((w >> FD_LEAF_PRECISE_BIT) & 1u);
     const uint32_t la = (uint32_t)(w >> 34) & 7u, lb = (uint32_t)(w >> 37) & 7u;
-    const MomExpr me = momentum_expr(mask, N, precise ? "(double)" : "");
+    const MomExpr me = momentum_expr(mask, N);
     const std::string hi = "    const " + vt + " pxh = " + me.x + ", pyh = " + me.y + ", pzh = " + me.z + ";\n";
     acc = nm + "[";
     if (precise) {
-        // FP64 family (the single G line of the order-1 diagram), per sample (packed: per lane)
-        o << "  " << vt << " " << nm << "[" << no << "];\n  {\n" << hi << time_diff_expr(la, lb, vt)
-          << "    const double bt = (double)Q.beta + (double)Q.betal, mu = (double)Q.muh + (double)Q.mul;\n";
+        // double-float family (the single G line of the order-1 diagram), per
+        // sample (packed: per lane); the remainder sums exact as double-floats
+        o << "  " << vt << " " << nm << "[" << no << "];\n  {\n" << hi << time_diff_expr(la, lb, vt);
         const int lanes = vt == "float" ? 1 : 2;
         for (int q = 0; q < lanes; ++q) {
             const std::string L = vt == "float" ? "" : ".v." + std::string(q ? "y" : "x");
-            const MomExpr ml = momentum_expr(mask, N, "(double)");
+            const MomExpr ml = momentum_df_expr(mask, N);
             auto lane = [&](const std::string &e) {
                 if (vt == "float") return e;
                 // packed operands: take this lane of every V member
@@ -318,11 +340,9 @@ std::string leaf_block(uint64_t w, const std::string &nm, uint32_t op, int N, co
                 }
                 return out + r.substr(pos);
             };
-            o << "    g_family_precise((double)" << (vt == "float" ? "pxh" : "pxh" + L) << ", (double)"
-              << (vt == "float" ? "pyh" : "pyh" + L) << ", (double)" << (vt == "float" ? "pzh" : "pzh" + L)
-              << ", " << lane(ml.xl) << ", " << lane(ml.yl) << ", " << lane(ml.zl) << ", " << me.ks << ", "
-              << (vt == "float" ? "dxh" : "dxh" + L) << ", " << (vt == "float" ? "dxl" : "dxl" + L)
-              << ", bt, mu, " << M << ", " << dk << ", [&](int j, float v) { ";
+            o << "    g_family_df(" << "pxh" << L << ", pyh" << L << ", pzh" << L << ", " << lane(ml.xl) << ", "
+              << lane(ml.yl) << ", " << lane(ml.zl) << ", " << me.ks << ", dxh" << L << ", dxl" << L
+              << ", Q.beta, Q.betal, Q.muh, Q.mul, " << M << ", " << dk << ", [&](int j, float v) { ";
             if (vt == "float")
                 o << nm << "[j] = v; });\n";
             else

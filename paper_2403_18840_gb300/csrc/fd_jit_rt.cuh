@@ -45,7 +45,7 @@ FD_HD float fd_mul_rn(float a, float b) {
 constexpr int FD_MAX_ORDER = 6;
 constexpr int FD_MAX_DIM = 4 * FD_MAX_ORDER - 1;
 constexpr int FD_MAX_M = 7;         // largest Taylor order of a leaf family (incl. d/dk)
-constexpr int FD_LEAF_PRECISE_BIT = 44;   // G leaf word: evaluate the family in FP64 (g_family_precise)
+constexpr int FD_LEAF_PRECISE_BIT = 44;   // G leaf word: evaluate the family in double-float (g_family_df)
 constexpr int FD_MAX_INST = 256;    // instances per launch (kernel-parameter descriptors)
 constexpr float FD_INV_2PI2 = 0.050660591821168885f;   // 1 / (2 pi^2)
 constexpr float FD_8PI = 25.132741228718345f;
@@ -146,6 +146,82 @@ FD_HD FdDF fd_two_prod(float a, float b) {
 FD_HD FdDF fd_df_mul(FdDF a, FdDF b) {
     const FdDF p = fd_two_prod(a.hi, b.hi);
     return fd_fast_two_sum(p.hi, p.lo + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+// a b for an FP32 b
+FD_HD FdDF fd_df_mulf(FdDF a, float b) {
+    const FdDF p = fd_two_prod(a.hi, b);
+    return fd_fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
+}
+// a + b: the error is a few 2^-48 of |a| + |b| (enough where a sum cancels
+// to ~1e-9 of its terms and keeps 1e-5 of its own value)
+FD_HD FdDF fd_df_add(FdDF a, FdDF b) {
+    const FdDF s = fd_two_sum(a.hi, b.hi);
+    return fd_two_sum(s.hi, fd_add_rn(s.lo, fd_add_rn(a.lo, b.lo)));
+}
+FD_HD FdDF fd_df_addf(FdDF a, float b) {
+    const FdDF s = fd_two_sum(a.hi, b);
+    return fd_two_sum(s.hi, fd_add_rn(s.lo, a.lo));
+}
+FD_HD FdDF fd_df_neg(FdDF a) { return FdDF{-a.hi, -a.lo}; }
+
+// 1 / d for d in [1, 2]: the rounded FP32 reciprocal r and one Newton step
+// r + r (1 - d r), with 1 - d r from the exact product d.hi r
+FD_HD FdDF fd_df_rcp(FdDF d) {
+#ifdef __CUDA_ARCH__
+    const float r = __frcp_rn(d.hi);
+#else
+    const float r = 1.0f / d.hi;
+#endif
+    const FdDF p = fd_two_prod(d.hi, r);
+    const float e = fd_add_rn(fd_add_rn(fd_add_rn(1.0f, -p.hi), -p.lo), -fd_mul_rn(d.lo, r));   // 1 - p.hi exact
+    return fd_fast_two_sum(r, fd_mul_rn(r, e));
+}
+
+// 2^k as FP32 for -126 <= k <= 127
+FD_HD float fd_pow2i(int k) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float((k + 127) << 23);
+#else
+    return ldexpf(1.0f, k);
+#endif
+}
+
+// exp(y) for y = y.hi + y.lo <= 0 as a double-float, relative error ~1e-13 (0
+// below 2^-149).  Cody and Waite's reduction y = n ln2 + r, |r| <= ln2 / 2,
+// with ln2 = L1 + L2 + L3 (L1 has 15 significant bits, so n L1 is exact for
+// |n| < 512); exp(r) = (1 + m)^16 with m = expm1(r / 16) from its Taylor
+// series (|r / 16| < 0.022: the terms from the fifth on in FP32, the series
+// ends at the seventh) and 16 = 2^4 squarings (1 + m)^2 = 1 + m (2 + m), which
+// keep m's relative precision; then 2^n as two exact power-of-two factors.
+FD_HD FdDF fd_exp_df(FdDF y) {
+    if (!(y.hi > -103.0f)) return FdDF{0.0f, 0.0f};
+    const float L1 = 0x1.62e4p-1f, L2 = 0x1.7f7d1cp-20f, L3 = 0x1.ef357ap-45f;
+    const float n = rintf(fd_mul_rn(y.hi, 0x1.715476p+0f));
+    FdDF r = fd_two_sum(y.hi, -fd_mul_rn(n, L1));
+    r = fd_df_add(r, fd_df_neg(fd_two_prod(n, L2)));
+    r = fd_df_add(r, fd_two_sum(y.lo, -fd_mul_rn(n, L3)));
+    const FdDF h = FdDF{fd_mul_rn(r.hi, 0.0625f), fd_mul_rn(r.lo, 0.0625f)};
+    // m = h (1 + h (1/2 + h (1/6 + h (1/24 + h t)))), t = 1/120 + h/720 + h^2/5040
+    const float t = fmaf(h.hi, fmaf(h.hi, 1.0f / 5040.0f, 1.0f / 720.0f), 1.0f / 120.0f);
+    FdDF p = fd_df_add(FdDF{0x1.555556p-5f, -0x1.555556p-30f}, fd_df_mulf(h, t));   // 1/24 + h t
+    p = fd_df_add(FdDF{0x1.555556p-3f, -0x1.555556p-28f}, fd_df_mul(h, p));         // 1/6 + h p
+    p = fd_df_addf(fd_df_mul(h, p), 0.5f);
+    p = fd_df_addf(fd_df_mul(h, p), 1.0f);
+    FdDF m = fd_df_mul(h, p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) m = fd_df_mul(m, fd_df_addf(m, 2.0f));
+    const FdDF e = fd_df_addf(m, 1.0f);
+    const int ni = (int)n, n1 = ni / 2;   // -149 <= n <= 0: both factors normal
+    const float s1 = fd_pow2i(n1), s2 = fd_pow2i(ni - n1);
+    return FdDF{fd_mul_rn(fd_mul_rn(e.hi, s1), s2), fd_mul_rn(fd_mul_rn(e.lo, s1), s2)};
+}
+
+// 1 / k as a double-float pair, k = 1..8
+FD_HD FdDF fd_df_inv_int(int k) {
+    return k == 1 ? FdDF{1.0f, 0.0f} : k == 2 ? FdDF{0.5f, 0.0f}
+         : k == 3 ? FdDF{0x1.555556p-2f, -0x1.555556p-27f} : k == 4 ? FdDF{0.25f, 0.0f}
+         : k == 5 ? FdDF{0x1.99999ap-3f, -0x1.99999ap-29f} : k == 6 ? FdDF{0x1.555556p-3f, -0x1.555556p-28f}
+         : k == 7 ? FdDF{0x1.24924ap-3f, -0x1.b6db6ep-28f} : FdDF{0.125f, 0.0f};
 }
 
 // cos(2 pi c), sin(2 pi c) for c = c.hi + c.lo in [0, 1], relative accuracy
@@ -265,17 +341,6 @@ FD_HD float rcp_approx(float x) {
     return 1.0f / x;
 #endif
 }
-// FP64 reciprocal of a normal x in [1, 2] (the Fermi factor 1 / (1 + E)):
-// the FP32 estimate refined by two Newton steps (relative error ~1e-15)
-FD_HD double rcp_approx(double x) {
-#ifdef __CUDA_ARCH__
-    double r = (double)__frcp_rn((float)x);
-    r = fma(r, fma(-x, r, 1.0), r);
-    return fma(r, fma(-x, r, 1.0), r);
-#else
-    return 1.0 / x;
-#endif
-}
 
 // Two samples' values in one register pair: every arithmetic operation is one
 // packed two-lane instruction (add, multiply, fused multiply-add; each lane
@@ -303,10 +368,8 @@ __device__ __forceinline__ FdF2 operator-(FdF2 a, FdF2 b) {
 }
 __device__ __forceinline__ FdF2 operator-(FdF2 a) { return fd_wrap(__fmul2_rn(a.v, make_float2(-1.0f, -1.0f))); }
 FD_HD float fd_fma(float a, float b, float c) { return fmaf(a, b, c); }
-FD_HD double fd_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ FdF2 fd_fma(FdF2 a, FdF2 b, FdF2 c) { return fd_wrap(__ffma2_rn(a.v, b.v, c.v)); }
 FD_HD float fd_abs(float a) { return fabsf(a); }
-FD_HD double fd_abs(double a) { return fabs(a); }
 __device__ __forceinline__ FdF2 fd_abs(FdF2 a) { return FdF2(fabsf(a.v.x), fabsf(a.v.y)); }
 FD_HD float fd_exp(float a) {
 #ifdef __CUDA_ARCH__
@@ -315,16 +378,12 @@ FD_HD float fd_exp(float a) {
     return expf(a);
 #endif
 }
-FD_HD double fd_exp(double a) { return exp(a); }
 __device__ __forceinline__ FdF2 fd_exp(FdF2 a) { return FdF2(__expf(a.v.x), __expf(a.v.y)); }
 FD_HD bool fd_gt0(float a) { return a > 0.0f; }
-FD_HD bool fd_gt0(double a) { return a > 0.0; }
 __device__ __forceinline__ FdM2 fd_gt0(FdF2 a) { return FdM2{a.v.x > 0.0f, a.v.y > 0.0f}; }
 FD_HD bool fd_lt0(float a) { return a < 0.0f; }
-FD_HD bool fd_lt0(double a) { return a < 0.0; }
 __device__ __forceinline__ FdM2 fd_lt0(FdF2 a) { return FdM2{a.v.x < 0.0f, a.v.y < 0.0f}; }
 FD_HD float fd_sel(bool c, float a, float b) { return c ? a : b; }
-FD_HD double fd_sel(bool c, double a, double b) { return c ? a : b; }
 __device__ __forceinline__ FdF2 fd_sel(FdM2 c, FdF2 a, FdF2 b) {
     return FdF2(c.x ? a.v.x : b.v.x, c.y ? a.v.y : b.v.y);
 }
@@ -338,10 +397,6 @@ FD_HD float inv_int(int k1) {
 template <class T>
 FD_HD T fd_inv_int(int k1) {
     return T(inv_int(k1));
-}
-template <>
-FD_HD double fd_inv_int<double>(int k1) {
-    return 1.0 / (double)k1;
 }
 
 // eps = |p|^2 - mu from a leaf's grid sums (ph: exact in FP32) and remainder
@@ -380,12 +435,10 @@ FD_HD void fd_time_diff(T tah, T tal, T tbh, T tbl, T &dh, T &dl) {
 // the dyadic times of the hypercube), so the exponent is never positive.  The
 // series of phi(eps - d) follows from the logistic ODE
 // d phi / d eps = +-beta phi (1 - phi) (a Taylor-mode recurrence); the series
-// of exp(d tau*) is tau*^k / k!.  T = float (the kernels' precision) or
-// double (the families whose value is the only term of a root, see
-// g_family_precise).  out(j, value) receives the (M + 1) (1 + dk) values.
-// ET (scalar T only): the two lines have equal times (0^-), so tau* = 0 or
-// beta and exp(-eps tau*) is 1 or the Fermi factor's exponential.
-template <class T, bool ET = false, class Out>
+// of exp(d tau*) is tau*^k / k!.  T = float or the packed FdF2 (the
+// families whose value is the only term of a root: g_family_df).  out(j,
+// value) receives the (M + 1) (1 + dk) values.
+template <class T, class Out>
 FD_HD void g_family(T eps, T pz, float ks, T dxh, T dxl, T beta, int M, int dk, Out &&out) {
     const T E = fd_exp(-beta * fd_abs(eps));
     const T phi = rcp_approx(T(1.0f) + E);
@@ -394,11 +447,7 @@ FD_HD void g_family(T eps, T pz, float ks, T dxh, T dxl, T beta, int M, int dk, 
     const auto occ = fd_lt0(eps);
     const T dstar = fd_sel(occ, fd_sel(pos, dxh - T(1.0f), dxh), fd_sel(pos, dxh, dxh + T(1.0f))) + dxl;
     const T tstar = beta * dstar;
-    T X;
-    if constexpr (ET)
-        X = occ ? phi : E * phi;
-    else
-        X = fd_sel(pos, T(-1.0f), T(1.0f)) * fd_exp(-eps * tstar) * phi;
+    const T X = fd_sel(pos, T(-1.0f), T(1.0f)) * fd_exp(-eps * tstar) * phi;
     if (M == 0 && !dk) {
         out(0, X);
         return;
@@ -445,18 +494,90 @@ FD_HD void g_family(T eps, T pz, float ks, T dxh, T dxl, T beta, int M, int dk, 
 // (the single line of the order-1 diagram): a coefficient (d/dmu)^j G0 of the
 // equal-time line has zeros in eps (f''(0) = 0 and the nonzero roots of the
 // higher logistic derivatives), near which an FP32 evaluation has a large
-// error relative to the value itself.  This variant takes eps, p_z and tau*
-// from the grid and remainder sums in FP64 and evaluates the family in FP64.
+// error relative to the value itself.
+// This family is therefore evaluated in double-float arithmetic (pairs of
+// FP32 numbers, ~48 significant bits) rather than FP64, whose instructions
+// issue at a small fraction of the FP32 rate on this GPU.  Inputs: the line's
+// momentum as grid parts (ph) and double-float remainders (pl), the time
+// difference dx = dxh + dxl, beta and mu as hi + lo.  eps = |ph + pl|^2 - mu
+// from exact products; E = exp(-beta |eps|) (fd_exp_df), the Fermi factor
+// phi = 1 / (1 + E) and psi = E phi, tau* = beta dx*, the Taylor recurrences of
+// g_family and the coefficient sums in double-float; the common factor
+// exp(-eps tau*) phi, which no sum cancels, in FP32 from the accurate expf of
+// the product's high part times 1 - (its low part).
 template <class Out>
-FD_HD void g_family_precise(double pxh, double pyh, double pzh, double pxl, double pyl, double pzl, float ks,
-                            float dxh, float dxl, double beta, double mu, int M, int dk, Out &&out) {
-    const double px = pxh + pxl, py = pyh + pyl, pz = pzh + pzl;
-    const double eps = fma(px, px, fma(py, py, pz * pz)) - mu;
-    if (dxh == 0.0f && dxl == 0.0f)
-        g_family<double, true>(eps, pz, ks, 0.0, 0.0, beta, M, dk, [&](int j, double v) { out(j, (float)v); });
-    else
-        g_family<double>(eps, pz, ks, (double)dxh, (double)dxl, beta, M, dk,
-                         [&](int j, double v) { out(j, (float)v); });
+FD_HD void g_family_df(float pxh, float pyh, float pzh, FdDF pxl, FdDF pyl, FdDF pzl, float ks, float dxh,
+                       float dxl, float bh, float bl, float muh, float mul, int M, int dk, Out &&out) {
+    // |ph + pl|^2 = sum ph^2 + 2 ph pl.hi + (2 ph pl.lo + pl.hi^2), the last
+    // terms below 1e-7 and rounded once
+    FdDF e2 = fd_two_prod(pxh, pxh);
+    e2 = fd_df_add(e2, fd_two_prod(pyh, pyh));
+    e2 = fd_df_add(e2, fd_two_prod(pzh, pzh));
+    e2 = fd_df_addf(e2, -muh);
+    FdDF cr = fd_two_prod(2.0f * pxh, pxl.hi);
+    cr = fd_df_add(cr, fd_two_prod(2.0f * pyh, pyl.hi));
+    cr = fd_df_add(cr, fd_two_prod(2.0f * pzh, pzl.hi));
+    const float small = fmaf(2.0f * pxh, pxl.lo, fmaf(pxl.hi, pxl.hi, fmaf(2.0f * pyh, pyl.lo,
+                        fmaf(pyl.hi, pyl.hi, fmaf(2.0f * pzh, pzl.lo, fmaf(pzl.hi, pzl.hi, -mul))))));
+    const FdDF eps = fd_df_addf(fd_df_add(e2, cr), small);
+    const bool occ = eps.hi < 0.0f;
+    const FdDF beta = FdDF{bh, bl};
+    const FdDF E = fd_exp_df(fd_df_neg(fd_df_mul(beta, occ ? fd_df_neg(eps) : eps)));
+    const FdDF phi = fd_df_rcp(fd_df_addf(E, 1.0f));
+    const FdDF psi = fd_df_mul(E, phi);
+    const bool et = dxh == 0.0f && dxl == 0.0f;   // equal times (0^-): tau* = 0 or beta
+    const bool pos = dxh > 0.0f;
+    const float shift = occ ? (pos ? -1.0f : 0.0f) : (pos ? 0.0f : 1.0f);
+    const FdDF tstar = fd_df_mul(beta, fd_df_addf(fd_two_sum(dxh, shift), dxl));
+    float X;
+    if (et) {
+        X = occ ? phi.hi : psi.hi;
+    } else {
+        const FdDF y = fd_df_mul(eps, tstar);   // >= 0: the exponent -eps tau* is never positive
+        X = (pos ? -1.0f : 1.0f) * fd_mul_rn(fd_mul_rn(expf(-y.hi), 1.0f - y.lo), phi.hi);
+    }
+    if (M == 0 && !dk) {
+        out(0, X);
+        return;
+    }
+    const int Mx = M + dk;
+    const FdDF g = occ ? beta : fd_df_neg(beta);
+    FdDF ph[FD_MAX_M + 1], ps[FD_MAX_M + 1], A[FD_MAX_M + 1];
+    ph[0] = FdDF{1.0f, 0.0f};
+    ps[0] = psi;
+    A[0] = FdDF{1.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < FD_MAX_M; ++k) {
+        if (k < Mx) {
+            FdDF s = ps[k];   // ph[0] = 1
+#pragma unroll
+            for (int i = 1; i <= k; ++i) s = fd_df_add(s, fd_df_mul(ph[i], ps[k - i]));
+            const FdDF inv = fd_df_inv_int(k + 1);
+            ph[k + 1] = fd_df_mul(fd_df_mul(g, s), inv);
+            ps[k + 1] = fd_df_neg(fd_df_mul(phi, ph[k + 1]));
+            A[k + 1] = fd_df_mul(fd_df_mul(A[k], tstar), inv);
+        }
+    }
+    float cf[FD_MAX_M + 1];
+#pragma unroll
+    for (int j = 0; j <= FD_MAX_M; ++j) {
+        if (j <= Mx) {
+            FdDF s = fd_df_add(A[j], ph[j]);   // the terms i = 0 and i = j (j >= 1)
+            if (j == 0) s = FdDF{1.0f, 0.0f};
+#pragma unroll
+            for (int i = 1; i < j; ++i) s = fd_df_add(s, fd_df_mul(A[j - i], ph[i]));
+            cf[j] = fmaf(X, s.hi, X * s.lo);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j <= FD_MAX_M; ++j)
+        if (j <= M) out(j, cf[j]);
+    if (dk) {
+        const float kz = -2.0f * ks * (pzh + pzl.hi);
+#pragma unroll
+        for (int j = 0; j < FD_MAX_M; ++j)
+            if (j <= M) out(M + 1 + j, kz * (float)(j + 1) * cf[j + 1]);
+    }
 }
 
 // V Taylor family: c_l = (d/dLambda)^l V / l! = 8 pi (-1)^l w^(l+1), w = 1/(q^2+Lambda),
@@ -521,8 +642,8 @@ struct FdSVT {
 __host__ __device__ constexpr int fd_sv_words(int N) { return 8 * N + 1; }
 
 // Per-instance parameters of the generated code: k_ext and mu as grid part +
-// remainder (grid g and g^2), beta (and its FP64 remainder for the precise
-// families), Lambda.
+// remainder (grid g and g^2), beta (and its remainder for the
+// double-float families), Lambda.
 struct FdPar {
     float kexth, kextl, beta, betal, muh, mul, Lam;
 };
@@ -549,9 +670,6 @@ __device__ __forceinline__ FdSVT<FdF2, N> fd_pack(const FdSVT<float, N> &a, cons
     return w;
 }
 
-// lane q of a packed value (the precise families run per sample in FP64)
-__device__ __forceinline__ float fd_lane(FdF2 v, int q) { return q ? v.v.y : v.v.x; }
-__device__ __forceinline__ float fd_lane(float v, int) { return v; }
 
 // Hypercube point of sample i (Philox stream or given point), VEGAS map (when
 // the instance has one), then loop momenta k_j, interaction-line times t_j

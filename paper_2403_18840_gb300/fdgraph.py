@@ -38,9 +38,9 @@ Tape format, version 4 (little endian; sections 16-byte aligned):
           Leaf ops keep in `a` a signed 2-bit coefficient per momentum
           variable (k_ext, k_1..k_N; 1 = +1, 3 = -1) and in the upper bits the
           two interaction lines (3 bits each), the Taylor order (3 bits),
-          the d/dk flag and (G leaves, bit 44) the FP64 flag: the family is
-          the only G line of a root's value (the order-1 diagram), evaluated
-          in FP64.  RACC: `a` = value slot, `b` = out-line; RFLUSH:
+          the d/dk flag and (G leaves, bit 44) the precise flag: the family
+          is the only G line of a root's value (the order-1 diagram),
+          evaluated in double-float arithmetic.  RACC: `a` = value slot, `b` = out-line; RFLUSH:
           `d` = root index; CONST: float in the high 32 bits.
 Per-sample state: slot 0 = 0.0, slot 1 = 1.0 and slots 2..N+1 = hypercube time
 of interaction lines 0..N-1 (written by the kernel), then constants, leaf
@@ -639,9 +639,10 @@ def compile_dag(order, roots, dag, outputs, budget=96, bundle=4, window=32):
     def fam_of(v):
         return ("G", v[1], v[2], v[3]) if v[0] in ("G", "Gd") else ("V", v[1])
 
-    # G families evaluated in FP64: those reachable from an order-1 root, whose
-    # value is one diagram with one G line (no other line's terms share its
-    # magnitude, so the zeros of its mu-derivatives need FP64)
+    # G families evaluated in double-float arithmetic: those reachable from an
+    # order-1 root, whose value is one diagram with one G line (no other line's
+    # terms share its magnitude, so the zeros of its mu-derivatives need ~48
+    # significant bits)
     precise = set()
     stk = [node for (r, _, node) in outputs if roots[r][0] == 1]
     seen = set()
@@ -875,15 +876,34 @@ MAP_MOMENTUM_FLOPS, MAP_MOMENTUM_SFU = 190, 2
 MAP_TIME_FLOPS, MAP_TIME_SFU = 3, 1
 
 
+def _g_family_df_instr(M, dk):
+    """FP32 instructions of one double-float G family (g_family_df) as
+    written: eps from exact products (~100), the double-float exponential
+    (~250), the Fermi factor's reciprocal and psi (~35), tau* and the common
+    factor with the accurate expf (~50); per recurrence step k (k inner
+    products of ~22 instructions, five products and a negation, ~41) and per
+    coefficient sum j >= 1 (~16 + 22 (j - 1)); 2 per k-derivative output."""
+    Mx = M + dk
+    i = 435
+    for k in range(Mx):
+        i += 22 * k + 41
+    for j in range(1, Mx + 1):
+        i += 16 + 22 * (j - 1)
+    if dk:
+        i += 2 * (M + 1) + 1
+    return i
+
+
 def _leaf_work(w, instr=False):
-    """(fp32 flops, sfu ops, fp64 ops) of one leaf word (with instr: FP32
-    instructions in place of flops, an FMA counting once).
+    """(fp32 flops, sfu ops) of one leaf word (with instr: FP32 instructions
+    in place of flops, an FMA counting once).
 
     Momentum: grid and remainder sums, 6 (t - 1) for t terms.  G: eps from the
     sums (fd_eps: 6 FMAs, a product and 3 sums: 19 flops, 10 instructions),
     p_z 1, the time difference of two nonzero lines 12, Fermi factor 3 + 2 SFU,
-    then the family (_g_family_work + 1 SFU).  A G family with the FP64 flag
-    counts its arithmetic as FP64 operations instead.  V: q = grid +
+    then the family (_g_family_work + 1 SFU).  A G family with the precise
+    flag has the same operations (flops) and executes them in double-float
+    arithmetic (instructions: _g_family_df_instr).  V: q = grid +
     remainder 3, |q|^2 5 (3 instructions), 1 / (q^2 + Lambda) 1 + 1 SFU, 8 pi 1,
     the powers (L + dk), the d/dk outputs 2 + 2 (L + 1).
     """
@@ -898,10 +918,10 @@ def _leaf_work(w, instr=False):
         td = 12 if (la != lb and la and lb) else 0
         gf, gi = _g_family_work(M, dk)
         fam = (10 if instr else 19) + 1 + 3 + (gi if instr else gf)
-        if (w >> LEAF_PRECISE_BIT) & 1:
-            return sums + td, 0, 19 + 1 + 3 + gf + 6
-        return sums + td + fam, 3, 0
-    return sums + 3 + (3 if instr else 5) + 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0), 1, 0
+        if instr and (w >> LEAF_PRECISE_BIT) & 1:
+            return sums + td + _g_family_df_instr(M, dk), 3
+        return sums + td + fam, 3
+    return sums + 3 + (3 if instr else 5) + 2 + (M + dk) + ((2 + 2 * (M + 1)) if dk else 0), 1
 
 
 def _map_work(dim, order, n_roots):
@@ -1027,7 +1047,7 @@ def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False, in
         return sum((((words[ins[j][1]] >> 40) & 7) + 1) * (2 if (words[ins[j][1]] >> 43) & 1 else 1) for j in cached)
     flops = sfu = 0
     for j in cached:
-        f, u, _ = _leaf_work(words[ins[j][1]], instr)
+        f, u = _leaf_work(words[ins[j][1]], instr)
         flops += f
         sfu += u
     for _, fmas, leaves in units:
@@ -1037,7 +1057,7 @@ def specialised_work(data, root_units=True, unit_cap=None, cross_roots=False, in
         for j in leaves:
             if j in cached:
                 continue
-            f, u, _ = _leaf_work(words[ins[j][1]], instr)
+            f, u = _leaf_work(words[ins[j][1]], instr)
             flops += f
             sfu += u
     n_racc = len(slices)
@@ -1069,9 +1089,9 @@ def contraction_ops(data):
     return ops
 
 
-def tape_work(data, fp64=False):
+def tape_work(data):
     """(fp32_flops, sfu_ops) per sample of a serialised tape, map and weighting
-    included (with fp64=True: the FP64 operations of the flagged families).
+    included.
 
     Counting rule (FMA = 2 flops, other arithmetic 1): tape FMA as written
     (a multiply by slot 1 = 1.0 or an add of slot 0 = 0.0 counts 1); leaves
@@ -1084,7 +1104,6 @@ def tape_work(data, fp64=False):
     words = struct.unpack("<%dQ" % n_instr, data[ins_off:ins_off + 8 * n_instr])
     flops = 0
     sfu = 0
-    f64 = 0
     k = 0
     while k < len(words):
         w = words[k]
@@ -1098,14 +1117,11 @@ def tape_work(data, fp64=False):
             k += 1 + n
             continue
         if op in (OP_GLEAF, OP_VLEAF):
-            f, u, d = _leaf_work(w)
+            f, u = _leaf_work(w)
             flops += f
             sfu += u
-            f64 += d
         elif op == OP_RACC:
             flops += 4
         k += 1
-    if fp64:
-        return f64
     mf, mu = _map_work(dim, order, n_roots)
     return flops + mf, sfu + mu

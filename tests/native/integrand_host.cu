@@ -1,6 +1,6 @@
 // Host driver for the integrand's per-sample device arithmetic
 // (fd_jit_rt.cuh): the double-float sampler map and loop momenta, the leaf
-// families (g_family, g_family_precise, v_family) with the grid / remainder
+// families (g_family, g_family_df, v_family) with the grid / remainder
 // momentum sums and the time differences, the tape's FMA bundles, root
 // accumulation and weighting, run on the CPU sample by sample as the tape
 // interpreter does, so that a CPU test can compare them with the FP64 oracle.
@@ -153,9 +153,8 @@ int main(int argc, char **argv) {
                     float dxh, dxl;
                     fd_time_diff(t[la], tl[la], t[lb], tl[lb], dxh, dxl);
                     if ((wd >> FD_LEAF_PRECISE_BIT) & 1u) {
-                        g_family_precise((double)h[0], (double)h[1], (double)h[2], (double)l[0], (double)l[1],
-                                         (double)l[2], ks, dxh, dxl, (double)P.beta + (double)P.beta_l,
-                                         (double)P.mu + (double)P.mu_l, M, dk, put);
+                        g_family_df(h[0], h[1], h[2], FdDF{l[0], 0.0f}, FdDF{l[1], 0.0f}, FdDF{l[2], 0.0f}, ks,
+                                    dxh, dxl, P.beta, P.beta_l, P.mu, P.mu_l, M, dk, put);
                     } else {
                         const float eps = fd_eps(h[0], h[1], h[2], l[0], l[1], l[2], P.mu, P.mu_l);
                         g_family<float>(eps, h[2] + l[2], ks, dxh, dxl, P.beta, M, dk, put);

@@ -142,3 +142,28 @@ def test_loop_momenta_double_float(kin_exe, tmp_path):
     err = np.abs(k - kref[1:])
     print("double-float momenta: max err %.2e" % err.max())
     assert err.max() <= 1e-10
+
+
+def test_host_build_order1_at_the_fermi_surface(exe, tmp_path):
+    """The order-1 roots' G families (m <= 4 mu-derivatives, with and without
+    the k-derivative) at points where |k_1|^2 - mu lies within 1e-4 .. 1e-2 of
+    the Fermi surface (both signs) or anywhere in |eps| <= 1 = 0.27 E_F, where
+    the mu-derivatives of the equal-time line cross zero (at beta eps of order
+    one).  Each root is a single term there, so its value has to hold 1e-5 of
+    itself where it is small: the double-float evaluation of eps, the Fermi
+    factor and the Taylor recurrences does (an FP32 family misses the bound
+    by orders of magnitude).  The lower end 1e-4 is set by the kinematics:
+    the momenta's FP32 remainders carry eps to ~1e-10, and the even
+    derivatives vanish linearly at eps = 0."""
+    n = 16384
+    roots = [(1, m, 0, dk) for m in range(5) for dk in (0, 1)]
+    P = conventions.ueg_params(1.0, 1.0 / 25.0, 1.0, 1.0)
+    rng = np.random.default_rng(2024)
+    eps = np.where(rng.random(n) < 0.5, 1.0, -1.0) * np.where(
+        np.arange(n) % 2 == 0, 10.0 ** rng.uniform(-4.0, -2.0, n), rng.uniform(0.0, 1.0, n))
+    x = ophilox.uniforms(77, 0, 0, np.arange(n), 3)
+    x[0] = np.sqrt(P.mu + eps) / P.kc
+    x = x.astype(np.float32).astype(np.float64)
+    f = run_host(exe, tmp_path, api.tape_bytes(1, roots), 1, roots, x, P)
+    ref, mag = oig.eval_roots(x, roots, P, with_l1=True)
+    _check(_rel(f, ref, mag), "host order 1 at the Fermi surface")
