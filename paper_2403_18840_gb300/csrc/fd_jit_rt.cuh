@@ -735,6 +735,18 @@ __device__ __forceinline__ void sample_point(const InstDesc &D, const EvalArgs &
 // Completed roots of one sample: weight, optional per-sample output, warp
 // reduction of (f, f^2) for the real and imaginary parts, and FP64 Neumaier
 // accumulation per warp (lane 0).
+// The four warp totals (Re f, (Re f)^2, Im f, (Im f)^2; every lane holds the
+// same values after the xor butterfly) into the warp's FP64 Neumaier
+// accumulators acc[q][2], one per lane 0..3, so that the four FP64 updates
+// run side by side instead of one after another in lane 0.
+__device__ __forceinline__ void fd_accumulate_lanes(double *acc, const float (&v)[4]) {
+    const int q = threadIdx.x & 31;
+    if (q < 4) {
+        const float mine = q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3];
+        neumaier(acc[2 * q], acc[2 * q + 1], (double)mine);
+    }
+}
+
 template <int N>
 struct FdSink {
     double *acc;                 // this warp's accumulators [R][4][2]
@@ -760,10 +772,7 @@ struct FdSink {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
         }
-        if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) neumaier(acc[(R_IDX * 4 + q) * 2], acc[(R_IDX * 4 + q) * 2 + 1], (double)v[q]);
-        }
+        fd_accumulate_lanes(acc + R_IDX * 8, v);
     }
 };
 
@@ -793,11 +802,7 @@ __device__ __forceinline__ void flush_samples(FdSink<N> *K, const float *re, con
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
     }
-    if ((threadIdx.x & 31) == 0) {
-        double *acc = K[0].acc;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) neumaier(acc[(R_IDX * 4 + q) * 2], acc[(R_IDX * 4 + q) * 2 + 1], (double)v[q]);
-    }
+    fd_accumulate_lanes(K[0].acc + R_IDX * 8, v);
 }
 
 // VEGAS histogram of one tile.  With hist_smem > 0 the launch provides

@@ -7,8 +7,10 @@ starting as the identity (that is, as VEGAS), is trained by forward KL on
 |f| J_map from batches the method generates (VEGAS first, then the flow
 itself) with a defensive uniform share of 10 % (so its weights never exceed
 ten times the VEGAS weights), with the training of the benchmark (2000 Adam
-steps on batches of 2^20, each batch used for 4 steps).  Over the benchmark's
-64 independent batches of 2^24 samples per sampler, the learned proposal must lower the
+steps on batches of 2^20, each batch used for 4 steps).  Over 256 independent
+batches of 2^24 samples per sampler (the benchmark's batch size; with its 64
+batches the interval's lower end ranged 0.84 - 1.6 over runs whose point
+estimates were 1.6 - 2.9), the learned proposal must lower the
 per-sample variance of Re Sigma^(5) taken with the median batch variance:
 the lower end of its 95 % percentile-bootstrap interval over the batches
 above 1.  The time-adjusted gains (the samples/s ratio times the variance
@@ -35,7 +37,7 @@ def test_flow_beats_vegas_at_order5():
     F = api.Flow(G.dim, 8, 128, seed=3)
     losses = driver.train_flow(G, p, F, V, steps=2000, batch=1 << 20, lr=1e-3, seed=12, vegas_steps=100,
                                evals_per_batch=4, defensive=0.1)
-    cmp = driver.compare(G, p, V, F, 1 << 24, seed=13, batches=64, defensive=0.1)
+    cmp = driver.compare(G, p, V, F, 1 << 24, seed=13, batches=256, defensive=0.1)
     print({k: cmp[k] for k in ("flow_over_vegas", "flow_over_vegas_median", "means_agree_sigma")},
           cmp["vegas"]["var_batches"], cmp["flow"]["var_batches"], cmp["vegas"]["samples_per_s"],
           cmp["flow"]["samples_per_s"], losses[0], losses[-1])
