@@ -186,8 +186,10 @@ FD_HD float fd_pow2i(int k) {
 #endif
 }
 
-// exp(y) for y = y.hi + y.lo <= 0 as a double-float, relative error ~1e-13 (0
-// below 2^-149).  Cody and Waite's reduction y = n ln2 + r, |r| <= ln2 / 2,
+// exp(y) for y = y.hi + y.lo <= 0 as a double-float: relative error ~1e-15
+// while exp(y) >= 2^-100 (y >= -69; its low part is then a normal FP32
+// number), growing to the FP32 rounding (2^-24) as the low part runs into the
+// subnormals near 2^-126; 0 for y <= -103, where exp(y) < 2^-148.  Cody and Waite's reduction y = n ln2 + r, |r| <= ln2 / 2,
 // with ln2 = L1 + L2 + L3 (L1 has 15 significant bits, so n L1 is exact for
 // |n| < 512); exp(r) = (1 + m)^16 with m = expm1(r / 16) from its Taylor
 // series (|r / 16| < 0.022: the terms from the fifth on in FP32, the series

@@ -167,3 +167,55 @@ def test_host_build_order1_at_the_fermi_surface(exe, tmp_path):
     f = run_host(exe, tmp_path, api.tape_bytes(1, roots), 1, roots, x, P)
     ref, mag = oig.eval_roots(x, roots, P, with_l1=True)
     _check(_rel(f, ref, mag), "host order 1 at the Fermi surface")
+
+
+@pytest.fixture(scope="module")
+def df_exe(tmp_path_factory):
+    return _build(tmp_path_factory, "df_host")
+
+
+def test_double_float_exp_and_reciprocal(df_exe, tmp_path):
+    """The order-1 family's double-float exponential (Cody-Waite reduction
+    with ln 2 in three FP32 parts, expm1 by a Taylor series, four squarings)
+    and reciprocal (a Newton step) against exact-rational references: exp(y)
+    for double-float y in [-103, 0] (the family's arguments -beta |eps| are
+    never positive) within 1e-13 relative while exp(y) >= 2^-100 (the low
+    half is a normal FP32 number), within the FP32 rounding 2^-24 relative
+    or 2^-148 absolute below (0 from -103 on); 1 / d for double-float d in
+    [1, 2] within 4e-14 relative (one Newton step: ~2^-46)."""
+    from fractions import Fraction
+    import math
+    rng = np.random.default_rng(5)
+    n = 4000
+    yv = np.concatenate([-10.0 ** rng.uniform(-9.0, math.log10(103.0), n - 8),
+                         [0.0, -1e-30, -0.34657359, -0.34657360, -87.0, -88.0, -103.0, -104.0]])
+    yh = yv.astype(np.float32)
+    yl = (yv - yh.astype(np.float64)).astype(np.float32)
+    dv = 1.0 + rng.random(n)
+    dv[:4] = [1.0, 2.0, 1.0 + 2.0 ** -23, 2.0 - 2.0 ** -22]
+    dh = dv.astype(np.float32)
+    dl = (dv - dh.astype(np.float64)).astype(np.float32)
+    src, dst = str(tmp_path / "df.in"), str(tmp_path / "df.out")
+    with open(src, "wb") as f:
+        np.array([n], np.int32).tofile(f)
+        np.stack([yh, yl], 1).astype(np.float32).tofile(f)
+        np.stack([dh, dl], 1).astype(np.float32).tofile(f)
+    subprocess.run([df_exe, src, dst], check=True)
+    out = np.fromfile(dst, np.float32).reshape(2, n, 2).astype(np.float64)
+    worst_e = worst_r = 0.0
+    for i in range(n):
+        y = Fraction(float(yh[i])) + Fraction(float(yl[i]))
+        # exp of the exact double-float argument: the FP64 exp of its nearest
+        # double times the exp of the tiny remainder (|r| < 2^-53 |y|)
+        yd = float(y)
+        ref = math.exp(yd) * (1.0 + float(y - Fraction(yd)))
+        got = out[0, i, 0] + out[0, i, 1]
+        if ref >= 2.0 ** -100:
+            worst_e = max(worst_e, abs(got - ref) / ref)
+        else:
+            assert abs(got - ref) <= max(2.0 ** -24 * ref, 2.0 ** -148), (yd, got, ref)
+        d = Fraction(float(dh[i])) + Fraction(float(dl[i]))
+        r = float(1 / d)
+        worst_r = max(worst_r, abs(out[1, i, 0] + out[1, i, 1] - r) / r)
+    print("double-float exp: max rel %.2e; reciprocal: max rel %.2e" % (worst_e, worst_r))
+    assert worst_e <= 1e-13 and worst_r <= 4e-14
