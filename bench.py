@@ -262,16 +262,32 @@ def flow_vs_vegas(args, api, params, order, seed):
     return eff
 
 
+def flow_algorithmic_flops(dim, n_layers, hidden=128):
+    """Forward flops per sample of the affine coupling flow's three GEMMs:
+    2 (|A| H + H^2 + H 2 |B|) per layer, |A| the conditioning half (h =
+    (dim + 1) / 2 coordinates on even layers, dim - h on odd ones), |B| the
+    transformed half (a scale and a shift each); the padding of the operands
+    to tensor-core tiles is not counted."""
+    h = (dim + 1) // 2
+    total = 0
+    for layer in range(n_layers):
+        a, b = (h, dim - h) if layer % 2 == 0 else (dim - h, h)
+        total += 2 * (a * hidden + hidden * hidden + hidden * 2 * b)
+    return total
+
+
 def affine_flow_sampling(api, F, default_path, n=1 << 24, reps=5):
     """Samples/s of the trained affine flow's sampling pass (x and w = 1/q) on
-    each tensor-core path, and its tensor roofline: 2 (16 x 128 + 128 x 128 +
-    128 x 32) flops per layer and sample as padded on the tensor cores, against
-    the measured BF16 burst peak (the kernel is timed alone)."""
+    each tensor-core path, and its tensor roofline: the algorithmic flops of
+    flow_algorithmic_flops against the measured BF16 burst peak (the kernel is
+    timed alone); the padded figure is what the tensor cores execute, 2 (16 x
+    128 + 128 x 128 + 128 x 32) per layer."""
     import torch
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak = json.load(open(path)).get("bf16_tflops") if os.path.exists(path) else None
-    flops = 2 * (16 * 128 + 128 * 128 + 128 * 32) * F.n_layers
-    out = {"samples": n, "padded_flops_per_sample": flops, "peak_tflops": peak,
+    flops = flow_algorithmic_flops(F.dim, F.n_layers, F.hidden)
+    padded = 2 * (16 * 128 + 128 * 128 + 128 * 32) * F.n_layers
+    out = {"samples": n, "flops_per_sample": flops, "padded_flops_per_sample": padded, "peak_tflops": peak,
            "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst)"}
     names = {0: "mma.sync", 1: "tcgen05 tile pairs", 2: "tcgen05 warp-specialised"}
     for path in (2, 0, 1):
@@ -287,12 +303,12 @@ def affine_flow_sampling(api, F, default_path, n=1 << 24, reps=5):
         ms = s.elapsed_time(e) / reps
         tf = flops * n / ms * 1e-9
         out[names[path]] = {"ms": ms, "samples_per_s": n / ms * 1e3, "tflops": tf,
-                            "frac": tf / peak if peak else None}
+                            "frac": tf / peak if peak else None, "padded_tflops": padded * n / ms * 1e-9}
     F.set_tensor_path(default_path)
     # the training gradient (forward-KL loss and its gradient on given points:
     # the inverse pass, then reverse mode layer by layer, mma.sync tiles): its
     # GEMMs are the forward's three per layer plus two per GEMM backward
-    # (input adjoints and weight gradients), 3x the padded forward flops
+    # (input adjoints and weight gradients), 3x the forward flops
     m = 1 << 20
     x, _ = F.sample(5, 0, 0, m)
     wts = torch.ones(m, dtype=torch.float32, device="cuda")
@@ -307,8 +323,8 @@ def affine_flow_sampling(api, F, default_path, n=1 << 24, reps=5):
     ms = s.elapsed_time(e) / reps
     tf = 3 * flops * m / ms * 1e-9
     out["training_gradient"] = {"samples": m, "ms": ms, "samples_per_s": m / ms * 1e3, "tflops": tf,
-                                "frac": tf / peak if peak else None,
-                                "padded_flops_per_sample": 3 * flops}
+                                "frac": tf / peak if peak else None, "flops_per_sample": 3 * flops,
+                                "padded_flops_per_sample": 3 * padded}
     return out
 
 
