@@ -203,9 +203,15 @@ def kish_ess(G, params, n, seed, it, root=0, vegas=None, flow=None, defensive=0.
     else:
         x, w = _flow_draw(flow, seed, it, 3, n, defensive)
         plan.run(seed, it, points=x, point_w=w)
-    f = plan.per_sample[0, root, 0].double()
+    return kish_fraction(plan.per_sample[0, root, 0])
+
+
+def kish_fraction(f):
+    """(sum |f|)^2 / (n sum f^2) of the n weighted values f (a tensor), in
+    FP64; 0 when every value is 0."""
+    f = f.double()
     a1, a2 = float(f.abs().sum().item()), float((f * f).sum().item())
-    return a1 * a1 / (n * a2) if a2 > 0 else 0.0
+    return a1 * a1 / (f.numel() * a2) if a2 > 0 else 0.0
 
 
 def bootstrap_ratio(num, den, stat, resamples=4000, seed=0, level=0.95):

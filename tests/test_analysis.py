@@ -118,3 +118,18 @@ def test_combine_iterations():
     assert abs(c.mean() - 1.0) < 0.02
     with pytest.raises(ValueError):
         A.combine_iterations([1.0, 2.0], [1.0, 0.0])
+
+
+def test_kish_fraction_matches_the_oracle():
+    """The host side of the bench's Kish effective sample size fraction
+    (driver.kish_fraction) against the oracle's Kish ESS divided by the
+    sample count, on heavy-tailed signed weights and the degenerate cases."""
+    import torch
+    from oracle import integrand as oig
+    from paper_2403_18840_gb300 import driver
+    rng = np.random.default_rng(8)
+    v = rng.standard_cauchy(50000) * rng.choice([-1.0, 1.0], 50000)
+    assert driver.kish_fraction(torch.tensor(v, dtype=torch.float32)) == pytest.approx(
+        oig.kish_ess(v.astype(np.float32)) / v.size, rel=1e-12)
+    assert driver.kish_fraction(torch.full((64,), 2.5)) == pytest.approx(1.0, rel=1e-15)
+    assert driver.kish_fraction(torch.zeros(16)) == 0.0
