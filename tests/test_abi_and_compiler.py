@@ -170,3 +170,57 @@ def test_spline_flow_entry_points_validate_arguments_before_any_device_work():
     assert lib.fd_nsf_train(None, p, p, 4, 1, 1e-3, None, None) == 1
     assert lib.fd_nsf_get_params(None, f32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 4) == 1
     assert lib.fd_nsf_param_count(None) == 0
+
+
+@pytest.mark.parametrize("case", [
+    "vegas_create_dim", "vegas_create_bins", "vegas_set_edges", "vegas_update", "vegas_update_batch",
+    "map_samples", "eval_null_graphs", "eval_no_graphs", "eval_null_graph", "accumulate", "flow_create_dim",
+    "flow_create_hidden", "flow_sample", "flow_set_tensor_path", "flow_grad", "flow_train", "mcmc_chains",
+    "mcmc_estimate", "nsf_create_small", "nsf_create_large", "nsf_set_tensor_path", "postprocess",
+    "wait_polls", "graph_load", "measure_peak"])
+def test_entry_points_reject_invalid_arguments_on_the_host(case):
+    # every entry point answers a null handle or pointer, or a size out of
+    # its documented range, with FD_EINVAL and a message before any device
+    # work (this runs without a device)
+    lib = L.lib()
+    f32 = np.zeros(64, dtype=np.float32)
+    p = f32.ctypes.data
+    f64 = np.zeros(64, dtype=np.float64)
+    pd = f64.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    par = L.fd_params(1.0, 1.0, 1.0, 1.0, 1.0, 6.0, 1, 0)
+    gi = (ctypes.c_int32 * 1)(0)
+    null_graph = (ctypes.c_void_p * 1)(None)
+    calls = {
+        "vegas_create_dim": lambda: lib.fd_vegas_create(0, 1024, ctypes.byref(h)),
+        "vegas_create_bins": lambda: lib.fd_vegas_create(3, 0, ctypes.byref(h)),
+        "vegas_set_edges": lambda: lib.fd_vegas_set_edges(None, pd),
+        "vegas_update": lambda: lib.fd_vegas_update(None, 0.5, None),
+        "vegas_update_batch": lambda: lib.fd_vegas_update_batch(None, -1, 0.5, None),
+        "map_samples": lambda: lib.fd_map_samples(None, 1, 0, 0, 16, 3, None, p, None),   # x is required
+        "eval_null_graphs": lambda: lib.fd_integrand_eval(None, 1, ctypes.byref(par), gi, 1, None, None, None,
+                                                          1, 0, 16, p, None, None),
+        "eval_no_graphs": lambda: lib.fd_integrand_eval(null_graph, 0, ctypes.byref(par), gi, 1, None, None,
+                                                        None, 1, 0, 16, p, None, None),
+        "eval_null_graph": lambda: lib.fd_integrand_eval(null_graph, 1, ctypes.byref(par), gi, 1, None, None,
+                                                         None, 1, 0, 16, p, None, None),
+        "accumulate": lambda: lib.fd_accumulate(None, 1, 1, 1, p, None),
+        "flow_create_dim": lambda: lib.fd_flow_create(0, 8, 128, 1, ctypes.byref(h)),
+        "flow_create_hidden": lambda: lib.fd_flow_create(19, 8, 64, 1, ctypes.byref(h)),
+        "flow_sample": lambda: lib.fd_flow_sample(None, 1, 0, 0, 16, p, p, None),
+        "flow_set_tensor_path": lambda: lib.fd_flow_set_tensor_path(None, 2),
+        "flow_grad": lambda: lib.fd_flow_grad(None, p, p, 16, p, None, None),
+        "flow_train": lambda: lib.fd_flow_train(None, p, p, 16, 1, 1e-3, None, None),
+        "mcmc_chains": lambda: lib.fd_mcmc_chains(None, 1, 16, 1, 16, 4, 0.5, 1, 0, 0, p, p, None),
+        "mcmc_estimate": lambda: lib.fd_mcmc_estimate(None, 1, 16, 4, p, None),
+        "nsf_create_small": lambda: lib.fd_nsf_create(1, 8, ctypes.byref(h)),
+        "nsf_create_large": lambda: lib.fd_nsf_create(25, 8, ctypes.byref(h)),
+        "nsf_set_tensor_path": lambda: lib.fd_nsf_set_tensor_path(None, 0),
+        "postprocess": lambda: lib.fd_postprocess(0, pd, pd, pd, 1.0, 1.0, 1.0, pd, pd, pd, pd),
+        "wait_polls": lambda: lib.fd_debug_set_wait_polls(1 << 32),
+        "graph_load": lambda: lib.fd_graph_load(None, 0, ctypes.byref(h)),
+        "measure_peak": lambda: lib.fd_measure_peak(9, pd),
+    }
+    assert calls[case]() == L.FD_EINVAL
+    assert lib.fd_last_error()
+    assert h.value is None
