@@ -50,4 +50,4 @@ def test_flow_beats_vegas_at_order5():
           % (cmp["ci95"]["variance_gain_median"], cmp["ci95"]["variance_gain_pooled"],
              cmp["ci95"]["flow_over_vegas_median"], cmp["ci95"]["flow_over_vegas"]))
     assert cmp["ci95"]["variance_gain_median"][0] > 1.0
-    assert cmp["means_agree_sigma"] < 4.0
+    assert cmp["means_agree_sigma"] < 3.0                 # measured 0.8 - 1.2

@@ -118,13 +118,15 @@ def test_mcmc_recovers_the_fock_closed_form(api, sampler):
     P = conventions.ueg_params(cfg["rs"], cfg["T_over_TF"], cfg["lam_over_kF"], 1.0)
     ref = _fock_quad(P, P.kext)
     print(sampler, "MCMC Fock", out[0], "ref", ref, "accepted", out[2, 0])
-    assert abs(out[0, 0] - ref) < 5.0 * math.sqrt(out[0, 1]), (out[0], ref)
+    # six estimates over the three samplers and two calls: 3.5 sigma each keeps the
+    # two-sided 3-sigma p-value 0.0027 overall (measured |z| 0.44 - 0.97 on the first calls)
+    assert abs(out[0, 0] - ref) < 3.5 * math.sqrt(out[0, 1]), (out[0], ref)
     assert out[1, 0] == 0.0                                  # the Fock self-energy is static: Im = 0
     assert 0.02 < out[2, 0] <= 1.0
     # continuing the same chains: a second call, estimate again consistent
     _, _, out2 = driver.mcmc(G, p, V, flow, C, S, 0.5, seed=9, it=101, chains=ch, plan=plan)
     out2 = out2.cpu().numpy()
-    assert abs(out2[0, 0] - ref) < 5.0 * math.sqrt(out2[0, 1])
+    assert abs(out2[0, 0] - ref) < 3.5 * math.sqrt(out2[0, 1]), (out2[0], ref)
 
 
 def test_long_chains_agree_with_importance_sampling_order3(api):
@@ -147,4 +149,4 @@ def test_long_chains_agree_with_importance_sampling_order3(api):
     _, _, out = driver.mcmc(G, p, V, None, C, S, 0.5, seed=7, it=601, chains=ch, plan=plan2)
     out = out.cpu().numpy()
     print("order 3: VEGAS IS %.6f +- %.6f, VEGAS-MCMC %.6f +- %.6f" % (ref, ref_err, out[0, 0], math.sqrt(out[0, 1])))
-    assert abs(out[0, 0] - ref) < 4.0 * math.sqrt(out[0, 1] + ref_err ** 2)
+    assert abs(out[0, 0] - ref) < 3.0 * math.sqrt(out[0, 1] + ref_err ** 2)   # measured 1.2 sigma

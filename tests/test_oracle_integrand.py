@@ -110,7 +110,7 @@ def test_free_density():
     m, v = ig.mean_var(W)
     mp.mp.dps = 30
     ref = float(mp.re(-mp.polylog(1.5, -mp.exp(P.beta * P.mu)) / (4 * mp.pi ** 1.5 * mp.mpf(P.beta) ** 1.5)))
-    assert abs(m - ref) < 4.5 * math.sqrt(v)
+    assert abs(m - ref) < 3.0 * math.sqrt(v), (m, math.sqrt(v), ref)
     # the T -> 0 limit of the same formula is the r_s density 3 / (4 pi r_s^3)
     P0 = conventions.ueg_params(1.0, 1e-4, 0.5, 0.0)
     n0 = float(mp.re(-mp.polylog(1.5, -mp.exp(P0.beta * P0.mu)) / (4 * mp.pi ** 1.5 * mp.mpf(P0.beta) ** 1.5)))
@@ -165,7 +165,7 @@ def test_rainbow_diagram_vs_2d_quadrature():
         return qq * fprime * s * math.log(((k + qq) ** 2 + P.Lambda) / ((k - qq) ** 2 + P.Lambda))
     val, _ = integrate.quad(integrand, 0, P.kc, points=[P.kF], limit=500)
     ref = -val / (math.pi * P.kext)   # -int V f' Sx with the Fock angular kernel
-    assert abs(m - ref) < 4.5 * math.sqrt(v) + 1e-4 * abs(ref), (m, math.sqrt(v), ref)
+    assert abs(m - ref) < 3.0 * math.sqrt(v) + 1e-4 * abs(ref), (m, math.sqrt(v), ref)   # + the quadrature's tolerance
 
 
 def test_second_order_quasiparticle_weight_below_one():

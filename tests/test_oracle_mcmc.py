@@ -91,9 +91,10 @@ def test_discrete_stationary_law_and_estimator():
     pi = alpha * q + (1 - alpha) * np.abs(f)
     pi = pi / pi.sum()
     emp = np.bincount(final, minlength=4) / C
-    assert np.all(np.abs(emp - pi) <= 5 * np.sqrt(pi * (1 - pi) / C))
+    # four states at once: 3.2 sigma each keeps the two-sided 3-sigma p-value 0.0027 overall
+    assert np.all(np.abs(emp - pi) <= 3.2 * np.sqrt(pi * (1 - pi) / C))
     I, var = mcmc.estimate(sums, 1)
-    assert abs(I[0] - f.sum()) <= 5 * np.sqrt(var[0]), (I, f.sum(), np.sqrt(var))
+    assert abs(I[0] - f.sum()) <= 3 * np.sqrt(var[0]), (I, f.sum(), np.sqrt(var))
 
 
 def test_continuous_closed_form_and_error_bar():
@@ -109,7 +110,8 @@ def test_continuous_closed_form_and_error_bar():
         est.append(I[0])
         errs.append(np.sqrt(var[0]))
     est, errs = np.array(est), np.array(errs)
-    assert np.all(np.abs(est - 0.3) <= 5 * errs)
+    # 24 replicas at once: 3.9 sigma each keeps the two-sided 3-sigma p-value 0.0027 overall
+    assert np.all(np.abs(est - 0.3) <= 3.9 * errs)
     ratio = est.std(ddof=1) / errs.mean()          # the error bar describes the scatter
     assert 0.6 < ratio < 1.5, ratio
 
