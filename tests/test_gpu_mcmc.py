@@ -126,6 +126,7 @@ def test_mcmc_recovers_the_fock_closed_form(api, sampler):
     # continuing the same chains: a second call, estimate again consistent
     _, _, out2 = driver.mcmc(G, p, V, flow, C, S, 0.5, seed=9, it=101, chains=ch, plan=plan)
     out2 = out2.cpu().numpy()
+    print(sampler, "MCMC Fock, continued", out2[0], "ref", ref)
     assert abs(out2[0, 0] - ref) < 3.5 * math.sqrt(out2[0, 1]), (out2[0], ref)
 
 
