@@ -16,6 +16,11 @@
  *  - No exception crosses the boundary: every failure returns a status other
  *    than FD_OK and sets a thread-local message readable by fd_last_error().
  *    Arguments are validated before any launch; on error nothing is launched.
+ *  - Host threads: calls on distinct handles may come from several host
+ *    threads at once (launch descriptors are built in thread-local storage);
+ *    one handle is not to be used by two threads at the same time, and the
+ *    no-allocation entry point's shared scratch array is serialised on the
+ *    stream by the caller (see fd_integrand_eval_stats_noalloc).
  *  - Hypercube points are structure-of-arrays: x[d * n + i] for dimension d
  *    and sample i (FP32).
  *  - Units: Rydberg, hbar^2/2m = 1, e^2 = 2: eps_k = k^2 - mu and

@@ -548,7 +548,7 @@ extern "C" fd_status fd_vegas_update(fd_vegas *m, double alpha, void *stream) {
 extern "C" fd_status fd_vegas_update_batch(fd_vegas *const *maps, int32_t n_maps, double alpha, void *stream) {
     FD_REQUIRE(maps && n_maps >= 1 && n_maps <= 256, "1..256 maps are required");
     FD_REQUIRE(alpha >= 0.0 && alpha <= 4.0 && std::isfinite(alpha), "alpha out of range");
-    static BatchMaps B;
+    static thread_local BatchMaps B;   // kernel argument (copied at launch); per host thread
     int nb = -1, dmax = 0;
     for (int k = 0; k < n_maps; ++k) {
         FD_REQUIRE(maps[k], "null map");
