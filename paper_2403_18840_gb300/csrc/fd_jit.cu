@@ -1078,7 +1078,10 @@ extern "C" fd_status fd_graph_jit(fd_graph *g, const fd_jit_options *opt, const 
         const fd_status st = build_cubin(P, maxrreg, cubin);
         if (st != FD_OK) return st;
         if (!path.empty()) {
-            const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+            // private to this process and thread: a concurrent writer of the same
+            // entry renames its own complete file
+            const std::string tmp = path + ".tmp" + std::to_string((long long)getpid()) + "." +
+                                    std::to_string(std::hash<std::thread::id>{}(std::this_thread::get_id()));
             std::ofstream f(tmp, std::ios::binary);
             f.write(cubin.data(), (std::streamsize)cubin.size());
             f.close();
