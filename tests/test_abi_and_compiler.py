@@ -224,3 +224,32 @@ def test_entry_points_reject_invalid_arguments_on_the_host(case):
     assert calls[case]() == L.FD_EINVAL
     assert lib.fd_last_error()
     assert h.value is None
+
+
+def test_last_error_is_per_host_thread():
+    # the boundary's error message is thread-local: threads failing different
+    # calls at once each read back their own message (no device involved)
+    import threading
+    lib = L.lib()
+    got, barrier = {}, threading.Barrier(8)
+
+    def work(k):
+        h = ctypes.c_void_p()
+        barrier.wait()
+        for _ in range(200):
+            if k % 2:
+                st = lib.fd_vegas_create(0, 64, ctypes.byref(h))
+            else:
+                st = lib.fd_vegas_create(3, 0, ctypes.byref(h))
+            msg = lib.fd_last_error()
+            if st != L.FD_EINVAL or msg != (b"dim out of range" if k % 2 else b"n_bins out of range"):
+                got[k] = (st, msg)
+                return
+        got[k] = "ok"
+
+    ts = [threading.Thread(target=work, args=(k,)) for k in range(8)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert all(v == "ok" for v in got.values()) and len(got) == 8, got
