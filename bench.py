@@ -18,7 +18,6 @@ data-path collective; `replicas.py`); rank 0 prints.
 """
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys

@@ -16,7 +16,6 @@ its target is |f(map(y))| J_map(y), which the kernel returns when it is given
 the map together with the points.
 """
 import math
-import time
 
 import numpy as np
 import torch

@@ -48,7 +48,6 @@ families and temporaries; loop momenta, Jacobians and root accumulators live
 in registers or fixed extra slots of the interpreter.
 """
 import collections
-import itertools
 import math
 import struct
 import sys

@@ -1,6 +1,5 @@
 """Pins for the affine coupling flow oracle (Appendix A, Eqs. NFtransform, coupling_layer)."""
 import numpy as np
-import pytest
 
 import workloads
 from oracle import flow

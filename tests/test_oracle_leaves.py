@@ -1,6 +1,5 @@
 """Pin the oracle's counterterm leaves against mpmath high-precision derivatives
 of the undifferentiated definitions (Eqs. propagator, green_ct, interaction_ct)."""
-import math
 
 import mpmath as mp
 import numpy as np

@@ -2,7 +2,6 @@
 sigma_xi_dmu_dlambda, eff_mass_ratio) against sympy series algebra."""
 import math
 
-import numpy as np
 import sympy as sp
 
 from oracle import postprocess
