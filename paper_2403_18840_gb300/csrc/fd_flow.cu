@@ -1434,12 +1434,7 @@ __device__ __forceinline__ bool wait_warp(uint64_t *bar, uint32_t k) {
     return __all_sync(0xffffffffu, ok);
 }
 
-// 8 / 16 consecutive FP32 columns of this thread's TMEM lane (asynchronous: wait_ld before use)
-__device__ __forceinline__ void ld8_async(uint32_t taddr, uint32_t *v) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                 : "r"(taddr));
-}
+// 16 consecutive FP32 columns of this thread's TMEM lane (asynchronous: wait_ld before use)
 __device__ __forceinline__ void ld16_async(uint32_t taddr, uint32_t *v) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"

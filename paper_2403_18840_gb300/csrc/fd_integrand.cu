@@ -104,7 +104,6 @@ __device__ __forceinline__ float pick(const float (&a)[NK][P], uint32_t idx, int
 __device__ __forceinline__ uint32_t f_d(uint64_t w) { return (uint32_t)(w >> 6) & 16383u; }
 __device__ __forceinline__ uint32_t f_a(uint64_t w) { return (uint32_t)(w >> 20) & 16383u; }
 __device__ __forceinline__ uint32_t f_b(uint64_t w) { return (uint32_t)(w >> 34) & 16383u; }
-__device__ __forceinline__ uint32_t f_c(uint64_t w) { return (uint32_t)(w >> 48) & 16383u; }
 
 // signed momentum sums from a 2-bit-per-variable mask, grid parts (h) and
 // remainders (l); k_ext is (0, 0, kext + kext_l)
