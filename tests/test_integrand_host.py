@@ -82,7 +82,7 @@ def _check(rel, label):
 
 
 @pytest.mark.parametrize("order,with_dk,n,seed", [(1, True, 16384, 71), (2, True, 16384, 72),
-                                                  (3, True, 8191, 73), (4, True, 1537, 74)])
+                                                  (3, True, 8191, 73), (4, True, 1537, 74), (5, False, 1025, 70)])
 def test_host_build_per_sample_parity(exe, tmp_path, order, with_dk, n, seed):
     roots = fdgraph.graph_roots(order, with_dk=with_dk)
     tape = api.tape_bytes(order, roots)
