@@ -133,3 +133,33 @@ def test_kish_fraction_matches_the_oracle():
         oig.kish_ess(v.astype(np.float32)) / v.size, rel=1e-12)
     assert driver.kish_fraction(torch.full((64,), 2.5)) == pytest.approx(1.0, rel=1e-15)
     assert driver.kish_fraction(torch.zeros(16)) == 0.0
+
+
+def test_production_protocol_recovers_a_known_model():
+    """The App. B protocol (production_run.protocol) on synthetic partial sums
+    with a known answer: m*/m(T) = m0 (1 + alpha T / T_F), partial sums
+    S_N = m*/m(T) + c q(lambda)^N that converge fastest at lambda_best (the
+    variation of the last three sums there well above the noise), and
+    Gaussian noise of known size on every sum.  The protocol must pick
+    lambda_best at every temperature and recover m0 and alpha within three
+    of its own error bars."""
+    from paper_2403_18840_gb300 import production_run as PR
+    m0, alpha, lam_best, c = 0.955, 1.8, 1.375, 1.0
+    lams, temps = [1.0, 1.25, 1.375, 1.5, 1.75], [1.0 / 40.0, 1.0 / 30.0, 1.0 / 25.0, 1.0 / 20.0]
+    rng = np.random.default_rng(31)
+
+    def runner(lam, T):
+        q = 0.1 + abs(lam - lam_best)                 # the series' convergence ratio
+        sig = np.array([1e-5, 2e-5, 5e-5, 1e-4, 2e-4, 4e-4])
+        exact = m0 * (1.0 + alpha * T) + c * q ** np.arange(1, 7)
+        return {"meff": exact + rng.normal(0.0, 1.0, 6) * sig, "meff_err": sig}
+
+    res = PR.protocol(runner, lams, temps)
+    assert [p["lam_over_kF"] for p in res["per_T"]] == [lam_best] * len(temps)
+    T0 = res["T0"]
+    assert abs(T0["meff_T0"] - m0) < 3.0 * T0["err_T0"], T0
+    assert abs(T0["alpha"] - alpha) < 3.0 * T0["dalpha"], T0
+    assert T0["err_T0"] < 2e-2
+    # one temperature: a choice but no extrapolation
+    one = PR.protocol(runner, lams, temps[:1])
+    assert one["T0"] is None and one["per_T"][0]["lam_over_kF"] == lam_best
