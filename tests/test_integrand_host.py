@@ -221,15 +221,19 @@ def test_double_float_exp_and_reciprocal(df_exe, tmp_path):
     assert worst_e <= 1e-13 and worst_r <= 4e-14
 
 
-@pytest.mark.parametrize("order,rs,kext,n,seed", [(3, 2.0, 0.4, 4097, 81), (3, 4.0, 1.6, 4097, 82),
-                                                  (5, 4.0, 2.0, 513, 83)])
-def test_host_build_at_other_densities(exe, tmp_path, order, rs, kext, n, seed):
+@pytest.mark.parametrize("order,rs,T,lam,kext,n,seed", [(3, 2.0, 1.0 / 25.0, 1.0, 0.4, 4097, 81),
+                                                         (3, 4.0, 1.0 / 25.0, 1.0, 1.6, 4097, 82),
+                                                         (5, 4.0, 1.0 / 25.0, 1.0, 2.0, 513, 83),
+                                                         (4, 5.0, 1.0 / 40.0, 1.375, 1.0, 1537, 84)])
+def test_host_build_at_other_densities(exe, tmp_path, order, rs, T, lam, kext, n, seed):
     """The batched configuration's other densities and external momenta
-    (r_s 2 and 4, k up to 2 k_F): k_F, mu and beta change, and with them the
-    loop momenta's grid and the instance split of the parameters."""
+    (r_s 2 and 4, k up to 2 k_F) and the production point of the effective
+    mass (r_s 5, T = T_F / 40, lambda_R = 1.375 k_F: sharper Fermi factors):
+    k_F, mu and beta change, and with them the loop momenta's grid and the
+    instance split of the parameters."""
     roots = fdgraph.graph_roots(order, with_dk=order < 5)
-    P = conventions.ueg_params(rs, 1.0 / 25.0, 1.0, kext)
+    P = conventions.ueg_params(rs, T, lam, kext)
     x = ophilox.uniforms(seed, 0, 0, np.arange(n), 4 * order - 1)
     f = run_host(exe, tmp_path, api.tape_bytes(order, roots), order, roots, x, P)
     ref, mag = oig.eval_roots(x, roots, P, with_l1=True)
-    _check(_rel(f, ref, mag), "host order %d at r_s %g, k = %g k_F" % (order, rs, kext))
+    _check(_rel(f, ref, mag), "host order %d at r_s %g, T = %.4f T_F, k = %g k_F" % (order, rs, T, kext))
